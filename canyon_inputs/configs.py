@@ -1,0 +1,66 @@
+"""Named synthetic workloads (input generation only; none of the method's arithmetic).
+
+Each workload fixes the mesh recipe, the particle count per element, the wall
+treatment, the precision mode and the run length. The numbers follow the
+paper's street-canyon set-up (Section 3: Re ~ 12,000 on U0 and H, so
+nu = 1/12000 with U0 = H = 1; log-law inflow; source at street level in the
+canyon centre) and the workload sizes of this project:
+
+  canyon_wf_small   ~1,600 triangles, wall functions (walls moved y_p = 0.05H
+                    into the fluid), 64 particles per element (~100k), 2x2x2
+                    velocity bins, C0 = 2.1, 100 steps at CFL 0.5, FP64.
+  canyon_er_full    ~40k triangles graded to a first-cell height nu/u* at the
+                    walls, elliptic relaxation solved by P1 finite elements every
+                    step, 256 particles per element (~10.3M), FP32 particle state
+                    with FP64 statistics and CG, 500 steps.
+
+The time step follows a CFL rule that depends on the mesh and the initial
+condition only: dt = CFL * min_e(2 r_e) / U_ref, with r_e the inradius and
+U_ref the largest mean speed of the initial log-law profile plus five standard
+deviations of the initial velocity fluctuation.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+from .mesh import canyon_mesh, inradius
+
+NU = 1.0 / 12000.0
+USTAR = 0.05
+
+
+def yplus30(nu: float = NU, ustar: float = USTAR) -> float:
+    """Wall distance at y+ = 30 (Section 3: first point of the wall-function grid)."""
+    return 30.0 * nu / ustar
+
+
+WORKLOADS = {
+    "canyon_wf_small": dict(
+        mesh=dict(H=1.0, W=1.0, B=2.0, T=2.0, offset=yplus30(), h=0.071, y1=None, seed=0),
+        wall_model="wf", per_element=64, bins=(2, 2, 2), C0=2.1, steps=100, cfl=0.5,
+        precision="fp64", seed=0, k0=1e-3),
+    "canyon_er_full": dict(
+        mesh=dict(H=1.0, W=1.0, B=2.0, T=2.0, offset=0.0, h=0.017, y1=NU / USTAR,
+                  growth=1.2, seed=0),
+        wall_model="er", per_element=256, bins=(2, 2, 2), C0=2.1, steps=500, cfl=0.5,
+        precision="fp32", seed=0, k0=1e-3),
+}
+
+
+def build_mesh(name_or_cfg) -> dict:
+    cfg = WORKLOADS[name_or_cfg] if isinstance(name_or_cfg, str) else name_or_cfg
+    return canyon_mesh(**cfg["mesh"])
+
+
+def reference_speed(mesh: dict, *, k0: float, ustar: float = USTAR, kappa: float = 0.41,
+                    E: float = 8.5, nu: float = NU) -> float:
+    """Largest initial mean speed plus five initial standard deviations."""
+    d_top = mesh["T"] - mesh["H"]
+    u_top = ustar / kappa * math.log(E * d_top * ustar / nu)
+    return u_top + 5.0 * math.sqrt(2.0 / 3.0 * k0)
+
+
+def cfl_dt(mesh: dict, *, cfl: float, k0: float) -> float:
+    return float(cfl * np.min(2.0 * inradius(mesh)) / reference_speed(mesh, k0=k0))

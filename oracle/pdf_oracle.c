@@ -1,0 +1,1127 @@
+/* pdf_oracle.c -- TEST INFRASTRUCTURE ONLY.
+ *
+ * Plain FP64, single-threaded CPU oracle of the per-particle time step of the
+ * joint velocity-frequency-scalar PDF method (Bakosi, Franzese & Boybeyi,
+ * Section 2 and Section 3). Everything is written out in the order the paper
+ * states it, with loops over particles, elements and nodes and no blocking,
+ * fusion or reordering. Only the test-suite, the smoke check and the
+ * benchmark's CPU-baseline leg may load it; it shares nothing with the CUDA
+ * library.
+ *
+ * Where the paper is silent the oracle takes these readings (each one is the
+ * same for the CUDA path, which is written separately):
+ *  - forward Euler-Maruyama: every right-hand side uses the statistics S^n and
+ *    the particle state at step n (Section 2, end of 2.2);
+ *  - the particle velocity has three components, mean fields are
+ *    two-dimensional (d/dz = 0, <W> = 0, <uw> = <vw> = 0 inside the model);
+ *  - element moments are ensemble averages over the element's particles
+ *    (divisor n); node values are particle-count weighted means over the
+ *    incident elements (periodic partners merged);
+ *  - <phi|V> uses equal-population bins: sort by (U, id), split, then by
+ *    (V, id), then by (W, id); an element with fewer particles than bins uses
+ *    its element mean (IEM);
+ *  - t_m, S_omega and L are element constants evaluated at the centroid;
+ *    grad <U> is the element P1 gradient; the Laplacian of <U> is the element
+ *    divergence of the area-weighted recovered node gradient;
+ *  - G_ij and C0*eps are formed at the nodes and interpolated linearly to the
+ *    particle together with <U>, <V> and <omega>;
+ *  - wall conditions: Eqs. wall-normal-velocity..wall-omega with the wall
+ *    statistics interpolated along the hit edge (wall functions); specular
+ *    reflection with U_R = -U_I (elliptic relaxation); symmetry at the top;
+ *    positions are mirrored about the crossed edge, at most reflect_max times;
+ *  - host element: the lowest-id element whose barycentric coordinates are all
+ *    >= 0 (brute force over a bucket grid of element bounding boxes).
+ *
+ * Parity pins live in the test-suite; the functions without an independent
+ * pin are listed in the oracle's README header below.
+ *   parity unpinned: the elliptic-relaxation wall value wp_ij = -4.5 eps n_i n_j
+ *   (taken from the companion work the paper cites, not stated in the paper).
+ */
+#include "pdf_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#ifndef M_PI
+#define M_PI 3.14159265358979323846
+#endif
+
+typedef struct seg_t {
+    double ax, ay, bx, by; /* end points */
+    double nx, ny;         /* unit normal pointing into the fluid */
+    int na, nb;            /* node ids of the end points */
+    int tag;               /* 1 wall, 2 top */
+} seg_t;
+
+struct orc_ctx {
+    orc_params p;
+    int nn, nt, nb;
+    double* xy;
+    int *tri, *etag, *pair, *rep;
+    double* area2;
+    /* node class -> incident elements */
+    int *n2e_off, *n2e;
+    /* reflecting segments (three periodic images each) */
+    int nseg;
+    seg_t* seg;
+    /* node wall data */
+    double *wnx, *wny, *wdist;
+    unsigned char* is_wall;
+    /* bucket grid */
+    int gx, gy;
+    double gx0, gy0, gdx, gdy;
+    int *gb_off, *gb;
+    /* particles */
+    int np, step;
+    double *x, *y, *u, *v, *w, *om, *psi;
+    uint32_t* id;
+    int* elem;
+    unsigned char* bin;
+    /* statistics */
+    int stats_valid;
+    double *en, *emean, *eR, *epsivar, *ecm;
+    double *nwt, *nmean, *nR, *nke, *npsivar;
+    double *eder, *ngrad, *npack, *nwp;
+    int cg_iters;
+    /* FE matrix (CSR over canonical nodes) */
+    int *rowptr, *colidx;
+    double* aval;
+};
+
+/* ------------------------------------------------------------------------- */
+/* Philox4x32-10 (Salmon, Moraes, Dror & Shaw 2011, "Parallel random numbers:  */
+/* as easy as 1, 2, 3"): ten rounds of the multiply-xor round function with    */
+/* the Weyl key schedule.                                                      */
+/* ------------------------------------------------------------------------- */
+void orc_philox4x32_10(const uint32_t key[2], const uint32_t ctr[4], uint32_t out[4]) {
+    const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+    const uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+    uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int r = 0; r < 10; ++r) {
+        uint64_t p0 = (uint64_t)M0 * c0;
+        uint64_t p1 = (uint64_t)M1 * c2;
+        uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        c0 = hi1 ^ c1 ^ k0;
+        c1 = lo1;
+        c2 = hi0 ^ c3 ^ k1;
+        c3 = lo0;
+        k0 += W0;
+        k1 += W1;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+static void orc_key(uint64_t seed, uint32_t case_id, uint32_t key[2]) {
+    key[0] = (uint32_t)seed;
+    key[1] = (uint32_t)(seed >> 32) ^ case_id;
+}
+
+/* uniform in (0, 1]: (w + 1) * 2^-32 */
+static double orc_unif(uint32_t w) { return ((double)w + 1.0) * (1.0 / 4294967296.0); }
+
+/* Box & Muller (1958) */
+static void orc_box_muller(double ua, double ub, double* za, double* zb) {
+    double r = sqrt(-2.0 * log(ua));
+    double t = 2.0 * M_PI * ub;
+    *za = r * cos(t);
+    *zb = r * sin(t);
+}
+
+/* The eight Gaussians of one particle-step: counter (id, step, call, 0),
+ * call 0 -> z0..z3, call 1 -> z4..z7. */
+void orc_gauss8(uint64_t seed, uint32_t case_id, uint32_t id, uint32_t step, double z[8]) {
+    uint32_t key[2], ctr[4], o[4];
+    orc_key(seed, case_id, key);
+    for (uint32_t call = 0; call < 2; ++call) {
+        ctr[0] = id; ctr[1] = step; ctr[2] = call; ctr[3] = 0;
+        orc_philox4x32_10(key, ctr, o);
+        orc_box_muller(orc_unif(o[0]), orc_unif(o[1]), &z[4 * call + 0], &z[4 * call + 1]);
+        orc_box_muller(orc_unif(o[2]), orc_unif(o[3]), &z[4 * call + 2], &z[4 * call + 3]);
+    }
+}
+
+/* ------------------------------------------------------------------------- */
+/* geometry                                                                   */
+/* ------------------------------------------------------------------------- */
+static double orient(double px, double py, double qx, double qy, double rx, double ry) {
+    return (qx - px) * (ry - py) - (qy - py) * (rx - px);
+}
+
+/* barycentric coordinate k of (x, y) in element e: orient(a_{k+1}, a_{k+2}, P) / (2A) */
+static double bary(const orc_ctx* c, int e, int k, double x, double y) {
+    int a = c->tri[3 * e + (k + 1) % 3], b = c->tri[3 * e + (k + 2) % 3];
+    return orient(c->xy[2 * a], c->xy[2 * a + 1], c->xy[2 * b], c->xy[2 * b + 1], x, y) / c->area2[e];
+}
+
+/* gradient of barycentric coordinate k of element e */
+static void grad_bary(const orc_ctx* c, int e, int k, double* gx, double* gy) {
+    int a = c->tri[3 * e + (k + 1) % 3], b = c->tri[3 * e + (k + 2) % 3];
+    *gx = -(c->xy[2 * b + 1] - c->xy[2 * a + 1]) / c->area2[e];
+    *gy = (c->xy[2 * b] - c->xy[2 * a]) / c->area2[e];
+}
+
+int32_t orc_locate(const orc_ctx* c, double x, double y) {
+    int ix = (int)floor((x - c->gx0) / c->gdx), iy = (int)floor((y - c->gy0) / c->gdy);
+    if (ix < 0) ix = 0;
+    if (iy < 0) iy = 0;
+    if (ix >= c->gx) ix = c->gx - 1;
+    if (iy >= c->gy) iy = c->gy - 1;
+    int cell = iy * c->gx + ix, best = -1;
+    for (int q = c->gb_off[cell]; q < c->gb_off[cell + 1]; ++q) {
+        int e = c->gb[q];
+        if (best >= 0 && e > best) continue;
+        if (bary(c, e, 0, x, y) >= 0.0 && bary(c, e, 1, x, y) >= 0.0 && bary(c, e, 2, x, y) >= 0.0)
+            best = e;
+    }
+    return best;
+}
+
+static int cmp_int2(const void* a, const void* b) {
+    const long long* x = (const long long*)a;
+    const long long* y = (const long long*)b;
+    if (x[0] != y[0]) return x[0] < y[0] ? -1 : 1;
+    if (x[1] != y[1]) return x[1] < y[1] ? -1 : 1;
+    return 0;
+}
+
+static void* xcalloc(size_t n, size_t s) { return calloc(n ? n : 1, s); }
+
+void orc_destroy(orc_ctx* c) {
+    if (!c) return;
+    void* ptrs[] = {c->xy, c->tri, c->etag, c->pair, c->rep, c->area2, c->n2e_off, c->n2e, c->seg,
+                    c->wnx, c->wny, c->wdist, c->is_wall, c->gb_off, c->gb, c->x, c->y, c->u, c->v,
+                    c->w, c->om, c->psi, c->id, c->elem, c->bin, c->en, c->emean, c->eR, c->epsivar,
+                    c->ecm, c->nwt, c->nmean, c->nR, c->nke, c->npsivar, c->eder, c->ngrad, c->npack,
+                    c->nwp, c->rowptr, c->colidx, c->aval};
+    for (size_t i = 0; i < sizeof(ptrs) / sizeof(ptrs[0]); ++i) free(ptrs[i]);
+    free(c);
+}
+
+static int build_fe_pattern(orc_ctx* c);
+
+orc_ctx* orc_create(const orc_params* p, int32_t nnode, const double* xy, int32_t ntri,
+                    const int32_t* tri, const int32_t* edge_tag, const int32_t* pair,
+                    int32_t* status) {
+    *status = ORC_ERR_MESH;
+    if (nnode < 3 || ntri < 1 || p->nb1 < 1 || p->nb2 < 1 || p->nb3 < 1) { *status = ORC_ERR_ARG; return NULL; }
+    orc_ctx* c = (orc_ctx*)xcalloc(1, sizeof(orc_ctx));
+    c->p = *p;
+    c->nn = nnode; c->nt = ntri; c->nb = p->nb1 * p->nb2 * p->nb3;
+    c->xy = (double*)malloc(sizeof(double) * 2 * nnode);
+    memcpy(c->xy, xy, sizeof(double) * 2 * nnode);
+    c->tri = (int*)malloc(sizeof(int) * 3 * ntri);
+    c->etag = (int*)malloc(sizeof(int) * 3 * ntri);
+    c->pair = (int*)malloc(sizeof(int) * nnode);
+    c->rep = (int*)malloc(sizeof(int) * nnode);
+    for (int i = 0; i < 3 * ntri; ++i) { c->tri[i] = tri[i]; c->etag[i] = edge_tag[i]; }
+    for (int i = 0; i < nnode; ++i) c->pair[i] = pair[i];
+    for (int i = 0; i < 3 * ntri; ++i)
+        if (c->tri[i] < 0 || c->tri[i] >= nnode || c->etag[i] < 0 || c->etag[i] > 3) goto fail;
+    for (int i = 0; i < nnode; ++i) {
+        int q = c->pair[i];
+        if (q >= nnode || (q >= 0 && c->pair[q] != i)) goto fail;
+        c->rep[i] = (q >= 0 && q < i) ? q : i;
+    }
+    c->area2 = (double*)malloc(sizeof(double) * ntri);
+    for (int e = 0; e < ntri; ++e) {
+        int a = c->tri[3 * e], b = c->tri[3 * e + 1], d = c->tri[3 * e + 2];
+        c->area2[e] = orient(xy[2 * a], xy[2 * a + 1], xy[2 * b], xy[2 * b + 1], xy[2 * d], xy[2 * d + 1]);
+        if (!(c->area2[e] > 0.0)) goto fail;
+    }
+    /* node class -> incident elements (sorted element ids, union over partners) */
+    {
+        int* cnt = (int*)xcalloc(nnode + 1, sizeof(int));
+        for (int e = 0; e < ntri; ++e)
+            for (int k = 0; k < 3; ++k) {
+                int a = c->tri[3 * e + k];
+                cnt[a + 1]++;
+                if (c->pair[a] >= 0) cnt[c->pair[a] + 1]++;
+            }
+        for (int i = 0; i < nnode; ++i) cnt[i + 1] += cnt[i];
+        c->n2e_off = (int*)xcalloc(nnode + 1, sizeof(int));
+        memcpy(c->n2e_off, cnt, sizeof(int) * (nnode + 1));
+        c->n2e = (int*)xcalloc(cnt[nnode], sizeof(int));
+        for (int e = 0; e < ntri; ++e)   /* increasing e: lists come out sorted */
+            for (int k = 0; k < 3; ++k) {
+                int a = c->tri[3 * e + k];
+                c->n2e[cnt[a]++] = e;
+                if (c->pair[a] >= 0) c->n2e[cnt[c->pair[a]]++] = e;
+            }
+        free(cnt);
+    }
+    /* reflecting segments and node wall normals */
+    {
+        int nb = 0;
+        for (int i = 0; i < 3 * ntri; ++i) if (c->etag[i] == 1 || c->etag[i] == 2) nb++;
+        c->nseg = 3 * nb;
+        c->seg = (seg_t*)xcalloc(c->nseg, sizeof(seg_t));
+        c->wnx = (double*)xcalloc(nnode, sizeof(double));
+        c->wny = (double*)xcalloc(nnode, sizeof(double));
+        c->is_wall = (unsigned char*)xcalloc(nnode, 1);
+        int s = 0;
+        for (int e = 0; e < ntri; ++e)
+            for (int k = 0; k < 3; ++k) {
+                int tag = c->etag[3 * e + k];
+                if (tag != 1 && tag != 2) continue;
+                int a = c->tri[3 * e + (k + 1) % 3], b = c->tri[3 * e + (k + 2) % 3];
+                double ax = xy[2 * a], ay = xy[2 * a + 1], bx = xy[2 * b], by = xy[2 * b + 1];
+                double len = hypot(bx - ax, by - ay);
+                double nx = -(by - ay) / len, ny = (bx - ax) / len;
+                for (int im = -1; im <= 1; ++im) {
+                    seg_t* g = &c->seg[s++];
+                    g->ax = ax + im * p->period; g->bx = bx + im * p->period;
+                    g->ay = ay; g->by = by; g->nx = nx; g->ny = ny;
+                    g->na = a; g->nb = b; g->tag = tag;
+                }
+                if (tag == 1) {
+                    int ends[2] = {a, b};
+                    for (int j = 0; j < 2; ++j) {
+                        int r = c->rep[ends[j]];
+                        c->wnx[r] += nx; c->wny[r] += ny; c->is_wall[r] = 1;
+                    }
+                }
+            }
+        for (int i = 0; i < nnode; ++i) {
+            int r = c->rep[i];
+            double l = hypot(c->wnx[r], c->wny[r]);
+            if (i == r && l > 0) { c->wnx[r] /= l; c->wny[r] /= l; }
+        }
+        for (int i = 0; i < nnode; ++i) {
+            int r = c->rep[i];
+            c->wnx[i] = c->wnx[r]; c->wny[i] = c->wny[r]; c->is_wall[i] = c->is_wall[r];
+        }
+        /* wall distance: nearest wall segment (all images) plus the wall offset */
+        c->wdist = (double*)xcalloc(nnode, sizeof(double));
+        for (int i = 0; i < nnode; ++i) {
+            double px = xy[2 * i], py = xy[2 * i + 1], best = 1e300;
+            for (int q = 0; q < c->nseg; ++q) {
+                const seg_t* g = &c->seg[q];
+                if (g->tag != 1) continue;
+                double dx = g->bx - g->ax, dy = g->by - g->ay;
+                double t = ((px - g->ax) * dx + (py - g->ay) * dy) / (dx * dx + dy * dy);
+                if (t < 0) t = 0;
+                if (t > 1) t = 1;
+                double d = hypot(px - (g->ax + t * dx), py - (g->ay + t * dy));
+                if (d < best) best = d;
+            }
+            c->wdist[i] = (best < 1e300 ? best : 0.0) + p->wall_offset;
+        }
+    }
+    /* bucket grid of element bounding boxes */
+    {
+        double xmin = 1e300, xmax = -1e300, ymin = 1e300, ymax = -1e300;
+        for (int i = 0; i < nnode; ++i) {
+            if (xy[2 * i] < xmin) xmin = xy[2 * i];
+            if (xy[2 * i] > xmax) xmax = xy[2 * i];
+            if (xy[2 * i + 1] < ymin) ymin = xy[2 * i + 1];
+            if (xy[2 * i + 1] > ymax) ymax = xy[2 * i + 1];
+        }
+        int g = (int)ceil(sqrt((double)ntri / 2.0));
+        if (g < 1) g = 1;
+        c->gx = g; c->gy = g;
+        c->gx0 = xmin; c->gy0 = ymin;
+        c->gdx = (xmax - xmin) / g * (1 + 1e-12); c->gdy = (ymax - ymin) / g * (1 + 1e-12);
+        int* cnt = (int*)xcalloc(g * g + 1, sizeof(int));
+        for (int pass = 0; pass < 2; ++pass) {
+            for (int e = 0; e < ntri; ++e) {
+                double bx0 = 1e300, bx1 = -1e300, by0 = 1e300, by1 = -1e300;
+                for (int k = 0; k < 3; ++k) {
+                    int a = c->tri[3 * e + k];
+                    if (xy[2 * a] < bx0) bx0 = xy[2 * a];
+                    if (xy[2 * a] > bx1) bx1 = xy[2 * a];
+                    if (xy[2 * a + 1] < by0) by0 = xy[2 * a + 1];
+                    if (xy[2 * a + 1] > by1) by1 = xy[2 * a + 1];
+                }
+                int i0 = (int)floor((bx0 - c->gx0) / c->gdx) - 1, i1 = (int)floor((bx1 - c->gx0) / c->gdx) + 1;
+                int j0 = (int)floor((by0 - c->gy0) / c->gdy) - 1, j1 = (int)floor((by1 - c->gy0) / c->gdy) + 1;
+                if (i0 < 0) i0 = 0;
+                if (j0 < 0) j0 = 0;
+                if (i1 >= g) i1 = g - 1;
+                if (j1 >= g) j1 = g - 1;
+                for (int j = j0; j <= j1; ++j)
+                    for (int i = i0; i <= i1; ++i) {
+                        if (pass == 0) cnt[j * g + i + 1]++;
+                        else c->gb[cnt[j * g + i]++] = e;
+                    }
+            }
+            if (pass == 0) {
+                c->gb_off = (int*)xcalloc(g * g + 1, sizeof(int));
+                for (int q = 0; q < g * g; ++q) cnt[q + 1] += cnt[q];
+                memcpy(c->gb_off, cnt, sizeof(int) * (g * g + 1));
+                c->gb = (int*)xcalloc(cnt[g * g], sizeof(int));
+            }
+        }
+        free(cnt);
+    }
+    /* statistics storage */
+    c->en = (double*)xcalloc(ntri, sizeof(double));
+    c->emean = (double*)xcalloc(5 * ntri, sizeof(double));
+    c->eR = (double*)xcalloc(6 * ntri, sizeof(double));
+    c->epsivar = (double*)xcalloc(ntri, sizeof(double));
+    c->ecm = (double*)xcalloc((size_t)c->nb * ntri, sizeof(double));
+    c->nwt = (double*)xcalloc(nnode, sizeof(double));
+    c->nmean = (double*)xcalloc(4 * nnode, sizeof(double));
+    c->nR = (double*)xcalloc(6 * nnode, sizeof(double));
+    c->nke = (double*)xcalloc(2 * nnode, sizeof(double));
+    c->npsivar = (double*)xcalloc(nnode, sizeof(double));
+    c->eder = (double*)xcalloc(9 * ntri, sizeof(double));
+    c->ngrad = (double*)xcalloc(4 * nnode, sizeof(double));
+    c->npack = (double*)xcalloc(11 * nnode, sizeof(double));
+    c->nwp = (double*)xcalloc(5 * nnode, sizeof(double));
+    if (build_fe_pattern(c) != ORC_OK) goto fail;
+    *status = ORC_OK;
+    return c;
+fail:
+    orc_destroy(c);
+    return NULL;
+}
+
+int32_t orc_num_particles(const orc_ctx* c) { return c->np; }
+int32_t orc_step_index(const orc_ctx* c) { return c->step; }
+int32_t orc_cg_iterations(const orc_ctx* c) { return c->cg_iters; }
+
+static void alloc_particles(orc_ctx* c, int n) {
+    free(c->x); free(c->y); free(c->u); free(c->v); free(c->w); free(c->om); free(c->psi);
+    free(c->id); free(c->elem); free(c->bin);
+    c->np = n;
+    c->x = (double*)xcalloc(n, sizeof(double)); c->y = (double*)xcalloc(n, sizeof(double));
+    c->u = (double*)xcalloc(n, sizeof(double)); c->v = (double*)xcalloc(n, sizeof(double));
+    c->w = (double*)xcalloc(n, sizeof(double)); c->om = (double*)xcalloc(n, sizeof(double));
+    c->psi = (double*)xcalloc(n, sizeof(double));
+    c->id = (uint32_t*)xcalloc(n, sizeof(uint32_t));
+    c->elem = (int*)xcalloc(n, sizeof(int));
+    c->bin = (unsigned char*)xcalloc(n, 1);
+}
+
+/* minimum-image distance in x */
+static double dist_source(const orc_params* p, double x, double y) {
+    double dx = x - p->x0;
+    dx -= p->period * floor(dx / p->period + 0.5);
+    return hypot(dx, y - p->y0);
+}
+
+/* Initial state: uniform positions in each element, U ~ N(log law, 2/3 k0 I),
+ * omega ~ Gamma(4, omega0/4) with omega0 = Cmu^1/2 u* / (kappa max(y_w, y_p)),
+ * psi = 1 inside the source disc. Draws: counter (id, 0, call, 1). */
+int orc_seed(orc_ctx* c, int32_t ppe) {
+    if (ppe < 0) return ORC_ERR_ARG;
+    const orc_params* p = &c->p;
+    alloc_particles(c, c->nt * ppe);
+    uint32_t key[2], ctr[4], o0[4], o1[4], o2[4];
+    orc_key(p->seed, p->case_id, key);
+    double sig = sqrt(2.0 / 3.0 * p->k0);
+    for (int e = 0; e < c->nt; ++e) {
+        int a = c->tri[3 * e], b = c->tri[3 * e + 1], d = c->tri[3 * e + 2];
+        for (int j = 0; j < ppe; ++j) {
+            int i = e * ppe + j;
+            uint32_t id = (uint32_t)i;
+            ctr[0] = id; ctr[1] = 0; ctr[3] = 1;
+            ctr[2] = 0; orc_philox4x32_10(key, ctr, o0);
+            ctr[2] = 1; orc_philox4x32_10(key, ctr, o1);
+            ctr[2] = 2; orc_philox4x32_10(key, ctr, o2);
+            double s = sqrt(orc_unif(o0[0])), t = orc_unif(o0[1]);
+            double l0 = 1.0 - s, l1 = s * (1.0 - t), l2 = s * t;
+            double x = l0 * c->xy[2 * a] + l1 * c->xy[2 * b] + l2 * c->xy[2 * d];
+            double y = l0 * c->xy[2 * a + 1] + l1 * c->xy[2 * b + 1] + l2 * c->xy[2 * d + 1];
+            double z0, z1, z2, z3;
+            orc_box_muller(orc_unif(o0[2]), orc_unif(o0[3]), &z0, &z1);
+            orc_box_muller(orc_unif(o1[0]), orc_unif(o1[1]), &z2, &z3);
+            double dy = y - p->y_roof, ulog = 0.0;
+            if (dy >= p->yp) ulog = p->ustar / p->kappa * log(p->E * dy * p->ustar / p->nu);
+            double dw = l0 * c->wdist[a] + l1 * c->wdist[b] + l2 * c->wdist[d];
+            double om0 = sqrt(p->Cmu) * p->ustar / (p->kappa * (dw > p->yp ? dw : p->yp));
+            double g = -log(orc_unif(o1[2])) - log(orc_unif(o1[3])) - log(orc_unif(o2[0])) -
+                       log(orc_unif(o2[1]));
+            c->x[i] = x; c->y[i] = y;
+            c->u[i] = ulog + sig * z0; c->v[i] = sig * z1; c->w[i] = sig * z2;
+            c->om[i] = 0.25 * om0 * g;
+            c->psi[i] = dist_source(p, x, y) < p->r0 ? 1.0 : 0.0;
+            c->id[i] = id;
+            c->elem[i] = e;
+        }
+    }
+    c->step = 0;
+    c->stats_valid = 0;
+    return ORC_OK;
+}
+
+int orc_set_particles(orc_ctx* c, int32_t n, const double* x, const double* y, const double* u,
+                      const double* v, const double* w, const double* om, const double* psi,
+                      const uint32_t* id, const int32_t* elem, int32_t step) {
+    if (n < 0) return ORC_ERR_ARG;
+    alloc_particles(c, n);
+    for (int i = 0; i < n; ++i) {
+        if (elem[i] < 0 || elem[i] >= c->nt) return ORC_ERR_ARG;
+        c->x[i] = x[i]; c->y[i] = y[i]; c->u[i] = u[i]; c->v[i] = v[i]; c->w[i] = w[i];
+        c->om[i] = om[i]; c->psi[i] = psi[i]; c->id[i] = id[i]; c->elem[i] = elem[i];
+    }
+    c->step = step;
+    c->stats_valid = 0;
+    return ORC_OK;
+}
+
+int orc_get_particles(const orc_ctx* c, double* x, double* y, double* u, double* v, double* w,
+                      double* om, double* psi, uint32_t* id, int32_t* elem, uint8_t* bin) {
+    for (int i = 0; i < c->np; ++i) {
+        x[i] = c->x[i]; y[i] = c->y[i]; u[i] = c->u[i]; v[i] = c->v[i]; w[i] = c->w[i];
+        om[i] = c->om[i]; psi[i] = c->psi[i]; id[i] = c->id[i]; elem[i] = c->elem[i];
+        bin[i] = c->bin[i];
+    }
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------- */
+/* statistics: element moments and velocity-conditioned scalar means          */
+/* ------------------------------------------------------------------------- */
+typedef struct { double key; uint32_t id; int idx; } sortrec;
+
+static int cmp_sortrec(const void* a, const void* b) {
+    const sortrec* x = (const sortrec*)a;
+    const sortrec* y = (const sortrec*)b;
+    if (x->key < y->key) return -1;
+    if (x->key > y->key) return 1;
+    if (x->id < y->id) return -1;
+    if (x->id > y->id) return 1;
+    return 0;
+}
+
+/* size of group g when m items are split into G groups, larger groups first */
+static int group_size(int m, int G, int g) { return m / G + (g < m % G ? 1 : 0); }
+
+/* Equal-population bins over n particles (arrays indexed 0..n-1). */
+int orc_bins(const orc_params* p, int32_t n, const double* u, const double* v, const double* w,
+             const uint32_t* id, int32_t* bin) {
+    int G[3] = {p->nb1, p->nb2, p->nb3};
+    int B = G[0] * G[1] * G[2];
+    if (n < B) {
+        for (int i = 0; i < n; ++i) bin[i] = 0;
+        return ORC_OK;
+    }
+    const double* comp[3] = {u, v, w};
+    sortrec* r = (sortrec*)xcalloc(n, sizeof(sortrec));
+    int* order = (int*)xcalloc(n, sizeof(int));
+    int* grp = (int*)xcalloc(n, sizeof(int)); /* running bin prefix per particle */
+    for (int i = 0; i < n; ++i) { order[i] = i; grp[i] = 0; }
+    /* level d: the particles are grouped consecutively in `order`; sort each
+     * group by component d, then split it into G[d] sub-groups */
+    int ngroups = 1;
+    int* gstart = (int*)xcalloc(B + 1, sizeof(int));
+    int* gtmp = (int*)xcalloc(B + 1, sizeof(int));
+    gstart[0] = 0; gstart[1] = n;
+    for (int d = 0; d < 3; ++d) {
+        int nnew = 0;
+        gtmp[0] = 0;
+        for (int g = 0; g < ngroups; ++g) {
+            int s0 = gstart[g], m = gstart[g + 1] - gstart[g];
+            for (int q = 0; q < m; ++q) {
+                int i = order[s0 + q];
+                r[q].key = comp[d][i]; r[q].id = id[i]; r[q].idx = i;
+            }
+            qsort(r, m, sizeof(sortrec), cmp_sortrec);
+            int pos = 0;
+            for (int h = 0; h < G[d]; ++h) {
+                int sz = group_size(m, G[d], h);
+                for (int q = 0; q < sz; ++q) {
+                    int i = r[pos + q].idx;
+                    order[s0 + pos + q] = i;
+                    grp[i] = grp[i] * G[d] + h;
+                }
+                pos += sz;
+                gtmp[nnew + 1] = gtmp[nnew] + sz;
+                nnew++;
+            }
+        }
+        ngroups = nnew;
+        memcpy(gstart, gtmp, sizeof(int) * (nnew + 1));
+    }
+    for (int i = 0; i < n; ++i) bin[i] = grp[i];
+    free(r); free(order); free(grp); free(gstart); free(gtmp);
+    return ORC_OK;
+}
+
+static void element_statistics(orc_ctx* c) {
+    const int nt = c->nt, B = c->nb;
+    /* particles of each element, in particle-array order */
+    int* cnt = (int*)xcalloc(nt + 1, sizeof(int));
+    for (int i = 0; i < c->np; ++i) cnt[c->elem[i] + 1]++;
+    for (int e = 0; e < nt; ++e) cnt[e + 1] += cnt[e];
+    int* list = (int*)xcalloc(c->np, sizeof(int));
+    int* fill = (int*)xcalloc(nt, sizeof(int));
+    for (int i = 0; i < c->np; ++i) list[cnt[c->elem[i]] + fill[c->elem[i]]++] = i;
+    int maxn = 0;
+    for (int e = 0; e < nt; ++e) if (cnt[e + 1] - cnt[e] > maxn) maxn = cnt[e + 1] - cnt[e];
+    double *bu = (double*)xcalloc(maxn, 8), *bv = (double*)xcalloc(maxn, 8), *bw = (double*)xcalloc(maxn, 8);
+    uint32_t* bid = (uint32_t*)xcalloc(maxn, 4);
+    int32_t* bb = (int32_t*)xcalloc(maxn, 4);
+    double* bsum = (double*)xcalloc(B, 8);
+    double* bcnt = (double*)xcalloc(B, 8);
+    for (int e = 0; e < nt; ++e) {
+        int s0 = cnt[e], n = cnt[e + 1] - cnt[e];
+        double* m = &c->emean[5 * e];
+        double* R = &c->eR[6 * e];
+        c->en[e] = n;
+        for (int k = 0; k < 5; ++k) m[k] = 0.0;
+        for (int k = 0; k < 6; ++k) R[k] = 0.0;
+        c->epsivar[e] = 0.0;
+        for (int b = 0; b < B; ++b) c->ecm[(size_t)B * e + b] = 0.0;
+        if (n == 0) continue;
+        for (int q = 0; q < n; ++q) {
+            int i = list[s0 + q];
+            m[0] += c->u[i]; m[1] += c->v[i]; m[2] += c->w[i]; m[3] += c->psi[i]; m[4] += c->om[i];
+        }
+        for (int k = 0; k < 5; ++k) m[k] /= n;
+        double pv = 0.0;
+        for (int q = 0; q < n; ++q) {
+            int i = list[s0 + q];
+            double du = c->u[i] - m[0], dv = c->v[i] - m[1], dw = c->w[i] - m[2], dp = c->psi[i] - m[3];
+            R[0] += du * du; R[1] += dv * dv; R[2] += dw * dw;
+            R[3] += du * dv; R[4] += du * dw; R[5] += dv * dw;
+            pv += dp * dp;
+        }
+        for (int k = 0; k < 6; ++k) R[k] /= n;
+        c->epsivar[e] = pv / n;
+        /* conditional means */
+        for (int q = 0; q < n; ++q) {
+            int i = list[s0 + q];
+            bu[q] = c->u[i]; bv[q] = c->v[i]; bw[q] = c->w[i]; bid[q] = c->id[i];
+        }
+        orc_bins(&c->p, n, bu, bv, bw, bid, bb);
+        if (n < B) {
+            for (int b = 0; b < B; ++b) c->ecm[(size_t)B * e + b] = m[3];
+            for (int q = 0; q < n; ++q) c->bin[list[s0 + q]] = 0;
+        } else {
+            for (int b = 0; b < B; ++b) { bsum[b] = 0.0; bcnt[b] = 0.0; }
+            for (int q = 0; q < n; ++q) {
+                bsum[bb[q]] += c->psi[list[s0 + q]];
+                bcnt[bb[q]] += 1.0;
+                c->bin[list[s0 + q]] = (unsigned char)bb[q];
+            }
+            for (int b = 0; b < B; ++b) c->ecm[(size_t)B * e + b] = bsum[b] / bcnt[b];
+        }
+    }
+    free(cnt); free(list); free(fill); free(bu); free(bv); free(bw); free(bid); free(bb);
+    free(bsum); free(bcnt);
+}
+
+/* ------------------------------------------------------------------------- */
+/* node values and derived fields                                             */
+/* ------------------------------------------------------------------------- */
+static double maxd(double a, double b) { return a > b ? a : b; }
+static double mind(double a, double b) { return a < b ? a : b; }
+
+int orc_h_contract(const orc_params* p, const double R[6], const double g[4], double k, double om,
+                   double f[5]) {
+    /* Eq. elliptic-relaxation right-hand side with Eq. H, for the statistically
+     * two-dimensional field: i, j in {1, 2}; <uw> = <vw> = 0; d/dz = 0. */
+    double gg[2][2] = {{g[0], g[1]}, {g[2], g[3]}};
+    double Rm[2][2] = {{R[0], R[3]}, {R[3], R[1]}};
+    double tr = R[0] + R[1] + R[2];
+    double b[2][2] = {{0, 0}, {0, 0}};
+    if (tr > 0.0)
+        for (int i = 0; i < 2; ++i)
+            for (int j = 0; j < 2; ++j) b[i][j] = Rm[i][j] / tr - (i == j ? 1.0 / 3.0 : 0.0);
+    double det = R[2] * (R[0] * R[1] - R[3] * R[3]);
+    double tk = 2.0 / 3.0 * k;
+    double Av = mind(1.0, p->Cv * det / (tk * tk * tk));
+    double iso = 0.5 * (1.0 - p->C1) * k * om;
+    int q = 0;
+    for (int i = 0; i < 2; ++i)
+        for (int j = 0; j < 2; ++j) {
+            double t = (p->C2 * Av + p->gamma5 / 3.0) * gg[i][j] - p->gamma5 / 3.0 * gg[j][i];
+            for (int m = 0; m < 2; ++m) t += p->gamma5 * b[i][m] * gg[m][j];
+            for (int l = 0; l < 2; ++l) t -= p->gamma5 * b[i][l] * gg[j][l];
+            f[q++] = (i == j ? iso : 0.0) + (p->rotta ? 0.0 : k * t);
+        }
+    f[4] = iso;
+    return ORC_OK;
+}
+
+static void node_statistics(orc_ctx* c) {
+    const orc_params* p = &c->p;
+    for (int i = 0; i < c->nn; ++i) {
+        double wt = 0.0, m[4] = {0, 0, 0, 0}, R[6] = {0, 0, 0, 0, 0, 0}, pv = 0.0;
+        for (int q = c->n2e_off[i]; q < c->n2e_off[i + 1]; ++q) {
+            int e = c->n2e[q];
+            double n = c->en[e];
+            wt += n;
+            m[0] += n * c->emean[5 * e + 0];
+            m[1] += n * c->emean[5 * e + 1];
+            m[2] += n * c->emean[5 * e + 3];
+            m[3] += n * c->emean[5 * e + 4];
+            for (int k = 0; k < 6; ++k) R[k] += n * c->eR[6 * e + k];
+            pv += n * c->epsivar[e];
+        }
+        c->nwt[i] = wt;
+        if (wt <= 0.0) continue; /* keeps the previous node values */
+        for (int k = 0; k < 4; ++k) c->nmean[4 * i + k] = m[k] / wt;
+        for (int k = 0; k < 6; ++k) c->nR[6 * i + k] = R[k] / wt;
+        c->npsivar[i] = pv / wt;
+        double kk = 0.5 * (c->nR[6 * i] + c->nR[6 * i + 1] + c->nR[6 * i + 2]);
+        double Om = maxd(c->nmean[4 * i + 3], p->floor_omega);
+        kk = maxd(kk, p->floor_k);
+        /* Eq. dissipation-from-frequency */
+        double eps = Om * (kk + p->nu * p->CT * p->CT * Om);
+        c->nke[2 * i] = kk;
+        c->nke[2 * i + 1] = maxd(eps, p->floor_eps);
+    }
+}
+
+static void element_derived(orc_ctx* c) {
+    const orc_params* p = &c->p;
+    for (int e = 0; e < c->nt; ++e) {
+        double* d = &c->eder[9 * e];
+        double Ux = 0, Uy = 0, Vx = 0, Vy = 0, kc = 0, ec = 0, Uc = 0, Vc = 0, xc = 0, yc = 0;
+        double Rc[6] = {0, 0, 0, 0, 0, 0};
+        for (int k = 0; k < 3; ++k) {
+            int a = c->tri[3 * e + k];
+            double gx, gy;
+            grad_bary(c, e, k, &gx, &gy);
+            Ux += c->nmean[4 * a] * gx; Uy += c->nmean[4 * a] * gy;
+            Vx += c->nmean[4 * a + 1] * gx; Vy += c->nmean[4 * a + 1] * gy;
+            kc += c->nke[2 * a] / 3.0; ec += c->nke[2 * a + 1] / 3.0;
+            Uc += c->nmean[4 * a] / 3.0; Vc += c->nmean[4 * a + 1] / 3.0;
+            for (int q = 0; q < 6; ++q) Rc[q] += c->nR[6 * a + q] / 3.0;
+            xc += c->xy[2 * a] / 3.0; yc += c->xy[2 * a + 1] / 3.0;
+        }
+        d[0] = Ux; d[1] = Uy; d[2] = Vx; d[3] = Vy;
+        /* production P = -<u_i u_j> d<U_i>/dx_j (in-plane) and Eq. frequency_source */
+        double P = -(Rc[0] * Ux + Rc[3] * Uy + Rc[3] * Vx + Rc[1] * Vy);
+        d[6] = p->Comega2 - p->Comega1 * P / ec;
+        /* Eq. micromixing-timescale */
+        double Ucn = sqrt(Uc * Uc + Vc * Vc);
+        double t1 = p->Cs * cbrt(p->r0 * p->r0 / ec);
+        t1 += (Ucn > 0.0) ? p->Ct * dist_source(p, xc, yc) / Ucn : HUGE_VAL;
+        double t2 = maxd(kc / ec, p->CT * sqrt(p->nu / ec));
+        d[7] = mind(t1, t2);
+        /* Eq. L with C_xi = 1 + 1.3 n_i n_i = 2.3 for a unit normal */
+        double Cxi = 1.0 + 1.3 * 1.0;
+        d[8] = p->CL * maxd(Cxi * pow(kc, 1.5) / ec, p->Ceta * pow(p->nu * p->nu * p->nu / ec, 0.25));
+    }
+    /* recovered node gradient: area-weighted mean of incident element gradients */
+    for (int i = 0; i < c->nn; ++i) {
+        double a = 0, g[4] = {0, 0, 0, 0};
+        for (int q = c->n2e_off[i]; q < c->n2e_off[i + 1]; ++q) {
+            int e = c->n2e[q];
+            double A = 0.5 * c->area2[e];
+            a += A;
+            for (int k = 0; k < 4; ++k) g[k] += A * c->eder[9 * e + k];
+        }
+        for (int k = 0; k < 4; ++k) c->ngrad[4 * i + k] = g[k] / a;
+    }
+    /* Laplacian: divergence of the P1 interpolant of the recovered gradient */
+    for (int e = 0; e < c->nt; ++e) {
+        double lu = 0, lv = 0;
+        for (int k = 0; k < 3; ++k) {
+            int a = c->tri[3 * e + k];
+            double gx, gy;
+            grad_bary(c, e, k, &gx, &gy);
+            lu += c->ngrad[4 * a] * gx + c->ngrad[4 * a + 1] * gy;
+            lv += c->ngrad[4 * a + 2] * gx + c->ngrad[4 * a + 3] * gy;
+        }
+        c->eder[9 * e + 4] = lu;
+        c->eder[9 * e + 5] = lv;
+    }
+}
+
+/* ------------------------------------------------------------------------- */
+/* elliptic relaxation: P1 Galerkin (M + K_{L^2}) wp = M f, Jacobi-PCG         */
+/* ------------------------------------------------------------------------- */
+static int build_fe_pattern(orc_ctx* c) {
+    long long* pr = (long long*)xcalloc((size_t)9 * c->nt * 2, sizeof(long long));
+    int m = 0;
+    for (int e = 0; e < c->nt; ++e)
+        for (int k = 0; k < 3; ++k)
+            for (int l = 0; l < 3; ++l) {
+                pr[2 * m] = c->rep[c->tri[3 * e + k]];
+                pr[2 * m + 1] = c->rep[c->tri[3 * e + l]];
+                m++;
+            }
+    qsort(pr, m, 2 * sizeof(long long), cmp_int2);
+    c->rowptr = (int*)xcalloc(c->nn + 1, sizeof(int));
+    c->colidx = (int*)xcalloc(m, sizeof(int));
+    int nz = 0;
+    for (int q = 0; q < m; ++q) {
+        if (q > 0 && pr[2 * q] == pr[2 * q - 2] && pr[2 * q + 1] == pr[2 * q - 1]) continue;
+        c->colidx[nz++] = (int)pr[2 * q + 1];
+        c->rowptr[pr[2 * q] + 1]++;
+    }
+    for (int i = 0; i < c->nn; ++i) c->rowptr[i + 1] += c->rowptr[i];
+    c->aval = (double*)xcalloc(nz, sizeof(double));
+    free(pr);
+    return ORC_OK;
+}
+
+static int csr_find(const orc_ctx* c, int r, int col) {
+    for (int q = c->rowptr[r]; q < c->rowptr[r + 1]; ++q) if (c->colidx[q] == col) return q;
+    return -1;
+}
+
+/* Solve (M + K_{L^2}) x = M f with x = g on Dirichlet nodes, for ncomp
+ * right-hand sides. L_elem: element L; f_node, g_node, x_out: nnode x ncomp
+ * (x_out also holds the starting guess). */
+int orc_fe_solve(orc_ctx* c, const double* L_elem, const double* f_node, const double* g_node,
+                 const uint8_t* is_dir, double* x_out, int32_t ncomp) {
+    const int nn = c->nn;
+    memset(c->aval, 0, sizeof(double) * c->rowptr[nn]);
+    double* b = (double*)xcalloc((size_t)nn * ncomp, sizeof(double));
+    for (int e = 0; e < c->nt; ++e) {
+        double A = 0.5 * c->area2[e], L2 = L_elem[e] * L_elem[e];
+        double gx[3], gy[3];
+        for (int k = 0; k < 3; ++k) grad_bary(c, e, k, &gx[k], &gy[k]);
+        for (int k = 0; k < 3; ++k)
+            for (int l = 0; l < 3; ++l) {
+                double Mkl = A / 12.0 * (k == l ? 2.0 : 1.0);
+                double Kkl = L2 * A * (gx[k] * gx[l] + gy[k] * gy[l]);
+                int r = c->rep[c->tri[3 * e + k]], col = c->rep[c->tri[3 * e + l]];
+                c->aval[csr_find(c, r, col)] += Mkl + Kkl;
+                for (int q = 0; q < ncomp; ++q)
+                    b[(size_t)r * ncomp + q] += Mkl * f_node[(size_t)c->tri[3 * e + l] * ncomp + q];
+            }
+    }
+    double *x = (double*)xcalloc(nn, 8), *r = (double*)xcalloc(nn, 8), *z = (double*)xcalloc(nn, 8);
+    double *pp = (double*)xcalloc(nn, 8), *Ap = (double*)xcalloc(nn, 8), *dg = (double*)xcalloc(nn, 8);
+    int status = ORC_OK, itmax = 0;
+    for (int i = 0; i < nn; ++i) {
+        int q = (c->rep[i] == i) ? csr_find(c, i, i) : -1;
+        dg[i] = q >= 0 ? c->aval[q] : 1.0;
+    }
+    for (int q = 0; q < ncomp; ++q) {
+        /* unknowns live on canonical nodes; Dirichlet nodes are fixed */
+        for (int i = 0; i < nn; ++i) {
+            x[i] = is_dir[i] ? g_node[(size_t)i * ncomp + q] : x_out[(size_t)i * ncomp + q];
+        }
+        double bn = 0.0, rr = 0.0, rz = 0.0;
+        for (int i = 0; i < nn; ++i) {
+            r[i] = 0.0;
+            if (c->rep[i] != i || is_dir[i]) continue;
+            double s = b[(size_t)i * ncomp + q], s0 = s;
+            for (int k = c->rowptr[i]; k < c->rowptr[i + 1]; ++k) {
+                int j = c->colidx[k];
+                s -= c->aval[k] * x[j];
+                if (is_dir[j]) s0 -= c->aval[k] * x[j];
+            }
+            r[i] = s;
+            bn += s0 * s0;
+        }
+        bn = sqrt(bn);
+        for (int i = 0; i < nn; ++i) { z[i] = r[i] / dg[i]; pp[i] = z[i]; rz += r[i] * z[i]; rr += r[i] * r[i]; }
+        int it = 0;
+        while (sqrt(rr) > c->p.cg_tol * bn && bn > 0.0) {
+            if (it >= c->p.cg_maxit) { status = ORC_ERR_CG; break; }
+            double pAp = 0.0;
+            for (int i = 0; i < nn; ++i) {
+                Ap[i] = 0.0;
+                if (c->rep[i] != i || is_dir[i]) continue;
+                double s = 0.0;
+                for (int k = c->rowptr[i]; k < c->rowptr[i + 1]; ++k) s += c->aval[k] * pp[c->colidx[k]];
+                Ap[i] = s;
+                pAp += pp[i] * s;
+            }
+            double alpha = rz / pAp, rz1 = 0.0;
+            rr = 0.0;
+            for (int i = 0; i < nn; ++i) {
+                x[i] += alpha * pp[i];
+                r[i] -= alpha * Ap[i];
+                z[i] = r[i] / dg[i];
+                rz1 += r[i] * z[i];
+                rr += r[i] * r[i];
+            }
+            double beta = rz1 / rz;
+            rz = rz1;
+            for (int i = 0; i < nn; ++i) pp[i] = z[i] + beta * pp[i];
+            it++;
+        }
+        if (it > itmax) itmax = it;
+        for (int i = 0; i < nn; ++i) x_out[(size_t)i * ncomp + q] = x[c->rep[i]];
+    }
+    c->cg_iters = itmax;
+    free(b); free(x); free(r); free(z); free(pp); free(Ap); free(dg);
+    return status;
+}
+
+static int elliptic_relaxation(orc_ctx* c) {
+    const orc_params* p = &c->p;
+    const int nn = c->nn;
+    double* f = (double*)xcalloc((size_t)5 * nn, 8);
+    double* g = (double*)xcalloc((size_t)5 * nn, 8);
+    double* L = (double*)xcalloc(c->nt, 8);
+    for (int i = 0; i < nn; ++i) {
+        orc_h_contract(p, &c->nR[6 * i], &c->ngrad[4 * i], c->nke[2 * i], maxd(c->nmean[4 * i + 3], p->floor_omega),
+                       &f[5 * i]);
+        if (c->is_wall[i]) {
+            double eps = c->nke[2 * i + 1], nx = c->wnx[i], ny = c->wny[i];
+            g[5 * i + 0] = -p->er_wall * eps * nx * nx;
+            g[5 * i + 1] = -p->er_wall * eps * nx * ny;
+            g[5 * i + 2] = -p->er_wall * eps * ny * nx;
+            g[5 * i + 3] = -p->er_wall * eps * ny * ny;
+            g[5 * i + 4] = 0.0;
+        }
+    }
+    for (int e = 0; e < c->nt; ++e) L[e] = c->eder[9 * e + 8];
+    int st = orc_fe_solve(c, L, f, g, c->is_wall, c->nwp, 5);
+    free(f); free(g); free(L);
+    return st;
+}
+
+static void node_pack(orc_ctx* c) {
+    const orc_params* p = &c->p;
+    for (int i = 0; i < c->nn; ++i) {
+        double* q = &c->npack[11 * i];
+        double kk = c->nke[2 * i], eps = c->nke[2 * i + 1];
+        double Om = maxd(c->nmean[4 * i + 3], p->floor_omega);
+        q[0] = c->nmean[4 * i]; q[1] = c->nmean[4 * i + 1]; q[2] = Om;
+        if (p->wall_model == 0) {
+            /* Eq. wall-GandC (simplified Langevin model) */
+            double a = -(0.5 + 0.75 * p->C0) * Om;
+            q[3] = p->C0 * eps;
+            q[4] = a; q[5] = 0.0; q[6] = 0.0; q[7] = a; q[8] = a;
+        } else {
+            /* Eqs. Gij and C0 */
+            const double* w = &c->nwp[5 * i];
+            const double* R = &c->nR[6 * i];
+            q[4] = (2.0 * w[0] - eps) / (2.0 * kk);
+            q[5] = w[1] / kk;
+            q[6] = w[2] / kk;
+            q[7] = (2.0 * w[3] - eps) / (2.0 * kk);
+            q[8] = (2.0 * w[4] - eps) / (2.0 * kk);
+            double s = w[0] * R[0] + w[1] * R[3] + w[2] * R[3] + w[3] * R[1] + w[4] * R[2];
+            double c0eps = -2.0 * s / (3.0 * kk);
+            q[3] = c0eps > 0.0 ? c0eps : 0.0;
+        }
+        q[9] = p->fx; q[10] = p->fy;
+    }
+}
+
+int orc_estimate_stats(orc_ctx* c) {
+    element_statistics(c);
+    node_statistics(c);
+    element_derived(c);
+    int st = ORC_OK;
+    if (c->p.wall_model == 1) st = elliptic_relaxation(c);
+    node_pack(c);
+    c->stats_valid = 1;
+    return st;
+}
+
+/* ------------------------------------------------------------------------- */
+/* particle step                                                              */
+/* ------------------------------------------------------------------------- */
+
+/* Eqs. IECM, frequency-model, Lagrangian-velocity for a particle, given the
+ * interpolated fields F (22 values):
+ *   0 <U>, 1 <V>, 2 Om, 3 C0eps, 4..8 G11 G12 G21 G22 G33, 9 Fx, 10 Fy,
+ *   11 Ux, 12 Uy, 13 Vx, 14 Vy, 15 lapU, 16 lapV, 17 S_omega, 18 t_m,
+ *   19 <phi|V>, 20 unused, 21 unused
+ * and the Gaussians z[8]; returns -1 if the Euler mixing ratio exceeds one. */
+static int sde_one(const orc_params* p, double dt, const double* F, const double* z, double* u,
+                   double* v, double* w, double* om, double* psi) {
+    double sdt = sqrt(dt), s2nu = sqrt(2.0 * p->nu);
+    /* IECM */
+    double r = p->mix_exp ? 1.0 - exp(-dt / F[18]) : dt / F[18];
+    int bad = (!p->mix_exp && r > 1.0) ? -1 : 0;
+    double psi1 = *psi - r * (*psi - F[19]);
+    /* stochastic frequency */
+    double Om = F[2], o = *om;
+    double om1 = o - p->C3 * Om * (o - Om) * dt - F[17] * Om * o * dt +
+                 sqrt(2.0 * p->C3 * p->C4 * Om * Om * o) * z[6] * sdt;
+    om1 = fabs(om1);
+    /* generalized Langevin velocity */
+    double du = *u - F[0], dv = *v - F[1], dw = *w;
+    double cc = sqrt(F[3] > 0.0 ? F[3] : 0.0);
+    double u1 = *u + (F[9] + 2.0 * p->nu * F[15] + F[4] * du + F[5] * dv) * dt +
+                s2nu * (F[11] * z[0] + F[12] * z[1]) * sdt + cc * z[3] * sdt;
+    double v1 = *v + (F[10] + 2.0 * p->nu * F[16] + F[6] * du + F[7] * dv) * dt +
+                s2nu * (F[13] * z[0] + F[14] * z[1]) * sdt + cc * z[4] * sdt;
+    double w1 = *w + (F[8] * dw) * dt + cc * z[5] * sdt;
+    *u = u1; *v = v1; *w = w1; *om = om1; *psi = psi1;
+    return bad;
+}
+
+void orc_sde(const orc_params* p, int32_t n, double dt, const double* fields, const double* z,
+             double* u, double* v, double* w, double* om, double* psi) {
+    for (int i = 0; i < n; ++i)
+        sde_one(p, dt, fields + 22 * (size_t)i, z + 8 * (size_t)i, &u[i], &v[i], &w[i], &om[i], &psi[i]);
+}
+
+/* Velocity and frequency at a boundary hit. stat = <U>,<V>,R11,R22,R33,R12,Om
+ * at the hit point; n = unit normal into the fluid. */
+int orc_reflect(const orc_ctx* c, int32_t tag, const double n[2], const double stat[7], double* u,
+                double* v, double* w, double* om) {
+    const orc_params* p = &c->p;
+    double nx = n[0], ny = n[1], tx = ny, ty = -nx;
+    double Ut = *u * tx + *v * ty, Vn = *u * nx + *v * ny;
+    (void)w;
+    if (tag == 2) { /* symmetry */
+        double VR = -Vn;
+        *u = Ut * tx + VR * nx; *v = Ut * ty + VR * ny;
+        return ORC_OK;
+    }
+    if (p->wall_model == 1) { /* fully resolved no-slip wall */
+        *u = -*u; *v = -*v; *w = -*w;
+        return ORC_OK;
+    }
+    /* Eqs. wall-normal-velocity .. wall-omega in the wall-element frame */
+    double Ump = stat[0] * tx + stat[1] * ty;
+    double R11 = stat[2], R22 = stat[3], R33 = stat[4], R12 = stat[5];
+    double v2 = R11 * nx * nx + 2.0 * R12 * nx * ny + R22 * ny * ny;
+    double uv = R11 * tx * nx + R12 * (tx * ny + ty * nx) + R22 * ty * ny;
+    v2 = maxd(v2, p->floor_k);
+    double kp = maxd(0.5 * (R11 + R22 + R33), p->floor_k);
+    double Omp = maxd(stat[6], p->floor_omega);
+    double dpdx = -(p->fx * tx + p->fy * ty); /* (1/rho) d<P>/dx in the wall frame */
+    double uhat2 = sqrt(p->Cmu) * kp;
+    double gam = (uv * dpdx > 0.0) ? 1.0 : 0.0;
+    double us = sqrt(uhat2 + gam * fabs(p->yp * dpdx));
+    double Ue = us / p->kappa * log(p->E * p->yp * us / p->nu);
+    double Ue2 = maxd(Ue * Ue, p->floor_k);
+    double alpha = 2.0 * uhat2 * Ump * fabs(Ump) / (v2 * Ue2);
+    double beta = -2.0 / (0.5 + 0.75 * p->C0 + p->C3 + p->Comega2 - p->Comega1);
+    double VR = -Vn, UR = Ut + alpha * Vn;
+    *u = UR * tx + VR * nx; *v = UR * ty + VR * ny;
+    *om = *om * exp(beta * Vn / (p->yp * Omp));
+    return ORC_OK;
+}
+
+static int advance_one(orc_ctx* c, int i, double dt) {
+    const orc_params* p = &c->p;
+    int e = c->elem[i];
+    double x = c->x[i], y = c->y[i];
+    double lam[3];
+    for (int k = 0; k < 3; ++k) lam[k] = bary(c, e, k, x, y);
+    double F[22];
+    for (int q = 0; q < 11; ++q) {
+        F[q] = 0.0;
+        for (int k = 0; k < 3; ++k) F[q] += lam[k] * c->npack[11 * c->tri[3 * e + k] + q];
+    }
+    const double* d = &c->eder[9 * e];
+    for (int q = 0; q < 8; ++q) F[11 + q] = d[q];
+    F[19] = c->ecm[(size_t)c->nb * e + c->bin[i]];
+    F[20] = F[21] = 0.0;
+    double z[8];
+    orc_gauss8(p->seed, p->case_id, c->id[i], (uint32_t)c->step, z);
+    double u0 = c->u[i], v0 = c->v[i];
+    double u = u0, v = v0, w = c->w[i], om = c->om[i], psi = c->psi[i];
+    int st = sde_one(p, dt, F, z, &u, &v, &w, &om, &psi) ? ORC_ERR_DT : ORC_OK;
+    /* Eq. Lagrangian-position with the velocity at step n */
+    double s2nu = sqrt(2.0 * p->nu), sdt = sqrt(dt);
+    double qx = x + u0 * dt + s2nu * z[0] * sdt;
+    double qy = y + v0 * dt + s2nu * z[1] * sdt;
+    /* boundaries: first crossing of a reflecting segment along the path */
+    double px = x, py = y;
+    int last = -1, nref = 0;
+    for (;;) {
+        int hit = -1;
+        double tbest = 2.0;
+        for (int s = 0; s < c->nseg; ++s) {
+            if (s == last) continue;
+            const seg_t* g = &c->seg[s];
+            double sp = g->nx * (px - g->ax) + g->ny * (py - g->ay);
+            double sq = g->nx * (qx - g->ax) + g->ny * (qy - g->ay);
+            if (!(sq < 0.0) || sp < -1e-12) continue;
+            double t = sp > 0.0 ? sp / (sp - sq) : 0.0;
+            double cx = px + t * (qx - px), cy = py + t * (qy - py);
+            double ex = g->bx - g->ax, ey = g->by - g->ay;
+            double mu = ((cx - g->ax) * ex + (cy - g->ay) * ey) / (ex * ex + ey * ey);
+            if (mu < 0.0 || mu > 1.0) continue;
+            if (t < tbest) { tbest = t; hit = s; }
+        }
+        if (hit < 0) break;
+        if (++nref > p->reflect_max) { st = ORC_ERR_WALL; break; }
+        const seg_t* g = &c->seg[hit];
+        double cx = px + tbest * (qx - px), cy = py + tbest * (qy - py);
+        double ex = g->bx - g->ax, ey = g->by - g->ay;
+        double mu = ((cx - g->ax) * ex + (cy - g->ay) * ey) / (ex * ex + ey * ey);
+        double stat[7];
+        const double* Ma = &c->nmean[4 * g->na];
+        const double* Mb = &c->nmean[4 * g->nb];
+        const double* Ra = &c->nR[6 * g->na];
+        const double* Rb = &c->nR[6 * g->nb];
+        stat[0] = (1 - mu) * Ma[0] + mu * Mb[0];
+        stat[1] = (1 - mu) * Ma[1] + mu * Mb[1];
+        stat[2] = (1 - mu) * Ra[0] + mu * Rb[0];
+        stat[3] = (1 - mu) * Ra[1] + mu * Rb[1];
+        stat[4] = (1 - mu) * Ra[2] + mu * Rb[2];
+        stat[5] = (1 - mu) * Ra[3] + mu * Rb[3];
+        stat[6] = (1 - mu) * Ma[3] + mu * Mb[3];
+        double nrm[2] = {g->nx, g->ny};
+        orc_reflect(c, g->tag, nrm, stat, &u, &v, &w, &om);
+        double sq = g->nx * (qx - g->ax) + g->ny * (qy - g->ay);
+        qx -= 2.0 * sq * g->nx;
+        qy -= 2.0 * sq * g->ny;
+        px = cx; py = cy;
+        last = hit;
+    }
+    /* periodic re-injection */
+    qx -= p->period * floor(qx / p->period);
+    if (qx >= p->period) qx -= p->period;
+    int e1 = orc_locate(c, qx, qy);
+    if (e1 < 0) {
+        if (st == ORC_OK) st = ORC_ERR_LOST;
+        e1 = e; qx = x; qy = y;
+    }
+    /* continuous source */
+    if (dist_source(p, qx, qy) < p->r0) psi = 1.0;
+    c->x[i] = qx; c->y[i] = qy; c->u[i] = u; c->v[i] = v; c->w[i] = w;
+    c->om[i] = om; c->psi[i] = psi; c->elem[i] = e1;
+    return st;
+}
+
+int orc_advance(orc_ctx* c, double dt) {
+    if (!c->stats_valid) return ORC_ERR_STATE;
+    if (!(dt > 0.0)) return ORC_ERR_ARG;
+    int st = ORC_OK;
+    for (int i = 0; i < c->np; ++i) {
+        int s = advance_one(c, i, dt);
+        if (s != ORC_OK && st == ORC_OK) st = s;
+    }
+    c->step++;
+    c->stats_valid = 0;
+    return st;
+}
+
+int orc_step(orc_ctx* c, double dt, int32_t nsteps) {
+    for (int s = 0; s < nsteps; ++s) {
+        int st = orc_advance(c, dt);
+        if (st != ORC_OK) return st;
+        st = orc_estimate_stats(c);
+        if (st != ORC_OK) return st;
+    }
+    return ORC_OK;
+}
+
+/* test hook: replace the node statistics and recompute the derived fields */
+int orc_set_node_fields(orc_ctx* c, const double* nmean, const double* nR, const double* nke) {
+    memcpy(c->nmean, nmean, sizeof(double) * 4 * (size_t)c->nn);
+    memcpy(c->nR, nR, sizeof(double) * 6 * (size_t)c->nn);
+    memcpy(c->nke, nke, sizeof(double) * 2 * (size_t)c->nn);
+    element_derived(c);
+    int st = ORC_OK;
+    if (c->p.wall_model == 1) st = elliptic_relaxation(c);
+    node_pack(c);
+    return st;
+}
+
+int orc_get_field(const orc_ctx* c, int32_t f, double* out) {
+    const int nt = c->nt, nn = c->nn;
+    switch (f) {
+    case ORC_F_ELEM_N: memcpy(out, c->en, 8 * (size_t)nt); break;
+    case ORC_F_ELEM_MEAN: memcpy(out, c->emean, 8 * (size_t)5 * nt); break;
+    case ORC_F_ELEM_R: memcpy(out, c->eR, 8 * (size_t)6 * nt); break;
+    case ORC_F_ELEM_PSIVAR: memcpy(out, c->epsivar, 8 * (size_t)nt); break;
+    case ORC_F_ELEM_CM: memcpy(out, c->ecm, 8 * (size_t)c->nb * nt); break;
+    case ORC_F_NODE_MEAN: memcpy(out, c->nmean, 8 * (size_t)4 * nn); break;
+    case ORC_F_NODE_R: memcpy(out, c->nR, 8 * (size_t)6 * nn); break;
+    case ORC_F_NODE_KE: memcpy(out, c->nke, 8 * (size_t)2 * nn); break;
+    case ORC_F_ELEM_DER: memcpy(out, c->eder, 8 * (size_t)9 * nt); break;
+    case ORC_F_NODE_PACK: memcpy(out, c->npack, 8 * (size_t)11 * nn); break;
+    case ORC_F_NODE_WP: memcpy(out, c->nwp, 8 * (size_t)5 * nn); break;
+    case ORC_F_NODE_WDIST: memcpy(out, c->wdist, 8 * (size_t)nn); break;
+    case ORC_F_NODE_GRAD: memcpy(out, c->ngrad, 8 * (size_t)4 * nn); break;
+    case ORC_F_NODE_PSIVAR: memcpy(out, c->npsivar, 8 * (size_t)nn); break;
+    default: return ORC_ERR_ARG;
+    }
+    return ORC_OK;
+}
