@@ -1,0 +1,206 @@
+/* pdf_canyon.h -- C ABI of the GB300 (sm_103a) particle-in-cell joint
+ * velocity-frequency-scalar PDF solver for a periodic street canyon.
+ *
+ * Method: Bakosi, Franzese & Boybeyi, "Joint PDF modelling of turbulent flow
+ * and dispersion in an urban street canyon", Section 2 (Eqs. Lagrangian-
+ * position, Lagrangian-velocity, IECM, dissipation, frequency-model,
+ * frequency_source, micromixing-timescale; elliptic relaxation Eqs. Gij, C0,
+ * elliptic-relaxation, H, L; wall functions Eqs. wall-GandC ... wall-omega;
+ * forward Euler-Maruyama, end of Section 2.2) and Section 3 (periodic canyon,
+ * continuous street-level source, ensemble averages on an unstructured
+ * triangular grid, velocity-conditioned means on a bin structure).
+ *
+ * Conventions for every entry point:
+ *  - return 0 (PDF_OK) on success or a negative PDF_ERR_* code; nothing aborts;
+ *    pdf_last_error() gives a message for the last failure of a context;
+ *  - inputs are copied; the caller keeps ownership of every pointer passed in;
+ *  - outputs go to caller buffers (host or device, as stated per call);
+ *  - work is enqueued on the CUDA stream given to pdf_init_mesh and is
+ *    asynchronous unless stated; pdf_sync() waits and returns the device
+ *    status word (errors raised inside kernels: mixing ratio, lost particle,
+ *    reflection cap, CG non-convergence);
+ *  - every device wait is bounded; a context owns all device memory it
+ *    allocates and frees it in pdf_destroy().
+ */
+#ifndef PDF_CANYON_H
+#define PDF_CANYON_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pdf_ctx pdf_ctx;
+
+enum pdf_status {
+    PDF_OK = 0,
+    PDF_ERR_ARG = -1,           /* bad argument or size */
+    PDF_ERR_MESH = -2,          /* malformed mesh (orientation, tags, periodic pairs) */
+    PDF_ERR_CUDA = -3,          /* CUDA runtime failure (message in pdf_last_error) */
+    PDF_ERR_NONFINITE = -4,     /* non-finite particle state or statistic */
+    PDF_ERR_LOST_PARTICLE = -5, /* element walk exceeded its cap */
+    PDF_ERR_WALL = -6,          /* more than reflect_max boundary reflections in one step */
+    PDF_ERR_CG_NOCONV = -7,     /* elliptic-relaxation CG did not reach cg_tol in cg_maxit */
+    PDF_ERR_DT = -8,            /* Euler mixing ratio dt/t_m above one */
+    PDF_ERR_STATE = -9,         /* call out of order (e.g. step before seeding) */
+    PDF_ERR_CAPACITY = -10      /* a size exceeds what the context was built for */
+};
+
+enum pdf_wall_model { PDF_WALL_FUNCTIONS = 0, PDF_ELLIPTIC_RELAXATION = 1 };
+
+/* particle state and SDE arithmetic precision (statistics are always FP64) */
+enum pdf_precision {
+    PDF_FP64 = 0,       /* FP64 state and SDE, FP64 reductions */
+    PDF_FP32 = 1,       /* FP32 state and SDE, FP64 reductions */
+    PDF_FP32_KAHAN = 2  /* FP32 state and SDE, compensated FP32 reductions */
+};
+
+/* Model constants and run options. pdf_default_params() fills Table 2, the
+ * wall-function constants of Section 2.2 and the Section 3 flow set-up. */
+typedef struct pdf_params {
+    /* Table 2 */
+    double C1, C2, C3, C4, CT, CL, Ceta, Cv, gamma5, Comega1, Comega2, Cs, Ct;
+    /* Section 2.2: C0 of the simplified Langevin model, C_mu, kappa, E */
+    double C0, Cmu, kappa, E;
+    double nu;             /* kinematic viscosity (Re = U0 H / nu) */
+    double fx, fy;         /* imposed mean driving force -(1/rho) d<P>/dx_i */
+    double yp;             /* wall-function distance y_p of Eqs. alpha .. wall-omega */
+    double wall_offset;    /* distance from the mesh wall to the physical wall */
+    double x0, y0, r0;     /* scalar source centre and radius (Eq. micromixing-timescale) */
+    double period;         /* periodic length in x */
+    double k0, ustar, y_roof; /* initial condition: log law above y_roof, 2/3 k0 variance */
+    double er_wall;        /* elliptic-relaxation wall value wp_ij = -er_wall eps n_i n_j */
+    double floor_k, floor_eps, floor_omega; /* positivity floors of k, eps, <omega> */
+    double cg_tol;         /* relative residual of the elliptic-relaxation CG */
+    int32_t cg_maxit;
+    int32_t nb1, nb2, nb3; /* velocity bins per direction for <phi|V> (product <= 255) */
+    int32_t wall_model;    /* enum pdf_wall_model */
+    int32_t mix_exp;       /* 0: Euler r = dt/t_m (error above one); 1: r = 1 - exp(-dt/t_m) */
+    int32_t reflect_max;   /* boundary reflections allowed per particle-step */
+    int32_t rotta;         /* 1: drop the H_ijkl term (the Section 4 SLM/Rotta variant) */
+    uint64_t seed;         /* Philox key (low word, high word xor case_id) */
+    uint32_t case_id;
+    int32_t precision;     /* enum pdf_precision; fixed for the life of a context */
+} pdf_params;
+
+/* Fields readable with pdf_get_fields. Particle fields are in the library's
+ * element-sorted order; rows of element/node fields are element/node ids. */
+enum pdf_field {
+    PDF_FIELD_X = 0, PDF_FIELD_Y = 1, PDF_FIELD_U = 2, PDF_FIELD_V = 3, PDF_FIELD_W = 4,
+    PDF_FIELD_OMEGA = 5, PDF_FIELD_PSI = 6, /* double[n] */
+    PDF_FIELD_ID = 7,        /* uint32[n] persistent particle id */
+    PDF_FIELD_ELEM = 8,      /* int32[n]  host element */
+    PDF_FIELD_BIN = 9,       /* uint8[n]  <phi|V> bin of the particle */
+    PDF_FIELD_ELEM_N = 10,   /* int32[ntri] particles per element */
+    PDF_FIELD_ELEM_MEAN = 11,/* double[ntri][5] <U>,<V>,<W>,<psi>,<omega> */
+    PDF_FIELD_ELEM_R = 12,   /* double[ntri][6] uu,vv,ww,uv,uw,vw (central, divisor n) */
+    PDF_FIELD_ELEM_PSIVAR = 13, /* double[ntri] */
+    PDF_FIELD_ELEM_CM = 14,  /* double[ntri][B] <phi|V> per bin, B = nb1*nb2*nb3 */
+    PDF_FIELD_NODE_MEAN = 15,/* double[nnode][4] <U>,<V>,<psi>,<omega> */
+    PDF_FIELD_NODE_R = 16,   /* double[nnode][6] */
+    PDF_FIELD_NODE_KE = 17,  /* double[nnode][2] k, eps (floored) */
+    PDF_FIELD_ELEM_DER = 18, /* double[ntri][9] dU/dx,dU/dy,dV/dx,dV/dy, lapU,lapV, S_omega, t_m, L */
+    PDF_FIELD_NODE_PACK = 19,/* double[nnode][11] <U>,<V>,<omega>,C0 eps,G11,G12,G21,G22,G33,Fx,Fy */
+    PDF_FIELD_NODE_WP = 20,  /* double[nnode][5] wp11,wp12,wp21,wp22,wp33 */
+    PDF_FIELD_NODE_WDIST = 21, /* double[nnode] wall distance */
+    PDF_FIELD_NODE_GRAD = 22,  /* double[nnode][4] recovered grad <U> */
+    PDF_FIELD_NODE_PSIVAR = 23 /* double[nnode] */
+};
+
+/* Kernel classes timed by pdf_kernel_time (CUDA events on the context stream). */
+enum pdf_kernel {
+    PDF_K_PARTICLE = 0,  /* per-particle step: Eqs. IECM, frequency-model, velocity, position, walls, walk */
+    PDF_K_SORT = 1,      /* element histogram scan + scatter of the particle state */
+    PDF_K_MOMENTS = 2,   /* element moments and <phi|V> bins */
+    PDF_K_FIELDS = 3,    /* node averages, gradients, t_m, S_omega, G_ij packs */
+    PDF_K_ELLIPTIC = 4,  /* FE assembly + Jacobi-PCG of Eq. elliptic-relaxation */
+    PDF_K_COUNT = 5
+};
+
+/* Defaults: Table 2, C0 = 3.5 and C_mu, kappa, E of Section 2.2, nu = 1/12000,
+ * u* = 0.05, bins 2x2x2, wall functions, FP64. Returns PDF_ERR_ARG on NULL. */
+int pdf_default_params(pdf_params* out);
+
+/* Build a context over a triangular mesh (Section 3: unstructured grid used to
+ * track particles, estimate statistics and solve the Eulerian equations).
+ *  xy[2*nnode]          node coordinates (host, double)
+ *  tri[3*ntri]          counter-clockwise node ids (host)
+ *  edge_tag[3*ntri]     edge k of a triangle is opposite its vertex k:
+ *                       0 interior, 1 no-slip wall, 2 top (symmetry), 3 periodic
+ *  periodic_pair[nnode] partner node across the periodic seam, or -1
+ *  cuda_stream          cudaStream_t to enqueue all work on (NULL: legacy stream)
+ * Returns PDF_ERR_MESH for inverted triangles, unmatched edges or periodic
+ * pairs, PDF_ERR_ARG for bad sizes or parameters, PDF_ERR_CUDA on allocation
+ * failure; *out is NULL on failure. */
+int pdf_init_mesh(const pdf_params* p, const double* xy, int32_t nnode, const int32_t* tri,
+                  int32_t ntri, const int32_t* edge_tag, const int32_t* periodic_pair,
+                  void* cuda_stream, pdf_ctx** out);
+
+/* Seed per_element particles in every element (particle id = element *
+ * per_element + j, born sorted by element): positions uniform in the
+ * triangle; U ~ N(log law above y_roof, 2/3 k0 I); omega ~ Gamma(4, omega0/4)
+ * with omega0 = C_mu^1/2 u* / (kappa max(wall distance, y_p)); psi = 1 inside
+ * the source disc. Draws use Philox counter (id, 0, call, 1). Resets the step
+ * counter to 0. Statistics must be estimated before the first step. */
+int pdf_seed_particles(pdf_ctx* c, int32_t per_element);
+
+/* Replace the particle ensemble (host arrays, double for the seven state
+ * components, converted to the context precision) and set the step counter.
+ * The library sorts the particles by element. elem[i] must hold particle i. */
+int pdf_set_particles(pdf_ctx* c, int32_t n, const double* x, const double* y, const double* u,
+                      const double* v, const double* w, const double* omega, const double* psi,
+                      const uint32_t* id, const int32_t* elem, int32_t step);
+
+/* Estimate S^n from the particles: element moments and <phi|V> bins, node
+ * averages, gradients, t_m, S_omega, and G_ij (Eq. wall-GandC, or Eqs. Gij/C0
+ * from the finite-element solve of Eq. elliptic-relaxation). */
+int pdf_estimate_stats(pdf_ctx* c);
+
+/* Advance nsteps forward Euler-Maruyama steps of size dt: per step the
+ * particle kernel (mixing, frequency, velocity, position, boundaries, host
+ * element walk, source), the element sort, and pdf_estimate_stats. */
+int pdf_step(pdf_ctx* c, double dt, int32_t nsteps);
+
+/* Wait for the context stream and return the device status (PDF_OK or the
+ * first PDF_ERR_* raised inside a kernel since the last pdf_sync). */
+int pdf_sync(pdf_ctx* c);
+
+/* Copy a field (enum pdf_field) into dst of the given size in bytes (must be
+ * exactly the field size); dst is device memory if dst_is_device, else host.
+ * Synchronous with respect to the host for host destinations. */
+int pdf_get_fields(pdf_ctx* c, int32_t field, void* dst, size_t bytes, int32_t dst_is_device);
+
+/* Sizes: particle count, elements, nodes, bins per element, step counter,
+ * CG iterations of the last elliptic solve. */
+int64_t pdf_num_particles(const pdf_ctx* c);
+int32_t pdf_num_elements(const pdf_ctx* c);
+int32_t pdf_num_nodes(const pdf_ctx* c);
+int32_t pdf_num_bins(const pdf_ctx* c);
+int32_t pdf_step_index(const pdf_ctx* c);
+int32_t pdf_cg_iterations(pdf_ctx* c);
+
+/* Per-kernel timing with CUDA events on the context stream: enable (1) or
+ * disable (0) recording; pdf_kernel_time returns the summed milliseconds and
+ * launch count of a kernel class (enum pdf_kernel) since the last reset
+ * (synchronises the stream). */
+int pdf_set_timing(pdf_ctx* c, int32_t on);
+int pdf_kernel_time(pdf_ctx* c, int32_t kernel, double* total_ms, int64_t* launches);
+int pdf_reset_timing(pdf_ctx* c);
+
+/* Number of kernels this context has launched so far (all classes, timing on
+ * or off). */
+int64_t pdf_launch_count(const pdf_ctx* c);
+
+/* Message of the last error of c (or of the last failed pdf_init_mesh when c
+ * is NULL). Never NULL. */
+const char* pdf_last_error(const pdf_ctx* c);
+
+/* Free the context and its device memory (waits for the stream). NULL is a no-op. */
+void pdf_destroy(pdf_ctx* c);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -75,6 +75,7 @@ def lib():
             L.orc_estimate_stats.argtypes = [C.c_void_p]
             L.orc_advance.argtypes = [C.c_void_p, C.c_double]
             L.orc_step.argtypes = [C.c_void_p, C.c_double, C.c_int32]
+            L.orc_advance_subset.argtypes = [C.c_void_p, C.c_double, i32, C.c_int32]
             L.orc_get_field.argtypes = [C.c_void_p, C.c_int32, d]
             L.orc_philox4x32_10.argtypes = [u32, u32, u32]
             L.orc_philox4x32_10.restype = None
@@ -188,6 +189,13 @@ class Oracle:
 
     def advance(self, dt: float, check: bool = True) -> int:
         st = lib().orc_advance(self._c, dt)
+        if check:
+            self._check(st)
+        return st
+
+    def advance_subset(self, dt: float, idx, check: bool = True) -> int:
+        idx = np.ascontiguousarray(idx, np.int32)
+        st = lib().orc_advance_subset(self._c, dt, _p(idx, C.c_int32), idx.size)
         if check:
             self._check(st)
         return st

@@ -1082,6 +1082,19 @@ int orc_advance(orc_ctx* c, double dt) {
     return st;
 }
 
+/* advance only the listed particles (statistics and step counter unchanged) */
+int orc_advance_subset(orc_ctx* c, double dt, const int32_t* idx, int32_t n) {
+    if (!c->stats_valid) return ORC_ERR_STATE;
+    if (!(dt > 0.0)) return ORC_ERR_ARG;
+    int st = ORC_OK;
+    for (int q = 0; q < n; ++q) {
+        if (idx[q] < 0 || idx[q] >= c->np) return ORC_ERR_ARG;
+        int s = advance_one(c, idx[q], dt);
+        if (s != ORC_OK && st == ORC_OK) st = s;
+    }
+    return st;
+}
+
 int orc_step(orc_ctx* c, double dt, int32_t nsteps) {
     for (int s = 0; s < nsteps; ++s) {
         int st = orc_advance(c, dt);

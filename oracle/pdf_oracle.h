@@ -86,6 +86,7 @@ int orc_get_particles(const orc_ctx* c, double* x, double* y, double* u, double*
 int orc_estimate_stats(orc_ctx* c);
 int orc_advance(orc_ctx* c, double dt);   /* particles only, fields from current stats */
 int orc_step(orc_ctx* c, double dt, int32_t nsteps); /* advance + re-estimate, nsteps times */
+int orc_advance_subset(orc_ctx* c, double dt, const int32_t* idx, int32_t n);
 int orc_get_field(const orc_ctx* c, int32_t field, double* out);
 int32_t orc_cg_iterations(const orc_ctx* c);
 

@@ -1,0 +1,231 @@
+"""Thin ctypes binding of the C ABI in include/pdf_canyon.h.
+
+Argument marshalling only: every step of the method runs in the CUDA library
+(_build/libpdfcanyon.so, built from csrc/ for sm_103a). There is no CPU
+fallback: if the library cannot be built or loaded, the import of the
+functions below raises.
+
+The function names are those of the C ABI. ``Canyon`` is a small convenience
+owner of one ``pdf_ctx`` that converts numpy arrays and torch tensors to
+pointers.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+_lock = threading.Lock()
+_lib = None
+
+PDF_OK = 0
+ERRORS = {-1: "PDF_ERR_ARG", -2: "PDF_ERR_MESH", -3: "PDF_ERR_CUDA", -4: "PDF_ERR_NONFINITE",
+          -5: "PDF_ERR_LOST_PARTICLE", -6: "PDF_ERR_WALL", -7: "PDF_ERR_CG_NOCONV", -8: "PDF_ERR_DT",
+          -9: "PDF_ERR_STATE", -10: "PDF_ERR_CAPACITY"}
+
+PDF_WALL_FUNCTIONS, PDF_ELLIPTIC_RELAXATION = 0, 1
+PDF_FP64, PDF_FP32, PDF_FP32_KAHAN = 0, 1, 2
+PRECISION = {"fp64": PDF_FP64, "fp32": PDF_FP32, "fp32_kahan": PDF_FP32_KAHAN}
+
+FIELD = dict(x=0, y=1, u=2, v=3, w=4, om=5, psi=6, id=7, elem=8, bin=9, elem_n=10, elem_mean=11, elem_R=12,
+             elem_psivar=13, elem_cm=14, node_mean=15, node_R=16, node_ke=17, elem_der=18, node_pack=19,
+             node_wp=20, node_wdist=21, node_grad=22, node_psivar=23)
+KERNEL = dict(particle=0, sort=1, moments=2, fields=3, elliptic=4)
+
+_DOUBLES = ("C1", "C2", "C3", "C4", "CT", "CL", "Ceta", "Cv", "gamma5", "Comega1", "Comega2", "Cs", "Ct",
+            "C0", "Cmu", "kappa", "E", "nu", "fx", "fy", "yp", "wall_offset", "x0", "y0", "r0", "period",
+            "k0", "ustar", "y_roof", "er_wall", "floor_k", "floor_eps", "floor_omega", "cg_tol")
+
+
+class pdf_params(C.Structure):
+    _fields_ = [(n, C.c_double) for n in _DOUBLES] + [
+        ("cg_maxit", C.c_int32), ("nb1", C.c_int32), ("nb2", C.c_int32), ("nb3", C.c_int32),
+        ("wall_model", C.c_int32), ("mix_exp", C.c_int32), ("reflect_max", C.c_int32), ("rotta", C.c_int32),
+        ("seed", C.c_uint64), ("case_id", C.c_uint32), ("precision", C.c_int32)]
+
+
+EXPORTS = ("pdf_default_params", "pdf_init_mesh", "pdf_seed_particles", "pdf_set_particles",
+           "pdf_estimate_stats", "pdf_step", "pdf_sync", "pdf_get_fields", "pdf_num_particles",
+           "pdf_num_elements", "pdf_num_nodes", "pdf_num_bins", "pdf_step_index", "pdf_cg_iterations",
+           "pdf_set_timing", "pdf_kernel_time", "pdf_reset_timing", "pdf_launch_count", "pdf_last_error",
+           "pdf_destroy")
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib(allow_build: bool = True):
+    """Load the CUDA library (building it first if it is missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.build() if allow_build else _build.LIB
+        if not os.path.exists(path):
+            raise RuntimeError(f"CUDA library missing: {path}")
+        L = C.CDLL(path)
+        P, vp = C.POINTER, C.c_void_p
+        d, i32, u32 = P(C.c_double), P(C.c_int32), P(C.c_uint32)
+        L.pdf_default_params.argtypes = [P(pdf_params)]
+        L.pdf_init_mesh.argtypes = [P(pdf_params), d, C.c_int32, i32, C.c_int32, i32, i32, vp, P(vp)]
+        L.pdf_seed_particles.argtypes = [vp, C.c_int32]
+        L.pdf_set_particles.argtypes = [vp, C.c_int32, d, d, d, d, d, d, d, u32, i32, C.c_int32]
+        L.pdf_estimate_stats.argtypes = [vp]
+        L.pdf_step.argtypes = [vp, C.c_double, C.c_int32]
+        L.pdf_sync.argtypes = [vp]
+        L.pdf_get_fields.argtypes = [vp, C.c_int32, vp, C.c_size_t, C.c_int32]
+        for n in ("pdf_num_particles", "pdf_launch_count"):
+            getattr(L, n).argtypes = [vp]
+            getattr(L, n).restype = C.c_int64
+        for n in ("pdf_num_elements", "pdf_num_nodes", "pdf_num_bins", "pdf_step_index", "pdf_cg_iterations"):
+            getattr(L, n).argtypes = [vp]
+            getattr(L, n).restype = C.c_int32
+        L.pdf_set_timing.argtypes = [vp, C.c_int32]
+        L.pdf_kernel_time.argtypes = [vp, C.c_int32, d, P(C.c_int64)]
+        L.pdf_reset_timing.argtypes = [vp]
+        L.pdf_last_error.argtypes = [vp]
+        L.pdf_last_error.restype = C.c_char_p
+        L.pdf_destroy.argtypes = [vp]
+        L.pdf_destroy.restype = None
+        _lib = L
+        return L
+
+
+class PdfError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+def _ptr(a, ct):
+    return a.ctypes.data_as(C.POINTER(ct))
+
+
+def default_params(**over) -> pdf_params:
+    p = pdf_params()
+    lib().pdf_default_params(C.byref(p))
+    for k, v in over.items():
+        if k == "precision" and isinstance(v, str):
+            v = PRECISION[v]
+        setattr(p, k, v)
+    return p
+
+
+def params_dict(p: pdf_params) -> dict:
+    return {n: getattr(p, n) for n, _ in pdf_params._fields_}
+
+
+class Canyon:
+    """Owner of one pdf_ctx over one mesh (see include/pdf_canyon.h)."""
+
+    def __init__(self, params: pdf_params, mesh: dict, stream=None):
+        L = lib()
+        self.params = params
+        xy = np.ascontiguousarray(mesh["xy"], np.float64)
+        tri = np.ascontiguousarray(mesh["tri"], np.int32)
+        tag = np.ascontiguousarray(mesh["edge_tag"], np.int32)
+        pair = np.ascontiguousarray(mesh["periodic_pair"], np.int32)
+        self._keep = (xy, tri, tag, pair)
+        h = C.c_void_p()
+        st = L.pdf_init_mesh(C.byref(params), _ptr(xy, C.c_double), xy.shape[0], _ptr(tri, C.c_int32),
+                             tri.shape[0], _ptr(tag, C.c_int32), _ptr(pair, C.c_int32),
+                             C.c_void_p(stream or 0), C.byref(h))
+        if st != PDF_OK:
+            raise PdfError(st, L.pdf_last_error(None).decode())
+        self._h = h
+        self.nt = L.pdf_num_elements(h)
+        self.nn = L.pdf_num_nodes(h)
+        self.nbins = L.pdf_num_bins(h)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().pdf_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st):
+        if st != PDF_OK:
+            raise PdfError(st, lib().pdf_last_error(self._h).decode())
+        return st
+
+    @property
+    def handle(self):
+        return self._h
+
+    # -- calls of the C ABI -------------------------------------------------
+    def seed_particles(self, per_element: int):
+        self._check(lib().pdf_seed_particles(self._h, per_element))
+
+    def set_particles(self, st: dict, step: int = 0):
+        n = int(len(st["x"]))
+        arrs = [np.ascontiguousarray(st[k], np.float64) for k in ("x", "y", "u", "v", "w", "om", "psi")]
+        ids = np.ascontiguousarray(st["id"], np.uint32)
+        el = np.ascontiguousarray(st["elem"], np.int32)
+        self._check(lib().pdf_set_particles(self._h, n, *[_ptr(a, C.c_double) for a in arrs],
+                                            _ptr(ids, C.c_uint32), _ptr(el, C.c_int32), step))
+
+    def estimate_stats(self):
+        self._check(lib().pdf_estimate_stats(self._h))
+
+    def step(self, dt: float, nsteps: int = 1):
+        self._check(lib().pdf_step(self._h, dt, nsteps))
+
+    def sync(self, check: bool = True) -> int:
+        st = lib().pdf_sync(self._h)
+        if check:
+            self._check(st)
+        return st
+
+    @property
+    def num_particles(self) -> int:
+        return lib().pdf_num_particles(self._h)
+
+    @property
+    def step_index(self) -> int:
+        return lib().pdf_step_index(self._h)
+
+    @property
+    def cg_iterations(self) -> int:
+        return lib().pdf_cg_iterations(self._h)
+
+    def field_shape(self, name: str):
+        n = self.num_particles
+        w = dict(elem_mean=5, elem_R=6, elem_cm=self.nbins, node_mean=4, node_R=6, node_ke=2, elem_der=9,
+                 node_pack=11, node_wp=5, node_grad=4).get(name, 1)
+        rows = n if FIELD[name] <= 9 else (self.nt if name.startswith("elem") else self.nn)
+        dt = {"id": np.uint32, "elem": np.int32, "bin": np.uint8, "elem_n": np.int32}.get(name, np.float64)
+        return (rows, w) if w > 1 else (rows,), dt
+
+    def field(self, name: str) -> np.ndarray:
+        shape, dt = self.field_shape(name)
+        out = np.empty(shape, dt)
+        self._check(lib().pdf_get_fields(self._h, FIELD[name], out.ctypes.data_as(C.c_void_p), out.nbytes, 0))
+        return out
+
+    def field_into(self, name: str, ptr: int, nbytes: int, device: bool):
+        self._check(lib().pdf_get_fields(self._h, FIELD[name], C.c_void_p(ptr), nbytes, 1 if device else 0))
+
+    def particles(self) -> dict:
+        return {k: self.field(k) for k in ("x", "y", "u", "v", "w", "om", "psi", "id", "elem", "bin")}
+
+    def set_timing(self, on: bool):
+        self._check(lib().pdf_set_timing(self._h, 1 if on else 0))
+
+    def kernel_time(self, kernel: str):
+        ms = C.c_double()
+        n = C.c_int64()
+        self._check(lib().pdf_kernel_time(self._h, KERNEL[kernel], C.byref(ms), C.byref(n)))
+        return ms.value, n.value
+
+    def reset_timing(self):
+        self._check(lib().pdf_reset_timing(self._h))

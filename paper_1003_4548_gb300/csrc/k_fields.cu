@@ -1,0 +1,192 @@
+// k_fields.cu -- node averages, derived element fields and the particle packs.
+//
+// FP64 throughout (a few doubles per node and element):
+//  * node statistics: particle-count weighted means over the incident
+//    elements (periodic partners merged), k = <u_i u_i>/2 and
+//    Eq. dissipation-from-frequency eps = <omega>(k + nu C_T^2 <omega>);
+//  * element: P1 gradient of <U>, production P = -<u_i u_j> d<U_i>/dx_j,
+//    Eq. frequency_source S_omega, Eq. micromixing-timescale t_m and the
+//    length scale of Eq. L at the centroid;
+//  * node gradient recovery (area-weighted) and the element Laplacian;
+//  * node pack for the particle kernel: <U>, <V>, <omega>, C0 eps and G_ij
+//    (Eq. wall-GandC, or Eqs. Gij and C0 from the elliptic relaxation), and
+//    the imposed mean driving force.
+#include "pdf_internal.cuh"
+
+namespace {
+
+__global__ void k_node_stats(int nn, const int* __restrict__ n2e_off, const int* __restrict__ n2e,
+                             const int* __restrict__ en, const double* __restrict__ emean,
+                             const double* __restrict__ eR, const double* __restrict__ epsivar,
+                             pdf_params p, double* nwt, double* nmean, double* nR, double* npsivar,
+                             double* nke) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nn) return;
+    double wt = 0.0, m[4] = {0, 0, 0, 0}, R[6] = {0, 0, 0, 0, 0, 0}, pv = 0.0;
+    for (int q = n2e_off[i]; q < n2e_off[i + 1]; ++q) {
+        const int e = n2e[q];
+        const double n = (double)en[e];
+        wt += n;
+        m[0] += n * emean[5 * e + 0];
+        m[1] += n * emean[5 * e + 1];
+        m[2] += n * emean[5 * e + 3];
+        m[3] += n * emean[5 * e + 4];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) R[k] += n * eR[6 * e + k];
+        pv += n * epsivar[e];
+    }
+    nwt[i] = wt;
+    if (wt <= 0.0) return;  // keeps the previous node values
+#pragma unroll
+    for (int k = 0; k < 4; ++k) nmean[4 * i + k] = m[k] / wt;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) nR[6 * i + k] = R[k] / wt;
+    npsivar[i] = pv / wt;
+    double kk = 0.5 * (nR[6 * i] + nR[6 * i + 1] + nR[6 * i + 2]);
+    double Om = nmean[4 * i + 3];
+    Om = Om > p.floor_omega ? Om : p.floor_omega;
+    kk = kk > p.floor_k ? kk : p.floor_k;
+    const double eps = Om * (kk + p.nu * p.CT * p.CT * Om);
+    nke[2 * i] = kk;
+    nke[2 * i + 1] = eps > p.floor_eps ? eps : p.floor_eps;
+}
+
+template <typename T>
+__global__ void k_elem_derived(int nt, const int* __restrict__ tri, const double* __restrict__ gradb,
+                               const double* __restrict__ cent, const double* __restrict__ nmean,
+                               const double* __restrict__ nR, const double* __restrict__ nke, pdf_params p,
+                               double* eder, T* epack) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= nt) return;
+    double Ux = 0, Uy = 0, Vx = 0, Vy = 0, kc = 0, ec = 0, Uc = 0, Vc = 0;
+    double Rc[6] = {0, 0, 0, 0, 0, 0};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const int a = tri[3 * e + k];
+        const double gx = gradb[6 * e + 2 * k], gy = gradb[6 * e + 2 * k + 1];
+        Ux += nmean[4 * a] * gx; Uy += nmean[4 * a] * gy;
+        Vx += nmean[4 * a + 1] * gx; Vy += nmean[4 * a + 1] * gy;
+        kc += nke[2 * a] / 3.0; ec += nke[2 * a + 1] / 3.0;
+        Uc += nmean[4 * a] / 3.0; Vc += nmean[4 * a + 1] / 3.0;
+#pragma unroll
+        for (int q = 0; q < 6; ++q) Rc[q] += nR[6 * a + q] / 3.0;
+    }
+    double* d = eder + 9 * (size_t)e;
+    d[0] = Ux; d[1] = Uy; d[2] = Vx; d[3] = Vy;
+    const double P = -(Rc[0] * Ux + Rc[3] * Uy + Rc[3] * Vx + Rc[1] * Vy);
+    d[6] = p.Comega2 - p.Comega1 * P / ec;
+    const double Ucn = sqrt(Uc * Uc + Vc * Vc);
+    double dx = cent[2 * e] - p.x0;
+    dx -= p.period * floor(dx / p.period + 0.5);
+    const double dist = hypot(dx, cent[2 * e + 1] - p.y0);
+    double t1 = p.Cs * cbrt(p.r0 * p.r0 / ec);
+    t1 += (Ucn > 0.0) ? p.Ct * dist / Ucn : HUGE_VAL;
+    const double t2a = kc / ec, t2b = p.CT * sqrt(p.nu / ec);
+    const double t2 = t2a > t2b ? t2a : t2b;
+    d[7] = t1 < t2 ? t1 : t2;
+    const double Cxi = 1.0 + 1.3 * 1.0;  // C_xi = 1 + 1.3 n_i n_i with a unit normal
+    const double La = Cxi * pow(kc, 1.5) / ec, Lb = p.Ceta * pow(p.nu * p.nu * p.nu / ec, 0.25);
+    d[8] = p.CL * (La > Lb ? La : Lb);
+    T* ep = epack + (size_t)ELEM_PACK_W * e;
+    ep[0] = (T)Ux; ep[1] = (T)Uy; ep[2] = (T)Vx; ep[3] = (T)Vy;
+    ep[6] = (T)d[6]; ep[7] = (T)d[7];
+}
+
+__global__ void k_node_grad(int nn, const int* __restrict__ n2e_off, const int* __restrict__ n2e,
+                            const double* __restrict__ area, const double* __restrict__ eder, double* ngrad) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nn) return;
+    double a = 0, g[4] = {0, 0, 0, 0};
+    for (int q = n2e_off[i]; q < n2e_off[i + 1]; ++q) {
+        const int e = n2e[q];
+        const double A = area[e];
+        a += A;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) g[k] += A * eder[9 * e + k];
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) ngrad[4 * i + k] = g[k] / a;
+}
+
+template <typename T>
+__global__ void k_elem_lap(int nt, const int* __restrict__ tri, const double* __restrict__ gradb,
+                           const double* __restrict__ ngrad, double* eder, T* epack) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= nt) return;
+    double lu = 0, lv = 0;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const int a = tri[3 * e + k];
+        const double gx = gradb[6 * e + 2 * k], gy = gradb[6 * e + 2 * k + 1];
+        lu += ngrad[4 * a] * gx + ngrad[4 * a + 1] * gy;
+        lv += ngrad[4 * a + 2] * gx + ngrad[4 * a + 3] * gy;
+    }
+    eder[9 * (size_t)e + 4] = lu;
+    eder[9 * (size_t)e + 5] = lv;
+    epack[(size_t)ELEM_PACK_W * e + 4] = (T)lu;
+    epack[(size_t)ELEM_PACK_W * e + 5] = (T)lv;
+}
+
+template <typename T>
+__global__ void k_node_pack(int nn, const double* __restrict__ nmean, const double* __restrict__ nR,
+                            const double* __restrict__ nke, const double* __restrict__ nwp, pdf_params p,
+                            double* npack, T* npackT) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nn) return;
+    double q[NODE_PACK_W];
+    const double kk = nke[2 * i], eps = nke[2 * i + 1];
+    double Om = nmean[4 * i + 3];
+    Om = Om > p.floor_omega ? Om : p.floor_omega;
+    q[0] = nmean[4 * i]; q[1] = nmean[4 * i + 1]; q[2] = Om;
+    if (p.wall_model == PDF_WALL_FUNCTIONS) {
+        const double a = -(0.5 + 0.75 * p.C0) * Om;  // Eq. wall-GandC
+        q[3] = p.C0 * eps;
+        q[4] = a; q[5] = 0.0; q[6] = 0.0; q[7] = a; q[8] = a;
+    } else {
+        const double* w = nwp + 5 * (size_t)i;  // Eqs. Gij and C0
+        const double* R = nR + 6 * (size_t)i;
+        q[4] = (2.0 * w[0] - eps) / (2.0 * kk);
+        q[5] = w[1] / kk;
+        q[6] = w[2] / kk;
+        q[7] = (2.0 * w[3] - eps) / (2.0 * kk);
+        q[8] = (2.0 * w[4] - eps) / (2.0 * kk);
+        const double s = w[0] * R[0] + w[1] * R[3] + w[2] * R[3] + w[3] * R[1] + w[4] * R[2];
+        const double c0eps = -2.0 * s / (3.0 * kk);
+        q[3] = c0eps > 0.0 ? c0eps : 0.0;
+    }
+    q[9] = p.fx; q[10] = p.fy; q[11] = 0.0;
+#pragma unroll
+    for (int k = 0; k < 11; ++k) npack[11 * (size_t)i + k] = q[k];
+#pragma unroll
+    for (int k = 0; k < NODE_PACK_W; ++k) npackT[(size_t)NODE_PACK_W * i + k] = (T)q[k];
+}
+
+template <typename T>
+int run(pdf_ctx* c) {
+    const int nn = c->m.nn, nt = c->m.nt, tb = 128;
+    const unsigned gn = (nn + tb - 1) / tb, ge = (nt + tb - 1) / tb;
+    timing_begin(c, PDF_K_FIELDS);
+    k_node_stats<<<gn, tb, 0, c->s>>>(nn, c->m.n2e_off, c->m.n2e, c->en, c->emean, c->eR, c->epsivar, c->p,
+                                      c->nwt, c->nmean, c->nR, c->npsivar, c->nke);
+    k_elem_derived<T><<<ge, tb, 0, c->s>>>(nt, c->m.tri, c->m.gradb, c->m.cent, c->nmean, c->nR, c->nke,
+                                           c->p, c->eder, (T*)c->epackT);
+    k_node_grad<<<gn, tb, 0, c->s>>>(nn, c->m.n2e_off, c->m.n2e, c->m.area, c->eder, c->ngrad);
+    k_elem_lap<T><<<ge, tb, 0, c->s>>>(nt, c->m.tri, c->m.gradb, c->ngrad, c->eder, (T*)c->epackT);
+    c->launches += 4;
+    timing_end(c, PDF_K_FIELDS);
+    PDF_CUDA(c, cudaGetLastError());
+    if (c->p.wall_model == PDF_ELLIPTIC_RELAXATION) {
+        const int st = launch_elliptic(c);
+        if (st != PDF_OK) return st;
+    }
+    timing_begin(c, PDF_K_FIELDS);
+    k_node_pack<T><<<gn, tb, 0, c->s>>>(nn, c->nmean, c->nR, c->nke, c->nwp, c->p, c->npack, (T*)c->npackT);
+    ++c->launches;
+    timing_end(c, PDF_K_FIELDS);
+    PDF_CUDA(c, cudaGetLastError());
+    return PDF_OK;
+}
+
+}  // namespace
+
+int launch_fields(pdf_ctx* c) { return c->prec == 0 ? run<double>(c) : run<float>(c); }

@@ -1,0 +1,346 @@
+// k_particle.cu -- seeding and the fused per-particle time step.
+//
+// One thread per particle, particles stored as structure-of-arrays sorted by
+// host element so that the element and node data of a warp are the same few
+// cache lines (broadcast loads). The step evaluates every right-hand side from
+// the statistics S^n (forward Euler-Maruyama, end of Section 2.2):
+//   Eq. IECM           psi <- psi - r (psi - <phi|V>_bin),  r = dt/t_m
+//   Eq. frequency-model, Eq. frequency_source
+//   Eq. Lagrangian-velocity (G_ij and C0 eps interpolated from the nodes)
+//   Eq. Lagrangian-position with the velocity at step n
+//   boundaries: periodic seams, symmetry top, wall reflections
+//   (Eqs. wall-normal-velocity .. wall-omega, or specular no-slip), the
+//   element walk to the new host element, and the continuous source.
+#include "pdf_internal.cuh"
+
+namespace {
+
+template <typename T>
+struct StepArgs {
+    int64_t n;
+    T dt, sdt, s2nu, nu;
+    uint32_t step;
+    uint2 key;
+    const int* __restrict__ tri;
+    const int* __restrict__ nbr;
+    const int* __restrict__ einfo;
+    const T* __restrict__ egeo;
+    const T* __restrict__ npack;
+    const T* __restrict__ epack;
+    const T* __restrict__ ecm;
+    const double* __restrict__ nmean;
+    const double* __restrict__ nR;
+    T *x, *y, *u, *v, *w, *om, *psi;
+    const uint32_t* __restrict__ id;
+    int* elem;
+    const unsigned char* __restrict__ bin;
+    int* cnt;
+    int* status;
+    int B, wall_model, mix_exp, reflect_max;
+    T C3, C4, C0, Cmu_half, kappa, E, yp, beta, fx, fy, x0, y0, r0, period, floor_k, floor_om;
+};
+
+// velocity and frequency at a boundary hit: tag 2 symmetry; tag 1 wall
+// (wall functions in the wall-element frame, or specular no-slip)
+template <typename T>
+__device__ void reflect(const StepArgs<T>& a, int tag, T nx, T ny, const double* st, T& u, T& v,
+                        T& w, T& om) {
+    const T tx = ny, ty = -nx;
+    const T Ut = u * tx + v * ty, Vn = u * nx + v * ny;
+    if (tag == 2) {
+        u = Ut * tx - Vn * nx;
+        v = Ut * ty - Vn * ny;
+        return;
+    }
+    if (a.wall_model == PDF_ELLIPTIC_RELAXATION) {
+        u = -u; v = -v; w = -w;
+        return;
+    }
+    const T Ump = (T)st[0] * tx + (T)st[1] * ty;
+    const T R11 = (T)st[2], R22 = (T)st[3], R33 = (T)st[4], R12 = (T)st[5];
+    T v2 = R11 * nx * nx + (T)2 * R12 * nx * ny + R22 * ny * ny;
+    const T uv = R11 * tx * nx + R12 * (tx * ny + ty * nx) + R22 * ty * ny;
+    v2 = v2 > a.floor_k ? v2 : a.floor_k;
+    T kp = (T)0.5 * (R11 + R22 + R33);
+    kp = kp > a.floor_k ? kp : a.floor_k;
+    T Omp = (T)st[6];
+    Omp = Omp > a.floor_om ? Omp : a.floor_om;
+    const T dpdx = -(a.fx * tx + a.fy * ty);
+    const T uhat2 = a.Cmu_half * kp;
+    const T gam = (uv * dpdx > (T)0) ? (T)1 : (T)0;
+    const T us = t_sqrt<T>(uhat2 + gam * fabs(a.yp * dpdx));
+    const T Ue = us / a.kappa * t_log<T>(a.E * a.yp * us / a.nu);
+    T Ue2 = Ue * Ue;
+    Ue2 = Ue2 > a.floor_k ? Ue2 : a.floor_k;
+    const T alpha = (T)2 * uhat2 * Ump * fabs(Ump) / (v2 * Ue2);
+    const T VR = -Vn, UR = Ut + alpha * Vn;
+    u = UR * tx + VR * nx;
+    v = UR * ty + VR * ny;
+    om = om * t_exp<T>(a.beta * Vn / (a.yp * Omp));
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_step(const StepArgs<T> a) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.n) return;
+    const int e0 = a.elem[i];
+    const T x = a.x[i], y = a.y[i];
+    T u = a.u[i], v = a.v[i], w = a.w[i], om = a.om[i], psi = a.psi[i];
+    const uint32_t pid = a.id[i];
+    const int b = a.bin[i];
+
+    // barycentric coordinates in the host element
+    const T* g = a.egeo + (size_t)EGEO_W * e0;
+    const T dx = x - g[0], dy = y - g[1];
+    const T l0 = g[2] * dx + g[3] * dy + g[4];
+    const T l1 = g[5] * dx + g[6] * dy + g[7];
+    const T l2 = g[8] * dx + g[9] * dy + g[10];
+    const int n0 = a.tri[3 * e0], n1 = a.tri[3 * e0 + 1], n2 = a.tri[3 * e0 + 2];
+    T F[11];
+#pragma unroll
+    for (int q = 0; q < 11; ++q)
+        F[q] = l0 * a.npack[NODE_PACK_W * n0 + q] + l1 * a.npack[NODE_PACK_W * n1 + q] +
+               l2 * a.npack[NODE_PACK_W * n2 + q];
+    const T* ep = a.epack + (size_t)ELEM_PACK_W * e0;
+    const T Ux = ep[0], Uy = ep[1], Vx = ep[2], Vy = ep[3], lapU = ep[4], lapV = ep[5];
+    const T Som = ep[6], tm = ep[7];
+    const T cm = a.ecm[(size_t)a.B * e0 + b];
+
+    // eight Gaussians: counter (id, step, call, 0)
+    T z[8];
+#pragma unroll
+    for (uint32_t call = 0; call < 2; ++call) {
+        const uint4 r = philox4x32_10(a.key, make_uint4(pid, a.step, call, 0u));
+        box_muller(unif<T>(r.x), unif<T>(r.y), z[4 * call + 0], z[4 * call + 1]);
+        box_muller(unif<T>(r.z), unif<T>(r.w), z[4 * call + 2], z[4 * call + 3]);
+    }
+    const T dt = a.dt, sdt = a.sdt;
+
+    // Eq. IECM
+    const T r = a.mix_exp ? (T)1 - t_exp<T>(-dt / tm) : dt / tm;
+    if (!a.mix_exp && r > (T)1) set_status(a.status, ST_DT);
+    const T psi1 = psi - r * (psi - cm);
+    // Eq. frequency-model with Eq. frequency_source
+    const T Om = F[2];
+    T om1 = om - a.C3 * Om * (om - Om) * dt - Som * Om * om * dt +
+            t_sqrt<T>((T)2 * a.C3 * a.C4 * Om * Om * om) * z[6] * sdt;
+    om1 = fabs(om1);
+    // Eq. Lagrangian-velocity
+    const T du = u - F[0], dv = v - F[1], dw = w;
+    const T cc = t_sqrt<T>(F[3] > (T)0 ? F[3] : (T)0);
+    T u1 = u + (F[9] + (T)2 * a.nu * lapU + F[4] * du + F[5] * dv) * dt +
+           a.s2nu * (Ux * z[0] + Uy * z[1]) * sdt + cc * z[3] * sdt;
+    T v1 = v + (F[10] + (T)2 * a.nu * lapV + F[6] * du + F[7] * dv) * dt +
+           a.s2nu * (Vx * z[0] + Vy * z[1]) * sdt + cc * z[4] * sdt;
+    T w1 = w + (F[8] * dw) * dt + cc * z[5] * sdt;
+    // Eq. Lagrangian-position with the velocity at step n
+    T qx = x + u * dt + a.s2nu * z[0] * sdt;
+    T qy = y + v * dt + a.s2nu * z[1] * sdt;
+
+    // boundaries and the element walk along the straight path P -> Q
+    T px = x, py = y;
+    int e = e0, entry = -1, nref = 0, it = 0;
+    for (; it < WALK_MAX; ++it) {
+        const T* ge = a.egeo + (size_t)EGEO_W * e;
+        const T qdx = qx - ge[0], qdy = qy - ge[1];
+        const T lq0 = ge[2] * qdx + ge[3] * qdy + ge[4];
+        const T lq1 = ge[5] * qdx + ge[6] * qdy + ge[7];
+        const T lq2 = ge[8] * qdx + ge[9] * qdy + ge[10];
+        const T pdx = px - ge[0], pdy = py - ge[1];
+        int kx = -1;
+        T tb = (T)2, lqk = (T)0;
+        {
+            const T lq[3] = {lq0, lq1, lq2};
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                if (k != entry && lq[k] < (T)0) {
+                    const T lp = ge[2 + 3 * k] * pdx + ge[3 + 3 * k] * pdy + ge[4 + 3 * k];
+                    const T t = lp / (lp - lq[k]);
+                    if (t < tb) { tb = t; kx = k; lqk = lq[k]; }
+                }
+            }
+        }
+        if (kx < 0) break;
+        const int info = a.einfo[e];
+        const int tag = (info >> (2 * kx)) & 3;
+        T cx = px + tb * (qx - px), cy = py + tb * (qy - py);
+        if (tag == 0 || tag == 3) {
+            const int sh = (info >> (6 + 2 * kx)) & 3;
+            if (sh) {
+                const T d = sh == 1 ? a.period : -a.period;
+                cx += d;
+                qx += d;
+            }
+            entry = (info >> (12 + 2 * kx)) & 3;
+            e = a.nbr[3 * e + kx];
+            px = cx; py = cy;
+        } else {
+            if (++nref > a.reflect_max) {
+                set_status(a.status, ST_WALL);
+                qx = px; qy = py;
+                break;
+            }
+            const T ax = ge[2 + 3 * kx], ay = ge[3 + 3 * kx];
+            const T inv = (T)1 / t_sqrt<T>(ax * ax + ay * ay);
+            const T nx = ax * inv, ny = ay * inv;
+            const T sd = lqk * inv;  // signed distance of Q from the edge line (< 0)
+            qx -= (T)2 * sd * nx;
+            qy -= (T)2 * sd * ny;
+            // wall statistics at the hit point, linear along the edge
+            const int ka = (kx + 1) % 3, kb = (kx + 2) % 3;
+            const T cdx = cx - ge[0], cdy = cy - ge[1];
+            const T la = ge[2 + 3 * ka] * cdx + ge[3 + 3 * ka] * cdy + ge[4 + 3 * ka];
+            const T lb = ge[2 + 3 * kb] * cdx + ge[3 + 3 * kb] * cdy + ge[4 + 3 * kb];
+            const double mu = (double)(lb / (la + lb));
+            const int na = a.tri[3 * e + ka], nb = a.tri[3 * e + kb];
+            double st[7];
+            st[0] = (1 - mu) * a.nmean[4 * na + 0] + mu * a.nmean[4 * nb + 0];
+            st[1] = (1 - mu) * a.nmean[4 * na + 1] + mu * a.nmean[4 * nb + 1];
+            st[2] = (1 - mu) * a.nR[6 * na + 0] + mu * a.nR[6 * nb + 0];
+            st[3] = (1 - mu) * a.nR[6 * na + 1] + mu * a.nR[6 * nb + 1];
+            st[4] = (1 - mu) * a.nR[6 * na + 2] + mu * a.nR[6 * nb + 2];
+            st[5] = (1 - mu) * a.nR[6 * na + 3] + mu * a.nR[6 * nb + 3];
+            st[6] = (1 - mu) * a.nmean[4 * na + 3] + mu * a.nmean[4 * nb + 3];
+            reflect<T>(a, tag, nx, ny, st, u1, v1, w1, om1);
+            px = cx; py = cy;
+            entry = kx;
+        }
+    }
+    if (it == WALK_MAX) {
+        set_status(a.status, ST_LOST);
+        e = e0; qx = x; qy = y;
+    }
+    // continuous source (minimum-image distance in x)
+    T psi2 = psi1;
+    {
+        T ddx = qx - a.x0;
+        ddx -= a.period * t_floor<T>(ddx / a.period + (T)0.5);
+        const T ddy = qy - a.y0;
+        if (ddx * ddx + ddy * ddy < a.r0 * a.r0) psi2 = (T)1;
+    }
+    if (!isfinite(u1 + v1 + w1 + om1)) set_status(a.status, ST_NONFINITE);
+
+    a.x[i] = qx; a.y[i] = qy;
+    a.u[i] = u1; a.v[i] = v1; a.w[i] = w1; a.om[i] = om1; a.psi[i] = psi2;
+    a.elem[i] = e;
+    // element histogram for the sort (warp-aggregated)
+    const unsigned mask = __match_any_sync(__activemask(), e);
+    if ((threadIdx.x & 31) == __ffs(mask) - 1) atomicAdd(&a.cnt[e], __popc(mask));
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_seed(int64_t n, int ppe, uint2 key, const int* __restrict__ tri,
+                                              const double* __restrict__ xy,
+                                              const double* __restrict__ wdist, pdf_params p, T* x, T* y,
+                                              T* u, T* v, T* w, T* om, T* psi, uint32_t* id, int* elem) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int e = (int)(i / ppe);
+    const uint32_t pid = (uint32_t)i;
+    const uint4 o0 = philox4x32_10(key, make_uint4(pid, 0u, 0u, 1u));
+    const uint4 o1 = philox4x32_10(key, make_uint4(pid, 0u, 1u, 1u));
+    const uint4 o2 = philox4x32_10(key, make_uint4(pid, 0u, 2u, 1u));
+    const int a = tri[3 * e], b = tri[3 * e + 1], d = tri[3 * e + 2];
+    const double s = sqrt(unif<double>(o0.x)), t = unif<double>(o0.y);
+    const double l0 = 1.0 - s, l1 = s * (1.0 - t), l2 = s * t;
+    const double px = l0 * xy[2 * a] + l1 * xy[2 * b] + l2 * xy[2 * d];
+    const double py = l0 * xy[2 * a + 1] + l1 * xy[2 * b + 1] + l2 * xy[2 * d + 1];
+    double z0, z1, z2, z3;
+    box_muller(unif<double>(o0.z), unif<double>(o0.w), z0, z1);
+    box_muller(unif<double>(o1.x), unif<double>(o1.y), z2, z3);
+    const double dyr = py - p.y_roof;
+    const double ulog = dyr >= p.yp ? p.ustar / p.kappa * log(p.E * dyr * p.ustar / p.nu) : 0.0;
+    const double dw = l0 * wdist[a] + l1 * wdist[b] + l2 * wdist[d];
+    const double om0 = sqrt(p.Cmu) * p.ustar / (p.kappa * (dw > p.yp ? dw : p.yp));
+    const double gsum = -log(unif<double>(o1.z)) - log(unif<double>(o1.w)) - log(unif<double>(o2.x)) -
+                        log(unif<double>(o2.y));
+    const double sig = sqrt(2.0 / 3.0 * p.k0);
+    double ddx = px - p.x0;
+    ddx -= p.period * floor(ddx / p.period + 0.5);
+    const double dd = hypot(ddx, py - p.y0);
+    x[i] = (T)px; y[i] = (T)py;
+    u[i] = (T)(ulog + sig * z0); v[i] = (T)(sig * z1); w[i] = (T)(sig * z2);
+    om[i] = (T)(0.25 * om0 * gsum);
+    psi[i] = dd < p.r0 ? (T)1 : (T)0;
+    id[i] = pid;
+    elem[i] = e;
+}
+
+template <typename T>
+StepArgs<T> step_args(pdf_ctx* c, double dt) {
+    const pdf_params& p = c->p;
+    StepArgs<T> a;
+    a.n = c->np;
+    a.dt = (T)dt;
+    a.sdt = (T)sqrt(dt);
+    a.s2nu = (T)sqrt(2.0 * p.nu);
+    a.nu = (T)p.nu;
+    a.step = (uint32_t)c->step;
+    a.key = philox_key(p.seed, p.case_id);
+    a.tri = c->m.tri;
+    a.nbr = c->m.nbr;
+    a.einfo = c->m.einfo;
+    a.egeo = (const T*)(sizeof(T) == 8 ? (const void*)c->m.egeo_d : (const void*)c->m.egeo_f);
+    a.npack = (const T*)c->npackT;
+    a.epack = (const T*)c->epackT;
+    a.ecm = (const T*)c->ecmT;
+    a.nmean = c->nmean;
+    a.nR = c->nR;
+    a.x = (T*)c->stA[0]; a.y = (T*)c->stA[1]; a.u = (T*)c->stA[2]; a.v = (T*)c->stA[3];
+    a.w = (T*)c->stA[4]; a.om = (T*)c->stA[5]; a.psi = (T*)c->stA[6];
+    a.id = c->idA;
+    a.elem = c->elemA;
+    a.bin = c->bin;
+    a.cnt = c->cnt;
+    a.status = c->d_status;
+    a.B = c->B;
+    a.wall_model = p.wall_model;
+    a.mix_exp = p.mix_exp;
+    a.reflect_max = p.reflect_max;
+    a.C3 = (T)p.C3; a.C4 = (T)p.C4; a.C0 = (T)p.C0;
+    a.Cmu_half = (T)sqrt(p.Cmu);
+    a.kappa = (T)p.kappa; a.E = (T)p.E; a.yp = (T)p.yp;
+    a.beta = (T)(-2.0 / (0.5 + 0.75 * p.C0 + p.C3 + p.Comega2 - p.Comega1));
+    a.fx = (T)p.fx; a.fy = (T)p.fy;
+    a.x0 = (T)p.x0; a.y0 = (T)p.y0; a.r0 = (T)p.r0; a.period = (T)p.period;
+    a.floor_k = (T)p.floor_k; a.floor_om = (T)p.floor_omega;
+    return a;
+}
+
+}  // namespace
+
+int launch_particle_step(pdf_ctx* c, double dt) {
+    PDF_CUDA(c, cudaMemsetAsync(c->cnt, 0, sizeof(int) * c->m.nt, c->s));
+    if (c->np == 0) return PDF_OK;
+    const int threads = 256;
+    const unsigned blocks = (unsigned)((c->np + threads - 1) / threads);
+    timing_begin(c, PDF_K_PARTICLE);
+    if (c->prec == 0)
+        k_step<double><<<blocks, threads, 0, c->s>>>(step_args<double>(c, dt));
+    else
+        k_step<float><<<blocks, threads, 0, c->s>>>(step_args<float>(c, dt));
+    ++c->launches;
+    timing_end(c, PDF_K_PARTICLE);
+    PDF_CUDA(c, cudaGetLastError());
+    return PDF_OK;
+}
+
+int launch_seed(pdf_ctx* c, int ppe) {
+    if (c->np == 0) return PDF_OK;
+    const int threads = 256;
+    const unsigned blocks = (unsigned)((c->np + threads - 1) / threads);
+    const uint2 key = philox_key(c->p.seed, c->p.case_id);
+    if (c->prec == 0)
+        k_seed<double><<<blocks, threads, 0, c->s>>>(
+            c->np, ppe, key, c->m.tri, c->m.xy, c->m.wdist, c->p, (double*)c->stA[0], (double*)c->stA[1],
+            (double*)c->stA[2], (double*)c->stA[3], (double*)c->stA[4], (double*)c->stA[5],
+            (double*)c->stA[6], c->idA, c->elemA);
+    else
+        k_seed<float><<<blocks, threads, 0, c->s>>>(
+            c->np, ppe, key, c->m.tri, c->m.xy, c->m.wdist, c->p, (float*)c->stA[0], (float*)c->stA[1],
+            (float*)c->stA[2], (float*)c->stA[3], (float*)c->stA[4], (float*)c->stA[5],
+            (float*)c->stA[6], c->idA, c->elemA);
+    ++c->launches;
+    PDF_CUDA(c, cudaGetLastError());
+    return PDF_OK;
+}

@@ -1,0 +1,126 @@
+// k_sort.cu -- keeps the particle state sorted by host element.
+//
+// The particle kernel leaves per-element counts; one block scans them into
+// segment offsets, then every particle claims a slot in its element's
+// segment with a warp-aggregated atomic and moves its state there. The order
+// inside a segment is not fixed; every later reduction orders the segment by
+// (velocity, id) first, so results do not depend on it.
+#include "pdf_internal.cuh"
+
+namespace {
+
+constexpr int SCAN_THREADS = 1024;
+
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan(const int* __restrict__ cnt, int nt, int* off,
+                                                       int* cursor) {
+    __shared__ int warp_tot[SCAN_THREADS / 32];
+    const int t = threadIdx.x;
+    const int chunk = (nt + SCAN_THREADS - 1) / SCAN_THREADS;
+    const int b0 = t * chunk, b1 = min(nt, b0 + chunk);
+    int s = 0;
+    for (int e = b0; e < b1; ++e) s += cnt[e];
+    // inclusive scan of the per-thread sums
+    const int lane = t & 31, wid = t >> 5;
+    int v = s;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int n = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += n;
+    }
+    if (lane == 31) warp_tot[wid] = v;
+    __syncthreads();
+    if (wid == 0) {
+        int w = warp_tot[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int n = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += n;
+        }
+        warp_tot[lane] = w;
+    }
+    __syncthreads();
+    int run = v - s + (wid > 0 ? warp_tot[wid - 1] : 0);
+    for (int e = b0; e < b1; ++e) {
+        off[e] = run;
+        cursor[e] = run;
+        run += cnt[e];
+    }
+    if (t == SCAN_THREADS - 1) off[nt] = run;
+}
+
+__global__ void __launch_bounds__(256) k_count(int64_t n, const int* __restrict__ elem, int nt, int* cnt,
+                                               int* status) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int e = elem[i];
+    if (e < 0 || e >= nt) {
+        set_status(status, ST_CAPACITY);
+        e = 0;
+    }
+    const unsigned mask = __match_any_sync(__activemask(), e);
+    if ((threadIdx.x & 31) == __ffs(mask) - 1) atomicAdd(&cnt[e], __popc(mask));
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_scatter(int64_t n, const T* __restrict__ x, const T* __restrict__ y,
+                                                 const T* __restrict__ u, const T* __restrict__ v,
+                                                 const T* __restrict__ w, const T* __restrict__ om,
+                                                 const T* __restrict__ psi, const uint32_t* __restrict__ id,
+                                                 const int* __restrict__ elem, int nt, int* cursor, T* x2,
+                                                 T* y2, T* u2, T* v2, T* w2, T* om2, T* psi2, uint32_t* id2,
+                                                 int* elem2) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int e = elem[i];
+    if (e < 0 || e >= nt) e = 0;  // reported by k_count
+    const unsigned mask = __match_any_sync(__activemask(), e);
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(mask) - 1;
+    int base = 0;
+    if (lane == leader) base = atomicAdd(&cursor[e], __popc(mask));
+    base = __shfl_sync(mask, base, leader);
+    const int64_t slot = base + __popc(mask & ((1u << lane) - 1u));
+    x2[slot] = x[i]; y2[slot] = y[i]; u2[slot] = u[i]; v2[slot] = v[i]; w2[slot] = w[i];
+    om2[slot] = om[i]; psi2[slot] = psi[i]; id2[slot] = id[i]; elem2[slot] = e;
+}
+
+template <typename T>
+void scatter(pdf_ctx* c, unsigned blocks) {
+    T** A = (T**)c->stA;
+    T** B = (T**)c->stB;
+    k_scatter<T><<<blocks, 256, 0, c->s>>>(c->np, A[0], A[1], A[2], A[3], A[4], A[5], A[6], c->idA, c->elemA,
+                                           c->m.nt, c->cursor, B[0], B[1], B[2], B[3], B[4], B[5], B[6],
+                                           c->idB, c->elemB);
+}
+
+}  // namespace
+
+int launch_sort(pdf_ctx* c) {
+    timing_begin(c, PDF_K_SORT);
+    k_scan<<<1, SCAN_THREADS, 0, c->s>>>(c->cnt, c->m.nt, c->off, c->cursor);
+    ++c->launches;
+    if (c->np > 0) {
+        const unsigned blocks = (unsigned)((c->np + 255) / 256);
+        if (c->prec == 0) scatter<double>(c, blocks);
+        else scatter<float>(c, blocks);
+        ++c->launches;
+    }
+    timing_end(c, PDF_K_SORT);
+    PDF_CUDA(c, cudaGetLastError());
+    for (int k = 0; k < 7; ++k) std::swap(c->stA[k], c->stB[k]);
+    std::swap(c->idA, c->idB);
+    std::swap(c->elemA, c->elemB);
+    return PDF_OK;
+}
+
+int launch_count_and_sort(pdf_ctx* c) {
+    PDF_CUDA(c, cudaMemsetAsync(c->cnt, 0, sizeof(int) * c->m.nt, c->s));
+    if (c->np > 0)
+    {
+        k_count<<<(unsigned)((c->np + 255) / 256), 256, 0, c->s>>>(c->np, c->elemA, c->m.nt, c->cnt,
+                                                                   c->d_status);
+        ++c->launches;
+    }
+    PDF_CUDA(c, cudaGetLastError());
+    return launch_sort(c);
+}

@@ -1,0 +1,319 @@
+// k_stats.cu -- element moments and velocity-conditioned scalar means.
+//
+// One block per element works on the element's contiguous segment of the
+// sorted particle state. The segment's keys (velocity component, particle id)
+// are sorted in shared memory with a bitonic network (global scratch for
+// segments above STATS_CAP particles):
+//  * after the first sort (by U, then id) the segment is in a canonical order,
+//    and the ensemble averages of Section 2 (n, <U_i>, central <u_i u_j>,
+//    <psi>, psi variance, <omega>) are reduced in that order, so the result
+//    does not depend on where the sort put each particle;
+//  * the equal-population bins of <phi|V> (Section 3, 2x2x2 by default) split
+//    the sorted segment into nb1 groups, re-sort each group by (V, id) and
+//    split into nb2, then by (W, id) into nb3; <phi|V> of a bin is its mean psi.
+// Reductions are FP64 (or compensated FP32 with PDF_FP32_KAHAN).
+#include "pdf_internal.cuh"
+
+namespace {
+
+struct AccD {
+    double s = 0.0;
+    __device__ void add(double x) { s += x; }
+    __device__ void merge(const AccD& o) { s += o.s; }
+    __device__ double value() const { return s; }
+    __device__ AccD shfl_down(int o) const {
+        AccD r;
+        r.s = __shfl_down_sync(0xffffffffu, s, o);
+        return r;
+    }
+};
+
+// Neumaier-compensated FP32 sum; merges add the compensations
+struct AccK {
+    float s = 0.f, c = 0.f;
+    __device__ void add(float x) {
+        const float t = s + x;
+        c += (fabsf(s) >= fabsf(x)) ? (s - t) + x : (x - t) + s;
+        s = t;
+    }
+    __device__ void merge(const AccK& o) {
+        add(o.s);
+        c += o.c;
+    }
+    __device__ double value() const { return (double)s + (double)c; }
+    __device__ AccK shfl_down(int o) const {
+        AccK r;
+        r.s = __shfl_down_sync(0xffffffffu, s, o);
+        r.c = __shfl_down_sync(0xffffffffu, c, o);
+        return r;
+    }
+};
+
+template <typename T, bool KAHAN> struct AccSel { using type = AccD; using R = double; };
+template <> struct AccSel<float, true> { using type = AccK; using R = float; };
+
+__device__ __forceinline__ bool key_gt(const SortKey& a, const SortKey& b) {
+    const uint32_t ga = a.gi >> 24, gb = b.gi >> 24;
+    if (ga != gb) return ga > gb;
+    if (a.v != b.v) return a.v > b.v;
+    return a.id > b.id;
+}
+
+// ascending bitonic sort of K[0..N2), N2 a power of two
+__device__ void bitonic(SortKey* K, int N2) {
+    const int half = N2 >> 1;
+    for (int k = 2; k <= N2; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int p = threadIdx.x; p < half; p += blockDim.x) {
+                const int i = 2 * j * (p / j) + (p % j);
+                const int ixj = i + j;
+                const SortKey A = K[i], Bk = K[ixj];
+                const bool asc = (i & k) == 0;
+                if (asc ? key_gt(A, Bk) : key_gt(Bk, A)) {
+                    K[i] = Bk;
+                    K[ixj] = A;
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// deterministic block reduction of NV accumulators (fixed tree)
+template <typename Acc, int NV>
+__device__ void block_reduce(Acc (&acc)[NV], double (&out)[NV]) {
+    __shared__ Acc part[STATS_THREADS / 32][NV];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc[q].merge(acc[q].shfl_down(o));
+    }
+    if (lane == 0)
+#pragma unroll
+        for (int q = 0; q < NV; ++q) part[wid][q] = acc[q];
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+        Acc t = part[0][q];
+        for (int w = 1; w < STATS_THREADS / 32; ++w) t.merge(part[w][q]);
+        out[q] = t.value();
+    }
+    __syncthreads();
+}
+
+template <typename T>
+struct MomArgs {
+    const int* __restrict__ off;
+    const T* __restrict__ u;
+    const T* __restrict__ v;
+    const T* __restrict__ w;
+    const T* __restrict__ om;
+    const T* __restrict__ psi;
+    const uint32_t* __restrict__ id;
+    int G0, G1, G2, B;
+    int* en;
+    double *emean, *eR, *epsivar, *ecm;
+    T* ecmT;
+    unsigned char* bin;
+    SortKey* scratch;
+    int64_t scratch_n;
+    int* status;
+};
+
+__device__ __forceinline__ int chunk_of(int r, int m, int G) {
+    const int base = m / G, rem = m % G;
+    const int big = rem * (base + 1);
+    return r < big ? r / (base + 1) : rem + (r - big) / base;
+}
+
+template <typename T, bool KAHAN>
+__global__ void __launch_bounds__(STATS_THREADS) k_moments(const MomArgs<T> a) {
+    using Acc = typename AccSel<T, KAHAN>::type;
+    using R = typename AccSel<T, KAHAN>::R;
+    extern __shared__ SortKey skeys[];
+    __shared__ int gstart[256], gsize[256], nstart[256], nsize[256];
+    __shared__ double mean_s[5];
+    const int e = blockIdx.x;
+    const int s0 = a.off[e], n = a.off[e + 1] - s0;
+    const int B = a.B;
+    if (n == 0) {
+        if (threadIdx.x == 0) {
+            a.en[e] = 0;
+            for (int q = 0; q < 5; ++q) a.emean[5 * e + q] = 0.0;
+            for (int q = 0; q < 6; ++q) a.eR[6 * e + q] = 0.0;
+            a.epsivar[e] = 0.0;
+        }
+        for (int b = threadIdx.x; b < B; b += blockDim.x) {
+            a.ecm[(size_t)B * e + b] = 0.0;
+            a.ecmT[(size_t)B * e + b] = (T)0;
+        }
+        return;
+    }
+    int N2 = 1;
+    while (N2 < n) N2 <<= 1;
+    SortKey* K = skeys;
+    if (N2 > STATS_CAP) {
+        if ((int64_t)2 * s0 + N2 > a.scratch_n || n > (1 << 24)) {
+            if (threadIdx.x == 0) set_status(a.status, ST_CAPACITY);
+            return;
+        }
+        K = a.scratch + (size_t)2 * s0;
+    }
+    // level 0: (U, id)
+    for (int q = threadIdx.x; q < N2; q += blockDim.x) {
+        SortKey k;
+        if (q < n) {
+            k.v = ord_bits(a.u[s0 + q]);
+            k.id = a.id[s0 + q];
+            k.gi = (uint32_t)q;
+        } else {
+            k.v = ~0ull;
+            k.id = 0xffffffffu;
+            k.gi = 0xffffffffu;
+        }
+        K[q] = k;
+    }
+    __syncthreads();
+    bitonic(K, N2);
+
+    // ensemble averages in the canonical (U, id) order
+    {
+        Acc acc[5];
+        for (int q = threadIdx.x; q < n; q += blockDim.x) {
+            const int j = s0 + (int)(K[q].gi & 0xffffffu);
+            acc[0].add((R)a.u[j]);
+            acc[1].add((R)a.v[j]);
+            acc[2].add((R)a.w[j]);
+            acc[3].add((R)a.psi[j]);
+            acc[4].add((R)a.om[j]);
+        }
+        double s[5];
+        block_reduce<Acc, 5>(acc, s);
+        if (threadIdx.x == 0)
+            for (int q = 0; q < 5; ++q) mean_s[q] = s[q] / n;
+        __syncthreads();
+        const R mu = (R)mean_s[0], mv = (R)mean_s[1], mw = (R)mean_s[2], mp = (R)mean_s[3];
+        Acc c2[7];
+        for (int q = threadIdx.x; q < n; q += blockDim.x) {
+            const int j = s0 + (int)(K[q].gi & 0xffffffu);
+            const R du = (R)a.u[j] - mu, dv = (R)a.v[j] - mv, dw = (R)a.w[j] - mw, dp = (R)a.psi[j] - mp;
+            c2[0].add(du * du);
+            c2[1].add(dv * dv);
+            c2[2].add(dw * dw);
+            c2[3].add(du * dv);
+            c2[4].add(du * dw);
+            c2[5].add(dv * dw);
+            c2[6].add(dp * dp);
+        }
+        double r2[7];
+        block_reduce<Acc, 7>(c2, r2);
+        if (threadIdx.x == 0) {
+            a.en[e] = n;
+            for (int q = 0; q < 5; ++q) a.emean[5 * e + q] = mean_s[q];
+            for (int q = 0; q < 6; ++q) a.eR[6 * e + q] = r2[q] / n;
+            a.epsivar[e] = r2[6] / n;
+        }
+    }
+
+    // equal-population bins
+    if (n < B) {
+        for (int q = threadIdx.x; q < n; q += blockDim.x) a.bin[s0 + q] = 0;
+        for (int b = threadIdx.x; b < B; b += blockDim.x) {
+            a.ecm[(size_t)B * e + b] = mean_s[3];
+            a.ecmT[(size_t)B * e + b] = (T)mean_s[3];
+        }
+        return;
+    }
+    const int G[3] = {a.G0, a.G1, a.G2};
+    if (threadIdx.x == 0) { gstart[0] = 0; gsize[0] = n; }
+    __syncthreads();
+    int ngroups = 1;
+    for (int d = 0; d < 3; ++d) {
+        if (d > 0) {
+            const T* comp = d == 1 ? a.v : a.w;
+            for (int q = threadIdx.x; q < n; q += blockDim.x) K[q].v = ord_bits(comp[s0 + (K[q].gi & 0xffffffu)]);
+            __syncthreads();
+            bitonic(K, N2);
+        }
+        for (int q = threadIdx.x; q < n; q += blockDim.x) {
+            const uint32_t gi = K[q].gi;
+            const int g = (int)(gi >> 24);
+            const int h = chunk_of(q - gstart[g], gsize[g], G[d]);
+            K[q].gi = ((uint32_t)(g * G[d] + h) << 24) | (gi & 0xffffffu);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int t = 0;
+            for (int g = 0; g < ngroups; ++g) {
+                int st = gstart[g];
+                const int m = gsize[g];
+                for (int h = 0; h < G[d]; ++h, ++t) {
+                    const int sz = m / G[d] + (h < m % G[d] ? 1 : 0);
+                    nstart[t] = st;
+                    nsize[t] = sz;
+                    st += sz;
+                }
+            }
+            for (int g = 0; g < t; ++g) { gstart[g] = nstart[g]; gsize[g] = nsize[g]; }
+        }
+        ngroups *= G[d];
+        __syncthreads();
+    }
+    for (int q = threadIdx.x; q < n; q += blockDim.x) {
+        const uint32_t gi = K[q].gi;
+        a.bin[s0 + (gi & 0xffffffu)] = (unsigned char)(gi >> 24);
+    }
+    // <phi|V> per bin: one warp per bin over its contiguous sorted range
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int b = wid; b < B; b += STATS_THREADS / 32) {
+        Acc acc;
+        for (int q = gstart[b] + lane; q < gstart[b] + gsize[b]; q += 32)
+            acc.add((R)a.psi[s0 + (K[q].gi & 0xffffffu)]);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc.merge(acc.shfl_down(o));
+        if (lane == 0) {
+            const double cm = acc.value() / gsize[b];
+            a.ecm[(size_t)B * e + b] = cm;
+            a.ecmT[(size_t)B * e + b] = (T)cm;
+        }
+    }
+}
+
+template <typename T, bool KAHAN>
+int run(pdf_ctx* c) {
+    MomArgs<T> a;
+    a.off = c->off;
+    a.u = (const T*)c->stA[2]; a.v = (const T*)c->stA[3]; a.w = (const T*)c->stA[4];
+    a.om = (const T*)c->stA[5]; a.psi = (const T*)c->stA[6];
+    a.id = c->idA;
+    a.G0 = c->p.nb1; a.G1 = c->p.nb2; a.G2 = c->p.nb3; a.B = c->B;
+    a.en = c->en; a.emean = c->emean; a.eR = c->eR; a.epsivar = c->epsivar; a.ecm = c->ecm;
+    a.ecmT = (T*)c->ecmT;
+    a.bin = c->bin;
+    a.scratch = c->sort_scratch;
+    a.scratch_n = c->sort_scratch_n;
+    a.status = c->d_status;
+    const size_t smem = sizeof(SortKey) * STATS_CAP;
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaFuncSetAttribute(k_moments<T, KAHAN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        attr_set = true;
+    }
+    k_moments<T, KAHAN><<<c->m.nt, STATS_THREADS, smem, c->s>>>(a);
+    ++c->launches;
+    PDF_CUDA(c, cudaGetLastError());
+    return PDF_OK;
+}
+
+}  // namespace
+
+int launch_moments(pdf_ctx* c) {
+    timing_begin(c, PDF_K_MOMENTS);
+    int st;
+    if (c->prec == 0) st = run<double, false>(c);
+    else if (c->prec == 1) st = run<float, false>(c);
+    else st = run<float, true>(c);
+    timing_end(c, PDF_K_MOMENTS);
+    return st;
+}

@@ -1,0 +1,226 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Both sides start from the same seeded mesh, the same particle state and the
+same Philox streams. Bars:
+  * host element ids: bit-exact except particles within 1e-9 (FP64) or 1e-5
+    (FP32) of an element edge in barycentric terms, where the GPU's element
+    must still contain the GPU's position;
+  * one-step particle state: |gpu - oracle| <= rtol (|oracle| + rms) with
+    rtol = 1e-12 (FP64) and 1e-5 (FP32), rms the root mean square of that
+    component over the ensemble;
+  * statistics from the same particles: rtol 1e-12 (FP64 reductions) or
+    2e-6 (compensated FP32 reductions); bins bit-exact;
+  * multi-step statistics of independent runs: within 3 Monte Carlo standard
+    errors (domain averages).
+"""
+import numpy as np
+import pytest
+
+from canyon_inputs.configs import WORKLOADS, build_mesh, cfl_dt
+from canyon_inputs.mesh import canyon_mesh
+from oracle.oracle import Oracle
+from tests.conftest import oracle_params_for
+
+pytestmark = pytest.mark.gpu
+
+STATE = ("x", "y", "u", "v", "w", "om", "psi")
+
+
+def gpu_params(mesh, **kw):
+    from paper_1003_4548_gb300 import canyon_params
+    return canyon_params(mesh, **kw)
+
+
+def both(mesh, *, precision="fp64", wall_model="wf", C0=2.1, seed=0, cg_tol=1e-12, **over):
+    from paper_1003_4548_gb300 import Canyon
+    gp = gpu_params(mesh, wall_model=wall_model, precision=precision, C0=C0, seed=seed, cg_tol=cg_tol,
+                    cg_maxit=20000, **over)
+    op = oracle_params_for(mesh, wall_model=0 if wall_model == "wf" else 1, C0=C0, seed=seed,
+                           cg_tol=1e-13, **over)
+    return Canyon(gp, mesh), Oracle(op, mesh)
+
+
+def by_id(P):
+    order = np.argsort(P["id"], kind="stable")
+    return {k: v[order] for k, v in P.items()}
+
+
+def bary_margin(mesh, P):
+    xy, tri = mesh["xy"], mesh["tri"][P["elem"]]
+    a, b, c = xy[tri[:, 0]], xy[tri[:, 1]], xy[tri[:, 2]]
+    X = np.stack([P["x"], P["y"]], 1)
+
+    def orient(p, q, r):
+        return (q[:, 0] - p[:, 0]) * (r[:, 1] - p[:, 1]) - (q[:, 1] - p[:, 1]) * (r[:, 0] - p[:, 0])
+
+    A = orient(a, b, c)
+    return np.minimum(np.minimum(orient(b, c, X) / A, orient(c, a, X) / A), orient(a, b, X) / A)
+
+
+def assert_state_close(g, o, rtol, skip=None):
+    for k in STATE:
+        d = np.abs(g[k] - o[k])
+        lim = rtol * (np.abs(o[k]) + np.sqrt(np.mean(o[k] ** 2)) + 1e-300)
+        bad = d > lim
+        if skip is not None:
+            bad &= ~skip
+        assert not bad.any(), (k, int(bad.sum()), float(d[bad].max()) if bad.any() else 0.0)
+
+
+def small_mesh():
+    return build_mesh(WORKLOADS["canyon_wf_small"])
+
+
+@pytest.fixture(scope="module")
+def wf_mesh():
+    return small_mesh()
+
+
+@pytest.fixture(scope="module")
+def er_mesh():
+    return canyon_mesh(offset=0.0, h=0.06, y1=2e-3, growth=1.25, seed=2)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_seeding_matches_oracle(wf_mesh, precision):
+    g, o = both(wf_mesh, precision=precision, seed=5)
+    g.seed_particles(24)
+    o.seed(24)
+    G, O = by_id(g.particles()), by_id(o.particles())
+    assert np.array_equal(G["id"], O["id"])
+    assert np.array_equal(G["elem"], O["elem"])
+    rtol = 1e-13 if precision == "fp64" else 1e-7
+    assert_state_close(G, O, rtol)
+    # the library keeps its particles sorted by element
+    assert np.all(np.diff(g.field("elem")) >= 0)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "fp32_kahan"])
+@pytest.mark.parametrize("wall_model", ["wf", "er"])
+def test_statistics_match_oracle(wf_mesh, er_mesh, precision, wall_model):
+    mesh = wf_mesh if wall_model == "wf" else er_mesh
+    g, o = both(mesh, precision=precision, wall_model=wall_model, seed=7)
+    g.seed_particles(24)
+    g.estimate_stats()
+    g.step(cfl_dt(mesh, cfl=0.5, k0=1e-3), 2)  # move the particles across elements
+    g.sync()
+    P = g.particles()
+    o.set_particles(P, step=g.step_index)
+    o.estimate_stats()
+    rt = 1e-12 if precision in ("fp64", "fp32") else 2e-6
+    assert np.array_equal(g.field("elem_n"), o.field("elem_n").astype(np.int32))
+    for name in ("elem_mean", "elem_R", "elem_psivar", "elem_cm", "node_mean", "node_R", "node_ke",
+                 "elem_der", "node_pack", "node_grad"):
+        a, b = g.field(name), o.field(name)
+        scale = np.sqrt(np.mean(b ** 2, axis=0)) + 1e-300
+        tol = rt * (np.abs(b) + scale)
+        if wall_model == "er" and name in ("node_pack",):
+            tol = tol + 1e-8 * scale  # CG tolerance of the drift tensor
+        assert np.all(np.abs(a - b) <= tol), (name, float(np.max(np.abs(a - b) / scale)))
+    if wall_model == "er":
+        a, b = g.field("node_wp"), o.field("node_wp")
+        scale = np.sqrt(np.mean(b ** 2, axis=0))
+        assert np.all(np.abs(a - b) <= 1e-8 * (np.abs(b) + scale))
+    # bins: identical assignment per particle
+    gb = by_id({"id": P["id"], "bin": P["bin"]})
+    ob = by_id({"id": o.particles()["id"], "bin": o.particles()["bin"]})
+    assert np.array_equal(gb["bin"], ob["bin"])
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("wall_model", ["wf", "er"])
+def test_one_step_matches_oracle(wf_mesh, er_mesh, precision, wall_model):
+    mesh = wf_mesh if wall_model == "wf" else er_mesh
+    g, o = both(mesh, precision=precision, wall_model=wall_model, seed=11)
+    dt = cfl_dt(mesh, cfl=0.5, k0=1e-3)
+    g.seed_particles(32)
+    g.estimate_stats()
+    g.step(dt, 3)
+    g.sync()
+    P0 = g.particles()
+    o.set_particles(P0, step=g.step_index)
+    o.estimate_stats()
+    g.step(dt, 1)
+    g.sync()
+    o.advance(dt)
+    G, O = by_id(g.particles()), by_id(o.particles())
+    assert np.array_equal(G["id"], O["id"])
+    edge_tol = 1e-9 if precision == "fp64" else 1e-5
+    near = np.abs(bary_margin(mesh, O)) < edge_tol
+    same = G["elem"] == O["elem"]
+    assert np.all(same | near), int((~same & ~near).sum())
+    if (~same).any():  # near an edge: the GPU element holds the GPU position
+        Gs = {k: v[~same] for k, v in G.items()}
+        assert np.all(bary_margin(mesh, Gs) > -10 * edge_tol)
+    rtol = 1e-12 if precision == "fp64" else 1e-5
+    assert_state_close(G, O, rtol)
+    assert np.array_equal(np.sort(G["elem"]), g.field("elem"))
+
+
+def test_full_size_sampled_parity():
+    """The bench configuration (~40k triangles, 256 per element, FP32 state,
+    elliptic relaxation): sampled particles against the oracle one by one."""
+    cfg = WORKLOADS["canyon_er_full"]
+    mesh = build_mesh(cfg)
+    g, o = both(mesh, precision="fp32", wall_model="er", C0=cfg["C0"], seed=cfg["seed"], cg_tol=1e-10)
+    dt = cfl_dt(mesh, cfl=cfg["cfl"], k0=cfg["k0"])
+    g.seed_particles(cfg["per_element"])
+    g.estimate_stats()
+    g.step(dt, 1)
+    g.sync()
+    P0 = g.particles()
+    n = P0["x"].size
+    assert n == cfg["per_element"] * mesh["tri"].shape[0]
+    # properties that hold at any size
+    assert np.array_equal(np.bincount(P0["elem"], minlength=mesh["tri"].shape[0]), g.field("elem_n"))
+    assert np.all((P0["psi"] >= 0) & (P0["psi"] <= 1))
+    assert np.array_equal(np.sort(P0["id"]), np.arange(n, dtype=np.uint32))
+    o.set_particles(P0, step=g.step_index)
+    o.estimate_stats()
+    g.step(dt, 1)
+    g.sync()
+    G = g.particles()
+    rng = np.random.default_rng(0)
+    sample = rng.choice(n, 4000, replace=False)  # indices into the oracle's (= P0) order
+    o.advance_subset(dt, sample)
+    O = o.particles()
+    Os = {k: v[sample] for k, v in O.items()}
+    pos = np.argsort(G["id"])
+    Gs = {k: v[pos[Os["id"]]] for k, v in G.items()}
+    near = np.abs(bary_margin(mesh, Os)) < 1e-5
+    same = Gs["elem"] == Os["elem"]
+    assert np.all(same | near)
+    assert_state_close(Gs, Os, 1e-5)
+
+
+def test_multistep_statistics_within_standard_errors(wf_mesh):
+    """Independent 100-step runs of the small wall-function canyon agree in
+    their domain-averaged statistics within 3 Monte Carlo standard errors."""
+    cfg = WORKLOADS["canyon_wf_small"]
+    g, o = both(wf_mesh, precision="fp64", seed=cfg["seed"])
+    dt = cfl_dt(wf_mesh, cfl=cfg["cfl"], k0=cfg["k0"])
+    g.seed_particles(cfg["per_element"])
+    g.estimate_stats()
+    o.seed(cfg["per_element"])
+    o.estimate_stats()
+    g.step(dt, cfg["steps"])
+    g.sync()
+    o.step(dt, cfg["steps"])
+    G, O = g.particles(), o.particles()
+    for k in ("u", "v", "w", "om", "psi"):
+        se = np.sqrt(G[k].var() / G[k].size + O[k].var() / O[k].size)
+        assert abs(G[k].mean() - O[k].mean()) <= 3 * se + 1e-12, k
+    for k in ("u", "v"):
+        se = np.sqrt(2.0 / G[k].size) * G[k].var() * np.sqrt(2)
+        assert abs(G[k].var() - O[k].var()) <= 3 * se + 1e-12, k
+
+
+def test_errors_are_reported_not_fatal(wf_mesh):
+    g, _ = both(wf_mesh, seed=3, Cs=1e-9, Ct=1e-9)  # tiny t_m: dt/t_m far above one
+    g.seed_particles(8)
+    g.estimate_stats()
+    g.step(1e-3, 1)
+    assert g.sync(check=False) == -8
+    assert g.sync(check=False) == 0  # the status word is reset, the context stays usable
+    P = g.particles()
+    assert P["x"].size == 8 * wf_mesh["tri"].shape[0]
