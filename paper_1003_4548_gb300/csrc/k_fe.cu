@@ -212,7 +212,7 @@ __global__ void __launch_bounds__(FE_THREADS) k_pcg(const CGArgs a) {
         s_rr[threadIdx.x] = s_new[NC + threadIdx.x];
         s_bn[threadIdx.x] = sqrt(s_new[2 * NC + threadIdx.x]);
     }
-    __syncthreads();
+    grid_barrier(a);  // every block has read the partials before they are reused
     int it = 0;
     for (;; ++it) {
         if (threadIdx.x < NC) {

@@ -155,7 +155,8 @@ __global__ void __launch_bounds__(256) k_step(const StepArgs<T> a) {
             for (int k = 0; k < 3; ++k) {
                 if (k != entry && lq[k] < (T)0) {
                     const T lp = ge[2 + 3 * k] * pdx + ge[3 + 3 * k] * pdy + ge[4 + 3 * k];
-                    const T t = lp / (lp - lq[k]);
+                    const T den = lp - lq[k];
+                    const T t = den > (T)0 ? lp / den : (T)0;
                     if (t < tb) { tb = t; kx = k; lqk = lq[k]; }
                 }
             }
