@@ -134,18 +134,38 @@ __device__ void block_partial(const CGArgs& a, double (&v)[NV], int slot) {
     __syncthreads();
 }
 
-// after a barrier: every block sums the partials in block order
+// after a barrier: every block sums the partials of all blocks; value q is
+// reduced by warp q % 8 over a fixed lane-strided order and shuffle tree
+// (deterministic, identical in every block)
 __device__ void grid_sum(const CGArgs& a, int slot, int nv, double* out_shared) {
-    if (threadIdx.x < nv) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int q = wid; q < nv; q += FE_THREADS / 32) {
         double s = 0.0;
-        for (int bl = 0; bl < (int)gridDim.x; ++bl) s += a.part[(size_t)bl * 3 * NC + slot + threadIdx.x];
-        out_shared[threadIdx.x] = s;
+        for (int bl = lane; bl < (int)gridDim.x; bl += 32) s += a.part[(size_t)bl * 3 * NC + slot + q];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        if (lane == 0) out_shared[q] = s;
     }
     __syncthreads();
 }
 
+// y = A v on the free canonical rows (0 elsewhere) for the NC components
+__device__ __forceinline__ void spmv_row(const CGArgs& a, int i, const double* v, double (&s)[NC]) {
+#pragma unroll
+    for (int k = 0; k < NC; ++k) s[k] = 0.0;
+    for (int q = a.rowptr[i]; q < a.rowptr[i + 1]; ++q) {
+        const int j = a.colidx[q];
+        const double A = a.aval[q];
+#pragma unroll
+        for (int k = 0; k < NC; ++k) s[k] += A * v[NC * (size_t)j + k];
+    }
+}
+
+// Jacobi-preconditioned CG with the product A p carried by the recurrence
+// A p_{k+1} = A z_{k+1} + beta_k A p_k, so each iteration needs one SpMV and
+// two grid-wide reductions (two barriers).
 __global__ void __launch_bounds__(FE_THREADS) k_pcg(const CGArgs a) {
-    __shared__ double s_rz[NC], s_rr[NC], s_bn[NC], s_pap[NC], s_new[2 * NC];
+    __shared__ double s_rz[NC], s_rr[NC], s_bn[NC], s_pap[NC], s_new[3 * NC];
     __shared__ int s_active[NC];
     const int stride = gridDim.x * blockDim.x;
     const int t0 = blockIdx.x * blockDim.x + threadIdx.x;
@@ -170,7 +190,7 @@ __global__ void __launch_bounds__(FE_THREADS) k_pcg(const CGArgs a) {
         }
     }
     grid_barrier(a);
-    // r = b - A x on free canonical rows; z = D^-1 r; p = z
+    // r = b - A x on free canonical rows; z = p = D^-1 r
     {
         double v[3 * NC] = {0};
         for (int i = t0; i < a.nn; i += stride) {
@@ -194,7 +214,7 @@ __global__ void __launch_bounds__(FE_THREADS) k_pcg(const CGArgs a) {
             const double dg = (free_row && a.diag[i] >= 0) ? a.aval[a.diag[i]] : 1.0;
 #pragma unroll
             for (int k = 0; k < NC; ++k) {
-                const double zi = ri[k] / dg;
+                const double zi = free_row ? ri[k] / dg : 0.0;
                 a.r[NC * (size_t)i + k] = ri[k];
                 a.z[NC * (size_t)i + k] = zi;
                 a.pv[NC * (size_t)i + k] = zi;
@@ -212,7 +232,25 @@ __global__ void __launch_bounds__(FE_THREADS) k_pcg(const CGArgs a) {
         s_rr[threadIdx.x] = s_new[NC + threadIdx.x];
         s_bn[threadIdx.x] = sqrt(s_new[2 * NC + threadIdx.x]);
     }
-    grid_barrier(a);  // every block has read the partials before they are reused
+    grid_barrier(a);  // all blocks have read the partials before they are reused
+    // A p_0 and p_0.A p_0
+    {
+        double v[NC] = {0, 0, 0, 0, 0};
+        for (int i = t0; i < a.nn; i += stride) {
+            const bool free_row = a.rep[i] == i && !a.is_wall[i];
+            double s[NC];
+            spmv_row(a, i, a.pv, s);
+#pragma unroll
+            for (int k = 0; k < NC; ++k) {
+                const double ap = free_row ? s[k] : 0.0;
+                a.ap[NC * (size_t)i + k] = ap;
+                v[k] += a.pv[NC * (size_t)i + k] * ap;
+            }
+        }
+        block_partial<NC>(a, v, 2 * NC);
+    }
+    grid_barrier(a);
+    grid_sum(a, 2 * NC, NC, s_pap);
     int it = 0;
     for (;; ++it) {
         if (threadIdx.x < NC) {
@@ -227,31 +265,7 @@ __global__ void __launch_bounds__(FE_THREADS) k_pcg(const CGArgs a) {
             if (t0 == 0) set_status(a.status, ST_CG);
             break;
         }
-        // Ap and p.Ap
-        {
-            double v[NC] = {0, 0, 0, 0, 0};
-            for (int i = t0; i < a.nn; i += stride) {
-                const bool free_row = a.rep[i] == i && !a.is_wall[i];
-                double s[NC] = {0, 0, 0, 0, 0};
-                if (free_row) {
-                    for (int q = a.rowptr[i]; q < a.rowptr[i + 1]; ++q) {
-                        const int j = a.colidx[q];
-                        const double A = a.aval[q];
-#pragma unroll
-                        for (int k = 0; k < NC; ++k) s[k] += A * a.pv[NC * (size_t)j + k];
-                    }
-                }
-#pragma unroll
-                for (int k = 0; k < NC; ++k) {
-                    a.ap[NC * (size_t)i + k] = s[k];
-                    v[k] += a.pv[NC * (size_t)i + k] * s[k];
-                }
-            }
-            block_partial<NC>(a, v, 0);
-        }
-        grid_barrier(a);
-        grid_sum(a, 0, NC, s_pap);
-        // x += alpha p, r -= alpha Ap, z = D^-1 r
+        // x += alpha p, r -= alpha Ap, z = D^-1 r; partial r.z, r.r
         {
             double v[2 * NC] = {0};
             for (int i = t0; i < a.nn; i += stride) {
@@ -265,32 +279,43 @@ __global__ void __launch_bounds__(FE_THREADS) k_pcg(const CGArgs a) {
                     a.x[o] += alpha * a.pv[o];
                     const double rn = a.r[o] - alpha * a.ap[o];
                     a.r[o] = rn;
-                    const double zn = rn / dg;
+                    const double zn = free_row ? rn / dg : 0.0;
                     a.z[o] = zn;
                     v[k] += rn * zn;
                     v[NC + k] += rn * rn;
                 }
             }
-            block_partial<2 * NC>(a, v, NC);
+            block_partial<2 * NC>(a, v, 0);
         }
         grid_barrier(a);
-        grid_sum(a, NC, 2 * NC, s_new);
-        // p = z + beta p
-        for (int i = t0; i < a.nn; i += stride) {
+        grid_sum(a, 0, 2 * NC, s_new);
+        // p = z + beta p; A p = A z + beta A p; partial p.Ap
+        {
+            double v[NC] = {0, 0, 0, 0, 0};
+            for (int i = t0; i < a.nn; i += stride) {
+                const bool free_row = a.rep[i] == i && !a.is_wall[i];
+                double s[NC];
+                spmv_row(a, i, a.z, s);
 #pragma unroll
-            for (int k = 0; k < NC; ++k) {
-                if (!s_active[k]) continue;
-                const double beta = s_new[k] / s_rz[k];
-                const size_t o = NC * (size_t)i + k;
-                a.pv[o] = a.z[o] + beta * a.pv[o];
+                for (int k = 0; k < NC; ++k) {
+                    if (!s_active[k]) continue;
+                    const double beta = s_new[k] / s_rz[k];
+                    const size_t o = NC * (size_t)i + k;
+                    const double pn = a.z[o] + beta * a.pv[o];
+                    const double apn = (free_row ? s[k] : 0.0) + beta * a.ap[o];
+                    a.pv[o] = pn;
+                    a.ap[o] = apn;
+                    v[k] += pn * apn;
+                }
             }
+            block_partial<NC>(a, v, 2 * NC);
         }
-        __syncthreads();
+        grid_barrier(a);
         if (threadIdx.x < NC && s_active[threadIdx.x]) {
             s_rz[threadIdx.x] = s_new[threadIdx.x];
             s_rr[threadIdx.x] = s_new[NC + threadIdx.x];
         }
-        grid_barrier(a);
+        grid_sum(a, 2 * NC, NC, s_pap);
     }
     if (t0 == 0) *a.iters = it;
 }

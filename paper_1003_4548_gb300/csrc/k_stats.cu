@@ -119,6 +119,7 @@ struct MomArgs {
     SortKey* scratch;
     int64_t scratch_n;
     int* status;
+    int min_n;  // the block kernel only takes elements with more particles than this
 };
 
 __device__ __forceinline__ int chunk_of(int r, int m, int G) {
@@ -137,6 +138,7 @@ __global__ void __launch_bounds__(STATS_THREADS) k_moments(const MomArgs<T> a) {
     const int e = blockIdx.x;
     const int s0 = a.off[e], n = a.off[e + 1] - s0;
     const int B = a.B;
+    if (n <= a.min_n) return;  // done by the warp kernel
     if (n == 0) {
         if (threadIdx.x == 0) {
             a.en[e] = 0;
@@ -280,6 +282,236 @@ __global__ void __launch_bounds__(STATS_THREADS) k_moments(const MomArgs<T> a) {
     }
 }
 
+
+// ---------------------------------------------------------------------------
+// warp-per-element variant for FP32 particle state: the segment's keys live in
+// registers (KPL per lane, lane-major sorted positions) and a bitonic network
+// runs with in-register compare-exchanges for partners in the same lane and
+// xor-shuffles across lanes. Key = (group, value bits, id) compared in that
+// order; payload = the particle's index in the segment (packed with the group).
+// ---------------------------------------------------------------------------
+constexpr int WARP_MAX_N = 512;
+constexpr int WARPS_PER_BLOCK = 4;
+
+struct WKey {
+    uint32_t gi;  // group << 16 | index in the segment
+    uint32_t v;   // order-preserving value bits
+    uint32_t id;
+};
+
+__device__ __forceinline__ bool wkey_gt(const WKey& a, const WKey& b) {
+    const uint32_t ga = a.gi >> 16, gb = b.gi >> 16;
+    if (ga != gb) return ga > gb;
+    if (a.v != b.v) return a.v > b.v;
+    return a.id > b.id;
+}
+
+__device__ __forceinline__ uint32_t ord32(float v) {
+    v = v + 0.0f;
+    const uint32_t b = __float_as_uint(v);
+    return (b >> 31) ? ~b : (b | 0x80000000u);
+}
+
+template <int KPL>
+__device__ __forceinline__ void warp_bitonic(WKey (&k)[KPL], int lane) {
+    constexpr int N = 32 * KPL;
+#pragma unroll
+    for (int kk = 2; kk <= N; kk <<= 1) {
+#pragma unroll
+        for (int j = kk >> 1; j > 0; j >>= 1) {
+            if (j < KPL) {
+#pragma unroll
+                for (int r = 0; r < KPL; ++r) {
+                    const int r2 = r ^ j;
+                    if (r2 > r) {
+                        const int p = lane * KPL + r;
+                        const bool asc = (p & kk) == 0;
+                        if (asc == wkey_gt(k[r], k[r2])) {
+                            const WKey t = k[r];
+                            k[r] = k[r2];
+                            k[r2] = t;
+                        }
+                    }
+                }
+            } else {
+                const int m = j / KPL;
+                const bool lower = (lane & m) == 0;
+#pragma unroll
+                for (int r = 0; r < KPL; ++r) {
+                    WKey o;
+                    o.gi = __shfl_xor_sync(0xffffffffu, k[r].gi, m);
+                    o.v = __shfl_xor_sync(0xffffffffu, k[r].v, m);
+                    o.id = __shfl_xor_sync(0xffffffffu, k[r].id, m);
+                    const int p = lane * KPL + r;
+                    const bool asc = (p & kk) == 0;
+                    const bool gt = wkey_gt(k[r], o);
+                    if ((lower == asc) ? gt : !gt) k[r] = o;
+                }
+            }
+        }
+    }
+}
+
+// start and size of group g (mixed-radix digits over the levels done so far)
+__device__ __forceinline__ void group_range(int n, const int* G, int level, int g, int& start, int& size) {
+    int digits[3];
+    int t = g;
+    for (int d = level - 1; d >= 0; --d) {
+        digits[d] = t % G[d];
+        t /= G[d];
+    }
+    start = 0;
+    size = n;
+    for (int d = 0; d < level; ++d) {
+        const int base = size / G[d], rem = size % G[d], h = digits[d];
+        start += h * base + (h < rem ? h : rem);
+        size = base + (h < rem ? 1 : 0);
+    }
+}
+
+template <typename Acc>
+__device__ __forceinline__ void warp_tree(Acc& a) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) a.merge(a.shfl_down(o));
+}
+
+template <bool KAHAN, int KPL>
+__device__ void warp_element(const MomArgs<float>& a, int e, int s0, int n, int lane, float* psi_s) {
+    using Acc = typename AccSel<float, KAHAN>::type;
+    using R = typename AccSel<float, KAHAN>::R;
+    const int B = a.B;
+    const int G[3] = {a.G0, a.G1, a.G2};
+    WKey k[KPL];
+    // coalesced load: element r*32+lane of the segment into slot r
+#pragma unroll
+    for (int r = 0; r < KPL; ++r) {
+        const int q = r * 32 + lane;
+        if (q < n) {
+            k[r].gi = (uint32_t)q;
+            k[r].v = ord32(a.u[s0 + q]);
+            k[r].id = a.id[s0 + q];
+        } else {
+            k[r].gi = 0xffffffffu; k[r].v = 0xffffffffu; k[r].id = 0xffffffffu;
+        }
+    }
+    warp_bitonic<KPL>(k, lane);
+    // ensemble averages in the canonical (U, id) order: lane-major positions
+    Acc m[5];
+#pragma unroll
+    for (int r = 0; r < KPL; ++r) {
+        if (lane * KPL + r < n) {
+            const int j = s0 + (int)(k[r].gi & 0xffffu);
+            m[0].add((R)a.u[j]); m[1].add((R)a.v[j]); m[2].add((R)a.w[j]);
+            m[3].add((R)a.psi[j]); m[4].add((R)a.om[j]);
+        }
+    }
+    double mean[5];
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+        warp_tree(m[q]);
+        mean[q] = __shfl_sync(0xffffffffu, m[q].value(), 0) / n;
+    }
+    const R mu = (R)mean[0], mv = (R)mean[1], mw = (R)mean[2], mp = (R)mean[3];
+    Acc c2[7];
+#pragma unroll
+    for (int r = 0; r < KPL; ++r) {
+        if (lane * KPL + r < n) {
+            const int j = s0 + (int)(k[r].gi & 0xffffu);
+            const R du = (R)a.u[j] - mu, dv = (R)a.v[j] - mv, dw = (R)a.w[j] - mw, dp = (R)a.psi[j] - mp;
+            c2[0].add(du * du); c2[1].add(dv * dv); c2[2].add(dw * dw);
+            c2[3].add(du * dv); c2[4].add(du * dw); c2[5].add(dv * dw); c2[6].add(dp * dp);
+        }
+    }
+    double r2[7];
+#pragma unroll
+    for (int q = 0; q < 7; ++q) {
+        warp_tree(c2[q]);
+        r2[q] = c2[q].value();
+    }
+    if (lane == 0) {
+        a.en[e] = n;
+        for (int q = 0; q < 5; ++q) a.emean[5 * e + q] = mean[q];
+        for (int q = 0; q < 6; ++q) a.eR[6 * e + q] = r2[q] / n;
+        a.epsivar[e] = r2[6] / n;
+    }
+    if (n < B) {
+        for (int q = lane; q < n; q += 32) a.bin[s0 + q] = 0;
+        for (int b = lane; b < B; b += 32) {
+            a.ecm[(size_t)B * e + b] = mean[3];
+            a.ecmT[(size_t)B * e + b] = (float)mean[3];
+        }
+        return;
+    }
+    // equal-population groups, level by level
+#pragma unroll 1
+    for (int d = 0; d < 3; ++d) {
+        if (d > 0) {
+            const float* comp = d == 1 ? a.v : a.w;
+#pragma unroll
+            for (int r = 0; r < KPL; ++r)
+                if (lane * KPL + r < n) k[r].v = ord32(comp[s0 + (k[r].gi & 0xffffu)]);
+            warp_bitonic<KPL>(k, lane);
+        }
+#pragma unroll
+        for (int r = 0; r < KPL; ++r) {
+            const int p = lane * KPL + r;
+            if (p < n) {
+                const int g = (int)(k[r].gi >> 16);
+                int st, sz;
+                group_range(n, G, d, g, st, sz);
+                const int h = chunk_of(p - st, sz, G[d]);
+                k[r].gi = ((uint32_t)(g * G[d] + h) << 16) | (k[r].gi & 0xffffu);
+            }
+        }
+    }
+    // bins per particle; psi in sorted order for the per-bin means
+#pragma unroll
+    for (int r = 0; r < KPL; ++r) {
+        const int p = lane * KPL + r;
+        if (p < n) {
+            const int j = s0 + (int)(k[r].gi & 0xffffu);
+            a.bin[j] = (unsigned char)(k[r].gi >> 16);
+            psi_s[p] = a.psi[j];
+        }
+    }
+    __syncwarp();
+    for (int b = lane; b < B; b += 32) {
+        int st, sz;
+        group_range(n, G, 3, b, st, sz);
+        Acc acc;
+        for (int q = st; q < st + sz; ++q) acc.add((R)psi_s[q]);
+        const double cm = acc.value() / sz;
+        a.ecm[(size_t)B * e + b] = cm;
+        a.ecmT[(size_t)B * e + b] = (float)cm;
+    }
+    __syncwarp();
+}
+
+template <bool KAHAN, int KPL>
+__global__ void __launch_bounds__(32 * WARPS_PER_BLOCK) k_moments_warp(const MomArgs<float> a, int nt) {
+    __shared__ float psi_s[WARPS_PER_BLOCK][32 * KPL];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int e = blockIdx.x * WARPS_PER_BLOCK + w;
+    if (e >= nt) return;
+    const int s0 = a.off[e], n = a.off[e + 1] - s0;
+    // size classes: 8 keys per lane for n <= 256, 16 for 256 < n <= 512
+    if (n > 32 * KPL || (KPL == 16 && n <= 256)) return;
+    if (n == 0) {
+        if (lane == 0) {
+            a.en[e] = 0;
+            for (int q = 0; q < 5; ++q) a.emean[5 * e + q] = 0.0;
+            for (int q = 0; q < 6; ++q) a.eR[6 * e + q] = 0.0;
+            a.epsivar[e] = 0.0;
+        }
+        for (int b = lane; b < a.B; b += 32) {
+            a.ecm[(size_t)a.B * e + b] = 0.0;
+            a.ecmT[(size_t)a.B * e + b] = 0.f;
+        }
+        return;
+    }
+    warp_element<KAHAN, KPL>(a, e, s0, n, lane, psi_s[w]);
+}
+
 template <typename T, bool KAHAN>
 int run(pdf_ctx* c) {
     MomArgs<T> a;
@@ -294,6 +526,15 @@ int run(pdf_ctx* c) {
     a.scratch = c->sort_scratch;
     a.scratch_n = c->sort_scratch_n;
     a.status = c->d_status;
+    a.min_n = -1;
+    if constexpr (sizeof(T) == 4) {
+        // warp-per-element kernels for the size classes (0,256] and (256,512]
+        a.min_n = WARP_MAX_N;
+        const unsigned blocks = (unsigned)((c->m.nt + WARPS_PER_BLOCK - 1) / WARPS_PER_BLOCK);
+        k_moments_warp<KAHAN, 8><<<blocks, 32 * WARPS_PER_BLOCK, 0, c->s>>>(a, c->m.nt);
+        k_moments_warp<KAHAN, 16><<<blocks, 32 * WARPS_PER_BLOCK, 0, c->s>>>(a, c->m.nt);
+        c->launches += 2;
+    }
     const size_t smem = sizeof(SortKey) * STATS_CAP;
     static bool attr_set = false;
     if (!attr_set) {
