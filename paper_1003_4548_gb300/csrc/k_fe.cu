@@ -72,20 +72,23 @@ struct CGArgs {
     const int* __restrict__ kc_elem;
     const double* __restrict__ kc_geo;
     const double* __restrict__ eder;  // L in column 8
-    const int* __restrict__ diag;
     const int* __restrict__ rep;
     const unsigned char* __restrict__ is_wall;
     const double* __restrict__ f;
     const double* __restrict__ g;
     double* aval;
-    double *x, *b, *r, *z, *pv, *ap;  // [nn][NC]; x is the node solution (warm start in, result out)
-    double* part;                      // [gridDim][3*NC]
+    double* x;     // [nn][NC] node solution: warm start in, result out (canonical rows)
+    double* zg;    // [nn][NC] preconditioned residual, shared between blocks for the SpMV
+    double* part;  // [gridDim][PART_W]
     unsigned* bar;
     int* iters;
     int* status;
     double tol;
     int maxit;
 };
+
+constexpr int BS = 128;        // rows per block = size of the block-Jacobi diagonal blocks
+constexpr int PART_W = 4 * NC; // partial sums per block: 3 NC in phase A, NC in phase B
 
 __device__ void grid_barrier(const CGArgs& a) {
     __syncthreads();
@@ -101,11 +104,11 @@ __device__ void grid_barrier(const CGArgs& a) {
         } else {
             long long spins = 0;
             while (*gen == g0) {
-                if (++spins > (1ll << 26)) {
+                if (++spins > (1ll << 27)) {
                     set_status(a.status, ST_BARRIER);
                     break;
                 }
-                __nanosleep(64);
+                __nanosleep(20);
             }
         }
         __threadfence();
@@ -113,10 +116,10 @@ __device__ void grid_barrier(const CGArgs& a) {
     __syncthreads();
 }
 
-// sum of NV per-thread values over the block, written to part[block][slot..]
+// block sums of NV per-thread values into part[block][slot..slot+NV)
 template <int NV>
 __device__ void block_partial(const CGArgs& a, double (&v)[NV], int slot) {
-    __shared__ double red[FE_THREADS / 32][3 * NC];
+    __shared__ double red[BS / 32][PART_W];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
     for (int q = 0; q < NV; ++q)
@@ -128,29 +131,28 @@ __device__ void block_partial(const CGArgs& a, double (&v)[NV], int slot) {
     __syncthreads();
     if (threadIdx.x < NV) {
         double s = 0.0;
-        for (int w = 0; w < FE_THREADS / 32; ++w) s += red[w][threadIdx.x];
-        a.part[(size_t)blockIdx.x * 3 * NC + slot + threadIdx.x] = s;
+#pragma unroll
+        for (int w = 0; w < BS / 32; ++w) s += red[w][threadIdx.x];
+        a.part[(size_t)blockIdx.x * PART_W + slot + threadIdx.x] = s;
     }
     __syncthreads();
 }
 
-// after a barrier: every block sums the partials of all blocks; value q is
-// reduced by warp q % 8 over a fixed lane-strided order and shuffle tree
-// (deterministic, identical in every block)
-__device__ void grid_sum(const CGArgs& a, int slot, int nv, double* out_shared) {
+// after a barrier: the sums over all blocks; value q is reduced by warp q % 4
+// in a fixed lane-strided order and shuffle tree (the same in every block)
+__device__ void grid_sum(const CGArgs& a, int slot, int nv, double* out) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    for (int q = wid; q < nv; q += FE_THREADS / 32) {
+    for (int q = wid; q < nv; q += BS / 32) {
         double s = 0.0;
-        for (int bl = lane; bl < (int)gridDim.x; bl += 32) s += a.part[(size_t)bl * 3 * NC + slot + q];
+        for (int bl = lane; bl < (int)gridDim.x; bl += 32) s += a.part[(size_t)bl * PART_W + slot + q];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-        if (lane == 0) out_shared[q] = s;
+        if (lane == 0) out[q] = s;
     }
     __syncthreads();
 }
 
-// y = A v on the free canonical rows (0 elsewhere) for the NC components
-__device__ __forceinline__ void spmv_row(const CGArgs& a, int i, const double* v, double (&s)[NC]) {
+__device__ __forceinline__ void spmv_row(const CGArgs& a, int i, const double* __restrict__ v, double (&s)[NC]) {
 #pragma unroll
     for (int k = 0; k < NC; ++k) s[k] = 0.0;
     for (int q = a.rowptr[i]; q < a.rowptr[i + 1]; ++q) {
@@ -161,17 +163,44 @@ __device__ __forceinline__ void spmv_row(const CGArgs& a, int i, const double* v
     }
 }
 
-// Jacobi-preconditioned CG with the product A p carried by the recurrence
-// A p_{k+1} = A z_{k+1} + beta_k A p_k, so each iteration needs one SpMV and
-// two grid-wide reductions (two barriers).
-__global__ void __launch_bounds__(FE_THREADS) k_pcg(const CGArgs a) {
-    __shared__ double s_rz[NC], s_rr[NC], s_bn[NC], s_pap[NC], s_new[3 * NC];
+// z = Ainv_b r for the block's rows (FP32 dense product in shared memory)
+__device__ __forceinline__ void block_precondition(const float* __restrict__ inv, float (*rv)[NC], int t,
+                                                   const double (&r)[NC], double (&z)[NC]) {
+#pragma unroll
+    for (int k = 0; k < NC; ++k) rv[t][k] = (float)r[k];
+    __syncthreads();
+    float acc[NC] = {0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll 4
+    for (int j = 0; j < BS; ++j) {
+        const float m = inv[j * BS + t];
+#pragma unroll
+        for (int k = 0; k < NC; ++k) acc[k] += m * rv[j][k];
+    }
+#pragma unroll
+    for (int k = 0; k < NC; ++k) z[k] = (double)acc[k];
+    __syncthreads();
+}
+
+// Flexible (Polak-Ribiere) preconditioned CG in FP64 for the NC right-hand
+// sides, block-Jacobi preconditioner with FP32 explicit inverses of the 128 x
+// 128 diagonal blocks (one block of rows per thread block, inverted in shared
+// memory by Gauss-Jordan without pivoting: the blocks are SPD). The vectors of
+// a row live in the registers of its thread; the product A p follows the
+// recurrence A p_{k+1} = A z_{k+1} + beta_k A p_k, so one SpMV (on z) and two
+// grid reductions per iteration.
+__global__ void __launch_bounds__(BS) k_pcg(const CGArgs a) {
+    extern __shared__ float inv[];  // BS*BS, column j at inv[j*BS .. j*BS+BS)
+    __shared__ float rv[BS][NC];
+    __shared__ double s_a[PART_W];
+    __shared__ double s_rz[NC], s_rr[NC], s_bn[NC], s_pap[NC];
     __shared__ int s_active[NC];
-    const int stride = gridDim.x * blockDim.x;
-    const int t0 = blockIdx.x * blockDim.x + threadIdx.x;
-    // assembly of M + K_{L^2}; b = M f; Dirichlet values into x
-    for (int i = t0; i < a.nn; i += stride) {
-        double bi[NC] = {0, 0, 0, 0, 0};
+    const int t = threadIdx.x;
+    const int i = blockIdx.x * BS + t;
+    const bool have = i < a.nn;
+    const bool free_row = have && a.rep[i] == i && !a.is_wall[i];
+    // assembly of M + K_{L^2}; b = M f; Dirichlet values
+    double b[NC] = {0, 0, 0, 0, 0}, x[NC] = {0, 0, 0, 0, 0};
+    if (have) {
         for (int q = a.rowptr[i]; q < a.rowptr[i + 1]; ++q) {
             double s = a.mval[q];
             for (int c = a.kc_off[q]; c < a.kc_off[q + 1]; ++c) {
@@ -181,143 +210,166 @@ __global__ void __launch_bounds__(FE_THREADS) k_pcg(const CGArgs a) {
             a.aval[q] = s;
             const int j = a.colidx[q];
 #pragma unroll
-            for (int k = 0; k < NC; ++k) bi[k] += a.mval[q] * a.f[NC * (size_t)j + k];
+            for (int k = 0; k < NC; ++k) b[k] += a.mval[q] * a.f[NC * (size_t)j + k];
         }
 #pragma unroll
         for (int k = 0; k < NC; ++k) {
-            a.b[NC * (size_t)i + k] = bi[k];
-            if (a.is_wall[i]) a.x[NC * (size_t)i + k] = a.g[NC * (size_t)i + k];
+            x[k] = a.is_wall[i] ? a.g[NC * (size_t)i + k] : a.x[NC * (size_t)i + k];
+            a.x[NC * (size_t)i + k] = x[k];
         }
     }
-    grid_barrier(a);
-    // r = b - A x on free canonical rows; z = p = D^-1 r
+    // diagonal block of the free rows (identity elsewhere), column-major
+    for (int q = t; q < BS * BS; q += BS) inv[q] = 0.f;
+    __syncthreads();
+    if (have) {
+        if (free_row) {
+            for (int q = a.rowptr[i]; q < a.rowptr[i + 1]; ++q) {
+                const int j = a.colidx[q], jl = j - blockIdx.x * BS;
+                if (jl >= 0 && jl < BS && a.rep[j] == j && !a.is_wall[j]) inv[jl * BS + t] = (float)a.aval[q];
+            }
+        } else {
+            inv[t * BS + t] = 1.f;
+        }
+    } else {
+        inv[t * BS + t] = 1.f;
+    }
+    __syncthreads();
+    for (int k = 0; k < BS; ++k) {  // in-place Gauss-Jordan inverse
+        const float fk = inv[k * BS + t];       // a[t][k]
+        const float p = inv[k * BS + k];
+        __syncthreads();
+        {
+            const float v = (t == k) ? 1.f : inv[t * BS + k];  // a[k][t]
+            inv[t * BS + k] = v / p;
+        }
+        __syncthreads();
+        if (t != k) {
+            inv[k * BS + t] = 0.f;
+            for (int j = 0; j < BS; ++j) inv[j * BS + t] -= fk * inv[j * BS + k];
+        }
+        __syncthreads();
+    }
+    grid_barrier(a);  // all x (warm start + Dirichlet) and matrix rows are in place
+    // r = b - A x; z = Ainv r; p = z
+    double r[NC], z[NC], p[NC], ap[NC];
     {
-        double v[3 * NC] = {0};
-        for (int i = t0; i < a.nn; i += stride) {
-            const bool free_row = a.rep[i] == i && !a.is_wall[i];
-            double ri[NC] = {0, 0, 0, 0, 0}, b0[NC] = {0, 0, 0, 0, 0};
-            if (free_row) {
+        double s[NC], b0[NC];
 #pragma unroll
-                for (int k = 0; k < NC; ++k) ri[k] = b0[k] = a.b[NC * (size_t)i + k];
-                for (int q = a.rowptr[i]; q < a.rowptr[i + 1]; ++q) {
-                    const int j = a.colidx[q];
-                    const double A = a.aval[q];
-                    const bool dj = a.is_wall[j];
+        for (int k = 0; k < NC; ++k) { s[k] = 0.0; b0[k] = b[k]; }
+        if (free_row) {
+            for (int q = a.rowptr[i]; q < a.rowptr[i + 1]; ++q) {
+                const int j = a.colidx[q];
+                const double A = a.aval[q];
+                const bool dj = a.is_wall[j];
 #pragma unroll
-                    for (int k = 0; k < NC; ++k) {
-                        const double xv = a.x[NC * (size_t)j + k];
-                        ri[k] -= A * xv;
-                        if (dj) b0[k] -= A * xv;
-                    }
+                for (int k = 0; k < NC; ++k) {
+                    const double xv = a.x[NC * (size_t)j + k];
+                    s[k] += A * xv;
+                    if (dj) b0[k] -= A * xv;
                 }
             }
-            const double dg = (free_row && a.diag[i] >= 0) ? a.aval[a.diag[i]] : 1.0;
+        }
 #pragma unroll
-            for (int k = 0; k < NC; ++k) {
-                const double zi = free_row ? ri[k] / dg : 0.0;
-                a.r[NC * (size_t)i + k] = ri[k];
-                a.z[NC * (size_t)i + k] = zi;
-                a.pv[NC * (size_t)i + k] = zi;
-                v[k] += ri[k] * zi;
-                v[NC + k] += ri[k] * ri[k];
-                v[2 * NC + k] += b0[k] * b0[k];
-            }
+        for (int k = 0; k < NC; ++k) r[k] = free_row ? b[k] - s[k] : 0.0;
+        block_precondition(inv, rv, t, r, z);
+        double v[3 * NC];
+#pragma unroll
+        for (int k = 0; k < NC; ++k) {
+            if (!free_row) z[k] = 0.0;
+            p[k] = z[k];
+            v[k] = r[k] * z[k];
+            v[NC + k] = r[k] * r[k];
+            v[2 * NC + k] = free_row ? b0[k] * b0[k] : 0.0;
+            if (have) a.zg[NC * (size_t)i + k] = z[k];
         }
         block_partial<3 * NC>(a, v, 0);
     }
     grid_barrier(a);
-    grid_sum(a, 0, 3 * NC, s_new);
-    if (threadIdx.x < NC) {
-        s_rz[threadIdx.x] = s_new[threadIdx.x];
-        s_rr[threadIdx.x] = s_new[NC + threadIdx.x];
-        s_bn[threadIdx.x] = sqrt(s_new[2 * NC + threadIdx.x]);
+    grid_sum(a, 0, 3 * NC, s_a);
+    if (t < NC) {
+        s_rz[t] = s_a[t];
+        s_rr[t] = s_a[NC + t];
+        s_bn[t] = sqrt(s_a[2 * NC + t]);
     }
-    grid_barrier(a);  // all blocks have read the partials before they are reused
-    // A p_0 and p_0.A p_0
-    {
-        double v[NC] = {0, 0, 0, 0, 0};
-        for (int i = t0; i < a.nn; i += stride) {
-            const bool free_row = a.rep[i] == i && !a.is_wall[i];
-            double s[NC];
-            spmv_row(a, i, a.pv, s);
+    {  // A p_0
+        double s[NC], v[NC];
+        if (free_row) spmv_row(a, i, a.zg, s);
 #pragma unroll
-            for (int k = 0; k < NC; ++k) {
-                const double ap = free_row ? s[k] : 0.0;
-                a.ap[NC * (size_t)i + k] = ap;
-                v[k] += a.pv[NC * (size_t)i + k] * ap;
-            }
+        for (int k = 0; k < NC; ++k) {
+            ap[k] = free_row ? s[k] : 0.0;
+            v[k] = p[k] * ap[k];
         }
-        block_partial<NC>(a, v, 2 * NC);
+        block_partial<NC>(a, v, 3 * NC);
     }
     grid_barrier(a);
-    grid_sum(a, 2 * NC, NC, s_pap);
+    grid_sum(a, 3 * NC, NC, s_pap);
     int it = 0;
     for (;; ++it) {
-        if (threadIdx.x < NC) {
-            const int k = threadIdx.x;
-            s_active[k] = (s_bn[k] > 0.0) && (sqrt(s_rr[k]) > a.tol * s_bn[k]);
-        }
+        if (t < NC) s_active[t] = (s_bn[t] > 0.0) && (sqrt(s_rr[t]) > a.tol * s_bn[t]);
         __syncthreads();
         bool any = false;
+#pragma unroll
         for (int k = 0; k < NC; ++k) any |= s_active[k] != 0;
         if (!any) break;
         if (it >= a.maxit) {
-            if (t0 == 0) set_status(a.status, ST_CG);
+            if (blockIdx.x == 0 && t == 0) set_status(a.status, ST_CG);
             break;
         }
-        // x += alpha p, r -= alpha Ap, z = D^-1 r; partial r.z, r.r
+        // phase A: x += alpha p, r -= alpha Ap, z = Ainv r
         {
-            double v[2 * NC] = {0};
-            for (int i = t0; i < a.nn; i += stride) {
-                const bool free_row = a.rep[i] == i && !a.is_wall[i];
-                const double dg = (free_row && a.diag[i] >= 0) ? a.aval[a.diag[i]] : 1.0;
+            double rold[NC];
 #pragma unroll
-                for (int k = 0; k < NC; ++k) {
-                    if (!s_active[k]) continue;
+            for (int k = 0; k < NC; ++k) {
+                rold[k] = r[k];
+                if (s_active[k]) {
                     const double alpha = s_rz[k] / s_pap[k];
-                    const size_t o = NC * (size_t)i + k;
-                    a.x[o] += alpha * a.pv[o];
-                    const double rn = a.r[o] - alpha * a.ap[o];
-                    a.r[o] = rn;
-                    const double zn = free_row ? rn / dg : 0.0;
-                    a.z[o] = zn;
-                    v[k] += rn * zn;
-                    v[NC + k] += rn * rn;
+                    x[k] += alpha * p[k];
+                    r[k] -= alpha * ap[k];
                 }
             }
-            block_partial<2 * NC>(a, v, 0);
-        }
-        grid_barrier(a);
-        grid_sum(a, 0, 2 * NC, s_new);
-        // p = z + beta p; A p = A z + beta A p; partial p.Ap
-        {
-            double v[NC] = {0, 0, 0, 0, 0};
-            for (int i = t0; i < a.nn; i += stride) {
-                const bool free_row = a.rep[i] == i && !a.is_wall[i];
-                double s[NC];
-                spmv_row(a, i, a.z, s);
+            double zn[NC];
+            block_precondition(inv, rv, t, r, zn);
+            double v[3 * NC];
 #pragma unroll
-                for (int k = 0; k < NC; ++k) {
-                    if (!s_active[k]) continue;
-                    const double beta = s_new[k] / s_rz[k];
-                    const size_t o = NC * (size_t)i + k;
-                    const double pn = a.z[o] + beta * a.pv[o];
-                    const double apn = (free_row ? s[k] : 0.0) + beta * a.ap[o];
-                    a.pv[o] = pn;
-                    a.ap[o] = apn;
-                    v[k] += pn * apn;
-                }
+            for (int k = 0; k < NC; ++k) {
+                if (!free_row) zn[k] = 0.0;
+                if (s_active[k]) z[k] = zn[k];
+                v[k] = r[k] * z[k];
+                v[NC + k] = rold[k] * z[k];
+                v[2 * NC + k] = r[k] * r[k];
+                if (have) a.zg[NC * (size_t)i + k] = z[k];
             }
-            block_partial<NC>(a, v, 2 * NC);
+            block_partial<3 * NC>(a, v, 0);
         }
         grid_barrier(a);
-        if (threadIdx.x < NC && s_active[threadIdx.x]) {
-            s_rz[threadIdx.x] = s_new[threadIdx.x];
-            s_rr[threadIdx.x] = s_new[NC + threadIdx.x];
+        grid_sum(a, 0, 3 * NC, s_a);
+        // phase B: p = z + beta p (Polak-Ribiere); A p = A z + beta A p
+        {
+            double s[NC], v[NC];
+            if (free_row) spmv_row(a, i, a.zg, s);
+#pragma unroll
+            for (int k = 0; k < NC; ++k) {
+                v[k] = 0.0;
+                if (s_active[k]) {
+                    const double beta = (s_a[k] - s_a[NC + k]) / s_rz[k];
+                    p[k] = z[k] + beta * p[k];
+                    ap[k] = (free_row ? s[k] : 0.0) + beta * ap[k];
+                }
+                v[k] = p[k] * ap[k];
+            }
+            block_partial<NC>(a, v, 3 * NC);
         }
-        grid_sum(a, 2 * NC, NC, s_pap);
+        grid_barrier(a);
+        if (t < NC && s_active[t]) {
+            s_rz[t] = s_a[t];
+            s_rr[t] = s_a[2 * NC + t];
+        }
+        grid_sum(a, 3 * NC, NC, s_pap);
     }
-    if (t0 == 0) *a.iters = it;
+    if (free_row)
+#pragma unroll
+        for (int k = 0; k < NC; ++k) a.x[NC * (size_t)i + k] = x[k];
+    if (blockIdx.x == 0 && t == 0) *a.iters = it;
 }
 
 __global__ void k_fe_copy_out(int nn, const int* __restrict__ rep, const double* __restrict__ x, double* nwp) {
@@ -336,26 +388,30 @@ int launch_elliptic(pdf_ctx* c) {
     k_fe_rhs<<<(nn + 127) / 128, 128, 0, c->s>>>(nn, c->nR, c->ngrad, c->nke, c->nmean, c->m.is_wall, c->m.wn,
                                                 c->p, c->fe_f, c->fe_g);
     PDF_CUDA(c, cudaGetLastError());
+    const int blocks = (nn + BS - 1) / BS;
+    const size_t smem = sizeof(float) * BS * BS;
     if (c->fe_blocks == 0) {
+        PDF_CUDA(c, cudaFuncSetAttribute(k_pcg, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         int per_sm = 0;
-        PDF_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg, FE_THREADS, 0));
-        if (per_sm < 1) return fail(c, PDF_ERR_CUDA, "elliptic solver cannot be made resident");
-        int want = (nn + FE_THREADS - 1) / FE_THREADS;
-        const int maxb = per_sm * c->num_sms;
-        c->fe_blocks = want < maxb ? (want > 0 ? want : 1) : maxb;
+        PDF_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg, BS, smem));
+        if (per_sm * c->num_sms < blocks)
+            return fail(c, PDF_ERR_CAPACITY, "elliptic solver: mesh too large for one resident grid");
+        if ((size_t)blocks * PART_W > (size_t)15 * 4096)
+            return fail(c, PDF_ERR_CAPACITY, "elliptic solver: partial-sum buffer too small");
+        c->fe_blocks = blocks;
     }
     CGArgs a;
     a.nn = nn;
     a.rowptr = c->m.rowptr; a.colidx = c->m.colidx; a.mval = c->m.mval;
     a.kc_off = c->m.kc_off; a.kc_elem = c->m.kc_elem; a.kc_geo = c->m.kc_geo;
-    a.eder = c->eder; a.diag = c->m.diag; a.rep = c->m.rep; a.is_wall = c->m.is_wall;
+    a.eder = c->eder; a.rep = c->m.rep; a.is_wall = c->m.is_wall;
     a.f = c->fe_f; a.g = c->fe_g; a.aval = c->m.aval;
     a.x = c->nwp;  // solution lives in the node array (canonical rows)
-    a.b = c->fe_b; a.r = c->fe_r; a.z = c->fe_z; a.pv = c->fe_p; a.ap = c->fe_ap;
+    a.zg = c->fe_z;
     a.part = c->fe_part; a.bar = c->fe_bar; a.iters = c->fe_iters; a.status = c->d_status;
     a.tol = c->p.cg_tol; a.maxit = c->p.cg_maxit;
     void* args[] = {&a};
-    PDF_CUDA(c, cudaLaunchCooperativeKernel((void*)k_pcg, dim3(c->fe_blocks), dim3(FE_THREADS), args, 0, c->s));
+    PDF_CUDA(c, cudaLaunchCooperativeKernel((void*)k_pcg, dim3(blocks), dim3(BS), args, smem, c->s));
     k_fe_copy_out<<<(nn + 127) / 128, 128, 0, c->s>>>(nn, c->m.rep, c->nwp, c->nwp);
     c->launches += 3;
     timing_end(c, PDF_K_ELLIPTIC);

@@ -284,27 +284,22 @@ __global__ void __launch_bounds__(STATS_THREADS) k_moments(const MomArgs<T> a) {
 
 
 // ---------------------------------------------------------------------------
-// warp-per-element variant for FP32 particle state: the segment's keys live in
-// registers (KPL per lane, lane-major sorted positions) and a bitonic network
-// runs with in-register compare-exchanges for partners in the same lane and
-// xor-shuffles across lanes. Key = (group, value bits, id) compared in that
-// order; payload = the particle's index in the segment (packed with the group).
+// warp-per-element variant for FP32 particle state (segments up to
+// WARP_MAX_N particles): the keys (group|index, value bits, id) live in the
+// warp's slice of shared memory as three word arrays and a bitonic network
+// runs warp-synchronously over them; group ranges of each level are
+// tabulated once per element.
 // ---------------------------------------------------------------------------
 constexpr int WARP_MAX_N = 512;
 constexpr int WARPS_PER_BLOCK = 4;
 
-struct WKey {
-    uint32_t gi;  // group << 16 | index in the segment
-    uint32_t v;   // order-preserving value bits
-    uint32_t id;
+struct WarpSmem {
+    uint32_t gi[WARP_MAX_N];  // group << 16 | index in the segment
+    uint32_t v[WARP_MAX_N];   // order-preserving value bits
+    uint32_t id[WARP_MAX_N];
+    float psi[WARP_MAX_N];
+    short gst[256], gsz[256], nst[256], nsz[256];
 };
-
-__device__ __forceinline__ bool wkey_gt(const WKey& a, const WKey& b) {
-    const uint32_t ga = a.gi >> 16, gb = b.gi >> 16;
-    if (ga != gb) return ga > gb;
-    if (a.v != b.v) return a.v > b.v;
-    return a.id > b.id;
-}
 
 __device__ __forceinline__ uint32_t ord32(float v) {
     v = v + 0.0f;
@@ -312,60 +307,32 @@ __device__ __forceinline__ uint32_t ord32(float v) {
     return (b >> 31) ? ~b : (b | 0x80000000u);
 }
 
-template <int KPL>
-__device__ __forceinline__ void warp_bitonic(WKey (&k)[KPL], int lane) {
-    constexpr int N = 32 * KPL;
-#pragma unroll
-    for (int kk = 2; kk <= N; kk <<= 1) {
-#pragma unroll
-        for (int j = kk >> 1; j > 0; j >>= 1) {
-            if (j < KPL) {
-#pragma unroll
-                for (int r = 0; r < KPL; ++r) {
-                    const int r2 = r ^ j;
-                    if (r2 > r) {
-                        const int p = lane * KPL + r;
-                        const bool asc = (p & kk) == 0;
-                        if (asc == wkey_gt(k[r], k[r2])) {
-                            const WKey t = k[r];
-                            k[r] = k[r2];
-                            k[r2] = t;
-                        }
-                    }
-                }
-            } else {
-                const int m = j / KPL;
-                const bool lower = (lane & m) == 0;
-#pragma unroll
-                for (int r = 0; r < KPL; ++r) {
-                    WKey o;
-                    o.gi = __shfl_xor_sync(0xffffffffu, k[r].gi, m);
-                    o.v = __shfl_xor_sync(0xffffffffu, k[r].v, m);
-                    o.id = __shfl_xor_sync(0xffffffffu, k[r].id, m);
-                    const int p = lane * KPL + r;
-                    const bool asc = (p & kk) == 0;
-                    const bool gt = wkey_gt(k[r], o);
-                    if ((lower == asc) ? gt : !gt) k[r] = o;
-                }
-            }
-        }
-    }
+__device__ __forceinline__ bool wgt(uint32_t ga, uint32_t va, uint32_t ia, uint32_t gb, uint32_t vb, uint32_t ib) {
+    ga >>= 16;
+    gb >>= 16;
+    if (ga != gb) return ga > gb;
+    if (va != vb) return va > vb;
+    return ia > ib;
 }
 
-// start and size of group g (mixed-radix digits over the levels done so far)
-__device__ __forceinline__ void group_range(int n, const int* G, int level, int g, int& start, int& size) {
-    int digits[3];
-    int t = g;
-    for (int d = level - 1; d >= 0; --d) {
-        digits[d] = t % G[d];
-        t /= G[d];
-    }
-    start = 0;
-    size = n;
-    for (int d = 0; d < level; ++d) {
-        const int base = size / G[d], rem = size % G[d], h = digits[d];
-        start += h * base + (h < rem ? h : rem);
-        size = base + (h < rem ? 1 : 0);
+__device__ void warp_bitonic(WarpSmem& S, int N2, int lane) {
+    const int half = N2 >> 1;
+    for (int k = 2; k <= N2; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            const int lj = __ffs(j) - 1;
+            for (int p = lane; p < half; p += 32) {
+                const int i = ((p >> lj) << (lj + 1)) + (p & (j - 1));
+                const int q = i + j;
+                const uint32_t ga = S.gi[i], va = S.v[i], ia = S.id[i];
+                const uint32_t gb = S.gi[q], vb = S.v[q], ib = S.id[q];
+                const bool asc = (i & k) == 0;
+                if (asc == wgt(ga, va, ia, gb, vb, ib)) {
+                    S.gi[i] = gb; S.v[i] = vb; S.id[i] = ib;
+                    S.gi[q] = ga; S.v[q] = va; S.id[q] = ia;
+                }
+            }
+            __syncwarp();
+        }
     }
 }
 
@@ -375,35 +342,50 @@ __device__ __forceinline__ void warp_tree(Acc& a) {
     for (int o = 16; o > 0; o >>= 1) a.merge(a.shfl_down(o));
 }
 
-template <bool KAHAN, int KPL>
-__device__ void warp_element(const MomArgs<float>& a, int e, int s0, int n, int lane, float* psi_s) {
+template <bool KAHAN>
+__global__ void __launch_bounds__(32 * WARPS_PER_BLOCK) k_moments_warp(const MomArgs<float> a, int nt) {
     using Acc = typename AccSel<float, KAHAN>::type;
     using R = typename AccSel<float, KAHAN>::R;
+    __shared__ WarpSmem sm[WARPS_PER_BLOCK];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int e = blockIdx.x * WARPS_PER_BLOCK + w;
+    if (e >= nt) return;
+    const int s0 = a.off[e], n = a.off[e + 1] - s0;
+    if (n > WARP_MAX_N) return;  // the block kernel takes it
     const int B = a.B;
-    const int G[3] = {a.G0, a.G1, a.G2};
-    WKey k[KPL];
-    // coalesced load: element r*32+lane of the segment into slot r
-#pragma unroll
-    for (int r = 0; r < KPL; ++r) {
-        const int q = r * 32 + lane;
+    WarpSmem& S = sm[w];
+    if (n == 0) {
+        if (lane == 0) {
+            a.en[e] = 0;
+            for (int q = 0; q < 5; ++q) a.emean[5 * e + q] = 0.0;
+            for (int q = 0; q < 6; ++q) a.eR[6 * e + q] = 0.0;
+            a.epsivar[e] = 0.0;
+        }
+        for (int b = lane; b < B; b += 32) {
+            a.ecm[(size_t)B * e + b] = 0.0;
+            a.ecmT[(size_t)B * e + b] = 0.f;
+        }
+        return;
+    }
+    int N2 = 32;
+    while (N2 < n) N2 <<= 1;
+    for (int q = lane; q < N2; q += 32) {
         if (q < n) {
-            k[r].gi = (uint32_t)q;
-            k[r].v = ord32(a.u[s0 + q]);
-            k[r].id = a.id[s0 + q];
+            S.gi[q] = (uint32_t)q;
+            S.v[q] = ord32(a.u[s0 + q]);
+            S.id[q] = a.id[s0 + q];
         } else {
-            k[r].gi = 0xffffffffu; k[r].v = 0xffffffffu; k[r].id = 0xffffffffu;
+            S.gi[q] = 0xffffffffu; S.v[q] = 0xffffffffu; S.id[q] = 0xffffffffu;
         }
     }
-    warp_bitonic<KPL>(k, lane);
-    // ensemble averages in the canonical (U, id) order: lane-major positions
+    __syncwarp();
+    warp_bitonic(S, N2, lane);
+    // ensemble averages in the canonical (U, id) order, lane-strided
     Acc m[5];
-#pragma unroll
-    for (int r = 0; r < KPL; ++r) {
-        if (lane * KPL + r < n) {
-            const int j = s0 + (int)(k[r].gi & 0xffffu);
-            m[0].add((R)a.u[j]); m[1].add((R)a.v[j]); m[2].add((R)a.w[j]);
-            m[3].add((R)a.psi[j]); m[4].add((R)a.om[j]);
-        }
+    for (int q = lane; q < n; q += 32) {
+        const int j = s0 + (int)(S.gi[q] & 0xffffu);
+        m[0].add((R)a.u[j]); m[1].add((R)a.v[j]); m[2].add((R)a.w[j]);
+        m[3].add((R)a.psi[j]); m[4].add((R)a.om[j]);
     }
     double mean[5];
 #pragma unroll
@@ -413,26 +395,20 @@ __device__ void warp_element(const MomArgs<float>& a, int e, int s0, int n, int 
     }
     const R mu = (R)mean[0], mv = (R)mean[1], mw = (R)mean[2], mp = (R)mean[3];
     Acc c2[7];
-#pragma unroll
-    for (int r = 0; r < KPL; ++r) {
-        if (lane * KPL + r < n) {
-            const int j = s0 + (int)(k[r].gi & 0xffffu);
-            const R du = (R)a.u[j] - mu, dv = (R)a.v[j] - mv, dw = (R)a.w[j] - mw, dp = (R)a.psi[j] - mp;
-            c2[0].add(du * du); c2[1].add(dv * dv); c2[2].add(dw * dw);
-            c2[3].add(du * dv); c2[4].add(du * dw); c2[5].add(dv * dw); c2[6].add(dp * dp);
-        }
+    for (int q = lane; q < n; q += 32) {
+        const int j = s0 + (int)(S.gi[q] & 0xffffu);
+        const R du = (R)a.u[j] - mu, dv = (R)a.v[j] - mv, dw = (R)a.w[j] - mw, dp = (R)a.psi[j] - mp;
+        c2[0].add(du * du); c2[1].add(dv * dv); c2[2].add(dw * dw);
+        c2[3].add(du * dv); c2[4].add(du * dw); c2[5].add(dv * dw); c2[6].add(dp * dp);
     }
-    double r2[7];
 #pragma unroll
-    for (int q = 0; q < 7; ++q) {
-        warp_tree(c2[q]);
-        r2[q] = c2[q].value();
-    }
+    for (int q = 0; q < 7; ++q) warp_tree(c2[q]);
     if (lane == 0) {
+        const double inv_n = 1.0 / n;
         a.en[e] = n;
         for (int q = 0; q < 5; ++q) a.emean[5 * e + q] = mean[q];
-        for (int q = 0; q < 6; ++q) a.eR[6 * e + q] = r2[q] / n;
-        a.epsivar[e] = r2[6] / n;
+        for (int q = 0; q < 6; ++q) a.eR[6 * e + q] = c2[q].value() * inv_n;
+        a.epsivar[e] = c2[6].value() * inv_n;
     }
     if (n < B) {
         for (int q = lane; q < n; q += 32) a.bin[s0 + q] = 0;
@@ -442,74 +418,56 @@ __device__ void warp_element(const MomArgs<float>& a, int e, int s0, int n, int 
         }
         return;
     }
-    // equal-population groups, level by level
-#pragma unroll 1
+    const int G[3] = {a.G0, a.G1, a.G2};
+    if (lane == 0) { S.gst[0] = 0; S.gsz[0] = (short)n; }
+    __syncwarp();
+    int ngroups = 1;
     for (int d = 0; d < 3; ++d) {
+        const int Gd = G[d];
         if (d > 0) {
             const float* comp = d == 1 ? a.v : a.w;
-#pragma unroll
-            for (int r = 0; r < KPL; ++r)
-                if (lane * KPL + r < n) k[r].v = ord32(comp[s0 + (k[r].gi & 0xffffu)]);
-            warp_bitonic<KPL>(k, lane);
+            for (int q = lane; q < n; q += 32) S.v[q] = ord32(comp[s0 + (S.gi[q] & 0xffffu)]);
+            __syncwarp();
+            warp_bitonic(S, N2, lane);
         }
-#pragma unroll
-        for (int r = 0; r < KPL; ++r) {
-            const int p = lane * KPL + r;
-            if (p < n) {
-                const int g = (int)(k[r].gi >> 16);
-                int st, sz;
-                group_range(n, G, d, g, st, sz);
-                const int h = chunk_of(p - st, sz, G[d]);
-                k[r].gi = ((uint32_t)(g * G[d] + h) << 16) | (k[r].gi & 0xffffu);
+        // sub-group table of this level (lane-parallel over the groups)
+        for (int g = lane; g < ngroups; g += 32) {
+            const int st = S.gst[g], m = S.gsz[g], base = m / Gd, rem = m % Gd;
+            int pos = st;
+            for (int h = 0; h < Gd; ++h) {
+                const int sz = base + (h < rem ? 1 : 0);
+                S.nst[g * Gd + h] = (short)pos;
+                S.nsz[g * Gd + h] = (short)sz;
+                pos += sz;
             }
         }
-    }
-    // bins per particle; psi in sorted order for the per-bin means
-#pragma unroll
-    for (int r = 0; r < KPL; ++r) {
-        const int p = lane * KPL + r;
-        if (p < n) {
-            const int j = s0 + (int)(k[r].gi & 0xffffu);
-            a.bin[j] = (unsigned char)(k[r].gi >> 16);
-            psi_s[p] = a.psi[j];
+        __syncwarp();
+        for (int q = lane; q < n; q += 32) {
+            const uint32_t gi = S.gi[q];
+            const int g = (int)(gi >> 16);
+            int h = Gd - 1;
+            while (h > 0 && q < S.nst[g * Gd + h]) --h;
+            S.gi[q] = ((uint32_t)(g * Gd + h) << 16) | (gi & 0xffffu);
         }
+        ngroups *= Gd;
+        for (int g = lane; g < ngroups; g += 32) { S.gst[g] = S.nst[g]; S.gsz[g] = S.nsz[g]; }
+        __syncwarp();
+    }
+    for (int q = lane; q < n; q += 32) {
+        const uint32_t gi = S.gi[q];
+        const int j = s0 + (int)(gi & 0xffffu);
+        a.bin[j] = (unsigned char)(gi >> 16);
+        S.psi[q] = a.psi[j];
     }
     __syncwarp();
     for (int b = lane; b < B; b += 32) {
-        int st, sz;
-        group_range(n, G, 3, b, st, sz);
+        const int st = S.gst[b], sz = S.gsz[b];
         Acc acc;
-        for (int q = st; q < st + sz; ++q) acc.add((R)psi_s[q]);
+        for (int q = st; q < st + sz; ++q) acc.add((R)S.psi[q]);
         const double cm = acc.value() / sz;
         a.ecm[(size_t)B * e + b] = cm;
         a.ecmT[(size_t)B * e + b] = (float)cm;
     }
-    __syncwarp();
-}
-
-template <bool KAHAN, int KPL>
-__global__ void __launch_bounds__(32 * WARPS_PER_BLOCK) k_moments_warp(const MomArgs<float> a, int nt) {
-    __shared__ float psi_s[WARPS_PER_BLOCK][32 * KPL];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int e = blockIdx.x * WARPS_PER_BLOCK + w;
-    if (e >= nt) return;
-    const int s0 = a.off[e], n = a.off[e + 1] - s0;
-    // size classes: 8 keys per lane for n <= 256, 16 for 256 < n <= 512
-    if (n > 32 * KPL || (KPL == 16 && n <= 256)) return;
-    if (n == 0) {
-        if (lane == 0) {
-            a.en[e] = 0;
-            for (int q = 0; q < 5; ++q) a.emean[5 * e + q] = 0.0;
-            for (int q = 0; q < 6; ++q) a.eR[6 * e + q] = 0.0;
-            a.epsivar[e] = 0.0;
-        }
-        for (int b = lane; b < a.B; b += 32) {
-            a.ecm[(size_t)a.B * e + b] = 0.0;
-            a.ecmT[(size_t)a.B * e + b] = 0.f;
-        }
-        return;
-    }
-    warp_element<KAHAN, KPL>(a, e, s0, n, lane, psi_s[w]);
 }
 
 template <typename T, bool KAHAN>
@@ -528,12 +486,11 @@ int run(pdf_ctx* c) {
     a.status = c->d_status;
     a.min_n = -1;
     if constexpr (sizeof(T) == 4) {
-        // warp-per-element kernels for the size classes (0,256] and (256,512]
+        // warp-per-element kernel for segments up to WARP_MAX_N particles
         a.min_n = WARP_MAX_N;
         const unsigned blocks = (unsigned)((c->m.nt + WARPS_PER_BLOCK - 1) / WARPS_PER_BLOCK);
-        k_moments_warp<KAHAN, 8><<<blocks, 32 * WARPS_PER_BLOCK, 0, c->s>>>(a, c->m.nt);
-        k_moments_warp<KAHAN, 16><<<blocks, 32 * WARPS_PER_BLOCK, 0, c->s>>>(a, c->m.nt);
-        c->launches += 2;
+        k_moments_warp<KAHAN><<<blocks, 32 * WARPS_PER_BLOCK, 0, c->s>>>(a, c->m.nt);
+        ++c->launches;
     }
     const size_t smem = sizeof(SortKey) * STATS_CAP;
     static bool attr_set = false;
