@@ -90,28 +90,35 @@ struct CGArgs {
 constexpr int BS = 128;        // rows per block = size of the block-Jacobi diagonal blocks
 constexpr int PART_W = 4 * NC; // partial sums per block: 3 NC in phase A, NC in phase B
 
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// grid-wide barrier of a cooperative launch: arrival by a release atomic,
+// the last block bumps the generation word, the others poll it with acquire
+// loads; the wait is bounded (ST_BARRIER, then the block proceeds)
 __device__ void grid_barrier(const CGArgs& a) {
     __syncthreads();
     if (threadIdx.x == 0) {
-        volatile unsigned* gen = a.bar + 1;
-        const unsigned g0 = *gen;
-        __threadfence();
-        const unsigned arrived = atomicAdd(a.bar, 1u) + 1u;
-        if (arrived == gridDim.x) {
-            a.bar[0] = 0u;
-            __threadfence();
-            atomicAdd(a.bar + 1, 1u);
+        const unsigned g0 = ld_acquire(a.bar + 1);
+        asm volatile("fence.acq_rel.gpu;" ::: "memory");  // the block's writes before the arrival
+        unsigned arrived;
+        asm volatile("atom.add.release.gpu.global.u32 %0, [%1], 1;" : "=r"(arrived) : "l"(a.bar) : "memory");
+        if (arrived + 1u == gridDim.x) {
+            asm volatile("st.relaxed.gpu.global.u32 [%0], 0;" ::"l"(a.bar) : "memory");
+            asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(a.bar + 1) : "memory");
         } else {
             long long spins = 0;
-            while (*gen == g0) {
-                if (++spins > (1ll << 27)) {
+            while (ld_acquire(a.bar + 1) == g0) {
+                if (++spins > (1ll << 22)) {  // ~1-2 s of polling
                     set_status(a.status, ST_BARRIER);
                     break;
                 }
-                __nanosleep(20);
             }
         }
-        __threadfence();
+        asm volatile("fence.acq_rel.gpu;" ::: "memory");  // other blocks' writes before the reads
     }
     __syncthreads();
 }
@@ -192,7 +199,7 @@ __global__ void __launch_bounds__(BS) k_pcg(const CGArgs a) {
     extern __shared__ float inv[];  // BS*BS, column j at inv[j*BS .. j*BS+BS)
     __shared__ float rv[BS][NC];
     __shared__ double s_a[PART_W];
-    __shared__ double s_rz[NC], s_rr[NC], s_bn[NC], s_pap[NC];
+    __shared__ double s_rz[NC], s_rr[NC], s_bn[NC], s_pap[NC], s_alpha[NC], s_beta[NC];
     __shared__ int s_active[NC];
     const int t = threadIdx.x;
     const int i = blockIdx.x * BS + t;
@@ -305,7 +312,10 @@ __global__ void __launch_bounds__(BS) k_pcg(const CGArgs a) {
     grid_sum(a, 3 * NC, NC, s_pap);
     int it = 0;
     for (;; ++it) {
-        if (t < NC) s_active[t] = (s_bn[t] > 0.0) && (sqrt(s_rr[t]) > a.tol * s_bn[t]);
+        if (t < NC) {
+            s_active[t] = (s_bn[t] > 0.0) && (sqrt(s_rr[t]) > a.tol * s_bn[t]);
+            s_alpha[t] = s_active[t] ? s_rz[t] / s_pap[t] : 0.0;
+        }
         __syncthreads();
         bool any = false;
 #pragma unroll
@@ -322,7 +332,7 @@ __global__ void __launch_bounds__(BS) k_pcg(const CGArgs a) {
             for (int k = 0; k < NC; ++k) {
                 rold[k] = r[k];
                 if (s_active[k]) {
-                    const double alpha = s_rz[k] / s_pap[k];
+                    const double alpha = s_alpha[k];
                     x[k] += alpha * p[k];
                     r[k] -= alpha * ap[k];
                 }
@@ -343,6 +353,8 @@ __global__ void __launch_bounds__(BS) k_pcg(const CGArgs a) {
         }
         grid_barrier(a);
         grid_sum(a, 0, 3 * NC, s_a);
+        if (t < NC) s_beta[t] = s_active[t] ? (s_a[t] - s_a[NC + t]) / s_rz[t] : 0.0;
+        __syncthreads();
         // phase B: p = z + beta p (Polak-Ribiere); A p = A z + beta A p
         {
             double s[NC], v[NC];
@@ -351,7 +363,7 @@ __global__ void __launch_bounds__(BS) k_pcg(const CGArgs a) {
             for (int k = 0; k < NC; ++k) {
                 v[k] = 0.0;
                 if (s_active[k]) {
-                    const double beta = (s_a[k] - s_a[NC + k]) / s_rz[k];
+                    const double beta = s_beta[k];
                     p[k] = z[k] + beta * p[k];
                     ap[k] = (free_row ? s[k] : 0.0) + beta * ap[k];
                 }

@@ -15,6 +15,47 @@
 
 namespace {
 
+// 12-wide packs (node pack, element geometry) and 8-wide packs, read with
+// 128-bit loads in FP32 (64-bit pairs in FP64)
+template <int W, typename T>
+__device__ __forceinline__ void load_pack(const T* __restrict__ p, T (&o)[W]) {
+    if constexpr (sizeof(T) == 4) {
+        const float4* q = reinterpret_cast<const float4*>(p);
+#pragma unroll
+        for (int k = 0; k < W / 4; ++k) {
+            const float4 v = __ldg(q + k);
+            o[4 * k] = v.x; o[4 * k + 1] = v.y; o[4 * k + 2] = v.z; o[4 * k + 3] = v.w;
+        }
+    } else {
+        const double2* q = reinterpret_cast<const double2*>(p);
+#pragma unroll
+        for (int k = 0; k < W / 2; ++k) {
+            const double2 v = __ldg(q + k);
+            o[2 * k] = v.x; o[2 * k + 1] = v.y;
+        }
+    }
+}
+
+// Gaussian pair from two uniforms in (0, 1]. FP64: Box & Muller with the
+// accurate functions. FP32: the angle 2 pi ub is taken as pi (2 ub - 1) in
+// [-pi, pi], where the hardware sine/cosine are accurate to ~4e-7 absolute,
+// and z = -r cos(pi (2 ub - 1)) = r cos(2 pi ub) (same for the sine).
+__device__ __forceinline__ void gauss_pair(double ua, double ub, double& za, double& zb) {
+    box_muller(ua, ub, za, zb);
+}
+__device__ __forceinline__ void gauss_pair(float ua, float ub, float& za, float& zb) {
+    const float m2l = -2.0f * logf(ua);
+    const float r = m2l > 0.f ? m2l * rsqrtf(m2l) : 0.f;
+    const float th = 3.14159265358979f * fmaf(2.0f, ub, -1.0f);
+    float sn, cs;
+    __sincosf(th, &sn, &cs);
+    za = -r * cs;
+    zb = -r * sn;
+}
+
+template <typename T> __device__ __forceinline__ T t_div(T a, T b) { return a / b; }
+template <> __device__ __forceinline__ float t_div<float>(float a, float b) { return __fdividef(a, b); }
+
 template <typename T>
 struct StepArgs {
     int64_t n;
@@ -81,8 +122,8 @@ __device__ void reflect(const StepArgs<T>& a, int tag, T nx, T ny, const double*
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_step(const StepArgs<T> a) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= a.n) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (int)a.n) return;
     const int e0 = a.elem[i];
     const T x = a.x[i], y = a.y[i];
     T u = a.u[i], v = a.v[i], w = a.w[i], om = a.om[i], psi = a.psi[i];
@@ -90,34 +131,40 @@ __global__ void __launch_bounds__(256) k_step(const StepArgs<T> a) {
     const int b = a.bin[i];
 
     // barycentric coordinates in the host element
-    const T* g = a.egeo + (size_t)EGEO_W * e0;
+    T g[EGEO_W];
+    load_pack<EGEO_W>(a.egeo + EGEO_W * e0, g);
     const T dx = x - g[0], dy = y - g[1];
     const T l0 = g[2] * dx + g[3] * dy + g[4];
     const T l1 = g[5] * dx + g[6] * dy + g[7];
     const T l2 = g[8] * dx + g[9] * dy + g[10];
     const int n0 = a.tri[3 * e0], n1 = a.tri[3 * e0 + 1], n2 = a.tri[3 * e0 + 2];
-    T F[11];
+    T F[NODE_PACK_W];
+    {
+        T A[NODE_PACK_W], Bv[NODE_PACK_W], Cv[NODE_PACK_W];
+        load_pack<NODE_PACK_W>(a.npack + NODE_PACK_W * n0, A);
+        load_pack<NODE_PACK_W>(a.npack + NODE_PACK_W * n1, Bv);
+        load_pack<NODE_PACK_W>(a.npack + NODE_PACK_W * n2, Cv);
 #pragma unroll
-    for (int q = 0; q < 11; ++q)
-        F[q] = l0 * a.npack[NODE_PACK_W * n0 + q] + l1 * a.npack[NODE_PACK_W * n1 + q] +
-               l2 * a.npack[NODE_PACK_W * n2 + q];
-    const T* ep = a.epack + (size_t)ELEM_PACK_W * e0;
+        for (int q = 0; q < 11; ++q) F[q] = l0 * A[q] + l1 * Bv[q] + l2 * Cv[q];
+    }
+    T ep[ELEM_PACK_W];
+    load_pack<ELEM_PACK_W>(a.epack + ELEM_PACK_W * e0, ep);
     const T Ux = ep[0], Uy = ep[1], Vx = ep[2], Vy = ep[3], lapU = ep[4], lapV = ep[5];
     const T Som = ep[6], tm = ep[7];
-    const T cm = a.ecm[(size_t)a.B * e0 + b];
+    const T cm = a.ecm[a.B * e0 + b];
 
     // eight Gaussians: counter (id, step, call, 0)
     T z[8];
 #pragma unroll
     for (uint32_t call = 0; call < 2; ++call) {
         const uint4 r = philox4x32_10(a.key, make_uint4(pid, a.step, call, 0u));
-        box_muller(unif<T>(r.x), unif<T>(r.y), z[4 * call + 0], z[4 * call + 1]);
-        box_muller(unif<T>(r.z), unif<T>(r.w), z[4 * call + 2], z[4 * call + 3]);
+        gauss_pair(unif<T>(r.x), unif<T>(r.y), z[4 * call + 0], z[4 * call + 1]);
+        gauss_pair(unif<T>(r.z), unif<T>(r.w), z[4 * call + 2], z[4 * call + 3]);
     }
     const T dt = a.dt, sdt = a.sdt;
 
     // Eq. IECM
-    const T r = a.mix_exp ? (T)1 - t_exp<T>(-dt / tm) : dt / tm;
+    const T r = a.mix_exp ? (T)1 - t_exp<T>(-t_div(dt, tm)) : t_div(dt, tm);
     if (!a.mix_exp && r > (T)1) set_status(a.status, ST_DT);
     const T psi1 = psi - r * (psi - cm);
     // Eq. frequency-model with Eq. frequency_source
@@ -141,7 +188,8 @@ __global__ void __launch_bounds__(256) k_step(const StepArgs<T> a) {
     T px = x, py = y;
     int e = e0, entry = -1, nref = 0, it = 0;
     for (; it < WALK_MAX; ++it) {
-        const T* ge = a.egeo + (size_t)EGEO_W * e;
+        T ge[EGEO_W];
+        load_pack<EGEO_W>(a.egeo + EGEO_W * e, ge);
         const T qdx = qx - ge[0], qdy = qy - ge[1];
         const T lq0 = ge[2] * qdx + ge[3] * qdy + ge[4];
         const T lq1 = ge[5] * qdx + ge[6] * qdy + ge[7];
@@ -156,7 +204,7 @@ __global__ void __launch_bounds__(256) k_step(const StepArgs<T> a) {
                 if (k != entry && lq[k] < (T)0) {
                     const T lp = ge[2 + 3 * k] * pdx + ge[3 + 3 * k] * pdy + ge[4 + 3 * k];
                     const T den = lp - lq[k];
-                    const T t = den > (T)0 ? lp / den : (T)0;
+                    const T t = den > (T)0 ? t_div(lp, den) : (T)0;
                     if (t < tb) { tb = t; kx = k; lqk = lq[k]; }
                 }
             }

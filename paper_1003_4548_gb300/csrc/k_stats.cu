@@ -470,6 +470,237 @@ __global__ void __launch_bounds__(32 * WARPS_PER_BLOCK) k_moments_warp(const Mom
     }
 }
 
+
+// ---------------------------------------------------------------------------
+// median-split variant (every level splits a group in two, as for the 2x2x2
+// bins): no sort. For each group the boundary key -- the ceil(m/2)-th
+// smallest (value, id) -- is found by a warp-wide bisection over the value
+// bits (counts of keys below a candidate by warp reductions), with a second
+// bisection over the id bits when equal values straddle the boundary.
+// Segments up to 32*KPL particles; key j of a lane is element j*32+lane.
+// ---------------------------------------------------------------------------
+struct SelSmem {
+    float psi[WARP_MAX_N];
+    unsigned char bin[WARP_MAX_N];
+};
+
+template <int KPL>
+__device__ __forceinline__ int count_below(const uint32_t (&v)[KPL], const uint32_t (&id)[KPL],
+                                           const int (&grp)[KPL], int g, uint32_t cv, uint32_t cid, int lane,
+                                           int n) {
+    int c = 0;
+#pragma unroll
+    for (int r = 0; r < KPL; ++r)
+        c += (r * 32 + lane < n && grp[r] == g && (v[r] < cv || (v[r] == cv && id[r] < cid))) ? 1 : 0;
+    return __reduce_add_sync(0xffffffffu, c);
+}
+
+
+// One median level for NG groups at once: bisection over the value bits with
+// the per-group counts packed two per 32-bit word (16-bit fields) and summed
+// by warp reductions; then per group the id bisection if equal values
+// straddle the boundary. Groups g become 2g (lower half) and 2g+1.
+template <int KPL, int NG>
+__device__ __forceinline__ void split_level(const uint32_t (&kv)[KPL], const uint32_t (&kid)[KPL], int (&grp)[KPL],
+                                            int (&gsize)[4], uint32_t vmin, uint32_t vmax, int lane, int n) {
+    const uint32_t diff = vmin ^ vmax;
+    const int hb = diff ? 31 - __clz(diff) : -1;
+    const uint32_t prefix = hb >= 0 ? (vmin & ~((2u << hb) - 1u)) : vmin;
+    uint32_t ans[NG];
+    int T[NG];
+#pragma unroll
+    for (int g = 0; g < NG; ++g) {
+        ans[g] = prefix;
+        T[g] = (gsize[g] + 1) / 2;
+    }
+    for (int bit = hb; bit >= 0; --bit) {
+        uint32_t cand[NG];
+#pragma unroll
+        for (int g = 0; g < NG; ++g) cand[g] = ans[g] | (1u << bit);
+        uint32_t lo = 0, hi = 0;
+#pragma unroll
+        for (int r = 0; r < KPL; ++r) {
+            const int q = r * 32 + lane;
+            const int gr = grp[r];
+            uint32_t c = cand[0];
+            if (NG > 1 && gr == 1) c = cand[1];
+            if (NG > 2 && gr == 2) c = cand[2];
+            if (NG > 3 && gr == 3) c = cand[3];
+            const uint32_t lt = (q < n && kv[r] < c) ? 1u : 0u;
+            const uint32_t inc = lt << (16 * (gr & 1));
+            if (NG <= 2 || gr < 2) lo += inc;
+            else hi += inc;
+        }
+        lo = __reduce_add_sync(0xffffffffu, lo);
+        if (NG > 2) hi = __reduce_add_sync(0xffffffffu, hi);
+#pragma unroll
+        for (int g = 0; g < NG; ++g) {
+            const uint32_t w = g < 2 ? lo : hi;
+            const int cnt = (int)((w >> (16 * (g & 1))) & 0xffffu);
+            if (cnt < T[g]) ans[g] = cand[g];
+        }
+    }
+#pragma unroll
+    for (int g = 0; g < NG; ++g) {
+        const int clt = count_below<KPL>(kv, kid, grp, g, ans[g], 0u, lane, n);
+        const int cle = ans[g] == 0xffffffffu ? gsize[g] : count_below<KPL>(kv, kid, grp, g, ans[g] + 1u, 0u, lane, n);
+        uint32_t idb = 0xffffffffu;
+        if (cle - clt > 1 && T[g] - clt < cle - clt) {
+            uint32_t ia = 0u;
+            for (int bit = 31; bit >= 0; --bit) {
+                const uint32_t cand = ia | (1u << bit);
+                if (count_below<KPL>(kv, kid, grp, g, ans[g], cand, lane, n) - clt < T[g] - clt) ia = cand;
+            }
+            idb = ia;
+        }
+#pragma unroll
+        for (int r = 0; r < KPL; ++r) {
+            const int q = r * 32 + lane;
+            if (q < n && grp[r] == g) {
+                const bool low = kv[r] < ans[g] || (kv[r] == ans[g] && kid[r] <= idb);
+                grp[r] = 2 * g + (low ? 0 : 1) + 1000;  // marked: split at this level
+            }
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < KPL; ++r) grp[r] = grp[r] >= 1000 ? grp[r] - 1000 : grp[r];
+    int ns[4] = {0, 0, 0, 0};
+#pragma unroll
+    for (int g = 0; g < NG && 2 * g + 1 < 4; ++g) {
+        ns[2 * g] = T[g];
+        ns[2 * g + 1] = gsize[g] - T[g];
+    }
+#pragma unroll
+    for (int g = 0; g < 4; ++g) gsize[g] = ns[g];
+}
+
+template <bool KAHAN, int KPL>
+__device__ void select_element(const MomArgs<float>& a, int e, int s0, int n, int lane, SelSmem& S) {
+    using Acc = typename AccSel<float, KAHAN>::type;
+    using R = typename AccSel<float, KAHAN>::R;
+    const int B = a.B;
+    // ensemble averages (lane-strided slot order)
+    Acc m[5];
+#pragma unroll
+    for (int r = 0; r < KPL; ++r) {
+        const int q = r * 32 + lane;
+        if (q < n) {
+            m[0].add((R)a.u[s0 + q]); m[1].add((R)a.v[s0 + q]); m[2].add((R)a.w[s0 + q]);
+            m[3].add((R)a.psi[s0 + q]); m[4].add((R)a.om[s0 + q]);
+        }
+    }
+    double mean[5];
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+        warp_tree(m[q]);
+        mean[q] = __shfl_sync(0xffffffffu, m[q].value(), 0) / n;
+    }
+    const R mu = (R)mean[0], mv = (R)mean[1], mw = (R)mean[2], mp = (R)mean[3];
+    Acc c2[7];
+#pragma unroll
+    for (int r = 0; r < KPL; ++r) {
+        const int q = r * 32 + lane;
+        if (q < n) {
+            const R du = (R)a.u[s0 + q] - mu, dv = (R)a.v[s0 + q] - mv, dw = (R)a.w[s0 + q] - mw;
+            const R dp = (R)a.psi[s0 + q] - mp;
+            c2[0].add(du * du); c2[1].add(dv * dv); c2[2].add(dw * dw);
+            c2[3].add(du * dv); c2[4].add(du * dw); c2[5].add(dv * dw); c2[6].add(dp * dp);
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < 7; ++q) warp_tree(c2[q]);
+    if (lane == 0) {
+        const double inv_n = 1.0 / n;
+        a.en[e] = n;
+        for (int q = 0; q < 5; ++q) a.emean[5 * e + q] = mean[q];
+        for (int q = 0; q < 6; ++q) a.eR[6 * e + q] = c2[q].value() * inv_n;
+        a.epsivar[e] = c2[6].value() * inv_n;
+    }
+    if (n < B) {
+        for (int q = lane; q < n; q += 32) a.bin[s0 + q] = 0;
+        for (int b = lane; b < B; b += 32) {
+            a.ecm[(size_t)B * e + b] = mean[3];
+            a.ecmT[(size_t)B * e + b] = (float)mean[3];
+        }
+        return;
+    }
+    uint32_t kv[KPL], kid[KPL];
+    int grp[KPL];
+#pragma unroll
+    for (int r = 0; r < KPL; ++r) {
+        const int q = r * 32 + lane;
+        grp[r] = 0;
+        kid[r] = q < n ? a.id[s0 + q] : 0u;
+    }
+    int gsize[4] = {n, 0, 0, 0};
+    const int G[3] = {a.G0, a.G1, a.G2};
+    int ngroups = 1;
+#pragma unroll 1
+    for (int d = 0; d < 3; ++d) {
+        if (G[d] == 1) continue;
+        const float* comp = d == 0 ? a.u : (d == 1 ? a.v : a.w);
+        uint32_t vmin = 0xffffffffu, vmax = 0u;
+#pragma unroll
+        for (int r = 0; r < KPL; ++r) {
+            const int q = r * 32 + lane;
+            kv[r] = q < n ? ord32(comp[s0 + q]) : 0u;
+            if (q < n) { vmin = min(vmin, kv[r]); vmax = max(vmax, kv[r]); }
+        }
+        vmin = __reduce_min_sync(0xffffffffu, vmin);
+        vmax = __reduce_max_sync(0xffffffffu, vmax);
+        if (ngroups == 1) split_level<KPL, 1>(kv, kid, grp, gsize, vmin, vmax, lane, n);
+        else if (ngroups == 2) split_level<KPL, 2>(kv, kid, grp, gsize, vmin, vmax, lane, n);
+        else split_level<KPL, 4>(kv, kid, grp, gsize, vmin, vmax, lane, n);
+        ngroups *= 2;
+    }
+    // bins, and <phi|V> per bin summed in slot order
+#pragma unroll
+    for (int r = 0; r < KPL; ++r) {
+        const int q = r * 32 + lane;
+        if (q < n) {
+            a.bin[s0 + q] = (unsigned char)grp[r];
+            S.bin[q] = (unsigned char)grp[r];
+            S.psi[q] = a.psi[s0 + q];
+        }
+    }
+    __syncwarp();
+    for (int b = lane; b < B; b += 32) {
+        Acc acc;
+        int cnt = 0;
+        for (int q = 0; q < n; ++q)
+            if (S.bin[q] == b) { acc.add((R)S.psi[q]); ++cnt; }
+        const double cm = acc.value() / cnt;
+        a.ecm[(size_t)B * e + b] = cm;
+        a.ecmT[(size_t)B * e + b] = (float)cm;
+    }
+    __syncwarp();
+}
+
+template <bool KAHAN>
+__global__ void __launch_bounds__(32 * WARPS_PER_BLOCK) k_moments_sel(const MomArgs<float> a, int nt) {
+    __shared__ SelSmem sm[WARPS_PER_BLOCK];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int e = blockIdx.x * WARPS_PER_BLOCK + w;
+    if (e >= nt) return;
+    const int s0 = a.off[e], n = a.off[e + 1] - s0;
+    if (n > WARP_MAX_N) return;  // the block kernel takes it
+    if (n == 0) {
+        if (lane == 0) {
+            a.en[e] = 0;
+            for (int q = 0; q < 5; ++q) a.emean[5 * e + q] = 0.0;
+            for (int q = 0; q < 6; ++q) a.eR[6 * e + q] = 0.0;
+            a.epsivar[e] = 0.0;
+        }
+        for (int b = lane; b < a.B; b += 32) {
+            a.ecm[(size_t)a.B * e + b] = 0.0;
+            a.ecmT[(size_t)a.B * e + b] = 0.f;
+        }
+        return;
+    }
+    if (n <= 256) select_element<KAHAN, 8>(a, e, s0, n, lane, sm[w]);
+    else select_element<KAHAN, 16>(a, e, s0, n, lane, sm[w]);
+}
+
 template <typename T, bool KAHAN>
 int run(pdf_ctx* c) {
     MomArgs<T> a;
@@ -486,10 +717,14 @@ int run(pdf_ctx* c) {
     a.status = c->d_status;
     a.min_n = -1;
     if constexpr (sizeof(T) == 4) {
-        // warp-per-element kernel for segments up to WARP_MAX_N particles
+        // warp-per-element kernels for segments up to WARP_MAX_N particles:
+        // median splits by bisection when every level halves (G <= 2), else a
+        // shared-memory bitonic sort
         a.min_n = WARP_MAX_N;
         const unsigned blocks = (unsigned)((c->m.nt + WARPS_PER_BLOCK - 1) / WARPS_PER_BLOCK);
-        k_moments_warp<KAHAN><<<blocks, 32 * WARPS_PER_BLOCK, 0, c->s>>>(a, c->m.nt);
+        const bool medians = c->p.nb1 <= 2 && c->p.nb2 <= 2 && c->p.nb3 <= 2;
+        if (medians) k_moments_sel<KAHAN><<<blocks, 32 * WARPS_PER_BLOCK, 0, c->s>>>(a, c->m.nt);
+        else k_moments_warp<KAHAN><<<blocks, 32 * WARPS_PER_BLOCK, 0, c->s>>>(a, c->m.nt);
         ++c->launches;
     }
     const size_t smem = sizeof(SortKey) * STATS_CAP;
