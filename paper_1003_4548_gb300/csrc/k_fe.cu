@@ -87,8 +87,7 @@ struct CGArgs {
     int maxit;
 };
 
-constexpr int BS = 128;        // rows per block = size of the block-Jacobi diagonal blocks
-constexpr int PART_W = 4 * NC; // partial sums per block: 3 NC in phase A, NC in phase B
+constexpr int PART_W = 4 * NC;  // partial sums per block: 3 NC in phase A, NC in phase B
 
 __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
     unsigned v;
@@ -103,7 +102,7 @@ __device__ void grid_barrier(const CGArgs& a) {
     __syncthreads();
     if (threadIdx.x == 0) {
         const unsigned g0 = ld_acquire(a.bar + 1);
-        asm volatile("fence.acq_rel.gpu;" ::: "memory");  // the block's writes before the arrival
+        asm volatile("fence.acq_rel.gpu;" ::: "memory");
         unsigned arrived;
         asm volatile("atom.add.release.gpu.global.u32 %0, [%1], 1;" : "=r"(arrived) : "l"(a.bar) : "memory");
         if (arrived + 1u == gridDim.x) {
@@ -118,38 +117,33 @@ __device__ void grid_barrier(const CGArgs& a) {
                 }
             }
         }
-        asm volatile("fence.acq_rel.gpu;" ::: "memory");  // other blocks' writes before the reads
+        asm volatile("fence.acq_rel.gpu;" ::: "memory");
     }
     __syncthreads();
 }
 
-// block sums of NV per-thread values into part[block][slot..slot+NV)
-template <int NV>
-__device__ void block_partial(const CGArgs& a, double (&v)[NV], int slot) {
-    __shared__ double red[BS / 32][PART_W];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-#pragma unroll
-    for (int q = 0; q < NV; ++q)
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v[q] += __shfl_down_sync(0xffffffffu, v[q], o);
-    if (lane == 0)
-#pragma unroll
-        for (int q = 0; q < NV; ++q) red[wid][q] = v[q];
+// Per-block sums over the rows of NV values per component (value v of
+// component c of row t staged at red[(v * NC + c) * BS + t]); warp q sums
+// value-component q in a fixed order and writes part[block][slot + q].
+template <int BS>
+__device__ void block_partial(const CGArgs& a, double* red, int nv, int slot) {
     __syncthreads();
-    if (threadIdx.x < NV) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int q = wid; q < nv * NC; q += (BS * NC) / 32) {
         double s = 0.0;
+        for (int t = lane; t < BS; t += 32) s += red[q * BS + t];
 #pragma unroll
-        for (int w = 0; w < BS / 32; ++w) s += red[w][threadIdx.x];
-        a.part[(size_t)blockIdx.x * PART_W + slot + threadIdx.x] = s;
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        if (lane == 0) a.part[(size_t)blockIdx.x * PART_W + slot + q] = s;
     }
     __syncthreads();
 }
 
-// after a barrier: the sums over all blocks; value q is reduced by warp q % 4
-// in a fixed lane-strided order and shuffle tree (the same in every block)
-__device__ void grid_sum(const CGArgs& a, int slot, int nv, double* out) {
+// after a barrier: sums over all blocks of nv*NC partials (warp q: value q,
+// fixed lane-strided order and shuffle tree; identical in every block)
+__device__ void grid_sum(const CGArgs& a, int slot, int nvals, double* out) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    for (int q = wid; q < nv; q += BS / 32) {
+    for (int q = wid; q < nvals; q += blockDim.x / 32) {
         double s = 0.0;
         for (int bl = lane; bl < (int)gridDim.x; bl += 32) s += a.part[(size_t)bl * PART_W + slot + q];
 #pragma unroll
@@ -159,76 +153,61 @@ __device__ void grid_sum(const CGArgs& a, int slot, int nv, double* out) {
     __syncthreads();
 }
 
-__device__ __forceinline__ void spmv_row(const CGArgs& a, int i, const double* __restrict__ v, double (&s)[NC]) {
-#pragma unroll
-    for (int k = 0; k < NC; ++k) s[k] = 0.0;
-    for (int q = a.rowptr[i]; q < a.rowptr[i + 1]; ++q) {
-        const int j = a.colidx[q];
-        const double A = a.aval[q];
-#pragma unroll
-        for (int k = 0; k < NC; ++k) s[k] += A * v[NC * (size_t)j + k];
-    }
-}
-
-// z = Ainv_b r for the block's rows (FP32 dense product in shared memory)
-__device__ __forceinline__ void block_precondition(const float* __restrict__ inv, float (*rv)[NC], int t,
-                                                   const double (&r)[NC], double (&z)[NC]) {
-#pragma unroll
-    for (int k = 0; k < NC; ++k) rv[t][k] = (float)r[k];
+// z = Ainv_b r for component c of the block's rows (FP32 dense product)
+template <int BS>
+__device__ __forceinline__ double block_precondition(const float* __restrict__ inv, float* rv, int c, int t,
+                                                     double r) {
+    rv[c * BS + t] = (float)r;
     __syncthreads();
-    float acc[NC] = {0.f, 0.f, 0.f, 0.f, 0.f};
-#pragma unroll 4
-    for (int j = 0; j < BS; ++j) {
-        const float m = inv[j * BS + t];
-#pragma unroll
-        for (int k = 0; k < NC; ++k) acc[k] += m * rv[j][k];
+    float acc0 = 0.f, acc1 = 0.f;
+    const float* rc = rv + c * BS;
+#pragma unroll 8
+    for (int j = 0; j < BS; j += 2) {
+        acc0 += inv[j * BS + t] * rc[j];
+        acc1 += inv[(j + 1) * BS + t] * rc[j + 1];
     }
-#pragma unroll
-    for (int k = 0; k < NC; ++k) z[k] = (double)acc[k];
     __syncthreads();
+    return (double)(acc0 + acc1);
 }
 
 // Flexible (Polak-Ribiere) preconditioned CG in FP64 for the NC right-hand
-// sides, block-Jacobi preconditioner with FP32 explicit inverses of the 128 x
-// 128 diagonal blocks (one block of rows per thread block, inverted in shared
-// memory by Gauss-Jordan without pivoting: the blocks are SPD). The vectors of
-// a row live in the registers of its thread; the product A p follows the
-// recurrence A p_{k+1} = A z_{k+1} + beta_k A p_k, so one SpMV (on z) and two
-// grid reductions per iteration.
-__global__ void __launch_bounds__(BS) k_pcg(const CGArgs a) {
-    extern __shared__ float inv[];  // BS*BS, column j at inv[j*BS .. j*BS+BS)
-    __shared__ float rv[BS][NC];
-    __shared__ double s_a[PART_W];
-    __shared__ double s_rz[NC], s_rr[NC], s_bn[NC], s_pap[NC], s_alpha[NC], s_beta[NC];
+// sides. One thread per (row, component); the rows of a block form the
+// diagonal block of a block-Jacobi preconditioner whose FP32 explicit inverse
+// (Gauss-Jordan without pivoting: the blocks are SPD) stays in shared memory
+// for the whole solve. A p follows A p_{k+1} = A z_{k+1} + beta_k A p_k, so
+// each iteration has one SpMV (on z) and two grid reductions.
+template <int BS>
+__global__ void __launch_bounds__(BS * NC) k_pcg(const CGArgs a) {
+    extern __shared__ float smem[];
+    float* inv = smem;                                           // BS*BS, column j at inv[j*BS ..]
+    float* rv = smem + BS * BS;                                  // NC*BS
+    double* red = reinterpret_cast<double*>(rv + NC * BS);       // 3*NC*BS
+    __shared__ double s_a[3 * NC], s_rz[NC], s_rr[NC], s_bn[NC], s_pap[NC], s_alpha[NC], s_beta[NC];
     __shared__ int s_active[NC];
-    const int t = threadIdx.x;
+    const int c = threadIdx.x / BS, t = threadIdx.x % BS;
     const int i = blockIdx.x * BS + t;
     const bool have = i < a.nn;
     const bool free_row = have && a.rep[i] == i && !a.is_wall[i];
-    // assembly of M + K_{L^2}; b = M f; Dirichlet values
-    double b[NC] = {0, 0, 0, 0, 0}, x[NC] = {0, 0, 0, 0, 0};
+    // assembly of M + K_{L^2} (component 0 threads), b = M f, Dirichlet values
+    double b = 0.0, x = 0.0;
     if (have) {
         for (int q = a.rowptr[i]; q < a.rowptr[i + 1]; ++q) {
-            double s = a.mval[q];
-            for (int c = a.kc_off[q]; c < a.kc_off[q + 1]; ++c) {
-                const double L = a.eder[9 * (size_t)a.kc_elem[c] + 8];
-                s += L * L * a.kc_geo[c];
+            if (c == 0) {
+                double s = a.mval[q];
+                for (int k = a.kc_off[q]; k < a.kc_off[q + 1]; ++k) {
+                    const double L = a.eder[9 * (size_t)a.kc_elem[k] + 8];
+                    s += L * L * a.kc_geo[k];
+                }
+                a.aval[q] = s;
             }
-            a.aval[q] = s;
-            const int j = a.colidx[q];
-#pragma unroll
-            for (int k = 0; k < NC; ++k) b[k] += a.mval[q] * a.f[NC * (size_t)j + k];
+            b += a.mval[q] * a.f[NC * (size_t)a.colidx[q] + c];
         }
-#pragma unroll
-        for (int k = 0; k < NC; ++k) {
-            x[k] = a.is_wall[i] ? a.g[NC * (size_t)i + k] : a.x[NC * (size_t)i + k];
-            a.x[NC * (size_t)i + k] = x[k];
-        }
+        x = a.is_wall[i] ? a.g[NC * (size_t)i + c] : a.x[NC * (size_t)i + c];
+        a.x[NC * (size_t)i + c] = x;
     }
-    // diagonal block of the free rows (identity elsewhere), column-major
-    for (int q = t; q < BS * BS; q += BS) inv[q] = 0.f;
+    for (int q = threadIdx.x; q < BS * BS; q += BS * NC) inv[q] = 0.f;
     __syncthreads();
-    if (have) {
+    if (c == 0) {
         if (free_row) {
             for (int q = a.rowptr[i]; q < a.rowptr[i + 1]; ++q) {
                 const int j = a.colidx[q], jl = j - blockIdx.x * BS;
@@ -237,84 +216,71 @@ __global__ void __launch_bounds__(BS) k_pcg(const CGArgs a) {
         } else {
             inv[t * BS + t] = 1.f;
         }
-    } else {
-        inv[t * BS + t] = 1.f;
     }
     __syncthreads();
     for (int k = 0; k < BS; ++k) {  // in-place Gauss-Jordan inverse
-        const float fk = inv[k * BS + t];       // a[t][k]
+        const float fk = inv[k * BS + t];  // a[t][k]
         const float p = inv[k * BS + k];
         __syncthreads();
-        {
+        if (c == 0) {
             const float v = (t == k) ? 1.f : inv[t * BS + k];  // a[k][t]
             inv[t * BS + k] = v / p;
         }
         __syncthreads();
         if (t != k) {
-            inv[k * BS + t] = 0.f;
-            for (int j = 0; j < BS; ++j) inv[j * BS + t] -= fk * inv[j * BS + k];
+            for (int j = c; j < BS; j += NC) {
+                if (j == k) inv[k * BS + t] = -fk * inv[k * BS + k];
+                else inv[j * BS + t] -= fk * inv[j * BS + k];
+            }
         }
         __syncthreads();
     }
     grid_barrier(a);  // all x (warm start + Dirichlet) and matrix rows are in place
     // r = b - A x; z = Ainv r; p = z
-    double r[NC], z[NC], p[NC], ap[NC];
+    double r, z, p, ap;
     {
-        double s[NC], b0[NC];
-#pragma unroll
-        for (int k = 0; k < NC; ++k) { s[k] = 0.0; b0[k] = b[k]; }
+        double s = 0.0, b0 = b;
         if (free_row) {
             for (int q = a.rowptr[i]; q < a.rowptr[i + 1]; ++q) {
                 const int j = a.colidx[q];
-                const double A = a.aval[q];
-                const bool dj = a.is_wall[j];
-#pragma unroll
-                for (int k = 0; k < NC; ++k) {
-                    const double xv = a.x[NC * (size_t)j + k];
-                    s[k] += A * xv;
-                    if (dj) b0[k] -= A * xv;
-                }
+                const double xv = a.aval[q] * a.x[NC * (size_t)j + c];
+                s += xv;
+                if (a.is_wall[j]) b0 -= xv;
             }
         }
-#pragma unroll
-        for (int k = 0; k < NC; ++k) r[k] = free_row ? b[k] - s[k] : 0.0;
-        block_precondition(inv, rv, t, r, z);
-        double v[3 * NC];
-#pragma unroll
-        for (int k = 0; k < NC; ++k) {
-            if (!free_row) z[k] = 0.0;
-            p[k] = z[k];
-            v[k] = r[k] * z[k];
-            v[NC + k] = r[k] * r[k];
-            v[2 * NC + k] = free_row ? b0[k] * b0[k] : 0.0;
-            if (have) a.zg[NC * (size_t)i + k] = z[k];
-        }
-        block_partial<3 * NC>(a, v, 0);
+        r = free_row ? b - s : 0.0;
+        z = block_precondition<BS>(inv, rv, c, t, r);
+        if (!free_row) z = 0.0;
+        p = z;
+        if (have) a.zg[NC * (size_t)i + c] = z;
+        red[(0 * NC + c) * BS + t] = r * z;
+        red[(1 * NC + c) * BS + t] = r * r;
+        red[(2 * NC + c) * BS + t] = free_row ? b0 * b0 : 0.0;
+        block_partial<BS>(a, red, 3, 0);
     }
     grid_barrier(a);
     grid_sum(a, 0, 3 * NC, s_a);
-    if (t < NC) {
-        s_rz[t] = s_a[t];
-        s_rr[t] = s_a[NC + t];
-        s_bn[t] = sqrt(s_a[2 * NC + t]);
+    if (threadIdx.x < NC) {
+        s_rz[threadIdx.x] = s_a[threadIdx.x];
+        s_rr[threadIdx.x] = s_a[NC + threadIdx.x];
+        s_bn[threadIdx.x] = sqrt(s_a[2 * NC + threadIdx.x]);
     }
     {  // A p_0
-        double s[NC], v[NC];
-        if (free_row) spmv_row(a, i, a.zg, s);
-#pragma unroll
-        for (int k = 0; k < NC; ++k) {
-            ap[k] = free_row ? s[k] : 0.0;
-            v[k] = p[k] * ap[k];
-        }
-        block_partial<NC>(a, v, 3 * NC);
+        double s = 0.0;
+        if (free_row)
+            for (int q = a.rowptr[i]; q < a.rowptr[i + 1]; ++q) s += a.aval[q] * a.zg[NC * (size_t)a.colidx[q] + c];
+        ap = free_row ? s : 0.0;
+        red[c * BS + t] = p * ap;
+        block_partial<BS>(a, red, 1, 3 * NC);
     }
     grid_barrier(a);
     grid_sum(a, 3 * NC, NC, s_pap);
     int it = 0;
     for (;; ++it) {
-        if (t < NC) {
-            s_active[t] = (s_bn[t] > 0.0) && (sqrt(s_rr[t]) > a.tol * s_bn[t]);
-            s_alpha[t] = s_active[t] ? s_rz[t] / s_pap[t] : 0.0;
+        if (threadIdx.x < NC) {
+            const int k = threadIdx.x;
+            s_active[k] = (s_bn[k] > 0.0) && (sqrt(s_rr[k]) > a.tol * s_bn[k]);
+            s_alpha[k] = s_active[k] ? s_rz[k] / s_pap[k] : 0.0;
         }
         __syncthreads();
         bool any = false;
@@ -322,66 +288,60 @@ __global__ void __launch_bounds__(BS) k_pcg(const CGArgs a) {
         for (int k = 0; k < NC; ++k) any |= s_active[k] != 0;
         if (!any) break;
         if (it >= a.maxit) {
-            if (blockIdx.x == 0 && t == 0) set_status(a.status, ST_CG);
+            if (blockIdx.x == 0 && threadIdx.x == 0) set_status(a.status, ST_CG);
             break;
         }
+        const bool act = s_active[c] != 0;
         // phase A: x += alpha p, r -= alpha Ap, z = Ainv r
         {
-            double rold[NC];
-#pragma unroll
-            for (int k = 0; k < NC; ++k) {
-                rold[k] = r[k];
-                if (s_active[k]) {
-                    const double alpha = s_alpha[k];
-                    x[k] += alpha * p[k];
-                    r[k] -= alpha * ap[k];
-                }
+            const double rold = r;
+            if (act) {
+                x += s_alpha[c] * p;
+                r -= s_alpha[c] * ap;
             }
-            double zn[NC];
-            block_precondition(inv, rv, t, r, zn);
-            double v[3 * NC];
-#pragma unroll
-            for (int k = 0; k < NC; ++k) {
-                if (!free_row) zn[k] = 0.0;
-                if (s_active[k]) z[k] = zn[k];
-                v[k] = r[k] * z[k];
-                v[NC + k] = rold[k] * z[k];
-                v[2 * NC + k] = r[k] * r[k];
-                if (have) a.zg[NC * (size_t)i + k] = z[k];
-            }
-            block_partial<3 * NC>(a, v, 0);
+            double zn = block_precondition<BS>(inv, rv, c, t, r);
+            if (!free_row) zn = 0.0;
+            if (act) z = zn;
+            if (have) a.zg[NC * (size_t)i + c] = z;
+            red[(0 * NC + c) * BS + t] = r * z;
+            red[(1 * NC + c) * BS + t] = rold * z;
+            red[(2 * NC + c) * BS + t] = r * r;
+            block_partial<BS>(a, red, 3, 0);
         }
         grid_barrier(a);
         grid_sum(a, 0, 3 * NC, s_a);
-        if (t < NC) s_beta[t] = s_active[t] ? (s_a[t] - s_a[NC + t]) / s_rz[t] : 0.0;
+        if (threadIdx.x < NC) {
+            const int k = threadIdx.x;
+            s_beta[k] = s_active[k] ? (s_a[k] - s_a[NC + k]) / s_rz[k] : 0.0;
+        }
         __syncthreads();
         // phase B: p = z + beta p (Polak-Ribiere); A p = A z + beta A p
         {
-            double s[NC], v[NC];
-            if (free_row) spmv_row(a, i, a.zg, s);
-#pragma unroll
-            for (int k = 0; k < NC; ++k) {
-                v[k] = 0.0;
-                if (s_active[k]) {
-                    const double beta = s_beta[k];
-                    p[k] = z[k] + beta * p[k];
-                    ap[k] = (free_row ? s[k] : 0.0) + beta * ap[k];
-                }
-                v[k] = p[k] * ap[k];
+            double s = 0.0;
+            if (free_row)
+                for (int q = a.rowptr[i]; q < a.rowptr[i + 1]; ++q)
+                    s += a.aval[q] * a.zg[NC * (size_t)a.colidx[q] + c];
+            if (act) {
+                p = z + s_beta[c] * p;
+                ap = (free_row ? s : 0.0) + s_beta[c] * ap;
             }
-            block_partial<NC>(a, v, 3 * NC);
+            red[c * BS + t] = p * ap;
+            block_partial<BS>(a, red, 1, 3 * NC);
         }
         grid_barrier(a);
-        if (t < NC && s_active[t]) {
-            s_rz[t] = s_a[t];
-            s_rr[t] = s_a[2 * NC + t];
+        if (threadIdx.x < NC && s_active[threadIdx.x]) {
+            s_rz[threadIdx.x] = s_a[threadIdx.x];
+            s_rr[threadIdx.x] = s_a[2 * NC + threadIdx.x];
         }
         grid_sum(a, 3 * NC, NC, s_pap);
     }
-    if (free_row)
-#pragma unroll
-        for (int k = 0; k < NC; ++k) a.x[NC * (size_t)i + k] = x[k];
-    if (blockIdx.x == 0 && t == 0) *a.iters = it;
+    if (free_row) a.x[NC * (size_t)i + c] = x;
+    if (blockIdx.x == 0 && threadIdx.x == 0) *a.iters = it;
+}
+
+template <int BS>
+constexpr size_t pcg_smem() {
+    return sizeof(float) * (BS * BS + NC * BS) + sizeof(double) * 3 * NC * BS;
 }
 
 __global__ void k_fe_copy_out(int nn, const int* __restrict__ rep, const double* __restrict__ x, double* nwp) {
@@ -394,20 +354,41 @@ __global__ void k_fe_copy_out(int nn, const int* __restrict__ rep, const double*
 
 }  // namespace
 
+namespace {
+
+template <int BS>
+int try_blocks(pdf_ctx* c, int nn, int& per_sm) {
+    const size_t smem = pcg_smem<BS>();
+    if (cudaFuncSetAttribute(k_pcg<BS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return -1;
+    per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg<BS>, BS * NC, smem) != cudaSuccess) return -1;
+    return (nn + BS - 1) / BS;
+}
+
+template <int BS>
+cudaError_t launch_pcg(const CGArgs& a, int blocks, cudaStream_t s) {
+    CGArgs aa = a;
+    void* args[] = {&aa};
+    return cudaLaunchCooperativeKernel((void*)k_pcg<BS>, dim3(blocks), dim3(BS * NC), args, pcg_smem<BS>(), s);
+}
+
+}  // namespace
+
 int launch_elliptic(pdf_ctx* c) {
     const int nn = c->m.nn;
     timing_begin(c, PDF_K_ELLIPTIC);
     k_fe_rhs<<<(nn + 127) / 128, 128, 0, c->s>>>(nn, c->nR, c->ngrad, c->nke, c->nmean, c->m.is_wall, c->m.wn,
                                                 c->p, c->fe_f, c->fe_g);
     PDF_CUDA(c, cudaGetLastError());
-    const int blocks = (nn + BS - 1) / BS;
-    const size_t smem = sizeof(float) * BS * BS;
     if (c->fe_blocks == 0) {
-        PDF_CUDA(c, cudaFuncSetAttribute(k_pcg, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        int per_sm = 0;
-        PDF_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg, BS, smem));
-        if (per_sm * c->num_sms < blocks)
-            return fail(c, PDF_ERR_CAPACITY, "elliptic solver: mesh too large for one resident grid");
+        // the smallest diagonal-block size whose grid is co-resident
+        int per_sm = 0, blocks = 0;
+        blocks = try_blocks<128>(c, nn, per_sm);
+        if (blocks > 0 && blocks <= per_sm * c->num_sms) c->fe_bs = 128;
+        else if ((blocks = try_blocks<160>(c, nn, per_sm)) > 0 && blocks <= per_sm * c->num_sms) c->fe_bs = 160;
+        else if ((blocks = try_blocks<192>(c, nn, per_sm)) > 0 && blocks <= per_sm * c->num_sms) c->fe_bs = 192;
+        else return fail(c, PDF_ERR_CAPACITY, "elliptic solver: mesh too large for one resident grid");
         if ((size_t)blocks * PART_W > (size_t)15 * 4096)
             return fail(c, PDF_ERR_CAPACITY, "elliptic solver: partial-sum buffer too small");
         c->fe_blocks = blocks;
@@ -422,8 +403,11 @@ int launch_elliptic(pdf_ctx* c) {
     a.zg = c->fe_z;
     a.part = c->fe_part; a.bar = c->fe_bar; a.iters = c->fe_iters; a.status = c->d_status;
     a.tol = c->p.cg_tol; a.maxit = c->p.cg_maxit;
-    void* args[] = {&a};
-    PDF_CUDA(c, cudaLaunchCooperativeKernel((void*)k_pcg, dim3(blocks), dim3(BS), args, smem, c->s));
+    cudaError_t err;
+    if (c->fe_bs == 128) err = launch_pcg<128>(a, c->fe_blocks, c->s);
+    else if (c->fe_bs == 160) err = launch_pcg<160>(a, c->fe_blocks, c->s);
+    else err = launch_pcg<192>(a, c->fe_blocks, c->s);
+    PDF_CUDA(c, err);
     k_fe_copy_out<<<(nn + 127) / 128, 128, 0, c->s>>>(nn, c->m.rep, c->nwp, c->nwp);
     c->launches += 3;
     timing_end(c, PDF_K_ELLIPTIC);

@@ -13,6 +13,7 @@
 //    split into nb2, then by (W, id) into nb3; <phi|V> of a bin is its mean psi.
 // Reductions are FP64 (or compensated FP32 with PDF_FP32_KAHAN).
 #include "pdf_internal.cuh"
+#include "exact_sum.cuh"
 
 namespace {
 
@@ -482,7 +483,15 @@ __global__ void __launch_bounds__(32 * WARPS_PER_BLOCK) k_moments_warp(const Mom
 struct SelSmem {
     float psi[WARP_MAX_N];
     unsigned char bin[WARP_MAX_N];
+    unsigned long long binsum[8];  // sum of psi per bin, unit 2^-54 (psi in [0, 1])
+    int bincnt[8];
 };
+
+__device__ __forceinline__ void x128_add_parts(Exact128& a, unsigned m, int e, bool neg) {
+    unsigned long long lo, hi;
+    x128_place((unsigned long long)m, e - 70, lo, hi);
+    x128_add(a, lo, hi, neg);
+}
 
 template <int KPL>
 __device__ __forceinline__ int count_below(const uint32_t (&v)[KPL], const uint32_t (&id)[KPL],
@@ -576,45 +585,107 @@ __device__ __forceinline__ void split_level(const uint32_t (&kv)[KPL], const uin
 
 template <bool KAHAN, int KPL>
 __device__ void select_element(const MomArgs<float>& a, int e, int s0, int n, int lane, SelSmem& S) {
-    using Acc = typename AccSel<float, KAHAN>::type;
-    using R = typename AccSel<float, KAHAN>::R;
     const int B = a.B;
-    // ensemble averages (lane-strided slot order)
-    Acc m[5];
-#pragma unroll
-    for (int r = 0; r < KPL; ++r) {
-        const int q = r * 32 + lane;
-        if (q < n) {
-            m[0].add((R)a.u[s0 + q]); m[1].add((R)a.v[s0 + q]); m[2].add((R)a.w[s0 + q]);
-            m[3].add((R)a.psi[s0 + q]); m[4].add((R)a.om[s0 + q]);
-        }
-    }
     double mean[5];
+    if constexpr (KAHAN) {
+        // compensated FP32 sums (the precision-study variant)
+        AccK m[5];
 #pragma unroll
-    for (int q = 0; q < 5; ++q) {
-        warp_tree(m[q]);
-        mean[q] = __shfl_sync(0xffffffffu, m[q].value(), 0) / n;
-    }
-    const R mu = (R)mean[0], mv = (R)mean[1], mw = (R)mean[2], mp = (R)mean[3];
-    Acc c2[7];
-#pragma unroll
-    for (int r = 0; r < KPL; ++r) {
-        const int q = r * 32 + lane;
-        if (q < n) {
-            const R du = (R)a.u[s0 + q] - mu, dv = (R)a.v[s0 + q] - mv, dw = (R)a.w[s0 + q] - mw;
-            const R dp = (R)a.psi[s0 + q] - mp;
-            c2[0].add(du * du); c2[1].add(dv * dv); c2[2].add(dw * dw);
-            c2[3].add(du * dv); c2[4].add(du * dw); c2[5].add(dv * dw); c2[6].add(dp * dp);
+        for (int r = 0; r < KPL; ++r) {
+            const int q = r * 32 + lane;
+            if (q < n) {
+                m[0].add(a.u[s0 + q]); m[1].add(a.v[s0 + q]); m[2].add(a.w[s0 + q]);
+                m[3].add(a.psi[s0 + q]); m[4].add(a.om[s0 + q]);
+            }
         }
-    }
 #pragma unroll
-    for (int q = 0; q < 7; ++q) warp_tree(c2[q]);
-    if (lane == 0) {
-        const double inv_n = 1.0 / n;
-        a.en[e] = n;
-        for (int q = 0; q < 5; ++q) a.emean[5 * e + q] = mean[q];
-        for (int q = 0; q < 6; ++q) a.eR[6 * e + q] = c2[q].value() * inv_n;
-        a.epsivar[e] = c2[6].value() * inv_n;
+        for (int q = 0; q < 5; ++q) {
+            warp_tree(m[q]);
+            mean[q] = __shfl_sync(0xffffffffu, m[q].value(), 0) / n;
+        }
+        const float mu = (float)mean[0], mv = (float)mean[1], mw = (float)mean[2], mp = (float)mean[3];
+        AccK c2[7];
+#pragma unroll
+        for (int r = 0; r < KPL; ++r) {
+            const int q = r * 32 + lane;
+            if (q < n) {
+                const float du = a.u[s0 + q] - mu, dv = a.v[s0 + q] - mv, dw = a.w[s0 + q] - mw;
+                const float dp = a.psi[s0 + q] - mp;
+                c2[0].add(du * du); c2[1].add(dv * dv); c2[2].add(dw * dw);
+                c2[3].add(du * dv); c2[4].add(du * dw); c2[5].add(dv * dw); c2[6].add(dp * dp);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < 7; ++q) warp_tree(c2[q]);
+        if (lane == 0) {
+            const double inv_n = 1.0 / n;
+            a.en[e] = n;
+            for (int q = 0; q < 5; ++q) a.emean[5 * e + q] = mean[q];
+            for (int q = 0; q < 6; ++q) a.eR[6 * e + q] = c2[q].value() * inv_n;
+            a.epsivar[e] = c2[6].value() * inv_n;
+        }
+    } else {
+        // exact sums of the values and of their products (integer pipes)
+        Exact128 s1[5], s2[7];
+        bool big = false;
+#pragma unroll
+        for (int r = 0; r < KPL; ++r) {
+            const int q = r * 32 + lane;
+            if (q < n) {
+                unsigned mu_, mv_, mw_, mp_, mo_;
+                int eu, ev, ew, ep, eo;
+                bool nu, nv, nw, np, no;
+                f32_parts(a.u[s0 + q], mu_, eu, nu);
+                f32_parts(a.v[s0 + q], mv_, ev, nv);
+                f32_parts(a.w[s0 + q], mw_, ew, nw);
+                f32_parts(a.psi[s0 + q], mp_, ep, np);
+                f32_parts(a.om[s0 + q], mo_, eo, no);
+                big |= max(max(max(eu, ev), max(ew, ep)), eo) > 145;  // |x| >= 2^19: outside the format
+                x128_add_parts(s1[0], mu_, eu, nu);
+                x128_add_parts(s1[1], mv_, ev, nv);
+                x128_add_parts(s1[2], mw_, ew, nw);
+                x128_add_parts(s1[3], mp_, ep, np);
+                x128_add_parts(s1[4], mo_, eo, no);
+                x128_add_prod(s2[0], mu_, eu, nu, mu_, eu, nu);
+                x128_add_prod(s2[1], mv_, ev, nv, mv_, ev, nv);
+                x128_add_prod(s2[2], mw_, ew, nw, mw_, ew, nw);
+                x128_add_prod(s2[3], mu_, eu, nu, mv_, ev, nv);
+                x128_add_prod(s2[4], mu_, eu, nu, mw_, ew, nw);
+                x128_add_prod(s2[5], mv_, ev, nv, mw_, ew, nw);
+                x128_add_prod(s2[6], mp_, ep, np, mp_, ep, np);
+            }
+        }
+        if (__any_sync(0xffffffffu, big) && lane == 0) set_status(a.status, ST_CAPACITY);
+#pragma unroll
+        for (int k = 0; k < 5; ++k) x128_warp_sum(s1[k]);
+#pragma unroll
+        for (int k = 0; k < 7; ++k) x128_warp_sum(s2[k]);
+        // lane k finishes moment k from the broadcast totals
+        Exact128 t1[5], t2[7];
+#pragma unroll
+        for (int k = 0; k < 5; ++k) {
+            t1[k].lo = __shfl_sync(0xffffffffu, s1[k].lo, 0);
+            t1[k].hi = __shfl_sync(0xffffffffu, s1[k].hi, 0);
+        }
+#pragma unroll
+        for (int k = 0; k < 7; ++k) {
+            t2[k].lo = __shfl_sync(0xffffffffu, s2[k].lo, 0);
+            t2[k].hi = __shfl_sync(0xffffffffu, s2[k].hi, 0);
+        }
+        const int ia[7] = {0, 1, 2, 0, 0, 1, 3}, ib[7] = {0, 1, 2, 1, 2, 2, 3};
+        double val = 0.0;
+        if (lane < 5) {
+            val = x128_to_double(t1[lane]) / n;
+        } else if (lane < 12) {
+            const int k = lane - 5;
+            val = x128_central(t2[k], t1[ia[k]], t1[ib[k]], (unsigned)n);
+        }
+#pragma unroll
+        for (int k = 0; k < 5; ++k) mean[k] = __shfl_sync(0xffffffffu, val, k);
+        if (lane < 5) a.emean[5 * e + lane] = val;
+        else if (lane < 11) a.eR[6 * e + lane - 5] = val;
+        else if (lane == 11) a.epsivar[e] = val;
+        if (lane == 0) a.en[e] = n;
     }
     if (n < B) {
         for (int q = lane; q < n; q += 32) a.bin[s0 + q] = 0;
@@ -653,23 +724,29 @@ __device__ void select_element(const MomArgs<float>& a, int e, int s0, int n, in
         else split_level<KPL, 4>(kv, kid, grp, gsize, vmin, vmax, lane, n);
         ngroups *= 2;
     }
-    // bins, and <phi|V> per bin summed in slot order
+    // bins, and <phi|V> per bin: exact fixed-point sums of psi (unit 2^-54)
+    for (int b = lane; b < 8; b += 32) { S.binsum[b] = 0ull; S.bincnt[b] = 0; }
+    __syncwarp();
 #pragma unroll
     for (int r = 0; r < KPL; ++r) {
         const int q = r * 32 + lane;
         if (q < n) {
-            a.bin[s0 + q] = (unsigned char)grp[r];
-            S.bin[q] = (unsigned char)grp[r];
-            S.psi[q] = a.psi[s0 + q];
+            const int bn = grp[r];
+            a.bin[s0 + q] = (unsigned char)bn;
+            unsigned m;
+            int ex;
+            bool ng;
+            f32_parts(fminf(fmaxf(a.psi[s0 + q], 0.f), 1.f), m, ex, ng);
+            const int sh = ex - 96;  // m 2^(ex-150) = m 2^(ex-96) 2^-54
+            const unsigned long long v = sh >= 0 ? ((unsigned long long)m << sh)
+                                                 : (-sh < 64 ? ((unsigned long long)m >> (-sh)) : 0ull);
+            atomicAdd(&S.binsum[bn], v);
+            atomicAdd(&S.bincnt[bn], 1);
         }
     }
     __syncwarp();
     for (int b = lane; b < B; b += 32) {
-        Acc acc;
-        int cnt = 0;
-        for (int q = 0; q < n; ++q)
-            if (S.bin[q] == b) { acc.add((R)S.psi[q]); ++cnt; }
-        const double cm = acc.value() / cnt;
+        const double cm = ldexp(__ull2double_rn(S.binsum[b]), -54) / S.bincnt[b];
         a.ecm[(size_t)B * e + b] = cm;
         a.ecmT[(size_t)B * e + b] = (float)cm;
     }

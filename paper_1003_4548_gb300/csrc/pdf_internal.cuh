@@ -109,6 +109,7 @@ struct pdf_ctx {
     unsigned int* fe_bar = nullptr;  // grid barrier words
     int* fe_iters = nullptr;
     int fe_blocks = 0;
+    int fe_bs = 0;  // rows per block of the elliptic solver (block-Jacobi block size)
     // status
     int* d_status = nullptr;
     int* h_status = nullptr;
