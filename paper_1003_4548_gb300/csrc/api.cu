@@ -355,8 +355,8 @@ int alloc_stats(pdf_ctx* c) {
         TRY(dalloc(c, &c->fe_ap, v));
         PDF_CUDA(c, cudaMemset(c->fe_g, 0, sizeof(double) * v));
         TRY(dalloc(c, &c->fe_part, (size_t)15 * 4096));
-        TRY(dalloc(c, &c->fe_bar, 2));
-        PDF_CUDA(c, cudaMemset(c->fe_bar, 0, 2 * sizeof(unsigned)));
+        TRY(dalloc(c, &c->fe_bar, 32 * 64));  // barrier lines: top/generation + 63 groups of 16 blocks
+        PDF_CUDA(c, cudaMemset(c->fe_bar, 0, 32 * 64 * sizeof(unsigned)));
         TRY(dalloc(c, &c->fe_iters, 1));
         PDF_CUDA(c, cudaMemset(c->fe_iters, 0, sizeof(int)));
     }

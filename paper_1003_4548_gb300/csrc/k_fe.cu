@@ -95,22 +95,37 @@ __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
     return v;
 }
 
-// grid-wide barrier of a cooperative launch: arrival by a release atomic,
-// the last block bumps the generation word, the others poll it with acquire
-// loads; the wait is bounded (ST_BARRIER, then the block proceeds)
+// grid-wide barrier of a cooperative launch, two-level arrival: a block
+// arrives at the counter of its group of 16 blocks (own 128-byte line); the
+// last of a group arrives at the top counter; the last there bumps the
+// generation word, which the others poll with acquire loads. Waits are
+// bounded (ST_BARRIER, then the block proceeds). Layout of bar (32-word
+// lines): line 0 = {top count, generation}, line 1+g = count of group g.
 __device__ void grid_barrier(const CGArgs& a) {
     __syncthreads();
     if (threadIdx.x == 0) {
-        const unsigned g0 = ld_acquire(a.bar + 1);
+        unsigned* gen = a.bar + 1;
+        unsigned* top = a.bar;
+        const int grp = blockIdx.x >> 4;
+        const unsigned ngroups = (gridDim.x + 15) >> 4;
+        const unsigned gsize = min(16u, gridDim.x - 16u * grp);
+        unsigned* sub = a.bar + 32 * (1 + grp);
+        const unsigned g0 = ld_acquire(gen);
         asm volatile("fence.acq_rel.gpu;" ::: "memory");
         unsigned arrived;
-        asm volatile("atom.add.release.gpu.global.u32 %0, [%1], 1;" : "=r"(arrived) : "l"(a.bar) : "memory");
-        if (arrived + 1u == gridDim.x) {
-            asm volatile("st.relaxed.gpu.global.u32 [%0], 0;" ::"l"(a.bar) : "memory");
-            asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(a.bar + 1) : "memory");
+        asm volatile("atom.add.acq_rel.gpu.global.u32 %0, [%1], 1;" : "=r"(arrived) : "l"(sub) : "memory");
+        bool last = false;
+        if (arrived + 1u == gsize) {
+            asm volatile("st.relaxed.gpu.global.u32 [%0], 0;" ::"l"(sub) : "memory");
+            asm volatile("atom.add.acq_rel.gpu.global.u32 %0, [%1], 1;" : "=r"(arrived) : "l"(top) : "memory");
+            last = arrived + 1u == ngroups;
+        }
+        if (last) {
+            asm volatile("st.relaxed.gpu.global.u32 [%0], 0;" ::"l"(top) : "memory");
+            asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(gen) : "memory");
         } else {
             long long spins = 0;
-            while (ld_acquire(a.bar + 1) == g0) {
+            while (ld_acquire(gen) == g0) {
                 if (++spins > (1ll << 22)) {  // ~1-2 s of polling
                     set_status(a.status, ST_BARRIER);
                     break;
@@ -153,21 +168,47 @@ __device__ void grid_sum(const CGArgs& a, int slot, int nvals, double* out) {
     __syncthreads();
 }
 
-// z = Ainv_b r for component c of the block's rows (FP32 dense product)
+__device__ __forceinline__ uint32_t to_tf32(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+
+// z = Ainv_b r for the NC components of the block's rows, on the tensor
+// cores: Z[BS x 8] = Ainv[BS x BS] R[BS x 8] (components padded to 8) with
+// mma.sync m16n8k8 TF32 inputs and FP32 accumulation; warp w < BS/16 owns
+// rows 16w..16w+15. Ainv is column-major in shared memory, R and Z are
+// component-major (rv[c*BS + row]).
 template <int BS>
-__device__ __forceinline__ double block_precondition(const float* __restrict__ inv, float* rv, int c, int t,
-                                                     double r) {
+__device__ __forceinline__ double block_precondition(const float* __restrict__ inv, float* rv, float* zv, int c,
+                                                     int t, double r) {
     rv[c * BS + t] = (float)r;
     __syncthreads();
-    float acc0 = 0.f, acc1 = 0.f;
-    const float* rc = rv + c * BS;
-#pragma unroll 8
-    for (int j = 0; j < BS; j += 2) {
-        acc0 += inv[j * BS + t] * rc[j];
-        acc1 += inv[(j + 1) * BS + t] * rc[j + 1];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (wid < BS / 16) {
+        const int g = lane >> 2, tq = lane & 3, m0 = 16 * wid;
+        float d0 = 0.f, d1 = 0.f, d2 = 0.f, d3 = 0.f;
+#pragma unroll 4
+        for (int k0 = 0; k0 < BS; k0 += 8) {
+            const uint32_t a0 = to_tf32(inv[(k0 + tq) * (BS + 4) + m0 + g]);
+            const uint32_t a1 = to_tf32(inv[(k0 + tq) * (BS + 4) + m0 + g + 8]);
+            const uint32_t a2 = to_tf32(inv[(k0 + tq + 4) * (BS + 4) + m0 + g]);
+            const uint32_t a3 = to_tf32(inv[(k0 + tq + 4) * (BS + 4) + m0 + g + 8]);
+            const uint32_t b0 = g < NC ? to_tf32(rv[g * BS + k0 + tq]) : 0u;
+            const uint32_t b1 = g < NC ? to_tf32(rv[g * BS + k0 + tq + 4]) : 0u;
+            asm volatile(
+                "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+                "{%0,%1,%2,%3};"
+                : "+f"(d0), "+f"(d1), "+f"(d2), "+f"(d3)
+                : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+        }
+        // D(row, col): d0 (g, 2tq), d1 (g, 2tq+1), d2 (g+8, 2tq), d3 (g+8, 2tq+1)
+        const int c0 = 2 * tq, c1 = 2 * tq + 1;
+        if (c0 < NC) { zv[c0 * BS + m0 + g] = d0; zv[c0 * BS + m0 + g + 8] = d2; }
+        if (c1 < NC) { zv[c1 * BS + m0 + g] = d1; zv[c1 * BS + m0 + g + 8] = d3; }
     }
     __syncthreads();
-    return (double)(acc0 + acc1);
+    return (double)zv[c * BS + t];
 }
 
 // Flexible (Polak-Ribiere) preconditioned CG in FP64 for the NC right-hand
@@ -179,9 +220,10 @@ __device__ __forceinline__ double block_precondition(const float* __restrict__ i
 template <int BS>
 __global__ void __launch_bounds__(BS * NC) k_pcg(const CGArgs a) {
     extern __shared__ float smem[];
-    float* inv = smem;                                           // BS*BS, column j at inv[j*BS ..]
-    float* rv = smem + BS * BS;                                  // NC*BS
-    double* red = reinterpret_cast<double*>(rv + NC * BS);       // 3*NC*BS
+    float* inv = smem;                                           // column j at inv[j*(BS+4) ..]
+    float* rv = smem + BS * (BS + 4);                            // NC*BS
+    float* zv = rv + NC * BS;                                    // NC*BS
+    double* red = reinterpret_cast<double*>(zv + NC * BS);       // 3*NC*BS
     __shared__ double s_a[3 * NC], s_rz[NC], s_rr[NC], s_bn[NC], s_pap[NC], s_alpha[NC], s_beta[NC];
     __shared__ int s_active[NC];
     const int c = threadIdx.x / BS, t = threadIdx.x % BS;
@@ -205,32 +247,32 @@ __global__ void __launch_bounds__(BS * NC) k_pcg(const CGArgs a) {
         x = a.is_wall[i] ? a.g[NC * (size_t)i + c] : a.x[NC * (size_t)i + c];
         a.x[NC * (size_t)i + c] = x;
     }
-    for (int q = threadIdx.x; q < BS * BS; q += BS * NC) inv[q] = 0.f;
+    for (int q = threadIdx.x; q < BS * (BS + 4); q += BS * NC) inv[q] = 0.f;
     __syncthreads();
     if (c == 0) {
         if (free_row) {
             for (int q = a.rowptr[i]; q < a.rowptr[i + 1]; ++q) {
                 const int j = a.colidx[q], jl = j - blockIdx.x * BS;
-                if (jl >= 0 && jl < BS && a.rep[j] == j && !a.is_wall[j]) inv[jl * BS + t] = (float)a.aval[q];
+                if (jl >= 0 && jl < BS && a.rep[j] == j && !a.is_wall[j]) inv[jl * (BS + 4) + t] = (float)a.aval[q];
             }
         } else {
-            inv[t * BS + t] = 1.f;
+            inv[t * (BS + 4) + t] = 1.f;
         }
     }
     __syncthreads();
     for (int k = 0; k < BS; ++k) {  // in-place Gauss-Jordan inverse
-        const float fk = inv[k * BS + t];  // a[t][k]
-        const float p = inv[k * BS + k];
+        const float fk = inv[k * (BS + 4) + t];  // a[t][k]
+        const float p = inv[k * (BS + 4) + k];
         __syncthreads();
         if (c == 0) {
-            const float v = (t == k) ? 1.f : inv[t * BS + k];  // a[k][t]
-            inv[t * BS + k] = v / p;
+            const float v = (t == k) ? 1.f : inv[t * (BS + 4) + k];  // a[k][t]
+            inv[t * (BS + 4) + k] = v / p;
         }
         __syncthreads();
         if (t != k) {
             for (int j = c; j < BS; j += NC) {
-                if (j == k) inv[k * BS + t] = -fk * inv[k * BS + k];
-                else inv[j * BS + t] -= fk * inv[j * BS + k];
+                if (j == k) inv[k * (BS + 4) + t] = -fk * inv[k * (BS + 4) + k];
+                else inv[j * (BS + 4) + t] -= fk * inv[j * (BS + 4) + k];
             }
         }
         __syncthreads();
@@ -249,7 +291,7 @@ __global__ void __launch_bounds__(BS * NC) k_pcg(const CGArgs a) {
             }
         }
         r = free_row ? b - s : 0.0;
-        z = block_precondition<BS>(inv, rv, c, t, r);
+        z = block_precondition<BS>(inv, rv, zv, c, t, r);
         if (!free_row) z = 0.0;
         p = z;
         if (have) a.zg[NC * (size_t)i + c] = z;
@@ -299,7 +341,7 @@ __global__ void __launch_bounds__(BS * NC) k_pcg(const CGArgs a) {
                 x += s_alpha[c] * p;
                 r -= s_alpha[c] * ap;
             }
-            double zn = block_precondition<BS>(inv, rv, c, t, r);
+            double zn = block_precondition<BS>(inv, rv, zv, c, t, r);
             if (!free_row) zn = 0.0;
             if (act) z = zn;
             if (have) a.zg[NC * (size_t)i + c] = z;
@@ -341,7 +383,7 @@ __global__ void __launch_bounds__(BS * NC) k_pcg(const CGArgs a) {
 
 template <int BS>
 constexpr size_t pcg_smem() {
-    return sizeof(float) * (BS * BS + NC * BS) + sizeof(double) * 3 * NC * BS;
+    return sizeof(float) * (BS * (BS + 4) + 2 * NC * BS) + sizeof(double) * 3 * NC * BS;
 }
 
 __global__ void k_fe_copy_out(int nn, const int* __restrict__ rep, const double* __restrict__ x, double* nwp) {
@@ -389,7 +431,7 @@ int launch_elliptic(pdf_ctx* c) {
         else if ((blocks = try_blocks<160>(c, nn, per_sm)) > 0 && blocks <= per_sm * c->num_sms) c->fe_bs = 160;
         else if ((blocks = try_blocks<192>(c, nn, per_sm)) > 0 && blocks <= per_sm * c->num_sms) c->fe_bs = 192;
         else return fail(c, PDF_ERR_CAPACITY, "elliptic solver: mesh too large for one resident grid");
-        if ((size_t)blocks * PART_W > (size_t)15 * 4096)
+        if ((size_t)blocks * PART_W > (size_t)15 * 4096 || (blocks + 15) / 16 > 63)
             return fail(c, PDF_ERR_CAPACITY, "elliptic solver: partial-sum buffer too small");
         c->fe_blocks = blocks;
     }

@@ -473,16 +473,22 @@ __global__ void __launch_bounds__(32 * WARPS_PER_BLOCK) k_moments_warp(const Mom
 
 
 // ---------------------------------------------------------------------------
-// median-split variant (every level splits a group in two, as for the 2x2x2
-// bins): no sort. For each group the boundary key -- the ceil(m/2)-th
-// smallest (value, id) -- is found by a warp-wide bisection over the value
-// bits (counts of keys below a candidate by warp reductions), with a second
-// bisection over the id bits when equal values straddle the boundary.
-// Segments up to 32*KPL particles; key j of a lane is element j*32+lane.
+// median-split variant (every level halves its groups, as for the 2x2x2
+// bins), one warp per element, compact code: the keys of the segment live in
+// the warp's shared-memory slice and every pass is a rolled loop over the
+// segment (element j handled by lane j % 32).
+//  * moments: exact fixed-point sums of the values and their products
+//    (integer pipes), correctly rounded to FP64 once per element;
+//  * bins: per level and per group the boundary key -- the ceil(m/2)-th
+//    smallest (value, id) -- by a bisection over the value bits, all groups
+//    of the level at once (counts packed two per 32-bit word, summed by warp
+//    reductions), then an id bisection when equal values straddle it;
+//  * <phi|V>: exact fixed-point psi sums per bin (shared-memory atomics).
 // ---------------------------------------------------------------------------
 struct SelSmem {
-    float psi[WARP_MAX_N];
-    unsigned char bin[WARP_MAX_N];
+    uint32_t kv[WARP_MAX_N];  // order-preserving value bits of the current level
+    uint32_t id[WARP_MAX_N];
+    unsigned char grp[WARP_MAX_N];
     unsigned long long binsum[8];  // sum of psi per bin, unit 2^-54 (psi in [0, 1])
     int bincnt[8];
 };
@@ -493,264 +499,170 @@ __device__ __forceinline__ void x128_add_parts(Exact128& a, unsigned m, int e, b
     x128_add(a, lo, hi, neg);
 }
 
-template <int KPL>
-__device__ __forceinline__ int count_below(const uint32_t (&v)[KPL], const uint32_t (&id)[KPL],
-                                           const int (&grp)[KPL], int g, uint32_t cv, uint32_t cid, int lane,
-                                           int n) {
+// #{keys of group g with (v < cv) or (v == cv and id < cid)} over the segment
+__device__ __noinline__ int sel_count(const SelSmem& S, int n, int g, uint32_t cv, uint32_t cid, int lane) {
     int c = 0;
-#pragma unroll
-    for (int r = 0; r < KPL; ++r)
-        c += (r * 32 + lane < n && grp[r] == g && (v[r] < cv || (v[r] == cv && id[r] < cid))) ? 1 : 0;
+    for (int q = lane; q < n; q += 32) {
+        const uint32_t v = S.kv[q];
+        c += (S.grp[q] == g && (v < cv || (v == cv && S.id[q] < cid))) ? 1 : 0;
+    }
     return __reduce_add_sync(0xffffffffu, c);
 }
 
-
-// One median level for NG groups at once: bisection over the value bits with
-// the per-group counts packed two per 32-bit word (16-bit fields) and summed
-// by warp reductions; then per group the id bisection if equal values
-// straddle the boundary. Groups g become 2g (lower half) and 2g+1.
-template <int KPL, int NG>
-__device__ __forceinline__ void split_level(const uint32_t (&kv)[KPL], const uint32_t (&kid)[KPL], int (&grp)[KPL],
-                                            int (&gsize)[4], uint32_t vmin, uint32_t vmax, int lane, int n) {
+// split every group g < ng of the current level into 2g (lower half) and 2g+1
+__device__ __noinline__ void sel_split(SelSmem& S, int n, int ng, int (&gsize)[4], int lane) {
+    uint32_t vmin = 0xffffffffu, vmax = 0u;
+    for (int q = lane; q < n; q += 32) {
+        vmin = min(vmin, S.kv[q]);
+        vmax = max(vmax, S.kv[q]);
+    }
+    vmin = __reduce_min_sync(0xffffffffu, vmin);
+    vmax = __reduce_max_sync(0xffffffffu, vmax);
     const uint32_t diff = vmin ^ vmax;
     const int hb = diff ? 31 - __clz(diff) : -1;
     const uint32_t prefix = hb >= 0 ? (vmin & ~((2u << hb) - 1u)) : vmin;
-    uint32_t ans[NG];
-    int T[NG];
-#pragma unroll
-    for (int g = 0; g < NG; ++g) {
-        ans[g] = prefix;
-        T[g] = (gsize[g] + 1) / 2;
-    }
+    uint32_t ans0 = prefix, ans1 = prefix, ans2 = prefix, ans3 = prefix;
+    const int T0 = (gsize[0] + 1) / 2, T1 = (gsize[1] + 1) / 2, T2 = (gsize[2] + 1) / 2, T3 = (gsize[3] + 1) / 2;
     for (int bit = hb; bit >= 0; --bit) {
-        uint32_t cand[NG];
-#pragma unroll
-        for (int g = 0; g < NG; ++g) cand[g] = ans[g] | (1u << bit);
+        const uint32_t m = 1u << bit;
+        const uint32_t c0 = ans0 | m, c1 = ans1 | m, c2 = ans2 | m, c3 = ans3 | m;
         uint32_t lo = 0, hi = 0;
-#pragma unroll
-        for (int r = 0; r < KPL; ++r) {
-            const int q = r * 32 + lane;
-            const int gr = grp[r];
-            uint32_t c = cand[0];
-            if (NG > 1 && gr == 1) c = cand[1];
-            if (NG > 2 && gr == 2) c = cand[2];
-            if (NG > 3 && gr == 3) c = cand[3];
-            const uint32_t lt = (q < n && kv[r] < c) ? 1u : 0u;
-            const uint32_t inc = lt << (16 * (gr & 1));
-            if (NG <= 2 || gr < 2) lo += inc;
+        for (int q = lane; q < n; q += 32) {
+            const int gr = S.grp[q];
+            const uint32_t cand = gr == 0 ? c0 : (gr == 1 ? c1 : (gr == 2 ? c2 : c3));
+            const uint32_t inc = (S.kv[q] < cand ? 1u : 0u) << (16 * (gr & 1));
+            if (gr < 2) lo += inc;
             else hi += inc;
         }
         lo = __reduce_add_sync(0xffffffffu, lo);
-        if (NG > 2) hi = __reduce_add_sync(0xffffffffu, hi);
-#pragma unroll
-        for (int g = 0; g < NG; ++g) {
-            const uint32_t w = g < 2 ? lo : hi;
-            const int cnt = (int)((w >> (16 * (g & 1))) & 0xffffu);
-            if (cnt < T[g]) ans[g] = cand[g];
-        }
+        if (ng > 2) hi = __reduce_add_sync(0xffffffffu, hi);
+        if ((int)(lo & 0xffffu) < T0) ans0 = c0;
+        if ((int)(lo >> 16) < T1) ans1 = c1;
+        if ((int)(hi & 0xffffu) < T2) ans2 = c2;
+        if ((int)(hi >> 16) < T3) ans3 = c3;
     }
-#pragma unroll
-    for (int g = 0; g < NG; ++g) {
-        const int clt = count_below<KPL>(kv, kid, grp, g, ans[g], 0u, lane, n);
-        const int cle = ans[g] == 0xffffffffu ? gsize[g] : count_below<KPL>(kv, kid, grp, g, ans[g] + 1u, 0u, lane, n);
+    for (int g = 0; g < ng; ++g) {
+        const uint32_t ans = g == 0 ? ans0 : (g == 1 ? ans1 : (g == 2 ? ans2 : ans3));
+        const int T = g == 0 ? T0 : (g == 1 ? T1 : (g == 2 ? T2 : T3));
+        const int clt = sel_count(S, n, g, ans, 0u, lane);
+        const int cle = ans == 0xffffffffu ? gsize[g] : sel_count(S, n, g, ans + 1u, 0u, lane);
         uint32_t idb = 0xffffffffu;
-        if (cle - clt > 1 && T[g] - clt < cle - clt) {
+        if (cle - clt > 1 && T - clt < cle - clt) {  // equal values straddle the boundary: split by id
             uint32_t ia = 0u;
             for (int bit = 31; bit >= 0; --bit) {
                 const uint32_t cand = ia | (1u << bit);
-                if (count_below<KPL>(kv, kid, grp, g, ans[g], cand, lane, n) - clt < T[g] - clt) ia = cand;
+                if (sel_count(S, n, g, ans, cand, lane) - clt < T - clt) ia = cand;
             }
             idb = ia;
         }
-#pragma unroll
-        for (int r = 0; r < KPL; ++r) {
-            const int q = r * 32 + lane;
-            if (q < n && grp[r] == g) {
-                const bool low = kv[r] < ans[g] || (kv[r] == ans[g] && kid[r] <= idb);
-                grp[r] = 2 * g + (low ? 0 : 1) + 1000;  // marked: split at this level
+        __syncwarp();
+        for (int q = lane; q < n; q += 32) {
+            if (S.grp[q] == g) {
+                const uint32_t v = S.kv[q];
+                const bool low = v < ans || (v == ans && S.id[q] <= idb);
+                S.grp[q] = (unsigned char)(2 * g + (low ? 0 : 1) + 16);  // marked: split at this level
             }
         }
+        __syncwarp();
     }
-#pragma unroll
-    for (int r = 0; r < KPL; ++r) grp[r] = grp[r] >= 1000 ? grp[r] - 1000 : grp[r];
+    for (int q = lane; q < n; q += 32) S.grp[q] = (unsigned char)(S.grp[q] - 16);
     int ns[4] = {0, 0, 0, 0};
-#pragma unroll
-    for (int g = 0; g < NG && 2 * g + 1 < 4; ++g) {
-        ns[2 * g] = T[g];
-        ns[2 * g + 1] = gsize[g] - T[g];
+    for (int g = 0; g < ng && 2 * g + 1 < 4; ++g) {
+        const int T = g == 0 ? T0 : (g == 1 ? T1 : (g == 2 ? T2 : T3));
+        ns[2 * g] = T;
+        ns[2 * g + 1] = gsize[g] - T;
     }
-#pragma unroll
     for (int g = 0; g < 4; ++g) gsize[g] = ns[g];
+    __syncwarp();
 }
 
-template <bool KAHAN, int KPL>
-__device__ void select_element(const MomArgs<float>& a, int e, int s0, int n, int lane, SelSmem& S) {
-    const int B = a.B;
-    double mean[5];
-    if constexpr (KAHAN) {
-        // compensated FP32 sums (the precision-study variant)
-        AccK m[5];
-#pragma unroll
-        for (int r = 0; r < KPL; ++r) {
-            const int q = r * 32 + lane;
-            if (q < n) {
-                m[0].add(a.u[s0 + q]); m[1].add(a.v[s0 + q]); m[2].add(a.w[s0 + q]);
-                m[3].add(a.psi[s0 + q]); m[4].add(a.om[s0 + q]);
-            }
-        }
-#pragma unroll
-        for (int q = 0; q < 5; ++q) {
-            warp_tree(m[q]);
-            mean[q] = __shfl_sync(0xffffffffu, m[q].value(), 0) / n;
-        }
-        const float mu = (float)mean[0], mv = (float)mean[1], mw = (float)mean[2], mp = (float)mean[3];
-        AccK c2[7];
-#pragma unroll
-        for (int r = 0; r < KPL; ++r) {
-            const int q = r * 32 + lane;
-            if (q < n) {
-                const float du = a.u[s0 + q] - mu, dv = a.v[s0 + q] - mv, dw = a.w[s0 + q] - mw;
-                const float dp = a.psi[s0 + q] - mp;
-                c2[0].add(du * du); c2[1].add(dv * dv); c2[2].add(dw * dw);
-                c2[3].add(du * dv); c2[4].add(du * dw); c2[5].add(dv * dw); c2[6].add(dp * dp);
-            }
-        }
-#pragma unroll
-        for (int q = 0; q < 7; ++q) warp_tree(c2[q]);
-        if (lane == 0) {
-            const double inv_n = 1.0 / n;
-            a.en[e] = n;
-            for (int q = 0; q < 5; ++q) a.emean[5 * e + q] = mean[q];
-            for (int q = 0; q < 6; ++q) a.eR[6 * e + q] = c2[q].value() * inv_n;
-            a.epsivar[e] = c2[6].value() * inv_n;
-        }
-    } else {
-        // exact sums of the values and of their products (integer pipes)
-        Exact128 s1[5], s2[7];
-        bool big = false;
-#pragma unroll
-        for (int r = 0; r < KPL; ++r) {
-            const int q = r * 32 + lane;
-            if (q < n) {
-                unsigned mu_, mv_, mw_, mp_, mo_;
-                int eu, ev, ew, ep, eo;
-                bool nu, nv, nw, np, no;
-                f32_parts(a.u[s0 + q], mu_, eu, nu);
-                f32_parts(a.v[s0 + q], mv_, ev, nv);
-                f32_parts(a.w[s0 + q], mw_, ew, nw);
-                f32_parts(a.psi[s0 + q], mp_, ep, np);
-                f32_parts(a.om[s0 + q], mo_, eo, no);
-                big |= max(max(max(eu, ev), max(ew, ep)), eo) > 145;  // |x| >= 2^19: outside the format
-                x128_add_parts(s1[0], mu_, eu, nu);
-                x128_add_parts(s1[1], mv_, ev, nv);
-                x128_add_parts(s1[2], mw_, ew, nw);
-                x128_add_parts(s1[3], mp_, ep, np);
-                x128_add_parts(s1[4], mo_, eo, no);
-                x128_add_prod(s2[0], mu_, eu, nu, mu_, eu, nu);
-                x128_add_prod(s2[1], mv_, ev, nv, mv_, ev, nv);
-                x128_add_prod(s2[2], mw_, ew, nw, mw_, ew, nw);
-                x128_add_prod(s2[3], mu_, eu, nu, mv_, ev, nv);
-                x128_add_prod(s2[4], mu_, eu, nu, mw_, ew, nw);
-                x128_add_prod(s2[5], mv_, ev, nv, mw_, ew, nw);
-                x128_add_prod(s2[6], mp_, ep, np, mp_, ep, np);
-            }
-        }
-        if (__any_sync(0xffffffffu, big) && lane == 0) set_status(a.status, ST_CAPACITY);
-#pragma unroll
-        for (int k = 0; k < 5; ++k) x128_warp_sum(s1[k]);
-#pragma unroll
-        for (int k = 0; k < 7; ++k) x128_warp_sum(s2[k]);
-        // lane k finishes moment k from the broadcast totals
-        Exact128 t1[5], t2[7];
-#pragma unroll
-        for (int k = 0; k < 5; ++k) {
-            t1[k].lo = __shfl_sync(0xffffffffu, s1[k].lo, 0);
-            t1[k].hi = __shfl_sync(0xffffffffu, s1[k].hi, 0);
-        }
-#pragma unroll
-        for (int k = 0; k < 7; ++k) {
-            t2[k].lo = __shfl_sync(0xffffffffu, s2[k].lo, 0);
-            t2[k].hi = __shfl_sync(0xffffffffu, s2[k].hi, 0);
-        }
-        const int ia[7] = {0, 1, 2, 0, 0, 1, 3}, ib[7] = {0, 1, 2, 1, 2, 2, 3};
-        double val = 0.0;
-        if (lane < 5) {
-            val = x128_to_double(t1[lane]) / n;
-        } else if (lane < 12) {
-            const int k = lane - 5;
-            val = x128_central(t2[k], t1[ia[k]], t1[ib[k]], (unsigned)n);
-        }
-#pragma unroll
-        for (int k = 0; k < 5; ++k) mean[k] = __shfl_sync(0xffffffffu, val, k);
-        if (lane < 5) a.emean[5 * e + lane] = val;
-        else if (lane < 11) a.eR[6 * e + lane - 5] = val;
-        else if (lane == 11) a.epsivar[e] = val;
-        if (lane == 0) a.en[e] = n;
+// exact moments of the segment: lanes 0..4 the means, 5..10 the central
+// second moments, 11 the psi variance
+__device__ __noinline__ void exact_moments(const MomArgs<float>& a, int e, int s0, int n, int lane, double* mean) {
+    Exact128 s1[5], s2[7];
+    bool big = false;
+    for (int q = lane; q < n; q += 32) {
+        unsigned mu_, mv_, mw_, mp_, mo_;
+        int eu, ev, ew, ep, eo;
+        bool nu, nv, nw, np, no;
+        f32_parts(a.u[s0 + q], mu_, eu, nu);
+        f32_parts(a.v[s0 + q], mv_, ev, nv);
+        f32_parts(a.w[s0 + q], mw_, ew, nw);
+        f32_parts(a.psi[s0 + q], mp_, ep, np);
+        f32_parts(a.om[s0 + q], mo_, eo, no);
+        big |= max(max(max(eu, ev), max(ew, ep)), eo) > 145;  // |x| >= 2^19: outside the format
+        x128_add_parts(s1[0], mu_, eu, nu);
+        x128_add_parts(s1[1], mv_, ev, nv);
+        x128_add_parts(s1[2], mw_, ew, nw);
+        x128_add_parts(s1[3], mp_, ep, np);
+        x128_add_parts(s1[4], mo_, eo, no);
+        x128_add_prod(s2[0], mu_, eu, nu, mu_, eu, nu);
+        x128_add_prod(s2[1], mv_, ev, nv, mv_, ev, nv);
+        x128_add_prod(s2[2], mw_, ew, nw, mw_, ew, nw);
+        x128_add_prod(s2[3], mu_, eu, nu, mv_, ev, nv);
+        x128_add_prod(s2[4], mu_, eu, nu, mw_, ew, nw);
+        x128_add_prod(s2[5], mv_, ev, nv, mw_, ew, nw);
+        x128_add_prod(s2[6], mp_, ep, np, mp_, ep, np);
     }
-    if (n < B) {
-        for (int q = lane; q < n; q += 32) a.bin[s0 + q] = 0;
-        for (int b = lane; b < B; b += 32) {
-            a.ecm[(size_t)B * e + b] = mean[3];
-            a.ecmT[(size_t)B * e + b] = (float)mean[3];
-        }
-        return;
-    }
-    uint32_t kv[KPL], kid[KPL];
-    int grp[KPL];
+    if (__any_sync(0xffffffffu, big) && lane == 0) set_status(a.status, ST_CAPACITY);
 #pragma unroll
-    for (int r = 0; r < KPL; ++r) {
-        const int q = r * 32 + lane;
-        grp[r] = 0;
-        kid[r] = q < n ? a.id[s0 + q] : 0u;
-    }
-    int gsize[4] = {n, 0, 0, 0};
-    const int G[3] = {a.G0, a.G1, a.G2};
-    int ngroups = 1;
-#pragma unroll 1
-    for (int d = 0; d < 3; ++d) {
-        if (G[d] == 1) continue;
-        const float* comp = d == 0 ? a.u : (d == 1 ? a.v : a.w);
-        uint32_t vmin = 0xffffffffu, vmax = 0u;
+    for (int k = 0; k < 5; ++k) x128_warp_sum(s1[k]);
 #pragma unroll
-        for (int r = 0; r < KPL; ++r) {
-            const int q = r * 32 + lane;
-            kv[r] = q < n ? ord32(comp[s0 + q]) : 0u;
-            if (q < n) { vmin = min(vmin, kv[r]); vmax = max(vmax, kv[r]); }
-        }
-        vmin = __reduce_min_sync(0xffffffffu, vmin);
-        vmax = __reduce_max_sync(0xffffffffu, vmax);
-        if (ngroups == 1) split_level<KPL, 1>(kv, kid, grp, gsize, vmin, vmax, lane, n);
-        else if (ngroups == 2) split_level<KPL, 2>(kv, kid, grp, gsize, vmin, vmax, lane, n);
-        else split_level<KPL, 4>(kv, kid, grp, gsize, vmin, vmax, lane, n);
-        ngroups *= 2;
-    }
-    // bins, and <phi|V> per bin: exact fixed-point sums of psi (unit 2^-54)
-    for (int b = lane; b < 8; b += 32) { S.binsum[b] = 0ull; S.bincnt[b] = 0; }
-    __syncwarp();
+    for (int k = 0; k < 7; ++k) x128_warp_sum(s2[k]);
+    // lane 5+k needs s2[k], s1[ia[k]], s1[ib[k]]; lane k < 5 needs s1[k]
+    Exact128 mine, xa, xb;
 #pragma unroll
-    for (int r = 0; r < KPL; ++r) {
-        const int q = r * 32 + lane;
-        if (q < n) {
-            const int bn = grp[r];
-            a.bin[s0 + q] = (unsigned char)bn;
-            unsigned m;
-            int ex;
-            bool ng;
-            f32_parts(fminf(fmaxf(a.psi[s0 + q], 0.f), 1.f), m, ex, ng);
-            const int sh = ex - 96;  // m 2^(ex-150) = m 2^(ex-96) 2^-54
-            const unsigned long long v = sh >= 0 ? ((unsigned long long)m << sh)
-                                                 : (-sh < 64 ? ((unsigned long long)m >> (-sh)) : 0ull);
-            atomicAdd(&S.binsum[bn], v);
-            atomicAdd(&S.bincnt[bn], 1);
-        }
+    for (int k = 0; k < 5; ++k) {
+        const unsigned long long lo = __shfl_sync(0xffffffffu, s1[k].lo, 0), hi = __shfl_sync(0xffffffffu, s1[k].hi, 0);
+        if (lane == k) { mine.lo = lo; mine.hi = hi; }
+        const int ia = lane == 5 || lane == 8 || lane == 9 ? 0 : (lane == 6 || lane == 10 ? 1 : (lane == 7 ? 2 : 3));
+        const int ib = lane == 5 ? 0 : (lane == 6 || lane == 8 ? 1 : (lane == 7 || lane == 9 || lane == 10 ? 2 : 3));
+        if (ia == k) { xa.lo = lo; xa.hi = hi; }
+        if (ib == k) { xb.lo = lo; xb.hi = hi; }
     }
-    __syncwarp();
-    for (int b = lane; b < B; b += 32) {
-        const double cm = ldexp(__ull2double_rn(S.binsum[b]), -54) / S.bincnt[b];
-        a.ecm[(size_t)B * e + b] = cm;
-        a.ecmT[(size_t)B * e + b] = (float)cm;
+#pragma unroll
+    for (int k = 0; k < 7; ++k) {
+        const unsigned long long lo = __shfl_sync(0xffffffffu, s2[k].lo, 0), hi = __shfl_sync(0xffffffffu, s2[k].hi, 0);
+        if (lane == 5 + k) { mine.lo = lo; mine.hi = hi; }
     }
-    __syncwarp();
+    double val = 0.0;
+    if (lane < 5) val = x128_to_double(mine) / n;
+    else if (lane < 12) val = x128_central(mine, xa, xb, (unsigned)n);
+#pragma unroll
+    for (int k = 0; k < 5; ++k) mean[k] = __shfl_sync(0xffffffffu, val, k);
+    if (lane < 5) a.emean[5 * e + lane] = val;
+    else if (lane < 11) a.eR[6 * e + lane - 5] = val;
+    else if (lane == 11) a.epsivar[e] = val;
+    if (lane == 0) a.en[e] = n;
+}
+
+__device__ __noinline__ void kahan_moments(const MomArgs<float>& a, int e, int s0, int n, int lane, double* mean) {
+    AccK m[5];
+    for (int q = lane; q < n; q += 32) {
+        m[0].add(a.u[s0 + q]); m[1].add(a.v[s0 + q]); m[2].add(a.w[s0 + q]);
+        m[3].add(a.psi[s0 + q]); m[4].add(a.om[s0 + q]);
+    }
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+        warp_tree(m[q]);
+        mean[q] = __shfl_sync(0xffffffffu, m[q].value(), 0) / n;
+    }
+    const float mu = (float)mean[0], mv = (float)mean[1], mw = (float)mean[2], mp = (float)mean[3];
+    AccK c2[7];
+    for (int q = lane; q < n; q += 32) {
+        const float du = a.u[s0 + q] - mu, dv = a.v[s0 + q] - mv, dw = a.w[s0 + q] - mw, dp = a.psi[s0 + q] - mp;
+        c2[0].add(du * du); c2[1].add(dv * dv); c2[2].add(dw * dw);
+        c2[3].add(du * dv); c2[4].add(du * dw); c2[5].add(dv * dw); c2[6].add(dp * dp);
+    }
+#pragma unroll
+    for (int q = 0; q < 7; ++q) warp_tree(c2[q]);
+    if (lane == 0) {
+        const double inv_n = 1.0 / n;
+        a.en[e] = n;
+        for (int q = 0; q < 5; ++q) a.emean[5 * e + q] = mean[q];
+        for (int q = 0; q < 6; ++q) a.eR[6 * e + q] = c2[q].value() * inv_n;
+        a.epsivar[e] = c2[6].value() * inv_n;
+    }
 }
 
 template <bool KAHAN>
@@ -761,6 +673,8 @@ __global__ void __launch_bounds__(32 * WARPS_PER_BLOCK) k_moments_sel(const MomA
     if (e >= nt) return;
     const int s0 = a.off[e], n = a.off[e + 1] - s0;
     if (n > WARP_MAX_N) return;  // the block kernel takes it
+    const int B = a.B;
+    SelSmem& S = sm[w];
     if (n == 0) {
         if (lane == 0) {
             a.en[e] = 0;
@@ -768,14 +682,60 @@ __global__ void __launch_bounds__(32 * WARPS_PER_BLOCK) k_moments_sel(const MomA
             for (int q = 0; q < 6; ++q) a.eR[6 * e + q] = 0.0;
             a.epsivar[e] = 0.0;
         }
-        for (int b = lane; b < a.B; b += 32) {
-            a.ecm[(size_t)a.B * e + b] = 0.0;
-            a.ecmT[(size_t)a.B * e + b] = 0.f;
+        for (int b = lane; b < B; b += 32) {
+            a.ecm[(size_t)B * e + b] = 0.0;
+            a.ecmT[(size_t)B * e + b] = 0.f;
         }
         return;
     }
-    if (n <= 256) select_element<KAHAN, 8>(a, e, s0, n, lane, sm[w]);
-    else select_element<KAHAN, 16>(a, e, s0, n, lane, sm[w]);
+    double mean[5];
+    if (KAHAN) kahan_moments(a, e, s0, n, lane, mean);
+    else exact_moments(a, e, s0, n, lane, mean);
+    if (n < B) {
+        for (int q = lane; q < n; q += 32) a.bin[s0 + q] = 0;
+        for (int b = lane; b < B; b += 32) {
+            a.ecm[(size_t)B * e + b] = mean[3];
+            a.ecmT[(size_t)B * e + b] = (float)mean[3];
+        }
+        return;
+    }
+    for (int q = lane; q < n; q += 32) {
+        S.id[q] = a.id[s0 + q];
+        S.grp[q] = 0;
+    }
+    int gsize[4] = {n, 0, 0, 0};
+    const int G[3] = {a.G0, a.G1, a.G2};
+    int ng = 1;
+    for (int d = 0; d < 3; ++d) {
+        if (G[d] == 1) continue;
+        const float* comp = d == 0 ? a.u : (d == 1 ? a.v : a.w);
+        for (int q = lane; q < n; q += 32) S.kv[q] = ord32(comp[s0 + q]);
+        __syncwarp();
+        sel_split(S, n, ng, gsize, lane);
+        ng *= 2;
+    }
+    // bins, and <phi|V> per bin: exact fixed-point sums of psi (unit 2^-54)
+    if (lane < 8) { S.binsum[lane] = 0ull; S.bincnt[lane] = 0; }
+    __syncwarp();
+    for (int q = lane; q < n; q += 32) {
+        const int bn = S.grp[q];
+        a.bin[s0 + q] = (unsigned char)bn;
+        unsigned m;
+        int ex;
+        bool negp;
+        f32_parts(fminf(fmaxf(a.psi[s0 + q], 0.f), 1.f), m, ex, negp);
+        const int sh = ex - 96;  // m 2^(ex-150) = m 2^(ex-96) 2^-54
+        const unsigned long long v = sh >= 0 ? ((unsigned long long)m << sh)
+                                             : (-sh < 64 ? ((unsigned long long)m >> (-sh)) : 0ull);
+        atomicAdd(&S.binsum[bn], v);
+        atomicAdd(&S.bincnt[bn], 1);
+    }
+    __syncwarp();
+    for (int b = lane; b < B; b += 32) {
+        const double cm = ldexp(__ull2double_rn(S.binsum[b]), -54) / S.bincnt[b];
+        a.ecm[(size_t)B * e + b] = cm;
+        a.ecmT[(size_t)B * e + b] = (float)cm;
+    }
 }
 
 template <typename T, bool KAHAN>
