@@ -489,6 +489,10 @@ struct SelSmem {
     uint32_t kv[WARP_MAX_N];  // order-preserving value bits of the current level
     uint32_t id[WARP_MAX_N];
     unsigned char grp[WARP_MAX_N];
+    int hist[4][256];          // per-group histogram of the top 8 varying value bits
+    uint32_t cv[32], cid[32];  // candidates of the boundary bucket
+    int ncand;
+    uint32_t bv, bid;          // boundary key found by the warp
     unsigned long long binsum[8];  // sum of psi per bin, unit 2^-54 (psi in [0, 1])
     int bincnt[8];
 };
@@ -509,7 +513,33 @@ __device__ __noinline__ int sel_count(const SelSmem& S, int n, int g, uint32_t c
     return __reduce_add_sync(0xffffffffu, c);
 }
 
-// split every group g < ng of the current level into 2g (lower half) and 2g+1
+// boundary key of group g by bisection over the value bits (then id bits):
+// the T-th smallest (value, id); used when the histogram leaves too many
+// candidates in one bucket
+__device__ __noinline__ void sel_bisect(const SelSmem& S, int n, int g, int T, int gsz, uint32_t prefix, int hb,
+                                        int lane, uint32_t& ans, uint32_t& idb) {
+    ans = prefix;
+    for (int bit = hb; bit >= 0; --bit) {
+        const uint32_t cand = ans | (1u << bit);
+        if (sel_count(S, n, g, cand, 0u, lane) < T) ans = cand;
+    }
+    const int clt = sel_count(S, n, g, ans, 0u, lane);
+    const int cle = ans == 0xffffffffu ? gsz : sel_count(S, n, g, ans + 1u, 0u, lane);
+    idb = 0xffffffffu;
+    if (cle - clt > 1 && T - clt < cle - clt) {
+        uint32_t ia = 0u;
+        for (int bit = 31; bit >= 0; --bit) {
+            const uint32_t cand = ia | (1u << bit);
+            if (sel_count(S, n, g, ans, cand, lane) - clt < T - clt) ia = cand;
+        }
+        idb = ia;
+    }
+}
+
+// Split every group g < ng of the current level into 2g (lower half, the
+// ceil(m/2) smallest (value, id) keys) and 2g+1: a 256-bucket histogram of the
+// top 8 varying value bits per group locates the bucket of each group's
+// boundary; the few keys in that bucket are ranked exactly among themselves.
 __device__ __noinline__ void sel_split(SelSmem& S, int n, int ng, int (&gsize)[4], int lane) {
     uint32_t vmin = 0xffffffffu, vmax = 0u;
     for (int q = lane; q < n; q += 32) {
@@ -521,56 +551,83 @@ __device__ __noinline__ void sel_split(SelSmem& S, int n, int ng, int (&gsize)[4
     const uint32_t diff = vmin ^ vmax;
     const int hb = diff ? 31 - __clz(diff) : -1;
     const uint32_t prefix = hb >= 0 ? (vmin & ~((2u << hb) - 1u)) : vmin;
-    uint32_t ans0 = prefix, ans1 = prefix, ans2 = prefix, ans3 = prefix;
-    const int T0 = (gsize[0] + 1) / 2, T1 = (gsize[1] + 1) / 2, T2 = (gsize[2] + 1) / 2, T3 = (gsize[3] + 1) / 2;
-    for (int bit = hb; bit >= 0; --bit) {
-        const uint32_t m = 1u << bit;
-        const uint32_t c0 = ans0 | m, c1 = ans1 | m, c2 = ans2 | m, c3 = ans3 | m;
-        uint32_t lo = 0, hi = 0;
-        for (int q = lane; q < n; q += 32) {
-            const int gr = S.grp[q];
-            const uint32_t cand = gr == 0 ? c0 : (gr == 1 ? c1 : (gr == 2 ? c2 : c3));
-            const uint32_t inc = (S.kv[q] < cand ? 1u : 0u) << (16 * (gr & 1));
-            if (gr < 2) lo += inc;
-            else hi += inc;
-        }
-        lo = __reduce_add_sync(0xffffffffu, lo);
-        if (ng > 2) hi = __reduce_add_sync(0xffffffffu, hi);
-        if ((int)(lo & 0xffffu) < T0) ans0 = c0;
-        if ((int)(lo >> 16) < T1) ans1 = c1;
-        if ((int)(hi & 0xffffu) < T2) ans2 = c2;
-        if ((int)(hi >> 16) < T3) ans3 = c3;
-    }
+    const int shift = hb >= 7 ? hb - 7 : 0;
+    for (int q = lane; q < ng * 256; q += 32) (&S.hist[0][0])[q] = 0;
+    __syncwarp();
+    for (int q = lane; q < n; q += 32) atomicAdd(&S.hist[S.grp[q]][(S.kv[q] - prefix) >> shift], 1);
+    __syncwarp();
+    uint32_t bvs[4], bids[4];
+    int Ts[4];
     for (int g = 0; g < ng; ++g) {
-        const uint32_t ans = g == 0 ? ans0 : (g == 1 ? ans1 : (g == 2 ? ans2 : ans3));
-        const int T = g == 0 ? T0 : (g == 1 ? T1 : (g == 2 ? T2 : T3));
-        const int clt = sel_count(S, n, g, ans, 0u, lane);
-        const int cle = ans == 0xffffffffu ? gsize[g] : sel_count(S, n, g, ans + 1u, 0u, lane);
-        uint32_t idb = 0xffffffffu;
-        if (cle - clt > 1 && T - clt < cle - clt) {  // equal values straddle the boundary: split by id
-            uint32_t ia = 0u;
-            for (int bit = 31; bit >= 0; --bit) {
-                const uint32_t cand = ia | (1u << bit);
-                if (sel_count(S, n, g, ans, cand, lane) - clt < T - clt) ia = cand;
-            }
-            idb = ia;
+        const int T = (gsize[g] + 1) / 2;
+        Ts[g] = T;
+        // bucket where the cumulative count reaches T (8 buckets per lane)
+        int loc[8], tot = 0;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            loc[k] = S.hist[g][8 * lane + k];
+            tot += loc[k];
         }
-        __syncwarp();
-        for (int q = lane; q < n; q += 32) {
-            if (S.grp[q] == g) {
-                const uint32_t v = S.kv[q];
-                const bool low = v < ans || (v == ans && S.id[q] <= idb);
-                S.grp[q] = (unsigned char)(2 * g + (low ? 0 : 1) + 16);  // marked: split at this level
+        int incl = tot;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        const int excl = incl - tot;
+        int mybucket = -1, mybelow = 0;
+        if (excl < T && incl >= T) {
+            int run = excl;
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                if (mybucket < 0 && run + loc[k] >= T) { mybucket = 8 * lane + k; mybelow = run; }
+                run += loc[k];
             }
         }
-        __syncwarp();
+        const unsigned who = __ballot_sync(0xffffffffu, mybucket >= 0);
+        const int src = __ffs(who) - 1;
+        const int bucket = __shfl_sync(0xffffffffu, mybucket, src);
+        const int below = __shfl_sync(0xffffffffu, mybelow, src);
+        const int kc = S.hist[g][bucket];
+        const int rank = T - below - 1;  // 0-based rank of the boundary among the bucket's keys
+        if (kc <= 32) {
+            if (lane == 0) S.ncand = 0;
+            __syncwarp();
+            for (int q = lane; q < n; q += 32) {
+                if (S.grp[q] == g && (int)((S.kv[q] - prefix) >> shift) == bucket) {
+                    const int slot = atomicAdd(&S.ncand, 1);
+                    S.cv[slot] = S.kv[q];
+                    S.cid[slot] = S.id[q];
+                }
+            }
+            __syncwarp();
+            if (lane < kc) {
+                const uint32_t v = S.cv[lane], id = S.cid[lane];
+                int r = 0;
+                for (int j = 0; j < kc; ++j) {
+                    const uint32_t vj = S.cv[j];
+                    r += (vj < v || (vj == v && S.cid[j] < id)) ? 1 : 0;
+                }
+                if (r == rank) { S.bv = v; S.bid = id; }
+            }
+            __syncwarp();
+            bvs[g] = S.bv;
+            bids[g] = S.bid;
+            __syncwarp();
+        } else {
+            sel_bisect(S, n, g, T, gsize[g], prefix, hb, lane, bvs[g], bids[g]);
+        }
     }
-    for (int q = lane; q < n; q += 32) S.grp[q] = (unsigned char)(S.grp[q] - 16);
+    for (int q = lane; q < n; q += 32) {
+        const int g = S.grp[q];
+        const uint32_t v = S.kv[q], bv = bvs[g];
+        const bool low = v < bv || (v == bv && S.id[q] <= bids[g]);
+        S.grp[q] = (unsigned char)(2 * g + (low ? 0 : 1));
+    }
     int ns[4] = {0, 0, 0, 0};
     for (int g = 0; g < ng && 2 * g + 1 < 4; ++g) {
-        const int T = g == 0 ? T0 : (g == 1 ? T1 : (g == 2 ? T2 : T3));
-        ns[2 * g] = T;
-        ns[2 * g + 1] = gsize[g] - T;
+        ns[2 * g] = Ts[g];
+        ns[2 * g + 1] = gsize[g] - Ts[g];
     }
     for (int g = 0; g < 4; ++g) gsize[g] = ns[g];
     __syncwarp();
