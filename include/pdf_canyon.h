@@ -83,6 +83,9 @@ typedef struct pdf_params {
     uint64_t seed;         /* Philox key (low word, high word xor case_id) */
     uint32_t case_id;
     int32_t precision;     /* enum pdf_precision; fixed for the life of a context */
+    int32_t cg_precision;  /* elliptic CG arithmetic: 0 FP64; 1 compensated FP32 (float-float,
+                              ~48-bit significand) with FP64 solution and coefficients */
+    int32_t reserved_;
 } pdf_params;
 
 /* Fields readable with pdf_get_fields. Particle fields are in the library's

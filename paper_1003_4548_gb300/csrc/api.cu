@@ -96,6 +96,7 @@ int check_params(const pdf_params* p) {
     if (p->nb1 < 1 || p->nb2 < 1 || p->nb3 < 1 || p->nb1 * p->nb2 * p->nb3 > 255) return PDF_ERR_ARG;
     if (p->precision < 0 || p->precision > 2) return PDF_ERR_ARG;
     if (p->wall_model < 0 || p->wall_model > 1) return PDF_ERR_ARG;
+    if (p->cg_precision < 0 || p->cg_precision > 1) return PDF_ERR_ARG;
     if (!(p->period > 0) || !(p->nu > 0) || p->reflect_max < 0 || p->cg_maxit < 0) return PDF_ERR_ARG;
     return PDF_OK;
 }
@@ -308,6 +309,7 @@ int build_mesh(pdf_ctx* c, const double* xy, int nn, const int* tri, int nt, con
         TRY(upload(c, &m.kc_geo, kc_geo));
         TRY(upload(c, &m.diag, diag));
         TRY(dalloc(c, &m.aval, m.nnz));
+        TRY(dalloc(c, &m.avf, m.nnz));
     }
     return PDF_OK;
 }
@@ -444,6 +446,8 @@ int pdf_default_params(pdf_params* p) {
     p->seed = 0;
     p->case_id = 0;
     p->precision = PDF_FP64;
+    p->cg_precision = 0;
+    p->reserved_ = 0;
     return PDF_OK;
 }
 
@@ -657,7 +661,7 @@ void pdf_destroy(pdf_ctx* c) {
     DevMesh& m = c->m;
     void* dev[] = {m.tri, m.nbr, m.einfo, m.xy, m.egeo_d, m.egeo_f, m.gradb, m.area, m.cent, m.n2e_off, m.n2e,
                    m.wdist, m.wn, m.is_wall, m.rep, m.rowptr, m.colidx, m.mval, m.kc_off, m.kc_elem, m.kc_geo,
-                   m.aval, m.diag, c->idA, c->idB, c->elemA, c->elemB, c->bin, c->cnt, c->off, c->cursor, c->en,
+                   m.aval, m.avf, m.diag, c->idA, c->idB, c->elemA, c->elemB, c->bin, c->cnt, c->off, c->cursor, c->en,
                    c->emean, c->eR, c->epsivar, c->ecm, c->nwt, c->nmean, c->nR, c->nke, c->npsivar, c->eder,
                    c->ngrad, c->npack, c->nwp, c->npackT, c->epackT, c->ecmT, c->sort_scratch, c->fe_f, c->fe_g,
                    c->fe_b, c->fe_r, c->fe_z, c->fe_p, c->fe_ap, c->fe_part, c->fe_bar, c->fe_iters, c->d_status,

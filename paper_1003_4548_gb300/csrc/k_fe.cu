@@ -14,6 +14,7 @@
 // barrier whose spin is bounded (status ST_BARRIER on expiry).
 #include <cooperative_groups.h>
 
+#include "ff.cuh"
 #include "pdf_internal.cuh"
 
 namespace {
@@ -77,6 +78,7 @@ struct CGArgs {
     const double* __restrict__ f;
     const double* __restrict__ g;
     double* aval;
+    float2* avf;   // aval as float-float (hi, lo), compensated-FP32 variant
     double* x;     // [nn][NC] node solution: warm start in, result out (canonical rows)
     double* zg;    // [nn][NC] preconditioned residual, shared between blocks for the SpMV
     double* part;  // [gridDim][PART_W]
@@ -369,6 +371,230 @@ __global__ void __launch_bounds__(BS * NC) k_pcg(const CGArgs a) {
     if (blockIdx.x == 0 && threadIdx.x == 0) *a.iters = it;
 }
 
+
+// ---------------------------------------------------------------------------
+// Compensated-FP32 variant of the same flexible PCG: the iteration runs in
+// float-float arithmetic (~48-bit significand: products by FMA TwoProduct,
+// sums by TwoSum) -- the SpMV, the vector updates and the dot products with
+// their block and grid reductions -- so no FP64 instruction sits in the
+// loop; the initial residual, the CG coefficients and the stored solution
+// are FP64. Its solution is checked against the FP64 CPU oracle.
+// ---------------------------------------------------------------------------
+template <int BS>
+__device__ void block_partial_ff(const CGArgs& a, const float* rh, const float* rl, int nv, int slot) {
+    __syncthreads();
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    float2* part = reinterpret_cast<float2*>(a.part);
+    for (int q = wid; q < nv * NC; q += (BS * NC) / 32) {
+        ff s = ff{0.f, 0.f};
+        for (int t = lane; t < BS; t += 32) s = ff_add(s, ff{rh[q * BS + t], rl[q * BS + t]});
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s = ff_add(s, ff_shfl_down(s, o));
+        if (lane == 0) part[(size_t)blockIdx.x * PART_W + slot + q] = make_float2(s.hi, s.lo);
+    }
+    __syncthreads();
+}
+
+__device__ void grid_sum_ff(const CGArgs& a, int slot, int nvals, double* out) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const float2* part = reinterpret_cast<const float2*>(a.part);
+    for (int q = wid; q < nvals; q += blockDim.x / 32) {
+        ff s = ff{0.f, 0.f};
+        for (int bl = lane; bl < (int)gridDim.x; bl += 32) {
+            const float2 v = part[(size_t)bl * PART_W + slot + q];
+            s = ff_add(s, ff{v.x, v.y});
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s = ff_add(s, ff_shfl_down(s, o));
+        if (lane == 0) out[q] = ff_to_double(s);
+    }
+    __syncthreads();
+}
+
+template <int BS>
+__global__ void __launch_bounds__(BS * NC) k_pcg_ff(const CGArgs a) {
+    extern __shared__ float smem[];
+    float* inv = smem;
+    float* rv = smem + BS * (BS + 4);
+    float* zv = rv + NC * BS;
+    float* redh = zv + NC * BS;      // 3*NC*BS
+    float* redl = redh + 3 * NC * BS;
+    __shared__ double s_a[3 * NC], s_rz[NC], s_rr[NC], s_bn[NC], s_pap[NC], s_alpha[NC], s_beta[NC];
+    __shared__ int s_active[NC];
+    const int c = threadIdx.x / BS, t = threadIdx.x % BS;
+    const int i = blockIdx.x * BS + t;
+    const bool have = i < a.nn;
+    const bool free_row = have && a.rep[i] == i && !a.is_wall[i];
+    double b = 0.0, x0 = 0.0;
+    if (have) {
+        for (int q = a.rowptr[i]; q < a.rowptr[i + 1]; ++q) {
+            if (c == 0) {
+                double s = a.mval[q];
+                for (int k = a.kc_off[q]; k < a.kc_off[q + 1]; ++k) {
+                    const double L = a.eder[9 * (size_t)a.kc_elem[k] + 8];
+                    s += L * L * a.kc_geo[k];
+                }
+                a.aval[q] = s;
+                const ff v = ff_from_double(s);
+                a.avf[q] = make_float2(v.hi, v.lo);
+            }
+            b += a.mval[q] * a.f[NC * (size_t)a.colidx[q] + c];
+        }
+        x0 = a.is_wall[i] ? a.g[NC * (size_t)i + c] : a.x[NC * (size_t)i + c];
+        a.x[NC * (size_t)i + c] = x0;
+    }
+    for (int q = threadIdx.x; q < BS * (BS + 4); q += BS * NC) inv[q] = 0.f;
+    __syncthreads();
+    if (c == 0) {
+        if (free_row) {
+            for (int q = a.rowptr[i]; q < a.rowptr[i + 1]; ++q) {
+                const int j = a.colidx[q], jl = j - blockIdx.x * BS;
+                if (jl >= 0 && jl < BS && a.rep[j] == j && !a.is_wall[j]) inv[jl * (BS + 4) + t] = (float)a.aval[q];
+            }
+        } else {
+            inv[t * (BS + 4) + t] = 1.f;
+        }
+    }
+    __syncthreads();
+    for (int k = 0; k < BS; ++k) {  // in-place Gauss-Jordan inverse (FP32)
+        const float fk = inv[k * (BS + 4) + t];
+        const float p = inv[k * (BS + 4) + k];
+        __syncthreads();
+        if (c == 0) {
+            const float v = (t == k) ? 1.f : inv[t * (BS + 4) + k];
+            inv[t * (BS + 4) + k] = v / p;
+        }
+        __syncthreads();
+        if (t != k) {
+            for (int j = c; j < BS; j += NC) {
+                if (j == k) inv[k * (BS + 4) + t] = -fk * inv[k * (BS + 4) + k];
+                else inv[j * (BS + 4) + t] -= fk * inv[j * (BS + 4) + k];
+            }
+        }
+        __syncthreads();
+    }
+    grid_barrier(a);
+    float* zg = reinterpret_cast<float*>(a.zg);
+    ff x = ff_from_double(x0), r, p, ap;
+    float z;
+    {  // r = b - A x in FP64 once, then float-float
+        double s = 0.0, b0 = b;
+        if (free_row) {
+            for (int q = a.rowptr[i]; q < a.rowptr[i + 1]; ++q) {
+                const int j = a.colidx[q];
+                const double xv = a.aval[q] * a.x[NC * (size_t)j + c];
+                s += xv;
+                if (a.is_wall[j]) b0 -= xv;
+            }
+        }
+        r = ff_from_double(free_row ? b - s : 0.0);
+        z = (float)block_precondition<BS>(inv, rv, zv, c, t, (double)r.hi);
+        if (!free_row) z = 0.f;
+        p = ff_make(z);
+        if (have) zg[NC * (size_t)i + c] = z;
+        const ff rz = ff_mul_f(r, z), rr = ff_mul(r, r), bb = ff_from_double(free_row ? b0 * b0 : 0.0);
+        redh[(0 * NC + c) * BS + t] = rz.hi; redl[(0 * NC + c) * BS + t] = rz.lo;
+        redh[(1 * NC + c) * BS + t] = rr.hi; redl[(1 * NC + c) * BS + t] = rr.lo;
+        redh[(2 * NC + c) * BS + t] = bb.hi; redl[(2 * NC + c) * BS + t] = bb.lo;
+        block_partial_ff<BS>(a, redh, redl, 3, 0);
+    }
+    grid_barrier(a);
+    grid_sum_ff(a, 0, 3 * NC, s_a);
+    if (threadIdx.x < NC) {
+        s_rz[threadIdx.x] = s_a[threadIdx.x];
+        s_rr[threadIdx.x] = s_a[NC + threadIdx.x];
+        s_bn[threadIdx.x] = sqrt(s_a[2 * NC + threadIdx.x]);
+    }
+    grid_barrier(a);  // the partials are reused below
+    {  // A p_0
+        ff s = ff{0.f, 0.f};
+        if (free_row)
+            for (int q = a.rowptr[i]; q < a.rowptr[i + 1]; ++q) {
+                const float2 av = a.avf[q];
+                s = ff_add(s, ff_mul_f(ff{av.x, av.y}, zg[NC * (size_t)a.colidx[q] + c]));
+            }
+        ap = free_row ? s : ff{0.f, 0.f};
+        const ff pap = ff_mul(p, ap);
+        redh[c * BS + t] = pap.hi;
+        redl[c * BS + t] = pap.lo;
+        block_partial_ff<BS>(a, redh, redl, 1, 3 * NC);
+    }
+    grid_barrier(a);
+    grid_sum_ff(a, 3 * NC, NC, s_pap);
+    int it = 0;
+    for (;; ++it) {
+        if (threadIdx.x < NC) {
+            const int k = threadIdx.x;
+            s_active[k] = (s_bn[k] > 0.0) && (sqrt(s_rr[k]) > a.tol * s_bn[k]);
+            s_alpha[k] = s_active[k] ? s_rz[k] / s_pap[k] : 0.0;
+        }
+        __syncthreads();
+        bool any = false;
+#pragma unroll
+        for (int k = 0; k < NC; ++k) any |= s_active[k] != 0;
+        if (!any) break;
+        if (it >= a.maxit) {
+            if (blockIdx.x == 0 && threadIdx.x == 0) set_status(a.status, ST_CG);
+            break;
+        }
+        const bool act = s_active[c] != 0;
+        {
+            const ff rold = r;
+            if (act) {
+                const ff al = ff_from_double(s_alpha[c]);
+                x = ff_add(x, ff_mul(al, p));
+                r = ff_add(r, ff_neg(ff_mul(al, ap)));
+            }
+            float zn = (float)block_precondition<BS>(inv, rv, zv, c, t, (double)r.hi);
+            if (!free_row) zn = 0.f;
+            if (act) z = zn;
+            if (have) zg[NC * (size_t)i + c] = z;
+            const ff rz = ff_mul_f(r, z), roz = ff_mul_f(rold, z), rr = ff_mul(r, r);
+            redh[(0 * NC + c) * BS + t] = rz.hi; redl[(0 * NC + c) * BS + t] = rz.lo;
+            redh[(1 * NC + c) * BS + t] = roz.hi; redl[(1 * NC + c) * BS + t] = roz.lo;
+            redh[(2 * NC + c) * BS + t] = rr.hi; redl[(2 * NC + c) * BS + t] = rr.lo;
+            block_partial_ff<BS>(a, redh, redl, 3, 0);
+        }
+        grid_barrier(a);
+        grid_sum_ff(a, 0, 3 * NC, s_a);
+        if (threadIdx.x < NC) {
+            const int k = threadIdx.x;
+            s_beta[k] = s_active[k] ? (s_a[k] - s_a[NC + k]) / s_rz[k] : 0.0;
+        }
+        __syncthreads();
+        {
+            ff s = ff{0.f, 0.f};
+            if (free_row)
+                for (int q = a.rowptr[i]; q < a.rowptr[i + 1]; ++q) {
+                    const float2 av = a.avf[q];
+                    s = ff_add(s, ff_mul_f(ff{av.x, av.y}, zg[NC * (size_t)a.colidx[q] + c]));
+                }
+            if (act) {
+                const ff be = ff_from_double(s_beta[c]);
+                p = ff_add(ff_make(z), ff_mul(be, p));
+                ap = ff_add(free_row ? s : ff{0.f, 0.f}, ff_mul(be, ap));
+            }
+            const ff pap = ff_mul(p, ap);
+            redh[c * BS + t] = pap.hi;
+            redl[c * BS + t] = pap.lo;
+            block_partial_ff<BS>(a, redh, redl, 1, 3 * NC);
+        }
+        grid_barrier(a);
+        if (threadIdx.x < NC && s_active[threadIdx.x]) {
+            s_rz[threadIdx.x] = s_a[threadIdx.x];
+            s_rr[threadIdx.x] = s_a[2 * NC + threadIdx.x];
+        }
+        grid_sum_ff(a, 3 * NC, NC, s_pap);
+    }
+    if (free_row) a.x[NC * (size_t)i + c] = ff_to_double(x);
+    if (blockIdx.x == 0 && threadIdx.x == 0) *a.iters = it;
+}
+
+template <int BS>
+constexpr size_t pcg_ff_smem() {
+    return sizeof(float) * (BS * (BS + 4) + 2 * NC * BS + 6 * NC * BS);
+}
+
 template <int BS>
 constexpr size_t pcg_smem() {
     return sizeof(float) * (BS * (BS + 4) + 2 * NC * BS) + sizeof(double) * 3 * NC * BS;
@@ -387,20 +613,26 @@ __global__ void k_fe_copy_out(int nn, const int* __restrict__ rep, const double*
 namespace {
 
 template <int BS>
-int try_blocks(pdf_ctx* c, int nn, int& per_sm) {
-    const size_t smem = pcg_smem<BS>();
-    if (cudaFuncSetAttribute(k_pcg<BS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+void* pcg_fn(bool ffv) { return ffv ? (void*)k_pcg_ff<BS> : (void*)k_pcg<BS>; }
+template <int BS>
+size_t pcg_bytes(bool ffv) { return ffv ? pcg_ff_smem<BS>() : pcg_smem<BS>(); }
+
+template <int BS>
+int try_blocks(pdf_ctx* c, int nn, int& per_sm, bool ffv) {
+    const size_t smem = pcg_bytes<BS>(ffv);
+    if (cudaFuncSetAttribute(pcg_fn<BS>(ffv), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return -1;
     per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg<BS>, BS * NC, smem) != cudaSuccess) return -1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pcg_fn<BS>(ffv), BS * NC, smem) != cudaSuccess)
+        return -1;
     return (nn + BS - 1) / BS;
 }
 
 template <int BS>
-cudaError_t launch_pcg(const CGArgs& a, int blocks, cudaStream_t s) {
+cudaError_t launch_pcg(const CGArgs& a, int blocks, cudaStream_t s, bool ffv) {
     CGArgs aa = a;
     void* args[] = {&aa};
-    return cudaLaunchCooperativeKernel((void*)k_pcg<BS>, dim3(blocks), dim3(BS * NC), args, pcg_smem<BS>(), s);
+    return cudaLaunchCooperativeKernel(pcg_fn<BS>(ffv), dim3(blocks), dim3(BS * NC), args, pcg_bytes<BS>(ffv), s);
 }
 
 }  // namespace
@@ -415,10 +647,11 @@ int launch_elliptic(pdf_ctx* c) {
         // the largest diagonal-block size (fewer blocks and partial sums, a
         // stronger block-Jacobi preconditioner) whose grid is co-resident
         int per_sm = 0, blocks = 0;
-        blocks = try_blocks<192>(c, nn, per_sm);
+        const bool ffv = c->p.cg_precision == 1;
+        blocks = try_blocks<192>(c, nn, per_sm, ffv);
         if (blocks > 0 && blocks <= per_sm * c->num_sms) c->fe_bs = 192;
-        else if ((blocks = try_blocks<160>(c, nn, per_sm)) > 0 && blocks <= per_sm * c->num_sms) c->fe_bs = 160;
-        else if ((blocks = try_blocks<128>(c, nn, per_sm)) > 0 && blocks <= per_sm * c->num_sms) c->fe_bs = 128;
+        else if ((blocks = try_blocks<160>(c, nn, per_sm, ffv)) > 0 && blocks <= per_sm * c->num_sms) c->fe_bs = 160;
+        else if ((blocks = try_blocks<128>(c, nn, per_sm, ffv)) > 0 && blocks <= per_sm * c->num_sms) c->fe_bs = 128;
         else return fail(c, PDF_ERR_CAPACITY, "elliptic solver: mesh too large for one resident grid");
         if ((size_t)blocks * PART_W > (size_t)15 * 4096 || (blocks + 15) / 16 > 63)
             return fail(c, PDF_ERR_CAPACITY, "elliptic solver: partial-sum buffer too small");
@@ -429,15 +662,16 @@ int launch_elliptic(pdf_ctx* c) {
     a.rowptr = c->m.rowptr; a.colidx = c->m.colidx; a.mval = c->m.mval;
     a.kc_off = c->m.kc_off; a.kc_elem = c->m.kc_elem; a.kc_geo = c->m.kc_geo;
     a.eder = c->eder; a.rep = c->m.rep; a.is_wall = c->m.is_wall;
-    a.f = c->fe_f; a.g = c->fe_g; a.aval = c->m.aval;
+    a.f = c->fe_f; a.g = c->fe_g; a.aval = c->m.aval; a.avf = c->m.avf;
     a.x = c->nwp;  // solution lives in the node array (canonical rows)
     a.zg = c->fe_z;
     a.part = c->fe_part; a.bar = c->fe_bar; a.iters = c->fe_iters; a.status = c->d_status;
     a.tol = c->p.cg_tol; a.maxit = c->p.cg_maxit;
     cudaError_t err;
-    if (c->fe_bs == 128) err = launch_pcg<128>(a, c->fe_blocks, c->s);
-    else if (c->fe_bs == 160) err = launch_pcg<160>(a, c->fe_blocks, c->s);
-    else err = launch_pcg<192>(a, c->fe_blocks, c->s);
+    const bool ffv = c->p.cg_precision == 1;
+    if (c->fe_bs == 128) err = launch_pcg<128>(a, c->fe_blocks, c->s, ffv);
+    else if (c->fe_bs == 160) err = launch_pcg<160>(a, c->fe_blocks, c->s, ffv);
+    else err = launch_pcg<192>(a, c->fe_blocks, c->s, ffv);
     PDF_CUDA(c, err);
     k_fe_copy_out<<<(nn + 127) / 128, 128, 0, c->s>>>(nn, c->m.rep, c->nwp, c->nwp);
     c->launches += 3;

@@ -61,6 +61,7 @@ struct DevMesh {
     int* kc_elem = nullptr;
     double* kc_geo = nullptr;  // A_e grad(l_k).grad(l_l)
     double* aval = nullptr;    // assembled M + K_{L^2}
+    float2* avf = nullptr;     // the same as float-float (compensated-FP32 CG)
     int* diag = nullptr;       // position of the diagonal entry per row (-1 if none)
 };
 

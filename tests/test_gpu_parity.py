@@ -31,10 +31,10 @@ def gpu_params(mesh, **kw):
     return canyon_params(mesh, **kw)
 
 
-def both(mesh, *, precision="fp64", wall_model="wf", C0=2.1, seed=0, cg_tol=1e-12, **over):
+def both(mesh, *, precision="fp64", wall_model="wf", C0=2.1, seed=0, cg_tol=1e-12, cg_precision=0, **over):
     from paper_1003_4548_gb300 import Canyon
     gp = gpu_params(mesh, wall_model=wall_model, precision=precision, C0=C0, seed=seed, cg_tol=cg_tol,
-                    cg_maxit=20000, **over)
+                    cg_maxit=20000, cg_precision=cg_precision, **over)
     op = oracle_params_for(mesh, wall_model=0 if wall_model == "wf" else 1, C0=C0, seed=seed,
                            cg_tol=1e-13, **over)
     return Canyon(gp, mesh), Oracle(op, mesh)
@@ -257,3 +257,22 @@ def test_errors_are_reported_not_fatal(wf_mesh):
     assert g.sync(check=False) == 0  # the status word is reset, the context stays usable
     P = g.particles()
     assert P["x"].size == 8 * wf_mesh["tri"].shape[0]
+
+
+@pytest.mark.parametrize("cg_tol", [1e-8, 1e-10])
+def test_compensated_fp32_cg_matches_fp64_oracle(er_mesh, cg_tol):
+    """The float-float elliptic-relaxation CG reaches the FP64 oracle's
+    discrete solution to the requested relative residual."""
+    g, o = both(er_mesh, precision="fp32", wall_model="er", seed=9, cg_tol=cg_tol, cg_precision=1)
+    g.seed_particles(24)
+    g.estimate_stats()
+    g.step(cfl_dt(er_mesh, cfl=0.5, k0=1e-3), 2)
+    g.sync()
+    P = g.particles()
+    o.set_particles(P, step=g.step_index)
+    o.estimate_stats()
+    a, b = g.field("node_wp"), o.field("node_wp")
+    scale = np.sqrt(np.mean(b ** 2, axis=0))
+    err = np.max(np.abs(a - b) / (np.abs(b) + scale), axis=0)
+    assert np.all(err < 100 * cg_tol), err
+    assert g.cg_iterations > 0
