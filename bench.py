@@ -38,6 +38,7 @@ def args_():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="canyon_er_full")
     ap.add_argument("--precision", default=None, help="override the workload precision")
+    ap.add_argument("--cg-precision", type=int, default=0, help="elliptic CG: 0 FP64, 1 compensated FP32")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
@@ -232,7 +233,7 @@ def main():
     stream = torch.cuda.current_stream()
     # each rank runs its own canyon case (independent problems, no exchange)
     p = canyon_params(mesh, wall_model=cfg["wall_model"], precision=cfg["precision"], C0=cfg["C0"],
-                      bins=cfg["bins"], seed=cfg["seed"], k0=cfg["k0"], case_id=rank)
+                      bins=cfg["bins"], seed=cfg["seed"], k0=cfg["k0"], case_id=rank, cg_precision=a.cg_precision)
     g = Canyon(p, mesh, stream=stream.cuda_stream)
     g.seed_particles(cfg["per_element"])
     g.estimate_stats()

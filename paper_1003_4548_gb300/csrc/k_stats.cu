@@ -485,15 +485,16 @@ __global__ void __launch_bounds__(32 * WARPS_PER_BLOCK) k_moments_warp(const Mom
 //    reductions), then an id bisection when equal values straddle it;
 //  * <phi|V>: exact fixed-point psi sums per bin (shared-memory atomics).
 // ---------------------------------------------------------------------------
+template <int NMAX>
 struct SelSmem {
-    uint32_t kv[WARP_MAX_N];  // order-preserving value bits of the current level
-    uint32_t id[WARP_MAX_N];
-    unsigned char grp[WARP_MAX_N];
+    uint32_t kv[NMAX];  // order-preserving value bits of the current level
+    uint32_t id[NMAX];
+    unsigned char grp[NMAX];
     int hist[4][256];          // per-group histogram of the top 8 varying value bits
     uint32_t cv[32], cid[32];  // candidates of the boundary bucket
     int ncand;
     uint32_t bv, bid;          // boundary key found by the warp
-    unsigned long long binsum[8];  // sum of psi per bin, unit 2^-54 (psi in [0, 1])
+    unsigned long long binsum[8];  // sum of psi per bin, unit 2^-(63 - log2 NMAX) (psi in [0, 1])
     int bincnt[8];
 };
 
@@ -504,7 +505,8 @@ __device__ __forceinline__ void x128_add_parts(Exact128& a, unsigned m, int e, b
 }
 
 // #{keys of group g with (v < cv) or (v == cv and id < cid)} over the segment
-__device__ __noinline__ int sel_count(const SelSmem& S, int n, int g, uint32_t cv, uint32_t cid, int lane) {
+template <int NMAX>
+__device__ __noinline__ int sel_count(const SelSmem<NMAX>& S, int n, int g, uint32_t cv, uint32_t cid, int lane) {
     int c = 0;
     for (int q = lane; q < n; q += 32) {
         const uint32_t v = S.kv[q];
@@ -516,7 +518,8 @@ __device__ __noinline__ int sel_count(const SelSmem& S, int n, int g, uint32_t c
 // boundary key of group g by bisection over the value bits (then id bits):
 // the T-th smallest (value, id); used when the histogram leaves too many
 // candidates in one bucket
-__device__ __noinline__ void sel_bisect(const SelSmem& S, int n, int g, int T, int gsz, uint32_t prefix, int hb,
+template <int NMAX>
+__device__ __noinline__ void sel_bisect(const SelSmem<NMAX>& S, int n, int g, int T, int gsz, uint32_t prefix, int hb,
                                         int lane, uint32_t& ans, uint32_t& idb) {
     ans = prefix;
     for (int bit = hb; bit >= 0; --bit) {
@@ -540,7 +543,8 @@ __device__ __noinline__ void sel_bisect(const SelSmem& S, int n, int g, int T, i
 // ceil(m/2) smallest (value, id) keys) and 2g+1: a 256-bucket histogram of the
 // top 8 varying value bits per group locates the bucket of each group's
 // boundary; the few keys in that bucket are ranked exactly among themselves.
-__device__ __noinline__ void sel_split(SelSmem& S, int n, int ng, int (&gsize)[4], int lane) {
+template <int NMAX>
+__device__ __noinline__ void sel_split(SelSmem<NMAX>& S, int n, int ng, int (&gsize)[4], int lane) {
     uint32_t vmin = 0xffffffffu, vmax = 0u;
     for (int q = lane; q < n; q += 32) {
         vmin = min(vmin, S.kv[q]);
@@ -722,16 +726,17 @@ __device__ __noinline__ void kahan_moments(const MomArgs<float>& a, int e, int s
     }
 }
 
-template <bool KAHAN>
-__global__ void __launch_bounds__(32 * WARPS_PER_BLOCK) k_moments_sel(const MomArgs<float> a, int nt) {
-    __shared__ SelSmem sm[WARPS_PER_BLOCK];
+// size classes: NMIN < n <= NMAX (n == 0 with the first class)
+template <bool KAHAN, int NMIN, int NMAX, int WPB>
+__global__ void __launch_bounds__(32 * WPB) k_moments_sel(const MomArgs<float> a, int nt) {
+    __shared__ SelSmem<NMAX> sm[WPB];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int e = blockIdx.x * WARPS_PER_BLOCK + w;
+    const int e = blockIdx.x * WPB + w;
     if (e >= nt) return;
     const int s0 = a.off[e], n = a.off[e + 1] - s0;
-    if (n > WARP_MAX_N) return;  // the block kernel takes it
+    if (n > NMAX || (n <= NMIN && !(NMIN == 0 && n == 0))) return;  // another size class
     const int B = a.B;
-    SelSmem& S = sm[w];
+    SelSmem<NMAX>& S = sm[w];
     if (n == 0) {
         if (lane == 0) {
             a.en[e] = 0;
@@ -771,7 +776,8 @@ __global__ void __launch_bounds__(32 * WARPS_PER_BLOCK) k_moments_sel(const MomA
         sel_split(S, n, ng, gsize, lane);
         ng *= 2;
     }
-    // bins, and <phi|V> per bin: exact fixed-point sums of psi (unit 2^-54)
+    // bins, and <phi|V> per bin: exact fixed-point sums of psi
+    constexpr int UNIT = NMAX <= 512 ? 54 : 51;  // psi <= 1 and n <= NMAX keep the sums below 2^63
     if (lane < 8) { S.binsum[lane] = 0ull; S.bincnt[lane] = 0; }
     __syncwarp();
     for (int q = lane; q < n; q += 32) {
@@ -781,7 +787,7 @@ __global__ void __launch_bounds__(32 * WARPS_PER_BLOCK) k_moments_sel(const MomA
         int ex;
         bool negp;
         f32_parts(fminf(fmaxf(a.psi[s0 + q], 0.f), 1.f), m, ex, negp);
-        const int sh = ex - 96;  // m 2^(ex-150) = m 2^(ex-96) 2^-54
+        const int sh = ex - 150 + UNIT;  // m 2^(ex-150) = m 2^(ex-150+UNIT) 2^-UNIT
         const unsigned long long v = sh >= 0 ? ((unsigned long long)m << sh)
                                              : (-sh < 64 ? ((unsigned long long)m >> (-sh)) : 0ull);
         atomicAdd(&S.binsum[bn], v);
@@ -789,7 +795,7 @@ __global__ void __launch_bounds__(32 * WARPS_PER_BLOCK) k_moments_sel(const MomA
     }
     __syncwarp();
     for (int b = lane; b < B; b += 32) {
-        const double cm = ldexp(__ull2double_rn(S.binsum[b]), -54) / S.bincnt[b];
+        const double cm = ldexp(__ull2double_rn(S.binsum[b]), -UNIT) / S.bincnt[b];
         a.ecm[(size_t)B * e + b] = cm;
         a.ecmT[(size_t)B * e + b] = (float)cm;
     }
@@ -817,9 +823,17 @@ int run(pdf_ctx* c) {
         a.min_n = WARP_MAX_N;
         const unsigned blocks = (unsigned)((c->m.nt + WARPS_PER_BLOCK - 1) / WARPS_PER_BLOCK);
         const bool medians = c->p.nb1 <= 2 && c->p.nb2 <= 2 && c->p.nb3 <= 2;
-        if (medians) k_moments_sel<KAHAN><<<blocks, 32 * WARPS_PER_BLOCK, 0, c->s>>>(a, c->m.nt);
-        else k_moments_warp<KAHAN><<<blocks, 32 * WARPS_PER_BLOCK, 0, c->s>>>(a, c->m.nt);
-        ++c->launches;
+        if (medians) {
+            // crowded elements (particle density drifts during a run) get their
+            // own size class with a larger shared-memory slice per warp
+            a.min_n = 4096;
+            k_moments_sel<KAHAN, 0, 512, WARPS_PER_BLOCK><<<blocks, 32 * WARPS_PER_BLOCK, 0, c->s>>>(a, c->m.nt);
+            k_moments_sel<KAHAN, 512, 4096, 1><<<c->m.nt, 32, 0, c->s>>>(a, c->m.nt);
+            c->launches += 2;
+        } else {
+            k_moments_warp<KAHAN><<<blocks, 32 * WARPS_PER_BLOCK, 0, c->s>>>(a, c->m.nt);
+            ++c->launches;
+        }
     }
     const size_t smem = sizeof(SortKey) * STATS_CAP;
     static bool attr_set = false;

@@ -276,3 +276,43 @@ def test_compensated_fp32_cg_matches_fp64_oracle(er_mesh, cg_tol):
     err = np.max(np.abs(a - b) / (np.abs(b) + scale), axis=0)
     assert np.all(err < 100 * cg_tol), err
     assert g.cg_iterations > 0
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp32_kahan", "fp64"])
+def test_crowded_elements_statistics(wf_mesh, precision):
+    """Elements far above the mean count (the density drifts during long runs)
+    go through the larger size classes of the moments kernel: 700, 3000 and
+    5000 particles in three elements, against the oracle."""
+    g, o = both(wf_mesh, precision=precision, seed=13)
+    o.seed(16)
+    P = o.particles()
+    rng = np.random.default_rng(3)
+    xy, tri = wf_mesh["xy"], wf_mesh["tri"]
+    extra = []
+    for e, m in ((5, 700), (77, 3000), (301, 5000)):
+        s = np.sqrt(rng.random(m))
+        t = rng.random(m)
+        lam = np.stack([1 - s, s * (1 - t), s * t], 1)
+        X = lam @ xy[tri[e]]
+        extra.append(dict(x=X[:, 0], y=X[:, 1], u=1.0 + 0.05 * rng.standard_normal(m),
+                          v=0.05 * rng.standard_normal(m), w=0.05 * rng.standard_normal(m),
+                          om=rng.gamma(4.0, 0.25, m), psi=rng.random(m), elem=np.full(m, e, np.int32)))
+    n0 = P["x"].size
+    Q = {k: np.concatenate([P[k]] + [ex[k] for ex in extra]) for k in ("x", "y", "u", "v", "w", "om", "psi", "elem")}
+    Q["id"] = np.arange(Q["x"].size, dtype=np.uint32)
+    g.set_particles(Q)
+    g.estimate_stats()
+    g.sync()
+    G = g.particles()
+    o.set_particles(G)
+    o.estimate_stats()
+    rt = 2e-6 if precision == "fp32_kahan" else 1e-12
+    cnt = g.field("elem_n")
+    assert cnt[77] == 3000 + 16 and cnt[301] == 5000 + 16 and cnt[5] == 716
+    for name in ("elem_mean", "elem_R", "elem_psivar", "elem_cm"):
+        a, b = g.field(name), o.field(name)
+        scale = np.sqrt(np.mean(b ** 2, axis=0)) + 1e-300
+        assert np.all(np.abs(a - b) <= rt * (np.abs(b) + scale)), name
+    gb = by_id({"id": G["id"], "bin": G["bin"]})
+    ob = by_id({"id": o.particles()["id"], "bin": o.particles()["bin"]})
+    assert np.array_equal(gb["bin"], ob["bin"])
