@@ -493,9 +493,49 @@ struct SelSmem {
     int hist[4][256];          // per-group histogram of the top 8 varying value bits
     uint32_t cv[32], cid[32];  // candidates of the boundary bucket
     int ncand;
-    uint32_t bv, bid;          // boundary key found by the warp
+    uint32_t bv[4], bid[4];    // boundary keys of the level's groups
+    int ired[8];               // team reduction scratch
+    unsigned ured[2][NMAX > 512 ? 8 : 1];
+    unsigned long long xred[NMAX > 512 ? 8 : 1][24];  // per-warp exact sums (12 x 128 bit), block teams only
+    double mean[5];
     unsigned long long binsum[8];  // sum of psi per bin, unit 2^-(63 - log2 NMAX) (psi in [0, 1])
     int bincnt[8];
+};
+
+// NT threads work on one element: a warp (NT = 32) or a whole block
+template <int NT>
+struct Team {
+    int tid, lane, wid;
+    __device__ Team() : tid(threadIdx.x % NT), lane(threadIdx.x & 31), wid((threadIdx.x % NT) >> 5) {}
+    __device__ void sync() const {
+        if (NT == 32) __syncwarp();
+        else __syncthreads();
+    }
+    template <int NMAX>
+    __device__ int sum(int v, SelSmem<NMAX>& S) const {
+        v = __reduce_add_sync(0xffffffffu, v);
+        if (NT == 32) return v;
+        if (lane == 0) S.ired[wid] = v;
+        __syncthreads();
+        int t = 0;
+#pragma unroll
+        for (int w = 0; w < NT / 32; ++w) t += S.ired[w];
+        __syncthreads();
+        return t;
+    }
+    template <int NMAX>
+    __device__ void minmax(unsigned& mn, unsigned& mx, SelSmem<NMAX>& S) const {
+        mn = __reduce_min_sync(0xffffffffu, mn);
+        mx = __reduce_max_sync(0xffffffffu, mx);
+        if (NT == 32) return;
+        if (lane == 0) { S.ured[0][wid] = mn; S.ured[1][wid] = mx; }
+        __syncthreads();
+        mn = 0xffffffffu;
+        mx = 0u;
+#pragma unroll
+        for (int w = 0; w < NT / 32; ++w) { mn = min(mn, S.ured[0][w]); mx = max(mx, S.ured[1][w]); }
+        __syncthreads();
+    }
 };
 
 __device__ __forceinline__ void x128_add_parts(Exact128& a, unsigned m, int e, bool neg) {
@@ -505,35 +545,36 @@ __device__ __forceinline__ void x128_add_parts(Exact128& a, unsigned m, int e, b
 }
 
 // #{keys of group g with (v < cv) or (v == cv and id < cid)} over the segment
-template <int NMAX>
-__device__ __noinline__ int sel_count(const SelSmem<NMAX>& S, int n, int g, uint32_t cv, uint32_t cid, int lane) {
+template <int NT, int NMAX>
+__device__ __noinline__ int sel_count(SelSmem<NMAX>& S, int n, int g, uint32_t cv, uint32_t cid) {
+    const Team<NT> T;
     int c = 0;
-    for (int q = lane; q < n; q += 32) {
+    for (int q = T.tid; q < n; q += NT) {
         const uint32_t v = S.kv[q];
         c += (S.grp[q] == g && (v < cv || (v == cv && S.id[q] < cid))) ? 1 : 0;
     }
-    return __reduce_add_sync(0xffffffffu, c);
+    return T.sum(c, S);
 }
 
 // boundary key of group g by bisection over the value bits (then id bits):
-// the T-th smallest (value, id); used when the histogram leaves too many
+// the Tk-th smallest (value, id); used when the histogram leaves too many
 // candidates in one bucket
-template <int NMAX>
-__device__ __noinline__ void sel_bisect(const SelSmem<NMAX>& S, int n, int g, int T, int gsz, uint32_t prefix, int hb,
-                                        int lane, uint32_t& ans, uint32_t& idb) {
+template <int NT, int NMAX>
+__device__ __noinline__ void sel_bisect(SelSmem<NMAX>& S, int n, int g, int Tk, int gsz, uint32_t prefix, int hb,
+                                        uint32_t& ans, uint32_t& idb) {
     ans = prefix;
     for (int bit = hb; bit >= 0; --bit) {
         const uint32_t cand = ans | (1u << bit);
-        if (sel_count(S, n, g, cand, 0u, lane) < T) ans = cand;
+        if (sel_count<NT>(S, n, g, cand, 0u) < Tk) ans = cand;
     }
-    const int clt = sel_count(S, n, g, ans, 0u, lane);
-    const int cle = ans == 0xffffffffu ? gsz : sel_count(S, n, g, ans + 1u, 0u, lane);
+    const int clt = sel_count<NT>(S, n, g, ans, 0u);
+    const int cle = ans == 0xffffffffu ? gsz : sel_count<NT>(S, n, g, ans + 1u, 0u);
     idb = 0xffffffffu;
-    if (cle - clt > 1 && T - clt < cle - clt) {
+    if (cle - clt > 1 && Tk - clt < cle - clt) {
         uint32_t ia = 0u;
         for (int bit = 31; bit >= 0; --bit) {
             const uint32_t cand = ia | (1u << bit);
-            if (sel_count(S, n, g, ans, cand, lane) - clt < T - clt) ia = cand;
+            if (sel_count<NT>(S, n, g, ans, cand) - clt < Tk - clt) ia = cand;
         }
         idb = ia;
     }
@@ -543,89 +584,87 @@ __device__ __noinline__ void sel_bisect(const SelSmem<NMAX>& S, int n, int g, in
 // ceil(m/2) smallest (value, id) keys) and 2g+1: a 256-bucket histogram of the
 // top 8 varying value bits per group locates the bucket of each group's
 // boundary; the few keys in that bucket are ranked exactly among themselves.
-template <int NMAX>
-__device__ __noinline__ void sel_split(SelSmem<NMAX>& S, int n, int ng, int (&gsize)[4], int lane) {
-    uint32_t vmin = 0xffffffffu, vmax = 0u;
-    for (int q = lane; q < n; q += 32) {
-        vmin = min(vmin, S.kv[q]);
-        vmax = max(vmax, S.kv[q]);
-    }
-    vmin = __reduce_min_sync(0xffffffffu, vmin);
-    vmax = __reduce_max_sync(0xffffffffu, vmax);
+template <int NT, int NMAX>
+__device__ __noinline__ void sel_split(SelSmem<NMAX>& S, int n, int ng, int (&gsize)[4], uint32_t vmin, uint32_t vmax) {
+    const Team<NT> T;
     const uint32_t diff = vmin ^ vmax;
     const int hb = diff ? 31 - __clz(diff) : -1;
     const uint32_t prefix = hb >= 0 ? (vmin & ~((2u << hb) - 1u)) : vmin;
     const int shift = hb >= 7 ? hb - 7 : 0;
-    for (int q = lane; q < ng * 256; q += 32) (&S.hist[0][0])[q] = 0;
-    __syncwarp();
-    for (int q = lane; q < n; q += 32) atomicAdd(&S.hist[S.grp[q]][(S.kv[q] - prefix) >> shift], 1);
-    __syncwarp();
-    uint32_t bvs[4], bids[4];
+    for (int q = T.tid; q < ng * 256; q += NT) (&S.hist[0][0])[q] = 0;
+    T.sync();
+    for (int q = T.tid; q < n; q += NT) atomicAdd(&S.hist[S.grp[q]][(S.kv[q] - prefix) >> shift], 1);
+    T.sync();
     int Ts[4];
     for (int g = 0; g < ng; ++g) {
-        const int T = (gsize[g] + 1) / 2;
-        Ts[g] = T;
-        // bucket where the cumulative count reaches T (8 buckets per lane)
-        int loc[8], tot = 0;
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            loc[k] = S.hist[g][8 * lane + k];
-            tot += loc[k];
-        }
-        int incl = tot;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += y;
-        }
-        const int excl = incl - tot;
-        int mybucket = -1, mybelow = 0;
-        if (excl < T && incl >= T) {
-            int run = excl;
+        const int Tk = (gsize[g] + 1) / 2;
+        Ts[g] = Tk;
+        int bucket = 0, below = 0;
+        if (T.wid == 0) {  // bucket where the cumulative count reaches Tk (8 buckets per lane)
+            const int lane = T.lane;
+            int loc[8], tot = 0;
 #pragma unroll
             for (int k = 0; k < 8; ++k) {
-                if (mybucket < 0 && run + loc[k] >= T) { mybucket = 8 * lane + k; mybelow = run; }
-                run += loc[k];
+                loc[k] = S.hist[g][8 * lane + k];
+                tot += loc[k];
             }
+            int incl = tot;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += y;
+            }
+            const int excl = incl - tot;
+            int mybucket = -1, mybelow = 0;
+            if (excl < Tk && incl >= Tk) {
+                int run = excl;
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    if (mybucket < 0 && run + loc[k] >= Tk) { mybucket = 8 * lane + k; mybelow = run; }
+                    run += loc[k];
+                }
+            }
+            const unsigned who = __ballot_sync(0xffffffffu, mybucket >= 0);
+            const int src = __ffs(who) - 1;
+            bucket = __shfl_sync(0xffffffffu, mybucket, src);
+            below = __shfl_sync(0xffffffffu, mybelow, src);
+            if (lane == 0) { S.ired[6] = bucket; S.ired[7] = below; S.ncand = 0; }
         }
-        const unsigned who = __ballot_sync(0xffffffffu, mybucket >= 0);
-        const int src = __ffs(who) - 1;
-        const int bucket = __shfl_sync(0xffffffffu, mybucket, src);
-        const int below = __shfl_sync(0xffffffffu, mybelow, src);
+        T.sync();
+        bucket = S.ired[6];
+        below = S.ired[7];
         const int kc = S.hist[g][bucket];
-        const int rank = T - below - 1;  // 0-based rank of the boundary among the bucket's keys
+        const int rank = Tk - below - 1;  // 0-based rank of the boundary among the bucket's keys
         if (kc <= 32) {
-            if (lane == 0) S.ncand = 0;
-            __syncwarp();
-            for (int q = lane; q < n; q += 32) {
+            for (int q = T.tid; q < n; q += NT) {
                 if (S.grp[q] == g && (int)((S.kv[q] - prefix) >> shift) == bucket) {
                     const int slot = atomicAdd(&S.ncand, 1);
                     S.cv[slot] = S.kv[q];
                     S.cid[slot] = S.id[q];
                 }
             }
-            __syncwarp();
-            if (lane < kc) {
-                const uint32_t v = S.cv[lane], id = S.cid[lane];
+            T.sync();
+            if (T.tid < kc) {
+                const uint32_t v = S.cv[T.tid], id = S.cid[T.tid];
                 int r = 0;
                 for (int j = 0; j < kc; ++j) {
                     const uint32_t vj = S.cv[j];
                     r += (vj < v || (vj == v && S.cid[j] < id)) ? 1 : 0;
                 }
-                if (r == rank) { S.bv = v; S.bid = id; }
+                if (r == rank) { S.bv[g] = v; S.bid[g] = id; }
             }
-            __syncwarp();
-            bvs[g] = S.bv;
-            bids[g] = S.bid;
-            __syncwarp();
+            T.sync();
         } else {
-            sel_bisect(S, n, g, T, gsize[g], prefix, hb, lane, bvs[g], bids[g]);
+            uint32_t bv, bid;
+            sel_bisect<NT>(S, n, g, Tk, gsize[g], prefix, hb, bv, bid);
+            if (T.tid == 0) { S.bv[g] = bv; S.bid[g] = bid; }
+            T.sync();
         }
     }
-    for (int q = lane; q < n; q += 32) {
+    for (int q = T.tid; q < n; q += NT) {
         const int g = S.grp[q];
-        const uint32_t v = S.kv[q], bv = bvs[g];
-        const bool low = v < bv || (v == bv && S.id[q] <= bids[g]);
+        const uint32_t v = S.kv[q], bv = S.bv[g];
+        const bool low = v < bv || (v == bv && S.id[q] <= S.bid[g]);
         S.grp[q] = (unsigned char)(2 * g + (low ? 0 : 1));
     }
     int ns[4] = {0, 0, 0, 0};
@@ -634,15 +673,17 @@ __device__ __noinline__ void sel_split(SelSmem<NMAX>& S, int n, int ng, int (&gs
         ns[2 * g + 1] = gsize[g] - Ts[g];
     }
     for (int g = 0; g < 4; ++g) gsize[g] = ns[g];
-    __syncwarp();
+    T.sync();
 }
 
-// exact moments of the segment: lanes 0..4 the means, 5..10 the central
-// second moments, 11 the psi variance
-__device__ __noinline__ void exact_moments(const MomArgs<float>& a, int e, int s0, int n, int lane, double* mean) {
+// exact moments of the segment; results of the 12 moments computed by warp 0
+// (lanes 0..4 the means, 5..10 the central second moments, 11 psi variance)
+template <int NT, int NMAX>
+__device__ __noinline__ void exact_moments(const MomArgs<float>& a, int e, int s0, int n, SelSmem<NMAX>& S) {
+    const Team<NT> T;
     Exact128 s1[5], s2[7];
     bool big = false;
-    for (int q = lane; q < n; q += 32) {
+    for (int q = T.tid; q < n; q += NT) {
         unsigned mu_, mv_, mw_, mp_, mo_;
         int eu, ev, ew, ep, eo;
         bool nu, nv, nw, np, no;
@@ -665,103 +706,110 @@ __device__ __noinline__ void exact_moments(const MomArgs<float>& a, int e, int s
         x128_add_prod(s2[5], mv_, ev, nv, mw_, ew, nw);
         x128_add_prod(s2[6], mp_, ep, np, mp_, ep, np);
     }
-    if (__any_sync(0xffffffffu, big) && lane == 0) set_status(a.status, ST_CAPACITY);
+    if (__any_sync(0xffffffffu, big) && T.lane == 0) set_status(a.status, ST_CAPACITY);
 #pragma unroll
     for (int k = 0; k < 5; ++k) x128_warp_sum(s1[k]);
 #pragma unroll
     for (int k = 0; k < 7; ++k) x128_warp_sum(s2[k]);
-    // lane 5+k needs s2[k], s1[ia[k]], s1[ib[k]]; lane k < 5 needs s1[k]
-    Exact128 mine, xa, xb;
+    if (NT > 32) {  // combine the warps' exact sums (exact, so in any order)
+        if (T.lane == 0) {
 #pragma unroll
-    for (int k = 0; k < 5; ++k) {
-        const unsigned long long lo = __shfl_sync(0xffffffffu, s1[k].lo, 0), hi = __shfl_sync(0xffffffffu, s1[k].hi, 0);
-        if (lane == k) { mine.lo = lo; mine.hi = hi; }
-        const int ia = lane == 5 || lane == 8 || lane == 9 ? 0 : (lane == 6 || lane == 10 ? 1 : (lane == 7 ? 2 : 3));
-        const int ib = lane == 5 ? 0 : (lane == 6 || lane == 8 ? 1 : (lane == 7 || lane == 9 || lane == 10 ? 2 : 3));
-        if (ia == k) { xa.lo = lo; xa.hi = hi; }
-        if (ib == k) { xb.lo = lo; xb.hi = hi; }
+            for (int k = 0; k < 5; ++k) { S.xred[T.wid][2 * k] = s1[k].lo; S.xred[T.wid][2 * k + 1] = s1[k].hi; }
+#pragma unroll
+            for (int k = 0; k < 7; ++k) { S.xred[T.wid][10 + 2 * k] = s2[k].lo; S.xred[T.wid][11 + 2 * k] = s2[k].hi; }
+        }
+        __syncthreads();
+        if (T.wid == 0 && T.lane == 0) {
+            for (int w = 1; w < NT / 32; ++w) {
+#pragma unroll
+                for (int k = 0; k < 5; ++k) x128_add(s1[k], S.xred[w][2 * k], S.xred[w][2 * k + 1], false);
+#pragma unroll
+                for (int k = 0; k < 7; ++k) x128_add(s2[k], S.xred[w][10 + 2 * k], S.xred[w][11 + 2 * k], false);
+            }
+        }
     }
+    if (T.wid == 0) {
+        const int lane = T.lane;
+        Exact128 mine, xa, xb;
 #pragma unroll
-    for (int k = 0; k < 7; ++k) {
-        const unsigned long long lo = __shfl_sync(0xffffffffu, s2[k].lo, 0), hi = __shfl_sync(0xffffffffu, s2[k].hi, 0);
-        if (lane == 5 + k) { mine.lo = lo; mine.hi = hi; }
+        for (int k = 0; k < 5; ++k) {
+            const unsigned long long lo = __shfl_sync(0xffffffffu, s1[k].lo, 0), hi = __shfl_sync(0xffffffffu, s1[k].hi, 0);
+            if (lane == k) { mine.lo = lo; mine.hi = hi; }
+            const int ia = lane == 5 || lane == 8 || lane == 9 ? 0 : (lane == 6 || lane == 10 ? 1 : (lane == 7 ? 2 : 3));
+            const int ib = lane == 5 ? 0 : (lane == 6 || lane == 8 ? 1 : (lane == 7 || lane == 9 || lane == 10 ? 2 : 3));
+            if (ia == k) { xa.lo = lo; xa.hi = hi; }
+            if (ib == k) { xb.lo = lo; xb.hi = hi; }
+        }
+#pragma unroll
+        for (int k = 0; k < 7; ++k) {
+            const unsigned long long lo = __shfl_sync(0xffffffffu, s2[k].lo, 0), hi = __shfl_sync(0xffffffffu, s2[k].hi, 0);
+            if (lane == 5 + k) { mine.lo = lo; mine.hi = hi; }
+        }
+        double val = 0.0;
+        if (lane < 5) val = x128_to_double(mine) / n;
+        else if (lane < 12) val = x128_central(mine, xa, xb, (unsigned)n);
+        if (lane < 5) { a.emean[5 * e + lane] = val; S.mean[lane] = val; }
+        else if (lane < 11) a.eR[6 * e + lane - 5] = val;
+        else if (lane == 11) a.epsivar[e] = val;
+        if (lane == 0) a.en[e] = n;
     }
-    double val = 0.0;
-    if (lane < 5) val = x128_to_double(mine) / n;
-    else if (lane < 12) val = x128_central(mine, xa, xb, (unsigned)n);
-#pragma unroll
-    for (int k = 0; k < 5; ++k) mean[k] = __shfl_sync(0xffffffffu, val, k);
-    if (lane < 5) a.emean[5 * e + lane] = val;
-    else if (lane < 11) a.eR[6 * e + lane - 5] = val;
-    else if (lane == 11) a.epsivar[e] = val;
-    if (lane == 0) a.en[e] = n;
+    T.sync();
 }
 
-__device__ __noinline__ void kahan_moments(const MomArgs<float>& a, int e, int s0, int n, int lane, double* mean) {
-    AccK m[5];
-    for (int q = lane; q < n; q += 32) {
-        m[0].add(a.u[s0 + q]); m[1].add(a.v[s0 + q]); m[2].add(a.w[s0 + q]);
-        m[3].add(a.psi[s0 + q]); m[4].add(a.om[s0 + q]);
-    }
+template <int NT, int NMAX>
+__device__ __noinline__ void kahan_moments(const MomArgs<float>& a, int e, int s0, int n, SelSmem<NMAX>& S) {
+    static_assert(NT == 32 || NT > 32, "");
+    const Team<NT> T;
+    // compensated FP32 sums; with NT > 32 warp 0 sums all particles
+    if (T.wid == 0) {
+        const int lane = T.lane;
+        AccK m[5];
+        for (int q = lane; q < n; q += 32) {
+            m[0].add(a.u[s0 + q]); m[1].add(a.v[s0 + q]); m[2].add(a.w[s0 + q]);
+            m[3].add(a.psi[s0 + q]); m[4].add(a.om[s0 + q]);
+        }
+        double mean[5];
 #pragma unroll
-    for (int q = 0; q < 5; ++q) {
-        warp_tree(m[q]);
-        mean[q] = __shfl_sync(0xffffffffu, m[q].value(), 0) / n;
-    }
-    const float mu = (float)mean[0], mv = (float)mean[1], mw = (float)mean[2], mp = (float)mean[3];
-    AccK c2[7];
-    for (int q = lane; q < n; q += 32) {
-        const float du = a.u[s0 + q] - mu, dv = a.v[s0 + q] - mv, dw = a.w[s0 + q] - mw, dp = a.psi[s0 + q] - mp;
-        c2[0].add(du * du); c2[1].add(dv * dv); c2[2].add(dw * dw);
-        c2[3].add(du * dv); c2[4].add(du * dw); c2[5].add(dv * dw); c2[6].add(dp * dp);
-    }
+        for (int q = 0; q < 5; ++q) {
+            warp_tree(m[q]);
+            mean[q] = __shfl_sync(0xffffffffu, m[q].value(), 0) / n;
+        }
+        const float mu = (float)mean[0], mv = (float)mean[1], mw = (float)mean[2], mp = (float)mean[3];
+        AccK c2[7];
+        for (int q = lane; q < n; q += 32) {
+            const float du = a.u[s0 + q] - mu, dv = a.v[s0 + q] - mv, dw = a.w[s0 + q] - mw, dp = a.psi[s0 + q] - mp;
+            c2[0].add(du * du); c2[1].add(dv * dv); c2[2].add(dw * dw);
+            c2[3].add(du * dv); c2[4].add(du * dw); c2[5].add(dv * dw); c2[6].add(dp * dp);
+        }
 #pragma unroll
-    for (int q = 0; q < 7; ++q) warp_tree(c2[q]);
-    if (lane == 0) {
-        const double inv_n = 1.0 / n;
-        a.en[e] = n;
-        for (int q = 0; q < 5; ++q) a.emean[5 * e + q] = mean[q];
-        for (int q = 0; q < 6; ++q) a.eR[6 * e + q] = c2[q].value() * inv_n;
-        a.epsivar[e] = c2[6].value() * inv_n;
-    }
-}
-
-// size classes: NMIN < n <= NMAX (n == 0 with the first class)
-template <bool KAHAN, int NMIN, int NMAX, int WPB>
-__global__ void __launch_bounds__(32 * WPB) k_moments_sel(const MomArgs<float> a, int nt) {
-    __shared__ SelSmem<NMAX> sm[WPB];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int e = blockIdx.x * WPB + w;
-    if (e >= nt) return;
-    const int s0 = a.off[e], n = a.off[e + 1] - s0;
-    if (n > NMAX || (n <= NMIN && !(NMIN == 0 && n == 0))) return;  // another size class
-    const int B = a.B;
-    SelSmem<NMAX>& S = sm[w];
-    if (n == 0) {
+        for (int q = 0; q < 7; ++q) warp_tree(c2[q]);
         if (lane == 0) {
-            a.en[e] = 0;
-            for (int q = 0; q < 5; ++q) a.emean[5 * e + q] = 0.0;
-            for (int q = 0; q < 6; ++q) a.eR[6 * e + q] = 0.0;
-            a.epsivar[e] = 0.0;
+            const double inv_n = 1.0 / n;
+            a.en[e] = n;
+            for (int q = 0; q < 5; ++q) { a.emean[5 * e + q] = mean[q]; S.mean[q] = mean[q]; }
+            for (int q = 0; q < 6; ++q) a.eR[6 * e + q] = c2[q].value() * inv_n;
+            a.epsivar[e] = c2[6].value() * inv_n;
         }
-        for (int b = lane; b < B; b += 32) {
-            a.ecm[(size_t)B * e + b] = 0.0;
-            a.ecmT[(size_t)B * e + b] = 0.f;
-        }
-        return;
     }
-    double mean[5];
-    if (KAHAN) kahan_moments(a, e, s0, n, lane, mean);
-    else exact_moments(a, e, s0, n, lane, mean);
+    T.sync();
+}
+
+// one element per team of NT threads (a warp: WPB elements per block; a block)
+template <bool KAHAN, int NT, int NMAX>
+__device__ void sel_element(const MomArgs<float>& a, int e, int s0, int n, SelSmem<NMAX>& S) {
+    const Team<NT> T;
+    const int B = a.B;
+    if (KAHAN) kahan_moments<NT>(a, e, s0, n, S);
+    else exact_moments<NT>(a, e, s0, n, S);
     if (n < B) {
-        for (int q = lane; q < n; q += 32) a.bin[s0 + q] = 0;
-        for (int b = lane; b < B; b += 32) {
-            a.ecm[(size_t)B * e + b] = mean[3];
-            a.ecmT[(size_t)B * e + b] = (float)mean[3];
+        for (int q = T.tid; q < n; q += NT) a.bin[s0 + q] = 0;
+        for (int b = T.tid; b < B; b += NT) {
+            a.ecm[(size_t)B * e + b] = S.mean[3];
+            a.ecmT[(size_t)B * e + b] = (float)S.mean[3];
         }
         return;
     }
-    for (int q = lane; q < n; q += 32) {
+    for (int q = T.tid; q < n; q += NT) {
         S.id[q] = a.id[s0 + q];
         S.grp[q] = 0;
     }
@@ -771,16 +819,23 @@ __global__ void __launch_bounds__(32 * WPB) k_moments_sel(const MomArgs<float> a
     for (int d = 0; d < 3; ++d) {
         if (G[d] == 1) continue;
         const float* comp = d == 0 ? a.u : (d == 1 ? a.v : a.w);
-        for (int q = lane; q < n; q += 32) S.kv[q] = ord32(comp[s0 + q]);
-        __syncwarp();
-        sel_split(S, n, ng, gsize, lane);
+        unsigned vmin = 0xffffffffu, vmax = 0u;
+        for (int q = T.tid; q < n; q += NT) {
+            const uint32_t k = ord32(comp[s0 + q]);
+            S.kv[q] = k;
+            vmin = min(vmin, k);
+            vmax = max(vmax, k);
+        }
+        T.minmax(vmin, vmax, S);
+        T.sync();
+        sel_split<NT>(S, n, ng, gsize, vmin, vmax);
         ng *= 2;
     }
     // bins, and <phi|V> per bin: exact fixed-point sums of psi
     constexpr int UNIT = NMAX <= 512 ? 54 : 51;  // psi <= 1 and n <= NMAX keep the sums below 2^63
-    if (lane < 8) { S.binsum[lane] = 0ull; S.bincnt[lane] = 0; }
-    __syncwarp();
-    for (int q = lane; q < n; q += 32) {
+    if (T.tid < 8) { S.binsum[T.tid] = 0ull; S.bincnt[T.tid] = 0; }
+    T.sync();
+    for (int q = T.tid; q < n; q += NT) {
         const int bn = S.grp[q];
         a.bin[s0 + q] = (unsigned char)bn;
         unsigned m;
@@ -793,12 +848,51 @@ __global__ void __launch_bounds__(32 * WPB) k_moments_sel(const MomArgs<float> a
         atomicAdd(&S.binsum[bn], v);
         atomicAdd(&S.bincnt[bn], 1);
     }
-    __syncwarp();
-    for (int b = lane; b < B; b += 32) {
+    T.sync();
+    for (int b = T.tid; b < B; b += NT) {
         const double cm = ldexp(__ull2double_rn(S.binsum[b]), -UNIT) / S.bincnt[b];
         a.ecm[(size_t)B * e + b] = cm;
         a.ecmT[(size_t)B * e + b] = (float)cm;
     }
+}
+
+__device__ void empty_element(const MomArgs<float>& a, int e, int tid, int nt_team) {
+    if (tid == 0) {
+        a.en[e] = 0;
+        for (int q = 0; q < 5; ++q) a.emean[5 * e + q] = 0.0;
+        for (int q = 0; q < 6; ++q) a.eR[6 * e + q] = 0.0;
+        a.epsivar[e] = 0.0;
+    }
+    for (int b = tid; b < a.B; b += nt_team) {
+        a.ecm[(size_t)a.B * e + b] = 0.0;
+        a.ecmT[(size_t)a.B * e + b] = 0.f;
+    }
+}
+
+// warp per element: 0 <= n <= 512
+template <bool KAHAN>
+__global__ void __launch_bounds__(32 * WARPS_PER_BLOCK) k_moments_sel(const MomArgs<float> a, int nt) {
+    __shared__ SelSmem<512> sm[WARPS_PER_BLOCK];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int e = blockIdx.x * WARPS_PER_BLOCK + w;
+    if (e >= nt) return;
+    const int s0 = a.off[e], n = a.off[e + 1] - s0;
+    if (n > 512) return;  // the block kernel takes it
+    if (n == 0) {
+        empty_element(a, e, lane, 32);
+        return;
+    }
+    sel_element<KAHAN, 32, 512>(a, e, s0, n, sm[w]);
+}
+
+// block of 256 threads per element: 512 < n <= 4096 (crowded elements)
+template <bool KAHAN>
+__global__ void __launch_bounds__(256) k_moments_sel_big(const MomArgs<float> a, int nt) {
+    __shared__ SelSmem<4096> sm;
+    const int e = blockIdx.x;
+    const int s0 = a.off[e], n = a.off[e + 1] - s0;
+    if (n <= 512 || n > 4096) return;
+    sel_element<KAHAN, 256, 4096>(a, e, s0, n, sm);
 }
 
 template <typename T, bool KAHAN>
@@ -827,8 +921,8 @@ int run(pdf_ctx* c) {
             // crowded elements (particle density drifts during a run) get their
             // own size class with a larger shared-memory slice per warp
             a.min_n = 4096;
-            k_moments_sel<KAHAN, 0, 512, WARPS_PER_BLOCK><<<blocks, 32 * WARPS_PER_BLOCK, 0, c->s>>>(a, c->m.nt);
-            k_moments_sel<KAHAN, 512, 4096, 1><<<c->m.nt, 32, 0, c->s>>>(a, c->m.nt);
+            k_moments_sel<KAHAN><<<blocks, 32 * WARPS_PER_BLOCK, 0, c->s>>>(a, c->m.nt);
+            k_moments_sel_big<KAHAN><<<c->m.nt, 256, 0, c->s>>>(a, c->m.nt);
             c->launches += 2;
         } else {
             k_moments_warp<KAHAN><<<blocks, 32 * WARPS_PER_BLOCK, 0, c->s>>>(a, c->m.nt);
