@@ -196,8 +196,41 @@ int pdf_reset_timing(pdf_ctx* c);
  * or off). */
 int64_t pdf_launch_count(const pdf_ctx* c);
 
-/* Message of the last error of c (or of the last failed pdf_init_mesh when c
- * is NULL). Never NULL. */
+/* Largest element count pdf_sort_by_element_static accepts. */
+#define PDF_SORT_STATIC_MAX_ELEMENTS 131072
+
+/* Counting sort of particle host-element indices that allocates nothing.
+ * The paper has no counterpart: this call serves callers that must not
+ * allocate device memory. It groups particles by element with the same count,
+ * scan and scatter kernels as the context's re-sort, but it takes its
+ * scratch (per-element counts and cursors and a status word, 1 MiB in all)
+ * from one fixed device array of the library instead of from a context, and it
+ * calls no cudaMalloc, cudaFree or other allocating routine.
+ *  elem[n]     device int32, host element of particle i, each in [0, nt)
+ *  n           particles, 0 <= n <= INT32_MAX
+ *  nt          elements, 1 <= nt <= PDF_SORT_STATIC_MAX_ELEMENTS
+ *  perm[n]     device int32, out: perm[k] = index i of the particle placed
+ *              at slot k; slots of one element are contiguous, in no fixed
+ *              order inside the segment
+ *  off[nt+1]   device int32, out: segment offsets (off[e] = number of
+ *              particles in elements < e, off[nt] = n)
+ *  cuda_stream cudaStream_t to run on (NULL: legacy stream)
+ * Caller owns all four arrays. The counts and the status word must start at
+ * zero: every call clears them on its stream before counting. All calls in
+ * the process share the one scratch array (one per device), so calls that
+ * overlap on the GPU (other streams, other host threads) race and give
+ * wrong results; the caller must order them. The call returns after its work
+ * has finished (it reads the status word back). Returns PDF_ERR_ARG for NULL
+ * pointers, nt < 1, n < 0 or an element index outside [0, nt),
+ * PDF_ERR_CAPACITY for nt above PDF_SORT_STATIC_MAX_ELEMENTS or n above
+ * INT32_MAX (nothing is launched), PDF_ERR_CUDA on a CUDA failure; the
+ * message is in pdf_last_error(NULL). */
+int pdf_sort_by_element_static(const int32_t* elem, int64_t n, int32_t nt, int32_t* perm, int32_t* off,
+                               void* cuda_stream);
+
+/* Message of the last error of c (or, when c is NULL, of the last failed
+ * pdf_init_mesh or pdf_sort_by_element_static of this host thread). Never
+ * NULL. */
 const char* pdf_last_error(const pdf_ctx* c);
 
 /* Free the context and its device memory (waits for the stream). NULL is a no-op. */

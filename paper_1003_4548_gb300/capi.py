@@ -53,7 +53,9 @@ EXPORTS = ("pdf_default_params", "pdf_init_mesh", "pdf_seed_particles", "pdf_set
            "pdf_estimate_stats", "pdf_step", "pdf_sync", "pdf_get_fields", "pdf_num_particles",
            "pdf_num_elements", "pdf_num_nodes", "pdf_num_bins", "pdf_step_index", "pdf_cg_iterations",
            "pdf_set_timing", "pdf_kernel_time", "pdf_reset_timing", "pdf_launch_count", "pdf_last_error",
-           "pdf_destroy")
+           "pdf_destroy", "pdf_sort_by_element_static")
+
+SORT_STATIC_MAX_ELEMENTS = 131072  # PDF_SORT_STATIC_MAX_ELEMENTS
 
 
 def library_path() -> str:
@@ -93,6 +95,7 @@ def lib(allow_build: bool = True):
         L.pdf_last_error.restype = C.c_char_p
         L.pdf_destroy.argtypes = [vp]
         L.pdf_destroy.restype = None
+        L.pdf_sort_by_element_static.argtypes = [vp, C.c_int64, C.c_int32, vp, vp, vp]
         _lib = L
         return L
 
@@ -115,6 +118,16 @@ def default_params(**over) -> pdf_params:
             v = PRECISION[v]
         setattr(p, k, v)
     return p
+
+
+def sort_by_element_static(elem_ptr: int, n: int, nt: int, perm_ptr: int, off_ptr: int, stream: int = 0):
+    """pdf_sort_by_element_static on device pointers (int32 elem[n], perm[n],
+    off[nt+1]); raises PdfError on a non-zero status."""
+    L = lib()
+    st = L.pdf_sort_by_element_static(C.c_void_p(elem_ptr), n, nt, C.c_void_p(perm_ptr), C.c_void_p(off_ptr),
+                                      C.c_void_p(stream))
+    if st != PDF_OK:
+        raise PdfError(st, L.pdf_last_error(None).decode())
 
 
 def params_dict(p: pdf_params) -> dict:

@@ -5,6 +5,8 @@
 // segment with a warp-aggregated atomic and moves its state there. The order
 // inside a segment is not fixed; every later reduction orders the segment by
 // (velocity, id) first, so results do not depend on it.
+#include <mutex>
+
 #include "pdf_internal.cuh"
 
 namespace {
@@ -93,7 +95,90 @@ void scatter(pdf_ctx* c, unsigned blocks) {
                                            c->idB, c->elemB);
 }
 
+__global__ void __launch_bounds__(256) k_scatter_perm(int64_t n, const int* __restrict__ elem, int nt, int* cursor,
+                                                      int* perm) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int e = elem[i];
+    if (e < 0 || e >= nt) e = 0;  // reported by k_count
+    const unsigned mask = __match_any_sync(__activemask(), e);
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(mask) - 1;
+    int base = 0;
+    if (lane == leader) base = atomicAdd(&cursor[e], __popc(mask));
+    base = __shfl_sync(mask, base, leader);
+    perm[base + __popc(mask & ((1u << lane) - 1u))] = (int)i;
+}
+
 }  // namespace
+
+// ---------------------------------------------------------------------------
+// allocation-free sort: scratch in a fixed device array shared by every call
+// ---------------------------------------------------------------------------
+constexpr int STATIC_SORT_WORDS = 2 * PDF_SORT_STATIC_MAX_ELEMENTS + 64;  // counts, cursors, status (1 MiB)
+static __device__ __align__(256) int g_static_sort_scratch[STATIC_SORT_WORDS];
+
+namespace {
+constexpr int STATIC_MAX_DEVICES = 64;
+std::mutex g_static_mu;
+int* g_static_ptr[STATIC_MAX_DEVICES] = {};
+
+// device address of the scratch array on the current device, looked up once
+// per device (with that device current)
+int static_scratch(int** out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return fail(nullptr, PDF_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+    if (dev < 0 || dev >= STATIC_MAX_DEVICES) return fail(nullptr, PDF_ERR_CUDA, "device ordinal out of range");
+    std::lock_guard<std::mutex> lk(g_static_mu);
+    if (!g_static_ptr[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_static_sort_scratch);
+        if (e != cudaSuccess || !p)
+            return fail(nullptr, PDF_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+        g_static_ptr[dev] = (int*)p;
+    }
+    *out = g_static_ptr[dev];
+    return PDF_OK;
+}
+}  // namespace
+
+extern "C" int pdf_sort_by_element_static(const int32_t* elem, int64_t n, int32_t nt, int32_t* perm, int32_t* off,
+                                          void* cuda_stream) {
+    if (!off || nt < 1 || n < 0 || (n > 0 && (!elem || !perm)))
+        return fail(nullptr, PDF_ERR_ARG, "pdf_sort_by_element_static: NULL array, nt < 1 or n < 0");
+    if (nt > PDF_SORT_STATIC_MAX_ELEMENTS)
+        return fail(nullptr, PDF_ERR_CAPACITY,
+                    "pdf_sort_by_element_static: nt = " + std::to_string(nt) + " exceeds the maximum of " +
+                        std::to_string(PDF_SORT_STATIC_MAX_ELEMENTS) + " elements");
+    if (n > 0x7fffffffll)
+        return fail(nullptr, PDF_ERR_CAPACITY, "pdf_sort_by_element_static: more than INT32_MAX particles");
+    int* base = nullptr;
+    const int st0 = static_scratch(&base);
+    if (st0 != PDF_OK) return st0;
+    int* cnt = base;
+    int* cursor = base + PDF_SORT_STATIC_MAX_ELEMENTS;
+    int* status = base + 2 * PDF_SORT_STATIC_MAX_ELEMENTS;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+#define STATIC_CUDA(call)                                                                              \
+    do {                                                                                               \
+        cudaError_t e_ = (call);                                                                       \
+        if (e_ != cudaSuccess) return fail(nullptr, PDF_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+    STATIC_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int) * (size_t)nt, s));
+    STATIC_CUDA(cudaMemsetAsync(status, 0, sizeof(int), s));
+    const unsigned blocks = (unsigned)((n + 255) / 256);
+    if (n > 0) k_count<<<blocks, 256, 0, s>>>(n, elem, nt, cnt, status);
+    k_scan<<<1, SCAN_THREADS, 0, s>>>(cnt, nt, off, cursor);
+    if (n > 0) k_scatter_perm<<<blocks, 256, 0, s>>>(n, elem, nt, cursor, perm);
+    STATIC_CUDA(cudaGetLastError());
+    int h = 0;
+    STATIC_CUDA(cudaMemcpyAsync(&h, status, sizeof(int), cudaMemcpyDeviceToHost, s));
+    STATIC_CUDA(cudaStreamSynchronize(s));
+#undef STATIC_CUDA
+    if (h & ST_CAPACITY) return fail(nullptr, PDF_ERR_ARG, "pdf_sort_by_element_static: element index outside [0, nt)");
+    return PDF_OK;
+}
 
 int launch_sort(pdf_ctx* c) {
     timing_begin(c, PDF_K_SORT);
