@@ -49,6 +49,22 @@ def env_rank():
             int(os.environ.get("LOCAL_RANK", 0)))
 
 
+def reduce_max(x: float, dist, device: str) -> float:
+    """Max of x over the ranks (x itself without a process group)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(world: int, particles_per_rank: int, steps: int, seconds: float) -> float:
+    """Particle-steps/s of the whole job: every rank advances its own case of
+    the same size, timed by the slowest rank."""
+    return world * particles_per_rank * steps / seconds
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -268,11 +284,8 @@ def main():
     launches = L.pdf_launch_count(g.handle) - launches0
     kt = {k: g.kernel_time(k) for k in capi.KERNEL}
     g.set_timing(False)
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * n * a.steps / (ms / 1e3)
+    ms = reduce_max(ms, dist, "cuda")
+    value = whole_job_value(world, n, a.steps, ms / 1e3)
 
     # end to end through the C ABI with host buffers: load the ensemble from
     # pinned host memory, then per step advance and read the element statistics
@@ -299,12 +312,8 @@ def main():
             g.step(dt, 1)
             g.field_into("elem_mean", out.data_ptr(), out.numel() * 8, device=False)
         g.sync(check=False)
-        te = time.perf_counter() - t0
-        if dist:
-            t = torch.tensor([te], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            te = float(t.item())
-        e2e = {"value": world * n * a.steps / te, "unit": UNIT, "h2d_bytes_per_step": h2d / a.steps,
+        te = reduce_max(time.perf_counter() - t0, dist, "cuda")
+        e2e = {"value": whole_job_value(world, n, a.steps, te), "unit": UNIT, "h2d_bytes_per_step": h2d / a.steps,
                "d2h_bytes_per_step": d2h}
 
     ts = 8 if cfg["precision"] == "fp64" else 4
