@@ -41,6 +41,8 @@ def args_():
     ap.add_argument("--cg-precision", type=int, default=0, help="elliptic CG: 0 FP64, 1 compensated FP32")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-surrogate", action="store_true", help="FE solve every step in the timed form")
+    ap.add_argument("--no-forms", action="store_true", help="skip the plain forms and the precision study")
     return ap.parse_args()
 
 
@@ -124,23 +126,29 @@ def gpu_index(local_rank: int) -> int:
     return local_rank
 
 
-def kernel_source_hash() -> str:
+KERNEL_SOURCES = {
+    "k_step": ("k_particle.cu", "pdf_internal.cuh"),
+    "k_moments_sel": ("k_stats.cu", "exact_sum.cuh", "pdf_internal.cuh"),
+}
+
+
+def kernel_source_hash(kernel: str = "k_step") -> str:
     h = hashlib.sha1()
-    for f in ("k_particle.cu", "pdf_internal.cuh"):
+    for f in KERNEL_SOURCES[kernel]:
         with open(os.path.join(ROOT, "paper_1003_4548_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:12]
 
 
-def profiled_traffic(workload: str, precision: str):
-    """DRAM bytes per particle of the particle kernel from the committed ncu
-    summary, if it was taken on the current kernel source."""
-    path = os.path.join(ROOT, "profiles", "particle_kernel_traffic.json")
+def profiled_traffic(kernel: str, workload: str, precision: str):
+    """DRAM bytes per particle of a kernel from the committed ncu summary, if
+    it was taken on the current source of that kernel."""
+    path = os.path.join(ROOT, "profiles", "kernel_traffic.json")
     try:
         with open(path) as f:
             d = json.load(f)
-        e = d[f"{workload}:{precision}"]
-        if e.get("source_hash") != kernel_source_hash():
+        e = d[f"{kernel}:{workload}:{precision}"]
+        if e.get("source_hash") != kernel_source_hash(kernel):
             return None
         return float(e["dram_bytes_per_particle"])
     except Exception:
@@ -207,7 +215,7 @@ def run_reference(a, cfg, mesh, dt):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": a.gpus,
             "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * total / a.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": config_block(cfg, mesh, r.n, "fp64"),
+            "data": "synthetic", "config": config_block(cfg, mesh, r.n, "fp64", "plain FP64 CPU oracle"),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": f"per step: {m} of {r.n} particles advanced plus m/N of one full "
                                        f"statistics estimate ({r.t_stats:.2f} s)"},
@@ -215,12 +223,164 @@ def run_reference(a, cfg, mesh, dt):
     print(json.dumps(line), flush=True)
 
 
-def config_block(cfg, mesh, n, precision):
+def config_block(cfg, mesh, n, precision, form):
     return {"workload": cfg["name"], "triangles": int(mesh["tri"].shape[0]), "nodes": int(mesh["xy"].shape[0]),
             "particles": int(n), "per_element": cfg["per_element"],
-            "wall_model": "elliptic relaxation (P1 FE, FP64 Jacobi-PCG)" if cfg["wall_model"] == "er"
-            else "wall functions", "precision": precision, "bins": list(cfg["bins"]),
+            "wall_model": "elliptic relaxation (P1 FE, FP64 block-Jacobi PCG)" if cfg["wall_model"] == "er"
+            else "wall functions", "precision": precision, "bins": list(cfg["bins"]), "form": form,
             "l2": "inputs larger than L2 (particle state > 0.7 GB)"}
+
+
+# algorithmic bytes per particle of the dominant kernel of each timed class
+def algorithmic_bytes(kclass: str, ts: int):
+    if kclass == "particle":  # k_step: read 7 state + id + elem + bin, write 7 state + elem
+        return 14 * ts + 13, "k_step (per-particle step)"
+    if kclass == "moments":   # k_moments_sel: read u v w psi omega id, write the bin
+        return 5 * ts + 5, "k_moments_sel (element moments and velocity bins)"
+    if kclass == "sort":      # k_scatter: read and write 7 state + id + elem
+        return 2 * (7 * ts + 8), "k_scatter (element re-sort)"
+    return None, None
+
+
+KTRAFFIC = {"particle": "k_step", "moments": "k_moments_sel"}
+
+
+def roofline(kclass, kt, n, ts, workload, precision):
+    bpp, name = algorithmic_bytes(kclass, ts)
+    ms, launches = kt[kclass]
+    peak, peak_kind = measured_peaks()
+    if bpp is None or not launches:
+        return {"bound": "latency", "kernel": kclass, "achieved": None, "peak": peak, "unit": "GB/s", "frac": None,
+                "traffic": None, "note": "L2-resident and latency-bound: no HBM roofline applies"}
+    achieved = bpp * n / (ms / launches / 1e3) / 1e9
+    tpp = profiled_traffic(KTRAFFIC[kclass], workload, precision) if kclass in KTRAFFIC else None
+    return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": tpp * n if tpp else None, "kernel": name, "bytes_per_particle": bpp,
+            "ms_per_launch": ms / launches,
+            "peak_source": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs), burst"
+            if peak_kind == "measured" else "fallback 6.8 TB/s"}
+
+
+def cell_stats(g, mesh, nx=12, ny=8):
+    """Particle-weighted <U>, <V>, k and <psi> over an nx x ny grid of cells
+    (element means grouped by centroid) for comparing runs."""
+    import numpy as np
+    cent = mesh["xy"][mesh["tri"]].mean(1)
+    cell = (np.clip((cent[:, 0] / mesh["L"] * nx).astype(int), 0, nx - 1) * ny +
+            np.clip((cent[:, 1] / mesh["T"] * ny).astype(int), 0, ny - 1))
+    n = g.field("elem_n").astype(float)
+    M, R = g.field("elem_mean"), g.field("elem_R")
+    out = {}
+    for name, q in (("U", M[:, 0]), ("V", M[:, 1]), ("k", 0.5 * (R[:, 0] + R[:, 1] + R[:, 2])), ("psi", M[:, 3])):
+        w = np.bincount(cell, weights=n, minlength=nx * ny)
+        out[name] = np.bincount(cell, weights=n * q, minlength=nx * ny) / np.maximum(w, 1.0)
+    return out
+
+
+def rel_rms(a, b):
+    import numpy as np
+    return float(np.sqrt(np.mean((a - b) ** 2)) / (np.sqrt(np.mean(b ** 2)) + 1e-300))
+
+
+class Form:
+    """One context of the workload in a given precision, with or without the
+    surrogate."""
+
+    def __init__(self, cfg, mesh, stream, *, precision, case_id=0, seed=None, cg_precision=0, sur=None):
+        from paper_1003_4548_gb300 import Canyon, canyon_params
+        p = canyon_params(mesh, wall_model=cfg["wall_model"], precision=precision, C0=cfg["C0"],
+                          bins=cfg["bins"], seed=cfg["seed"] if seed is None else seed, k0=cfg["k0"],
+                          case_id=case_id, cg_precision=cg_precision)
+        self.g = Canyon(p, mesh, stream=stream.cuda_stream)
+        self.g.seed_particles(cfg["per_element"])
+        self.g.estimate_stats()
+        if sur is not None:
+            self.g.set_surrogate(1, sur["params"], sur["norm"], sur["tol"])
+        self.stream = stream
+
+    def timed(self, dt, steps, warmup, dist=None, clocks=None):
+        import torch
+        from paper_1003_4548_gb300 import capi
+        g = self.g
+        for _ in range(warmup):
+            g.step(dt, 1)
+        g.sync()
+        if clocks:
+            clocks.start()
+            time.sleep(0.3)
+        g.set_timing(True)
+        g.reset_timing()
+        L = capi.lib()
+        launches0 = L.pdf_launch_count(g.handle)
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(self.stream)
+        for _ in range(steps):
+            g.step(dt, 1)
+        e1.record(self.stream)
+        st = g.sync(check=False)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        ms = e0.elapsed_time(e1)
+        ck = None
+        if clocks:
+            time.sleep(0.2)
+            ck = clocks.stop()
+        kt = {k: g.kernel_time(k) for k in capi.KERNEL}
+        g.set_timing(False)
+        return {"ms": ms, "kt": kt, "launches": L.pdf_launch_count(g.handle) - launches0, "status": st,
+                "clocks": ck, "cg_iterations_last": g.cg_iterations}
+
+    def close(self):
+        self.g.close()
+
+
+def prepare_surrogate(cfg, mesh, dt, seed=0):
+    """Harvest FE runs at W/H = 0.5 .. 2 (this workload's mesh recipe), train
+    the network with the library's kernels, and calibrate the check on a
+    held-out run of this workload: threshold = 1.5 x the largest coarse
+    residual seen there."""
+    from canyon_inputs.configs import cfl_dt
+    from canyon_inputs.mesh import canyon_mesh
+    from paper_1003_4548_gb300 import surrogate
+    t0 = time.perf_counter()
+    meshes = []
+    for i, W in enumerate((0.5, 0.75, 1.0, 1.5, 2.0)):
+        m = dict(cfg["mesh"])
+        m["W"], m["seed"] = W, 10 + i
+        meshes.append(canyon_mesh(**m))
+    X, T, counts = surrogate.harvest(meshes, steps=100, every=5, per_element=cfg["per_element"],
+                                     dt_of=lambda m: cfl_dt(m, cfl=cfg["cfl"], k0=cfg["k0"]), C0=cfg["C0"],
+                                     seed=seed + 1000)
+    t1 = time.perf_counter()
+    params, norm, hist = surrogate.train(X, T, epochs=10, batch=4096, lr=2e-3, lr_final=1e-4, seed=seed)
+    t2 = time.perf_counter()
+    res = surrogate.calibrate(params, norm, mesh, steps=100, every=5, per_element=cfg["per_element"], dt=dt,
+                              seed=seed + 99, C0=cfg["C0"])
+    tol = 1.5 * max(r[0] for r in res)
+    info = {"samples": int(X.shape[0]), "aspect_ratios": [0.5, 0.75, 1.0, 1.5, 2.0], "epochs": 10,
+            "final_loss_standardised": hist[-1][1], "harvest_s": t1 - t0, "train_s": t2 - t1,
+            "calibration_coarse_residual_max": max(r[0] for r in res), "residual_tol": tol,
+            "check": "coarse FE residual (aggregates of 128 Morton-ordered nodes) <= residual_tol"}
+    del X, T
+    return {"params": params, "norm": norm, "tol": tol}, info
+
+
+def surrogate_error(form, mesh):
+    """wp of the network against the FE solve on the same statistics, at the
+    end of a run (relative L2 over the nodes, per component)."""
+    import numpy as np
+    g = form.g
+    solves, falls, res = g.surrogate_stats()
+    g.set_surrogate(0)
+    g.estimate_stats()
+    wfe = g.field("node_wp")
+    return {"solves": solves, "fallbacks": falls, "last_residual_coarse": res[0], "last_residual_fine": res[1],
+            "wp_rel_l2_vs_fe": [round(float(x), 4) for x in
+                                np.linalg.norm(form.last_wp - wfe, axis=0) / np.linalg.norm(wfe, axis=0)]}
 
 
 def main():
@@ -238,7 +398,6 @@ def main():
 
     import numpy as np
     import torch
-    from paper_1003_4548_gb300 import Canyon, canyon_params, capi
 
     rank, world, local = env_rank()
     torch.cuda.set_device(local)
@@ -247,50 +406,34 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl")
     stream = torch.cuda.current_stream()
+    use_sur = cfg["wall_model"] == "er" and not a.no_surrogate
+    sur, sur_info = (prepare_surrogate(cfg, mesh, dt) if use_sur else (None, None))
+    prec = cfg["precision"]
+    form_name = (f"{prec} particle state, FP64 exact statistics" +
+                 (", surrogate wp with the FE solve as checked fallback" if use_sur else ", FE solve every step"))
     # each rank runs its own canyon case (independent problems, no exchange)
-    p = canyon_params(mesh, wall_model=cfg["wall_model"], precision=cfg["precision"], C0=cfg["C0"],
-                      bins=cfg["bins"], seed=cfg["seed"], k0=cfg["k0"], case_id=rank, cg_precision=a.cg_precision)
-    g = Canyon(p, mesh, stream=stream.cuda_stream)
-    g.seed_particles(cfg["per_element"])
-    g.estimate_stats()
-    g.sync()
-    n = g.num_particles
-    for _ in range(a.warmup):
-        g.step(dt, 1)
-    g.sync()
-    L = capi.lib()
-
-    clocks = Clocks(gpu_index(local))
-    clocks.start()
-    time.sleep(0.3)
-    g.set_timing(True)
-    g.reset_timing()
-    launches0 = L.pdf_launch_count(g.handle)
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(a.steps):
-        g.step(dt, 1)
-    e1.record(stream)
-    st = g.sync(check=False)
-    torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
-    ms = e0.elapsed_time(e1)
-    time.sleep(0.2)
-    ck = clocks.stop()
-    launches = L.pdf_launch_count(g.handle) - launches0
-    kt = {k: g.kernel_time(k) for k in capi.KERNEL}
-    g.set_timing(False)
-    ms = reduce_max(ms, dist, "cuda")
+    chosen = Form(cfg, mesh, stream, precision=prec, case_id=rank, cg_precision=a.cg_precision, sur=sur)
+    n = chosen.g.num_particles
+    r = chosen.timed(dt, a.steps, a.warmup, dist, Clocks(gpu_index(local)))
+    ms = reduce_max(r["ms"], dist, "cuda")
     value = whole_job_value(world, n, a.steps, ms / 1e3)
+    kt = r["kt"]
+    ts = 8 if prec == "fp64" else 4
+    dominant = max((k for k in kt if kt[k][1]), key=lambda k: kt[k][0])
+    roof = roofline(dominant, kt, n, ts, a.workload, prec)
+    rooflines = {k: roofline(k, kt, n, ts, a.workload, prec) for k in ("particle", "moments", "sort")}
+    kernels = {k: {"ms_per_step": v[0] / a.steps, "launches": v[1]} for k, v in kt.items()}
+    stated = {}
+    if use_sur:
+        chosen.last_wp = chosen.g.field("node_wp")
+        stated["surrogate"] = surrogate_error(chosen, mesh)
+        chosen.g.set_surrogate(1, sur["params"], sur["norm"], sur["tol"])
 
     # end to end through the C ABI with host buffers: load the ensemble from
     # pinned host memory, then per step advance and read the element statistics
     e2e = None
     if not a.no_e2e:
+        g = chosen.g
         P = {k: g.field(k) for k in ("x", "y", "u", "v", "w", "om", "psi", "id", "elem")}
         pin = {}
         for k, v in P.items():
@@ -315,35 +458,70 @@ def main():
         te = reduce_max(time.perf_counter() - t0, dist, "cuda")
         e2e = {"value": whole_job_value(world, n, a.steps, te), "unit": UNIT, "h2d_bytes_per_step": h2d / a.steps,
                "d2h_bytes_per_step": d2h}
+    chosen_stats = cell_stats(chosen.g, mesh) if rank == 0 else None
+    chosen_step = chosen.g.step_index
+    chosen.close()
 
-    ts = 8 if cfg["precision"] == "fp64" else 4
-    bytes_per_particle = 14 * ts + 13  # read 7 state + id + elem + bin, write 7 state + elem
-    pk_ms, pk_n = kt["particle"]
-    peak, peak_kind = measured_peaks()
-    achieved = bytes_per_particle * n / (pk_ms / pk_n / 1e3) / 1e9 if pk_n else None
-    traffic_pp = profiled_traffic(a.workload, cfg["precision"])
-    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak if achieved else None,
-            "traffic": traffic_pp * n if traffic_pp else None,
-            "kernel": "k_step (per-particle step)", "bytes_per_particle": bytes_per_particle,
-            "peak_source": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
-            else "fallback 6.8 TB/s"}
-    kernels = {k: {"ms_per_step": v[0] / a.steps, "launches": v[1]} for k, v in kt.items()}
+    # the plain forms on the same workload (fewer steps), and the stated error
+    forms = {}
+    if not a.no_forms and rank == 0:
+        k = max(10, a.steps // 5)
+        for name, fp, cgp in (("plain_fp64_fe", "fp64", 0), ("fp32_fe", "fp32", 0)):
+            f = Form(cfg, mesh, stream, precision=fp, cg_precision=cgp)
+            rr = f.timed(dt, k, 3)
+            forms[name] = {"value": f.g.num_particles * k / (rr["ms"] / 1e3), "ms_per_step": rr["ms"] / k,
+                           "steps": k, "cg_iterations_last": rr["cg_iterations_last"],
+                           "kernels_ms_per_step": {q: v[0] / k for q, v in rr["kt"].items()}}
+            f.close()
+        stated["precision_study"] = precision_study(cfg, mesh, dt, stream, sur, steps=50)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": ms / a.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32" if cfg["precision"] != "fp64" else "f64",
-            "data": "synthetic", "config": config_block(cfg, mesh, n, cfg["precision"]),
-            "roofline": roof, "e2e": e2e, "gpu_launches": int(launches), "clocks": ck,
-            "kernels": kernels, "status": capi.ERRORS.get(st, "ok") if st else "ok",
-            "cg_iterations_last": g.cg_iterations}
+            "vs_baseline": None, "dtype": "f32" if prec != "fp64" else "f64",
+            "data": "synthetic", "config": config_block(cfg, mesh, n, prec, form_name),
+            "roofline": roof, "rooflines": rooflines, "e2e": e2e, "gpu_launches": int(r["launches"]),
+            "clocks": r["clocks"], "kernels": kernels, "status": capi_status(r["status"]),
+            "cg_iterations_last": r["cg_iterations_last"], "surrogate": sur_info}
+    if forms:
+        line["forms"] = forms
+        line["speedup_vs_plain_fp64"] = value / forms["plain_fp64_fe"]["value"]
+    if stated:
+        line["stated_error"] = stated
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(cfg, mesh, dt)
     if rank == 0:
         print(json.dumps(line), flush=True)
-    g.close()
     if dist:
         dist.barrier()
         dist.destroy_process_group()
+
+
+def capi_status(st):
+    from paper_1003_4548_gb300 import capi
+    return capi.ERRORS.get(st, "ok") if st else "ok"
+
+
+def precision_study(cfg, mesh, dt, stream, sur, steps):
+    """The same seeded ensemble advanced `steps` steps in each form; statistics
+    on a 12 x 8 grid of cells compared with the all-FP64 form (relative rms),
+    next to the Monte Carlo scale (the FP64 form with another seed)."""
+    variants = (("fp64_fe", "fp64", 0, None, None), ("fp64_fe_other_seed", "fp64", 0, None, 1),
+                ("fp32_fe", "fp32", 0, None, None), ("fp32_kahan_fe", "fp32_kahan", 0, None, None),
+                ("fp32_fe_ff_cg", "fp32", 1, None, None), ("fp32_surrogate", "fp32", 0, sur, None))
+    ref, out = None, {}
+    for name, prec, cgp, s, seed in variants:
+        if s is None and name == "fp32_surrogate":
+            continue
+        f = Form(cfg, mesh, stream, precision=prec, cg_precision=cgp, sur=s, seed=seed)
+        rr = f.timed(dt, steps, 0)
+        st = cell_stats(f.g, mesh)
+        rate = f.g.num_particles * steps / (rr["ms"] / 1e3)
+        f.close()
+        if ref is None:
+            ref = st
+        out[name] = {"particle_steps_per_s": rate,
+                     "rel_rms_vs_fp64": {q: rel_rms(st[q], ref[q]) for q in st}}
+    return {"steps": steps, "cells": "12 x 8 grid, particle-weighted element means", "variants": out,
+            "note": "fp64_fe_other_seed is the Monte Carlo scale: differences below it are within sampling noise"}
 
 
 if __name__ == "__main__":

@@ -196,6 +196,109 @@ int pdf_reset_timing(pdf_ctx* c);
  * or off). */
 int64_t pdf_launch_count(const pdf_ctx* c);
 
+/* ---------------------------------------------------------------------------
+ * Learned surrogate of the elliptic-relaxation solve (Eqs. elliptic-relaxation,
+ * Gij, C0). The paper solves Eq. elliptic-relaxation by finite elements every
+ * step. This optional part maps local node quantities to wp_ij with a small
+ * MLP, checks the FE residual of that guess, and runs the FE solve (warm
+ * started from the guess) only when the residual is above a threshold.
+ *
+ * Network: 10 -> 64 -> 64 -> 64 -> 5, SiLU after the three hidden layers.
+ * Parameters are FP32, flat, in this order (row-major, out x in):
+ *   W1[64][10] b1[64] W2[64][64] b2[64] W3[64][64] b3[64] W4[5][64] b4[5]
+ * (PDF_MLP_NPARAM floats).
+ *
+ * Inputs at a node, before standardisation (features):
+ *   log d, log k, log eps, (k/eps) dU/dx, (k/eps) dU/dy, (k/eps) dV/dx,
+ *   (k/eps) dV/dy, <uu>/k, <uv>/k, <vv>/k
+ * d is the wall distance floored at 1e-6; k and eps are the floored node
+ * values; the gradients are the recovered node gradients.
+ *
+ * Outputs (targets): wp11/eps, wp12/eps, wp21/eps, wp22/eps, wp33/eps.
+ *
+ * Standardisation vector (PDF_MLP_NNORM floats):
+ *   in_mean[10] in_std[10] out_mean[5] out_std[5]
+ * The network sees (x - in_mean)/in_std and predicts (y - out_mean)/out_std.
+ * ------------------------------------------------------------------------- */
+#define PDF_MLP_IN 10
+#define PDF_MLP_HIDDEN 64
+#define PDF_MLP_OUT 5
+#define PDF_MLP_NPARAM 9349
+#define PDF_MLP_NNORM 30
+
+/* Floats of scratch that pdf_mlp_forward / pdf_mlp_loss_grad need for a batch
+ * of n samples (caller-allocated device memory). */
+int64_t pdf_mlp_work_floats(int32_t n);
+
+/* Forward pass over a batch. All arrays are device, float32, row-major:
+ *   params[PDF_MLP_NPARAM]  X[n][10] (standardised inputs)  Y[n][5] out
+ * bf16_weights = 1 rounds every parameter to bfloat16 (round to nearest
+ * even) before use, as the node inference does; 0 uses them as given.
+ * Accumulation is FP32. Enqueued on cuda_stream. */
+int pdf_mlp_forward(const float* params, const float* X, int32_t n, float* Y, float* work, int32_t bf16_weights,
+                    void* cuda_stream);
+
+/* Mean-squared-error loss L = sum((Y - T)^2) / (5 n) of the FP32 network
+ * over a batch, and its gradient with respect to every parameter (device
+ * grad[PDF_MLP_NPARAM], same layout as params; device loss[1]). Own
+ * forward and backward kernels; deterministic (no atomics). */
+int pdf_mlp_loss_grad(const float* params, const float* X, const float* T, int32_t n, float* work, float* grad,
+                      float* loss, void* cuda_stream);
+
+/* One Adam step (Kingma & Ba 2015) on device params/m/v with gradient grad:
+ *   m = b1 m + (1 - b1) g;  v = b2 v + (1 - b2) g^2;
+ *   params -= lr (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps)
+ * where t >= 1 is the step number. */
+int pdf_mlp_adam(float* params, const float* grad, float* m, float* v, int32_t t, float lr, float beta1,
+                 float beta2, float eps, void* cuda_stream);
+
+/* Column means and standard deviations (divisor n) of a device float matrix
+ * X[n][d], into device mean[d], std[d] (std floored at 1e-12). The sums run
+ * in FP64 in a fixed order. */
+int pdf_mlp_column_stats(const float* X, int64_t n, int32_t d, float* mean, float* std, void* cuda_stream);
+
+/* dst[r][j] = src[idx[r]][j] for r < n, j < d (device arrays; idx values must
+ * be valid rows of src: the caller owns that check). Used to draw training
+ * mini-batches. */
+int pdf_mlp_gather_rows(const float* src, const int32_t* idx, int32_t n, int32_t d, float* dst, void* cuda_stream);
+
+/* In place: X[i][j] = (X[i][j] - mean[j]) / std[j] (device arrays). */
+int pdf_mlp_standardize(float* X, int64_t n, int32_t d, const float* mean, const float* std, void* cuda_stream);
+
+/* Number of rows pdf_surrogate_harvest writes: free canonical nodes of an
+ * elliptic-relaxation context (periodic partners counted once, Dirichlet
+ * wall nodes excluded). */
+int32_t pdf_surrogate_rows(const pdf_ctx* c);
+
+/* Training samples from the context's current statistics and wp solution:
+ * features (above, not standardised) into device X[rows][10] and targets
+ * wp/eps into device T[rows][5], rows = pdf_surrogate_rows(c). Call after
+ * pdf_estimate_stats or pdf_step with the FE solve active. Enqueued on the
+ * context stream. */
+int pdf_surrogate_harvest(pdf_ctx* c, float* X, float* T);
+
+/* Install (mode 1, 2) or remove (mode 0) the surrogate. Host arrays are copied.
+ *  mode 0  FE solve every step (the paper's method)
+ *  mode 1  the network at the nodes proposes wp; its FE residual
+ *          r = M f - (M + K_{L^2}) wp is checked on the device in a coarse
+ *          norm: r and the effective right-hand side b0 = M f - A_wall g
+ *          are summed over aggregates of 128 consecutive (Morton-ordered)
+ *          nodes, and the check is max over the five components of
+ *          |sum_agg r| / |sum_agg b0| <= residual_tol. The aggregates average
+ *          out the node-to-node noise of the estimated statistics, which the
+ *          fine residual amplifies by (L/h)^2. Otherwise the FE solve runs to
+ *          cg_tol from the previous solution.
+ *  mode 2  the network's wp is used without the check (for measurement)
+ * Weights are rounded to bfloat16; inference accumulates in FP32. Requires
+ * an elliptic-relaxation context (else PDF_ERR_ARG). */
+int pdf_set_surrogate(pdf_ctx* c, int32_t mode, const float* params, const float* norm, double residual_tol);
+
+/* Surrogate counters since the last pdf_set_surrogate: solves, FE fallbacks
+ * taken, and the last checked relative residuals residual[0] (coarse: the
+ * check) and residual[1] (fine, node-wise). Synchronises the context
+ * stream. */
+int pdf_surrogate_stats(pdf_ctx* c, int64_t* solves, int64_t* fallbacks, double residual[2]);
+
 /* Largest element count pdf_sort_by_element_static accepts. */
 #define PDF_SORT_STATIC_MAX_ELEMENTS 131072
 

@@ -53,7 +53,12 @@ EXPORTS = ("pdf_default_params", "pdf_init_mesh", "pdf_seed_particles", "pdf_set
            "pdf_estimate_stats", "pdf_step", "pdf_sync", "pdf_get_fields", "pdf_num_particles",
            "pdf_num_elements", "pdf_num_nodes", "pdf_num_bins", "pdf_step_index", "pdf_cg_iterations",
            "pdf_set_timing", "pdf_kernel_time", "pdf_reset_timing", "pdf_launch_count", "pdf_last_error",
-           "pdf_destroy", "pdf_sort_by_element_static")
+           "pdf_destroy", "pdf_sort_by_element_static", "pdf_mlp_work_floats", "pdf_mlp_forward",
+           "pdf_mlp_loss_grad", "pdf_mlp_adam", "pdf_mlp_column_stats", "pdf_mlp_gather_rows",
+           "pdf_mlp_standardize", "pdf_surrogate_rows", "pdf_surrogate_harvest", "pdf_set_surrogate",
+           "pdf_surrogate_stats")
+
+MLP_IN, MLP_HIDDEN, MLP_OUT, MLP_NPARAM, MLP_NNORM = 10, 64, 5, 9349, 30
 
 SORT_STATIC_MAX_ELEMENTS = 131072  # PDF_SORT_STATIC_MAX_ELEMENTS
 
@@ -96,6 +101,19 @@ def lib(allow_build: bool = True):
         L.pdf_destroy.argtypes = [vp]
         L.pdf_destroy.restype = None
         L.pdf_sort_by_element_static.argtypes = [vp, C.c_int64, C.c_int32, vp, vp, vp]
+        L.pdf_mlp_work_floats.argtypes = [C.c_int32]
+        L.pdf_mlp_work_floats.restype = C.c_int64
+        L.pdf_mlp_forward.argtypes = [vp, vp, C.c_int32, vp, vp, C.c_int32, vp]
+        L.pdf_mlp_loss_grad.argtypes = [vp, vp, vp, C.c_int32, vp, vp, vp, vp]
+        L.pdf_mlp_adam.argtypes = [vp, vp, vp, vp, C.c_int32, C.c_float, C.c_float, C.c_float, C.c_float, vp]
+        L.pdf_mlp_column_stats.argtypes = [vp, C.c_int64, C.c_int32, vp, vp, vp]
+        L.pdf_mlp_gather_rows.argtypes = [vp, vp, C.c_int32, C.c_int32, vp, vp]
+        L.pdf_mlp_standardize.argtypes = [vp, C.c_int64, C.c_int32, vp, vp, vp]
+        L.pdf_surrogate_rows.argtypes = [vp]
+        L.pdf_surrogate_rows.restype = C.c_int32
+        L.pdf_surrogate_harvest.argtypes = [vp, vp, vp]
+        L.pdf_set_surrogate.argtypes = [vp, C.c_int32, P(C.c_float), P(C.c_float), C.c_double]
+        L.pdf_surrogate_stats.argtypes = [vp, P(C.c_int64), P(C.c_int64), d]
         _lib = L
         return L
 
@@ -128,6 +146,47 @@ def sort_by_element_static(elem_ptr: int, n: int, nt: int, perm_ptr: int, off_pt
                                       C.c_void_p(stream))
     if st != PDF_OK:
         raise PdfError(st, L.pdf_last_error(None).decode())
+
+
+def _chk(st, what):
+    if st != PDF_OK:
+        raise PdfError(st, f"{what}: " + lib().pdf_last_error(None).decode())
+
+
+def _vp(x):
+    return C.c_void_p(int(x))
+
+
+def mlp_work_floats(n: int) -> int:
+    return int(lib().pdf_mlp_work_floats(n))
+
+
+def mlp_forward(params, X, n, Y, work, bf16_weights=False, stream=0):
+    """pdf_mlp_forward on device pointers."""
+    _chk(lib().pdf_mlp_forward(_vp(params), _vp(X), n, _vp(Y), _vp(work), 1 if bf16_weights else 0, _vp(stream)),
+         "pdf_mlp_forward")
+
+
+def mlp_loss_grad(params, X, T, n, work, grad, loss, stream=0):
+    _chk(lib().pdf_mlp_loss_grad(_vp(params), _vp(X), _vp(T), n, _vp(work), _vp(grad), _vp(loss), _vp(stream)),
+         "pdf_mlp_loss_grad")
+
+
+def mlp_adam(params, grad, m, v, t, lr, beta1=0.9, beta2=0.999, eps=1e-8, stream=0):
+    _chk(lib().pdf_mlp_adam(_vp(params), _vp(grad), _vp(m), _vp(v), t, lr, beta1, beta2, eps, _vp(stream)),
+         "pdf_mlp_adam")
+
+
+def mlp_column_stats(X, n, d, mean, std, stream=0):
+    _chk(lib().pdf_mlp_column_stats(_vp(X), n, d, _vp(mean), _vp(std), _vp(stream)), "pdf_mlp_column_stats")
+
+
+def mlp_gather_rows(src, idx, n, d, dst, stream=0):
+    _chk(lib().pdf_mlp_gather_rows(_vp(src), _vp(idx), n, d, _vp(dst), _vp(stream)), "pdf_mlp_gather_rows")
+
+
+def mlp_standardize(X, n, d, mean, std, stream=0):
+    _chk(lib().pdf_mlp_standardize(_vp(X), n, d, _vp(mean), _vp(std), _vp(stream)), "pdf_mlp_standardize")
 
 
 def params_dict(p: pdf_params) -> dict:
@@ -231,6 +290,32 @@ class Canyon:
 
     def particles(self) -> dict:
         return {k: self.field(k) for k in ("x", "y", "u", "v", "w", "om", "psi", "id", "elem", "bin")}
+
+    # -- learned surrogate of the elliptic solve ------------------------------
+    def surrogate_rows(self) -> int:
+        r = lib().pdf_surrogate_rows(self._h)
+        if r < 0:
+            raise PdfError(-1, lib().pdf_last_error(self._h).decode())
+        return r
+
+    def surrogate_harvest(self, X_ptr: int, T_ptr: int):
+        self._check(lib().pdf_surrogate_harvest(self._h, _vp(X_ptr), _vp(T_ptr)))
+
+    def set_surrogate(self, mode: int, params=None, norm=None, residual_tol: float = 0.0):
+        if mode == 0:
+            self._check(lib().pdf_set_surrogate(self._h, 0, None, None, 0.0))
+            return
+        p = np.ascontiguousarray(params, np.float32)
+        q = np.ascontiguousarray(norm, np.float32)
+        assert p.size == MLP_NPARAM and q.size == MLP_NNORM
+        self._check(lib().pdf_set_surrogate(self._h, mode, _ptr(p, C.c_float), _ptr(q, C.c_float),
+                                            float(residual_tol)))
+
+    def surrogate_stats(self):
+        """(solves, fallbacks, (coarse residual, fine residual)) of the last check."""
+        a, b, r = C.c_int64(), C.c_int64(), (C.c_double * 2)()
+        self._check(lib().pdf_surrogate_stats(self._h, C.byref(a), C.byref(b), r))
+        return a.value, b.value, (r[0], r[1])
 
     def set_timing(self, on: bool):
         self._check(lib().pdf_set_timing(self._h, 1 if on else 0))

@@ -350,11 +350,8 @@ int alloc_stats(pdf_ctx* c) {
         const size_t v = 5 * (size_t)nn;
         TRY(dalloc(c, &c->fe_f, v));
         TRY(dalloc(c, &c->fe_g, v));
-        TRY(dalloc(c, &c->fe_b, v));
-        TRY(dalloc(c, &c->fe_r, v));
+        TRY(dalloc(c, &c->fe_prop, v));
         TRY(dalloc(c, &c->fe_z, v));
-        TRY(dalloc(c, &c->fe_p, v));
-        TRY(dalloc(c, &c->fe_ap, v));
         PDF_CUDA(c, cudaMemset(c->fe_g, 0, sizeof(double) * v));
         TRY(dalloc(c, &c->fe_part, (size_t)15 * 4096));
         TRY(dalloc(c, &c->fe_bar, 32 * 64));  // barrier lines: top/generation + 63 groups of 16 blocks
@@ -664,8 +661,8 @@ void pdf_destroy(pdf_ctx* c) {
                    m.aval, m.avf, m.diag, c->idA, c->idB, c->elemA, c->elemB, c->bin, c->cnt, c->off, c->cursor, c->en,
                    c->emean, c->eR, c->epsivar, c->ecm, c->nwt, c->nmean, c->nR, c->nke, c->npsivar, c->eder,
                    c->ngrad, c->npack, c->nwp, c->npackT, c->epackT, c->ecmT, c->sort_scratch, c->fe_f, c->fe_g,
-                   c->fe_b, c->fe_r, c->fe_z, c->fe_p, c->fe_ap, c->fe_part, c->fe_bar, c->fe_iters, c->d_status,
-                   c->conv_buf};
+                   c->fe_prop, c->fe_z, c->fe_part, c->fe_bar, c->fe_iters, c->d_status,
+                   c->conv_buf, c->sur_w, c->sur_rows, c->sur_skip, c->sur_cnt, c->sur_part};
     for (void* p : dev) cudaFree(p);
     for (int k = 0; k < 7; ++k) {
         cudaFree(c->stA[k]);

@@ -85,9 +85,21 @@ struct CGArgs {
     unsigned* bar;
     int* iters;
     int* status;
+    const int* skip;       // surrogate: 1 = the network's wp passed the residual check, no solve
+    const double* xprop;   // surrogate proposal (network at the free rows, Dirichlet values at the walls)
     double tol;
     int maxit;
 };
+
+// the surrogate's check passed: take its proposal as the solution
+__device__ __forceinline__ bool skip_solve(const CGArgs& a) {
+    if (a.skip == nullptr || *(volatile const int*)a.skip == 0) return false;
+    const int nc = blockDim.x / NC;  // rows per block
+    const int c = threadIdx.x / nc, i = blockIdx.x * nc + threadIdx.x % nc;
+    if (i < a.nn && a.rep[i] == i) a.x[NC * (size_t)i + c] = a.xprop[NC * (size_t)i + c];
+    if (blockIdx.x == 0 && threadIdx.x == 0) *a.iters = 0;
+    return true;
+}
 
 constexpr int PART_W = 4 * NC;  // partial sums per block: 3 NC in phase A, NC in phase B
 
@@ -209,6 +221,7 @@ __device__ __forceinline__ double block_precondition(const float* __restrict__ i
 // each iteration has one SpMV (on z) and two grid reductions.
 template <int BS>
 __global__ void __launch_bounds__(BS * NC) k_pcg(const CGArgs a) {
+    if (skip_solve(a)) return;
     extern __shared__ float smem[];
     float* inv = smem;                                           // column j at inv[j*(BS+4) ..]
     float* rv = smem + BS * (BS + 4);                            // NC*BS
@@ -413,6 +426,7 @@ __device__ void grid_sum_ff(const CGArgs& a, int slot, int nvals, double* out) {
 
 template <int BS>
 __global__ void __launch_bounds__(BS * NC) k_pcg_ff(const CGArgs a) {
+    if (skip_solve(a)) return;
     extern __shared__ float smem[];
     float* inv = smem;
     float* rv = smem + BS * (BS + 4);
@@ -643,6 +657,10 @@ int launch_elliptic(pdf_ctx* c) {
     k_fe_rhs<<<(nn + 127) / 128, 128, 0, c->s>>>(nn, c->nR, c->ngrad, c->nke, c->nmean, c->m.is_wall, c->m.wn,
                                                 c->p, c->fe_f, c->fe_g);
     PDF_CUDA(c, cudaGetLastError());
+    if (c->sur_mode) {
+        const int st = launch_surrogate(c);
+        if (st != PDF_OK) return st;
+    }
     if (c->fe_blocks == 0) {
         // the largest diagonal-block size (fewer blocks and partial sums, a
         // stronger block-Jacobi preconditioner) whose grid is co-resident
@@ -667,6 +685,8 @@ int launch_elliptic(pdf_ctx* c) {
     a.zg = c->fe_z;
     a.part = c->fe_part; a.bar = c->fe_bar; a.iters = c->fe_iters; a.status = c->d_status;
     a.tol = c->p.cg_tol; a.maxit = c->p.cg_maxit;
+    a.skip = c->sur_mode ? c->sur_skip : nullptr;
+    a.xprop = c->fe_prop;
     cudaError_t err;
     const bool ffv = c->p.cg_precision == 1;
     if (c->fe_bs == 128) err = launch_pcg<128>(a, c->fe_blocks, c->s, ffv);

@@ -1,0 +1,670 @@
+// k_mlp.cu -- learned surrogate of the elliptic-relaxation solve.
+//
+// The paper solves Eq. elliptic-relaxation for wp_ij by finite elements every
+// step; wp_ij then gives the GLM drift G_ij and C0 eps (Eqs. Gij, C0). Here
+// a 10 -> 64 -> 64 -> 64 -> 5 SiLU network maps local node quantities (wall
+// distance, k, eps, the mean velocity gradient and the in-plane Reynolds
+// stresses) to wp_ij / eps. This file holds:
+//  * training: a tiled FP32 GEMM and the element-wise kernels of the forward
+//    pass, the backward pass of the mean-squared error, and Adam;
+//  * harvesting of (features, targets) at the free canonical nodes;
+//  * node inference with bfloat16-rounded weights and FP32 accumulation, the
+//    FE residual of its wp, and the device-side decision whether the CG runs.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cmath>
+
+#include "pdf_internal.cuh"
+
+namespace {
+
+constexpr int IN = PDF_MLP_IN, H = PDF_MLP_HIDDEN, OUT = PDF_MLP_OUT;
+constexpr int OFF_W1 = 0, OFF_B1 = OFF_W1 + H * IN, OFF_W2 = OFF_B1 + H, OFF_B2 = OFF_W2 + H * H;
+constexpr int OFF_W3 = OFF_B2 + H, OFF_B3 = OFF_W3 + H * H, OFF_W4 = OFF_B3 + H, OFF_B4 = OFF_W4 + OUT * H;
+static_assert(OFF_B4 + OUT == PDF_MLP_NPARAM, "parameter layout");
+constexpr int NC = 5;
+constexpr int LOSS_BLOCKS = 1024;
+
+__device__ __forceinline__ float sigm(float z) { return 1.f / (1.f + expf(-z)); }
+__device__ __forceinline__ float silu(float z) { return z * sigm(z); }
+__device__ __forceinline__ float silu_grad(float z) {
+    const float s = sigm(z);
+    return s * (1.f + z * (1.f - s));
+}
+
+// C[M][N] = op(A)[M][K] op(B)[K][N], row-major, FP32. op(A)(m, k) is
+// A[m*lda + k] (or A[k*lda + m] with TA); op(B)(k, n) is B[k*ldb + n] (or
+// B[n*ldb + k] with TB). 32x32 output tile per 256-thread block.
+template <bool TA, bool TB>
+__global__ void __launch_bounds__(256) k_sgemm(int M, int N, int K, const float* __restrict__ A, int lda,
+                                               const float* __restrict__ B, int ldb, float* C, int ldc) {
+    __shared__ float As[32][33], Bs[32][33];
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const int m0 = blockIdx.y * 32, n0 = blockIdx.x * 32;
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int k0 = 0; k0 < K; k0 += 32) {
+        for (int r = ty; r < 32; r += 8) {
+            const int m = m0 + r, k = k0 + tx;
+            As[r][tx] = (m < M && k < K) ? (TA ? A[(size_t)k * lda + m] : A[(size_t)m * lda + k]) : 0.f;
+            const int kk = k0 + r, n = n0 + tx;
+            Bs[r][tx] = (kk < K && n < N) ? (TB ? B[(size_t)n * ldb + kk] : B[(size_t)kk * ldb + n]) : 0.f;
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int kk = 0; kk < 32; ++kk) {
+            const float b = Bs[kk][tx];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[j] = fmaf(As[ty + 8 * j][kk], b, acc[j]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int m = m0 + ty + 8 * j, n = n0 + tx;
+        if (m < M && n < N) C[(size_t)m * ldc + n] = acc[j];
+    }
+}
+
+// Z[r][o] += b[o]; A = SiLU(Z) (act) or A = Z
+__global__ void k_bias_act(float* Z, float* A, int64_t n, int d, const float* __restrict__ b, int act) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n * d) return;
+    const float z = Z[i] + b[i % d];
+    Z[i] = z;
+    if (A) A[i] = act ? silu(z) : z;
+}
+
+// dZ = dA * SiLU'(Z)
+__global__ void k_silu_bwd(const float* __restrict__ dA, const float* __restrict__ Z, float* dZ, int64_t count) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < count) dZ[i] = dA[i] * silu_grad(Z[i]);
+}
+
+// db[col] = sum over rows of dZ[row][col] (block per column, fixed order)
+__global__ void __launch_bounds__(256) k_colsum(const float* __restrict__ dZ, int64_t n, int d, float* db) {
+    __shared__ float red[256];
+    const int col = blockIdx.x;
+    float s = 0.f;
+    for (int64_t r = threadIdx.x; r < n; r += 256) s += dZ[r * d + col];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) db[col] = red[0];
+}
+
+// dY = 2 (Y - T) / (5 n); per-block partial sums of (Y - T)^2
+__global__ void __launch_bounds__(256) k_mse(const float* __restrict__ Y, const float* __restrict__ T, int64_t count,
+                                             float scale, float* dY, float* part) {
+    __shared__ float red[256];
+    float s = 0.f;
+    for (int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x; i < count; i += (int64_t)gridDim.x * 256) {
+        const float e = Y[i] - T[i];
+        dY[i] = 2.f * e * scale;
+        s += e * e;
+    }
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = red[0];
+}
+
+__global__ void k_loss_final(const float* __restrict__ part, int nb, float scale, float* loss) {
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int b = 0; b < nb; ++b) s += part[b];
+        *loss = (float)(s * scale);
+    }
+}
+
+__global__ void k_adam(float* p, const float* __restrict__ g, float* m, float* v, int count, float lr, float b1,
+                       float b2, float eps, float c1, float c2) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.f - b1) * gi;
+    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+}
+
+__global__ void k_bf16_round(const float* __restrict__ src, float* dst, int count) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < count) dst[i] = __bfloat162float(__float2bfloat16_rn(src[i]));
+}
+
+// column mean and standard deviation, FP64 sums in a fixed order
+__global__ void __launch_bounds__(256) k_colstats(const float* __restrict__ X, int64_t n, int d, float* mean,
+                                                  float* sd) {
+    __shared__ double red[256];
+    __shared__ double mu;
+    const int col = blockIdx.x;
+    double s = 0.0;
+    for (int64_t r = threadIdx.x; r < n; r += 256) s += X[r * d + col];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) mu = n > 0 ? red[0] / (double)n : 0.0;
+    __syncthreads();
+    const double m = mu;
+    s = 0.0;
+    for (int64_t r = threadIdx.x; r < n; r += 256) {
+        const double e = X[r * d + col] - m;
+        s += e * e;
+    }
+    __syncthreads();
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const double sdev = n > 0 ? sqrt(red[0] / (double)n) : 0.0;
+        mean[col] = (float)m;
+        sd[col] = (float)(sdev > 1e-12 ? sdev : 1e-12);
+    }
+}
+
+__global__ void k_gather_rows(const float* __restrict__ src, const int* __restrict__ idx, int n, int d, float* dst) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (int64_t)n * d) return;
+    const int r = (int)(i / d), j = (int)(i % d);
+    dst[i] = src[(size_t)idx[r] * d + j];
+}
+
+__global__ void k_standardize(float* X, int64_t n, int d, const float* __restrict__ mean,
+                              const float* __restrict__ sd) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n * d) return;
+    const int j = (int)(i % d);
+    X[i] = (X[i] - mean[j]) / sd[j];
+}
+
+unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+template <bool TA, bool TB>
+void gemm(int M, int N, int K, const float* A, int lda, const float* B, int ldb, float* C, int ldc, cudaStream_t s) {
+    dim3 grid((N + 31) / 32, (M + 31) / 32);
+    k_sgemm<TA, TB><<<grid, 256, 0, s>>>(M, N, K, A, lda, B, ldb, C, ldc);
+}
+
+struct Work {
+    float *Z1, *A1, *Z2, *A2, *Z3, *A3, *Y, *dY, *dA, *dZ, *wq, *lpart;
+    Work(float* w, int64_t n) {
+        Z1 = w; A1 = Z1 + H * n; Z2 = A1 + H * n; A2 = Z2 + H * n; Z3 = A2 + H * n; A3 = Z3 + H * n;
+        Y = A3 + H * n; dY = Y + OUT * n; dA = dY + OUT * n; dZ = dA + H * n;
+        wq = dZ + H * n; lpart = wq + PDF_MLP_NPARAM + 3;
+    }
+};
+
+void forward(const float* P, const float* X, int n, Work& w, float* Y, cudaStream_t s) {
+    const unsigned bh = blocks_for((int64_t)n * H, 256);
+    gemm<false, true>(n, H, IN, X, IN, P + OFF_W1, IN, w.Z1, H, s);
+    k_bias_act<<<bh, 256, 0, s>>>(w.Z1, w.A1, n, H, P + OFF_B1, 1);
+    gemm<false, true>(n, H, H, w.A1, H, P + OFF_W2, H, w.Z2, H, s);
+    k_bias_act<<<bh, 256, 0, s>>>(w.Z2, w.A2, n, H, P + OFF_B2, 1);
+    gemm<false, true>(n, H, H, w.A2, H, P + OFF_W3, H, w.Z3, H, s);
+    k_bias_act<<<bh, 256, 0, s>>>(w.Z3, w.A3, n, H, P + OFF_B3, 1);
+    gemm<false, true>(n, OUT, H, w.A3, H, P + OFF_W4, H, Y, OUT, s);
+    k_bias_act<<<blocks_for((int64_t)n * OUT, 256), 256, 0, s>>>(Y, nullptr, n, OUT, P + OFF_B4, 0);
+}
+
+}  // namespace
+
+extern "C" {
+
+int64_t pdf_mlp_work_floats(int32_t n) {
+    if (n < 0) return -1;
+    return (int64_t)(6 * H + 2 * OUT + 2 * H) * n + PDF_MLP_NPARAM + 3 + LOSS_BLOCKS + 64;
+}
+
+int pdf_mlp_forward(const float* params, const float* X, int32_t n, float* Y, float* work, int32_t bf16_weights,
+                    void* cuda_stream) {
+    if (!params || !work || n < 0 || (n > 0 && (!X || !Y)))
+        return fail(nullptr, PDF_ERR_ARG, "pdf_mlp_forward: NULL array or n < 0");
+    if (n == 0) return PDF_OK;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    Work w(work, n);
+    const float* P = params;
+    if (bf16_weights) {
+        k_bf16_round<<<blocks_for(PDF_MLP_NPARAM, 256), 256, 0, s>>>(params, w.wq, PDF_MLP_NPARAM);
+        P = w.wq;
+    }
+    forward(P, X, n, w, Y, s);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(nullptr, PDF_ERR_CUDA, std::string("pdf_mlp_forward: ") + cudaGetErrorString(e));
+    return PDF_OK;
+}
+
+int pdf_mlp_loss_grad(const float* params, const float* X, const float* T, int32_t n, float* work, float* grad,
+                      float* loss, void* cuda_stream) {
+    if (!params || !work || !grad || !loss || n < 1 || !X || !T)
+        return fail(nullptr, PDF_ERR_ARG, "pdf_mlp_loss_grad: NULL array or n < 1");
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    Work w(work, n);
+    const float* P = params;
+    forward(P, X, n, w, w.Y, s);
+    const int64_t ny = (int64_t)n * OUT;
+    const int nb = (int)std::min<int64_t>(LOSS_BLOCKS, (ny + 255) / 256);
+    const float scale = 1.f / (float)ny;
+    k_mse<<<nb, 256, 0, s>>>(w.Y, T, ny, scale, w.dY, w.lpart);
+    k_loss_final<<<1, 32, 0, s>>>(w.lpart, nb, (float)(1.0 / (double)ny), loss);
+    // layer 4: dW4 = dY^T A3, db4 = colsum dY, dA3 = dY W4
+    gemm<true, false>(OUT, H, n, w.dY, OUT, w.A3, H, grad + OFF_W4, H, s);
+    k_colsum<<<OUT, 256, 0, s>>>(w.dY, n, OUT, grad + OFF_B4);
+    gemm<false, false>(n, H, OUT, w.dY, OUT, P + OFF_W4, H, w.dA, H, s);
+    const unsigned bh = blocks_for((int64_t)n * H, 256);
+    // layer 3
+    k_silu_bwd<<<bh, 256, 0, s>>>(w.dA, w.Z3, w.dZ, (int64_t)n * H);
+    gemm<true, false>(H, H, n, w.dZ, H, w.A2, H, grad + OFF_W3, H, s);
+    k_colsum<<<H, 256, 0, s>>>(w.dZ, n, H, grad + OFF_B3);
+    gemm<false, false>(n, H, H, w.dZ, H, P + OFF_W3, H, w.dA, H, s);
+    // layer 2
+    k_silu_bwd<<<bh, 256, 0, s>>>(w.dA, w.Z2, w.dZ, (int64_t)n * H);
+    gemm<true, false>(H, H, n, w.dZ, H, w.A1, H, grad + OFF_W2, H, s);
+    k_colsum<<<H, 256, 0, s>>>(w.dZ, n, H, grad + OFF_B2);
+    gemm<false, false>(n, H, H, w.dZ, H, P + OFF_W2, H, w.dA, H, s);
+    // layer 1
+    k_silu_bwd<<<bh, 256, 0, s>>>(w.dA, w.Z1, w.dZ, (int64_t)n * H);
+    gemm<true, false>(H, IN, n, w.dZ, H, X, IN, grad + OFF_W1, IN, s);
+    k_colsum<<<H, 256, 0, s>>>(w.dZ, n, H, grad + OFF_B1);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(nullptr, PDF_ERR_CUDA, std::string("pdf_mlp_loss_grad: ") + cudaGetErrorString(e));
+    return PDF_OK;
+}
+
+int pdf_mlp_adam(float* params, const float* grad, float* m, float* v, int32_t t, float lr, float beta1,
+                 float beta2, float eps, void* cuda_stream) {
+    if (!params || !grad || !m || !v || t < 1) return fail(nullptr, PDF_ERR_ARG, "pdf_mlp_adam: bad argument");
+    const float c1 = 1.f - powf(beta1, (float)t), c2 = 1.f - powf(beta2, (float)t);
+    k_adam<<<blocks_for(PDF_MLP_NPARAM, 256), 256, 0, (cudaStream_t)cuda_stream>>>(
+        params, grad, m, v, PDF_MLP_NPARAM, lr, beta1, beta2, eps, c1, c2);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(nullptr, PDF_ERR_CUDA, std::string("pdf_mlp_adam: ") + cudaGetErrorString(e));
+    return PDF_OK;
+}
+
+int pdf_mlp_column_stats(const float* X, int64_t n, int32_t d, float* mean, float* std, void* cuda_stream) {
+    if (!X || !mean || !std || n < 1 || d < 1) return fail(nullptr, PDF_ERR_ARG, "pdf_mlp_column_stats: bad argument");
+    k_colstats<<<d, 256, 0, (cudaStream_t)cuda_stream>>>(X, n, d, mean, std);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(nullptr, PDF_ERR_CUDA, std::string("pdf_mlp_column_stats: ") + cudaGetErrorString(e));
+    return PDF_OK;
+}
+
+int pdf_mlp_gather_rows(const float* src, const int32_t* idx, int32_t n, int32_t d, float* dst, void* cuda_stream) {
+    if (!src || !idx || !dst || n < 0 || d < 1) return fail(nullptr, PDF_ERR_ARG, "pdf_mlp_gather_rows: bad argument");
+    if (n == 0) return PDF_OK;
+    k_gather_rows<<<blocks_for((int64_t)n * d, 256), 256, 0, (cudaStream_t)cuda_stream>>>(src, idx, n, d, dst);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(nullptr, PDF_ERR_CUDA, std::string("pdf_mlp_gather_rows: ") + cudaGetErrorString(e));
+    return PDF_OK;
+}
+
+int pdf_mlp_standardize(float* X, int64_t n, int32_t d, const float* mean, const float* std, void* cuda_stream) {
+    if (!X || !mean || !std || n < 0 || d < 1) return fail(nullptr, PDF_ERR_ARG, "pdf_mlp_standardize: bad argument");
+    if (n == 0) return PDF_OK;
+    k_standardize<<<blocks_for(n * d, 256), 256, 0, (cudaStream_t)cuda_stream>>>(X, n, d, mean, std);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(nullptr, PDF_ERR_CUDA, std::string("pdf_mlp_standardize: ") + cudaGetErrorString(e));
+    return PDF_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// the surrogate inside a context: features, node inference, FE residual check
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int SUR_THREADS = 256;
+constexpr int SUR_SMEM = sizeof(float) * (PDF_MLP_NPARAM + PDF_MLP_NNORM + 2 * H * (SUR_THREADS / 32));
+
+struct SurArgs {
+    int nn;
+    const int* __restrict__ rep;
+    const unsigned char* __restrict__ is_wall;
+    const double* __restrict__ wdist;
+    const double* __restrict__ nke;
+    const double* __restrict__ ngrad;
+    const double* __restrict__ nR;
+};
+
+// features at node i: log d, log k, log eps, (k/eps) grad <U>, R/k
+__device__ void node_features(const SurArgs& a, int i, float f[IN], double& eps) {
+    const double d = a.wdist[i] > 1e-6 ? a.wdist[i] : 1e-6;
+    const double k = a.nke[2 * i];
+    eps = a.nke[2 * i + 1];
+    const double tau = k / eps;
+    f[0] = (float)log(d);
+    f[1] = (float)log(k);
+    f[2] = (float)log(eps);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) f[3 + q] = (float)(tau * a.ngrad[4 * i + q]);
+    f[7] = (float)(a.nR[6 * i + 0] / k);
+    f[8] = (float)(a.nR[6 * i + 3] / k);
+    f[9] = (float)(a.nR[6 * i + 1] / k);
+}
+
+__global__ void k_sur_harvest(SurArgs a, int nrows, const int* __restrict__ rows, const double* __restrict__ wp,
+                              float* X, float* T) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= nrows) return;
+    const int i = rows[r];
+    float f[IN];
+    double eps;
+    node_features(a, i, f, eps);
+#pragma unroll
+    for (int q = 0; q < IN; ++q) X[(size_t)IN * r + q] = f[q];
+#pragma unroll
+    for (int q = 0; q < OUT; ++q) T[(size_t)OUT * r + q] = (float)(wp[NC * (size_t)i + q] / eps);
+}
+
+// wp at the canonical nodes: the network at the free ones, the Dirichlet
+// value at the walls. One warp per node: lane l computes neurons l and l + 32
+// of each hidden layer. The bfloat16-rounded weights sit transposed in shared
+// memory (in x out), so the lanes read consecutive words, and the
+// activations of the warp's node are broadcast from shared memory.
+__global__ void __launch_bounds__(SUR_THREADS) k_sur_nodes(SurArgs a, const float* __restrict__ wq,
+                                                           const double* __restrict__ g, double* x) {
+    extern __shared__ float sm[];
+    float* WT1 = sm;                 // [IN][H]
+    float* WT2 = WT1 + IN * H;       // [H][H]
+    float* WT3 = WT2 + H * H;        // [H][H]
+    float* WT4 = WT3 + H * H;        // [H][OUT]
+    float* B = WT4 + H * OUT;        // b1 b2 b3 b4 (H, H, H, OUT)
+    float* nm = B + 3 * H + OUT;     // in_mean in_std out_mean out_std
+    float* act = nm + PDF_MLP_NNORM; // [warps][2][H]
+    for (int q = threadIdx.x; q < H * IN; q += SUR_THREADS) WT1[(q % IN) * H + q / IN] = wq[OFF_W1 + q];
+    for (int q = threadIdx.x; q < H * H; q += SUR_THREADS) {
+        WT2[(q % H) * H + q / H] = wq[OFF_W2 + q];
+        WT3[(q % H) * H + q / H] = wq[OFF_W3 + q];
+    }
+    for (int q = threadIdx.x; q < OUT * H; q += SUR_THREADS) WT4[(q % H) * OUT + q / H] = wq[OFF_W4 + q];
+    for (int q = threadIdx.x; q < H; q += SUR_THREADS) {
+        B[q] = wq[OFF_B1 + q];
+        B[H + q] = wq[OFF_B2 + q];
+        B[2 * H + q] = wq[OFF_B3 + q];
+    }
+    if (threadIdx.x < OUT) B[3 * H + threadIdx.x] = wq[OFF_B4 + threadIdx.x];
+    if (threadIdx.x < PDF_MLP_NNORM) nm[threadIdx.x] = wq[PDF_MLP_NPARAM + threadIdx.x];
+    __syncthreads();
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    float* h0 = act + wid * 2 * H;
+    float* h1 = h0 + H;
+    const int warps = gridDim.x * (SUR_THREADS / 32);
+    for (int i = blockIdx.x * (SUR_THREADS / 32) + wid; i < a.nn; i += warps) {
+        if (a.rep[i] != i) continue;
+        if (a.is_wall[i]) {
+            if (lane < NC) x[NC * (size_t)i + lane] = g[NC * (size_t)i + lane];
+            continue;
+        }
+        float f[IN];
+        double eps;
+        node_features(a, i, f, eps);
+#pragma unroll
+        for (int q = 0; q < IN; ++q) f[q] = (f[q] - nm[q]) / nm[IN + q];
+        float z0 = B[lane], z1 = B[lane + 32];
+#pragma unroll
+        for (int q = 0; q < IN; ++q) {
+            z0 = fmaf(WT1[q * H + lane], f[q], z0);
+            z1 = fmaf(WT1[q * H + lane + 32], f[q], z1);
+        }
+        h0[lane] = silu(z0);
+        h0[lane + 32] = silu(z1);
+        __syncwarp();
+        z0 = B[H + lane];
+        z1 = B[H + lane + 32];
+#pragma unroll 16
+        for (int q = 0; q < H; ++q) {
+            const float v = h0[q];
+            z0 = fmaf(WT2[q * H + lane], v, z0);
+            z1 = fmaf(WT2[q * H + lane + 32], v, z1);
+        }
+        h1[lane] = silu(z0);
+        h1[lane + 32] = silu(z1);
+        __syncwarp();
+        z0 = B[2 * H + lane];
+        z1 = B[2 * H + lane + 32];
+#pragma unroll 16
+        for (int q = 0; q < H; ++q) {
+            const float v = h1[q];
+            z0 = fmaf(WT3[q * H + lane], v, z0);
+            z1 = fmaf(WT3[q * H + lane + 32], v, z1);
+        }
+        h0[lane] = silu(z0);
+        h0[lane + 32] = silu(z1);
+        __syncwarp();
+        if (lane < OUT) {
+            float z = B[3 * H + lane];
+#pragma unroll 16
+            for (int q = 0; q < H; ++q) z = fmaf(WT4[q * OUT + lane], h0[q], z);
+            const double y = (double)z * nm[2 * IN + OUT + lane] + nm[2 * IN + lane];
+            x[NC * (size_t)i + lane] = eps * y;
+        }
+        __syncwarp();
+    }
+}
+
+struct ResArgs {
+    int nn;
+    const int* __restrict__ rowptr;
+    const int* __restrict__ colidx;
+    const double* __restrict__ mval;
+    const int* __restrict__ kc_off;
+    const int* __restrict__ kc_elem;
+    const double* __restrict__ kc_geo;
+    const double* __restrict__ eder;
+    const int* __restrict__ rep;
+    const unsigned char* __restrict__ is_wall;
+    const double* __restrict__ f;
+    const double* __restrict__ x;
+    double* part;  // [gridDim][4 NC]: sum r^2, sum b0^2, sum r, sum b0 per component
+};
+
+// r = M f - A x over the free rows (x holds the Dirichlet values at the walls),
+// b0 = M f - A_wall g; block partial sums of r^2, b0^2 (fine norm) and of r,
+// b0 (the coarse residual: one aggregate per block of 128 Morton-ordered
+// nodes, which averages out the node-to-node noise of the estimated
+// statistics) in a fixed order
+__global__ void __launch_bounds__(128) k_sur_residual(ResArgs a) {
+    __shared__ double red[4 * NC][128];
+    const int i = blockIdx.x * 128 + threadIdx.x;
+    double r[NC] = {0, 0, 0, 0, 0}, b0[NC] = {0, 0, 0, 0, 0};
+    if (i < a.nn && a.rep[i] == i && !a.is_wall[i]) {
+        double b[NC] = {0, 0, 0, 0, 0}, s[NC] = {0, 0, 0, 0, 0}, sw[NC] = {0, 0, 0, 0, 0};
+        for (int q = a.rowptr[i]; q < a.rowptr[i + 1]; ++q) {
+            double A = a.mval[q];
+            for (int k = a.kc_off[q]; k < a.kc_off[q + 1]; ++k) {
+                const double L = a.eder[9 * (size_t)a.kc_elem[k] + 8];
+                A += L * L * a.kc_geo[k];
+            }
+            const int j = a.colidx[q];
+            const bool wall = a.is_wall[j];
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                b[c] += a.mval[q] * a.f[NC * (size_t)j + c];
+                const double ax = A * a.x[NC * (size_t)j + c];
+                s[c] += ax;
+                if (wall) sw[c] += ax;
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            r[c] = b[c] - s[c];
+            b0[c] = b[c] - sw[c];
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+        red[c][threadIdx.x] = r[c] * r[c];
+        red[NC + c][threadIdx.x] = b0[c] * b0[c];
+        red[2 * NC + c][threadIdx.x] = r[c];
+        red[3 * NC + c][threadIdx.x] = b0[c];
+    }
+    __syncthreads();
+    for (int w = 64; w > 0; w >>= 1) {
+        if (threadIdx.x < w)
+#pragma unroll
+            for (int c = 0; c < 4 * NC; ++c) red[c][threadIdx.x] += red[c][threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x < 4 * NC) a.part[(size_t)blockIdx.x * 4 * NC + threadIdx.x] = red[threadIdx.x][0];
+}
+
+// relative residuals (max over components): last[0] coarse (the check),
+// last[1] fine; the decision and the counters
+__global__ void k_sur_decide(const double* __restrict__ part, int nb, int mode, double tol, int* skip,
+                             unsigned long long* cnt, double* last) {
+    if (threadIdx.x != 0) return;
+    double rr[NC] = {0, 0, 0, 0, 0}, bb[NC] = {0, 0, 0, 0, 0}, cr[NC] = {0, 0, 0, 0, 0}, cb[NC] = {0, 0, 0, 0, 0};
+    for (int b = 0; b < nb; ++b)
+        for (int c = 0; c < NC; ++c) {
+            const double* q = part + (size_t)b * 4 * NC;
+            rr[c] += q[c];
+            bb[c] += q[NC + c];
+            cr[c] += q[2 * NC + c] * q[2 * NC + c];
+            cb[c] += q[3 * NC + c] * q[3 * NC + c];
+        }
+    double fine = 0.0, coarse = 0.0;
+    for (int c = 0; c < NC; ++c) {
+        const double f = bb[c] > 0.0 ? sqrt(rr[c] / bb[c]) : sqrt(rr[c]);
+        const double g = cb[c] > 0.0 ? sqrt(cr[c] / cb[c]) : sqrt(cr[c]);
+        fine = f > fine ? f : fine;
+        coarse = g > coarse ? g : coarse;
+    }
+    const int ok = (mode == 2) || (coarse <= tol);
+    *skip = ok;
+    last[0] = coarse;
+    last[1] = fine;
+    cnt[0] += 1ull;
+    cnt[1] += ok ? 0ull : 1ull;
+}
+
+SurArgs sur_args(pdf_ctx* c) {
+    SurArgs a;
+    a.nn = c->m.nn; a.rep = c->m.rep; a.is_wall = c->m.is_wall; a.wdist = c->m.wdist;
+    a.nke = c->nke; a.ngrad = c->ngrad; a.nR = c->nR;
+    return a;
+}
+
+int sur_blocks(pdf_ctx* c) { return (c->m.nn + 127) / 128; }
+
+}  // namespace
+
+int surrogate_rows(pdf_ctx* c) {
+    if (c->sur_rows) return PDF_OK;
+    const int nn = c->m.nn;
+    std::vector<int> rep(nn);
+    std::vector<unsigned char> wall(nn);
+    PDF_CUDA(c, cudaStreamSynchronize(c->s));
+    PDF_CUDA(c, cudaMemcpy(rep.data(), c->m.rep, sizeof(int) * nn, cudaMemcpyDeviceToHost));
+    PDF_CUDA(c, cudaMemcpy(wall.data(), c->m.is_wall, nn, cudaMemcpyDeviceToHost));
+    std::vector<int> rows;
+    for (int i = 0; i < nn; ++i)
+        if (rep[i] == i && !wall[i]) rows.push_back(i);
+    PDF_CUDA(c, cudaMalloc((void**)&c->sur_rows, sizeof(int) * (rows.size() + 1)));
+    PDF_CUDA(c, cudaMemcpy(c->sur_rows, rows.data(), sizeof(int) * rows.size(), cudaMemcpyHostToDevice));
+    c->sur_nrows = (int)rows.size();
+    return PDF_OK;
+}
+
+int launch_surrogate(pdf_ctx* c) {
+    const int nn = c->m.nn;
+    const SurArgs a = sur_args(c);
+    const int warps_needed = (nn + 7) / 8;  // up to 8 nodes per warp
+    const int blocks = std::min(2 * c->num_sms, std::max(1, (warps_needed + SUR_THREADS / 32 - 1) / (SUR_THREADS / 32)));
+    k_sur_nodes<<<blocks, SUR_THREADS, SUR_SMEM, c->s>>>(a, c->sur_w, c->fe_g, c->fe_prop);
+    ResArgs r;
+    r.nn = nn; r.rowptr = c->m.rowptr; r.colidx = c->m.colidx; r.mval = c->m.mval; r.kc_off = c->m.kc_off;
+    r.kc_elem = c->m.kc_elem; r.kc_geo = c->m.kc_geo; r.eder = c->eder; r.rep = c->m.rep; r.is_wall = c->m.is_wall;
+    r.f = c->fe_f; r.x = c->fe_prop; r.part = c->sur_part;
+    const int nb = sur_blocks(c);
+    k_sur_residual<<<nb, 128, 0, c->s>>>(r);
+    k_sur_decide<<<1, 32, 0, c->s>>>(c->sur_part, nb, c->sur_mode, c->sur_tol, c->sur_skip, c->sur_cnt,
+                                     c->sur_part + (size_t)nb * 4 * NC);
+    c->launches += 3;
+    PDF_CUDA(c, cudaGetLastError());
+    return PDF_OK;
+}
+
+extern "C" {
+
+int32_t pdf_surrogate_rows(const pdf_ctx* c) {
+    if (!c || c->p.wall_model != PDF_ELLIPTIC_RELAXATION) return -1;
+    if (surrogate_rows(const_cast<pdf_ctx*>(c)) != PDF_OK) return -1;
+    return c->sur_nrows;
+}
+
+int pdf_surrogate_harvest(pdf_ctx* c, float* X, float* T) {
+    if (!c || !X || !T) return PDF_ERR_ARG;
+    if (c->p.wall_model != PDF_ELLIPTIC_RELAXATION) return fail(c, PDF_ERR_ARG, "harvest needs elliptic relaxation");
+    if (!c->stats_valid) return fail(c, PDF_ERR_STATE, "statistics not estimated");
+    const int st = surrogate_rows(c);
+    if (st != PDF_OK) return st;
+    if (c->sur_nrows == 0) return PDF_OK;
+    k_sur_harvest<<<(c->sur_nrows + 127) / 128, 128, 0, c->s>>>(sur_args(c), c->sur_nrows, c->sur_rows, c->nwp, X, T);
+    ++c->launches;
+    PDF_CUDA(c, cudaGetLastError());
+    return PDF_OK;
+}
+
+int pdf_set_surrogate(pdf_ctx* c, int32_t mode, const float* params, const float* norm, double residual_tol) {
+    if (!c) return PDF_ERR_ARG;
+    if (mode < 0 || mode > 2) return fail(c, PDF_ERR_ARG, "surrogate mode must be 0, 1 or 2");
+    if (mode == 0) {
+        c->sur_mode = 0;
+        return PDF_OK;
+    }
+    if (c->p.wall_model != PDF_ELLIPTIC_RELAXATION) return fail(c, PDF_ERR_ARG, "surrogate needs elliptic relaxation");
+    if (!params || !norm || !(residual_tol >= 0)) return fail(c, PDF_ERR_ARG, "surrogate: NULL array or bad tolerance");
+    for (int q = 0; q < PDF_MLP_NNORM; ++q)
+        if (!std::isfinite(norm[q]) || (((q >= IN && q < 2 * IN) || q >= 2 * IN + OUT) && !(norm[q] > 0.f)))
+            return fail(c, PDF_ERR_ARG, "surrogate: standard deviations must be positive and finite");
+    if (!c->sur_w) {
+        PDF_CUDA(c, cudaMalloc((void**)&c->sur_w, sizeof(float) * (PDF_MLP_NPARAM + PDF_MLP_NNORM)));
+        PDF_CUDA(c, cudaMalloc((void**)&c->sur_skip, sizeof(int)));
+        PDF_CUDA(c, cudaMalloc((void**)&c->sur_cnt, 2 * sizeof(unsigned long long)));
+        PDF_CUDA(c, cudaMalloc((void**)&c->sur_part, sizeof(double) * ((size_t)sur_blocks(c) * 4 * NC + 2)));
+        PDF_CUDA(c, cudaFuncSetAttribute(k_sur_nodes, cudaFuncAttributeMaxDynamicSharedMemorySize, SUR_SMEM));
+    }
+    std::vector<float> h(PDF_MLP_NPARAM + PDF_MLP_NNORM);
+    for (int q = 0; q < PDF_MLP_NPARAM; ++q) h[q] = __bfloat162float(__float2bfloat16_rn(params[q]));
+    for (int q = 0; q < PDF_MLP_NNORM; ++q) h[PDF_MLP_NPARAM + q] = norm[q];
+    PDF_CUDA(c, cudaStreamSynchronize(c->s));
+    PDF_CUDA(c, cudaMemcpy(c->sur_w, h.data(), sizeof(float) * h.size(), cudaMemcpyHostToDevice));
+    PDF_CUDA(c, cudaMemset(c->sur_skip, 0, sizeof(int)));
+    PDF_CUDA(c, cudaMemset(c->sur_cnt, 0, 2 * sizeof(unsigned long long)));
+    PDF_CUDA(c, cudaMemset(c->sur_part, 0, sizeof(double) * ((size_t)sur_blocks(c) * 4 * NC + 2)));
+    c->sur_mode = mode;
+    c->sur_tol = residual_tol;
+    return PDF_OK;
+}
+
+int pdf_surrogate_stats(pdf_ctx* c, int64_t* solves, int64_t* fallbacks, double last_residual[2]) {
+    if (!c || !solves || !fallbacks || !last_residual) return PDF_ERR_ARG;
+    *solves = *fallbacks = 0;
+    last_residual[0] = last_residual[1] = 0.0;
+    if (!c->sur_cnt) return PDF_OK;
+    unsigned long long h[2];
+    PDF_CUDA(c, cudaStreamSynchronize(c->s));
+    PDF_CUDA(c, cudaMemcpy(h, c->sur_cnt, sizeof(h), cudaMemcpyDeviceToHost));
+    PDF_CUDA(c, cudaMemcpy(last_residual, c->sur_part + (size_t)sur_blocks(c) * 4 * NC, 2 * sizeof(double),
+                           cudaMemcpyDeviceToHost));
+    *solves = (int64_t)h[0];
+    *fallbacks = (int64_t)h[1];
+    return PDF_OK;
+}
+
+}  // extern "C"

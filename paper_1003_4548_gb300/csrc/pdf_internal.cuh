@@ -105,12 +105,21 @@ struct pdf_ctx {
     SortKey* sort_scratch = nullptr;
     int64_t sort_scratch_n = 0;
     // elliptic relaxation work vectors (canonical nodes x 5)
-    double *fe_f = nullptr, *fe_g = nullptr, *fe_b = nullptr, *fe_r = nullptr, *fe_z = nullptr;
-    double *fe_p = nullptr, *fe_ap = nullptr, *fe_part = nullptr, *fe_bnorm = nullptr;
+    double *fe_f = nullptr, *fe_g = nullptr, *fe_z = nullptr, *fe_part = nullptr;
+    double* fe_prop = nullptr;  // surrogate proposal for wp (canonical rows x 5)
     unsigned int* fe_bar = nullptr;  // grid barrier words
     int* fe_iters = nullptr;
     int fe_blocks = 0;
     int fe_bs = 0;  // rows per block of the elliptic solver (block-Jacobi block size)
+    // learned surrogate of the elliptic solve (mode 0: off)
+    int sur_mode = 0;
+    double sur_tol = 0.0;
+    float* sur_w = nullptr;               // PDF_MLP_NPARAM bf16-rounded parameters + PDF_MLP_NNORM
+    int* sur_rows = nullptr;              // free canonical node ids
+    int sur_nrows = 0;
+    int* sur_skip = nullptr;              // 1: the network's wp passed the residual check this step
+    unsigned long long* sur_cnt = nullptr;  // solves, fallbacks
+    double* sur_part = nullptr;           // per-block residual partial sums, then the last residual
     // status
     int* d_status = nullptr;
     int* h_status = nullptr;
@@ -148,6 +157,8 @@ int launch_count_and_sort(pdf_ctx* c);  // histogram of elemA, then launch_sort
 int launch_moments(pdf_ctx* c);
 int launch_fields(pdf_ctx* c);      // node stats, derived, recovery, ER solve, packs
 int launch_elliptic(pdf_ctx* c);
+int launch_surrogate(pdf_ctx* c);   // network wp at the nodes + FE residual check (before the CG)
+int surrogate_rows(pdf_ctx* c);     // builds the free canonical row list once
 int launch_to_double(pdf_ctx* c, const void* src, double* dst, int64_t n);
 
 // ---------------------------------------------------------------------------

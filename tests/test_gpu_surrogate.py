@@ -1,0 +1,223 @@
+"""The surrogate network's CUDA kernels against the FP64 oracle (oracle/mlp.py),
+and the surrogate inside an elliptic-relaxation context.
+
+Bars: the FP32 loss gradient within 1e-4 of the oracle (relative to the
+gradient's magnitude plus its rms); FP32 forward within 1e-5 and the bf16
+forward within 1e-4 of the oracle with the same bf16-rounded weights (FP32
+accumulation is the only difference); Adam, column statistics,
+standardisation and gathers to FP32 rounding; harvested features within 1e-6
+of the oracle's features of the context's own node fields.
+"""
+import numpy as np
+import pytest
+
+from canyon_inputs.mesh import canyon_mesh
+from oracle import mlp
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    t = pytest.importorskip("torch")
+    if not t.cuda.is_available():
+        pytest.skip("needs a GPU")
+    return t
+
+
+def dev(torch, a, dtype=None):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype or np.float32)).cuda()
+
+
+def close(a, b, rtol):
+    a, b = np.asarray(a, np.float64), np.asarray(b, np.float64)
+    scale = np.abs(b) + np.sqrt(np.mean(b * b)) + 1e-30
+    return float(np.max(np.abs(a - b) / scale)) <= rtol, float(np.max(np.abs(a - b) / scale))
+
+
+def test_loss_gradient_matches_oracle(torch):
+    from paper_1003_4548_gb300 import capi
+    rng = np.random.default_rng(3)
+    n = 333  # ragged against the 32-wide tiles and the 256-thread blocks
+    p = (rng.normal(0, 0.3, mlp.NPARAM)).astype(np.float32)
+    X = rng.normal(size=(n, mlp.IN)).astype(np.float32)
+    T = rng.normal(size=(n, mlp.OUT)).astype(np.float32)
+    P, Xd, Td = dev(torch, p), dev(torch, X), dev(torch, T)
+    G = torch.zeros(mlp.NPARAM, dtype=torch.float32, device="cuda")
+    L = torch.zeros(1, dtype=torch.float32, device="cuda")
+    work = torch.empty(capi.mlp_work_floats(n), dtype=torch.float32, device="cuda")
+    s = torch.cuda.current_stream().cuda_stream
+    capi.mlp_loss_grad(P.data_ptr(), Xd.data_ptr(), Td.data_ptr(), n, work.data_ptr(), G.data_ptr(), L.data_ptr(), s)
+    torch.cuda.synchronize()
+    Lo, go = mlp.loss_grad(p.astype(np.float64), X, T)
+    assert float(L.item()) == pytest.approx(Lo, rel=1e-5)
+    ok, err = close(G.cpu().numpy(), go, 1e-4)
+    assert ok, err
+    # a second call on the same buffers gives the same numbers (no accumulation)
+    G2 = G.clone()
+    capi.mlp_loss_grad(P.data_ptr(), Xd.data_ptr(), Td.data_ptr(), n, work.data_ptr(), G.data_ptr(), L.data_ptr(), s)
+    torch.cuda.synchronize()
+    assert torch.equal(G, G2)
+
+
+@pytest.mark.parametrize("bf16", [False, True])
+def test_forward_matches_oracle(torch, bf16):
+    from paper_1003_4548_gb300 import capi
+    rng = np.random.default_rng(5)
+    n = 1001
+    p = rng.normal(0, 0.3, mlp.NPARAM).astype(np.float32)
+    X = rng.normal(size=(n, mlp.IN)).astype(np.float32)
+    Y = torch.empty((n, mlp.OUT), dtype=torch.float32, device="cuda")
+    work = torch.empty(capi.mlp_work_floats(n), dtype=torch.float32, device="cuda")
+    Pd, Xd = dev(torch, p), dev(torch, X)  # keep the buffers alive while the kernels run
+    capi.mlp_forward(Pd.data_ptr(), Xd.data_ptr(), n, Y.data_ptr(), work.data_ptr(), bf16,
+                     torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    ok, err = close(Y.cpu().numpy(), mlp.forward(p.astype(np.float64), X, bf16=bf16), 1e-4 if bf16 else 1e-5)
+    assert ok, err
+
+
+def test_adam_stats_gather_standardize(torch):
+    from paper_1003_4548_gb300 import capi
+    rng = np.random.default_rng(6)
+    s = torch.cuda.current_stream().cuda_stream
+    p, g = rng.normal(size=mlp.NPARAM).astype(np.float32), rng.normal(size=mlp.NPARAM).astype(np.float32)
+    m0, v0 = rng.normal(size=mlp.NPARAM).astype(np.float32) * 0.1, np.abs(rng.normal(size=mlp.NPARAM)).astype(np.float32)
+    P, M, V = dev(torch, p), dev(torch, m0), dev(torch, v0)
+    Gd = dev(torch, g)
+    capi.mlp_adam(P.data_ptr(), Gd.data_ptr(), M.data_ptr(), V.data_ptr(), 7, 1e-3, stream=s)
+    po, mo, vo = mlp.adam(p, g.astype(np.float64), m0, v0, 7, 1e-3)
+    torch.cuda.synchronize()
+    assert np.allclose(P.cpu().numpy(), po, rtol=0, atol=2e-6)
+    assert np.allclose(M.cpu().numpy(), mo, rtol=1e-6, atol=1e-7)
+    assert np.allclose(V.cpu().numpy(), vo, rtol=1e-6, atol=1e-7)
+    X = (rng.normal(size=(5000, 7)) * np.arange(1, 8) + np.arange(7)).astype(np.float32)
+    Xd = dev(torch, X)
+    mean = torch.empty(7, dtype=torch.float32, device="cuda")
+    sd = torch.empty(7, dtype=torch.float32, device="cuda")
+    capi.mlp_column_stats(Xd.data_ptr(), 5000, 7, mean.data_ptr(), sd.data_ptr(), s)
+    capi.mlp_standardize(Xd.data_ptr(), 5000, 7, mean.data_ptr(), sd.data_ptr(), s)
+    torch.cuda.synchronize()
+    X64 = X.astype(np.float64)
+    assert np.allclose(mean.cpu().numpy(), X64.mean(0), rtol=1e-6, atol=1e-6)
+    assert np.allclose(sd.cpu().numpy(), X64.std(0), rtol=1e-6)
+    assert np.allclose(Xd.cpu().numpy(), (X64 - X64.mean(0)) / X64.std(0), atol=2e-5)
+    idx = rng.integers(0, 5000, 777).astype(np.int32)
+    out = torch.empty((777, 7), dtype=torch.float32, device="cuda")
+    Id = dev(torch, idx, np.int32)
+    capi.mlp_gather_rows(Xd.data_ptr(), Id.data_ptr(), 777, 7, out.data_ptr(), s)
+    torch.cuda.synchronize()
+    assert torch.equal(out, Xd[torch.from_numpy(idx).long().cuda()])
+
+
+@pytest.fixture(scope="module")
+def er_case(torch):
+    from paper_1003_4548_gb300 import Canyon, canyon_params
+    mesh = canyon_mesh(offset=0.0, h=0.08, y1=3e-3, growth=1.3, seed=4)
+    return mesh, lambda **kw: Canyon(canyon_params(mesh, wall_model="er", precision="fp64", C0=2.1, seed=9,
+                                                   cg_tol=1e-10, cg_maxit=20000, **kw), mesh,
+                                     stream=torch.cuda.current_stream().cuda_stream)
+
+
+def test_harvest_matches_oracle_features(torch, er_case):
+    mesh, make = er_case
+    g = make()
+    g.seed_particles(32)
+    g.estimate_stats()
+    rows = g.surrogate_rows()
+    X = torch.empty((rows, 10), dtype=torch.float32, device="cuda")
+    T = torch.empty((rows, 5), dtype=torch.float32, device="cuda")
+    g.surrogate_harvest(X.data_ptr(), T.data_ptr())
+    ke, gr, R, wd, wp = (g.field(k) for k in ("node_ke", "node_grad", "node_R", "node_wdist", "node_wp"))
+    n = len(wd)
+    pair = mesh["periodic_pair"]
+    canon = np.array([i if pair[i] < 0 or pair[i] > i else pair[i] for i in range(n)])
+    wall = np.zeros(n, bool)
+    tri, tag = mesh["tri"], mesh["edge_tag"]
+    for e in range(len(tri)):
+        for k in range(3):
+            if tag[e, k] == 1:
+                wall[tri[e, (k + 1) % 3]] = wall[tri[e, (k + 2) % 3]] = True
+    wall |= np.where(pair >= 0, wall[np.maximum(pair, 0)], False)
+    free = np.flatnonzero((canon == np.arange(n)) & ~wall)
+    assert rows == free.size
+    F = mlp.features(wd[free], ke[free, 0], ke[free, 1], gr[free], R[free])
+    Tt = mlp.targets(wp[free], ke[free, 1])
+    ok, err = close(X.cpu().numpy(), F, 1e-6)
+    assert ok, err
+    ok, err = close(T.cpu().numpy(), Tt, 1e-6)
+    assert ok, err
+    g.close()
+
+
+def _dt(mesh):
+    from canyon_inputs.configs import cfl_dt
+    return cfl_dt(mesh, cfl=0.5, k0=1e-3)
+
+
+def _trained_surrogate(torch, mesh, make):
+    from paper_1003_4548_gb300 import surrogate
+    X, T, _ = surrogate.harvest([mesh], steps=20, every=2, per_element=32, dt_of=_dt, precision="fp64")
+    params, norm, hist = surrogate.train(X, T, epochs=30, batch=512, lr=3e-3, lr_final=3e-4, seed=1)
+    return X, T, params, norm, hist
+
+
+def test_training_and_the_surrogate_in_the_step(torch, er_case):
+    """Training lowers the loss; with the check disabled (mode 2) the context's
+    wp equals the network's output on the harvested features; with a zero
+    tolerance (mode 1) every step falls back to the FE solve and reproduces
+    the FE-only run exactly; the trained network's gain: no CG iteration in mode 2, and
+    its wp error against the FE solve is reported."""
+    from paper_1003_4548_gb300 import capi
+    mesh, make = er_case
+    X, T, params, norm, hist = _trained_surrogate(torch, mesh, make)
+    assert hist[-1][1] < 0.5 * hist[0][1]
+    # mode 2: wp from the network at the free nodes
+    g = make()
+    g.seed_particles(32)
+    g.estimate_stats()
+    wp_fe = g.field("node_wp")
+    g.set_surrogate(2, params, norm, 0.0)
+    g.estimate_stats()
+    assert g.cg_iterations == 0
+    rows = g.surrogate_rows()
+    Xh = torch.empty((rows, 10), dtype=torch.float32, device="cuda")
+    Th = torch.empty((rows, 5), dtype=torch.float32, device="cuda")
+    g.surrogate_harvest(Xh.data_ptr(), Th.data_ptr())  # targets now hold the network's wp / eps
+    q = dev(torch, norm)
+    s = torch.cuda.current_stream().cuda_stream
+    capi.mlp_standardize(Xh.data_ptr(), rows, 10, q[0:].data_ptr(), q[10:].data_ptr(), s)
+    Y = torch.empty((rows, 5), dtype=torch.float32, device="cuda")
+    work = torch.empty(capi.mlp_work_floats(rows), dtype=torch.float32, device="cuda")
+    Pd = dev(torch, params)
+    capi.mlp_forward(Pd.data_ptr(), Xh.data_ptr(), rows, Y.data_ptr(), work.data_ptr(), True, s)
+    torch.cuda.synchronize()
+    y = Y.cpu().numpy().astype(np.float64) * norm[25:30] + norm[20:25]
+    ok, err = close(Th.cpu().numpy(), y, 1e-5)
+    assert ok, err
+    solves, falls, res = g.surrogate_stats()
+    assert solves == 1 and falls == 0 and res[0] > 0 and res[1] > 0
+    wp_mlp = g.field("node_wp")
+    rel = np.linalg.norm(wp_mlp - wp_fe) / np.linalg.norm(wp_fe)
+    print(f"surrogate wp relative error vs FE: {rel:.3e}; FE residual of the network's wp: coarse {res[0]:.3e}, "
+          f"fine {res[1]:.3e}")
+    assert rel < 0.5
+    g.close()
+    # mode 1 with a zero tolerance: every step falls back, results match FE-only
+    a, b = make(), make()
+    for c in (a, b):
+        c.seed_particles(32)
+        c.estimate_stats()
+    b.set_surrogate(1, params, norm, 0.0)
+    for c in (a, b):
+        c.step(_dt(mesh), 3)
+        c.sync()
+    solves, falls, _ = b.surrogate_stats()
+    assert solves == 3 and falls == 3
+    # the fallback solves from the previous solution, exactly as the FE-only run
+    assert np.array_equal(a.field("node_wp"), b.field("node_wp"))
+    oa, ob = np.argsort(a.field("id")), np.argsort(b.field("id"))
+    for k in ("x", "u", "om", "psi"):
+        assert np.array_equal(a.field(k)[oa], b.field(k)[ob]), k
+    a.close()
+    b.close()
