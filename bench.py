@@ -388,8 +388,11 @@ def main():
     from canyon_inputs.configs import WORKLOADS, build_mesh, cfl_dt
     cfg = dict(WORKLOADS[a.workload])
     cfg["name"] = a.workload
+    plain_precision = cfg["precision"]
     if a.precision:
         cfg["precision"] = a.precision
+    elif a.impl != "reference" and not a.no_surrogate and cfg.get("chosen_precision"):
+        cfg["precision"] = cfg["chosen_precision"]
     mesh = build_mesh(cfg)
     dt = cfl_dt(mesh, cfl=cfg["cfl"], k0=cfg["k0"])
     if a.impl == "reference":
@@ -409,7 +412,8 @@ def main():
     use_sur = cfg["wall_model"] == "er" and not a.no_surrogate
     sur, sur_info = (prepare_surrogate(cfg, mesh, dt) if use_sur else (None, None))
     prec = cfg["precision"]
-    form_name = (f"{prec} particle state, FP64 exact statistics" +
+    red = {"fp64": "FP64", "fp32": "FP64-exact", "fp32_kahan": "compensated FP32"}[prec]
+    form_name = (f"{prec} particle state, {red} statistics" +
                  (", surrogate wp with the FE solve as checked fallback" if use_sur else ", FE solve every step"))
     # each rank runs its own canyon case (independent problems, no exchange)
     chosen = Form(cfg, mesh, stream, precision=prec, case_id=rank, cg_precision=a.cg_precision, sur=sur)
@@ -466,7 +470,7 @@ def main():
     forms = {}
     if not a.no_forms and rank == 0:
         k = max(10, a.steps // 5)
-        for name, fp, cgp in (("plain_fp64_fe", "fp64", 0), ("fp32_fe", "fp32", 0)):
+        for name, fp, cgp in (("plain_fp64_fe", "fp64", 0), (f"{plain_precision}_fe", plain_precision, 0)):
             f = Form(cfg, mesh, stream, precision=fp, cg_precision=cgp)
             rr = f.timed(dt, k, 3)
             forms[name] = {"value": f.g.num_particles * k / (rr["ms"] / 1e3), "ms_per_step": rr["ms"] / k,
@@ -506,10 +510,11 @@ def precision_study(cfg, mesh, dt, stream, sur, steps):
     next to the Monte Carlo scale (the FP64 form with another seed)."""
     variants = (("fp64_fe", "fp64", 0, None, None), ("fp64_fe_other_seed", "fp64", 0, None, 1),
                 ("fp32_fe", "fp32", 0, None, None), ("fp32_kahan_fe", "fp32_kahan", 0, None, None),
-                ("fp32_fe_ff_cg", "fp32", 1, None, None), ("fp32_surrogate", "fp32", 0, sur, None))
+                ("fp32_fe_ff_cg", "fp32", 1, None, None),
+                ("chosen_fp32_kahan_surrogate", "fp32_kahan", 0, sur, None))
     ref, out = None, {}
     for name, prec, cgp, s, seed in variants:
-        if s is None and name == "fp32_surrogate":
+        if s is None and name == "chosen_fp32_kahan_surrogate":
             continue
         f = Form(cfg, mesh, stream, precision=prec, cg_precision=cgp, sur=s, seed=seed)
         rr = f.timed(dt, steps, 0)

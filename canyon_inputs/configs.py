@@ -12,7 +12,9 @@ canyon centre) and the workload sizes of this project:
   canyon_er_full    ~40k triangles graded to a first-cell height nu/u* at the
                     walls, elliptic relaxation solved by P1 finite elements every
                     step, 256 particles per element (~10.3M), FP32 particle state
-                    with FP64 statistics and CG, 500 steps.
+                    with FP64 statistics and CG, 500 steps. The chosen form
+                    keeps the FP32 state, reduces in compensated FP32 and
+                    takes wp from the surrogate (FE solve as checked fallback).
 
 The time step follows a CFL rule that depends on the mesh and the initial
 condition only: dt = CFL * min_e(2 r_e) / U_ref, with r_e the inradius and
@@ -45,7 +47,7 @@ WORKLOADS = {
         mesh=dict(H=1.0, W=1.0, B=2.0, T=2.0, offset=0.0, h=0.017, y1=NU / USTAR,
                   growth=1.2, seed=0),
         wall_model="er", per_element=256, bins=(2, 2, 2), C0=2.1, steps=500, cfl=0.5,
-        precision="fp32", seed=0, k0=1e-3),
+        precision="fp32", chosen_precision="fp32_kahan", seed=0, k0=1e-3),
 }
 
 

@@ -325,6 +325,7 @@ int alloc_stats(pdf_ctx* c) {
     TRY(dalloc(c, &c->eR, 6 * (size_t)nt));
     TRY(dalloc(c, &c->epsivar, nt));
     TRY(dalloc(c, &c->ecm, (size_t)B * nt));
+    TRY(dalloc(c, &c->elist, 2 + 2 * (size_t)nt));
     TRY(dalloc(c, &c->nwt, nn));
     TRY(dalloc(c, &c->nmean, 4 * (size_t)nn));
     TRY(dalloc(c, &c->nR, 6 * (size_t)nn));
@@ -662,7 +663,7 @@ void pdf_destroy(pdf_ctx* c) {
                    c->emean, c->eR, c->epsivar, c->ecm, c->nwt, c->nmean, c->nR, c->nke, c->npsivar, c->eder,
                    c->ngrad, c->npack, c->nwp, c->npackT, c->epackT, c->ecmT, c->sort_scratch, c->fe_f, c->fe_g,
                    c->fe_prop, c->fe_z, c->fe_part, c->fe_bar, c->fe_iters, c->d_status,
-                   c->conv_buf, c->sur_w, c->sur_rows, c->sur_skip, c->sur_cnt, c->sur_part};
+                   c->conv_buf, c->elist, c->sur_w, c->sur_rows, c->sur_skip, c->sur_cnt, c->sur_part};
     for (void* p : dev) cudaFree(p);
     for (int k = 0; k < 7; ++k) {
         cudaFree(c->stA[k]);

@@ -64,6 +64,25 @@ __global__ void k_fe_rhs(int nn, const double* __restrict__ nR, const double* __
     }
 }
 
+// values of M + K_{L^2} (Eq. elliptic-relaxation in Galerkin form): each
+// nonzero is its mass entry plus the L^2-weighted stiffness contributions of
+// the elements that share the edge (L is an element constant, Eq. L);
+// FP64, and the float-float pair for the compensated-FP32 CG
+__global__ void k_fe_assemble(int64_t nnz, const double* __restrict__ mval, const int* __restrict__ kc_off,
+                              const int* __restrict__ kc_elem, const double* __restrict__ kc_geo,
+                              const double* __restrict__ eder, double* aval, float2* avf) {
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= nnz) return;
+    double s = mval[q];
+    for (int k = kc_off[q]; k < kc_off[q + 1]; ++k) {
+        const double L = eder[9 * (size_t)kc_elem[k] + 8];
+        s += L * L * kc_geo[k];
+    }
+    aval[q] = s;
+    const ff v = ff_from_double(s);
+    avf[q] = make_float2(v.hi, v.lo);
+}
+
 struct CGArgs {
     int nn;
     const int* __restrict__ rowptr;
@@ -233,20 +252,10 @@ __global__ void __launch_bounds__(BS * NC) k_pcg(const CGArgs a) {
     const int i = blockIdx.x * BS + t;
     const bool have = i < a.nn;
     const bool free_row = have && a.rep[i] == i && !a.is_wall[i];
-    // assembly of M + K_{L^2} (component 0 threads), b = M f, Dirichlet values
+    // b = M f and the Dirichlet values (the matrix was assembled by k_fe_assemble)
     double b = 0.0, x = 0.0;
     if (have) {
-        for (int q = a.rowptr[i]; q < a.rowptr[i + 1]; ++q) {
-            if (c == 0) {
-                double s = a.mval[q];
-                for (int k = a.kc_off[q]; k < a.kc_off[q + 1]; ++k) {
-                    const double L = a.eder[9 * (size_t)a.kc_elem[k] + 8];
-                    s += L * L * a.kc_geo[k];
-                }
-                a.aval[q] = s;
-            }
-            b += a.mval[q] * a.f[NC * (size_t)a.colidx[q] + c];
-        }
+        for (int q = a.rowptr[i]; q < a.rowptr[i + 1]; ++q) b += a.mval[q] * a.f[NC * (size_t)a.colidx[q] + c];
         x = a.is_wall[i] ? a.g[NC * (size_t)i + c] : a.x[NC * (size_t)i + c];
         a.x[NC * (size_t)i + c] = x;
     }
@@ -441,19 +450,7 @@ __global__ void __launch_bounds__(BS * NC) k_pcg_ff(const CGArgs a) {
     const bool free_row = have && a.rep[i] == i && !a.is_wall[i];
     double b = 0.0, x0 = 0.0;
     if (have) {
-        for (int q = a.rowptr[i]; q < a.rowptr[i + 1]; ++q) {
-            if (c == 0) {
-                double s = a.mval[q];
-                for (int k = a.kc_off[q]; k < a.kc_off[q + 1]; ++k) {
-                    const double L = a.eder[9 * (size_t)a.kc_elem[k] + 8];
-                    s += L * L * a.kc_geo[k];
-                }
-                a.aval[q] = s;
-                const ff v = ff_from_double(s);
-                a.avf[q] = make_float2(v.hi, v.lo);
-            }
-            b += a.mval[q] * a.f[NC * (size_t)a.colidx[q] + c];
-        }
+        for (int q = a.rowptr[i]; q < a.rowptr[i + 1]; ++q) b += a.mval[q] * a.f[NC * (size_t)a.colidx[q] + c];
         x0 = a.is_wall[i] ? a.g[NC * (size_t)i + c] : a.x[NC * (size_t)i + c];
         a.x[NC * (size_t)i + c] = x0;
     }
@@ -656,6 +653,10 @@ int launch_elliptic(pdf_ctx* c) {
     timing_begin(c, PDF_K_ELLIPTIC);
     k_fe_rhs<<<(nn + 127) / 128, 128, 0, c->s>>>(nn, c->nR, c->ngrad, c->nke, c->nmean, c->m.is_wall, c->m.wn,
                                                 c->p, c->fe_f, c->fe_g);
+    k_fe_assemble<<<(unsigned)((c->m.nnz + 255) / 256), 256, 0, c->s>>>(c->m.nnz, c->m.mval, c->m.kc_off,
+                                                                       c->m.kc_elem, c->m.kc_geo, c->eder,
+                                                                       c->m.aval, c->m.avf);
+    c->launches += 1;
     PDF_CUDA(c, cudaGetLastError());
     if (c->sur_mode) {
         const int st = launch_surrogate(c);

@@ -85,7 +85,7 @@ __global__ void k_elem_derived(int nt, const int* __restrict__ tri, const double
     const double t2 = t2a > t2b ? t2a : t2b;
     d[7] = t1 < t2 ? t1 : t2;
     const double Cxi = 1.0 + 1.3 * 1.0;  // C_xi = 1 + 1.3 n_i n_i with a unit normal
-    const double La = Cxi * pow(kc, 1.5) / ec, Lb = p.Ceta * pow(p.nu * p.nu * p.nu / ec, 0.25);
+    const double La = Cxi * kc * sqrt(kc) / ec, Lb = p.Ceta * sqrt(sqrt(p.nu * p.nu * p.nu / ec));
     d[8] = p.CL * (La > Lb ? La : Lb);
     T* ep = epack + (size_t)ELEM_PACK_W * e;
     ep[0] = (T)Ux; ep[1] = (T)Uy; ep[2] = (T)Vx; ep[3] = (T)Vy;

@@ -341,20 +341,25 @@ struct SurArgs {
     const double* __restrict__ nR;
 };
 
-// features at node i: log d, log k, log eps, (k/eps) grad <U>, R/k
+// features at node i: log d, log k, log eps, (k/eps) grad <U>, R/k. The
+// network's inputs are FP32, so they are formed in FP32 from the FP64 node
+// fields (one warp evaluates a node: FP64 work on every lane would saturate
+// GB300's FP64 pipe).
 __device__ void node_features(const SurArgs& a, int i, float f[IN], double& eps) {
-    const double d = a.wdist[i] > 1e-6 ? a.wdist[i] : 1e-6;
-    const double k = a.nke[2 * i];
+    const double dd = a.wdist[i];
+    const float d = dd > 1e-6 ? (float)dd : 1e-6f;
+    const float k = (float)a.nke[2 * i];
     eps = a.nke[2 * i + 1];
-    const double tau = k / eps;
-    f[0] = (float)log(d);
-    f[1] = (float)log(k);
-    f[2] = (float)log(eps);
+    const float e = (float)eps;
+    const float tau = k / e, ik = 1.f / k;
+    f[0] = logf(d);
+    f[1] = logf(k);
+    f[2] = logf(e);
 #pragma unroll
-    for (int q = 0; q < 4; ++q) f[3 + q] = (float)(tau * a.ngrad[4 * i + q]);
-    f[7] = (float)(a.nR[6 * i + 0] / k);
-    f[8] = (float)(a.nR[6 * i + 3] / k);
-    f[9] = (float)(a.nR[6 * i + 1] / k);
+    for (int q = 0; q < 4; ++q) f[3 + q] = tau * (float)a.ngrad[4 * i + q];
+    f[7] = (float)a.nR[6 * i + 0] * ik;
+    f[8] = (float)a.nR[6 * i + 3] * ik;
+    f[9] = (float)a.nR[6 * i + 1] * ik;
 }
 
 __global__ void k_sur_harvest(SurArgs a, int nrows, const int* __restrict__ rows, const double* __restrict__ wp,
@@ -411,10 +416,16 @@ __global__ void __launch_bounds__(SUR_THREADS) k_sur_nodes(SurArgs a, const floa
             continue;
         }
         float f[IN];
-        double eps;
-        node_features(a, i, f, eps);
+        double eps = 0.0;
+        if (lane == 0) {
+            node_features(a, i, f, eps);
 #pragma unroll
-        for (int q = 0; q < IN; ++q) f[q] = (f[q] - nm[q]) / nm[IN + q];
+            for (int q = 0; q < IN; ++q) h1[q] = (f[q] - nm[q]) / nm[IN + q];
+        }
+        eps = __shfl_sync(0xffffffffu, eps, 0);
+        __syncwarp();
+#pragma unroll
+        for (int q = 0; q < IN; ++q) f[q] = h1[q];
         float z0 = B[lane], z1 = B[lane + 32];
 #pragma unroll
         for (int q = 0; q < IN; ++q) {
@@ -462,10 +473,7 @@ struct ResArgs {
     const int* __restrict__ rowptr;
     const int* __restrict__ colidx;
     const double* __restrict__ mval;
-    const int* __restrict__ kc_off;
-    const int* __restrict__ kc_elem;
-    const double* __restrict__ kc_geo;
-    const double* __restrict__ eder;
+    const double* __restrict__ aval;  // assembled M + K_{L^2}
     const int* __restrict__ rep;
     const unsigned char* __restrict__ is_wall;
     const double* __restrict__ f;
@@ -473,28 +481,26 @@ struct ResArgs {
     double* part;  // [gridDim][4 NC]: sum r^2, sum b0^2, sum r, sum b0 per component
 };
 
+constexpr int RES_ROWS = 128;
+
 // r = M f - A x over the free rows (x holds the Dirichlet values at the walls),
 // b0 = M f - A_wall g; block partial sums of r^2, b0^2 (fine norm) and of r,
-// b0 (the coarse residual: one aggregate per block of 128 Morton-ordered
+// b0 (the coarse residual: one aggregate per block of RES_ROWS Morton-ordered
 // nodes, which averages out the node-to-node noise of the estimated
-// statistics) in a fixed order
-__global__ void __launch_bounds__(128) k_sur_residual(ResArgs a) {
-    __shared__ double red[4 * NC][128];
-    const int i = blockIdx.x * 128 + threadIdx.x;
+// statistics), in a fixed order
+__global__ void __launch_bounds__(RES_ROWS) k_sur_residual(ResArgs a) {
+    __shared__ double red[4 * NC][RES_ROWS];
+    const int t = threadIdx.x, i = blockIdx.x * RES_ROWS + t;
     double r[NC] = {0, 0, 0, 0, 0}, b0[NC] = {0, 0, 0, 0, 0};
     if (i < a.nn && a.rep[i] == i && !a.is_wall[i]) {
         double b[NC] = {0, 0, 0, 0, 0}, s[NC] = {0, 0, 0, 0, 0}, sw[NC] = {0, 0, 0, 0, 0};
         for (int q = a.rowptr[i]; q < a.rowptr[i + 1]; ++q) {
-            double A = a.mval[q];
-            for (int k = a.kc_off[q]; k < a.kc_off[q + 1]; ++k) {
-                const double L = a.eder[9 * (size_t)a.kc_elem[k] + 8];
-                A += L * L * a.kc_geo[k];
-            }
             const int j = a.colidx[q];
+            const double A = a.aval[q], M = a.mval[q];
             const bool wall = a.is_wall[j];
 #pragma unroll
             for (int c = 0; c < NC; ++c) {
-                b[c] += a.mval[q] * a.f[NC * (size_t)j + c];
+                b[c] += M * a.f[NC * (size_t)j + c];
                 const double ax = A * a.x[NC * (size_t)j + c];
                 s[c] += ax;
                 if (wall) sw[c] += ax;
@@ -508,39 +514,50 @@ __global__ void __launch_bounds__(128) k_sur_residual(ResArgs a) {
     }
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
-        red[c][threadIdx.x] = r[c] * r[c];
-        red[NC + c][threadIdx.x] = b0[c] * b0[c];
-        red[2 * NC + c][threadIdx.x] = r[c];
-        red[3 * NC + c][threadIdx.x] = b0[c];
+        red[c][t] = r[c] * r[c];
+        red[NC + c][t] = b0[c] * b0[c];
+        red[2 * NC + c][t] = r[c];
+        red[3 * NC + c][t] = b0[c];
     }
     __syncthreads();
-    for (int w = 64; w > 0; w >>= 1) {
-        if (threadIdx.x < w)
+    for (int w = RES_ROWS / 2; w > 0; w >>= 1) {
+        if (t < w)
 #pragma unroll
-            for (int c = 0; c < 4 * NC; ++c) red[c][threadIdx.x] += red[c][threadIdx.x + w];
+            for (int v = 0; v < 4 * NC; ++v) red[v][t] += red[v][t + w];
         __syncthreads();
     }
-    if (threadIdx.x < 4 * NC) a.part[(size_t)blockIdx.x * 4 * NC + threadIdx.x] = red[threadIdx.x][0];
+    if (t < 4 * NC) a.part[(size_t)blockIdx.x * 4 * NC + t] = red[t][0];
 }
 
 // relative residuals (max over components): last[0] coarse (the check),
-// last[1] fine; the decision and the counters
-__global__ void k_sur_decide(const double* __restrict__ part, int nb, int mode, double tol, int* skip,
-                             unsigned long long* cnt, double* last) {
-    if (threadIdx.x != 0) return;
-    double rr[NC] = {0, 0, 0, 0, 0}, bb[NC] = {0, 0, 0, 0, 0}, cr[NC] = {0, 0, 0, 0, 0}, cb[NC] = {0, 0, 0, 0, 0};
-    for (int b = 0; b < nb; ++b)
+// last[1] fine; the decision and the counters. One warp: lane l sums the
+// partials of blocks l, l + 32, ..., then a shuffle tree in a fixed order.
+__global__ void __launch_bounds__(32) k_sur_decide(const double* __restrict__ part, int nb, int mode, double tol,
+                                                   int* skip, unsigned long long* cnt, double* last) {
+    const int lane = threadIdx.x;
+    double acc[4 * NC];
+#pragma unroll
+    for (int c = 0; c < 4 * NC; ++c) acc[c] = 0.0;
+    for (int b = lane; b < nb; b += 32) {
+        const double* q = part + (size_t)b * 4 * NC;
+#pragma unroll
         for (int c = 0; c < NC; ++c) {
-            const double* q = part + (size_t)b * 4 * NC;
-            rr[c] += q[c];
-            bb[c] += q[NC + c];
-            cr[c] += q[2 * NC + c] * q[2 * NC + c];
-            cb[c] += q[3 * NC + c] * q[3 * NC + c];
+            acc[c] += q[c];
+            acc[NC + c] += q[NC + c];
+            acc[2 * NC + c] += q[2 * NC + c] * q[2 * NC + c];
+            acc[3 * NC + c] += q[3 * NC + c] * q[3 * NC + c];
         }
+    }
+#pragma unroll
+    for (int c = 0; c < 4 * NC; ++c)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc[c] += __shfl_down_sync(0xffffffffu, acc[c], o);
+    if (lane != 0) return;
     double fine = 0.0, coarse = 0.0;
     for (int c = 0; c < NC; ++c) {
-        const double f = bb[c] > 0.0 ? sqrt(rr[c] / bb[c]) : sqrt(rr[c]);
-        const double g = cb[c] > 0.0 ? sqrt(cr[c] / cb[c]) : sqrt(cr[c]);
+        const double rr = acc[c], bb = acc[NC + c], cr = acc[2 * NC + c], cb = acc[3 * NC + c];
+        const double f = bb > 0.0 ? sqrt(rr / bb) : sqrt(rr);
+        const double g = cb > 0.0 ? sqrt(cr / cb) : sqrt(cr);
         fine = f > fine ? f : fine;
         coarse = g > coarse ? g : coarse;
     }
@@ -559,7 +576,7 @@ SurArgs sur_args(pdf_ctx* c) {
     return a;
 }
 
-int sur_blocks(pdf_ctx* c) { return (c->m.nn + 127) / 128; }
+int sur_blocks(pdf_ctx* c) { return (c->m.nn + RES_ROWS - 1) / RES_ROWS; }
 
 }  // namespace
 
@@ -587,11 +604,11 @@ int launch_surrogate(pdf_ctx* c) {
     const int blocks = std::min(2 * c->num_sms, std::max(1, (warps_needed + SUR_THREADS / 32 - 1) / (SUR_THREADS / 32)));
     k_sur_nodes<<<blocks, SUR_THREADS, SUR_SMEM, c->s>>>(a, c->sur_w, c->fe_g, c->fe_prop);
     ResArgs r;
-    r.nn = nn; r.rowptr = c->m.rowptr; r.colidx = c->m.colidx; r.mval = c->m.mval; r.kc_off = c->m.kc_off;
-    r.kc_elem = c->m.kc_elem; r.kc_geo = c->m.kc_geo; r.eder = c->eder; r.rep = c->m.rep; r.is_wall = c->m.is_wall;
+    r.nn = nn; r.rowptr = c->m.rowptr; r.colidx = c->m.colidx; r.mval = c->m.mval; r.aval = c->m.aval;
+    r.rep = c->m.rep; r.is_wall = c->m.is_wall;
     r.f = c->fe_f; r.x = c->fe_prop; r.part = c->sur_part;
     const int nb = sur_blocks(c);
-    k_sur_residual<<<nb, 128, 0, c->s>>>(r);
+    k_sur_residual<<<nb, RES_ROWS, 0, c->s>>>(r);
     k_sur_decide<<<1, 32, 0, c->s>>>(c->sur_part, nb, c->sur_mode, c->sur_tol, c->sur_skip, c->sur_cnt,
                                      c->sur_part + (size_t)nb * 4 * NC);
     c->launches += 3;

@@ -13,41 +13,50 @@ namespace {
 
 constexpr int SCAN_THREADS = 1024;
 
+// exclusive scan of the element counts by one block: warp w owns a contiguous
+// range of elements; pass 1 sums it with coalesced loads, warp 0 scans the 32
+// totals, pass 2 scans the range 32 elements at a time with a running carry
 __global__ void __launch_bounds__(SCAN_THREADS) k_scan(const int* __restrict__ cnt, int nt, int* off,
                                                        int* cursor) {
-    __shared__ int warp_tot[SCAN_THREADS / 32];
-    const int t = threadIdx.x;
-    const int chunk = (nt + SCAN_THREADS - 1) / SCAN_THREADS;
-    const int b0 = t * chunk, b1 = min(nt, b0 + chunk);
+    __shared__ int warp_ex[SCAN_THREADS / 32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    constexpr int NW = SCAN_THREADS / 32;
+    const int per = (nt + NW - 1) / NW;
+    const int b0 = min(nt, wid * per), b1 = min(nt, b0 + per);
     int s = 0;
-    for (int e = b0; e < b1; ++e) s += cnt[e];
-    // inclusive scan of the per-thread sums
-    const int lane = t & 31, wid = t >> 5;
-    int v = s;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int n = __shfl_up_sync(0xffffffffu, v, o);
-        if (lane >= o) v += n;
-    }
-    if (lane == 31) warp_tot[wid] = v;
+#pragma unroll 4
+    for (int e = b0 + lane; e < b1; e += 32) s += cnt[e];
+    s = __reduce_add_sync(0xffffffffu, s);
+    if (lane == 0) warp_ex[wid] = s;
     __syncthreads();
     if (wid == 0) {
-        int w = warp_tot[lane];
+        const int v = lane < NW ? warp_ex[lane] : 0;
+        int incl = v;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            const int n = __shfl_up_sync(0xffffffffu, w, o);
-            if (lane >= o) w += n;
+            const int y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
         }
-        warp_tot[lane] = w;
+        if (lane < NW) warp_ex[lane] = incl - v;
+        if (lane == 31) off[nt] = incl;
     }
     __syncthreads();
-    int run = v - s + (wid > 0 ? warp_tot[wid - 1] : 0);
-    for (int e = b0; e < b1; ++e) {
-        off[e] = run;
-        cursor[e] = run;
-        run += cnt[e];
+    int carry = warp_ex[wid];
+    for (int e0 = b0; e0 < b1; e0 += 32) {
+        const int e = e0 + lane;
+        const int c = e < b1 ? cnt[e] : 0;
+        int incl = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        if (e < b1) {
+            off[e] = carry + incl - c;
+            cursor[e] = carry + incl - c;
+        }
+        carry += __shfl_sync(0xffffffffu, incl, 31);
     }
-    if (t == SCAN_THREADS - 1) off[nt] = run;
 }
 
 __global__ void __launch_bounds__(256) k_count(int64_t n, const int* __restrict__ elem, int nt, int* cnt,

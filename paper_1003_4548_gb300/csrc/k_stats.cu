@@ -12,6 +12,8 @@
 //    the sorted segment into nb1 groups, re-sort each group by (V, id) and
 //    split into nb2, then by (W, id) into nb3; <phi|V> of a bin is its mean psi.
 // Reductions are FP64 (or compensated FP32 with PDF_FP32_KAHAN).
+#include <algorithm>
+
 #include "pdf_internal.cuh"
 #include "exact_sum.cuh"
 
@@ -121,6 +123,11 @@ struct MomArgs {
     int64_t scratch_n;
     int* status;
     int min_n;  // the block kernel only takes elements with more particles than this
+    // FP32 median path: elements too crowded for a warp, appended by the warp
+    // kernel (lcnt[0]: 512 < n <= 4096 in listA, lcnt[1]: n > 4096 in listB)
+    int* lcnt;
+    int* listA;
+    int* listB;
 };
 
 __device__ __forceinline__ int chunk_of(int r, int m, int G) {
@@ -130,13 +137,12 @@ __device__ __forceinline__ int chunk_of(int r, int m, int G) {
 }
 
 template <typename T, bool KAHAN>
-__global__ void __launch_bounds__(STATS_THREADS) k_moments(const MomArgs<T> a) {
+__device__ void moments_element(const MomArgs<T>& a, const int e) {
     using Acc = typename AccSel<T, KAHAN>::type;
     using R = typename AccSel<T, KAHAN>::R;
     extern __shared__ SortKey skeys[];
     __shared__ int gstart[256], gsize[256], nstart[256], nsize[256];
     __shared__ double mean_s[5];
-    const int e = blockIdx.x;
     const int s0 = a.off[e], n = a.off[e + 1] - s0;
     const int B = a.B;
     if (n <= a.min_n) return;  // done by the warp kernel
@@ -283,6 +289,21 @@ __global__ void __launch_bounds__(STATS_THREADS) k_moments(const MomArgs<T> a) {
     }
 }
 
+// one block per element (FP64 path, every element), or a persistent grid over
+// the listed crowded elements (FP32 median path)
+template <typename T, bool KAHAN>
+__global__ void __launch_bounds__(STATS_THREADS) k_moments(const MomArgs<T> a) {
+    if (a.listB == nullptr) {
+        moments_element<T, KAHAN>(a, blockIdx.x);
+        return;
+    }
+    const int cnt = a.lcnt[1];
+    for (int j = blockIdx.x; j < cnt; j += gridDim.x) {
+        moments_element<T, KAHAN>(a, a.listB[j]);
+        __syncthreads();
+    }
+}
+
 
 // ---------------------------------------------------------------------------
 // warp-per-element variant for FP32 particle state (segments up to
@@ -306,6 +327,10 @@ __device__ __forceinline__ uint32_t ord32(float v) {
     v = v + 0.0f;
     const uint32_t b = __float_as_uint(v);
     return (b >> 31) ? ~b : (b | 0x80000000u);
+}
+
+__device__ __forceinline__ float ord32_inv(uint32_t k) {
+    return (k >> 31) ? __uint_as_float(k & 0x7fffffffu) : __uint_as_float(~k);
 }
 
 __device__ __forceinline__ bool wgt(uint32_t ga, uint32_t va, uint32_t ia, uint32_t gb, uint32_t vb, uint32_t ib) {
@@ -491,8 +516,8 @@ struct SelSmem {
     uint32_t id[NMAX];
     unsigned char grp[NMAX];
     int hist[4][256];          // per-group histogram of the top 8 varying value bits
-    uint32_t cv[32], cid[32];  // candidates of the boundary bucket
-    int ncand;
+    uint32_t cv[4][32], cid[4][32];  // candidates of each group's boundary bucket
+    int nc[4], bkt[4], brank[4];
     uint32_t bv[4], bid[4];    // boundary keys of the level's groups
     int ired[8];               // team reduction scratch
     unsigned ured[2][NMAX > 512 ? 8 : 1];
@@ -590,18 +615,26 @@ __device__ __noinline__ void sel_split(SelSmem<NMAX>& S, int n, int ng, int (&gs
     const uint32_t diff = vmin ^ vmax;
     const int hb = diff ? 31 - __clz(diff) : -1;
     const uint32_t prefix = hb >= 0 ? (vmin & ~((2u << hb) - 1u)) : vmin;
-    const int shift = hb >= 7 ? hb - 7 : 0;
+    // 256 equal-width buckets between the smallest and largest value: a
+    // monotone map, so the bucket of the boundary holds few keys for any
+    // smooth distribution (a split of the order-preserving bits puts all
+    // values of one binade, e.g. the small ones of a component near zero,
+    // into one bucket)
+    const float fmin = ord32_inv(vmin), span = ord32_inv(vmax) - fmin;
+    const float sc = 256.f / span;
+    const float scale = (span > 0.f && sc <= 3.0e38f) ? sc : 0.f;
+    auto bucket_of = [&](uint32_t k) { return min(255, (int)((ord32_inv(k) - fmin) * scale)); };
     for (int q = T.tid; q < ng * 256; q += NT) (&S.hist[0][0])[q] = 0;
     T.sync();
-    for (int q = T.tid; q < n; q += NT) atomicAdd(&S.hist[S.grp[q]][(S.kv[q] - prefix) >> shift], 1);
+    for (int q = T.tid; q < n; q += NT) atomicAdd(&S.hist[S.grp[q]][bucket_of(S.kv[q])], 1);
     T.sync();
+    // boundary bucket of every group (warp 0: 8 buckets per lane, one group after another)
     int Ts[4];
-    for (int g = 0; g < ng; ++g) {
-        const int Tk = (gsize[g] + 1) / 2;
-        Ts[g] = Tk;
-        int bucket = 0, below = 0;
-        if (T.wid == 0) {  // bucket where the cumulative count reaches Tk (8 buckets per lane)
-            const int lane = T.lane;
+    for (int g = 0; g < ng; ++g) Ts[g] = (gsize[g] + 1) / 2;
+    if (T.wid == 0) {
+        const int lane = T.lane;
+        for (int g = 0; g < ng; ++g) {
+            const int Tk = Ts[g];
             int loc[8], tot = 0;
 #pragma unroll
             for (int k = 0; k < 8; ++k) {
@@ -626,37 +659,46 @@ __device__ __noinline__ void sel_split(SelSmem<NMAX>& S, int n, int ng, int (&gs
             }
             const unsigned who = __ballot_sync(0xffffffffu, mybucket >= 0);
             const int src = __ffs(who) - 1;
-            bucket = __shfl_sync(0xffffffffu, mybucket, src);
-            below = __shfl_sync(0xffffffffu, mybelow, src);
-            if (lane == 0) { S.ired[6] = bucket; S.ired[7] = below; S.ncand = 0; }
+            const int bucket = __shfl_sync(0xffffffffu, mybucket, src);
+            const int below = __shfl_sync(0xffffffffu, mybelow, src);
+            if (lane == 0) {
+                S.bkt[g] = bucket;
+                S.brank[g] = Tk - below - 1;  // 0-based rank of the boundary among the bucket's keys
+                S.nc[g] = 0;
+            }
         }
-        T.sync();
-        bucket = S.ired[6];
-        below = S.ired[7];
-        const int kc = S.hist[g][bucket];
-        const int rank = Tk - below - 1;  // 0-based rank of the boundary among the bucket's keys
-        if (kc <= 32) {
-            for (int q = T.tid; q < n; q += NT) {
-                if (S.grp[q] == g && (int)((S.kv[q] - prefix) >> shift) == bucket) {
-                    const int slot = atomicAdd(&S.ncand, 1);
-                    S.cv[slot] = S.kv[q];
-                    S.cid[slot] = S.id[q];
-                }
+    }
+    T.sync();
+    // candidates of all groups in one pass (groups whose bucket holds <= 32 keys)
+    for (int q = T.tid; q < n; q += NT) {
+        const int g = S.grp[q];
+        const int b = S.bkt[g];
+        if (S.hist[g][b] <= 32 && bucket_of(S.kv[q]) == b) {
+            const int slot = atomicAdd(&S.nc[g], 1);
+            S.cv[g][slot] = S.kv[q];
+            S.cid[g][slot] = S.id[q];
+        }
+    }
+    T.sync();
+    // exact rank of each candidate among its bucket's keys
+    for (int t = T.tid; t < 32 * ng; t += NT) {
+        const int g = t >> 5, j0 = t & 31;
+        const int kc = S.hist[g][S.bkt[g]];
+        if (kc <= 32 && j0 < kc) {
+            const uint32_t v = S.cv[g][j0], id = S.cid[g][j0];
+            int r = 0;
+            for (int j = 0; j < kc; ++j) {
+                const uint32_t vj = S.cv[g][j];
+                r += (vj < v || (vj == v && S.cid[g][j] < id)) ? 1 : 0;
             }
-            T.sync();
-            if (T.tid < kc) {
-                const uint32_t v = S.cv[T.tid], id = S.cid[T.tid];
-                int r = 0;
-                for (int j = 0; j < kc; ++j) {
-                    const uint32_t vj = S.cv[j];
-                    r += (vj < v || (vj == v && S.cid[j] < id)) ? 1 : 0;
-                }
-                if (r == rank) { S.bv[g] = v; S.bid[g] = id; }
-            }
-            T.sync();
-        } else {
+            if (r == S.brank[g]) { S.bv[g] = v; S.bid[g] = id; }
+        }
+    }
+    T.sync();
+    for (int g = 0; g < ng; ++g) {  // crowded buckets: bisection
+        if (S.hist[g][S.bkt[g]] > 32) {
             uint32_t bv, bid;
-            sel_bisect<NT>(S, n, g, Tk, gsize[g], prefix, hb, bv, bid);
+            sel_bisect<NT>(S, n, g, Ts[g], gsize[g], prefix, hb, bv, bid);
             if (T.tid == 0) { S.bv[g] = bv; S.bid[g] = bid; }
             T.sync();
         }
@@ -877,7 +919,13 @@ __global__ void __launch_bounds__(32 * WARPS_PER_BLOCK) k_moments_sel(const MomA
     const int e = blockIdx.x * WARPS_PER_BLOCK + w;
     if (e >= nt) return;
     const int s0 = a.off[e], n = a.off[e + 1] - s0;
-    if (n > 512) return;  // the block kernel takes it
+    if (n > 512) {  // a block kernel takes it
+        if (lane == 0) {
+            if (n <= 4096) a.listA[atomicAdd(&a.lcnt[0], 1)] = e;
+            else a.listB[atomicAdd(&a.lcnt[1], 1)] = e;
+        }
+        return;
+    }
     if (n == 0) {
         empty_element(a, e, lane, 32);
         return;
@@ -887,12 +935,15 @@ __global__ void __launch_bounds__(32 * WARPS_PER_BLOCK) k_moments_sel(const MomA
 
 // block of 256 threads per element: 512 < n <= 4096 (crowded elements)
 template <bool KAHAN>
-__global__ void __launch_bounds__(256) k_moments_sel_big(const MomArgs<float> a, int nt) {
+__global__ void __launch_bounds__(256) k_moments_sel_big(const MomArgs<float> a) {
     __shared__ SelSmem<4096> sm;
-    const int e = blockIdx.x;
-    const int s0 = a.off[e], n = a.off[e + 1] - s0;
-    if (n <= 512 || n > 4096) return;
-    sel_element<KAHAN, 256, 4096>(a, e, s0, n, sm);
+    const int cnt = a.lcnt[0];
+    for (int j = blockIdx.x; j < cnt; j += gridDim.x) {
+        const int e = a.listA[j];
+        const int s0 = a.off[e], n = a.off[e + 1] - s0;
+        sel_element<KAHAN, 256, 4096>(a, e, s0, n, sm);
+        __syncthreads();
+    }
 }
 
 template <typename T, bool KAHAN>
@@ -910,6 +961,7 @@ int run(pdf_ctx* c) {
     a.scratch_n = c->sort_scratch_n;
     a.status = c->d_status;
     a.min_n = -1;
+    a.lcnt = a.listA = a.listB = nullptr;
     if constexpr (sizeof(T) == 4) {
         // warp-per-element kernels for segments up to WARP_MAX_N particles:
         // median splits by bisection when every level halves (G <= 2), else a
@@ -921,8 +973,12 @@ int run(pdf_ctx* c) {
             // crowded elements (particle density drifts during a run) get their
             // own size class with a larger shared-memory slice per warp
             a.min_n = 4096;
+            a.lcnt = c->elist;
+            a.listA = c->elist + 2;
+            a.listB = c->elist + 2 + c->m.nt;
+            PDF_CUDA(c, cudaMemsetAsync(a.lcnt, 0, 2 * sizeof(int), c->s));
             k_moments_sel<KAHAN><<<blocks, 32 * WARPS_PER_BLOCK, 0, c->s>>>(a, c->m.nt);
-            k_moments_sel_big<KAHAN><<<c->m.nt, 256, 0, c->s>>>(a, c->m.nt);
+            k_moments_sel_big<KAHAN><<<std::min(c->m.nt, 2 * c->num_sms), 256, 0, c->s>>>(a);
             c->launches += 2;
         } else {
             k_moments_warp<KAHAN><<<blocks, 32 * WARPS_PER_BLOCK, 0, c->s>>>(a, c->m.nt);
@@ -935,7 +991,8 @@ int run(pdf_ctx* c) {
         cudaFuncSetAttribute(k_moments<T, KAHAN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         attr_set = true;
     }
-    k_moments<T, KAHAN><<<c->m.nt, STATS_THREADS, smem, c->s>>>(a);
+    const unsigned grid = a.listB ? (unsigned)std::min(c->m.nt, c->num_sms) : (unsigned)c->m.nt;
+    k_moments<T, KAHAN><<<grid, STATS_THREADS, smem, c->s>>>(a);
     ++c->launches;
     PDF_CUDA(c, cudaGetLastError());
     return PDF_OK;

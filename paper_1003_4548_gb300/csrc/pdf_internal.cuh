@@ -101,6 +101,8 @@ struct pdf_ctx {
     void* npackT = nullptr;
     void* epackT = nullptr;
     void* ecmT = nullptr;
+    // crowded-element lists of the FP32 moments path: 2 counters, then 2 x nt ids
+    int* elist = nullptr;
     // scratch of the moments kernel for elements above STATS_CAP particles
     SortKey* sort_scratch = nullptr;
     int64_t sort_scratch_n = 0;
