@@ -505,17 +505,17 @@ __global__ void __launch_bounds__(32 * WARPS_PER_BLOCK) k_moments_warp(const Mom
 //  * moments: exact fixed-point sums of the values and their products
 //    (integer pipes), correctly rounded to FP64 once per element;
 //  * bins: per level and per group the boundary key -- the ceil(m/2)-th
-//    smallest (value, id) -- by a bisection over the value bits, all groups
-//    of the level at once (counts packed two per 32-bit word, summed by warp
-//    reductions), then an id bisection when equal values straddle it;
+//    smallest (value, id) -- from a 256-bucket histogram over the value range
+//    (16-bit counts, two per word) and an exact ranking of the few keys in
+//    the boundary bucket; a bisection over the value bits (then the ids) when
+//    that bucket is crowded;
 //  * <phi|V>: exact fixed-point psi sums per bin (shared-memory atomics).
 // ---------------------------------------------------------------------------
 template <int NMAX>
 struct SelSmem {
     uint32_t kv[NMAX];  // order-preserving value bits of the current level
-    uint32_t id[NMAX];
     unsigned char grp[NMAX];
-    int hist[4][256];          // per-group histogram of the top 8 varying value bits
+    unsigned hist[4][128];     // per-group 256-bucket histogram, two 16-bit counts per word
     uint32_t cv[4][32], cid[4][32];  // candidates of each group's boundary bucket
     int nc[4], bkt[4], brank[4];
     uint32_t bv[4], bid[4];    // boundary keys of the level's groups
@@ -523,9 +523,15 @@ struct SelSmem {
     unsigned ured[2][NMAX > 512 ? 8 : 1];
     unsigned long long xred[NMAX > 512 ? 8 : 1][24];  // per-warp exact sums (12 x 128 bit), block teams only
     double mean[5];
+    double rd[3];              // <uu>, <vv>, <ww> of the element (bucket ranges of the splits)
     unsigned long long binsum[8];  // sum of psi per bin, unit 2^-(63 - log2 NMAX) (psi in [0, 1])
     int bincnt[8];
 };
+
+template <int NMAX>
+__device__ __forceinline__ int hcount(const SelSmem<NMAX>& S, int g, int b) {
+    return (int)((S.hist[g][b >> 1] >> (16 * (b & 1))) & 0xffffu);
+}
 
 // NT threads work on one element: a warp (NT = 32) or a whole block
 template <int NT>
@@ -571,12 +577,13 @@ __device__ __forceinline__ void x128_add_parts(Exact128& a, unsigned m, int e, b
 
 // #{keys of group g with (v < cv) or (v == cv and id < cid)} over the segment
 template <int NT, int NMAX>
-__device__ __noinline__ int sel_count(SelSmem<NMAX>& S, int n, int g, uint32_t cv, uint32_t cid) {
+__device__ __noinline__ int sel_count(SelSmem<NMAX>& S, const uint32_t* __restrict__ ids, int n, int g, uint32_t cv,
+                                      uint32_t cid) {
     const Team<NT> T;
     int c = 0;
     for (int q = T.tid; q < n; q += NT) {
         const uint32_t v = S.kv[q];
-        c += (S.grp[q] == g && (v < cv || (v == cv && S.id[q] < cid))) ? 1 : 0;
+        c += (S.grp[q] == g && (v < cv || (v == cv && ids[q] < cid))) ? 1 : 0;
     }
     return T.sum(c, S);
 }
@@ -585,61 +592,66 @@ __device__ __noinline__ int sel_count(SelSmem<NMAX>& S, int n, int g, uint32_t c
 // the Tk-th smallest (value, id); used when the histogram leaves too many
 // candidates in one bucket
 template <int NT, int NMAX>
-__device__ __noinline__ void sel_bisect(SelSmem<NMAX>& S, int n, int g, int Tk, int gsz, uint32_t prefix, int hb,
-                                        uint32_t& ans, uint32_t& idb) {
+__device__ __noinline__ void sel_bisect(SelSmem<NMAX>& S, const uint32_t* __restrict__ ids, int n, int g, int Tk,
+                                        int gsz, uint32_t prefix, int hb, uint32_t& ans, uint32_t& idb) {
     ans = prefix;
     for (int bit = hb; bit >= 0; --bit) {
         const uint32_t cand = ans | (1u << bit);
-        if (sel_count<NT>(S, n, g, cand, 0u) < Tk) ans = cand;
+        if (sel_count<NT>(S, ids, n, g, cand, 0u) < Tk) ans = cand;
     }
-    const int clt = sel_count<NT>(S, n, g, ans, 0u);
-    const int cle = ans == 0xffffffffu ? gsz : sel_count<NT>(S, n, g, ans + 1u, 0u);
+    const int clt = sel_count<NT>(S, ids, n, g, ans, 0u);
+    const int cle = ans == 0xffffffffu ? gsz : sel_count<NT>(S, ids, n, g, ans + 1u, 0u);
     idb = 0xffffffffu;
     if (cle - clt > 1 && Tk - clt < cle - clt) {
         uint32_t ia = 0u;
         for (int bit = 31; bit >= 0; --bit) {
             const uint32_t cand = ia | (1u << bit);
-            if (sel_count<NT>(S, n, g, ans, cand) - clt < Tk - clt) ia = cand;
+            if (sel_count<NT>(S, ids, n, g, ans, cand) - clt < Tk - clt) ia = cand;
         }
         idb = ia;
     }
 }
 
-// Split every group g < ng of the current level into 2g (lower half, the
-// ceil(m/2) smallest (value, id) keys) and 2g+1: a 256-bucket histogram of the
-// top 8 varying value bits per group locates the bucket of each group's
-// boundary; the few keys in that bucket are ranked exactly among themselves.
+// Bucket of a key for the histogram of one split level: 256 equal-width
+// buckets over [mean - 4 sd, mean + 4 sd] of the element's component,
+// clamped at both ends. The map is monotone, so the boundary (a median, always
+// within one sd of the mean) falls into a bucket with few keys for any smooth
+// distribution.
+struct Buckets {
+    float lo, sc;
+    __device__ int operator()(uint32_t k) const {
+        return max(0, min(255, (int)((ord32_inv(k) - lo) * sc)));
+    }
+};
+
+__device__ __forceinline__ Buckets make_buckets(double mean, double var) {
+    const double sd = var > 0.0 ? sqrt(var) : 0.0;
+    const double sc = sd > 0.0 ? 256.0 / (8.0 * sd) : 0.0;
+    Buckets b;
+    b.lo = (float)(mean - 4.0 * sd);
+    b.sc = (sc > 0.0 && sc < 1e30) ? (float)sc : 0.f;
+    return b;
+}
+
+// Boundary key of every group g < ng of the current level -- the Tk-th
+// smallest (value, id), Tk = ceil(m/2) -- from the level's histogram: the
+// bucket where the running count reaches Tk, then an exact rank of the keys
+// in that bucket (bisection over the value bits when it holds more than 32).
 template <int NT, int NMAX>
-__device__ __noinline__ void sel_split(SelSmem<NMAX>& S, int n, int ng, int (&gsize)[4], uint32_t vmin, uint32_t vmax) {
+__device__ __noinline__ void sel_boundaries(SelSmem<NMAX>& S, const uint32_t* __restrict__ ids, int n, int ng,
+                                            const int (&gsize)[4], const Buckets bk) {
     const Team<NT> T;
-    const uint32_t diff = vmin ^ vmax;
-    const int hb = diff ? 31 - __clz(diff) : -1;
-    const uint32_t prefix = hb >= 0 ? (vmin & ~((2u << hb) - 1u)) : vmin;
-    // 256 equal-width buckets between the smallest and largest value: a
-    // monotone map, so the bucket of the boundary holds few keys for any
-    // smooth distribution (a split of the order-preserving bits puts all
-    // values of one binade, e.g. the small ones of a component near zero,
-    // into one bucket)
-    const float fmin = ord32_inv(vmin), span = ord32_inv(vmax) - fmin;
-    const float sc = 256.f / span;
-    const float scale = (span > 0.f && sc <= 3.0e38f) ? sc : 0.f;
-    auto bucket_of = [&](uint32_t k) { return min(255, (int)((ord32_inv(k) - fmin) * scale)); };
-    for (int q = T.tid; q < ng * 256; q += NT) (&S.hist[0][0])[q] = 0;
-    T.sync();
-    for (int q = T.tid; q < n; q += NT) atomicAdd(&S.hist[S.grp[q]][bucket_of(S.kv[q])], 1);
-    T.sync();
-    // boundary bucket of every group (warp 0: 8 buckets per lane, one group after another)
-    int Ts[4];
-    for (int g = 0; g < ng; ++g) Ts[g] = (gsize[g] + 1) / 2;
-    if (T.wid == 0) {
+    if (T.wid == 0) {  // boundary bucket of every group (8 buckets per lane)
         const int lane = T.lane;
         for (int g = 0; g < ng; ++g) {
-            const int Tk = Ts[g];
+            const int Tk = (gsize[g] + 1) / 2;
             int loc[8], tot = 0;
 #pragma unroll
-            for (int k = 0; k < 8; ++k) {
-                loc[k] = S.hist[g][8 * lane + k];
-                tot += loc[k];
+            for (int k = 0; k < 4; ++k) {
+                const unsigned w2 = S.hist[g][4 * lane + k];
+                loc[2 * k] = (int)(w2 & 0xffffu);
+                loc[2 * k + 1] = (int)(w2 >> 16);
+                tot += loc[2 * k] + loc[2 * k + 1];
             }
             int incl = tot;
 #pragma unroll
@@ -663,27 +675,25 @@ __device__ __noinline__ void sel_split(SelSmem<NMAX>& S, int n, int ng, int (&gs
             const int below = __shfl_sync(0xffffffffu, mybelow, src);
             if (lane == 0) {
                 S.bkt[g] = bucket;
-                S.brank[g] = Tk - below - 1;  // 0-based rank of the boundary among the bucket's keys
+                S.brank[g] = Tk - below - 1;
                 S.nc[g] = 0;
             }
         }
     }
     T.sync();
-    // candidates of all groups in one pass (groups whose bucket holds <= 32 keys)
-    for (int q = T.tid; q < n; q += NT) {
+    for (int q = T.tid; q < n; q += NT) {  // candidates of all groups in one pass
         const int g = S.grp[q];
         const int b = S.bkt[g];
-        if (S.hist[g][b] <= 32 && bucket_of(S.kv[q]) == b) {
+        if (hcount(S, g, b) <= 32 && bk(S.kv[q]) == b) {
             const int slot = atomicAdd(&S.nc[g], 1);
             S.cv[g][slot] = S.kv[q];
-            S.cid[g][slot] = S.id[q];
+            S.cid[g][slot] = ids[q];
         }
     }
     T.sync();
-    // exact rank of each candidate among its bucket's keys
-    for (int t = T.tid; t < 32 * ng; t += NT) {
+    for (int t = T.tid; t < 32 * ng; t += NT) {  // exact rank among the bucket's keys
         const int g = t >> 5, j0 = t & 31;
-        const int kc = S.hist[g][S.bkt[g]];
+        const int kc = hcount(S, g, S.bkt[g]);
         if (kc <= 32 && j0 < kc) {
             const uint32_t v = S.cv[g][j0], id = S.cid[g][j0];
             int r = 0;
@@ -695,27 +705,23 @@ __device__ __noinline__ void sel_split(SelSmem<NMAX>& S, int n, int ng, int (&gs
         }
     }
     T.sync();
-    for (int g = 0; g < ng; ++g) {  // crowded buckets: bisection
-        if (S.hist[g][S.bkt[g]] > 32) {
+    for (int g = 0; g < ng; ++g) {  // crowded bucket (rare): bisection over the value bits
+        if (hcount(S, g, S.bkt[g]) > 32) {
+            unsigned vmin = 0xffffffffu, vmax = 0u;
+            for (int q = T.tid; q < n; q += NT) {
+                vmin = min(vmin, S.kv[q]);
+                vmax = max(vmax, S.kv[q]);
+            }
+            T.minmax(vmin, vmax, S);
+            const uint32_t diff = vmin ^ vmax;
+            const int hb = diff ? 31 - __clz(diff) : -1;
+            const uint32_t prefix = hb >= 0 ? (vmin & ~((2u << hb) - 1u)) : vmin;
             uint32_t bv, bid;
-            sel_bisect<NT>(S, n, g, Ts[g], gsize[g], prefix, hb, bv, bid);
+            sel_bisect<NT>(S, ids, n, g, (gsize[g] + 1) / 2, gsize[g], prefix, hb, bv, bid);
             if (T.tid == 0) { S.bv[g] = bv; S.bid[g] = bid; }
             T.sync();
         }
     }
-    for (int q = T.tid; q < n; q += NT) {
-        const int g = S.grp[q];
-        const uint32_t v = S.kv[q], bv = S.bv[g];
-        const bool low = v < bv || (v == bv && S.id[q] <= S.bid[g]);
-        S.grp[q] = (unsigned char)(2 * g + (low ? 0 : 1));
-    }
-    int ns[4] = {0, 0, 0, 0};
-    for (int g = 0; g < ng && 2 * g + 1 < 4; ++g) {
-        ns[2 * g] = Ts[g];
-        ns[2 * g + 1] = gsize[g] - Ts[g];
-    }
-    for (int g = 0; g < 4; ++g) gsize[g] = ns[g];
-    T.sync();
 }
 
 // exact moments of the segment; results of the 12 moments computed by warp 0
@@ -793,54 +799,63 @@ __device__ __noinline__ void exact_moments(const MomArgs<float>& a, int e, int s
         if (lane < 5) { a.emean[5 * e + lane] = val; S.mean[lane] = val; }
         else if (lane < 11) a.eR[6 * e + lane - 5] = val;
         else if (lane == 11) a.epsivar[e] = val;
+        if (lane >= 5 && lane < 8) S.rd[lane - 5] = val;
         if (lane == 0) a.en[e] = n;
     }
     T.sync();
 }
 
+// compensated-FP32 moments in one pass over the segment, on data shifted by
+// the segment's first particle (x - s, whose sums stay small when the mean is
+// large against the spread): sums of the shifted values and of their
+// products, then mean = s + S1/n and central moments S2/n - (S1/n)^2. With
+// NT > 32 warp 0 sums all particles.
 template <int NT, int NMAX>
 __device__ __noinline__ void kahan_moments(const MomArgs<float>& a, int e, int s0, int n, SelSmem<NMAX>& S) {
-    static_assert(NT == 32 || NT > 32, "");
     const Team<NT> T;
-    // compensated FP32 sums; with NT > 32 warp 0 sums all particles
     if (T.wid == 0) {
         const int lane = T.lane;
-        AccK m[5];
+        const float su = a.u[s0], sv = a.v[s0], sw = a.w[s0], sp = a.psi[s0];
+        AccK m[5], c2[7];
         for (int q = lane; q < n; q += 32) {
-            m[0].add(a.u[s0 + q]); m[1].add(a.v[s0 + q]); m[2].add(a.w[s0 + q]);
-            m[3].add(a.psi[s0 + q]); m[4].add(a.om[s0 + q]);
-        }
-        double mean[5];
-#pragma unroll
-        for (int q = 0; q < 5; ++q) {
-            warp_tree(m[q]);
-            mean[q] = __shfl_sync(0xffffffffu, m[q].value(), 0) / n;
-        }
-        const float mu = (float)mean[0], mv = (float)mean[1], mw = (float)mean[2], mp = (float)mean[3];
-        AccK c2[7];
-        for (int q = lane; q < n; q += 32) {
-            const float du = a.u[s0 + q] - mu, dv = a.v[s0 + q] - mv, dw = a.w[s0 + q] - mw, dp = a.psi[s0 + q] - mp;
+            const float du = a.u[s0 + q] - su, dv = a.v[s0 + q] - sv, dw = a.w[s0 + q] - sw;
+            const float dp = a.psi[s0 + q] - sp;
+            m[0].add(du); m[1].add(dv); m[2].add(dw); m[3].add(dp); m[4].add(a.om[s0 + q]);
             c2[0].add(du * du); c2[1].add(dv * dv); c2[2].add(dw * dw);
             c2[3].add(du * dv); c2[4].add(du * dw); c2[5].add(dv * dw); c2[6].add(dp * dp);
         }
 #pragma unroll
+        for (int q = 0; q < 5; ++q) warp_tree(m[q]);
+#pragma unroll
         for (int q = 0; q < 7; ++q) warp_tree(c2[q]);
         if (lane == 0) {
             const double inv_n = 1.0 / n;
+            const double d0 = m[0].value() * inv_n, d1 = m[1].value() * inv_n, d2 = m[2].value() * inv_n;
+            const double d3 = m[3].value() * inv_n;
+            const double mean[5] = {su + d0, sv + d1, sw + d2, sp + d3, m[4].value() * inv_n};
+            const double R[6] = {c2[0].value() * inv_n - d0 * d0, c2[1].value() * inv_n - d1 * d1,
+                                 c2[2].value() * inv_n - d2 * d2, c2[3].value() * inv_n - d0 * d1,
+                                 c2[4].value() * inv_n - d0 * d2, c2[5].value() * inv_n - d1 * d2};
             a.en[e] = n;
             for (int q = 0; q < 5; ++q) { a.emean[5 * e + q] = mean[q]; S.mean[q] = mean[q]; }
-            for (int q = 0; q < 6; ++q) a.eR[6 * e + q] = c2[q].value() * inv_n;
-            a.epsivar[e] = c2[6].value() * inv_n;
+            for (int q = 0; q < 6; ++q) a.eR[6 * e + q] = R[q];
+            for (int q = 0; q < 3; ++q) S.rd[q] = R[q];
+            a.epsivar[e] = c2[6].value() * inv_n - d3 * d3;
         }
     }
     T.sync();
 }
 
-// one element per team of NT threads (a warp: WPB elements per block; a block)
+// one element per team of NT threads (a warp: WPB elements per block; a block).
+// Passes over the segment: moments; then per split level one pass that
+// applies the previous level's boundaries, loads the level's component and
+// fills its histogram, and one candidate pass; a last pass applies the last
+// level and sums psi per bin.
 template <bool KAHAN, int NT, int NMAX>
 __device__ void sel_element(const MomArgs<float>& a, int e, int s0, int n, SelSmem<NMAX>& S) {
     const Team<NT> T;
     const int B = a.B;
+    const uint32_t* __restrict__ ids = a.id + s0;
     if (KAHAN) kahan_moments<NT>(a, e, s0, n, S);
     else exact_moments<NT>(a, e, s0, n, S);
     if (n < B) {
@@ -851,34 +866,52 @@ __device__ void sel_element(const MomArgs<float>& a, int e, int s0, int n, SelSm
         }
         return;
     }
-    for (int q = T.tid; q < n; q += NT) {
-        S.id[q] = a.id[s0 + q];
-        S.grp[q] = 0;
-    }
     int gsize[4] = {n, 0, 0, 0};
     const int G[3] = {a.G0, a.G1, a.G2};
-    int ng = 1;
+    int ng = 0;  // groups of the previous level (0: none yet)
     for (int d = 0; d < 3; ++d) {
         if (G[d] == 1) continue;
         const float* comp = d == 0 ? a.u : (d == 1 ? a.v : a.w);
-        unsigned vmin = 0xffffffffu, vmax = 0u;
+        const Buckets bk = make_buckets(S.mean[d], S.rd[d]);
+        const int ngl = ng == 0 ? 1 : 2 * ng;  // groups of this level
+        for (int q = T.tid; q < ngl * 128; q += NT) (&S.hist[0][0])[q] = 0u;
+        T.sync();
         for (int q = T.tid; q < n; q += NT) {
+            int g = 0;
+            if (ng) {
+                const int gp = S.grp[q];
+                const uint32_t v = S.kv[q], bv = S.bv[gp];
+                g = 2 * gp + ((v < bv || (v == bv && ids[q] <= S.bid[gp])) ? 0 : 1);
+            }
+            S.grp[q] = (unsigned char)g;
             const uint32_t k = ord32(comp[s0 + q]);
             S.kv[q] = k;
-            vmin = min(vmin, k);
-            vmax = max(vmax, k);
+            const int b = bk(k);
+            atomicAdd(&S.hist[g][b >> 1], 1u << (16 * (b & 1)));
         }
-        T.minmax(vmin, vmax, S);
+        if (ng) {  // sizes of the new groups: the lower half takes the extra key
+            int ns[4] = {0, 0, 0, 0};
+            for (int g = 0; g < ng; ++g) {
+                ns[2 * g] = (gsize[g] + 1) / 2;
+                ns[2 * g + 1] = gsize[g] - ns[2 * g];
+            }
+            for (int g = 0; g < 4; ++g) gsize[g] = ns[g];
+        }
+        ng = ngl;
         T.sync();
-        sel_split<NT>(S, n, ng, gsize, vmin, vmax);
-        ng *= 2;
+        sel_boundaries<NT>(S, ids, n, ng, gsize, bk);
     }
     // bins, and <phi|V> per bin: exact fixed-point sums of psi
     constexpr int UNIT = NMAX <= 512 ? 54 : 51;  // psi <= 1 and n <= NMAX keep the sums below 2^63
     if (T.tid < 8) { S.binsum[T.tid] = 0ull; S.bincnt[T.tid] = 0; }
     T.sync();
     for (int q = T.tid; q < n; q += NT) {
-        const int bn = S.grp[q];
+        int bn = 0;
+        if (ng) {
+            const int gp = S.grp[q];
+            const uint32_t v = S.kv[q], bv = S.bv[gp];
+            bn = 2 * gp + ((v < bv || (v == bv && ids[q] <= S.bid[gp])) ? 0 : 1);
+        }
         a.bin[s0 + q] = (unsigned char)bn;
         unsigned m;
         int ex;
@@ -913,7 +946,7 @@ __device__ void empty_element(const MomArgs<float>& a, int e, int tid, int nt_te
 
 // warp per element: 0 <= n <= 512
 template <bool KAHAN>
-__global__ void __launch_bounds__(32 * WARPS_PER_BLOCK) k_moments_sel(const MomArgs<float> a, int nt) {
+__global__ void __launch_bounds__(32 * WARPS_PER_BLOCK, KAHAN ? 8 : 4) k_moments_sel(const MomArgs<float> a, int nt) {
     __shared__ SelSmem<512> sm[WARPS_PER_BLOCK];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int e = blockIdx.x * WARPS_PER_BLOCK + w;
