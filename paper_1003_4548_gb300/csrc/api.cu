@@ -382,16 +382,19 @@ int alloc_particles(pdf_ctx* c, int64_t n) {
     c->conv_buf = nullptr;
     c->cap = 0;
     const size_t ts = c->prec == 0 ? 8 : 4;
+    // whole tiles of 256 particles: the particle kernel stages tiles with
+    // 16-byte-granular bulk copies that may run past n inside the allocation
+    const int64_t na = (n + 255) / 256 * 256;
     for (int k = 0; k < 7; ++k) {
-        PDF_CUDA(c, cudaMalloc(&c->stA[k], ts * n));
-        PDF_CUDA(c, cudaMalloc(&c->stB[k], ts * n));
+        PDF_CUDA(c, cudaMalloc(&c->stA[k], ts * na));
+        PDF_CUDA(c, cudaMalloc(&c->stB[k], ts * na));
     }
-    TRY(dalloc(c, &c->idA, n));
-    TRY(dalloc(c, &c->idB, n));
-    TRY(dalloc(c, &c->elemA, n));
-    TRY(dalloc(c, &c->elemB, n));
-    TRY(dalloc(c, &c->bin, n));
-    PDF_CUDA(c, cudaMemset(c->bin, 0, n));
+    TRY(dalloc(c, &c->idA, na));
+    TRY(dalloc(c, &c->idB, na));
+    TRY(dalloc(c, &c->elemA, na));
+    TRY(dalloc(c, &c->elemB, na));
+    TRY(dalloc(c, &c->bin, na));
+    PDF_CUDA(c, cudaMemset(c->bin, 0, na));
     TRY(dalloc(c, &c->sort_scratch, 2 * (size_t)n));
     c->sort_scratch_n = 2 * n;
     c->conv_bytes = sizeof(double) * (size_t)n;

@@ -11,6 +11,8 @@
 //   boundaries: periodic seams, symmetry top, wall reflections
 //   (Eqs. wall-normal-velocity .. wall-omega, or specular no-slip), the
 //   element walk to the new host element, and the continuous source.
+#include <algorithm>
+
 #include "pdf_internal.cuh"
 
 namespace {
@@ -37,14 +39,15 @@ __device__ __forceinline__ void load_pack(const T* __restrict__ p, T (&o)[W]) {
 }
 
 // Gaussian pair from two uniforms in (0, 1]. FP64: Box & Muller with the
-// accurate functions. FP32: the angle 2 pi ub is taken as pi (2 ub - 1) in
-// [-pi, pi], where the hardware sine/cosine are accurate to ~4e-7 absolute,
-// and z = -r cos(pi (2 ub - 1)) = r cos(2 pi ub) (same for the sine).
+// accurate functions. FP32: the hardware logarithm, and the angle 2 pi ub
+// taken as pi (2 ub - 1) in [-pi, pi], where the hardware sine/cosine are
+// accurate to ~4e-7 absolute; z = -r cos(pi (2 ub - 1)) = r cos(2 pi ub)
+// (same for the sine).
 __device__ __forceinline__ void gauss_pair(double ua, double ub, double& za, double& zb) {
     box_muller(ua, ub, za, zb);
 }
 __device__ __forceinline__ void gauss_pair(float ua, float ub, float& za, float& zb) {
-    const float m2l = -2.0f * logf(ua);
+    const float m2l = -2.0f * __logf(ua);  // absolute error < 4e-7 on (0, 1]: within the FP32 step tolerance
     const float r = m2l > 0.f ? m2l * rsqrtf(m2l) : 0.f;
     const float th = 3.14159265358979f * fmaf(2.0f, ub, -1.0f);
     float sn, cs;
@@ -120,15 +123,11 @@ __device__ void reflect(const StepArgs<T>& a, int tag, T nx, T ny, const double*
     om = om * t_exp<T>(a.beta * Vn / (a.yp * Omp));
 }
 
+// one particle-step of particle i whose state at step n was staged in
+// shared memory; writes the state at step n+1 in place
 template <typename T>
-__global__ void __launch_bounds__(256) k_step(const StepArgs<T> a) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= (int)a.n) return;
-    const int e0 = a.elem[i];
-    const T x = a.x[i], y = a.y[i];
-    T u = a.u[i], v = a.v[i], w = a.w[i], om = a.om[i], psi = a.psi[i];
-    const uint32_t pid = a.id[i];
-    const int b = a.bin[i];
+__device__ __forceinline__ void advance_particle(const StepArgs<T>& a, const int i, const T x, const T y, T u, T v,
+                                                 T w, T om, T psi, const uint32_t pid, const int e0, const int b) {
 
     // barycentric coordinates in the host element
     T g[EGEO_W];
@@ -277,6 +276,110 @@ __global__ void __launch_bounds__(256) k_step(const StepArgs<T> a) {
     if ((threadIdx.x & 31) == __ffs(mask) - 1) atomicAdd(&a.cnt[e], __popc(mask));
 }
 
+// ---------------------------------------------------------------------------
+// The step kernel: a persistent grid over tiles of TILE consecutive particles.
+// Thread 0 of a block stages the next tile's state (seven state arrays, id,
+// element, bin) into shared memory with bulk asynchronous copies that complete
+// on an mbarrier, while the block advances the current tile, so the load
+// latency of the HBM-streamed state overlaps the arithmetic. The arrays are
+// allocated in whole tiles, so every copy starts 16-byte aligned and its size
+// is rounded up to 16 bytes inside the allocation.
+// ---------------------------------------------------------------------------
+constexpr int TILE = 256;
+
+template <typename T>
+struct Stage {
+    T s[7][TILE];  // x y u v w omega psi
+    uint32_t id[TILE];
+    int elem[TILE];
+    unsigned char bin[TILE];
+};
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void bulk_to_smem(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+    uint64_t g;
+    asm("cvta.to.global.u64 %0, %1;" : "=l"(g) : "l"(src));
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(smem_addr(dst)), "l"(g), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// bounded wait for a phase of the barrier (ST_BARRIER if it never completes)
+__device__ __forceinline__ void mbar_wait(uint64_t* bar, unsigned parity, int* status) {
+    for (int spin = 0; !mbar_try_wait(bar, parity); ++spin) {
+        if (spin > (1 << 20)) {
+            set_status(status, ST_BARRIER);
+            break;
+        }
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void stage_tile(const StepArgs<T>& a, Stage<T>& st, uint64_t* bar, int64_t base, int cnt) {
+    const unsigned bt = (unsigned)(((size_t)cnt * sizeof(T) + 15) & ~(size_t)15);
+    const unsigned b4 = (unsigned)(((size_t)cnt * 4 + 15) & ~(size_t)15);
+    const unsigned b1 = (unsigned)((cnt + 15) & ~15);
+    mbar_expect_tx(bar, 7 * bt + 2 * b4 + b1);
+    const T* src[7] = {a.x, a.y, a.u, a.v, a.w, a.om, a.psi};
+#pragma unroll
+    for (int k = 0; k < 7; ++k) bulk_to_smem(st.s[k], src[k] + base, bt, bar);
+    bulk_to_smem(st.id, a.id + base, b4, bar);
+    bulk_to_smem(st.elem, a.elem + base, b4, bar);
+    bulk_to_smem(st.bin, a.bin + base, b1, bar);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(TILE) k_step(const StepArgs<T> a) {
+    __shared__ __align__(128) Stage<T> st[2];
+    __shared__ __align__(8) uint64_t bar[2];
+    const int64_t ntiles = (a.n + TILE - 1) / TILE;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    int64_t t = blockIdx.x;
+    if (threadIdx.x == 0 && t < ntiles) stage_tile(a, st[0], &bar[0], t * TILE, (int)min((int64_t)TILE, a.n - t * TILE));
+    for (int k = 0; t < ntiles; t += gridDim.x, ++k) {
+        const int s = k & 1;
+        const int64_t tn = t + gridDim.x;
+        if (threadIdx.x == 0 && tn < ntiles) {
+            // the other stage was released by every thread at the end of the last tile
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            stage_tile(a, st[s ^ 1], &bar[s ^ 1], tn * TILE, (int)min((int64_t)TILE, a.n - tn * TILE));
+        }
+        mbar_wait(&bar[s], (unsigned)((k >> 1) & 1), a.status);
+        const int64_t i = t * TILE + threadIdx.x;
+        if (i < a.n) {
+            const Stage<T>& q = st[s];
+            const int j = threadIdx.x;
+            advance_particle(a, (int)i, q.s[0][j], q.s[1][j], q.s[2][j], q.s[3][j], q.s[4][j], q.s[5][j], q.s[6][j],
+                             q.id[j], q.elem[j], (int)q.bin[j]);
+        }
+        __syncthreads();
+    }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) k_seed(int64_t n, int ppe, uint2 key, const int* __restrict__ tri,
                                               const double* __restrict__ xy,
@@ -361,13 +464,20 @@ StepArgs<T> step_args(pdf_ctx* c, double dt) {
 int launch_particle_step(pdf_ctx* c, double dt) {
     PDF_CUDA(c, cudaMemsetAsync(c->cnt, 0, sizeof(int) * c->m.nt, c->s));
     if (c->np == 0) return PDF_OK;
-    const int threads = 256;
-    const unsigned blocks = (unsigned)((c->np + threads - 1) / threads);
+    // persistent grid: the resident blocks of every SM
+    if (c->step_blocks == 0) {
+        int per_sm = 0;
+        if (c->prec == 0) PDF_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step<double>, TILE, 0));
+        else PDF_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step<float>, TILE, 0));
+        c->step_blocks = std::max(1, per_sm) * c->num_sms;
+    }
+    const int64_t ntiles = (c->np + TILE - 1) / TILE;
+    const unsigned blocks = (unsigned)std::min<int64_t>(ntiles, c->step_blocks);
     timing_begin(c, PDF_K_PARTICLE);
     if (c->prec == 0)
-        k_step<double><<<blocks, threads, 0, c->s>>>(step_args<double>(c, dt));
+        k_step<double><<<blocks, TILE, 0, c->s>>>(step_args<double>(c, dt));
     else
-        k_step<float><<<blocks, threads, 0, c->s>>>(step_args<float>(c, dt));
+        k_step<float><<<blocks, TILE, 0, c->s>>>(step_args<float>(c, dt));
     ++c->launches;
     timing_end(c, PDF_K_PARTICLE);
     PDF_CUDA(c, cudaGetLastError());

@@ -130,6 +130,7 @@ struct pdf_ctx {
     Timing tm;
     int timing = 0;
     int64_t launches = 0;  // kernels launched by this context
+    int step_blocks = 0;   // persistent grid of the particle kernel
     std::string err;
     int num_sms = 0;
 };
