@@ -197,6 +197,55 @@ int pdf_reset_timing(pdf_ctx* c);
 int64_t pdf_launch_count(const pdf_ctx* c);
 
 /* ---------------------------------------------------------------------------
+ * Many independent cases (the paper runs one canyon at a time; this serves
+ * batches of cases with their own meshes, particle counts, seeds and sources).
+ * ------------------------------------------------------------------------- */
+typedef struct pdf_batch pdf_batch;
+
+/* Capture two time steps of every context (each with its own dt) into one
+ * CUDA graph launched on cuda_stream: the contexts' steps run as parallel
+ * branches; their cooperative CG launches are chained so that no two of them
+ * are resident side by side. (Two steps: the particle state moves between two
+ * buffers every step, so a pair of steps starts and ends in the same ones.) Requirements: n >= 1, every context seeded with
+ * estimated statistics and created with its own non-NULL stream, distinct
+ * from the others and from cuda_stream (PDF_ERR_ARG otherwise). Nothing is
+ * executed by this call; per-context launch set-up (grids, attributes) is
+ * done first. The contexts must not be stepped or destroyed by other calls
+ * while the batch exists. Returns PDF_ERR_CUDA if the capture or the
+ * instantiation fails (message in pdf_last_error(NULL)). */
+int pdf_batch_create(pdf_ctx* const* ctx, const double* dt, int32_t n, void* cuda_stream, pdf_batch** out);
+
+/* Advance every context by nsteps (even; PDF_ERR_ARG otherwise): nsteps/2
+ * launches of the graph on the batch stream (asynchronous). */
+int pdf_batch_step(pdf_batch* b, int32_t nsteps);
+
+/* Wait for the batch stream, then report the first failing context's status
+ * (pdf_sync of each; its index in *failed, -1 if none). */
+int pdf_batch_sync(pdf_batch* b, int32_t* failed);
+
+void pdf_batch_destroy(pdf_batch* b);
+
+/* Launch shapes chosen by pdf_autotune for one context. */
+typedef struct pdf_tuning {
+    int32_t step_blocks_per_sm;  /* persistent grid of the particle kernel */
+    int32_t scatter_threads;     /* block size of the re-sort scatter */
+    int32_t cg_rows_per_block;   /* elliptic CG block (block-Jacobi) size, 0 without elliptic relaxation */
+    double ms_particle, ms_sort, ms_elliptic;  /* best per-step times (CUDA events) */
+} pdf_tuning;
+
+/* Autotuner: times the candidate launch shapes of the particle kernel
+ * (1 .. resident blocks per SM), of the scatter (128, 256, 512 threads) and
+ * of the CG block (128, 160, 192 rows, those whose grid is co-resident) by
+ * running steps_per_trial steps of dt for each candidate, one parameter at a
+ * time, and keeps the fastest. The context advances by every step it times
+ * (use it as warm-up). Results of a step do not depend on the particle-kernel
+ * grid or on the scatter block size for the FP64 and exact-FP32 reductions
+ * (the compensated-FP32 sums depend on the order of the particles inside an
+ * element); the CG block size changes the preconditioner, so wp changes
+ * within the CG tolerance. out may be NULL. */
+int pdf_autotune(pdf_ctx* c, double dt, int32_t steps_per_trial, pdf_tuning* out);
+
+/* ---------------------------------------------------------------------------
  * Learned surrogate of the elliptic-relaxation solve (Eqs. elliptic-relaxation,
  * Gij, C0). The paper solves Eq. elliptic-relaxation by finite elements every
  * step. This optional part maps local node quantities to wp_ij with a small

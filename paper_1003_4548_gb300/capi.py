@@ -56,11 +56,17 @@ EXPORTS = ("pdf_default_params", "pdf_init_mesh", "pdf_seed_particles", "pdf_set
            "pdf_destroy", "pdf_sort_by_element_static", "pdf_mlp_work_floats", "pdf_mlp_forward",
            "pdf_mlp_loss_grad", "pdf_mlp_adam", "pdf_mlp_column_stats", "pdf_mlp_gather_rows",
            "pdf_mlp_standardize", "pdf_surrogate_rows", "pdf_surrogate_harvest", "pdf_set_surrogate",
-           "pdf_surrogate_stats")
+           "pdf_surrogate_stats", "pdf_batch_create", "pdf_batch_step", "pdf_batch_sync", "pdf_batch_destroy",
+           "pdf_autotune")
 
 MLP_IN, MLP_HIDDEN, MLP_OUT, MLP_NPARAM, MLP_NNORM = 10, 64, 5, 9349, 30
 
 SORT_STATIC_MAX_ELEMENTS = 131072  # PDF_SORT_STATIC_MAX_ELEMENTS
+
+
+class pdf_tuning(C.Structure):
+    _fields_ = [("step_blocks_per_sm", C.c_int32), ("scatter_threads", C.c_int32), ("cg_rows_per_block", C.c_int32),
+                ("ms_particle", C.c_double), ("ms_sort", C.c_double), ("ms_elliptic", C.c_double)]
 
 
 def library_path() -> str:
@@ -114,6 +120,12 @@ def lib(allow_build: bool = True):
         L.pdf_surrogate_harvest.argtypes = [vp, vp, vp]
         L.pdf_set_surrogate.argtypes = [vp, C.c_int32, P(C.c_float), P(C.c_float), C.c_double]
         L.pdf_surrogate_stats.argtypes = [vp, P(C.c_int64), P(C.c_int64), d]
+        L.pdf_batch_create.argtypes = [P(vp), d, C.c_int32, vp, P(vp)]
+        L.pdf_batch_step.argtypes = [vp, C.c_int32]
+        L.pdf_batch_sync.argtypes = [vp, i32]
+        L.pdf_batch_destroy.argtypes = [vp]
+        L.pdf_batch_destroy.restype = None
+        L.pdf_autotune.argtypes = [vp, C.c_double, C.c_int32, P(pdf_tuning)]
         _lib = L
         return L
 
@@ -317,6 +329,11 @@ class Canyon:
         self._check(lib().pdf_surrogate_stats(self._h, C.byref(a), C.byref(b), r))
         return a.value, b.value, (r[0], r[1])
 
+    def autotune(self, dt: float, steps_per_trial: int = 3) -> dict:
+        t = pdf_tuning()
+        self._check(lib().pdf_autotune(self._h, dt, steps_per_trial, C.byref(t)))
+        return {n: getattr(t, n) for n, _ in pdf_tuning._fields_}
+
     def set_timing(self, on: bool):
         self._check(lib().pdf_set_timing(self._h, 1 if on else 0))
 
@@ -328,3 +345,38 @@ class Canyon:
 
     def reset_timing(self):
         self._check(lib().pdf_reset_timing(self._h))
+
+
+class Batch:
+    """One CUDA graph holding a time step of several contexts (pdf_batch_*)."""
+
+    def __init__(self, canyons, dts, stream: int):
+        L = lib()
+        self.canyons = list(canyons)
+        hs = (C.c_void_p * len(self.canyons))(*[c.handle.value for c in self.canyons])
+        dt = (C.c_double * len(self.canyons))(*[float(x) for x in dts])
+        h = C.c_void_p()
+        st = L.pdf_batch_create(hs, dt, len(self.canyons), C.c_void_p(stream), C.byref(h))
+        if st != PDF_OK:
+            raise PdfError(st, L.pdf_last_error(None).decode())
+        self._h = h
+
+    def step(self, nsteps: int = 1):
+        _chk(lib().pdf_batch_step(self._h, nsteps), "pdf_batch_step")
+
+    def sync(self):
+        f = C.c_int32(-1)
+        st = lib().pdf_batch_sync(self._h, C.byref(f))
+        if st != PDF_OK:
+            raise PdfError(st, f"case {f.value}: " + lib().pdf_last_error(self.canyons[f.value].handle).decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().pdf_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -67,6 +67,8 @@ __global__ void k_from_double(const double* __restrict__ s, T* d, int64_t n) {
     if (i < n) d[i] = (T)s[i];
 }
 
+__global__ void k_set_u32(uint32_t* p, uint32_t v) { *p = v; }
+
 double orient(double px, double py, double qx, double qy, double rx, double ry) {
     return (qx - px) * (ry - py) - (qy - py) * (rx - px);
 }
@@ -345,6 +347,8 @@ int alloc_stats(pdf_ctx* c) {
     PDF_CUDA(c, cudaMemset(c->npsivar, 0, sizeof(double) * nn));
     PDF_CUDA(c, cudaMemset(c->nwp, 0, sizeof(double) * 5 * nn));
     TRY(dalloc(c, &c->d_status, 1));
+    TRY(dalloc(c, &c->d_step, 1));
+    PDF_CUDA(c, cudaMemset(c->d_step, 0, sizeof(uint32_t)));
     PDF_CUDA(c, cudaMemset(c->d_status, 0, sizeof(int)));
     PDF_CUDA(c, cudaMallocHost((void**)&c->h_status, sizeof(int)));
     if (c->p.wall_model == PDF_ELLIPTIC_RELAXATION) {
@@ -405,6 +409,13 @@ int alloc_particles(pdf_ctx* c, int64_t n) {
 }
 
 }  // namespace
+
+int set_device_step(pdf_ctx* c) {
+    k_set_u32<<<1, 1, 0, c->s>>>(c->d_step, (uint32_t)c->step);
+    ++c->launches;
+    PDF_CUDA(c, cudaGetLastError());
+    return PDF_OK;
+}
 
 int launch_to_double(pdf_ctx* c, const void* src, double* dst, int64_t n) {
     if (n == 0) return PDF_OK;
@@ -469,6 +480,7 @@ int pdf_init_mesh(const pdf_params* p, const double* xy, int32_t nnode, const in
     cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, dev);
     int st = build_mesh(c, xy, nnode, tri, ntri, edge_tag, periodic_pair);
     if (st == PDF_OK) st = alloc_stats(c);
+    if (st == PDF_OK) st = prepare_moments(c);
     if (st != PDF_OK) {
         g_init_error = c->err;
         pdf_destroy(c);
@@ -486,6 +498,7 @@ int pdf_seed_particles(pdf_ctx* c, int32_t per_element) {
     TRY(launch_seed(c, per_element));
     TRY(launch_count_and_sort(c));
     c->step = 0;
+    TRY(set_device_step(c));
     c->seeded = true;
     c->stats_valid = false;
     return PDF_OK;
@@ -518,6 +531,7 @@ int pdf_set_particles(pdf_ctx* c, int32_t n, const double* x, const double* y, c
     if (st == PDF_ERR_CAPACITY) return fail(c, PDF_ERR_ARG, "element id out of range");
     if (st != PDF_OK) return st;
     c->step = step;
+    TRY(set_device_step(c));
     c->seeded = true;
     c->stats_valid = false;
     return PDF_OK;
@@ -538,7 +552,7 @@ int pdf_step(pdf_ctx* c, double dt, int32_t nsteps) {
     if (!c->stats_valid) return fail(c, PDF_ERR_STATE, "statistics not estimated");
     for (int s = 0; s < nsteps; ++s) {
         TRY(launch_particle_step(c, dt));
-        TRY(launch_sort(c));
+        TRY(launch_sort(c, true));
         c->step++;
         TRY(launch_moments(c));
         TRY(launch_fields(c));
@@ -666,7 +680,7 @@ void pdf_destroy(pdf_ctx* c) {
                    c->emean, c->eR, c->epsivar, c->ecm, c->nwt, c->nmean, c->nR, c->nke, c->npsivar, c->eder,
                    c->ngrad, c->npack, c->nwp, c->npackT, c->epackT, c->ecmT, c->sort_scratch, c->fe_f, c->fe_g,
                    c->fe_prop, c->fe_z, c->fe_part, c->fe_bar, c->fe_iters, c->d_status,
-                   c->conv_buf, c->elist, c->sur_w, c->sur_rows, c->sur_skip, c->sur_cnt, c->sur_part};
+                   c->conv_buf, c->elist, c->d_step, c->sur_w, c->sur_rows, c->sur_skip, c->sur_cnt, c->sur_part};
     for (void* p : dev) cudaFree(p);
     for (int k = 0; k < 7; ++k) {
         cudaFree(c->stA[k]);

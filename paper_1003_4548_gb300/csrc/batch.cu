@@ -1,0 +1,223 @@
+// batch.cu -- many independent cases in one CUDA graph, and the autotuner of
+// the launch shapes.
+//
+// A batch captures two pdf_steps of every context into a single graph: a fork
+// event on the batch stream, every context's steps on its own stream, a join
+// back. Replaying the graph launches all cases' kernels with one call; cases
+// of uneven size overlap on the GPU. Two steps, because the re-sort moves the
+// particle state between two buffers and swaps them on the host: a captured
+// pair of steps starts and ends in the same buffers. The step counter of every context lives
+// on the device (advanced by the re-sort), so replays draw new Philox streams.
+// Cooperative CG grids are chained with events (one resident at a time): two
+// partially resident cooperative grids waiting at their grid barriers could
+// otherwise starve each other.
+#include <algorithm>
+#include <vector>
+
+#include "pdf_internal.cuh"
+
+struct pdf_batch {
+    std::vector<pdf_ctx*> ctx;
+    cudaStream_t s = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    std::vector<cudaEvent_t> ev;
+    std::vector<int64_t> launches;  // kernels of one captured step, per context
+};
+
+namespace {
+
+void release(pdf_batch* b) {
+    if (!b) return;
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    for (cudaEvent_t e : b->ev) cudaEventDestroy(e);
+    delete b;
+}
+
+int cuda_fail(const char* what, cudaError_t e) {
+    return fail(nullptr, PDF_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+}  // namespace
+
+extern "C" {
+
+int pdf_batch_create(pdf_ctx* const* ctx, const double* dt, int32_t n, void* cuda_stream, pdf_batch** out) {
+    if (!out) return fail(nullptr, PDF_ERR_ARG, "pdf_batch_create: out is NULL");
+    *out = nullptr;
+    if (!ctx || !dt || n < 1 || !cuda_stream) return fail(nullptr, PDF_ERR_ARG, "pdf_batch_create: bad arguments");
+    for (int i = 0; i < n; ++i) {
+        pdf_ctx* c = ctx[i];
+        if (!c || !c->s || c->s == (cudaStream_t)cuda_stream || !(dt[i] > 0) || !c->stats_valid)
+            return fail(nullptr, PDF_ERR_ARG, "pdf_batch_create: context " + std::to_string(i) +
+                                                  " needs its own stream, a positive dt and estimated statistics");
+        for (int j = 0; j < i; ++j)
+            if (ctx[j] == c || ctx[j]->s == c->s)
+                return fail(nullptr, PDF_ERR_ARG, "pdf_batch_create: contexts and streams must be distinct");
+    }
+    // launch set-up outside the capture
+    for (int i = 0; i < n; ++i) {
+        pdf_ctx* c = ctx[i];
+        int st = c->step_blocks ? PDF_OK : prepare_particle(c, 0);
+        if (st == PDF_OK && c->p.wall_model == PDF_ELLIPTIC_RELAXATION && !c->fe_blocks) st = prepare_elliptic(c, 0);
+        if (st != PDF_OK) return fail(nullptr, st, "pdf_batch_create: context " + std::to_string(i) + ": " + c->err);
+    }
+    pdf_batch* b = new pdf_batch;
+    b->ctx.assign(ctx, ctx + n);
+    b->s = (cudaStream_t)cuda_stream;
+    b->ev.resize(1 + 2 * (size_t)n);
+    b->launches.assign(n, 0);
+    for (auto& e : b->ev) {
+        const cudaError_t err = cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
+        if (err != cudaSuccess) {
+            e = nullptr;
+            release(b);
+            return cuda_fail("cudaEventCreateWithFlags", err);
+        }
+    }
+    cudaEvent_t fork = b->ev[0];
+    cudaError_t err = cudaStreamBeginCapture(b->s, cudaStreamCaptureModeRelaxed);
+    if (err != cudaSuccess) {
+        release(b);
+        return cuda_fail("cudaStreamBeginCapture", err);
+    }
+    int st = PDF_OK;
+    err = cudaEventRecord(fork, b->s);
+    for (int i = 0; i < n && st == PDF_OK && err == cudaSuccess; ++i) {
+        pdf_ctx* c = ctx[i];
+        err = cudaStreamWaitEvent(c->s, fork, 0);
+        if (err != cudaSuccess) break;
+        const int timing = c->timing;
+        c->timing = 0;
+        c->coop_wait = i ? b->ev[1 + n + i - 1] : nullptr;
+        c->coop_done = b->ev[1 + n + i];
+        const int64_t l0 = c->launches;
+        st = pdf_step(c, dt[i], 2);
+        b->launches[i] = c->launches - l0;
+        c->launches = l0;
+        c->coop_wait = c->coop_done = nullptr;
+        c->timing = timing;
+        if (st == PDF_OK) c->step -= 2;  // captured, not executed
+        else st = fail(nullptr, st, "pdf_batch_create: step of context " + std::to_string(i) + ": " + c->err);
+        if (st == PDF_OK) err = cudaEventRecord(b->ev[1 + i], c->s);
+        if (st == PDF_OK && err == cudaSuccess) err = cudaStreamWaitEvent(b->s, b->ev[1 + i], 0);
+    }
+    const cudaError_t end = cudaStreamEndCapture(b->s, &b->graph);
+    if (st != PDF_OK || err != cudaSuccess || end != cudaSuccess) {
+        release(b);
+        if (st != PDF_OK) return st;
+        return cuda_fail("stream capture of the batch step", err != cudaSuccess ? err : end);
+    }
+    err = cudaGraphInstantiate(&b->exec, b->graph, 0);
+    if (err != cudaSuccess) {
+        release(b);
+        return cuda_fail("cudaGraphInstantiate", err);
+    }
+    *out = b;
+    return PDF_OK;
+}
+
+int pdf_batch_step(pdf_batch* b, int32_t nsteps) {
+    if (!b || nsteps < 0 || (nsteps & 1))
+        return fail(nullptr, PDF_ERR_ARG, "pdf_batch_step: nsteps must be even and >= 0");
+    for (int k = 0; k < nsteps / 2; ++k) {
+        const cudaError_t err = cudaGraphLaunch(b->exec, b->s);
+        if (err != cudaSuccess) return cuda_fail("cudaGraphLaunch", err);
+    }
+    for (size_t i = 0; i < b->ctx.size(); ++i) {
+        b->ctx[i]->step += nsteps;
+        b->ctx[i]->launches += b->launches[i] * (nsteps / 2);
+    }
+    return PDF_OK;
+}
+
+int pdf_batch_sync(pdf_batch* b, int32_t* failed) {
+    if (!b) return PDF_ERR_ARG;
+    if (failed) *failed = -1;
+    const cudaError_t err = cudaStreamSynchronize(b->s);
+    if (err != cudaSuccess) return cuda_fail("cudaStreamSynchronize", err);
+    for (size_t i = 0; i < b->ctx.size(); ++i) {
+        const int st = pdf_sync(b->ctx[i]);
+        if (st != PDF_OK) {
+            if (failed) *failed = (int32_t)i;
+            return st;
+        }
+    }
+    return PDF_OK;
+}
+
+void pdf_batch_destroy(pdf_batch* b) {
+    if (!b) return;
+    cudaStreamSynchronize(b->s);
+    release(b);
+}
+
+int pdf_autotune(pdf_ctx* c, double dt, int32_t steps_per_trial, pdf_tuning* out) {
+    if (!c || !(dt > 0) || steps_per_trial < 1) return PDF_ERR_ARG;
+    if (!c->stats_valid) return fail(c, PDF_ERR_STATE, "statistics not estimated");
+    const int timing = c->timing;
+    c->timing = 1;
+    auto trial = [&](int kernel, double& ms) -> int {
+        int st = pdf_step(c, dt, 1);  // warm-up with the new shape
+        if (st == PDF_OK) st = pdf_reset_timing(c);
+        if (st == PDF_OK) st = pdf_step(c, dt, steps_per_trial);
+        int64_t n = 0;
+        if (st == PDF_OK) st = pdf_kernel_time(c, kernel, &ms, &n);
+        if (st == PDF_OK) st = pdf_sync(c);
+        ms /= steps_per_trial;
+        return st;
+    };
+    pdf_tuning t{};
+    int st = PDF_OK;
+    // particle kernel: resident blocks per SM
+    {
+        const int occ = particle_occupancy(c);
+        int best = occ;
+        double best_ms = 1e300;
+        for (int per = 1; per <= occ && st == PDF_OK; ++per) {
+            st = prepare_particle(c, per);
+            double ms = 0;
+            if (st == PDF_OK) st = trial(PDF_K_PARTICLE, ms);
+            if (st == PDF_OK && ms < best_ms) { best_ms = ms; best = per; }
+        }
+        if (st == PDF_OK) st = prepare_particle(c, best);
+        t.step_blocks_per_sm = best;
+        t.ms_particle = best_ms;
+    }
+    // scatter block size
+    if (st == PDF_OK) {
+        const int cand[3] = {128, 256, 512};
+        int best = 256;
+        double best_ms = 1e300;
+        for (int k = 0; k < 3 && st == PDF_OK; ++k) {
+            c->scatter_threads = cand[k];
+            double ms = 0;
+            st = trial(PDF_K_SORT, ms);
+            if (st == PDF_OK && ms < best_ms) { best_ms = ms; best = cand[k]; }
+        }
+        c->scatter_threads = best;
+        t.scatter_threads = best;
+        t.ms_sort = best_ms;
+    }
+    // CG block size (co-resident grids only)
+    if (st == PDF_OK && c->p.wall_model == PDF_ELLIPTIC_RELAXATION) {
+        const int cand[3] = {128, 160, 192};
+        int best = 0;
+        double best_ms = 1e300;
+        for (int k = 0; k < 3 && st == PDF_OK; ++k) {
+            if (prepare_elliptic(c, cand[k]) != PDF_OK) continue;  // not co-resident: skip
+            double ms = 0;
+            st = trial(PDF_K_ELLIPTIC, ms);
+            if (st == PDF_OK && ms < best_ms) { best_ms = ms; best = cand[k]; }
+        }
+        if (st == PDF_OK) st = best ? prepare_elliptic(c, best) : prepare_elliptic(c, 0);
+        t.cg_rows_per_block = c->fe_bs;
+        t.ms_elliptic = best_ms;
+    }
+    c->timing = timing;
+    if (st == PDF_OK && out) *out = t;
+    return st;
+}
+
+}  // extern "C"

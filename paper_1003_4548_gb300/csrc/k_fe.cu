@@ -648,6 +648,30 @@ cudaError_t launch_pcg(const CGArgs& a, int blocks, cudaStream_t s, bool ffv) {
 
 }  // namespace
 
+// grid of the cooperative CG for rows-per-block bs (0: the largest size whose
+// grid is co-resident: fewer blocks and partial sums, a stronger block-Jacobi
+// preconditioner)
+int prepare_elliptic(pdf_ctx* c, int bs) {
+    const int nn = c->m.nn;
+    int per_sm = 0, blocks = 0;
+    const bool ffv = c->p.cg_precision == 1;
+    const int order[3] = {192, 160, 128};
+    int chosen = 0;
+    for (int k = 0; k < 3 && !chosen; ++k) {
+        const int b = order[k];
+        if (bs && b != bs) continue;
+        blocks = b == 192 ? try_blocks<192>(c, nn, per_sm, ffv)
+                          : (b == 160 ? try_blocks<160>(c, nn, per_sm, ffv) : try_blocks<128>(c, nn, per_sm, ffv));
+        if (blocks > 0 && blocks <= per_sm * c->num_sms) chosen = b;
+    }
+    if (!chosen) return fail(c, PDF_ERR_CAPACITY, "elliptic solver: mesh too large for one resident grid");
+    if ((size_t)blocks * PART_W > (size_t)15 * 4096 || (blocks + 15) / 16 > 63)
+        return fail(c, PDF_ERR_CAPACITY, "elliptic solver: partial-sum buffer too small");
+    c->fe_bs = chosen;
+    c->fe_blocks = blocks;
+    return PDF_OK;
+}
+
 int launch_elliptic(pdf_ctx* c) {
     const int nn = c->m.nn;
     timing_begin(c, PDF_K_ELLIPTIC);
@@ -663,18 +687,8 @@ int launch_elliptic(pdf_ctx* c) {
         if (st != PDF_OK) return st;
     }
     if (c->fe_blocks == 0) {
-        // the largest diagonal-block size (fewer blocks and partial sums, a
-        // stronger block-Jacobi preconditioner) whose grid is co-resident
-        int per_sm = 0, blocks = 0;
-        const bool ffv = c->p.cg_precision == 1;
-        blocks = try_blocks<192>(c, nn, per_sm, ffv);
-        if (blocks > 0 && blocks <= per_sm * c->num_sms) c->fe_bs = 192;
-        else if ((blocks = try_blocks<160>(c, nn, per_sm, ffv)) > 0 && blocks <= per_sm * c->num_sms) c->fe_bs = 160;
-        else if ((blocks = try_blocks<128>(c, nn, per_sm, ffv)) > 0 && blocks <= per_sm * c->num_sms) c->fe_bs = 128;
-        else return fail(c, PDF_ERR_CAPACITY, "elliptic solver: mesh too large for one resident grid");
-        if ((size_t)blocks * PART_W > (size_t)15 * 4096 || (blocks + 15) / 16 > 63)
-            return fail(c, PDF_ERR_CAPACITY, "elliptic solver: partial-sum buffer too small");
-        c->fe_blocks = blocks;
+        const int st = prepare_elliptic(c, 0);
+        if (st != PDF_OK) return st;
     }
     CGArgs a;
     a.nn = nn;
@@ -690,10 +704,14 @@ int launch_elliptic(pdf_ctx* c) {
     a.xprop = c->fe_prop;
     cudaError_t err;
     const bool ffv = c->p.cg_precision == 1;
+    // cooperative grids of different contexts never run side by side (a
+    // batch orders them in a chain)
+    if (c->coop_wait) PDF_CUDA(c, cudaStreamWaitEvent(c->s, c->coop_wait, 0));
     if (c->fe_bs == 128) err = launch_pcg<128>(a, c->fe_blocks, c->s, ffv);
     else if (c->fe_bs == 160) err = launch_pcg<160>(a, c->fe_blocks, c->s, ffv);
     else err = launch_pcg<192>(a, c->fe_blocks, c->s, ffv);
     PDF_CUDA(c, err);
+    if (c->coop_done) PDF_CUDA(c, cudaEventRecord(c->coop_done, c->s));
     k_fe_copy_out<<<(nn + 127) / 128, 128, 0, c->s>>>(nn, c->m.rep, c->nwp, c->nwp);
     c->launches += 3;
     timing_end(c, PDF_K_ELLIPTIC);

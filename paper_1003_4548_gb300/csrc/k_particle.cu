@@ -63,7 +63,7 @@ template <typename T>
 struct StepArgs {
     int64_t n;
     T dt, sdt, s2nu, nu;
-    uint32_t step;
+    const uint32_t* stepp;  // step counter on the device (advanced by the sort after each step)
     uint2 key;
     const int* __restrict__ tri;
     const int* __restrict__ nbr;
@@ -126,8 +126,9 @@ __device__ void reflect(const StepArgs<T>& a, int tag, T nx, T ny, const double*
 // one particle-step of particle i whose state at step n was staged in
 // shared memory; writes the state at step n+1 in place
 template <typename T>
-__device__ __forceinline__ void advance_particle(const StepArgs<T>& a, const int i, const T x, const T y, T u, T v,
-                                                 T w, T om, T psi, const uint32_t pid, const int e0, const int b) {
+__device__ __forceinline__ void advance_particle(const StepArgs<T>& a, const uint32_t step, const int i, const T x,
+                                                 const T y, T u, T v, T w, T om, T psi, const uint32_t pid,
+                                                 const int e0, const int b) {
 
     // barycentric coordinates in the host element
     T g[EGEO_W];
@@ -156,7 +157,7 @@ __device__ __forceinline__ void advance_particle(const StepArgs<T>& a, const int
     T z[8];
 #pragma unroll
     for (uint32_t call = 0; call < 2; ++call) {
-        const uint4 r = philox4x32_10(a.key, make_uint4(pid, a.step, call, 0u));
+        const uint4 r = philox4x32_10(a.key, make_uint4(pid, step, call, 0u));
         gauss_pair(unif<T>(r.x), unif<T>(r.y), z[4 * call + 0], z[4 * call + 1]);
         gauss_pair(unif<T>(r.z), unif<T>(r.w), z[4 * call + 2], z[4 * call + 3]);
     }
@@ -358,6 +359,7 @@ __global__ void __launch_bounds__(TILE) k_step(const StepArgs<T> a) {
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
+    const uint32_t step = *a.stepp;
     int64_t t = blockIdx.x;
     if (threadIdx.x == 0 && t < ntiles) stage_tile(a, st[0], &bar[0], t * TILE, (int)min((int64_t)TILE, a.n - t * TILE));
     for (int k = 0; t < ntiles; t += gridDim.x, ++k) {
@@ -373,7 +375,7 @@ __global__ void __launch_bounds__(TILE) k_step(const StepArgs<T> a) {
         if (i < a.n) {
             const Stage<T>& q = st[s];
             const int j = threadIdx.x;
-            advance_particle(a, (int)i, q.s[0][j], q.s[1][j], q.s[2][j], q.s[3][j], q.s[4][j], q.s[5][j], q.s[6][j],
+            advance_particle(a, step, (int)i, q.s[0][j], q.s[1][j], q.s[2][j], q.s[3][j], q.s[4][j], q.s[5][j], q.s[6][j],
                              q.id[j], q.elem[j], (int)q.bin[j]);
         }
         __syncthreads();
@@ -427,7 +429,7 @@ StepArgs<T> step_args(pdf_ctx* c, double dt) {
     a.sdt = (T)sqrt(dt);
     a.s2nu = (T)sqrt(2.0 * p.nu);
     a.nu = (T)p.nu;
-    a.step = (uint32_t)c->step;
+    a.stepp = c->d_step;
     a.key = philox_key(p.seed, p.case_id);
     a.tri = c->m.tri;
     a.nbr = c->m.nbr;
@@ -461,15 +463,31 @@ StepArgs<T> step_args(pdf_ctx* c, double dt) {
 
 }  // namespace
 
+// persistent grid of the particle kernel: per_sm blocks on every SM (0: as
+// many as are resident)
+int prepare_particle(pdf_ctx* c, int per_sm) {
+    int occ = 0;
+    if (c->prec == 0) PDF_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_step<double>, TILE, 0));
+    else PDF_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_step<float>, TILE, 0));
+    occ = std::max(1, occ);
+    if (per_sm <= 0 || per_sm > occ) per_sm = occ;
+    c->step_blocks = per_sm * c->num_sms;
+    return PDF_OK;
+}
+
+int particle_occupancy(pdf_ctx* c) {
+    int occ = 0;
+    if (c->prec == 0) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_step<double>, TILE, 0);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_step<float>, TILE, 0);
+    return std::max(1, occ);
+}
+
 int launch_particle_step(pdf_ctx* c, double dt) {
     PDF_CUDA(c, cudaMemsetAsync(c->cnt, 0, sizeof(int) * c->m.nt, c->s));
     if (c->np == 0) return PDF_OK;
-    // persistent grid: the resident blocks of every SM
     if (c->step_blocks == 0) {
-        int per_sm = 0;
-        if (c->prec == 0) PDF_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step<double>, TILE, 0));
-        else PDF_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step<float>, TILE, 0));
-        c->step_blocks = std::max(1, per_sm) * c->num_sms;
+        const int st = prepare_particle(c, 0);
+        if (st != PDF_OK) return st;
     }
     const int64_t ntiles = (c->np + TILE - 1) / TILE;
     const unsigned blocks = (unsigned)std::min<int64_t>(ntiles, c->step_blocks);

@@ -17,7 +17,8 @@ constexpr int SCAN_THREADS = 1024;
 // range of elements; pass 1 sums it with coalesced loads, warp 0 scans the 32
 // totals, pass 2 scans the range 32 elements at a time with a running carry
 __global__ void __launch_bounds__(SCAN_THREADS) k_scan(const int* __restrict__ cnt, int nt, int* off,
-                                                       int* cursor) {
+                                                       int* cursor, uint32_t* bump) {
+    if (bump != nullptr && threadIdx.x == 0) *bump += 1u;  // the step counter moves with the re-sort
     __shared__ int warp_ex[SCAN_THREADS / 32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     constexpr int NW = SCAN_THREADS / 32;
@@ -73,7 +74,7 @@ __global__ void __launch_bounds__(256) k_count(int64_t n, const int* __restrict_
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_scatter(int64_t n, const T* __restrict__ x, const T* __restrict__ y,
+__global__ void __launch_bounds__(512) k_scatter(int64_t n, const T* __restrict__ x, const T* __restrict__ y,
                                                  const T* __restrict__ u, const T* __restrict__ v,
                                                  const T* __restrict__ w, const T* __restrict__ om,
                                                  const T* __restrict__ psi, const uint32_t* __restrict__ id,
@@ -96,10 +97,10 @@ __global__ void __launch_bounds__(256) k_scatter(int64_t n, const T* __restrict_
 }
 
 template <typename T>
-void scatter(pdf_ctx* c, unsigned blocks) {
+void scatter(pdf_ctx* c, unsigned blocks, int threads) {
     T** A = (T**)c->stA;
     T** B = (T**)c->stB;
-    k_scatter<T><<<blocks, 256, 0, c->s>>>(c->np, A[0], A[1], A[2], A[3], A[4], A[5], A[6], c->idA, c->elemA,
+    k_scatter<T><<<blocks, threads, 0, c->s>>>(c->np, A[0], A[1], A[2], A[3], A[4], A[5], A[6], c->idA, c->elemA,
                                            c->m.nt, c->cursor, B[0], B[1], B[2], B[3], B[4], B[5], B[6],
                                            c->idB, c->elemB);
 }
@@ -178,7 +179,7 @@ extern "C" int pdf_sort_by_element_static(const int32_t* elem, int64_t n, int32_
     STATIC_CUDA(cudaMemsetAsync(status, 0, sizeof(int), s));
     const unsigned blocks = (unsigned)((n + 255) / 256);
     if (n > 0) k_count<<<blocks, 256, 0, s>>>(n, elem, nt, cnt, status);
-    k_scan<<<1, SCAN_THREADS, 0, s>>>(cnt, nt, off, cursor);
+    k_scan<<<1, SCAN_THREADS, 0, s>>>(cnt, nt, off, cursor, nullptr);
     if (n > 0) k_scatter_perm<<<blocks, 256, 0, s>>>(n, elem, nt, cursor, perm);
     STATIC_CUDA(cudaGetLastError());
     int h = 0;
@@ -189,14 +190,15 @@ extern "C" int pdf_sort_by_element_static(const int32_t* elem, int64_t n, int32_
     return PDF_OK;
 }
 
-int launch_sort(pdf_ctx* c) {
+int launch_sort(pdf_ctx* c, bool advance_step) {
     timing_begin(c, PDF_K_SORT);
-    k_scan<<<1, SCAN_THREADS, 0, c->s>>>(c->cnt, c->m.nt, c->off, c->cursor);
+    k_scan<<<1, SCAN_THREADS, 0, c->s>>>(c->cnt, c->m.nt, c->off, c->cursor, advance_step ? c->d_step : nullptr);
     ++c->launches;
     if (c->np > 0) {
-        const unsigned blocks = (unsigned)((c->np + 255) / 256);
-        if (c->prec == 0) scatter<double>(c, blocks);
-        else scatter<float>(c, blocks);
+        const int th = c->scatter_threads;
+        const unsigned blocks = (unsigned)((c->np + th - 1) / th);
+        if (c->prec == 0) scatter<double>(c, blocks, th);
+        else scatter<float>(c, blocks, th);
         ++c->launches;
     }
     timing_end(c, PDF_K_SORT);

@@ -1019,11 +1019,6 @@ int run(pdf_ctx* c) {
         }
     }
     const size_t smem = sizeof(SortKey) * STATS_CAP;
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaFuncSetAttribute(k_moments<T, KAHAN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        attr_set = true;
-    }
     const unsigned grid = a.listB ? (unsigned)std::min(c->m.nt, c->num_sms) : (unsigned)c->m.nt;
     k_moments<T, KAHAN><<<grid, STATS_THREADS, smem, c->s>>>(a);
     ++c->launches;
@@ -1032,6 +1027,14 @@ int run(pdf_ctx* c) {
 }
 
 }  // namespace
+
+int prepare_moments(pdf_ctx* c) {
+    const int smem = (int)(sizeof(SortKey) * STATS_CAP);
+    PDF_CUDA(c, cudaFuncSetAttribute(k_moments<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    PDF_CUDA(c, cudaFuncSetAttribute(k_moments<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    PDF_CUDA(c, cudaFuncSetAttribute(k_moments<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    return PDF_OK;
+}
 
 int launch_moments(pdf_ctx* c) {
     timing_begin(c, PDF_K_MOMENTS);

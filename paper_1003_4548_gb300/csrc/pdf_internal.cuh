@@ -80,6 +80,7 @@ struct pdf_ctx {
     DevMesh m;
     int64_t np = 0;
     int step = 0;
+    uint32_t* d_step = nullptr;  // the step counter on the device (Philox counter word 1)
     bool seeded = false, stats_valid = false;
     // particle state, double-buffered for the element sort; T = double or float
     void* stA[7] = {nullptr};
@@ -131,6 +132,8 @@ struct pdf_ctx {
     int timing = 0;
     int64_t launches = 0;  // kernels launched by this context
     int step_blocks = 0;   // persistent grid of the particle kernel
+    int scatter_threads = 256;  // block size of the re-sort scatter
+    cudaEvent_t coop_wait = nullptr, coop_done = nullptr;  // batch: chain of the cooperative CG launches
     std::string err;
     int num_sms = 0;
 };
@@ -155,11 +158,16 @@ void timing_end(pdf_ctx* c, int k);
 // ---------------------------------------------------------------------------
 int launch_seed(pdf_ctx* c, int ppe);
 int launch_particle_step(pdf_ctx* c, double dt);
-int launch_sort(pdf_ctx* c);        // scan of counts + scatter A -> B + swap
+int launch_sort(pdf_ctx* c, bool advance_step = false);  // scan + scatter A -> B + swap (+ d_step += 1)
+int set_device_step(pdf_ctx* c);    // d_step = step
 int launch_count_and_sort(pdf_ctx* c);  // histogram of elemA, then launch_sort
 int launch_moments(pdf_ctx* c);
 int launch_fields(pdf_ctx* c);      // node stats, derived, recovery, ER solve, packs
 int launch_elliptic(pdf_ctx* c);
+int prepare_particle(pdf_ctx* c, int per_sm);   // persistent grid (0: all resident blocks)
+int particle_occupancy(pdf_ctx* c);
+int prepare_elliptic(pdf_ctx* c, int bs);       // CG rows per block (0: largest co-resident)
+int prepare_moments(pdf_ctx* c);
 int launch_surrogate(pdf_ctx* c);   // network wp at the nodes + FE residual check (before the CG)
 int surrogate_rows(pdf_ctx* c);     // builds the free canonical row list once
 int launch_to_double(pdf_ctx* c, const void* src, double* dst, int64_t n);

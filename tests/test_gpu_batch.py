@@ -1,0 +1,108 @@
+"""Batched cases in one CUDA graph, and the autotuner.
+
+A batch replays one captured step of several contexts; every case must end
+exactly where the same case stepped on its own ends (same kernels in the same
+order per case; FP64 reductions, so the particle order inside an element
+does not matter). The autotuner changes launch shapes only: a tuned FP64
+wall-function context must match an untuned twin stepped as often.
+"""
+import numpy as np
+import pytest
+
+from canyon_inputs.configs import cfl_dt, yplus30
+from canyon_inputs.mesh import canyon_mesh
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    t = pytest.importorskip("torch")
+    if not t.cuda.is_available():
+        pytest.skip("needs a GPU")
+    return t
+
+
+def cases():
+    out = []
+    for k, (W, ppe, wm) in enumerate(((0.75, 16, "wf"), (1.0, 24, "er"), (1.5, 32, "wf"))):
+        if wm == "wf":
+            mesh = canyon_mesh(W=W, offset=yplus30(), h=0.12, seed=20 + k)
+        else:
+            mesh = canyon_mesh(W=W, offset=0.0, h=0.1, y1=3e-3, growth=1.3, seed=20 + k)
+        out.append((mesh, ppe, wm, k))
+    return out
+
+
+def make(torch, mesh, ppe, wm, k, stream, **over):
+    from paper_1003_4548_gb300 import Canyon, canyon_params
+    p = canyon_params(mesh, wall_model=wm, precision="fp64", C0=2.1, seed=100 + k, case_id=k, cg_tol=1e-10,
+                      cg_maxit=20000, **over)
+    g = Canyon(p, mesh, stream=stream.cuda_stream)
+    g.seed_particles(ppe)
+    g.estimate_stats()
+    return g
+
+
+def by_id(g):
+    P = g.particles()
+    o = np.argsort(P["id"])
+    return {k: v[o] for k, v in P.items()}
+
+
+def test_batch_graph_matches_individual_steps(torch):
+    from paper_1003_4548_gb300 import capi
+    cs = cases()
+    streams = [torch.cuda.Stream() for _ in range(2 * len(cs) + 1)]
+    batched = [make(torch, m, ppe, wm, k, streams[k]) for m, ppe, wm, k in cs]
+    alone = [make(torch, m, ppe, wm, k, streams[len(cs) + k]) for m, ppe, wm, k in cs]
+    dts = [cfl_dt(m, cfl=0.5, k0=1e-3) for m, _, _, _ in cs]
+    b = capi.Batch(batched, dts, streams[-1].cuda_stream)
+    for g, dt in zip(alone, dts):
+        g.step(dt, 4)
+        g.sync()
+    b.step(2)
+    b.step(2)
+    b.sync()
+    with pytest.raises(capi.PdfError):
+        b.step(3)
+    for ga, gb in zip(alone, batched):
+        assert gb.step_index == ga.step_index == 4
+        A, B = by_id(ga), by_id(gb)
+        for k in ("x", "y", "u", "v", "w", "om", "psi", "elem"):
+            assert np.array_equal(A[k], B[k]), k
+        assert np.array_equal(ga.field("elem_mean"), gb.field("elem_mean"))
+    b.close()
+    for g in batched + alone:
+        g.close()
+
+
+def test_batch_rejects_shared_streams(torch):
+    from paper_1003_4548_gb300 import capi
+    m, ppe, wm, k = cases()[0]
+    s = torch.cuda.Stream()
+    g1 = make(torch, m, ppe, wm, 0, s)
+    g2 = make(torch, m, ppe, wm, 1, s)
+    with pytest.raises(capi.PdfError):
+        capi.Batch([g1, g2], [1e-3, 1e-3], torch.cuda.Stream().cuda_stream)
+    g1.close()
+    g2.close()
+
+
+def test_autotune_changes_shapes_not_results(torch):
+    m, ppe, wm, k = cases()[0]
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    tuned = make(torch, m, ppe, wm, k, s1, mix_exp=1)
+    twin = make(torch, m, ppe, wm, k, s2, mix_exp=1)
+    dt = cfl_dt(m, cfl=0.25, k0=1e-3)
+    t = tuned.autotune(dt, 1)
+    assert 1 <= t["step_blocks_per_sm"] <= 8 and t["scatter_threads"] in (128, 256, 512)
+    assert t["cg_rows_per_block"] == 0 and t["ms_particle"] > 0
+    twin.step(dt, tuned.step_index)
+    tuned.sync()
+    twin.sync()
+    A, B = by_id(tuned), by_id(twin)
+    for key in ("x", "u", "om", "psi", "elem"):
+        assert np.array_equal(A[key], B[key]), key
+    tuned.close()
+    twin.close()
