@@ -338,20 +338,22 @@ class Form:
         self.g.close()
 
 
-def prepare_surrogate(cfg, mesh, dt, seed=0):
-    """Harvest FE runs at W/H = 0.5 .. 2 (this workload's mesh recipe), train
-    the network with the library's kernels, and calibrate the check on a
-    held-out run of this workload: threshold = 1.5 x the largest coarse
-    residual seen there."""
+def prepare_surrogate(cfg, mesh, dt, seed=0, harvest_meshes=None, ratios=(0.5, 0.75, 1.0, 1.5, 2.0)):
+    """Harvest FE runs at W/H = 0.5 .. 2 (this workload's mesh recipe, or the
+    given meshes), train the network with the library's kernels, and
+    calibrate the check on a held-out run of this workload: threshold = 1.5 x
+    the largest coarse residual seen there."""
     from canyon_inputs.configs import cfl_dt
     from canyon_inputs.mesh import canyon_mesh
     from paper_1003_4548_gb300 import surrogate
     t0 = time.perf_counter()
-    meshes = []
-    for i, W in enumerate((0.5, 0.75, 1.0, 1.5, 2.0)):
-        m = dict(cfg["mesh"])
-        m["W"], m["seed"] = W, 10 + i
-        meshes.append(canyon_mesh(**m))
+    meshes = harvest_meshes
+    if meshes is None:
+        meshes = []
+        for i, W in enumerate(ratios):
+            m = dict(cfg["mesh"])
+            m["W"], m["seed"] = W, 10 + i
+            meshes.append(canyon_mesh(**m))
     X, T, counts = surrogate.harvest(meshes, steps=100, every=5, per_element=cfg["per_element"],
                                      dt_of=lambda m: cfl_dt(m, cfl=cfg["cfl"], k0=cfg["k0"]), C0=cfg["C0"],
                                      seed=seed + 1000)
@@ -361,7 +363,8 @@ def prepare_surrogate(cfg, mesh, dt, seed=0):
     res = surrogate.calibrate(params, norm, mesh, steps=100, every=5, per_element=cfg["per_element"], dt=dt,
                               seed=seed + 99, C0=cfg["C0"])
     tol = 1.5 * max(r[0] for r in res)
-    info = {"samples": int(X.shape[0]), "aspect_ratios": [0.5, 0.75, 1.0, 1.5, 2.0], "epochs": 10,
+    info = {"samples": int(X.shape[0]), "aspect_ratios": [round(float(m["W"]), 3) for m in meshes],
+            "harvest_triangles": [int(m["tri"].shape[0]) for m in meshes], "epochs": 10,
             "final_loss_standardised": hist[-1][1], "harvest_s": t1 - t0, "train_s": t2 - t1,
             "calibration_coarse_residual_max": max(r[0] for r in res), "residual_tol": tol,
             "check": "coarse FE residual (aggregates of 128 Morton-ordered nodes) <= residual_tol"}
@@ -383,11 +386,158 @@ def surrogate_error(form, mesh):
                                 np.linalg.norm(form.last_wp - wfe, axis=0) / np.linalg.norm(wfe, axis=0)]}
 
 
+def run_batch(a, cfg):
+    """Many independent cases in one CUDA graph (pdf_batch_*): each case its own
+    mesh, particle count, seed and source, autotuned launch shapes, the chosen
+    form (FP32 state, compensated-FP32 reductions, surrogate wp with the FE
+    solve as checked fallback). value = all cases' particle-steps per second."""
+    import torch
+    from canyon_inputs.configs import WORKLOADS, batch_cases, build_mesh, cfl_dt
+    from canyon_inputs.mesh import canyon_mesh
+    from paper_1003_4548_gb300 import Canyon, canyon_params, capi
+    rank, world, local = env_rank()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    prec = a.precision or cfg["chosen_precision"]
+    cases = batch_cases(cfg)
+    meshes = [canyon_mesh(**c["mesh"]) for c in cases]
+    # the surrogate: trained on held-out cases of the same family (another draw
+    # of the batch recipe: W/H 0.5 .. 3, spacing 0.017 .. 0.1), calibrated on
+    # the wall-resolved W/H = 1 canyon
+    ref = dict(WORKLOADS["canyon_er_full"])
+    ref["name"] = "canyon_er_full"
+    ref_mesh = build_mesh(ref)
+    held = batch_cases(dict(cfg, seed=cfg["seed"] + 1))[:8]
+    sur, sur_info = prepare_surrogate(ref, ref_mesh, cfl_dt(ref_mesh, cfl=ref["cfl"], k0=ref["k0"]),
+                                      harvest_meshes=[canyon_mesh(**c["mesh"]) for c in held])
+    # torch hands out pooled streams (32 per priority): the cases take the
+    # low-priority pool, the batch stream comes from the high-priority one
+    streams = [torch.cuda.Stream() for _ in cases]
+    bstream = torch.cuda.Stream(priority=-1)
+    assert len({s_.cuda_stream for s_ in streams + [bstream]}) == len(cases) + 1, "streams must be distinct"
+    ctxs, dts, tunings, tols = [], [], [], []
+    t0 = time.perf_counter()
+    for c, m, st in zip(cases, meshes, streams):
+        p = canyon_params(m, wall_model="er", precision=prec, C0=cfg["C0"], bins=cfg["bins"], seed=c["seed"],
+                          k0=cfg["k0"], case_id=rank)
+        g = Canyon(p, m, stream=st.cuda_stream)
+        g.seed_particles(c["per_element"])
+        g.estimate_stats()
+        dt = cfl_dt(m, cfl=cfg["cfl"], k0=cfg["k0"])
+        # the check's threshold per case: 1.5 x the largest coarse residual of
+        # the network's wp over this case's first steps (the warm-up)
+        g.set_surrogate(2, sur["params"], sur["norm"], 0.0)
+        res = []
+        for _ in range(3):
+            g.step(dt, 2)
+            res.append(g.surrogate_stats()[2][0])
+        tols.append(1.5 * max(res))
+        g.set_surrogate(1, sur["params"], sur["norm"], tols[-1])
+        tunings.append(g.autotune(dt, 2))
+        ctxs.append(g)
+        dts.append(dt)
+    torch.cuda.synchronize()
+    t_setup = time.perf_counter() - t0
+    n_total = sum(g.num_particles for g in ctxs)
+    b = capi.Batch(ctxs, dts, bstream.cuda_stream)
+    steps = a.steps + (a.steps & 1)
+    b.step(2 * max(2, (a.warmup + 1) // 2))
+    b.sync()
+    L = capi.lib()
+    launches0 = sum(L.pdf_launch_count(g.handle) for g in ctxs)
+    sur0 = [g.surrogate_stats() for g in ctxs]
+    clocks = Clocks(gpu_index(local))
+    clocks.start()
+    time.sleep(0.3)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(bstream)
+    b.step(steps)
+    e1.record(bstream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ms = e0.elapsed_time(e1)
+    time.sleep(0.2)
+    ck = clocks.stop()
+    try:
+        b.sync()
+        status = "ok"
+    except capi.PdfError as err:
+        status = str(err)
+    ms = reduce_max(ms, dist, "cuda")
+    value = whole_job_value(world, n_total, steps, ms / 1e3)
+    launches = sum(L.pdf_launch_count(g.handle) for g in ctxs) - launches0
+    sur1 = [g.surrogate_stats() for g in ctxs]
+    solves = sum(x[0] - y[0] for x, y in zip(sur1, sur0))
+    falls = sum(x[1] - y[1] for x, y in zip(sur1, sur0))
+    # the same cases launched context by context on their streams, without the graph
+    torch.cuda.synchronize()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    k = min(steps, 10)
+    f0.record(bstream)
+    for s_ in streams:
+        s_.wait_event(f0)
+    for _ in range(k):
+        for g, dt in zip(ctxs, dts):
+            g.step(dt, 1)
+    for s_ in streams:
+        bstream.wait_stream(s_)
+    f1.record(bstream)
+    torch.cuda.synchronize()
+    no_graph = n_total * k / (f0.elapsed_time(f1) / 1e3)
+    b.close()
+    tri = [int(m["tri"].shape[0]) for m in meshes]
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps, "warmup": a.warmup,
+            "ms_per_step": ms / steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": cfg["name"], "cases": len(cases), "particles": int(n_total),
+                       "triangles_min_max_total": [min(tri), max(tri), sum(tri)],
+                       "per_element_min_max": [min(c["per_element"] for c in cases),
+                                               max(c["per_element"] for c in cases)],
+                       "W_over_H_min_max": [round(min(c["mesh"]["W"] for c in cases), 3),
+                                            round(max(c["mesh"]["W"] for c in cases), 3)],
+                       "precision": prec, "form": "one CUDA graph per step pair over all cases; chosen form",
+                       "l2": "inputs larger than L2"},
+            "roofline": {"bound": "hbm", "kernel": "whole step, all cases (69 B per particle-step algorithmic)",
+                         "achieved": 69 * n_total * steps / (ms / 1e3) / 1e9, "peak": measured_peaks()[0],
+                         "unit": "GB/s", "frac": 69 * n_total * steps / (ms / 1e3) / 1e9 / measured_peaks()[0],
+                         "traffic": None},
+            "gpu_launches": int(launches), "clocks": ck, "status": status,
+            "streams_without_graph": {"value": no_graph, "steps": k},
+            "autotuned": {"step_blocks_per_sm": sorted({t["step_blocks_per_sm"] for t in tunings}),
+                          "scatter_threads": sorted({t["scatter_threads"] for t in tunings}),
+                          "cg_rows_per_block": sorted({t["cg_rows_per_block"] for t in tunings})},
+            "surrogate": dict(sur_info, solves=solves, fallbacks=falls,
+                              residual_tol_per_case_min_max=[min(tols), max(tols)],
+                              check_calibration="per case: 1.5 x the largest coarse residual over its first "
+                                                "6 steps (warm-up)"), "setup_s": t_setup,
+            "e2e": None}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    for g in ctxs:
+        g.close()
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
 def main():
     a = args_()
     from canyon_inputs.configs import WORKLOADS, build_mesh, cfl_dt
     cfg = dict(WORKLOADS[a.workload])
     cfg["name"] = a.workload
+    if cfg.get("kind") == "batch":
+        if a.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable": "the batch workload has no oracle arm"}))
+            return
+        run_batch(a, cfg)
+        return
     plain_precision = cfg["precision"]
     if a.precision:
         cfg["precision"] = a.precision

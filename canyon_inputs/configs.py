@@ -9,6 +9,11 @@ canyon centre) and the workload sizes of this project:
   canyon_wf_small   ~1,600 triangles, wall functions (walls moved y_p = 0.05H
                     into the fluid), 64 particles per element (~100k), 2x2x2
                     velocity bins, C0 = 2.1, 100 steps at CFL 0.5, FP64.
+  canyon_batch32    32 independent wall-resolved canyons: W/H uniform in [0.5, 3],
+                    meshes of ~6k-61k triangles (spacing log-uniform in
+                    [0.017, 0.1], growth 1.3), 32-256 particles per element
+                    (~105M particles in all), each case with its own seed and its
+                    source at its own canyon centre.
   canyon_er_full    ~40k triangles graded to a first-cell height nu/u* at the
                     walls, elliptic relaxation solved by P1 finite elements every
                     step, 256 particles per element (~10.3M), FP32 particle state
@@ -49,6 +54,26 @@ WORKLOADS = {
         wall_model="er", per_element=256, bins=(2, 2, 2), C0=2.1, steps=500, cfl=0.5,
         precision="fp32", chosen_precision="fp32_kahan", seed=0, k0=1e-3),
 }
+
+
+WORKLOADS["canyon_batch32"] = dict(kind="batch", cases=32, seed=0, wall_model="er", bins=(2, 2, 2), C0=2.1,
+                                   cfl=0.5, k0=1e-3, precision="fp32", chosen_precision="fp32_kahan",
+                                   mesh=WORKLOADS["canyon_er_full"]["mesh"], per_element=256)
+
+
+def batch_cases(cfg: dict) -> list[dict]:
+    """The seeded case list of a batch workload: mesh recipe, particles per
+    element and seed of every case."""
+    rng = np.random.default_rng(cfg["seed"])
+    out = []
+    for i in range(cfg["cases"]):
+        W = float(rng.uniform(0.5, 3.0))
+        h = float(np.exp(rng.uniform(np.log(0.017), np.log(0.1))))
+        ppe = int(rng.integers(4, 33)) * 8  # 32 .. 256
+        out.append(dict(mesh=dict(H=1.0, W=W, B=2.0, T=2.0, offset=0.0, h=h, y1=NU / USTAR, growth=1.3,
+                                  seed=1000 + i),
+                        per_element=ppe, seed=cfg["seed"] * 1000 + 17 * i + 1))
+    return out
 
 
 def build_mesh(name_or_cfg) -> dict:
