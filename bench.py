@@ -43,6 +43,8 @@ def args_():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-surrogate", action="store_true", help="FE solve every step in the timed form")
     ap.add_argument("--no-forms", action="store_true", help="skip the plain forms and the precision study")
+    ap.add_argument("--save-surrogate", default=None, help="write the trained network (npz) here")
+    ap.add_argument("--load-surrogate", default=None, help="use this trained network (npz) instead of training")
     return ap.parse_args()
 
 
@@ -560,7 +562,15 @@ def main():
         dist.init_process_group("nccl")
     stream = torch.cuda.current_stream()
     use_sur = cfg["wall_model"] == "er" and not a.no_surrogate
-    sur, sur_info = (prepare_surrogate(cfg, mesh, dt) if use_sur else (None, None))
+    sur, sur_info = None, None
+    if use_sur and a.load_surrogate:
+        z = np.load(a.load_surrogate)
+        sur = {"params": z["params"], "norm": z["norm"], "tol": float(z["tol"])}
+        sur_info = {"loaded_from": os.path.basename(a.load_surrogate), "residual_tol": sur["tol"]}
+    elif use_sur:
+        sur, sur_info = prepare_surrogate(cfg, mesh, dt)
+    if sur is not None and a.save_surrogate:
+        np.savez(a.save_surrogate, params=sur["params"], norm=sur["norm"], tol=sur["tol"])
     prec = cfg["precision"]
     red = {"fp64": "FP64", "fp32": "FP64-exact", "fp32_kahan": "compensated FP32"}[prec]
     form_name = (f"{prec} particle state, {red} statistics" +

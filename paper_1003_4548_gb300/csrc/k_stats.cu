@@ -624,12 +624,15 @@ struct Buckets {
     }
 };
 
+// (in FP32: any monotone map is exact for the selection, and FP64 on every
+// lane of a warp would occupy GB300's narrow FP64 pipe)
 __device__ __forceinline__ Buckets make_buckets(double mean, double var) {
-    const double sd = var > 0.0 ? sqrt(var) : 0.0;
-    const double sc = sd > 0.0 ? 256.0 / (8.0 * sd) : 0.0;
+    const float v = (float)var;
+    const float sd = v > 0.f ? sqrtf(v) : 0.f;
+    const float sc = sd > 0.f ? 32.f / sd : 0.f;  // 256 buckets over 8 sd
     Buckets b;
-    b.lo = (float)(mean - 4.0 * sd);
-    b.sc = (sc > 0.0 && sc < 1e30) ? (float)sc : 0.f;
+    b.lo = (float)mean - 4.f * sd;
+    b.sc = (sc > 0.f && sc < 1e30f) ? sc : 0.f;
     return b;
 }
 
@@ -828,20 +831,49 @@ __device__ __noinline__ void kahan_moments(const MomArgs<float>& a, int e, int s
         for (int q = 0; q < 5; ++q) warp_tree(m[q]);
 #pragma unroll
         for (int q = 0; q < 7; ++q) warp_tree(c2[q]);
-        if (lane == 0) {
-            const double inv_n = 1.0 / n;
-            const double d0 = m[0].value() * inv_n, d1 = m[1].value() * inv_n, d2 = m[2].value() * inv_n;
-            const double d3 = m[3].value() * inv_n;
-            const double mean[5] = {su + d0, sv + d1, sw + d2, sp + d3, m[4].value() * inv_n};
-            const double R[6] = {c2[0].value() * inv_n - d0 * d0, c2[1].value() * inv_n - d1 * d1,
-                                 c2[2].value() * inv_n - d2 * d2, c2[3].value() * inv_n - d0 * d1,
-                                 c2[4].value() * inv_n - d0 * d2, c2[5].value() * inv_n - d1 * d2};
-            a.en[e] = n;
-            for (int q = 0; q < 5; ++q) { a.emean[5 * e + q] = mean[q]; S.mean[q] = mean[q]; }
-            for (int q = 0; q < 6; ++q) a.eR[6 * e + q] = R[q];
-            for (int q = 0; q < 3; ++q) S.rd[q] = R[q];
-            a.epsivar[e] = c2[6].value() * inv_n - d3 * d3;
+        // lane q < 12 finishes moment q (FP64, all lanes at once): lanes 0..4
+        // the means, 5..10 the central second moments uu vv ww uv uw vw, 11 the
+        // psi variance; each takes the sums it needs from lane 0
+        int ia = 0, ib = 0, ic = 0;  // first-moment sums used by this lane; ic: second-moment sum
+        if (lane < 5) ia = lane;
+        else if (lane < 11) {
+            const int k = lane - 5;  // uu vv ww uv uw vw
+            ia = k < 3 ? k : (k == 5 ? 1 : 0);
+            ib = k < 3 ? k : (k == 3 ? 1 : 2);
+            ic = k;
+        } else {
+            ia = ib = 3;
+            ic = 6;
         }
+        AccK A, Bq, Cq;
+#pragma unroll
+        for (int q = 0; q < 5; ++q) {
+            const float ss = __shfl_sync(0xffffffffu, m[q].s, 0), cc = __shfl_sync(0xffffffffu, m[q].c, 0);
+            if (ia == q) { A.s = ss; A.c = cc; }
+            if (ib == q) { Bq.s = ss; Bq.c = cc; }
+        }
+#pragma unroll
+        for (int q = 0; q < 7; ++q) {
+            const float ss = __shfl_sync(0xffffffffu, c2[q].s, 0), cc = __shfl_sync(0xffffffffu, c2[q].c, 0);
+            if (ic == q) { Cq.s = ss; Cq.c = cc; }
+        }
+        if (lane < 12) {
+            const double inv_n = 1.0 / n;
+            const double da = A.value() * inv_n;
+            double val;
+            if (lane < 5) {
+                const float shift = lane == 0 ? su : (lane == 1 ? sv : (lane == 2 ? sw : (lane == 3 ? sp : 0.f)));
+                val = shift + da;
+                a.emean[5 * e + lane] = val;
+                S.mean[lane] = val;
+            } else {
+                val = Cq.value() * inv_n - da * (Bq.value() * inv_n);
+                if (lane < 11) a.eR[6 * e + lane - 5] = val;
+                else a.epsivar[e] = val;
+                if (lane < 8) S.rd[lane - 5] = val;
+            }
+        }
+        if (lane == 0) a.en[e] = n;
     }
     T.sync();
 }
@@ -925,7 +957,7 @@ __device__ void sel_element(const MomArgs<float>& a, int e, int s0, int n, SelSm
     }
     T.sync();
     for (int b = T.tid; b < B; b += NT) {
-        const double cm = ldexp(__ull2double_rn(S.binsum[b]), -UNIT) / S.bincnt[b];
+        const double cm = __ull2double_rn(S.binsum[b]) * (1.0 / (double)(1ull << UNIT)) / S.bincnt[b];
         a.ecm[(size_t)B * e + b] = cm;
         a.ecmT[(size_t)B * e + b] = (float)cm;
     }
