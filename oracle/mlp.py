@@ -57,16 +57,20 @@ def bf16_round(a) -> np.ndarray:
     return r.view(np.float32)
 
 
-def forward(p, X, bf16: bool = False):
+def forward(p, X, bf16: bool = False, bf16_act: bool = False):
     """Network output Y[n][5] for standardised inputs X[n][10] (FP64
-    arithmetic; bf16=True first rounds the parameters to bfloat16)."""
+    arithmetic). bf16=True first rounds the parameters to bfloat16;
+    bf16_act=True also rounds the inputs and every hidden activation to
+    bfloat16 (the operands of a bf16 tensor-core product), the biases and
+    the accumulation staying exact."""
     if bf16:
         p = bf16_round(np.asarray(p, np.float32)).astype(np.float64)
     w = unpack(p)
-    X = np.asarray(X, np.float64)
-    a1 = silu(X @ w["W1"].T + w["b1"])
-    a2 = silu(a1 @ w["W2"].T + w["b2"])
-    a3 = silu(a2 @ w["W3"].T + w["b3"])
+    r = (lambda a: bf16_round(np.asarray(a, np.float32)).astype(np.float64)) if bf16_act else (lambda a: a)
+    X = r(np.asarray(X, np.float64))
+    a1 = r(silu(X @ w["W1"].T + w["b1"]))
+    a2 = r(silu(a1 @ w["W2"].T + w["b2"]))
+    a3 = r(silu(a2 @ w["W3"].T + w["b3"]))
     return a3 @ w["W4"].T + w["b4"]
 
 

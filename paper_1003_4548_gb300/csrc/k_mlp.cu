@@ -16,6 +16,7 @@
 #include <cmath>
 
 #include "pdf_internal.cuh"
+#include "tc.cuh"
 
 namespace {
 
@@ -328,8 +329,6 @@ int pdf_mlp_standardize(float* X, int64_t n, int32_t d, const float* mean, const
 // ---------------------------------------------------------------------------
 namespace {
 
-constexpr int SUR_THREADS = 256;
-constexpr int SUR_SMEM = sizeof(float) * (PDF_MLP_NPARAM + PDF_MLP_NNORM + 2 * H * (SUR_THREADS / 32));
 
 struct SurArgs {
     int nn;
@@ -377,94 +376,129 @@ __global__ void k_sur_harvest(SurArgs a, int nrows, const int* __restrict__ rows
 }
 
 // wp at the canonical nodes: the network at the free ones, the Dirichlet
-// value at the walls. One warp per node: lane l computes neurons l and l + 32
-// of each hidden layer. The bfloat16-rounded weights sit transposed in shared
-// memory (in x out), so the lanes read consecutive words, and the
-// activations of the warp's node are broadcast from shared memory.
-__global__ void __launch_bounds__(SUR_THREADS) k_sur_nodes(SurArgs a, const float* __restrict__ wq,
-                                                           const double* __restrict__ g, double* x) {
-    extern __shared__ float sm[];
-    float* WT1 = sm;                 // [IN][H]
-    float* WT2 = WT1 + IN * H;       // [H][H]
-    float* WT3 = WT2 + H * H;        // [H][H]
-    float* WT4 = WT3 + H * H;        // [H][OUT]
-    float* B = WT4 + H * OUT;        // b1 b2 b3 b4 (H, H, H, OUT)
-    float* nm = B + 3 * H + OUT;     // in_mean in_std out_mean out_std
-    float* act = nm + PDF_MLP_NNORM; // [warps][2][H]
-    for (int q = threadIdx.x; q < H * IN; q += SUR_THREADS) WT1[(q % IN) * H + q / IN] = wq[OFF_W1 + q];
-    for (int q = threadIdx.x; q < H * H; q += SUR_THREADS) {
-        WT2[(q % H) * H + q / H] = wq[OFF_W2 + q];
-        WT3[(q % H) * H + q / H] = wq[OFF_W3 + q];
+// value at the walls, on the 5th-generation tensor cores. One CTA of 128
+// threads takes 128 nodes (thread t: node row t). Every layer is one
+// 128 x N x K tcgen05 MMA chain: activations (A, bf16, K-major) and weights
+// (B = W, bf16, K-major: W is stored out x in) in shared memory, the FP32
+// accumulator in tensor memory. Thread t reads its row back (tensor-memory
+// lane t), adds the bias, applies SiLU and writes the bf16 activation row as
+// the next layer's A. Layer shapes: 128x64x16 (inputs padded to 16),
+// 128x64x64, 128x64x64, 128x16x64 (outputs padded to 16).
+constexpr int TC_M = 128;
+
+struct TcSmem {
+    __align__(128) uint16_t A[TC_M * H];  // activations, core-matrix layout (kc = 2 for layer 1, 8 after)
+    __align__(128) uint16_t W1[H * 16];   // 64 x 16
+    __align__(128) uint16_t W2[H * H];
+    __align__(128) uint16_t W3[H * H];
+    __align__(128) uint16_t W4[16 * H];   // 16 x 64 (rows 5..15 zero)
+    float bias[3 * H + 16];
+    float nm[PDF_MLP_NNORM];
+    __align__(8) uint64_t bar;
+    uint32_t tmem;
+};
+
+__device__ __forceinline__ uint16_t bf16_bits(float x) { return __bfloat16_as_ushort(__float2bfloat16_rn(x)); }
+
+__global__ void __launch_bounds__(TC_M) k_sur_nodes(SurArgs a, const float* __restrict__ wq,
+                                                    const double* __restrict__ g, double* x, int* status) {
+    __shared__ TcSmem S;
+    const int t = threadIdx.x, warp = t >> 5;
+    // weights (already bf16-rounded) into the canonical K-major layouts
+    for (int q = t; q < H * 16; q += TC_M) {
+        const int n = q / 16, k = q % 16;
+        S.W1[tc::core_offset(n, k, 2)] = bf16_bits(k < IN ? wq[OFF_W1 + IN * n + k] : 0.f);
     }
-    for (int q = threadIdx.x; q < OUT * H; q += SUR_THREADS) WT4[(q % H) * OUT + q / H] = wq[OFF_W4 + q];
-    for (int q = threadIdx.x; q < H; q += SUR_THREADS) {
-        B[q] = wq[OFF_B1 + q];
-        B[H + q] = wq[OFF_B2 + q];
-        B[2 * H + q] = wq[OFF_B3 + q];
+    for (int q = t; q < H * H; q += TC_M) {
+        const int n = q / H, k = q % H;
+        S.W2[tc::core_offset(n, k, 8)] = bf16_bits(wq[OFF_W2 + q]);
+        S.W3[tc::core_offset(n, k, 8)] = bf16_bits(wq[OFF_W3 + q]);
     }
-    if (threadIdx.x < OUT) B[3 * H + threadIdx.x] = wq[OFF_B4 + threadIdx.x];
-    if (threadIdx.x < PDF_MLP_NNORM) nm[threadIdx.x] = wq[PDF_MLP_NPARAM + threadIdx.x];
+    for (int q = t; q < 16 * H; q += TC_M) {
+        const int n = q / H, k = q % H;
+        S.W4[tc::core_offset(n, k, 8)] = bf16_bits(n < OUT ? wq[OFF_W4 + H * n + k] : 0.f);
+    }
+    for (int q = t; q < H; q += TC_M) {
+        S.bias[q] = wq[OFF_B1 + q];
+        S.bias[H + q] = wq[OFF_B2 + q];
+        S.bias[2 * H + q] = wq[OFF_B3 + q];
+    }
+    if (t < 16) S.bias[3 * H + t] = t < OUT ? wq[OFF_B4 + t] : 0.f;
+    if (t < PDF_MLP_NNORM) S.nm[t] = wq[PDF_MLP_NPARAM + t];
+    if (t == 0) tc::mbar_init(&S.bar, 1);
+    __syncwarp();
+    if (warp == 0) tc::tmem_alloc(&S.tmem, 64);
     __syncthreads();
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    float* h0 = act + wid * 2 * H;
-    float* h1 = h0 + H;
-    const int warps = gridDim.x * (SUR_THREADS / 32);
-    for (int i = blockIdx.x * (SUR_THREADS / 32) + wid; i < a.nn; i += warps) {
-        if (a.rep[i] != i) continue;
-        if (a.is_wall[i]) {
-            if (lane < NC) x[NC * (size_t)i + lane] = g[NC * (size_t)i + lane];
-            continue;
-        }
+    // this thread's node: standardised features as a bf16 row of A (kc = 2)
+    const int i = blockIdx.x * TC_M + t;
+    const bool row = i < a.nn && a.rep[i] == i;
+    const bool net = row && !a.is_wall[i];
+    double eps = 0.0;
+    {
         float f[IN];
-        double eps = 0.0;
-        if (lane == 0) {
-            node_features(a, i, f, eps);
+        if (net) node_features(a, i, f, eps);
 #pragma unroll
-            for (int q = 0; q < IN; ++q) h1[q] = (f[q] - nm[q]) / nm[IN + q];
+        for (int k = 0; k < 16; ++k) {
+            const float v = (net && k < IN) ? (f[k] - S.nm[k]) / S.nm[IN + k] : 0.f;
+            S.A[tc::core_offset(t, k, 2)] = bf16_bits(v);
         }
-        eps = __shfl_sync(0xffffffffu, eps, 0);
-        __syncwarp();
+    }
+    const uint32_t tmem = S.tmem;
+    const uint32_t lane_base = (uint32_t)(warp * 32) << 16;  // this warp's tensor-memory lanes
+    bool ok = true;
+    for (int layer = 0; layer < 4 && ok; ++layer) {
+        // make the shared-memory operands visible to the tensor cores
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        tc::fence_before_sync();
+        __syncthreads();
+        if (t == 0) {
+            tc::fence_after_sync();
+            const int kc = layer == 0 ? 2 : 8;
+            const int ksteps = layer == 0 ? 1 : 4;
+            const uint16_t* W = layer == 0 ? S.W1 : (layer == 1 ? S.W2 : (layer == 2 ? S.W3 : S.W4));
+            const uint32_t idesc = tc::idesc_bf16(TC_M, layer == 3 ? 16 : H);
+            for (int j = 0; j < ksteps; ++j) {
+                const uint64_t ad = tc::smem_desc(S.A + j * 128, 128, kc * 128);
+                const uint64_t bd = tc::smem_desc(W + j * 128, 128, kc * 128);
+                tc::mma_bf16(tmem, ad, bd, idesc, j > 0 ? 1u : 0u);
+            }
+            tc::commit(&S.bar);
+        }
+        ok = __syncthreads_and(tc::mbar_wait(&S.bar, (unsigned)(layer & 1)) ? 1 : 0) != 0;
+        tc::fence_after_sync();
+        if (!ok) break;
+        if (layer < 3) {
+            const float* bias = S.bias + layer * H;
 #pragma unroll
-        for (int q = 0; q < IN; ++q) f[q] = h1[q];
-        float z0 = B[lane], z1 = B[lane + 32];
+            for (int c0 = 0; c0 < H; c0 += 16) {
+                float v[16];
+                tc::ld16(tmem + lane_base + (uint32_t)c0, v);
 #pragma unroll
-        for (int q = 0; q < IN; ++q) {
-            z0 = fmaf(WT1[q * H + lane], f[q], z0);
-            z1 = fmaf(WT1[q * H + lane + 32], f[q], z1);
+                for (int k = 0; k < 16; ++k) S.A[tc::core_offset(t, c0 + k, 8)] = bf16_bits(silu(v[k] + bias[c0 + k]));
+            }
+            tc::fence_before_sync();
+        } else {
+            float v[16];
+            tc::ld16(tmem + lane_base, v);
+            if (net) {
+#pragma unroll
+                for (int o = 0; o < OUT; ++o) {
+                    const double y = (double)(v[o] + S.bias[3 * H + o]) * S.nm[2 * IN + OUT + o] + S.nm[2 * IN + o];
+                    x[NC * (size_t)i + o] = eps * y;
+                }
+            }
         }
-        h0[lane] = silu(z0);
-        h0[lane + 32] = silu(z1);
-        __syncwarp();
-        z0 = B[H + lane];
-        z1 = B[H + lane + 32];
-#pragma unroll 16
-        for (int q = 0; q < H; ++q) {
-            const float v = h0[q];
-            z0 = fmaf(WT2[q * H + lane], v, z0);
-            z1 = fmaf(WT2[q * H + lane + 32], v, z1);
-        }
-        h1[lane] = silu(z0);
-        h1[lane + 32] = silu(z1);
-        __syncwarp();
-        z0 = B[2 * H + lane];
-        z1 = B[2 * H + lane + 32];
-#pragma unroll 16
-        for (int q = 0; q < H; ++q) {
-            const float v = h1[q];
-            z0 = fmaf(WT3[q * H + lane], v, z0);
-            z1 = fmaf(WT3[q * H + lane + 32], v, z1);
-        }
-        h0[lane] = silu(z0);
-        h0[lane + 32] = silu(z1);
-        __syncwarp();
-        if (lane < OUT) {
-            float z = B[3 * H + lane];
-#pragma unroll 16
-            for (int q = 0; q < H; ++q) z = fmaf(WT4[q * OUT + lane], h0[q], z);
-            const double y = (double)z * nm[2 * IN + OUT + lane] + nm[2 * IN + lane];
-            x[NC * (size_t)i + lane] = eps * y;
-        }
-        __syncwarp();
+    }
+    if (!ok && t == 0) set_status(status, ST_BARRIER);
+    if (row && !net) {
+#pragma unroll
+        for (int q = 0; q < NC; ++q) x[NC * (size_t)i + q] = g[NC * (size_t)i + q];
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) {
+        tc::fence_after_sync();
+        tc::tmem_dealloc(tmem, 64);
     }
 }
 
@@ -600,9 +634,7 @@ int surrogate_rows(pdf_ctx* c) {
 int launch_surrogate(pdf_ctx* c) {
     const int nn = c->m.nn;
     const SurArgs a = sur_args(c);
-    const int warps_needed = (nn + 7) / 8;  // up to 8 nodes per warp
-    const int blocks = std::min(2 * c->num_sms, std::max(1, (warps_needed + SUR_THREADS / 32 - 1) / (SUR_THREADS / 32)));
-    k_sur_nodes<<<blocks, SUR_THREADS, SUR_SMEM, c->s>>>(a, c->sur_w, c->fe_g, c->fe_prop);
+    k_sur_nodes<<<(nn + TC_M - 1) / TC_M, TC_M, 0, c->s>>>(a, c->sur_w, c->fe_g, c->fe_prop, c->d_status);
     ResArgs r;
     r.nn = nn; r.rowptr = c->m.rowptr; r.colidx = c->m.colidx; r.mval = c->m.mval; r.aval = c->m.aval;
     r.rep = c->m.rep; r.is_wall = c->m.is_wall;
@@ -654,7 +686,6 @@ int pdf_set_surrogate(pdf_ctx* c, int32_t mode, const float* params, const float
         PDF_CUDA(c, cudaMalloc((void**)&c->sur_skip, sizeof(int)));
         PDF_CUDA(c, cudaMalloc((void**)&c->sur_cnt, 2 * sizeof(unsigned long long)));
         PDF_CUDA(c, cudaMalloc((void**)&c->sur_part, sizeof(double) * ((size_t)sur_blocks(c) * 4 * NC + 2)));
-        PDF_CUDA(c, cudaFuncSetAttribute(k_sur_nodes, cudaFuncAttributeMaxDynamicSharedMemorySize, SUR_SMEM));
     }
     std::vector<float> h(PDF_MLP_NPARAM + PDF_MLP_NNORM);
     for (int q = 0; q < PDF_MLP_NPARAM; ++q) h[q] = __bfloat162float(__float2bfloat16_rn(params[q]));

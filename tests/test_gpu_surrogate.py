@@ -187,14 +187,15 @@ def test_training_and_the_surrogate_in_the_step(torch, er_case):
     q = dev(torch, norm)
     s = torch.cuda.current_stream().cuda_stream
     capi.mlp_standardize(Xh.data_ptr(), rows, 10, q[0:].data_ptr(), q[10:].data_ptr(), s)
-    Y = torch.empty((rows, 5), dtype=torch.float32, device="cuda")
-    work = torch.empty(capi.mlp_work_floats(rows), dtype=torch.float32, device="cuda")
-    Pd = dev(torch, params)
-    capi.mlp_forward(Pd.data_ptr(), Xh.data_ptr(), rows, Y.data_ptr(), work.data_ptr(), True, s)
     torch.cuda.synchronize()
-    y = Y.cpu().numpy().astype(np.float64) * norm[25:30] + norm[20:25]
-    ok, err = close(Th.cpu().numpy(), y, 1e-5)
-    assert ok, err
+    # the node inference runs on the tensor cores with bf16 operands (weights,
+    # inputs, hidden activations) and FP32 accumulation: against the FP64
+    # oracle with the same bf16 operands, differences come from the FP32
+    # accumulation and the rare activation whose bf16 rounding it flips
+    y = mlp.forward(params, Xh.cpu().numpy(), bf16=True, bf16_act=True) * norm[25:30] + norm[20:25]
+    got = Th.cpu().numpy().astype(np.float64)
+    rel = np.abs(got - y) / (np.abs(y) + np.sqrt(np.mean(y * y, axis=0)))
+    assert np.quantile(rel, 0.99) < 2e-3 and rel.max() < 3e-2, (np.quantile(rel, 0.99), rel.max())
     solves, falls, res = g.surrogate_stats()
     assert solves == 1 and falls == 0 and res[0] > 0 and res[1] > 0
     wp_mlp = g.field("node_wp")

@@ -85,3 +85,22 @@ def test_features_by_hand():
     assert F[0, 3:7].tolist() == pytest.approx([5.0, 10.0, 15.0, 20.0])  # k/eps = 5
     assert F[0, 7:].tolist() == pytest.approx([0.5, -0.1, 0.3])
     assert mlp.targets(np.ones((2, 5)), eps)[1].tolist() == pytest.approx([500.0] * 5)
+
+
+def test_bf16_activation_mode_closed_form():
+    """With zero hidden weights the bf16-operand network is W4 bf16(SiLU(b3)) + b4
+    (bf16-rounded W4), whatever the inputs."""
+    rng = np.random.default_rng(8)
+    w = mlp.unpack(random_params(rng))
+    w["W1"][:] = 0.0
+    w["W2"][:] = 0.0
+    w["W3"][:] = 0.0
+    p = mlp.pack(w).astype(np.float32)
+    X = rng.normal(size=(4, mlp.IN))
+    Y = mlp.forward(p, X, bf16=True, bf16_act=True)
+    wq = mlp.unpack(mlp.bf16_round(p).astype(np.float64))
+    a3 = mlp.bf16_round(mlp.silu(wq["b3"]).astype(np.float32)).astype(np.float64)
+    assert np.allclose(Y, (wq["W4"] @ a3 + wq["b4"])[None, :], rtol=0, atol=1e-12)
+    # and it differs from the FP32-activation network by about a bf16 ulp
+    Yf = mlp.forward(p, X, bf16=True)
+    assert 0 < np.max(np.abs(Y - Yf)) < 0.05 * np.max(np.abs(Yf))
