@@ -45,6 +45,8 @@ def args_():
     ap.add_argument("--no-forms", action="store_true", help="skip the plain forms and the precision study")
     ap.add_argument("--save-surrogate", default=None, help="write the trained network (npz) here")
     ap.add_argument("--load-surrogate", default=None, help="use this trained network (npz) instead of training")
+    ap.add_argument("--surrogate-mode", type=int, default=1, choices=[1, 3],
+                    help="1: network at the nodes; 3: network at every particle inside the particle kernel")
     return ap.parse_args()
 
 
@@ -297,7 +299,7 @@ class Form:
         self.g.seed_particles(cfg["per_element"])
         self.g.estimate_stats()
         if sur is not None:
-            self.g.set_surrogate(1, sur["params"], sur["norm"], sur["tol"])
+            self.g.set_surrogate(sur.get("mode", 1), sur["params"], sur["norm"], sur["tol"])
         self.stream = stream
 
     def timed(self, dt, steps, warmup, dist=None, clocks=None):
@@ -569,6 +571,8 @@ def main():
         sur_info = {"loaded_from": os.path.basename(a.load_surrogate), "residual_tol": sur["tol"]}
     elif use_sur:
         sur, sur_info = prepare_surrogate(cfg, mesh, dt)
+    if sur is not None:
+        sur["mode"] = a.surrogate_mode
     if sur is not None and a.save_surrogate:
         np.savez(a.save_surrogate, params=sur["params"], norm=sur["norm"], tol=sur["tol"])
     prec = cfg["precision"]
@@ -591,7 +595,7 @@ def main():
     if use_sur:
         chosen.last_wp = chosen.g.field("node_wp")
         stated["surrogate"] = surrogate_error(chosen, mesh)
-        chosen.g.set_surrogate(1, sur["params"], sur["norm"], sur["tol"])
+        chosen.g.set_surrogate(sur["mode"], sur["params"], sur["norm"], sur["tol"])
 
     # end to end through the C ABI with host buffers: load the ensemble from
     # pinned host memory, then per step advance and read the element statistics

@@ -109,7 +109,10 @@ enum pdf_field {
     PDF_FIELD_NODE_WP = 20,  /* double[nnode][5] wp11,wp12,wp21,wp22,wp33 */
     PDF_FIELD_NODE_WDIST = 21, /* double[nnode] wall distance */
     PDF_FIELD_NODE_GRAD = 22,  /* double[nnode][4] recovered grad <U> */
-    PDF_FIELD_NODE_PSIVAR = 23 /* double[nnode] */
+    PDF_FIELD_NODE_PSIVAR = 23, /* double[nnode] */
+    PDF_FIELD_PARTICLE_WP = 24  /* float[n][5] wp at every particle, as used by the last step
+                                   (surrogate mode 4; rows in the order of the particles at the
+                                   start of that step) */
 };
 
 /* Kernel classes timed by pdf_kernel_time (CUDA events on the context stream). */
@@ -338,6 +341,13 @@ int pdf_surrogate_harvest(pdf_ctx* c, float* X, float* T);
  *          fine residual amplifies by (L/h)^2. Otherwise the FE solve runs to
  *          cg_tol from the previous solution.
  *  mode 2  the network's wp is used without the check (for measurement)
+ *  mode 3  per-particle form: as mode 1 at the nodes (the check and the FE
+ *          fallback), but when the check passes the particle kernel evaluates
+ *          the network at every particle on the tensor cores (inputs: the
+ *          standardised node features interpolated to the particle) and forms
+ *          G_ij and C0 eps there from the particle's wp and the interpolated
+ *          k, eps and stresses (FP32 state only, else PDF_ERR_ARG)
+ *  mode 4  mode 3, and every particle's wp is kept (PDF_FIELD_PARTICLE_WP)
  * Weights are rounded to bfloat16; inference accumulates in FP32. Requires
  * an elliptic-relaxation context (else PDF_ERR_ARG). */
 int pdf_set_surrogate(pdf_ctx* c, int32_t mode, const float* params, const float* norm, double residual_tol);

@@ -33,7 +33,7 @@ PRECISION = {"fp64": PDF_FP64, "fp32": PDF_FP32, "fp32_kahan": PDF_FP32_KAHAN}
 
 FIELD = dict(x=0, y=1, u=2, v=3, w=4, om=5, psi=6, id=7, elem=8, bin=9, elem_n=10, elem_mean=11, elem_R=12,
              elem_psivar=13, elem_cm=14, node_mean=15, node_R=16, node_ke=17, elem_der=18, node_pack=19,
-             node_wp=20, node_wdist=21, node_grad=22, node_psivar=23)
+             node_wp=20, node_wdist=21, node_grad=22, node_psivar=23, particle_wp=24)
 KERNEL = dict(particle=0, sort=1, moments=2, fields=3, elliptic=4)
 
 _DOUBLES = ("C1", "C2", "C3", "C4", "CT", "CL", "Ceta", "Cv", "gamma5", "Comega1", "Comega2", "Cs", "Ct",
@@ -286,9 +286,10 @@ class Canyon:
     def field_shape(self, name: str):
         n = self.num_particles
         w = dict(elem_mean=5, elem_R=6, elem_cm=self.nbins, node_mean=4, node_R=6, node_ke=2, elem_der=9,
-                 node_pack=11, node_wp=5, node_grad=4).get(name, 1)
-        rows = n if FIELD[name] <= 9 else (self.nt if name.startswith("elem") else self.nn)
-        dt = {"id": np.uint32, "elem": np.int32, "bin": np.uint8, "elem_n": np.int32}.get(name, np.float64)
+                 node_pack=11, node_wp=5, node_grad=4, particle_wp=5).get(name, 1)
+        rows = n if (FIELD[name] <= 9 or name == "particle_wp") else (self.nt if name.startswith("elem") else self.nn)
+        dt = {"id": np.uint32, "elem": np.int32, "bin": np.uint8, "elem_n": np.int32,
+              "particle_wp": np.float32}.get(name, np.float64)
         return (rows, w) if w > 1 else (rows,), dt
 
     def field(self, name: str) -> np.ndarray:

@@ -604,6 +604,10 @@ int pdf_get_fields(pdf_ctx* c, int32_t field, void* dst, size_t bytes, int32_t d
     case PDF_FIELD_NODE_WDIST: src = c->m.wdist; need = 8 * (size_t)nn; break;
     case PDF_FIELD_NODE_GRAD: src = c->ngrad; need = 8 * 4 * (size_t)nn; break;
     case PDF_FIELD_NODE_PSIVAR: src = c->npsivar; need = 8 * (size_t)nn; break;
+    case PDF_FIELD_PARTICLE_WP:
+        if (c->sur_mode != 4 || !c->pwp || c->pwp_n < n)
+            return fail(c, PDF_ERR_STATE, "particle wp is recorded in surrogate mode 4 only");
+        src = c->pwp; need = 4 * 5 * (size_t)n; break;
     default: return fail(c, PDF_ERR_ARG, "unknown field id");
     }
     if (bytes != need) return fail(c, PDF_ERR_ARG, "field size mismatch: expected " + std::to_string(need));
@@ -680,7 +684,7 @@ void pdf_destroy(pdf_ctx* c) {
                    c->emean, c->eR, c->epsivar, c->ecm, c->nwt, c->nmean, c->nR, c->nke, c->npsivar, c->eder,
                    c->ngrad, c->npack, c->nwp, c->npackT, c->epackT, c->ecmT, c->sort_scratch, c->fe_f, c->fe_g,
                    c->fe_prop, c->fe_z, c->fe_part, c->fe_bar, c->fe_iters, c->d_status,
-                   c->conv_buf, c->elist, c->d_step, c->sur_w, c->sur_rows, c->sur_skip, c->sur_cnt, c->sur_part};
+                   c->conv_buf, c->elist, c->d_step, c->nsurT, c->pwp, c->sur_w, c->sur_rows, c->sur_skip, c->sur_cnt, c->sur_part};
     for (void* p : dev) cudaFree(p);
     for (int k = 0; k < 7; ++k) {
         cudaFree(c->stA[k]);

@@ -15,6 +15,7 @@
 #include <algorithm>
 #include <cmath>
 
+#include "mlp_tc.cuh"
 #include "pdf_internal.cuh"
 #include "tc.cuh"
 
@@ -361,6 +362,25 @@ __device__ void node_features(const SurArgs& a, int i, float f[IN], double& eps)
     f[9] = (float)a.nR[6 * i + 1] * ik;
 }
 
+// node pack of the per-particle form: standardised features, then k, eps,
+// uu, vv, ww, uv (every node: the particle kernel interpolates over elements)
+__global__ void k_sur_featpack(SurArgs a, const float* __restrict__ nm, float* pack) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.nn) return;
+    float f[IN];
+    double eps;
+    node_features(a, i, f, eps);
+    float* o = pack + 16 * (size_t)i;
+#pragma unroll
+    for (int q = 0; q < IN; ++q) o[q] = (f[q] - nm[q]) / nm[IN + q];
+    o[10] = (float)a.nke[2 * i];
+    o[11] = (float)eps;
+    o[12] = (float)a.nR[6 * i + 0];
+    o[13] = (float)a.nR[6 * i + 1];
+    o[14] = (float)a.nR[6 * i + 2];
+    o[15] = (float)a.nR[6 * i + 3];
+}
+
 __global__ void k_sur_harvest(SurArgs a, int nrows, const int* __restrict__ rows, const double* __restrict__ wp,
                               float* X, float* T) {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
@@ -375,61 +395,27 @@ __global__ void k_sur_harvest(SurArgs a, int nrows, const int* __restrict__ rows
     for (int q = 0; q < OUT; ++q) T[(size_t)OUT * r + q] = (float)(wp[NC * (size_t)i + q] / eps);
 }
 
-// wp at the canonical nodes: the network at the free ones, the Dirichlet
-// value at the walls, on the 5th-generation tensor cores. One CTA of 128
-// threads takes 128 nodes (thread t: node row t). Every layer is one
-// 128 x N x K tcgen05 MMA chain: activations (A, bf16, K-major) and weights
-// (B = W, bf16, K-major: W is stored out x in) in shared memory, the FP32
-// accumulator in tensor memory. Thread t reads its row back (tensor-memory
-// lane t), adds the bias, applies SiLU and writes the bf16 activation row as
-// the next layer's A. Layer shapes: 128x64x16 (inputs padded to 16),
-// 128x64x64, 128x64x64, 128x16x64 (outputs padded to 16).
-constexpr int TC_M = 128;
+// wp at the canonical nodes: the network at the free ones (tensor cores, one
+// CTA of 128 threads per 128 nodes, thread t: node row t), the Dirichlet value
+// at the walls.
+constexpr int TC_M = mlptc::TILE_ROWS;
 
 struct TcSmem {
-    __align__(128) uint16_t A[TC_M * H];  // activations, core-matrix layout (kc = 2 for layer 1, 8 after)
-    __align__(128) uint16_t W1[H * 16];   // 64 x 16
-    __align__(128) uint16_t W2[H * H];
-    __align__(128) uint16_t W3[H * H];
-    __align__(128) uint16_t W4[16 * H];   // 16 x 64 (rows 5..15 zero)
-    float bias[3 * H + 16];
-    float nm[PDF_MLP_NNORM];
+    __align__(128) uint16_t A[mlptc::TILE_ELEMS];
+    mlptc::Weights W;
     __align__(8) uint64_t bar;
     uint32_t tmem;
 };
-
-__device__ __forceinline__ uint16_t bf16_bits(float x) { return __bfloat16_as_ushort(__float2bfloat16_rn(x)); }
 
 __global__ void __launch_bounds__(TC_M) k_sur_nodes(SurArgs a, const float* __restrict__ wq,
                                                     const double* __restrict__ g, double* x, int* status) {
     __shared__ TcSmem S;
     const int t = threadIdx.x, warp = t >> 5;
-    // weights (already bf16-rounded) into the canonical K-major layouts
-    for (int q = t; q < H * 16; q += TC_M) {
-        const int n = q / 16, k = q % 16;
-        S.W1[tc::core_offset(n, k, 2)] = bf16_bits(k < IN ? wq[OFF_W1 + IN * n + k] : 0.f);
-    }
-    for (int q = t; q < H * H; q += TC_M) {
-        const int n = q / H, k = q % H;
-        S.W2[tc::core_offset(n, k, 8)] = bf16_bits(wq[OFF_W2 + q]);
-        S.W3[tc::core_offset(n, k, 8)] = bf16_bits(wq[OFF_W3 + q]);
-    }
-    for (int q = t; q < 16 * H; q += TC_M) {
-        const int n = q / H, k = q % H;
-        S.W4[tc::core_offset(n, k, 8)] = bf16_bits(n < OUT ? wq[OFF_W4 + H * n + k] : 0.f);
-    }
-    for (int q = t; q < H; q += TC_M) {
-        S.bias[q] = wq[OFF_B1 + q];
-        S.bias[H + q] = wq[OFF_B2 + q];
-        S.bias[2 * H + q] = wq[OFF_B3 + q];
-    }
-    if (t < 16) S.bias[3 * H + t] = t < OUT ? wq[OFF_B4 + t] : 0.f;
-    if (t < PDF_MLP_NNORM) S.nm[t] = wq[PDF_MLP_NPARAM + t];
+    mlptc::load(S.W, wq, t, TC_M);
     if (t == 0) tc::mbar_init(&S.bar, 1);
     __syncwarp();
     if (warp == 0) tc::tmem_alloc(&S.tmem, 64);
     __syncthreads();
-    // this thread's node: standardised features as a bf16 row of A (kc = 2)
     const int i = blockIdx.x * TC_M + t;
     const bool row = i < a.nn && a.rep[i] == i;
     const bool net = row && !a.is_wall[i];
@@ -438,55 +424,18 @@ __global__ void __launch_bounds__(TC_M) k_sur_nodes(SurArgs a, const float* __re
         float f[IN];
         if (net) node_features(a, i, f, eps);
 #pragma unroll
-        for (int k = 0; k < 16; ++k) {
-            const float v = (net && k < IN) ? (f[k] - S.nm[k]) / S.nm[IN + k] : 0.f;
-            S.A[tc::core_offset(t, k, 2)] = bf16_bits(v);
-        }
+        for (int k = 0; k < 16; ++k)
+            mlptc::put_input(S.A, t, k, (net && k < IN) ? (f[k] - S.W.nm[k]) / S.W.nm[IN + k] : 0.f);
     }
     const uint32_t tmem = S.tmem;
-    const uint32_t lane_base = (uint32_t)(warp * 32) << 16;  // this warp's tensor-memory lanes
-    bool ok = true;
-    for (int layer = 0; layer < 4 && ok; ++layer) {
-        // make the shared-memory operands visible to the tensor cores
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        tc::fence_before_sync();
-        __syncthreads();
-        if (t == 0) {
-            tc::fence_after_sync();
-            const int kc = layer == 0 ? 2 : 8;
-            const int ksteps = layer == 0 ? 1 : 4;
-            const uint16_t* W = layer == 0 ? S.W1 : (layer == 1 ? S.W2 : (layer == 2 ? S.W3 : S.W4));
-            const uint32_t idesc = tc::idesc_bf16(TC_M, layer == 3 ? 16 : H);
-            for (int j = 0; j < ksteps; ++j) {
-                const uint64_t ad = tc::smem_desc(S.A + j * 128, 128, kc * 128);
-                const uint64_t bd = tc::smem_desc(W + j * 128, 128, kc * 128);
-                tc::mma_bf16(tmem, ad, bd, idesc, j > 0 ? 1u : 0u);
-            }
-            tc::commit(&S.bar);
-        }
-        ok = __syncthreads_and(tc::mbar_wait(&S.bar, (unsigned)(layer & 1)) ? 1 : 0) != 0;
-        tc::fence_after_sync();
-        if (!ok) break;
-        if (layer < 3) {
-            const float* bias = S.bias + layer * H;
+    unsigned phase = 0;
+    float y[16];
+    const bool ok = mlptc::run(S.W, S.A, 1, tmem, &S.bar, phase, y);
+    if (ok && net) {
 #pragma unroll
-            for (int c0 = 0; c0 < H; c0 += 16) {
-                float v[16];
-                tc::ld16(tmem + lane_base + (uint32_t)c0, v);
-#pragma unroll
-                for (int k = 0; k < 16; ++k) S.A[tc::core_offset(t, c0 + k, 8)] = bf16_bits(silu(v[k] + bias[c0 + k]));
-            }
-            tc::fence_before_sync();
-        } else {
-            float v[16];
-            tc::ld16(tmem + lane_base, v);
-            if (net) {
-#pragma unroll
-                for (int o = 0; o < OUT; ++o) {
-                    const double y = (double)(v[o] + S.bias[3 * H + o]) * S.nm[2 * IN + OUT + o] + S.nm[2 * IN + o];
-                    x[NC * (size_t)i + o] = eps * y;
-                }
-            }
+        for (int o = 0; o < OUT; ++o) {
+            const double yo = (double)y[o] * S.W.nm[2 * IN + OUT + o] + S.W.nm[2 * IN + o];
+            x[NC * (size_t)i + o] = eps * yo;
         }
     }
     if (!ok && t == 0) set_status(status, ST_BARRIER);
@@ -644,6 +593,10 @@ int launch_surrogate(pdf_ctx* c) {
     k_sur_decide<<<1, 32, 0, c->s>>>(c->sur_part, nb, c->sur_mode, c->sur_tol, c->sur_skip, c->sur_cnt,
                                      c->sur_part + (size_t)nb * 4 * NC);
     c->launches += 3;
+    if (c->sur_mode >= 3) {
+        k_sur_featpack<<<(nn + 127) / 128, 128, 0, c->s>>>(a, c->sur_w + PDF_MLP_NPARAM, c->nsurT);
+        ++c->launches;
+    }
     PDF_CUDA(c, cudaGetLastError());
     return PDF_OK;
 }
@@ -671,7 +624,8 @@ int pdf_surrogate_harvest(pdf_ctx* c, float* X, float* T) {
 
 int pdf_set_surrogate(pdf_ctx* c, int32_t mode, const float* params, const float* norm, double residual_tol) {
     if (!c) return PDF_ERR_ARG;
-    if (mode < 0 || mode > 2) return fail(c, PDF_ERR_ARG, "surrogate mode must be 0, 1 or 2");
+    if (mode < 0 || mode > 4) return fail(c, PDF_ERR_ARG, "surrogate mode must be 0 .. 4");
+    if (mode >= 3 && c->prec == 0) return fail(c, PDF_ERR_ARG, "the per-particle surrogate needs an FP32 state");
     if (mode == 0) {
         c->sur_mode = 0;
         return PDF_OK;
@@ -681,6 +635,14 @@ int pdf_set_surrogate(pdf_ctx* c, int32_t mode, const float* params, const float
     for (int q = 0; q < PDF_MLP_NNORM; ++q)
         if (!std::isfinite(norm[q]) || (((q >= IN && q < 2 * IN) || q >= 2 * IN + OUT) && !(norm[q] > 0.f)))
             return fail(c, PDF_ERR_ARG, "surrogate: standard deviations must be positive and finite");
+    if (mode >= 3 && !c->nsurT) PDF_CUDA(c, cudaMalloc((void**)&c->nsurT, sizeof(float) * 16 * (size_t)c->m.nn));
+    if (mode == 4 && c->pwp_n < c->np) {
+        cudaFree(c->pwp);
+        c->pwp = nullptr;
+        c->pwp_n = 0;
+        PDF_CUDA(c, cudaMalloc((void**)&c->pwp, sizeof(float) * 5 * (size_t)std::max<int64_t>(c->np, 1)));
+        c->pwp_n = c->np;
+    }
     if (!c->sur_w) {
         PDF_CUDA(c, cudaMalloc((void**)&c->sur_w, sizeof(float) * (PDF_MLP_NPARAM + PDF_MLP_NNORM)));
         PDF_CUDA(c, cudaMalloc((void**)&c->sur_skip, sizeof(int)));

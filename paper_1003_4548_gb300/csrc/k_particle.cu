@@ -13,6 +13,7 @@
 //   element walk to the new host element, and the continuous source.
 #include <algorithm>
 
+#include "mlp_tc.cuh"
 #include "pdf_internal.cuh"
 
 namespace {
@@ -82,6 +83,11 @@ struct StepArgs {
     int* status;
     int B, wall_model, mix_exp, reflect_max;
     T C3, C4, C0, Cmu_half, kappa, E, yp, beta, fx, fy, x0, y0, r0, period, floor_k, floor_om;
+    // per-particle surrogate (FP32 state only)
+    const float* __restrict__ nsur;   // node pack: 10 standardised features, k, eps, uu, vv, ww, uv
+    const float* __restrict__ surw;   // bf16-rounded parameters, then the standardisation
+    const int* __restrict__ sur_ok;   // the network passed this step's residual check
+    float* pwp;                       // wp of every particle (mode 4), or NULL
 };
 
 // velocity and frequency at a boundary hit: tag 2 symmetry; tag 1 wall
@@ -125,10 +131,10 @@ __device__ void reflect(const StepArgs<T>& a, int tag, T nx, T ny, const double*
 
 // one particle-step of particle i whose state at step n was staged in
 // shared memory; writes the state at step n+1 in place
-template <typename T>
+template <typename T, bool SUR = false>
 __device__ __forceinline__ void advance_particle(const StepArgs<T>& a, const uint32_t step, const int i, const T x,
                                                  const T y, T u, T v, T w, T om, T psi, const uint32_t pid,
-                                                 const int e0, const int b) {
+                                                 const int e0, const int b, const float* ysur = nullptr) {
 
     // barycentric coordinates in the host element
     T g[EGEO_W];
@@ -146,6 +152,42 @@ __device__ __forceinline__ void advance_particle(const StepArgs<T>& a, const uin
         load_pack<NODE_PACK_W>(a.npack + NODE_PACK_W * n2, Cv);
 #pragma unroll
         for (int q = 0; q < 11; ++q) F[q] = l0 * A[q] + l1 * Bv[q] + l2 * Cv[q];
+    }
+    if constexpr (SUR) {
+        if (ysur != nullptr) {
+            // wp of the network at this particle (standardised outputs in ysur),
+            // then G_ij and C0 eps from it as Eqs. Gij and C0 do at the nodes,
+            // with k, eps and the stresses interpolated to the particle
+            float kk = 0.f, ee = 0.f, R[4] = {0.f, 0.f, 0.f, 0.f};
+            const int nd[3] = {n0, n1, n2};
+            const T lw[3] = {l0, l1, l2};
+#pragma unroll
+            for (int m = 0; m < 3; ++m) {
+                const float4 ke = __ldg(reinterpret_cast<const float4*>(a.nsur + 16 * (size_t)nd[m]) + 2);
+                const float4 rr = __ldg(reinterpret_cast<const float4*>(a.nsur + 16 * (size_t)nd[m]) + 3);
+                kk += lw[m] * ke.z;
+                ee += lw[m] * ke.w;
+                R[0] += lw[m] * rr.x; R[1] += lw[m] * rr.y; R[2] += lw[m] * rr.z; R[3] += lw[m] * rr.w;
+            }
+            kk = kk > (float)a.floor_k ? kk : (float)a.floor_k;
+            const float* nm = a.surw + PDF_MLP_NPARAM;
+            float wp[5];
+#pragma unroll
+            for (int o = 0; o < 5; ++o) wp[o] = ee * (ysur[o] * nm[25 + o] + nm[20 + o]);
+            const float ik = 1.f / kk, h2k = 0.5f * ik;
+            F[4] = (T)((2.f * wp[0] - ee) * h2k);
+            F[5] = (T)(wp[1] * ik);
+            F[6] = (T)(wp[2] * ik);
+            F[7] = (T)((2.f * wp[3] - ee) * h2k);
+            F[8] = (T)((2.f * wp[4] - ee) * h2k);
+            const float s = wp[0] * R[0] + (wp[1] + wp[2]) * R[3] + wp[3] * R[1] + wp[4] * R[2];
+            const float c0e = -2.f * s * ik * (1.f / 3.f);
+            F[3] = (T)(c0e > 0.f ? c0e : 0.f);
+            if (a.pwp != nullptr) {
+#pragma unroll
+                for (int o = 0; o < 5; ++o) a.pwp[5 * (size_t)i + o] = wp[o];
+            }
+        }
     }
     T ep[ELEM_PACK_W];
     load_pack<ELEM_PACK_W>(a.epack + ELEM_PACK_W * e0, ep);
@@ -458,10 +500,109 @@ StepArgs<T> step_args(pdf_ctx* c, double dt) {
     a.fx = (T)p.fx; a.fy = (T)p.fy;
     a.x0 = (T)p.x0; a.y0 = (T)p.y0; a.r0 = (T)p.r0; a.period = (T)p.period;
     a.floor_k = (T)p.floor_k; a.floor_om = (T)p.floor_omega;
+    a.nsur = nullptr; a.surw = nullptr; a.sur_ok = nullptr; a.pwp = nullptr;
     return a;
 }
 
 }  // namespace
+
+// ---------------------------------------------------------------------------
+// Per-particle form of the surrogate (modes 3, 4): the staged step kernel
+// with the network evaluated at every particle on the tensor cores. A block
+// of 256 threads is two 128-row tiles; each particle's row holds the
+// standardised node features interpolated to it. The outputs (wp / eps,
+// standardised) go to shared memory, and advance_particle forms G_ij and
+// C0 eps from them. When this step's residual check failed, the kernel
+// takes G_ij from the node pack (the FE solve) and skips the network.
+// ---------------------------------------------------------------------------
+struct SurShared {
+    __align__(128) uint16_t A[2 * mlptc::TILE_ELEMS];
+    mlptc::Weights W;
+    float Y[TILE][5];
+    __align__(8) uint64_t bar;
+    uint32_t tmem;
+};
+
+constexpr size_t SUR_STEP_SMEM = 2 * sizeof(Stage<float>) + sizeof(SurShared) + 128;
+
+__global__ void __launch_bounds__(TILE) k_step_sur(const StepArgs<float> a) {
+    extern __shared__ __align__(128) unsigned char dsm[];
+    Stage<float>* st = reinterpret_cast<Stage<float>*>(dsm);
+    SurShared& U = *reinterpret_cast<SurShared*>(dsm + 2 * sizeof(Stage<float>));
+    __shared__ __align__(8) uint64_t bar[2];
+    const int64_t ntiles = (a.n + TILE - 1) / TILE;
+    const bool use_net = *a.sur_ok != 0;  // uniform over the grid
+    const int warp = threadIdx.x >> 5;
+    if (use_net) mlptc::load(U.W, a.surw, threadIdx.x, TILE);
+    if (threadIdx.x == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        if (use_net) tc::mbar_init(&U.bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncwarp();
+    if (use_net && warp == 0) tc::tmem_alloc(&U.tmem, 128);
+    __syncthreads();
+    const uint32_t tmem = use_net ? U.tmem : 0u;
+    unsigned phase = 0;
+    bool net_ok = true;
+    const uint32_t step = *a.stepp;
+    int64_t t = blockIdx.x;
+    if (threadIdx.x == 0 && t < ntiles) stage_tile(a, st[0], &bar[0], t * TILE, (int)min((int64_t)TILE, a.n - t * TILE));
+    for (int k = 0; t < ntiles; t += gridDim.x, ++k) {
+        const int s = k & 1;
+        const int64_t tn = t + gridDim.x;
+        if (threadIdx.x == 0 && tn < ntiles) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            stage_tile(a, st[s ^ 1], &bar[s ^ 1], tn * TILE, (int)min((int64_t)TILE, a.n - tn * TILE));
+        }
+        mbar_wait(&bar[s], (unsigned)((k >> 1) & 1), a.status);
+        const int64_t i = t * TILE + threadIdx.x;
+        const int j = threadIdx.x;
+        const Stage<float>& q = st[s];
+        if (use_net && net_ok) {
+            // inputs: the node features interpolated to the particle
+            float f[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+            if (i < a.n) {
+                const int e0 = q.elem[j];
+                float g[EGEO_W];
+                load_pack<EGEO_W>(a.egeo + EGEO_W * e0, g);
+                const float dx = q.s[0][j] - g[0], dy = q.s[1][j] - g[1];
+                const float lw[3] = {g[2] * dx + g[3] * dy + g[4], g[5] * dx + g[6] * dy + g[7],
+                                     g[8] * dx + g[9] * dy + g[10]};
+#pragma unroll
+                for (int m = 0; m < 3; ++m) {
+                    const float4* np4 = reinterpret_cast<const float4*>(a.nsur + 16 * (size_t)a.tri[3 * e0 + m]);
+                    const float4 f0 = __ldg(np4), f1 = __ldg(np4 + 1), f2 = __ldg(np4 + 2);
+                    f[0] += lw[m] * f0.x; f[1] += lw[m] * f0.y; f[2] += lw[m] * f0.z; f[3] += lw[m] * f0.w;
+                    f[4] += lw[m] * f1.x; f[5] += lw[m] * f1.y; f[6] += lw[m] * f1.z; f[7] += lw[m] * f1.w;
+                    f[8] += lw[m] * f2.x; f[9] += lw[m] * f2.y;
+                }
+            }
+            uint16_t* tileA = U.A + (j >> 7) * mlptc::TILE_ELEMS;
+#pragma unroll
+            for (int kk = 0; kk < 16; ++kk) mlptc::put_input(tileA, j & 127, kk, kk < 10 ? f[kk] : 0.f);
+            float y[16];
+            net_ok = mlptc::run(U.W, U.A, 2, tmem, &U.bar, phase, y);
+#pragma unroll
+            for (int o = 0; o < 5; ++o) U.Y[j][o] = y[o];
+            if (!net_ok && threadIdx.x == 0) set_status(a.status, ST_BARRIER);
+        }
+        if (i < a.n)
+            advance_particle<float, true>(a, step, (int)i, q.s[0][j], q.s[1][j], q.s[2][j], q.s[3][j], q.s[4][j],
+                                          q.s[5][j], q.s[6][j], q.id[j], q.elem[j], (int)q.bin[j],
+                                          (use_net && net_ok) ? U.Y[j] : nullptr);
+        __syncthreads();
+    }
+    if (use_net) {
+        tc::fence_before_sync();
+        __syncthreads();
+        if (warp == 0) {
+            tc::fence_after_sync();
+            tc::tmem_dealloc(tmem, 128);
+        }
+    }
+}
 
 // persistent grid of the particle kernel: per_sm blocks on every SM (0: as
 // many as are resident)
@@ -490,8 +631,28 @@ int launch_particle_step(pdf_ctx* c, double dt) {
         if (st != PDF_OK) return st;
     }
     const int64_t ntiles = (c->np + TILE - 1) / TILE;
-    const unsigned blocks = (unsigned)std::min<int64_t>(ntiles, c->step_blocks);
     timing_begin(c, PDF_K_PARTICLE);
+    if (c->sur_mode >= 3 && c->prec != 0) {
+        if (!c->step_sur_blocks) {
+            int per_sm = 0;
+            PDF_CUDA(c, cudaFuncSetAttribute(k_step_sur, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)SUR_STEP_SMEM));
+            PDF_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step_sur, TILE, SUR_STEP_SMEM));
+            c->step_sur_blocks = std::max(1, std::min(per_sm, 4)) * c->num_sms;  // 128 TMEM columns each
+        }
+        StepArgs<float> sa = step_args<float>(c, dt);
+        sa.nsur = c->nsurT;
+        sa.surw = c->sur_w;
+        sa.sur_ok = c->sur_skip;
+        sa.pwp = (c->sur_mode == 4 && c->pwp_n >= c->np) ? c->pwp : nullptr;
+        const unsigned blocks = (unsigned)std::min<int64_t>(ntiles, c->step_sur_blocks);
+        k_step_sur<<<blocks, TILE, SUR_STEP_SMEM, c->s>>>(sa);
+        ++c->launches;
+        timing_end(c, PDF_K_PARTICLE);
+        PDF_CUDA(c, cudaGetLastError());
+        return PDF_OK;
+    }
+    const unsigned blocks = (unsigned)std::min<int64_t>(ntiles, c->step_blocks);
     if (c->prec == 0)
         k_step<double><<<blocks, TILE, 0, c->s>>>(step_args<double>(c, dt));
     else

@@ -123,6 +123,10 @@ struct pdf_ctx {
     int* sur_skip = nullptr;              // 1: the network's wp passed the residual check this step
     unsigned long long* sur_cnt = nullptr;  // solves, fallbacks
     double* sur_part = nullptr;           // per-block residual partial sums, then the last residual
+    float* nsurT = nullptr;               // per-particle form: node pack [nn][16] (10 standardised
+                                          // features, k, eps, uu, vv, ww, uv)
+    float* pwp = nullptr;                 // per-particle form, mode 4: wp of every particle [n][5]
+    int64_t pwp_n = 0;
     // status
     int* d_status = nullptr;
     int* h_status = nullptr;
@@ -132,6 +136,7 @@ struct pdf_ctx {
     int timing = 0;
     int64_t launches = 0;  // kernels launched by this context
     int step_blocks = 0;   // persistent grid of the particle kernel
+    int step_sur_blocks = 0;  // persistent grid of the per-particle surrogate form
     int scatter_threads = 256;  // block size of the re-sort scatter
     cudaEvent_t coop_wait = nullptr, coop_done = nullptr;  // batch: chain of the cooperative CG launches
     std::string err;

@@ -222,3 +222,65 @@ def test_training_and_the_surrogate_in_the_step(torch, er_case):
         assert np.array_equal(a.field(k)[oa], b.field(k)[ob]), k
     a.close()
     b.close()
+
+
+def test_per_particle_form(torch, er_case):
+    """Modes 3/4: the network inside the particle kernel. With a zero
+    tolerance the check always fails and the step must equal the FE step
+    exactly; with the check disabled the kernel's per-particle wp must match
+    the FP64 oracle network (same bf16 operands) on the node features
+    interpolated to the particle."""
+    from paper_1003_4548_gb300 import Canyon, canyon_params
+    mesh, make = er_case
+    X, T, params, norm, hist = _trained_surrogate(torch, mesh, make)
+    dt = _dt(mesh)
+
+    def make32(**kw):
+        return Canyon(canyon_params(mesh, wall_model="er", precision="fp32", C0=2.1, seed=9, cg_tol=1e-10,
+                                    cg_maxit=20000, **kw), mesh, stream=torch.cuda.current_stream().cuda_stream)
+
+    a, b = make32(), make32()
+    for c in (a, b):
+        c.seed_particles(32)
+        c.estimate_stats()
+    b.set_surrogate(3, params, norm, 0.0)
+    for c in (a, b):
+        c.step(dt, 2)
+        c.sync()
+    assert b.surrogate_stats()[1] == 2  # both steps fell back
+    oa, ob = np.argsort(a.field("id")), np.argsort(b.field("id"))
+    for k in ("x", "u", "v", "om", "psi"):
+        assert np.array_equal(a.field(k)[oa], b.field(k)[ob]), k
+    a.close()
+    b.close()
+
+    g = make32()
+    g.seed_particles(32)
+    g.estimate_stats()
+    g.set_surrogate(4, params, norm, 1e30)
+    g.estimate_stats()  # statistics and the check of this mode
+    P = g.particles()
+    ke, gr, R, wd = (g.field(k) for k in ("node_ke", "node_grad", "node_R", "node_wdist"))
+    g.step(dt, 1)
+    g.sync()
+    wp = g.field("particle_wp").astype(np.float64)
+    Fn = (mlp.features(wd, ke[:, 0], ke[:, 1], gr, R) - norm[:10]) / norm[10:20]
+    xy, tri = mesh["xy"], mesh["tri"][P["elem"]]
+    A, Bq, Cq = xy[tri[:, 0]], xy[tri[:, 1]], xy[tri[:, 2]]
+    Xp = np.stack([P["x"], P["y"]], 1)
+
+    def orient(p, q, r):
+        return (q[:, 0] - p[:, 0]) * (r[:, 1] - p[:, 1]) - (q[:, 1] - p[:, 1]) * (r[:, 0] - p[:, 0])
+
+    area = orient(A, Bq, Cq)
+    lam = np.stack([orient(Bq, Cq, Xp), orient(Cq, A, Xp), orient(A, Bq, Xp)], 1) / area[:, None]
+    fp = sum(lam[:, m:m + 1] * Fn[tri[:, m]] for m in range(3))
+    eps_p = sum(lam[:, m] * ke[tri[:, m], 1] for m in range(3))
+    y = mlp.forward(params, fp, bf16=True, bf16_act=True)
+    expect = eps_p[:, None] * (y * norm[25:30] + norm[20:25])
+    rel = np.abs(wp - expect) / (np.abs(expect) + np.sqrt(np.mean(expect * expect, axis=0)))
+    assert np.quantile(rel, 0.99) < 3e-3 and rel.max() < 5e-2, (np.quantile(rel, 0.99), rel.max())
+    g.step(dt, 4)
+    g.sync()
+    assert g.surrogate_stats()[1] == 0
+    g.close()
