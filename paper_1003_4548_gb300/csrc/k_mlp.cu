@@ -421,11 +421,11 @@ __global__ void __launch_bounds__(TC_M) k_sur_nodes(SurArgs a, const float* __re
     const bool net = row && !a.is_wall[i];
     double eps = 0.0;
     {
-        float f[IN];
+        float f[IN], in[16];
         if (net) node_features(a, i, f, eps);
 #pragma unroll
-        for (int k = 0; k < 16; ++k)
-            mlptc::put_input(S.A, t, k, (net && k < IN) ? (f[k] - S.W.nm[k]) / S.W.nm[IN + k] : 0.f);
+        for (int k = 0; k < 16; ++k) in[k] = (net && k < IN) ? (f[k] - S.W.nm[k]) / S.W.nm[IN + k] : 0.f;
+        mlptc::put_inputs(S.A, t, in);
     }
     const uint32_t tmem = S.tmem;
     unsigned phase = 0;

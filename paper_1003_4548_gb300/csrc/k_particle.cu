@@ -562,7 +562,7 @@ __global__ void __launch_bounds__(TILE) k_step_sur(const StepArgs<float> a) {
         const Stage<float>& q = st[s];
         if (use_net && net_ok) {
             // inputs: the node features interpolated to the particle
-            float f[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+            float f[16] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
             if (i < a.n) {
                 const int e0 = q.elem[j];
                 float g[EGEO_W];
@@ -579,9 +579,7 @@ __global__ void __launch_bounds__(TILE) k_step_sur(const StepArgs<float> a) {
                     f[8] += lw[m] * f2.x; f[9] += lw[m] * f2.y;
                 }
             }
-            uint16_t* tileA = U.A + (j >> 7) * mlptc::TILE_ELEMS;
-#pragma unroll
-            for (int kk = 0; kk < 16; ++kk) mlptc::put_input(tileA, j & 127, kk, kk < 10 ? f[kk] : 0.f);
+            mlptc::put_inputs(U.A + (j >> 7) * mlptc::TILE_ELEMS, j & 127, f);
             float y[16];
             net_ok = mlptc::run(U.W, U.A, 2, tmem, &U.bar, phase, y);
 #pragma unroll

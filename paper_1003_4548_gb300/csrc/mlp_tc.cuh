@@ -31,7 +31,20 @@ struct Weights {
 };
 
 __device__ __forceinline__ uint16_t bf16_bits(float x) { return __bfloat16_as_ushort(__float2bfloat16_rn(x)); }
-__device__ __forceinline__ float silu(float z) { return z / (1.f + expf(-z)); }
+// SiLU with the hardware exponential and a fast divide: its error (a few
+// ulp of FP32) is far below the bf16 rounding of the activation
+__device__ __forceinline__ float silu(float z) { return __fdividef(z, 1.f + __expf(-z)); }
+
+// 8 consecutive activations of one row (k = 8 j .. 8 j + 7) as one 16-byte
+// store: they are contiguous in the canonical layout
+__device__ __forceinline__ void put8(uint16_t* tile, int r, int k0, int kc, const float* v) {
+    uint4 q;
+    q.x = (uint32_t)bf16_bits(v[0]) | ((uint32_t)bf16_bits(v[1]) << 16);
+    q.y = (uint32_t)bf16_bits(v[2]) | ((uint32_t)bf16_bits(v[3]) << 16);
+    q.z = (uint32_t)bf16_bits(v[4]) | ((uint32_t)bf16_bits(v[5]) << 16);
+    q.w = (uint32_t)bf16_bits(v[6]) | ((uint32_t)bf16_bits(v[7]) << 16);
+    *reinterpret_cast<uint4*>(tile + tc::core_offset(r, k0, kc)) = q;
+}
 
 // weights (already bf16-rounded floats, parameter layout of the C ABI, then
 // the standardisation) into the canonical layouts; threads t of nt
@@ -58,9 +71,10 @@ __device__ __forceinline__ void load(Weights& W, const float* __restrict__ wq, i
     for (int q = t; q < PDF_MLP_NNORM; q += nt) W.nm[q] = wq[PDF_MLP_NPARAM + q];
 }
 
-// standardised input k < 16 of row r of a tile (layer-1 layout)
-__device__ __forceinline__ void put_input(uint16_t* tile, int r, int k, float v) {
-    tile[tc::core_offset(r, k, 2)] = bf16_bits(v);
+// the 16 standardised inputs (10 used, 6 zero) of row r of a tile (layer-1 layout)
+__device__ __forceinline__ void put_inputs(uint16_t* tile, int r, const float (&f)[16]) {
+    put8(tile, r, 0, 2, f);
+    put8(tile, r, 8, 2, f + 8);
 }
 
 // The network on ntiles tiles of 128 rows: thread t is row t % 128 of tile
@@ -105,7 +119,9 @@ __device__ __forceinline__ bool run(const Weights& W, uint16_t* A, int ntiles, u
                 float v[16];
                 tc::ld16(tmem + lane_base + col0 + (uint32_t)c0, v);
 #pragma unroll
-                for (int k = 0; k < 16; ++k) At[tc::core_offset(row, c0 + k, 8)] = bf16_bits(silu(v[k] + bias[c0 + k]));
+                for (int k = 0; k < 16; ++k) v[k] = silu(v[k] + bias[c0 + k]);
+                put8(At, row, c0, 8, v);
+                put8(At, row, c0 + 8, 8, v + 8);
             }
             tc::fence_before_sync();
         } else {
