@@ -316,3 +316,65 @@ def test_crowded_elements_statistics(wf_mesh, precision):
     gb = by_id({"id": G["id"], "bin": G["bin"]})
     ob = by_id({"id": o.particles()["id"], "bin": o.particles()["bin"]})
     assert np.array_equal(gb["bin"], ob["bin"])
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "fp32_kahan"])
+def test_ragged_empty_and_tied_elements(wf_mesh, precision):
+    """Degenerate element populations against the oracle: empty elements,
+    elements with fewer particles than bins (the IEM fallback), exactly as
+    many as bins, and elements whose particles share one velocity (bins then
+    split by particle id); then one step from that state (FP64)."""
+    g, o = both(wf_mesh, precision=precision, seed=17)
+    o.seed(12)
+    P = o.particles()
+    keep = np.zeros(P["x"].size, bool)
+    nt = wf_mesh["tri"].shape[0]
+    for e in range(nt):
+        idx = np.flatnonzero(P["elem"] == e)
+        keep[idx[: e % 11]] = True  # 0 .. 10 particles: empty, < 8 bins, = 8, > 8
+    Q = {k: v[keep].copy() for k, v in P.items() if k != "bin"}
+    tied = np.isin(Q["elem"], np.arange(9, nt, 22))  # elements holding 9 particles
+    Q["u"][tied] = 0.75
+    Q["v"][tied] = -0.25
+    Q["w"][tied] = 0.125
+    g.set_particles(Q)
+    g.estimate_stats()
+    g.sync()
+    G = g.particles()
+    o.set_particles(G)
+    o.estimate_stats()
+    cnt = g.field("elem_n")
+    assert np.array_equal(cnt, np.arange(nt) % 11)
+    assert np.array_equal(cnt, o.field("elem_n").astype(np.int32))
+    rt = 2e-6 if precision == "fp32_kahan" else 1e-12
+    for name in ("elem_mean", "elem_R", "elem_psivar", "elem_cm", "node_mean", "node_R"):
+        a, b = g.field(name), o.field(name)
+        scale = np.sqrt(np.mean(b ** 2, axis=0)) + 1e-300
+        assert np.all(np.abs(a - b) <= rt * (np.abs(b) + scale)), name
+    assert np.all(g.field("elem_mean")[cnt == 0] == 0.0)
+    gb = by_id({"id": G["id"], "bin": G["bin"]})
+    ob = by_id({"id": o.particles()["id"], "bin": o.particles()["bin"]})
+    assert np.array_equal(gb["bin"], ob["bin"])
+    if precision == "fp64":
+        dt = cfl_dt(wf_mesh, cfl=0.5, k0=1e-3)
+        g.step(dt, 1)
+        g.sync()
+        o.advance(dt)
+        Gs, Os = by_id(g.particles()), by_id(o.particles())
+        near = np.abs(edge_distance(wf_mesh, Os)) < 1e-9
+        assert np.all((Gs["elem"] == Os["elem"]) | near)
+        assert_state_close(Gs, Os, 1e-12)
+
+
+def test_empty_ensemble(wf_mesh):
+    """No particles at all: statistics are zero, a step is a no-op."""
+    g, _ = both(wf_mesh, seed=19)
+    empty = {k: np.zeros(0) for k in ("x", "y", "u", "v", "w", "om", "psi")}
+    empty["id"] = np.zeros(0, np.uint32)
+    empty["elem"] = np.zeros(0, np.int32)
+    g.set_particles(empty)
+    g.estimate_stats()
+    g.step(1e-3, 2)
+    g.sync()
+    assert g.num_particles == 0
+    assert not g.field("elem_n").any() and not g.field("elem_mean").any()
