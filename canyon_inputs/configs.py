@@ -91,3 +91,28 @@ def reference_speed(mesh: dict, *, k0: float, ustar: float = USTAR, kappa: float
 
 def cfl_dt(mesh: dict, *, cfl: float, k0: float) -> float:
     return float(cfl * np.min(2.0 * inradius(mesh)) / reference_speed(mesh, k0=k0))
+
+
+# Sampling locations of Section 3's Table 1 (building walls and roofs) in the
+# paper's coordinates (building height 2, canyon between x = 2 and x = 4),
+# mapped to these canyons (H = 1, canyon between 1 and 2): x' = (x - 2)/2 + 1,
+# y' = y / 2. Entry 10 of the first row prints x = 2.5 in the middle of the
+# x = 2 wall sequence and is read as x = 2.
+_TABLE1 = ((0.5, 2.0), (1.0, 2.0), (1.5, 2.0), (2.0, 2.0), (2.0, 1.93), (2.0, 1.5), (2.0, 1.33), (2.0, 1.0),
+           (2.0, 0.67), (2.0, 0.5), (2.0, 0.33), (2.0, 0.17), (4.0, 0.17), (4.0, 0.33), (4.0, 0.5), (4.0, 0.67),
+           (4.0, 1.0), (4.0, 1.33), (4.0, 1.5), (4.0, 1.93), (4.0, 2.0), (4.5, 2.0), (5.0, 2.0), (5.5, 2.0))
+# Fig. 7's scalar CDF points (3, 0.2) and (3, 2), mapped the same way
+_CDF_POINTS = ((3.0, 0.2), (3.0, 2.0))
+
+
+def _map(pts, W: float = 1.0):
+    return np.array([((x - 2.0) / 2.0 * W + 1.0, y / 2.0) for x, y in pts])
+
+
+def table1_points(W: float = 1.0) -> np.ndarray:
+    """The 24 wall and roof sampling points, shape (24, 2)."""
+    return _map(_TABLE1, W)
+
+
+def cdf_points(W: float = 1.0) -> np.ndarray:
+    return _map(_CDF_POINTS, W)

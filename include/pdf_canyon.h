@@ -200,6 +200,47 @@ int pdf_reset_timing(pdf_ctx* c);
 int64_t pdf_launch_count(const pdf_ctx* c);
 
 /* ---------------------------------------------------------------------------
+ * Time averaging, probes and scalar CDFs (Section 3: after the flow has become
+ * statistically stationary, the statistics are averaged in time; scalar
+ * concentrations are sampled at wall points; Fig. 7 shows cumulative
+ * distributions of the scalar at points of the canyon).
+ * ------------------------------------------------------------------------- */
+
+/* on = 1: from now on every pdf_step adds the element means, second moments
+ * and scalar variance and the node means to running sums, and the scalar
+ * values of the particles in each CDF probe's element to its histogram (the
+ * step count is kept on the device, so batch graphs count too); on = 0 stops.
+ * reset = 1 clears the sums and histograms first. */
+int pdf_set_averaging(pdf_ctx* c, int32_t on, int32_t reset);
+
+/* Number of averaged steps (synchronises the context stream). */
+int64_t pdf_averaging_count(pdf_ctx* c);
+
+/* Time averages into host out: which = 0 element means [ntri][5] (U, V, W,
+ * psi, omega), 1 element second moments [ntri][6], 2 scalar variance [ntri],
+ * 3 node means [nnode][4] (U, V, psi, omega). PDF_ERR_STATE before any
+ * averaged step. */
+int pdf_get_averages(pdf_ctx* c, int32_t which, double* out);
+
+/* Values at n points (host x[n], y[n]; x taken modulo the period). The
+ * point's element is the one with the largest smallest barycentric
+ * coordinate: the containing element, or the nearest one for a point on a
+ * wall. which = 0 node means (linear in the element), 1 element means,
+ * 2 element second moments, 3 .. 5 the same time-averaged; comp selects the
+ * component. Host out[n]; the elements in elem_out[n] when not NULL. */
+int pdf_probe(pdf_ctx* c, int32_t which, int32_t comp, const double* x, const double* y, int32_t n, double* out,
+              int32_t* elem_out);
+
+/* Scalar CDF probes: n points (located as above), histograms of nbins
+ * (1 .. 4096) equal bins on [0, 1]; filled while averaging is on. n = 0
+ * removes them. */
+int pdf_set_cdf_probes(pdf_ctx* c, const double* x, const double* y, int32_t n, int32_t nbins);
+
+/* Cumulative distributions F(b) at the bin edges b = 1/nbins .. 1: host
+ * out[n][nbins]; the probe elements in elem_out[n] when not NULL. */
+int pdf_get_cdf(pdf_ctx* c, double* out, int32_t* elem_out);
+
+/* ---------------------------------------------------------------------------
  * Many independent cases (the paper runs one canyon at a time; this serves
  * batches of cases with their own meshes, particle counts, seeds and sources).
  * ------------------------------------------------------------------------- */

@@ -57,7 +57,8 @@ EXPORTS = ("pdf_default_params", "pdf_init_mesh", "pdf_seed_particles", "pdf_set
            "pdf_mlp_loss_grad", "pdf_mlp_adam", "pdf_mlp_column_stats", "pdf_mlp_gather_rows",
            "pdf_mlp_standardize", "pdf_surrogate_rows", "pdf_surrogate_harvest", "pdf_set_surrogate",
            "pdf_surrogate_stats", "pdf_batch_create", "pdf_batch_step", "pdf_batch_sync", "pdf_batch_destroy",
-           "pdf_autotune")
+           "pdf_autotune", "pdf_set_averaging", "pdf_averaging_count", "pdf_get_averages", "pdf_probe",
+           "pdf_set_cdf_probes", "pdf_get_cdf")
 
 MLP_IN, MLP_HIDDEN, MLP_OUT, MLP_NPARAM, MLP_NNORM = 10, 64, 5, 9349, 30
 
@@ -126,6 +127,13 @@ def lib(allow_build: bool = True):
         L.pdf_batch_destroy.argtypes = [vp]
         L.pdf_batch_destroy.restype = None
         L.pdf_autotune.argtypes = [vp, C.c_double, C.c_int32, P(pdf_tuning)]
+        L.pdf_set_averaging.argtypes = [vp, C.c_int32, C.c_int32]
+        L.pdf_averaging_count.argtypes = [vp]
+        L.pdf_averaging_count.restype = C.c_int64
+        L.pdf_get_averages.argtypes = [vp, C.c_int32, d]
+        L.pdf_probe.argtypes = [vp, C.c_int32, C.c_int32, d, d, C.c_int32, d, i32]
+        L.pdf_set_cdf_probes.argtypes = [vp, d, d, C.c_int32, C.c_int32]
+        L.pdf_get_cdf.argtypes = [vp, d, i32]
         _lib = L
         return L
 
@@ -334,6 +342,45 @@ class Canyon:
         t = pdf_tuning()
         self._check(lib().pdf_autotune(self._h, dt, steps_per_trial, C.byref(t)))
         return {n: getattr(t, n) for n, _ in pdf_tuning._fields_}
+
+    # -- time averaging, probes, scalar CDFs --------------------------------
+    def set_averaging(self, on: bool, reset: bool = False):
+        self._check(lib().pdf_set_averaging(self._h, 1 if on else 0, 1 if reset else 0))
+
+    @property
+    def averaging_count(self) -> int:
+        return int(lib().pdf_averaging_count(self._h))
+
+    def averages(self, which: str) -> np.ndarray:
+        k = {"elem_mean": 0, "elem_R": 1, "elem_psivar": 2, "node_mean": 3}[which]
+        rows = self.nn if k == 3 else self.nt
+        out = np.empty((rows, (5, 6, 1, 4)[k]), np.float64)
+        self._check(lib().pdf_get_averages(self._h, k, _ptr(out, C.c_double)))
+        return out[:, 0] if k == 2 else out
+
+    PROBE = {"node_mean": 0, "elem_mean": 1, "elem_R": 2, "avg_node_mean": 3, "avg_elem_mean": 4, "avg_elem_R": 5}
+
+    def probe(self, which: str, comp: int, x, y):
+        x = np.ascontiguousarray(x, np.float64)
+        y = np.ascontiguousarray(y, np.float64)
+        out = np.empty(x.size, np.float64)
+        el = np.empty(x.size, np.int32)
+        self._check(lib().pdf_probe(self._h, self.PROBE[which], comp, _ptr(x, C.c_double), _ptr(y, C.c_double),
+                                    x.size, _ptr(out, C.c_double), _ptr(el, C.c_int32)))
+        return out, el
+
+    def set_cdf_probes(self, x, y, nbins: int):
+        x = np.ascontiguousarray(x, np.float64)
+        y = np.ascontiguousarray(y, np.float64)
+        self._cdf = (x.size, nbins)
+        self._check(lib().pdf_set_cdf_probes(self._h, _ptr(x, C.c_double), _ptr(y, C.c_double), x.size, nbins))
+
+    def cdf(self):
+        n, nb = self._cdf
+        out = np.empty((n, nb), np.float64)
+        el = np.empty(n, np.int32)
+        self._check(lib().pdf_get_cdf(self._h, _ptr(out, C.c_double), _ptr(el, C.c_int32)))
+        return out, el
 
     def set_timing(self, on: bool):
         self._check(lib().pdf_set_timing(self._h, 1 if on else 0))

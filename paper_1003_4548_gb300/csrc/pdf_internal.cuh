@@ -127,6 +127,13 @@ struct pdf_ctx {
                                           // features, k, eps, uu, vv, ww, uv)
     float* pwp = nullptr;                 // per-particle form, mode 4: wp of every particle [n][5]
     int64_t pwp_n = 0;
+    // time averaging and probes
+    int avg_on = 0;
+    double* avg_sum = nullptr;                 // [nt][12] element sums, then [nn][4] node sums
+    unsigned long long* avg_count = nullptr;   // averaged steps (on the device)
+    int cdf_n = 0, cdf_bins = 0;
+    int* cdf_elem = nullptr;
+    unsigned long long* cdf_hist = nullptr;    // [cdf_n][cdf_bins]
     // status
     int* d_status = nullptr;
     int* h_status = nullptr;
@@ -147,6 +154,11 @@ struct pdf_ctx {
 // error helpers
 // ---------------------------------------------------------------------------
 int fail(pdf_ctx* c, int code, const std::string& msg);
+#define TRY_OK(x)                        \
+    do {                                 \
+        const int st_ = (x);             \
+        if (st_ != PDF_OK) return st_;   \
+    } while (0)
 #define PDF_CUDA(c, call)                                                              \
     do {                                                                               \
         cudaError_t e_ = (call);                                                       \
@@ -173,7 +185,8 @@ int prepare_particle(pdf_ctx* c, int per_sm);   // persistent grid (0: all resid
 int particle_occupancy(pdf_ctx* c);
 int prepare_elliptic(pdf_ctx* c, int bs);       // CG rows per block (0: largest co-resident)
 int prepare_moments(pdf_ctx* c);
-int launch_surrogate(pdf_ctx* c);   // network wp at the nodes + FE residual check (before the CG)
+int launch_surrogate(pdf_ctx* c);
+int launch_averaging(pdf_ctx* c);   // running sums of the statistics and the CDF probes (when on)   // network wp at the nodes + FE residual check (before the CG)
 int surrogate_rows(pdf_ctx* c);     // builds the free canonical row list once
 int launch_to_double(pdf_ctx* c, const void* src, double* dst, int64_t n);
 

@@ -1,0 +1,75 @@
+"""Time averaging, probes and scalar CDFs against their plain definitions
+(the per-step fields read back and averaged or histogrammed on the host)."""
+import numpy as np
+import pytest
+
+from canyon_inputs.configs import cdf_points, cfl_dt, table1_points, yplus30
+from canyon_inputs.mesh import canyon_mesh
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def case():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("needs a GPU")
+    from paper_1003_4548_gb300 import Canyon, canyon_params
+    mesh = canyon_mesh(offset=yplus30(), h=0.1, seed=8)
+    g = Canyon(canyon_params(mesh, wall_model="wf", precision="fp64", C0=2.1, seed=21, mix_exp=1), mesh)
+    g.seed_particles(24)
+    g.estimate_stats()
+    return mesh, g, cfl_dt(mesh, cfl=0.5, k0=1e-3)
+
+
+def test_time_averages_and_cdfs(case):
+    mesh, g, dt = case
+    g.step(dt, 2)
+    g.set_cdf_probes(cdf_points()[:, 0], cdf_points()[:, 1], 20)
+    g.set_averaging(True, reset=True)
+    sums = {k: 0.0 for k in ("elem_mean", "elem_R", "elem_psivar", "node_mean")}
+    hist = np.zeros((2, 20))
+    _, pel = g.cdf()
+    for _ in range(5):
+        g.step(dt, 1)
+        g.sync()
+        for k in sums:
+            sums[k] = sums[k] + g.field(k)
+        P = g.particles()
+        for j, e in enumerate(pel):
+            v = P["psi"][P["elem"] == e]
+            hist[j] += np.bincount(np.clip((v * 20).astype(int), 0, 19), minlength=20)
+    g.set_averaging(False)
+    g.step(dt, 1)  # not averaged
+    assert g.averaging_count == 5
+    for k, s in sums.items():
+        assert np.allclose(g.averages(k), s / 5, rtol=1e-13, atol=1e-300), k
+    F, el = g.cdf()
+    assert np.array_equal(el, pel)
+    tot = hist.sum(1, keepdims=True)
+    assert np.allclose(F, np.cumsum(hist, 1) / np.maximum(tot, 1), rtol=0, atol=1e-15)
+    assert np.all(F[:, -1] == (tot[:, 0] > 0))
+
+
+def test_probes(case):
+    mesh, g, dt = case
+    xy, tri = mesh["xy"], mesh["tri"]
+    cent = xy[tri].mean(1)
+    es = np.array([0, 17, 200, len(tri) - 1])
+    v, el = g.probe("elem_mean", 3, cent[es, 0], cent[es, 1])
+    assert np.array_equal(el, es)
+    assert np.array_equal(v, g.field("elem_mean")[es, 3])
+    # node field: linear in the element
+    lam = np.array([0.2, 0.3, 0.5])
+    p = np.einsum("m,kmd->kd", lam, xy[tri[es]])
+    v, el = g.probe("node_mean", 0, p[:, 0], p[:, 1])
+    nm = g.field("node_mean")[:, 0]
+    assert np.array_equal(el, es)
+    assert np.allclose(v, (nm[tri[es]] * lam).sum(1), rtol=1e-12)
+    # Table 1 points sit on walls and roofs (outside the offset fluid domain
+    # of the wall-function mesh): the nearest element is taken
+    pts = table1_points()
+    v, el = g.probe("node_mean", 2, pts[:, 0], pts[:, 1])
+    assert np.all((el >= 0) & (el < len(tri))) and np.all(np.isfinite(v))
+    d = np.hypot(*(cent[el] - pts).T)
+    assert np.all(d < 0.2)
