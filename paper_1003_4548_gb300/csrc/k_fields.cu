@@ -37,11 +37,12 @@ __global__ void k_node_stats(int nn, const int* __restrict__ n2e_off, const int*
     }
     nwt[i] = wt;
     if (wt <= 0.0) return;  // keeps the previous node values
+    const double iw = 1.0 / wt;  // one FP64 division (the FP64 pipe is narrow on GB300)
 #pragma unroll
-    for (int k = 0; k < 4; ++k) nmean[4 * i + k] = m[k] / wt;
+    for (int k = 0; k < 4; ++k) nmean[4 * i + k] = m[k] * iw;
 #pragma unroll
-    for (int k = 0; k < 6; ++k) nR[6 * i + k] = R[k] / wt;
-    npsivar[i] = pv / wt;
+    for (int k = 0; k < 6; ++k) nR[6 * i + k] = R[k] * iw;
+    npsivar[i] = pv * iw;
     double kk = 0.5 * (nR[6 * i] + nR[6 * i + 1] + nR[6 * i + 2]);
     double Om = nmean[4 * i + 3];
     Om = Om > p.floor_omega ? Om : p.floor_omega;
@@ -66,26 +67,32 @@ __global__ void k_elem_derived(int nt, const int* __restrict__ tri, const double
         const double gx = gradb[6 * e + 2 * k], gy = gradb[6 * e + 2 * k + 1];
         Ux += nmean[4 * a] * gx; Uy += nmean[4 * a] * gy;
         Vx += nmean[4 * a + 1] * gx; Vy += nmean[4 * a + 1] * gy;
-        kc += nke[2 * a] / 3.0; ec += nke[2 * a + 1] / 3.0;
-        Uc += nmean[4 * a] / 3.0; Vc += nmean[4 * a + 1] / 3.0;
+        kc += nke[2 * a]; ec += nke[2 * a + 1];
+        Uc += nmean[4 * a]; Vc += nmean[4 * a + 1];
 #pragma unroll
-        for (int q = 0; q < 6; ++q) Rc[q] += nR[6 * a + q] / 3.0;
+        for (int q = 0; q < 6; ++q) Rc[q] += nR[6 * a + q];
     }
+    // centroid values: one multiply by 1/3 instead of a division per term
+    const double third = 1.0 / 3.0;
+    kc *= third; ec *= third; Uc *= third; Vc *= third;
+#pragma unroll
+    for (int q = 0; q < 6; ++q) Rc[q] *= third;
     double* d = eder + 9 * (size_t)e;
     d[0] = Ux; d[1] = Uy; d[2] = Vx; d[3] = Vy;
     const double P = -(Rc[0] * Ux + Rc[3] * Uy + Rc[3] * Vx + Rc[1] * Vy);
-    d[6] = p.Comega2 - p.Comega1 * P / ec;
+    const double iec = 1.0 / ec;
+    d[6] = p.Comega2 - p.Comega1 * P * iec;
     const double Ucn = sqrt(Uc * Uc + Vc * Vc);
     double dx = cent[2 * e] - p.x0;
-    dx -= p.period * floor(dx / p.period + 0.5);
+    dx -= p.period * floor(dx * (1.0 / p.period) + 0.5);
     const double dist = hypot(dx, cent[2 * e + 1] - p.y0);
-    double t1 = p.Cs * cbrt(p.r0 * p.r0 / ec);
+    double t1 = p.Cs * cbrt(p.r0 * p.r0 * iec);
     t1 += (Ucn > 0.0) ? p.Ct * dist / Ucn : HUGE_VAL;
-    const double t2a = kc / ec, t2b = p.CT * sqrt(p.nu / ec);
+    const double t2a = kc * iec, t2b = p.CT * sqrt(p.nu * iec);
     const double t2 = t2a > t2b ? t2a : t2b;
     d[7] = t1 < t2 ? t1 : t2;
     const double Cxi = 1.0 + 1.3 * 1.0;  // C_xi = 1 + 1.3 n_i n_i with a unit normal
-    const double La = Cxi * kc * sqrt(kc) / ec, Lb = p.Ceta * sqrt(sqrt(p.nu * p.nu * p.nu / ec));
+    const double La = Cxi * kc * sqrt(kc) * iec, Lb = p.Ceta * sqrt(sqrt(p.nu * p.nu * p.nu * iec));
     d[8] = p.CL * (La > Lb ? La : Lb);
     T* ep = epack + (size_t)ELEM_PACK_W * e;
     ep[0] = (T)Ux; ep[1] = (T)Uy; ep[2] = (T)Vx; ep[3] = (T)Vy;
@@ -104,8 +111,9 @@ __global__ void k_node_grad(int nn, const int* __restrict__ n2e_off, const int* 
 #pragma unroll
         for (int k = 0; k < 4; ++k) g[k] += A * eder[9 * e + k];
     }
+    const double ia = 1.0 / a;
 #pragma unroll
-    for (int k = 0; k < 4; ++k) ngrad[4 * i + k] = g[k] / a;
+    for (int k = 0; k < 4; ++k) ngrad[4 * i + k] = g[k] * ia;
 }
 
 template <typename T>
@@ -145,13 +153,14 @@ __global__ void k_node_pack(int nn, const double* __restrict__ nmean, const doub
     } else {
         const double* w = nwp + 5 * (size_t)i;  // Eqs. Gij and C0
         const double* R = nR + 6 * (size_t)i;
-        q[4] = (2.0 * w[0] - eps) / (2.0 * kk);
-        q[5] = w[1] / kk;
-        q[6] = w[2] / kk;
-        q[7] = (2.0 * w[3] - eps) / (2.0 * kk);
-        q[8] = (2.0 * w[4] - eps) / (2.0 * kk);
+        const double ik = 1.0 / kk, h2k = 0.5 * ik;
+        q[4] = (2.0 * w[0] - eps) * h2k;
+        q[5] = w[1] * ik;
+        q[6] = w[2] * ik;
+        q[7] = (2.0 * w[3] - eps) * h2k;
+        q[8] = (2.0 * w[4] - eps) * h2k;
         const double s = w[0] * R[0] + w[1] * R[3] + w[2] * R[3] + w[3] * R[1] + w[4] * R[2];
-        const double c0eps = -2.0 * s / (3.0 * kk);
+        const double c0eps = -2.0 * s * ik * (1.0 / 3.0);
         q[3] = c0eps > 0.0 ? c0eps : 0.0;
     }
     q[9] = p.fx; q[10] = p.fy; q[11] = 0.0;

@@ -462,7 +462,54 @@ struct ResArgs {
     const double* __restrict__ f;
     const double* __restrict__ x;
     double* part;  // [gridDim][4 NC]: sum r^2, sum b0^2, sum r, sum b0 per component
+    unsigned* done;  // blocks finished (the last one decides, then resets it)
+    int mode;
+    double tol;
+    int* skip;
+    unsigned long long* cnt;
+    double* last;
 };
+
+// relative residuals (max over components): last[0] coarse (the check),
+// last[1] fine; the decision and the counters. One warp (the residual
+// kernel's last block): lane l sums the partials of blocks l, l + 32, ...,
+// then a shuffle tree in a fixed order.
+__device__ void sur_decide(const double* __restrict__ part, int nb, int mode, double tol, int* skip,
+                           unsigned long long* cnt, double* last) {
+    const int lane = threadIdx.x & 31;
+    double acc[4 * NC];
+#pragma unroll
+    for (int c = 0; c < 4 * NC; ++c) acc[c] = 0.0;
+    for (int b = lane; b < nb; b += 32) {
+        const double* q = part + (size_t)b * 4 * NC;
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            acc[c] += q[c];
+            acc[NC + c] += q[NC + c];
+            acc[2 * NC + c] += q[2 * NC + c] * q[2 * NC + c];
+            acc[3 * NC + c] += q[3 * NC + c] * q[3 * NC + c];
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < 4 * NC; ++c)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc[c] += __shfl_down_sync(0xffffffffu, acc[c], o);
+    if (lane != 0) return;
+    double fine = 0.0, coarse = 0.0;
+    for (int c = 0; c < NC; ++c) {
+        const double rr = acc[c], bb = acc[NC + c], cr = acc[2 * NC + c], cb = acc[3 * NC + c];
+        const double f = bb > 0.0 ? sqrt(rr / bb) : sqrt(rr);
+        const double g = cb > 0.0 ? sqrt(cr / cb) : sqrt(cr);
+        fine = f > fine ? f : fine;
+        coarse = g > coarse ? g : coarse;
+    }
+    const int ok = (mode == 2) || (coarse <= tol);
+    *skip = ok;
+    last[0] = coarse;
+    last[1] = fine;
+    cnt[0] += 1ull;
+    cnt[1] += ok ? 0ull : 1ull;
+}
 
 constexpr int RES_ROWS = 128;
 
@@ -510,46 +557,17 @@ __global__ void __launch_bounds__(RES_ROWS) k_sur_residual(ResArgs a) {
         __syncthreads();
     }
     if (t < 4 * NC) a.part[(size_t)blockIdx.x * 4 * NC + t] = red[t][0];
-}
-
-// relative residuals (max over components): last[0] coarse (the check),
-// last[1] fine; the decision and the counters. One warp: lane l sums the
-// partials of blocks l, l + 32, ..., then a shuffle tree in a fixed order.
-__global__ void __launch_bounds__(32) k_sur_decide(const double* __restrict__ part, int nb, int mode, double tol,
-                                                   int* skip, unsigned long long* cnt, double* last) {
-    const int lane = threadIdx.x;
-    double acc[4 * NC];
-#pragma unroll
-    for (int c = 0; c < 4 * NC; ++c) acc[c] = 0.0;
-    for (int b = lane; b < nb; b += 32) {
-        const double* q = part + (size_t)b * 4 * NC;
-#pragma unroll
-        for (int c = 0; c < NC; ++c) {
-            acc[c] += q[c];
-            acc[NC + c] += q[NC + c];
-            acc[2 * NC + c] += q[2 * NC + c] * q[2 * NC + c];
-            acc[3 * NC + c] += q[3 * NC + c] * q[3 * NC + c];
-        }
+    // the last block to finish reduces all partials and takes the decision
+    __shared__ bool last_block;
+    __threadfence();
+    __syncthreads();
+    if (t == 0) last_block = atomicAdd(a.done, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (last_block && t < 32) {
+        __threadfence();
+        sur_decide(a.part, gridDim.x, a.mode, a.tol, a.skip, a.cnt, a.last);
+        if (t == 0) *a.done = 0u;
     }
-#pragma unroll
-    for (int c = 0; c < 4 * NC; ++c)
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) acc[c] += __shfl_down_sync(0xffffffffu, acc[c], o);
-    if (lane != 0) return;
-    double fine = 0.0, coarse = 0.0;
-    for (int c = 0; c < NC; ++c) {
-        const double rr = acc[c], bb = acc[NC + c], cr = acc[2 * NC + c], cb = acc[3 * NC + c];
-        const double f = bb > 0.0 ? sqrt(rr / bb) : sqrt(rr);
-        const double g = cb > 0.0 ? sqrt(cr / cb) : sqrt(cr);
-        fine = f > fine ? f : fine;
-        coarse = g > coarse ? g : coarse;
-    }
-    const int ok = (mode == 2) || (coarse <= tol);
-    *skip = ok;
-    last[0] = coarse;
-    last[1] = fine;
-    cnt[0] += 1ull;
-    cnt[1] += ok ? 0ull : 1ull;
 }
 
 SurArgs sur_args(pdf_ctx* c) {
@@ -589,10 +607,14 @@ int launch_surrogate(pdf_ctx* c) {
     r.rep = c->m.rep; r.is_wall = c->m.is_wall;
     r.f = c->fe_f; r.x = c->fe_prop; r.part = c->sur_part;
     const int nb = sur_blocks(c);
+    r.done = reinterpret_cast<unsigned*>(c->sur_part + (size_t)nb * 4 * NC + 2);
+    r.mode = c->sur_mode;
+    r.tol = c->sur_tol;
+    r.skip = c->sur_skip;
+    r.cnt = c->sur_cnt;
+    r.last = c->sur_part + (size_t)nb * 4 * NC;
     k_sur_residual<<<nb, RES_ROWS, 0, c->s>>>(r);
-    k_sur_decide<<<1, 32, 0, c->s>>>(c->sur_part, nb, c->sur_mode, c->sur_tol, c->sur_skip, c->sur_cnt,
-                                     c->sur_part + (size_t)nb * 4 * NC);
-    c->launches += 3;
+    c->launches += 2;
     if (c->sur_mode >= 3) {
         k_sur_featpack<<<(nn + 127) / 128, 128, 0, c->s>>>(a, c->sur_w + PDF_MLP_NPARAM, c->nsurT);
         ++c->launches;
@@ -647,7 +669,7 @@ int pdf_set_surrogate(pdf_ctx* c, int32_t mode, const float* params, const float
         PDF_CUDA(c, cudaMalloc((void**)&c->sur_w, sizeof(float) * (PDF_MLP_NPARAM + PDF_MLP_NNORM)));
         PDF_CUDA(c, cudaMalloc((void**)&c->sur_skip, sizeof(int)));
         PDF_CUDA(c, cudaMalloc((void**)&c->sur_cnt, 2 * sizeof(unsigned long long)));
-        PDF_CUDA(c, cudaMalloc((void**)&c->sur_part, sizeof(double) * ((size_t)sur_blocks(c) * 4 * NC + 2)));
+        PDF_CUDA(c, cudaMalloc((void**)&c->sur_part, sizeof(double) * ((size_t)sur_blocks(c) * 4 * NC + 3)));
     }
     std::vector<float> h(PDF_MLP_NPARAM + PDF_MLP_NNORM);
     for (int q = 0; q < PDF_MLP_NPARAM; ++q) h[q] = __bfloat162float(__float2bfloat16_rn(params[q]));
@@ -656,7 +678,7 @@ int pdf_set_surrogate(pdf_ctx* c, int32_t mode, const float* params, const float
     PDF_CUDA(c, cudaMemcpy(c->sur_w, h.data(), sizeof(float) * h.size(), cudaMemcpyHostToDevice));
     PDF_CUDA(c, cudaMemset(c->sur_skip, 0, sizeof(int)));
     PDF_CUDA(c, cudaMemset(c->sur_cnt, 0, 2 * sizeof(unsigned long long)));
-    PDF_CUDA(c, cudaMemset(c->sur_part, 0, sizeof(double) * ((size_t)sur_blocks(c) * 4 * NC + 2)));
+    PDF_CUDA(c, cudaMemset(c->sur_part, 0, sizeof(double) * ((size_t)sur_blocks(c) * 4 * NC + 3)));
     c->sur_mode = mode;
     c->sur_tol = residual_tol;
     return PDF_OK;
