@@ -470,47 +470,6 @@ struct ResArgs {
     double* last;
 };
 
-// relative residuals (max over components): last[0] coarse (the check),
-// last[1] fine; the decision and the counters. One warp (the residual
-// kernel's last block): lane l sums the partials of blocks l, l + 32, ...,
-// then a shuffle tree in a fixed order.
-__device__ void sur_decide(const double* __restrict__ part, int nb, int mode, double tol, int* skip,
-                           unsigned long long* cnt, double* last) {
-    const int lane = threadIdx.x & 31;
-    double acc[4 * NC];
-#pragma unroll
-    for (int c = 0; c < 4 * NC; ++c) acc[c] = 0.0;
-    for (int b = lane; b < nb; b += 32) {
-        const double* q = part + (size_t)b * 4 * NC;
-#pragma unroll
-        for (int c = 0; c < NC; ++c) {
-            acc[c] += q[c];
-            acc[NC + c] += q[NC + c];
-            acc[2 * NC + c] += q[2 * NC + c] * q[2 * NC + c];
-            acc[3 * NC + c] += q[3 * NC + c] * q[3 * NC + c];
-        }
-    }
-#pragma unroll
-    for (int c = 0; c < 4 * NC; ++c)
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) acc[c] += __shfl_down_sync(0xffffffffu, acc[c], o);
-    if (lane != 0) return;
-    double fine = 0.0, coarse = 0.0;
-    for (int c = 0; c < NC; ++c) {
-        const double rr = acc[c], bb = acc[NC + c], cr = acc[2 * NC + c], cb = acc[3 * NC + c];
-        const double f = bb > 0.0 ? sqrt(rr / bb) : sqrt(rr);
-        const double g = cb > 0.0 ? sqrt(cr / cb) : sqrt(cr);
-        fine = f > fine ? f : fine;
-        coarse = g > coarse ? g : coarse;
-    }
-    const int ok = (mode == 2) || (coarse <= tol);
-    *skip = ok;
-    last[0] = coarse;
-    last[1] = fine;
-    cnt[0] += 1ull;
-    cnt[1] += ok ? 0ull : 1ull;
-}
-
 constexpr int RES_ROWS = 128;
 
 // r = M f - A x over the free rows (x holds the Dirichlet values at the walls),
@@ -563,10 +522,43 @@ __global__ void __launch_bounds__(RES_ROWS) k_sur_residual(ResArgs a) {
     __syncthreads();
     if (t == 0) last_block = atomicAdd(a.done, 1u) == gridDim.x - 1;
     __syncthreads();
-    if (last_block && t < 32) {
+    if (last_block) {
+        // 6 groups of 20 threads: thread (grp, v) sums value v over the blocks
+        // b = grp, grp + 6, ... (squared for the coarse sums), in a fixed order
         __threadfence();
-        sur_decide(a.part, gridDim.x, a.mode, a.tol, a.skip, a.cnt, a.last);
-        if (t == 0) *a.done = 0u;
+        __shared__ double acc6[6][4 * NC];
+        const int grp = t / (4 * NC), v = t % (4 * NC);
+        if (grp < 6) {
+            double sacc = 0.0;
+            for (int b = grp; b < (int)gridDim.x; b += 6) {
+                const double q = a.part[(size_t)b * 4 * NC + v];
+                sacc += v < 2 * NC ? q : q * q;
+            }
+            acc6[grp][v] = sacc;
+        }
+        __syncthreads();
+        if (t == 0) {
+            double tot[4 * NC];
+            for (int k = 0; k < 4 * NC; ++k) {
+                tot[k] = 0.0;
+                for (int g2 = 0; g2 < 6; ++g2) tot[k] += acc6[g2][k];
+            }
+            double fine = 0.0, coarse = 0.0;
+            for (int c = 0; c < NC; ++c) {
+                const double rr = tot[c], bb = tot[NC + c], cr = tot[2 * NC + c], cb = tot[3 * NC + c];
+                const double f = bb > 0.0 ? sqrt(rr / bb) : sqrt(rr);
+                const double g = cb > 0.0 ? sqrt(cr / cb) : sqrt(cr);
+                fine = f > fine ? f : fine;
+                coarse = g > coarse ? g : coarse;
+            }
+            const int ok = (a.mode == 2) || (coarse <= a.tol);
+            *a.skip = ok;
+            a.last[0] = coarse;
+            a.last[1] = fine;
+            a.cnt[0] += 1ull;
+            a.cnt[1] += ok ? 0ull : 1ull;
+            *a.done = 0u;
+        }
     }
 }
 

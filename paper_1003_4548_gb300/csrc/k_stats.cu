@@ -827,44 +827,66 @@ __device__ __noinline__ void kahan_moments(const MomArgs<float>& a, int e, int s
     if (T.wid == 0) {
         const int lane = T.lane;
         const float su = a.u[s0], sv = a.v[s0], sw = a.w[s0], sp = a.psi[s0];
-        AccK m[5], c2[7];
+        // 16 compensated sums (12 used): 0..4 the shifted u v w psi and omega,
+        // 5..10 the products uu vv ww uv uw vw, 11 psi psi
+        AccK acc[16];
         for (int q = lane; q < n; q += 32) {
             const float du = a.u[s0 + q] - su, dv = a.v[s0 + q] - sv, dw = a.w[s0 + q] - sw;
             const float dp = a.psi[s0 + q] - sp;
-            m[0].add(du); m[1].add(dv); m[2].add(dw); m[3].add(dp); m[4].add(a.om[s0 + q]);
-            c2[0].add(du * du); c2[1].add(dv * dv); c2[2].add(dw * dw);
-            c2[3].add(du * dv); c2[4].add(du * dw); c2[5].add(dv * dw); c2[6].add(dp * dp);
+            acc[0].add(du); acc[1].add(dv); acc[2].add(dw); acc[3].add(dp); acc[4].add(a.om[s0 + q]);
+            acc[5].add(du * du); acc[6].add(dv * dv); acc[7].add(dw * dw);
+            acc[8].add(du * dv); acc[9].add(du * dw); acc[10].add(dv * dw); acc[11].add(dp * dp);
         }
+        // butterfly reduce-scatter over the warp: after the xor-16, 8, 4, 2
+        // exchanges (each lane merging the half it keeps with the partner's)
+        // lane l holds sum (l >> 1) of its lane pair, the xor-1 merge completes it
 #pragma unroll
-        for (int q = 0; q < 5; ++q) warp_tree(m[q]);
+        for (int w = 8, o = 16; w >= 1; w >>= 1, o >>= 1) {
+            const bool upper = (lane & o) != 0;
 #pragma unroll
-        for (int q = 0; q < 7; ++q) warp_tree(c2[q]);
-        // lane q < 12 finishes moment q (FP64, all lanes at once): lanes 0..4
-        // the means, 5..10 the central second moments uu vv ww uv uw vw, 11 the
-        // psi variance; each takes the sums it needs from lane 0
-        int ia = 0, ib = 0, ic = 0;  // first-moment sums used by this lane; ic: second-moment sum
+            for (int k = 0; k < w; ++k) {
+                AccK send = upper ? acc[k] : acc[w + k];
+                AccK keep = upper ? acc[w + k] : acc[k];
+                AccK recv;
+                recv.s = __shfl_xor_sync(0xffffffffu, send.s, o);
+                recv.c = __shfl_xor_sync(0xffffffffu, send.c, o);
+                keep.merge(recv);
+                acc[k] = keep;
+            }
+        }
+        {
+            AccK recv;
+            recv.s = __shfl_xor_sync(0xffffffffu, acc[0].s, 1);
+            recv.c = __shfl_xor_sync(0xffffffffu, acc[0].c, 1);
+            if (lane & 1) {  // the same order of operands in both lanes of the pair
+                AccK mine = recv;
+                mine.merge(acc[0]);
+                acc[0] = mine;
+            } else {
+                acc[0].merge(recv);
+            }
+        }
+        // sum v sits in lanes 2v and 2v + 1: lane q < 12 finishes moment q (FP64,
+        // all lanes at once): lanes 0..4 the means, 5..10 the central second
+        // moments uu vv ww uv uw vw, 11 the psi variance
+        int ia = 0, ib = 0, ic = 0;  // first-moment sums used by this lane; ic: its second-moment sum
         if (lane < 5) ia = lane;
         else if (lane < 11) {
             const int k = lane - 5;  // uu vv ww uv uw vw
             ia = k < 3 ? k : (k == 5 ? 1 : 0);
             ib = k < 3 ? k : (k == 3 ? 1 : 2);
-            ic = k;
+            ic = 5 + k;
         } else {
             ia = ib = 3;
-            ic = 6;
+            ic = 11;
         }
         AccK A, Bq, Cq;
-#pragma unroll
-        for (int q = 0; q < 5; ++q) {
-            const float ss = __shfl_sync(0xffffffffu, m[q].s, 0), cc = __shfl_sync(0xffffffffu, m[q].c, 0);
-            if (ia == q) { A.s = ss; A.c = cc; }
-            if (ib == q) { Bq.s = ss; Bq.c = cc; }
-        }
-#pragma unroll
-        for (int q = 0; q < 7; ++q) {
-            const float ss = __shfl_sync(0xffffffffu, c2[q].s, 0), cc = __shfl_sync(0xffffffffu, c2[q].c, 0);
-            if (ic == q) { Cq.s = ss; Cq.c = cc; }
-        }
+        A.s = __shfl_sync(0xffffffffu, acc[0].s, 2 * ia);
+        A.c = __shfl_sync(0xffffffffu, acc[0].c, 2 * ia);
+        Bq.s = __shfl_sync(0xffffffffu, acc[0].s, 2 * ib);
+        Bq.c = __shfl_sync(0xffffffffu, acc[0].c, 2 * ib);
+        Cq.s = __shfl_sync(0xffffffffu, acc[0].s, 2 * ic);
+        Cq.c = __shfl_sync(0xffffffffu, acc[0].c, 2 * ic);
         if (lane < 12) {
             const double inv_n = recip_n(n);
             const double da = A.value() * inv_n;
