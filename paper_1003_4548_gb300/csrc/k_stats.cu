@@ -511,12 +511,20 @@ __global__ void __launch_bounds__(32 * WARPS_PER_BLOCK) k_moments_warp(const Mom
 //    that bucket is crowded;
 //  * <phi|V>: exact fixed-point psi sums per bin (shared-memory atomics).
 // ---------------------------------------------------------------------------
+// histogram buckets and boundary-bucket candidate cap of a size class (the
+// block class ranks up to 64 keys of a crowded bucket before bisecting)
+template <int NMAX>
+struct SelCfg {
+    static constexpr int NB = 256;
+    static constexpr int CMAX = NMAX <= 512 ? 32 : 64;
+};
+
 template <int NMAX>
 struct SelSmem {
     uint32_t kv[NMAX];  // order-preserving value bits of the current level
     unsigned char grp[NMAX];
-    unsigned hist[4][128];     // per-group 256-bucket histogram, two 16-bit counts per word
-    uint32_t cv[4][32], cid[4][32];  // candidates of each group's boundary bucket
+    unsigned hist[4][SelCfg<NMAX>::NB / 2];  // per-group histogram, two 16-bit counts per word
+    uint32_t cv[4][SelCfg<NMAX>::CMAX], cid[4][SelCfg<NMAX>::CMAX];  // keys of each group's boundary bucket
     int nc[4], bkt[4], brank[4];
     uint32_t bv[4], bid[4];    // boundary keys of the level's groups
     int ired[8];               // team reduction scratch
@@ -619,8 +627,9 @@ __device__ __noinline__ void sel_bisect(SelSmem<NMAX>& S, const uint32_t* __rest
 // distribution.
 struct Buckets {
     float lo, sc;
+    int top;  // number of buckets - 1
     __device__ int operator()(uint32_t k) const {
-        return max(0, min(255, (int)((ord32_inv(k) - lo) * sc)));
+        return max(0, min(top, (int)((ord32_inv(k) - lo) * sc)));
     }
 };
 
@@ -634,11 +643,12 @@ __device__ __forceinline__ double recip_n(int n) {
 
 // (in FP32: any monotone map is exact for the selection, and FP64 on every
 // lane of a warp would occupy GB300's narrow FP64 pipe)
-__device__ __forceinline__ Buckets make_buckets(double mean, double var) {
+__device__ __forceinline__ Buckets make_buckets(double mean, double var, int nb) {
     const float v = (float)var;
     const float sd = v > 0.f ? sqrtf(v) : 0.f;
-    const float sc = sd > 0.f ? 32.f / sd : 0.f;  // 256 buckets over 8 sd
+    const float sc = sd > 0.f ? (float)nb / (8.f * sd) : 0.f;  // nb buckets over 8 sd
     Buckets b;
+    b.top = nb - 1;
     b.lo = (float)mean - 4.f * sd;
     b.sc = (sc > 0.f && sc < 1e30f) ? sc : 0.f;
     return b;
@@ -652,14 +662,15 @@ template <int NT, int NMAX>
 __device__ __noinline__ void sel_boundaries(SelSmem<NMAX>& S, const uint32_t* __restrict__ ids, int n, int ng,
                                             const int (&gsize)[4], const Buckets bk) {
     const Team<NT> T;
-    if (T.wid == 0) {  // boundary bucket of every group (8 buckets per lane)
+    constexpr int NB = SelCfg<NMAX>::NB, PL = NB / 32, CMAX = SelCfg<NMAX>::CMAX;  // PL buckets per lane
+    if (T.wid == 0) {  // boundary bucket of every group
         const int lane = T.lane;
         for (int g = 0; g < ng; ++g) {
             const int Tk = (gsize[g] + 1) / 2;
-            int loc[8], tot = 0;
+            int loc[PL], tot = 0;
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const unsigned w2 = S.hist[g][4 * lane + k];
+            for (int k = 0; k < PL / 2; ++k) {
+                const unsigned w2 = S.hist[g][(PL / 2) * lane + k];
                 loc[2 * k] = (int)(w2 & 0xffffu);
                 loc[2 * k + 1] = (int)(w2 >> 16);
                 tot += loc[2 * k] + loc[2 * k + 1];
@@ -675,8 +686,8 @@ __device__ __noinline__ void sel_boundaries(SelSmem<NMAX>& S, const uint32_t* __
             if (excl < Tk && incl >= Tk) {
                 int run = excl;
 #pragma unroll
-                for (int k = 0; k < 8; ++k) {
-                    if (mybucket < 0 && run + loc[k] >= Tk) { mybucket = 8 * lane + k; mybelow = run; }
+                for (int k = 0; k < PL; ++k) {
+                    if (mybucket < 0 && run + loc[k] >= Tk) { mybucket = PL * lane + k; mybelow = run; }
                     run += loc[k];
                 }
             }
@@ -695,17 +706,17 @@ __device__ __noinline__ void sel_boundaries(SelSmem<NMAX>& S, const uint32_t* __
     for (int q = T.tid; q < n; q += NT) {  // candidates of all groups in one pass
         const int g = S.grp[q];
         const int b = S.bkt[g];
-        if (hcount(S, g, b) <= 32 && bk(S.kv[q]) == b) {
+        if (hcount(S, g, b) <= CMAX && bk(S.kv[q]) == b) {
             const int slot = atomicAdd(&S.nc[g], 1);
             S.cv[g][slot] = S.kv[q];
             S.cid[g][slot] = ids[q];
         }
     }
     T.sync();
-    for (int t = T.tid; t < 32 * ng; t += NT) {  // exact rank among the bucket's keys
-        const int g = t >> 5, j0 = t & 31;
+    for (int t = T.tid; t < CMAX * ng; t += NT) {  // exact rank among the bucket's keys
+        const int g = t / CMAX, j0 = t % CMAX;
         const int kc = hcount(S, g, S.bkt[g]);
-        if (kc <= 32 && j0 < kc) {
+        if (kc <= CMAX && j0 < kc) {
             const uint32_t v = S.cv[g][j0], id = S.cid[g][j0];
             int r = 0;
             for (int j = 0; j < kc; ++j) {
@@ -717,7 +728,7 @@ __device__ __noinline__ void sel_boundaries(SelSmem<NMAX>& S, const uint32_t* __
     }
     T.sync();
     for (int g = 0; g < ng; ++g) {  // crowded bucket (rare): bisection over the value bits
-        if (hcount(S, g, S.bkt[g]) > 32) {
+        if (hcount(S, g, S.bkt[g]) > CMAX) {
             unsigned vmin = 0xffffffffu, vmax = 0u;
             for (int q = T.tid; q < n; q += NT) {
                 vmin = min(vmin, S.kv[q]);
@@ -934,9 +945,9 @@ __device__ void sel_element(const MomArgs<float>& a, int e, int s0, int n, SelSm
     for (int d = 0; d < 3; ++d) {
         if (G[d] == 1) continue;
         const float* comp = d == 0 ? a.u : (d == 1 ? a.v : a.w);
-        const Buckets bk = make_buckets(S.mean[d], S.rd[d]);
+        const Buckets bk = make_buckets(S.mean[d], S.rd[d], SelCfg<NMAX>::NB);
         const int ngl = ng == 0 ? 1 : 2 * ng;  // groups of this level
-        for (int q = T.tid; q < ngl * 128; q += NT) (&S.hist[0][0])[q] = 0u;
+        for (int q = T.tid; q < ngl * (SelCfg<NMAX>::NB / 2); q += NT) (&S.hist[0][0])[q] = 0u;
         T.sync();
         for (int q = T.tid; q < n; q += NT) {
             int g = 0;
