@@ -28,6 +28,10 @@
  *  - wall conditions: Eqs. wall-normal-velocity..wall-omega with the wall
  *    statistics interpolated along the hit edge (wall functions); specular
  *    reflection with U_R = -U_I (elliptic relaxation); symmetry at the top;
+ *    with omega_wall = 1 the frequency follows the Section 4 alternative
+ *    omega_R = omega_I exp(-2 V_I <omega v>_p / <omega v^2>_p), the
+ *    frequency-weighted moments formed like the Reynolds stresses (element
+ *    fluctuations, count-weighted node means, linear along the edge);
  *    positions are mirrored about the crossed edge, at most reflect_max times;
  *  - host element: the lowest-id element whose barycentric coordinates are all
  *    >= 0 (brute force over a bucket grid of element bounding boxes).
@@ -81,7 +85,9 @@ struct orc_ctx {
     /* statistics */
     int stats_valid;
     double *en, *emean, *eR, *epsivar, *ecm;
+    double* eomw; /* ntri x 5: <omega u>, <omega v>, <omega uu>, <omega uv>, <omega vv> */
     double *nwt, *nmean, *nR, *nke, *npsivar;
+    double* nomw; /* nnode x 5, the same at the nodes */
     double *eder, *ngrad, *npack, *nwp;
     int cg_iters;
     /* FE matrix (CSR over canonical nodes) */
@@ -194,7 +200,7 @@ void orc_destroy(orc_ctx* c) {
     void* ptrs[] = {c->xy, c->tri, c->etag, c->pair, c->rep, c->area2, c->n2e_off, c->n2e, c->seg,
                     c->wnx, c->wny, c->wdist, c->is_wall, c->gb_off, c->gb, c->x, c->y, c->u, c->v,
                     c->w, c->om, c->psi, c->id, c->elem, c->bin, c->en, c->emean, c->eR, c->epsivar,
-                    c->ecm, c->nwt, c->nmean, c->nR, c->nke, c->npsivar, c->eder, c->ngrad, c->npack,
+                    c->ecm, c->eomw, c->nomw, c->nwt, c->nmean, c->nR, c->nke, c->npsivar, c->eder, c->ngrad, c->npack,
                     c->nwp, c->rowptr, c->colidx, c->aval};
     for (size_t i = 0; i < sizeof(ptrs) / sizeof(ptrs[0]); ++i) free(ptrs[i]);
     free(c);
@@ -362,6 +368,8 @@ orc_ctx* orc_create(const orc_params* p, int32_t nnode, const double* xy, int32_
     c->eR = (double*)xcalloc(6 * ntri, sizeof(double));
     c->epsivar = (double*)xcalloc(ntri, sizeof(double));
     c->ecm = (double*)xcalloc((size_t)c->nb * ntri, sizeof(double));
+    c->eomw = (double*)xcalloc(5 * ntri, sizeof(double));
+    c->nomw = (double*)xcalloc(5 * nnode, sizeof(double));
     c->nwt = (double*)xcalloc(nnode, sizeof(double));
     c->nmean = (double*)xcalloc(4 * nnode, sizeof(double));
     c->nR = (double*)xcalloc(6 * nnode, sizeof(double));
@@ -565,6 +573,7 @@ static void element_statistics(orc_ctx* c) {
         c->en[e] = n;
         for (int k = 0; k < 5; ++k) m[k] = 0.0;
         for (int k = 0; k < 6; ++k) R[k] = 0.0;
+        for (int k = 0; k < 5; ++k) c->eomw[5 * e + k] = 0.0;
         c->epsivar[e] = 0.0;
         for (int b = 0; b < B; ++b) c->ecm[(size_t)B * e + b] = 0.0;
         if (n == 0) continue;
@@ -583,6 +592,17 @@ static void element_statistics(orc_ctx* c) {
         }
         for (int k = 0; k < 6; ++k) R[k] /= n;
         c->epsivar[e] = pv / n;
+        /* frequency-weighted in-plane velocity moments of the Section 4
+         * frequency reflection: <omega u_i>, <omega u_i u_j>, fluctuations
+         * about the element mean velocity */
+        double* W = &c->eomw[5 * e];
+        for (int q = 0; q < n; ++q) {
+            int i = list[s0 + q];
+            double du = c->u[i] - m[0], dv = c->v[i] - m[1], o = c->om[i];
+            W[0] += o * du; W[1] += o * dv;
+            W[2] += o * du * du; W[3] += o * du * dv; W[4] += o * dv * dv;
+        }
+        for (int k = 0; k < 5; ++k) W[k] /= n;
         /* conditional means */
         for (int q = 0; q < n; ++q) {
             int i = list[s0 + q];
@@ -642,7 +662,7 @@ int orc_h_contract(const orc_params* p, const double R[6], const double g[4], do
 static void node_statistics(orc_ctx* c) {
     const orc_params* p = &c->p;
     for (int i = 0; i < c->nn; ++i) {
-        double wt = 0.0, m[4] = {0, 0, 0, 0}, R[6] = {0, 0, 0, 0, 0, 0}, pv = 0.0;
+        double wt = 0.0, m[4] = {0, 0, 0, 0}, R[6] = {0, 0, 0, 0, 0, 0}, pv = 0.0, W[5] = {0, 0, 0, 0, 0};
         for (int q = c->n2e_off[i]; q < c->n2e_off[i + 1]; ++q) {
             int e = c->n2e[q];
             double n = c->en[e];
@@ -652,12 +672,14 @@ static void node_statistics(orc_ctx* c) {
             m[2] += n * c->emean[5 * e + 3];
             m[3] += n * c->emean[5 * e + 4];
             for (int k = 0; k < 6; ++k) R[k] += n * c->eR[6 * e + k];
+            for (int k = 0; k < 5; ++k) W[k] += n * c->eomw[5 * e + k];
             pv += n * c->epsivar[e];
         }
         c->nwt[i] = wt;
         if (wt <= 0.0) continue; /* keeps the previous node values */
         for (int k = 0; k < 4; ++k) c->nmean[4 * i + k] = m[k] / wt;
         for (int k = 0; k < 6; ++k) c->nR[6 * i + k] = R[k] / wt;
+        for (int k = 0; k < 5; ++k) c->nomw[5 * i + k] = W[k] / wt;
         c->npsivar[i] = pv / wt;
         double kk = 0.5 * (c->nR[6 * i] + c->nR[6 * i + 1] + c->nR[6 * i + 2]);
         double Om = maxd(c->nmean[4 * i + 3], p->floor_omega);
@@ -946,9 +968,11 @@ void orc_sde(const orc_params* p, int32_t n, double dt, const double* fields, co
         sde_one(p, dt, fields + 22 * (size_t)i, z + 8 * (size_t)i, &u[i], &v[i], &w[i], &om[i], &psi[i]);
 }
 
-/* Velocity and frequency at a boundary hit. stat = <U>,<V>,R11,R22,R33,R12,Om
- * at the hit point; n = unit normal into the fluid. */
-int orc_reflect(const orc_ctx* c, int32_t tag, const double n[2], const double stat[7], double* u,
+/* Velocity and frequency at a boundary hit. stat = <U>,<V>,R11,R22,R33,R12,Om,
+ * then <omega u>,<omega v>,<omega uu>,<omega uv>,<omega vv> (read only by the
+ * Section 4 frequency reflection, omega_wall = 1), at the hit point, in the
+ * flow frame; n = unit normal into the fluid. */
+int orc_reflect(const orc_ctx* c, int32_t tag, const double n[2], const double stat[12], double* u,
                 double* v, double* w, double* om) {
     const orc_params* p = &c->p;
     double nx = n[0], ny = n[1], tx = ny, ty = -nx;
@@ -981,7 +1005,17 @@ int orc_reflect(const orc_ctx* c, int32_t tag, const double n[2], const double s
     double beta = -2.0 / (0.5 + 0.75 * p->C0 + p->C3 + p->Comega2 - p->Comega1);
     double VR = -Vn, UR = Ut + alpha * Vn;
     *u = UR * tx + VR * nx; *v = UR * ty + VR * ny;
-    *om = *om * exp(beta * Vn / (p->yp * Omp));
+    if (p->omega_wall) {
+        /* Section 4: omega_R = omega_I exp(-2 V_I <omega v>_p / <omega v^2>_p),
+         * v the wall-normal velocity fluctuation; the frequency-weighted
+         * second moment is floored at floor_k <omega>_p */
+        double wv = stat[7] * nx + stat[8] * ny;
+        double wv2 = stat[9] * nx * nx + 2.0 * stat[10] * nx * ny + stat[11] * ny * ny;
+        wv2 = maxd(wv2, p->floor_k * Omp);
+        *om = *om * exp(-2.0 * Vn * wv / wv2);
+    } else {
+        *om = *om * exp(beta * Vn / (p->yp * Omp));
+    }
     return ORC_OK;
 }
 
@@ -1034,7 +1068,7 @@ static int advance_one(orc_ctx* c, int i, double dt) {
         double cx = px + tbest * (qx - px), cy = py + tbest * (qy - py);
         double ex = g->bx - g->ax, ey = g->by - g->ay;
         double mu = ((cx - g->ax) * ex + (cy - g->ay) * ey) / (ex * ex + ey * ey);
-        double stat[7];
+        double stat[12];
         const double* Ma = &c->nmean[4 * g->na];
         const double* Mb = &c->nmean[4 * g->nb];
         const double* Ra = &c->nR[6 * g->na];
@@ -1046,6 +1080,8 @@ static int advance_one(orc_ctx* c, int i, double dt) {
         stat[4] = (1 - mu) * Ra[2] + mu * Rb[2];
         stat[5] = (1 - mu) * Ra[3] + mu * Rb[3];
         stat[6] = (1 - mu) * Ma[3] + mu * Mb[3];
+        for (int k = 0; k < 5; ++k)
+            stat[7 + k] = (1 - mu) * c->nomw[5 * g->na + k] + mu * c->nomw[5 * g->nb + k];
         double nrm[2] = {g->nx, g->ny};
         orc_reflect(c, g->tag, nrm, stat, &u, &v, &w, &om);
         double sq = g->nx * (qx - g->ax) + g->ny * (qy - g->ay);
@@ -1134,6 +1170,8 @@ int orc_get_field(const orc_ctx* c, int32_t f, double* out) {
     case ORC_F_NODE_WDIST: memcpy(out, c->wdist, 8 * (size_t)nn); break;
     case ORC_F_NODE_GRAD: memcpy(out, c->ngrad, 8 * (size_t)4 * nn); break;
     case ORC_F_NODE_PSIVAR: memcpy(out, c->npsivar, 8 * (size_t)nn); break;
+    case ORC_F_ELEM_OMW: memcpy(out, c->eomw, 8 * (size_t)5 * nt); break;
+    case ORC_F_NODE_OMW: memcpy(out, c->nomw, 8 * (size_t)5 * nn); break;
     default: return ORC_ERR_ARG;
     }
     return ORC_OK;

@@ -43,7 +43,7 @@ typedef struct orc_params {
     int32_t rotta;          /* 1: drop the H_ijkl term (Section 4 variant) */
     uint64_t seed;
     uint32_t case_id;
-    uint32_t pad_;
+    int32_t omega_wall;     /* 1: Section 4 frequency reflection with <omega v>/<omega v^2> */
 } orc_params;
 
 typedef struct orc_ctx orc_ctx;
@@ -68,7 +68,9 @@ enum {
     ORC_F_NODE_WP = 10,    /* nnode x 5       wp11,wp12,wp21,wp22,wp33 */
     ORC_F_NODE_WDIST = 11, /* nnode           wall distance */
     ORC_F_NODE_GRAD = 12,  /* nnode x 4       recovered grad <U> */
-    ORC_F_NODE_PSIVAR = 13 /* nnode */
+    ORC_F_NODE_PSIVAR = 13, /* nnode */
+    ORC_F_ELEM_OMW = 14,   /* ntri x 5        <omega u>,<omega v>,<omega uu>,<omega uv>,<omega vv> */
+    ORC_F_NODE_OMW = 15    /* nnode x 5 */
 };
 
 orc_ctx* orc_create(const orc_params* p, int32_t nnode, const double* xy, int32_t ntri,
@@ -94,7 +96,7 @@ int32_t orc_cg_iterations(const orc_ctx* c);
 void orc_philox4x32_10(const uint32_t key[2], const uint32_t ctr[4], uint32_t out[4]);
 void orc_gauss8(uint64_t seed, uint32_t case_id, uint32_t id, uint32_t step, double z[8]);
 int32_t orc_locate(const orc_ctx* c, double x, double y);
-int orc_reflect(const orc_ctx* c, int32_t tag, const double n[2], const double stat[7],
+int orc_reflect(const orc_ctx* c, int32_t tag, const double n[2], const double stat[12],
                 double* u, double* v, double* w, double* om);
 void orc_sde(const orc_params* p, int32_t n, double dt, const double* fields, const double* z,
              double* u, double* v, double* w, double* om, double* psi);
