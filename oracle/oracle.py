@@ -41,7 +41,8 @@ class orc_params(C.Structure):
         "cg_tol")] + [
         ("cg_maxit", C.c_int32), ("nb1", C.c_int32), ("nb2", C.c_int32), ("nb3", C.c_int32),
         ("wall_model", C.c_int32), ("mix_exp", C.c_int32), ("reflect_max", C.c_int32),
-        ("rotta", C.c_int32), ("seed", C.c_uint64), ("case_id", C.c_uint32), ("omega_wall", C.c_int32)]
+        ("rotta", C.c_int32), ("seed", C.c_uint64), ("case_id", C.c_uint32), ("omega_wall", C.c_int32),
+        ("pressure", C.c_int32), ("pad_", C.c_int32)]
 
 
 def build(force: bool = False) -> str:
@@ -74,6 +75,7 @@ def lib():
             L.orc_get_particles.argtypes = [C.c_void_p] + [d] * 7 + [u32, i32, u8]
             L.orc_estimate_stats.argtypes = [C.c_void_p]
             L.orc_advance.argtypes = [C.c_void_p, C.c_double]
+            L.orc_project.argtypes = [C.c_void_p, C.c_double]
             L.orc_step.argtypes = [C.c_void_p, C.c_double, C.c_int32]
             L.orc_advance_subset.argtypes = [C.c_void_p, C.c_double, i32, C.c_int32]
             L.orc_get_field.argtypes = [C.c_void_p, C.c_int32, d]
@@ -105,7 +107,7 @@ def default_params(**over) -> dict:
              x0=1.5, y0=0.0, r0=0.05, period=3.0, k0=1e-3, ustar=ustar, y_roof=1.0, er_wall=4.5,
              floor_k=1e-12, floor_eps=1e-12, floor_omega=1e-12, cg_tol=1e-12, cg_maxit=50000,
              nb1=2, nb2=2, nb3=2, wall_model=0, mix_exp=0, reflect_max=8, rotta=0, seed=0,
-             case_id=0, omega_wall=0)
+             case_id=0, omega_wall=0, pressure=0, pad_=0)
     p.update(over)
     return p
 
@@ -120,7 +122,7 @@ def make_params(d: dict) -> orc_params:
 FIELDS = dict(elem_n=(0, 1), elem_mean=(1, 5), elem_R=(2, 6), elem_psivar=(3, 1), elem_cm=(4, None),
               node_mean=(5, 4), node_R=(6, 6), node_ke=(7, 2), elem_der=(8, 9), node_pack=(9, 11),
               node_wp=(10, 5), node_wdist=(11, 1), node_grad=(12, 4), node_psivar=(13, 1),
-              elem_omw=(14, 5), node_omw=(15, 5))
+              elem_omw=(14, 5), node_omw=(15, 5), node_p=(16, 1))
 
 
 class Oracle:
@@ -190,6 +192,12 @@ class Oracle:
 
     def advance(self, dt: float, check: bool = True) -> int:
         st = lib().orc_advance(self._c, dt)
+        if check:
+            self._check(st)
+        return st
+
+    def project(self, dt: float, check: bool = True) -> int:
+        st = lib().orc_project(self._c, dt)
         if check:
             self._check(st)
         return st

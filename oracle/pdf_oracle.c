@@ -34,7 +34,10 @@
  *    fluctuations, count-weighted node means, linear along the edge);
  *    positions are mirrored about the crossed edge, at most reflect_max times;
  *  - host element: the lowest-id element whose barycentric coordinates are all
- *    >= 0 (brute force over a bucket grid of element bounding boxes).
+ *    >= 0 (brute force over a bucket grid of element bounding boxes);
+ *  - mean pressure: the imposed driving force, plus (pressure = 1) a P1
+ *    projection of the element mean velocities after every step
+ *    (orc_project).
  *
  * Parity pins live in the test-suite; the functions without an independent
  * pin are listed in the oracle's README header below.
@@ -88,6 +91,7 @@ struct orc_ctx {
     double* eomw; /* ntri x 5: <omega u>, <omega v>, <omega uu>, <omega uv>, <omega vv> */
     double *nwt, *nmean, *nR, *nke, *npsivar;
     double* nomw; /* nnode x 5, the same at the nodes */
+    double* npres; /* nnode: projection pressure (canonical value on every class member) */
     double *eder, *ngrad, *npack, *nwp;
     int cg_iters;
     /* FE matrix (CSR over canonical nodes) */
@@ -200,7 +204,7 @@ void orc_destroy(orc_ctx* c) {
     void* ptrs[] = {c->xy, c->tri, c->etag, c->pair, c->rep, c->area2, c->n2e_off, c->n2e, c->seg,
                     c->wnx, c->wny, c->wdist, c->is_wall, c->gb_off, c->gb, c->x, c->y, c->u, c->v,
                     c->w, c->om, c->psi, c->id, c->elem, c->bin, c->en, c->emean, c->eR, c->epsivar,
-                    c->ecm, c->eomw, c->nomw, c->nwt, c->nmean, c->nR, c->nke, c->npsivar, c->eder, c->ngrad, c->npack,
+                    c->ecm, c->eomw, c->nomw, c->npres, c->nwt, c->nmean, c->nR, c->nke, c->npsivar, c->eder, c->ngrad, c->npack,
                     c->nwp, c->rowptr, c->colidx, c->aval};
     for (size_t i = 0; i < sizeof(ptrs) / sizeof(ptrs[0]); ++i) free(ptrs[i]);
     free(c);
@@ -370,6 +374,7 @@ orc_ctx* orc_create(const orc_params* p, int32_t nnode, const double* xy, int32_
     c->ecm = (double*)xcalloc((size_t)c->nb * ntri, sizeof(double));
     c->eomw = (double*)xcalloc(5 * ntri, sizeof(double));
     c->nomw = (double*)xcalloc(5 * nnode, sizeof(double));
+    c->npres = (double*)xcalloc(nnode, sizeof(double));
     c->nwt = (double*)xcalloc(nnode, sizeof(double));
     c->nmean = (double*)xcalloc(4 * nnode, sizeof(double));
     c->nR = (double*)xcalloc(6 * nnode, sizeof(double));
@@ -1131,12 +1136,114 @@ int orc_advance_subset(orc_ctx* c, double dt, const int32_t* idx, int32_t n) {
     return st;
 }
 
+/* ------------------------------------------------------------------------- */
+/* mean-pressure projection (the scheme the paper cites is not given; this is  */
+/* a first-principles fractional step)                                         */
+/* ------------------------------------------------------------------------- */
+/* After a step, the element mean velocity <U>_e* (element constant, in-plane)
+ * is split into a weakly divergence-free part and a P1 gradient:
+ *   sum_e A_e grad N_i . grad N_j p_j = (1/dt) sum_e A_e grad N_i . <U>_e*
+ * for every node class i (periodic partners merged), natural conditions on
+ * the walls and the top (no mean flux through them, imposed weakly); the
+ * constant is fixed by p = 0 at the lowest-id canonical node. Each particle's
+ * in-plane velocity then loses dt grad p of its element, a uniform shift per
+ * element, so the element means satisfy sum_e A_e grad N_i . <U>_e = 0 for
+ * every node i while the Reynolds stresses and the velocity bins are
+ * unchanged. The imposed mean driving force stays in the velocity equation. */
+int orc_project(orc_ctx* c, double dt) {
+    if (!c->stats_valid) return ORC_ERR_STATE;
+    if (!(dt > 0.0)) return ORC_ERR_ARG;
+    const int nn = c->nn, nz = c->rowptr[nn];
+    int pin = -1;
+    for (int i = 0; i < nn && pin < 0; ++i)
+        if (c->rep[i] == i) pin = i;
+    double* K = (double*)xcalloc(nz, 8);
+    double* b = (double*)xcalloc(nn, 8);
+    for (int e = 0; e < c->nt; ++e) {
+        double A = 0.5 * c->area2[e], gx[3], gy[3];
+        double Ue = c->emean[5 * e + 0], Ve = c->emean[5 * e + 1];
+        for (int k = 0; k < 3; ++k) grad_bary(c, e, k, &gx[k], &gy[k]);
+        for (int k = 0; k < 3; ++k) {
+            int r = c->rep[c->tri[3 * e + k]];
+            b[r] += A * (gx[k] * Ue + gy[k] * Ve) / dt;
+            for (int l = 0; l < 3; ++l)
+                K[csr_find(c, r, c->rep[c->tri[3 * e + l]])] += A * (gx[k] * gx[l] + gy[k] * gy[l]);
+        }
+    }
+    /* Jacobi-preconditioned CG over the free canonical nodes, started from the
+     * previous pressure */
+    double *x = (double*)xcalloc(nn, 8), *r = (double*)xcalloc(nn, 8), *z = (double*)xcalloc(nn, 8);
+    double *pp = (double*)xcalloc(nn, 8), *Ap = (double*)xcalloc(nn, 8), *dg = (double*)xcalloc(nn, 8);
+    unsigned char* fr = (unsigned char*)xcalloc(nn, 1);
+    for (int i = 0; i < nn; ++i) {
+        fr[i] = c->rep[i] == i && i != pin;
+        x[i] = fr[i] ? c->npres[i] : 0.0;
+        dg[i] = fr[i] ? K[csr_find(c, i, i)] : 1.0;
+    }
+    double bn = 0.0, rr = 0.0, rz = 0.0;
+    for (int i = 0; i < nn; ++i) {
+        if (!fr[i]) continue;
+        double s = b[i];
+        for (int q = c->rowptr[i]; q < c->rowptr[i + 1]; ++q) s -= K[q] * x[c->colidx[q]];
+        r[i] = s;
+        bn += b[i] * b[i];
+    }
+    bn = sqrt(bn);
+    for (int i = 0; i < nn; ++i) { z[i] = r[i] / dg[i]; pp[i] = z[i]; rz += r[i] * z[i]; rr += r[i] * r[i]; }
+    int it = 0, status = ORC_OK;
+    while (bn > 0.0 && sqrt(rr) > c->p.cg_tol * bn) {
+        if (it >= c->p.cg_maxit) { status = ORC_ERR_CG; break; }
+        double pAp = 0.0;
+        for (int i = 0; i < nn; ++i) {
+            Ap[i] = 0.0;
+            if (!fr[i]) continue;
+            for (int q = c->rowptr[i]; q < c->rowptr[i + 1]; ++q) Ap[i] += K[q] * pp[c->colidx[q]];
+            pAp += pp[i] * Ap[i];
+        }
+        double alpha = rz / pAp, rz1 = 0.0;
+        rr = 0.0;
+        for (int i = 0; i < nn; ++i) {
+            x[i] += alpha * pp[i];
+            r[i] -= alpha * Ap[i];
+            z[i] = r[i] / dg[i];
+            rz1 += r[i] * z[i];
+            rr += r[i] * r[i];
+        }
+        double beta = rz1 / rz;
+        rz = rz1;
+        for (int i = 0; i < nn; ++i) pp[i] = z[i] + beta * pp[i];
+        it++;
+    }
+    for (int i = 0; i < nn; ++i) c->npres[i] = x[c->rep[i]];
+    c->cg_iters = it;
+    /* U_p -= dt grad p of the host element */
+    for (int i = 0; i < c->np; ++i) {
+        int e = c->elem[i];
+        double gpx = 0.0, gpy = 0.0;
+        for (int k = 0; k < 3; ++k) {
+            double gx, gy;
+            grad_bary(c, e, k, &gx, &gy);
+            gpx += c->npres[c->tri[3 * e + k]] * gx;
+            gpy += c->npres[c->tri[3 * e + k]] * gy;
+        }
+        c->u[i] -= dt * gpx;
+        c->v[i] -= dt * gpy;
+    }
+    free(K); free(b); free(x); free(r); free(z); free(pp); free(Ap); free(dg); free(fr);
+    if (status != ORC_OK) return status;
+    return orc_estimate_stats(c);
+}
+
 int orc_step(orc_ctx* c, double dt, int32_t nsteps) {
     for (int s = 0; s < nsteps; ++s) {
         int st = orc_advance(c, dt);
         if (st != ORC_OK) return st;
         st = orc_estimate_stats(c);
         if (st != ORC_OK) return st;
+        if (c->p.pressure) {
+            st = orc_project(c, dt);
+            if (st != ORC_OK) return st;
+        }
     }
     return ORC_OK;
 }
@@ -1172,6 +1279,7 @@ int orc_get_field(const orc_ctx* c, int32_t f, double* out) {
     case ORC_F_NODE_PSIVAR: memcpy(out, c->npsivar, 8 * (size_t)nn); break;
     case ORC_F_ELEM_OMW: memcpy(out, c->eomw, 8 * (size_t)5 * nt); break;
     case ORC_F_NODE_OMW: memcpy(out, c->nomw, 8 * (size_t)5 * nn); break;
+    case ORC_F_NODE_P: memcpy(out, c->npres, 8 * (size_t)nn); break;
     default: return ORC_ERR_ARG;
     }
     return ORC_OK;

@@ -44,6 +44,8 @@ typedef struct orc_params {
     uint64_t seed;
     uint32_t case_id;
     int32_t omega_wall;     /* 1: Section 4 frequency reflection with <omega v>/<omega v^2> */
+    int32_t pressure;       /* 1: mean-pressure projection after each step (see orc_project) */
+    int32_t pad_;
 } orc_params;
 
 typedef struct orc_ctx orc_ctx;
@@ -70,7 +72,8 @@ enum {
     ORC_F_NODE_GRAD = 12,  /* nnode x 4       recovered grad <U> */
     ORC_F_NODE_PSIVAR = 13, /* nnode */
     ORC_F_ELEM_OMW = 14,   /* ntri x 5        <omega u>,<omega v>,<omega uu>,<omega uv>,<omega vv> */
-    ORC_F_NODE_OMW = 15    /* nnode x 5 */
+    ORC_F_NODE_OMW = 15,   /* nnode x 5 */
+    ORC_F_NODE_P = 16      /* nnode           projection pressure p (pressure = 1) */
 };
 
 orc_ctx* orc_create(const orc_params* p, int32_t nnode, const double* xy, int32_t ntri,
@@ -98,6 +101,11 @@ void orc_gauss8(uint64_t seed, uint32_t case_id, uint32_t id, uint32_t step, dou
 int32_t orc_locate(const orc_ctx* c, double x, double y);
 int orc_reflect(const orc_ctx* c, int32_t tag, const double n[2], const double stat[12],
                 double* u, double* v, double* w, double* om);
+/* Mean-pressure projection of the particle velocities over a step dt (the
+ * element statistics must be current): solves the P1 Galerkin pressure
+ * problem K p = (1/dt) D <U>, corrects U_p -= dt grad p, and re-estimates
+ * the statistics. */
+int orc_project(orc_ctx* c, double dt);
 void orc_sde(const orc_params* p, int32_t n, double dt, const double* fields, const double* z,
              double* u, double* v, double* w, double* om, double* psi);
 int orc_fe_solve(orc_ctx* c, const double* L_elem, const double* f_node, const double* g_node,
