@@ -85,6 +85,19 @@ typedef struct pdf_params {
     int32_t precision;     /* enum pdf_precision; fixed for the life of a context */
     int32_t cg_precision;  /* elliptic CG arithmetic: 0 FP64; 1 compensated FP32 (float-float,
                               ~48-bit significand) with FP64 solution and coefficients */
+    int32_t omega_wall;    /* wall-function frequency reflection: 0 Eq. wall-omega (constant beta
+                              of the SLM); 1 the Section 4 form for general GLM closures,
+                              omega_R = omega_I exp(-2 V_I <omega v>_p / <omega v^2>_p), with the
+                              frequency-weighted moments estimated next to the walls each step
+                              (<omega v^2> floored at floor_k <omega>_p) */
+    int32_t pressure;      /* 0: the mean pressure gradient is the imposed driving force (fx, fy);
+                              1: in addition, a mean-pressure projection after every step: the P1
+                              Galerkin problem sum_e A_e grad N_i . grad N_j p_j =
+                              (1/dt) sum_e A_e grad N_i . <U>_e over the node classes (no mean
+                              flux through walls and top, imposed weakly; p = 0 at the lowest-id
+                              canonical node), then U_p -= dt grad p of the host element, so the
+                              element mean velocities become weakly divergence-free (the scheme the
+                              paper cites for its mean pressure is not given in it) */
     int32_t reserved_;
 } pdf_params;
 
@@ -110,9 +123,15 @@ enum pdf_field {
     PDF_FIELD_NODE_WDIST = 21, /* double[nnode] wall distance */
     PDF_FIELD_NODE_GRAD = 22,  /* double[nnode][4] recovered grad <U> */
     PDF_FIELD_NODE_PSIVAR = 23, /* double[nnode] */
-    PDF_FIELD_PARTICLE_WP = 24  /* float[n][5] wp at every particle, as used by the last step
+    PDF_FIELD_PARTICLE_WP = 24, /* float[n][5] wp at every particle, as used by the last step
                                    (surrogate mode 4; rows in the order of the particles at the
                                    start of that step) */
+    PDF_FIELD_ELEM_OMW = 25,  /* double[ntri][5] <omega u>,<omega v>,<omega uu>,<omega uv>,<omega vv>
+                                 (fluctuations about the element mean; omega_wall = 1 only, rows of
+                                 elements without a wall node are zero) */
+    PDF_FIELD_NODE_OMW = 26,  /* double[nnode][5] the same at the nodes (count-weighted; wall nodes
+                                 only, other rows zero) */
+    PDF_FIELD_NODE_P = 27     /* double[nnode] projection pressure p of the last step (pressure = 1) */
 };
 
 /* Kernel classes timed by pdf_kernel_time (CUDA events on the context stream). */
@@ -122,7 +141,8 @@ enum pdf_kernel {
     PDF_K_MOMENTS = 2,   /* element moments and <phi|V> bins */
     PDF_K_FIELDS = 3,    /* node averages, gradients, t_m, S_omega, G_ij packs */
     PDF_K_ELLIPTIC = 4,  /* FE assembly + Jacobi-PCG of Eq. elliptic-relaxation */
-    PDF_K_COUNT = 5
+    PDF_K_PRESSURE = 5,  /* mean-pressure projection: right-hand side, PCG, velocity correction */
+    PDF_K_COUNT = 6
 };
 
 /* Defaults: Table 2, C0 = 3.5 and C_mu, kappa, E of Section 2.2, nu = 1/12000,
@@ -179,13 +199,16 @@ int pdf_sync(pdf_ctx* c);
 int pdf_get_fields(pdf_ctx* c, int32_t field, void* dst, size_t bytes, int32_t dst_is_device);
 
 /* Sizes: particle count, elements, nodes, bins per element, step counter,
- * CG iterations of the last elliptic solve. */
+ * CG iterations of the last elliptic solve and of the last pressure
+ * projection (0 when pressure = 0); the iteration counts synchronise with
+ * the context stream. */
 int64_t pdf_num_particles(const pdf_ctx* c);
 int32_t pdf_num_elements(const pdf_ctx* c);
 int32_t pdf_num_nodes(const pdf_ctx* c);
 int32_t pdf_num_bins(const pdf_ctx* c);
 int32_t pdf_step_index(const pdf_ctx* c);
 int32_t pdf_cg_iterations(pdf_ctx* c);
+int32_t pdf_pressure_iterations(pdf_ctx* c);
 
 /* Per-kernel timing with CUDA events on the context stream: enable (1) or
  * disable (0) recording; pdf_kernel_time returns the summed milliseconds and

@@ -33,8 +33,9 @@ PRECISION = {"fp64": PDF_FP64, "fp32": PDF_FP32, "fp32_kahan": PDF_FP32_KAHAN}
 
 FIELD = dict(x=0, y=1, u=2, v=3, w=4, om=5, psi=6, id=7, elem=8, bin=9, elem_n=10, elem_mean=11, elem_R=12,
              elem_psivar=13, elem_cm=14, node_mean=15, node_R=16, node_ke=17, elem_der=18, node_pack=19,
-             node_wp=20, node_wdist=21, node_grad=22, node_psivar=23, particle_wp=24)
-KERNEL = dict(particle=0, sort=1, moments=2, fields=3, elliptic=4)
+             node_wp=20, node_wdist=21, node_grad=22, node_psivar=23, particle_wp=24,
+             elem_omw=25, node_omw=26, node_p=27)
+KERNEL = dict(particle=0, sort=1, moments=2, fields=3, elliptic=4, pressure=5)
 
 _DOUBLES = ("C1", "C2", "C3", "C4", "CT", "CL", "Ceta", "Cv", "gamma5", "Comega1", "Comega2", "Cs", "Ct",
             "C0", "Cmu", "kappa", "E", "nu", "fx", "fy", "yp", "wall_offset", "x0", "y0", "r0", "period",
@@ -46,12 +47,13 @@ class pdf_params(C.Structure):
         ("cg_maxit", C.c_int32), ("nb1", C.c_int32), ("nb2", C.c_int32), ("nb3", C.c_int32),
         ("wall_model", C.c_int32), ("mix_exp", C.c_int32), ("reflect_max", C.c_int32), ("rotta", C.c_int32),
         ("seed", C.c_uint64), ("case_id", C.c_uint32), ("precision", C.c_int32), ("cg_precision", C.c_int32),
-        ("reserved_", C.c_int32)]
+        ("omega_wall", C.c_int32), ("pressure", C.c_int32), ("reserved_", C.c_int32)]
 
 
 EXPORTS = ("pdf_default_params", "pdf_init_mesh", "pdf_seed_particles", "pdf_set_particles",
            "pdf_estimate_stats", "pdf_step", "pdf_sync", "pdf_get_fields", "pdf_num_particles",
            "pdf_num_elements", "pdf_num_nodes", "pdf_num_bins", "pdf_step_index", "pdf_cg_iterations",
+           "pdf_pressure_iterations",
            "pdf_set_timing", "pdf_kernel_time", "pdf_reset_timing", "pdf_launch_count", "pdf_last_error",
            "pdf_destroy", "pdf_sort_by_element_static", "pdf_mlp_work_floats", "pdf_mlp_forward",
            "pdf_mlp_loss_grad", "pdf_mlp_adam", "pdf_mlp_column_stats", "pdf_mlp_gather_rows",
@@ -97,7 +99,8 @@ def lib(allow_build: bool = True):
         for n in ("pdf_num_particles", "pdf_launch_count"):
             getattr(L, n).argtypes = [vp]
             getattr(L, n).restype = C.c_int64
-        for n in ("pdf_num_elements", "pdf_num_nodes", "pdf_num_bins", "pdf_step_index", "pdf_cg_iterations"):
+        for n in ("pdf_num_elements", "pdf_num_nodes", "pdf_num_bins", "pdf_step_index", "pdf_cg_iterations",
+                  "pdf_pressure_iterations"):
             getattr(L, n).argtypes = [vp]
             getattr(L, n).restype = C.c_int32
         L.pdf_set_timing.argtypes = [vp, C.c_int32]
@@ -291,10 +294,15 @@ class Canyon:
     def cg_iterations(self) -> int:
         return lib().pdf_cg_iterations(self._h)
 
+    @property
+    def pressure_iterations(self) -> int:
+        return lib().pdf_pressure_iterations(self._h)
+
     def field_shape(self, name: str):
         n = self.num_particles
         w = dict(elem_mean=5, elem_R=6, elem_cm=self.nbins, node_mean=4, node_R=6, node_ke=2, elem_der=9,
-                 node_pack=11, node_wp=5, node_grad=4, particle_wp=5).get(name, 1)
+                 node_pack=11, node_wp=5, node_grad=4, particle_wp=5, elem_omw=5,
+                 node_omw=5).get(name, 1)
         rows = n if (FIELD[name] <= 9 or name == "particle_wp") else (self.nt if name.startswith("elem") else self.nn)
         dt = {"id": np.uint32, "elem": np.int32, "bin": np.uint8, "elem_n": np.int32,
               "particle_wp": np.float32}.get(name, np.float64)

@@ -99,6 +99,8 @@ int check_params(const pdf_params* p) {
     if (p->precision < 0 || p->precision > 2) return PDF_ERR_ARG;
     if (p->wall_model < 0 || p->wall_model > 1) return PDF_ERR_ARG;
     if (p->cg_precision < 0 || p->cg_precision > 1) return PDF_ERR_ARG;
+    if (p->omega_wall < 0 || p->omega_wall > 1) return PDF_ERR_ARG;
+    if (p->pressure < 0 || p->pressure > 1) return PDF_ERR_ARG;
     if (!(p->period > 0) || !(p->nu > 0) || p->reflect_max < 0 || p->cg_maxit < 0) return PDF_ERR_ARG;
     return PDF_OK;
 }
@@ -264,8 +266,25 @@ int build_mesh(pdf_ctx* c, const double* xy, int nn, const int* tri, int nt, con
     TRY(upload(c, &m.wn, wn));
     TRY(upload(c, &m.is_wall, is_wall));
     TRY(upload(c, &m.rep, rep));
-    // finite-element pattern over canonical nodes (elliptic relaxation only)
-    if (c->p.wall_model == PDF_ELLIPTIC_RELAXATION) {
+    // Section 4 frequency reflection: wall nodes and the elements around them
+    if (c->p.wall_model == PDF_WALL_FUNCTIONS && c->p.omega_wall) {
+        std::vector<int> wnodes, welems;
+        std::vector<unsigned char> mark(nt, 0);
+        for (int i = 0; i < nn; ++i) {
+            if (!is_wall[i]) continue;
+            wnodes.push_back(i);
+            for (int q = n2e_off[i]; q < n2e_off[i + 1]; ++q) mark[n2e[q]] = 1;
+        }
+        for (int e = 0; e < nt; ++e)
+            if (mark[e]) welems.push_back(e);
+        m.n_owall_node = (int)wnodes.size();
+        m.n_owall_elem = (int)welems.size();
+        TRY(upload(c, &m.owall_node, wnodes));
+        TRY(upload(c, &m.owall_elem, welems));
+    }
+    // finite-element pattern over canonical nodes (elliptic relaxation and
+    // the pressure projection)
+    if (c->p.wall_model == PDF_ELLIPTIC_RELAXATION || c->p.pressure) {
         std::vector<std::pair<long long, int>> ent;  // (row*nn + col, contribution id)
         ent.reserve(9 * (size_t)nt);
         std::vector<double> mloc(9 * (size_t)nt), kloc(9 * (size_t)nt);
@@ -312,6 +331,17 @@ int build_mesh(pdf_ctx* c, const double* xy, int nn, const int* tri, int nt, con
         TRY(upload(c, &m.diag, diag));
         TRY(dalloc(c, &m.aval, m.nnz));
         TRY(dalloc(c, &m.avf, m.nnz));
+        if (c->p.pressure) {
+            // stiffness sum_e A_e grad N_k . grad N_l, and p = 0 at the lowest-id canonical node
+            std::vector<double> pval(m.nnz, 0.0);
+            for (int q = 0; q < m.nnz; ++q)
+                for (int r = kc_off[q]; r < kc_off[q + 1]; ++r) pval[q] += kc_geo[r];
+            std::vector<unsigned char> pin(nn, 0);
+            for (int i = 0; i < nn; ++i)
+                if (rep[i] == i) { pin[i] = 1; break; }
+            TRY(upload(c, &m.pval, pval));
+            TRY(upload(c, &m.pin, pin));
+        }
     }
     return PDF_OK;
 }
@@ -337,6 +367,12 @@ int alloc_stats(pdf_ctx* c) {
     TRY(dalloc(c, &c->ngrad, 4 * (size_t)nn));
     TRY(dalloc(c, &c->npack, 11 * (size_t)nn));
     TRY(dalloc(c, &c->nwp, 5 * (size_t)nn));
+    if (c->m.n_owall_elem > 0) {
+        TRY(dalloc(c, &c->eomw, 5 * (size_t)nt));
+        TRY(dalloc(c, &c->nomw, 5 * (size_t)nn));
+        PDF_CUDA(c, cudaMemset(c->eomw, 0, sizeof(double) * 5 * nt));
+        PDF_CUDA(c, cudaMemset(c->nomw, 0, sizeof(double) * 5 * nn));
+    }
     PDF_CUDA(c, cudaMalloc(&c->npackT, ts * NODE_PACK_W * nn));
     PDF_CUDA(c, cudaMalloc(&c->epackT, ts * ELEM_PACK_W * nt));
     PDF_CUDA(c, cudaMalloc(&c->ecmT, ts * (size_t)B * nt));
@@ -351,13 +387,28 @@ int alloc_stats(pdf_ctx* c) {
     PDF_CUDA(c, cudaMemset(c->d_step, 0, sizeof(uint32_t)));
     PDF_CUDA(c, cudaMemset(c->d_status, 0, sizeof(int)));
     PDF_CUDA(c, cudaMallocHost((void**)&c->h_status, sizeof(int)));
-    if (c->p.wall_model == PDF_ELLIPTIC_RELAXATION) {
+    if (c->p.wall_model == PDF_ELLIPTIC_RELAXATION || c->p.pressure) {
         const size_t v = 5 * (size_t)nn;
-        TRY(dalloc(c, &c->fe_f, v));
-        TRY(dalloc(c, &c->fe_g, v));
-        TRY(dalloc(c, &c->fe_prop, v));
+        if (c->p.wall_model == PDF_ELLIPTIC_RELAXATION) {
+            TRY(dalloc(c, &c->fe_f, v));
+            TRY(dalloc(c, &c->fe_g, v));
+            TRY(dalloc(c, &c->fe_prop, v));
+            PDF_CUDA(c, cudaMemset(c->fe_g, 0, sizeof(double) * v));
+        }
+        if (c->p.pressure) {
+            TRY(dalloc(c, &c->pr_b, v));
+            TRY(dalloc(c, &c->pr_zero, v));
+            TRY(dalloc(c, &c->pr_x, v));
+            TRY(dalloc(c, &c->pres, nn));
+            TRY(dalloc(c, &c->egp, 2 * (size_t)nt));
+            TRY(dalloc(c, &c->pr_iters, 1));
+            PDF_CUDA(c, cudaMemset(c->pr_b, 0, sizeof(double) * v));
+            PDF_CUDA(c, cudaMemset(c->pr_zero, 0, sizeof(double) * v));
+            PDF_CUDA(c, cudaMemset(c->pr_x, 0, sizeof(double) * v));
+            PDF_CUDA(c, cudaMemset(c->pres, 0, sizeof(double) * nn));
+            PDF_CUDA(c, cudaMemset(c->pr_iters, 0, sizeof(int)));
+        }
         TRY(dalloc(c, &c->fe_z, v));
-        PDF_CUDA(c, cudaMemset(c->fe_g, 0, sizeof(double) * v));
         TRY(dalloc(c, &c->fe_part, (size_t)15 * 4096));
         TRY(dalloc(c, &c->fe_bar, 32 * 64));  // barrier lines: top/generation + 63 groups of 16 blocks
         PDF_CUDA(c, cudaMemset(c->fe_bar, 0, 32 * 64 * sizeof(unsigned)));
@@ -459,6 +510,8 @@ int pdf_default_params(pdf_params* p) {
     p->case_id = 0;
     p->precision = PDF_FP64;
     p->cg_precision = 0;
+    p->omega_wall = 0;
+    p->pressure = 0;
     p->reserved_ = 0;
     return PDF_OK;
 }
@@ -555,6 +608,7 @@ int pdf_step(pdf_ctx* c, double dt, int32_t nsteps) {
         TRY(launch_sort(c, true));
         c->step++;
         TRY(launch_moments(c));
+        if (c->p.pressure) TRY(launch_pressure(c, dt));
         TRY(launch_fields(c));
         TRY(launch_averaging(c));
     }
@@ -605,6 +659,14 @@ int pdf_get_fields(pdf_ctx* c, int32_t field, void* dst, size_t bytes, int32_t d
     case PDF_FIELD_NODE_WDIST: src = c->m.wdist; need = 8 * (size_t)nn; break;
     case PDF_FIELD_NODE_GRAD: src = c->ngrad; need = 8 * 4 * (size_t)nn; break;
     case PDF_FIELD_NODE_PSIVAR: src = c->npsivar; need = 8 * (size_t)nn; break;
+    case PDF_FIELD_ELEM_OMW: case PDF_FIELD_NODE_OMW:
+        if (!c->eomw) return fail(c, PDF_ERR_STATE, "frequency-weighted wall moments exist with omega_wall = 1 only");
+        if (field == PDF_FIELD_ELEM_OMW) { src = c->eomw; need = 8 * 5 * (size_t)nt; }
+        else { src = c->nomw; need = 8 * 5 * (size_t)nn; }
+        break;
+    case PDF_FIELD_NODE_P:
+        if (!c->pres) return fail(c, PDF_ERR_STATE, "the projection pressure exists with pressure = 1 only");
+        src = c->pres; need = 8 * (size_t)nn; break;
     case PDF_FIELD_PARTICLE_WP:
         if (c->sur_mode != 4 || !c->pwp || c->pwp_n < n)
             return fail(c, PDF_ERR_STATE, "particle wp is recorded in surrogate mode 4 only");
@@ -631,6 +693,13 @@ int32_t pdf_num_elements(const pdf_ctx* c) { return c ? c->m.nt : -1; }
 int32_t pdf_num_nodes(const pdf_ctx* c) { return c ? c->m.nn : -1; }
 int32_t pdf_num_bins(const pdf_ctx* c) { return c ? c->B : -1; }
 int32_t pdf_step_index(const pdf_ctx* c) { return c ? c->step : -1; }
+
+int32_t pdf_pressure_iterations(pdf_ctx* c) {
+    if (!c || !c->pr_iters) return 0;
+    int it = 0;
+    if (cudaMemcpy(&it, c->pr_iters, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return -1;
+    return it;
+}
 
 int32_t pdf_cg_iterations(pdf_ctx* c) {
     if (!c || !c->fe_iters) return 0;
@@ -681,7 +750,8 @@ void pdf_destroy(pdf_ctx* c) {
     DevMesh& m = c->m;
     void* dev[] = {m.tri, m.nbr, m.einfo, m.xy, m.egeo_d, m.egeo_f, m.gradb, m.area, m.cent, m.n2e_off, m.n2e,
                    m.wdist, m.wn, m.is_wall, m.rep, m.rowptr, m.colidx, m.mval, m.kc_off, m.kc_elem, m.kc_geo,
-                   m.aval, m.avf, m.diag, c->idA, c->idB, c->elemA, c->elemB, c->bin, c->cnt, c->off, c->cursor, c->en,
+                   m.aval, m.avf, m.diag, m.owall_node, m.owall_elem, m.pval, m.pin, c->eomw, c->nomw, c->pr_b, c->pr_zero, c->pr_x,
+                   c->pres, c->egp, c->pr_iters, c->idA, c->idB, c->elemA, c->elemB, c->bin, c->cnt, c->off, c->cursor, c->en,
                    c->emean, c->eR, c->epsivar, c->ecm, c->nwt, c->nmean, c->nR, c->nke, c->npsivar, c->eder,
                    c->ngrad, c->npack, c->nwp, c->npackT, c->epackT, c->ecmT, c->sort_scratch, c->fe_f, c->fe_g,
                    c->fe_prop, c->fe_z, c->fe_part, c->fe_bar, c->fe_iters, c->d_status,

@@ -12,6 +12,12 @@
 // rows, and the reductions of each iteration go through per-block partials
 // summed in block order by every block (deterministic), separated by a grid
 // barrier whose spin is bounded (status ST_BARRIER on expiry).
+//
+// The same solver runs the mean-pressure projection (pressure = 1): the
+// stiffness matrix on the same pattern, one right-hand side (component 0;
+// the other four are zero and stay inactive), the lowest-id canonical node
+// held at p = 0; then the element gradient of p shifts every particle's
+// in-plane velocity and the element means by -dt grad p.
 #include <cooperative_groups.h>
 
 #include "ff.cuh"
@@ -252,10 +258,14 @@ __global__ void __launch_bounds__(BS * NC) k_pcg(const CGArgs a) {
     const int i = blockIdx.x * BS + t;
     const bool have = i < a.nn;
     const bool free_row = have && a.rep[i] == i && !a.is_wall[i];
-    // b = M f and the Dirichlet values (the matrix was assembled by k_fe_assemble)
+    // b = M f (or f itself when mval is null) and the Dirichlet values (the
+    // matrix was assembled by k_fe_assemble, or at set-up for the pressure)
     double b = 0.0, x = 0.0;
     if (have) {
-        for (int q = a.rowptr[i]; q < a.rowptr[i + 1]; ++q) b += a.mval[q] * a.f[NC * (size_t)a.colidx[q] + c];
+        if (a.mval)
+            for (int q = a.rowptr[i]; q < a.rowptr[i + 1]; ++q) b += a.mval[q] * a.f[NC * (size_t)a.colidx[q] + c];
+        else
+            b = a.f[NC * (size_t)i + c];
         x = a.is_wall[i] ? a.g[NC * (size_t)i + c] : a.x[NC * (size_t)i + c];
         a.x[NC * (size_t)i + c] = x;
     }
@@ -611,6 +621,67 @@ constexpr size_t pcg_smem() {
     return sizeof(float) * (BS * (BS + 4) + 2 * NC * BS) + sizeof(double) * 3 * NC * BS;
 }
 
+// right-hand side of the projection at every canonical node i:
+// (1/dt) sum over the elements around its class of A_e grad N_i . <U>_e
+__global__ void k_pr_rhs(int nn, const int* __restrict__ rep, const int* __restrict__ n2e_off,
+                         const int* __restrict__ n2e, const int* __restrict__ tri, const double* __restrict__ area,
+                         const double* __restrict__ gradb, const double* __restrict__ emean, double idt,
+                         double* __restrict__ b) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nn) return;
+    double s = 0.0;
+    if (rep[i] == i) {
+        for (int q = n2e_off[i]; q < n2e_off[i + 1]; ++q) {
+            const int e = n2e[q];
+            int k = 0;
+            while (k < 2 && rep[tri[3 * e + k]] != i) ++k;
+            s += area[e] * (gradb[6 * e + 2 * k] * emean[5 * e + 0] + gradb[6 * e + 2 * k + 1] * emean[5 * e + 1]);
+        }
+        s *= idt;
+    }
+    b[NC * (size_t)i] = s;
+}
+
+// node pressure from the canonical solution; element gradient; the element
+// means of occupied elements shift by -dt grad p
+__global__ void k_pr_grad(int nn, int nt, const int* __restrict__ rep, const double* __restrict__ x,
+                          const int* __restrict__ tri, const double* __restrict__ gradb, const int* __restrict__ en,
+                          double dt, double* __restrict__ pres, double* __restrict__ egp, double* __restrict__ emean) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < nn) pres[t] = x[NC * (size_t)rep[t]];
+    if (t >= nt) return;
+    double gx = 0.0, gy = 0.0;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const double pk = x[NC * (size_t)rep[tri[3 * t + k]]];
+        gx += pk * gradb[6 * t + 2 * k];
+        gy += pk * gradb[6 * t + 2 * k + 1];
+    }
+    egp[2 * t] = gx;
+    egp[2 * t + 1] = gy;
+    if (en[t] > 0) {
+        emean[5 * t + 0] -= dt * gx;
+        emean[5 * t + 1] -= dt * gy;
+    }
+}
+
+// U_p -= dt grad p of the host element: one warp per element over its
+// particles (element-sorted state)
+template <typename T>
+__global__ void k_pr_correct(int nt, const int* __restrict__ off, const double* __restrict__ egp, double dt,
+                             T* __restrict__ u, T* __restrict__ v) {
+    const int lane = threadIdx.x & 31;
+    const int nw = (int)((gridDim.x * blockDim.x) >> 5);
+    for (int e = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); e < nt; e += nw) {
+        const T du = (T)(dt * egp[2 * e]), dv = (T)(dt * egp[2 * e + 1]);
+        const int s1 = off[e + 1];
+        for (int q = off[e] + lane; q < s1; q += 32) {
+            u[q] -= du;
+            v[q] -= dv;
+        }
+    }
+}
+
 __global__ void k_fe_copy_out(int nn, const int* __restrict__ rep, const double* __restrict__ x, double* nwp) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nn) return;
@@ -651,10 +722,25 @@ cudaError_t launch_pcg(const CGArgs& a, int blocks, cudaStream_t s, bool ffv) {
 // grid of the cooperative CG for rows-per-block bs (0: the largest size whose
 // grid is co-resident: fewer blocks and partial sums, a stronger block-Jacobi
 // preconditioner)
+namespace {
+
+int choose_grid(pdf_ctx* c, int bs, bool ffv, int& chosen_bs, int& chosen_blocks);
+
+}  // namespace
+
 int prepare_elliptic(pdf_ctx* c, int bs) {
+    int chosen = 0, blocks = 0;
+    TRY_OK(choose_grid(c, bs, c->p.cg_precision == 1, chosen, blocks));
+    c->fe_bs = chosen;
+    c->fe_blocks = blocks;
+    return PDF_OK;
+}
+
+namespace {
+
+int choose_grid(pdf_ctx* c, int bs, bool ffv, int& chosen_bs, int& chosen_blocks) {
     const int nn = c->m.nn;
     int per_sm = 0, blocks = 0;
-    const bool ffv = c->p.cg_precision == 1;
     const int order[3] = {192, 160, 128};
     int chosen = 0;
     for (int k = 0; k < 3 && !chosen; ++k) {
@@ -667,10 +753,12 @@ int prepare_elliptic(pdf_ctx* c, int bs) {
     if (!chosen) return fail(c, PDF_ERR_CAPACITY, "elliptic solver: mesh too large for one resident grid");
     if ((size_t)blocks * PART_W > (size_t)15 * 4096 || (blocks + 15) / 16 > 63)
         return fail(c, PDF_ERR_CAPACITY, "elliptic solver: partial-sum buffer too small");
-    c->fe_bs = chosen;
-    c->fe_blocks = blocks;
+    chosen_bs = chosen;
+    chosen_blocks = blocks;
     return PDF_OK;
 }
+
+}  // namespace
 
 int launch_elliptic(pdf_ctx* c) {
     const int nn = c->m.nn;
@@ -715,6 +803,44 @@ int launch_elliptic(pdf_ctx* c) {
     k_fe_copy_out<<<(nn + 127) / 128, 128, 0, c->s>>>(nn, c->m.rep, c->nwp, c->nwp);
     c->launches += 3;
     timing_end(c, PDF_K_ELLIPTIC);
+    PDF_CUDA(c, cudaGetLastError());
+    return PDF_OK;
+}
+
+int launch_pressure(pdf_ctx* c, double dt) {
+    const int nn = c->m.nn, nt = c->m.nt;
+    if (c->pr_blocks == 0) TRY_OK(choose_grid(c, 0, false, c->pr_bs, c->pr_blocks));
+    timing_begin(c, PDF_K_PRESSURE);
+    k_pr_rhs<<<(nn + 127) / 128, 128, 0, c->s>>>(nn, c->m.rep, c->m.n2e_off, c->m.n2e, c->m.tri, c->m.area,
+                                                c->m.gradb, c->emean, 1.0 / dt, c->pr_b);
+    CGArgs a;
+    a.nn = nn;
+    a.rowptr = c->m.rowptr; a.colidx = c->m.colidx; a.mval = nullptr;
+    a.kc_off = nullptr; a.kc_elem = nullptr; a.kc_geo = nullptr; a.eder = nullptr;
+    a.rep = c->m.rep; a.is_wall = c->m.pin;
+    a.f = c->pr_b; a.g = c->pr_zero; a.aval = c->m.pval; a.avf = nullptr;
+    a.x = c->pr_x;  // warm start from the previous step's pressure
+    a.zg = c->fe_z;
+    a.part = c->fe_part; a.bar = c->fe_bar; a.iters = c->pr_iters; a.status = c->d_status;
+    a.tol = c->p.cg_tol; a.maxit = c->p.cg_maxit;
+    a.skip = nullptr; a.xprop = nullptr;
+    if (c->coop_wait) PDF_CUDA(c, cudaStreamWaitEvent(c->s, c->coop_wait, 0));
+    cudaError_t err;
+    if (c->pr_bs == 128) err = launch_pcg<128>(a, c->pr_blocks, c->s, false);
+    else if (c->pr_bs == 160) err = launch_pcg<160>(a, c->pr_blocks, c->s, false);
+    else err = launch_pcg<192>(a, c->pr_blocks, c->s, false);
+    PDF_CUDA(c, err);
+    if (c->coop_done) PDF_CUDA(c, cudaEventRecord(c->coop_done, c->s));
+    const int mx = nn > nt ? nn : nt;
+    k_pr_grad<<<(mx + 127) / 128, 128, 0, c->s>>>(nn, nt, c->m.rep, c->pr_x, c->m.tri, c->m.gradb, c->en, dt,
+                                                 c->pres, c->egp, c->emean);
+    const unsigned gw = (unsigned)((nt + 7) / 8);
+    if (c->prec == 0)
+        k_pr_correct<double><<<gw, 256, 0, c->s>>>(nt, c->off, c->egp, dt, (double*)c->stA[2], (double*)c->stA[3]);
+    else
+        k_pr_correct<float><<<gw, 256, 0, c->s>>>(nt, c->off, c->egp, dt, (float*)c->stA[2], (float*)c->stA[3]);
+    c->launches += 4;
+    timing_end(c, PDF_K_PRESSURE);
     PDF_CUDA(c, cudaGetLastError());
     return PDF_OK;
 }

@@ -10,10 +10,71 @@
 //  * node gradient recovery (area-weighted) and the element Laplacian;
 //  * node pack for the particle kernel: <U>, <V>, <omega>, C0 eps and G_ij
 //    (Eq. wall-GandC, or Eqs. Gij and C0 from the elliptic relaxation), and
-//    the imposed mean driving force.
+//    the imposed mean driving force;
+//  * with the Section 4 frequency reflection: <omega u_i> and <omega u_i u_j>
+//    (in-plane, fluctuations about the element mean) in the elements around
+//    the wall nodes, then their count-weighted means at the wall nodes.
 #include "pdf_internal.cuh"
 
 namespace {
+
+// frequency-weighted moments of the listed elements: one warp per element
+// over its particles (element-sorted state), FP64 sums, divisor n
+template <typename T>
+__global__ void k_omw_elem(int nl, const int* __restrict__ list, const int* __restrict__ off,
+                           const double* __restrict__ emean, const T* __restrict__ u, const T* __restrict__ v,
+                           const T* __restrict__ om, double* __restrict__ eomw) {
+    const int lane = threadIdx.x & 31;
+    const int nw = (int)((gridDim.x * blockDim.x) >> 5);
+    for (int j = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); j < nl; j += nw) {
+        const int e = list[j];
+        const int s0 = off[e], s1 = off[e + 1];
+        const double mu = emean[5 * e + 0], mv = emean[5 * e + 1];
+        double acc[5] = {0, 0, 0, 0, 0};
+        for (int q = s0 + lane; q < s1; q += 32) {
+            const double du = (double)u[q] - mu, dv = (double)v[q] - mv, o = (double)om[q];
+            const double ou = o * du, ov = o * dv;
+            acc[0] += ou;
+            acc[1] += ov;
+            acc[2] += ou * du;
+            acc[3] += ou * dv;
+            acc[4] += ov * dv;
+        }
+#pragma unroll
+        for (int k = 0; k < 5; ++k)
+#pragma unroll
+            for (int d = 16; d > 0; d >>= 1) acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], d);
+        if (lane < 5) {
+            const int n = s1 - s0;
+            double a = acc[0];
+#pragma unroll
+            for (int k = 1; k < 5; ++k) a = lane == k ? acc[k] : a;
+            eomw[5 * e + lane] = n > 0 ? a / (double)n : 0.0;
+        }
+    }
+}
+
+// count-weighted means at the listed wall nodes (periodic partners merged);
+// a node without particles keeps its previous values
+__global__ void k_omw_node(int nl, const int* __restrict__ list, const int* __restrict__ n2e_off,
+                           const int* __restrict__ n2e, const int* __restrict__ en,
+                           const double* __restrict__ eomw, double* __restrict__ nomw) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= nl) return;
+    const int i = list[j];
+    double wt = 0.0, W[5] = {0, 0, 0, 0, 0};
+    for (int q = n2e_off[i]; q < n2e_off[i + 1]; ++q) {
+        const int e = n2e[q];
+        const double n = (double)en[e];
+        wt += n;
+#pragma unroll
+        for (int k = 0; k < 5; ++k) W[k] += n * eomw[5 * e + k];
+    }
+    if (wt <= 0.0) return;
+    const double iw = 1.0 / wt;
+#pragma unroll
+    for (int k = 0; k < 5; ++k) nomw[5 * i + k] = W[k] * iw;
+}
 
 __global__ void k_node_stats(int nn, const int* __restrict__ n2e_off, const int* __restrict__ n2e,
                              const int* __restrict__ en, const double* __restrict__ emean,
@@ -182,6 +243,15 @@ int run(pdf_ctx* c) {
     k_node_grad<<<gn, tb, 0, c->s>>>(nn, c->m.n2e_off, c->m.n2e, c->m.area, c->eder, c->ngrad);
     k_elem_lap<T><<<ge, tb, 0, c->s>>>(nt, c->m.tri, c->m.gradb, c->ngrad, c->eder, (T*)c->epackT);
     c->launches += 4;
+    if (c->m.n_owall_elem > 0) {
+        const int nle = c->m.n_owall_elem, nln = c->m.n_owall_node;
+        k_omw_elem<T><<<(nle + 7) / 8, 256, 0, c->s>>>(nle, c->m.owall_elem, c->off, c->emean,
+                                                        (const T*)c->stA[2], (const T*)c->stA[3],
+                                                        (const T*)c->stA[5], c->eomw);
+        k_omw_node<<<(nln + tb - 1) / tb, tb, 0, c->s>>>(nln, c->m.owall_node, c->m.n2e_off, c->m.n2e, c->en,
+                                                          c->eomw, c->nomw);
+        c->launches += 2;
+    }
     timing_end(c, PDF_K_FIELDS);
     PDF_CUDA(c, cudaGetLastError());
     if (c->p.wall_model == PDF_ELLIPTIC_RELAXATION) {

@@ -75,6 +75,7 @@ struct StepArgs {
     const T* __restrict__ ecm;
     const double* __restrict__ nmean;
     const double* __restrict__ nR;
+    const double* __restrict__ nomw;  // Section 4 frequency reflection: wall-node <omega u_i>, <omega u_i u_j>
     T *x, *y, *u, *v, *w, *om, *psi;
     const uint32_t* __restrict__ id;
     int* elem;
@@ -91,10 +92,11 @@ struct StepArgs {
 };
 
 // velocity and frequency at a boundary hit: tag 2 symmetry; tag 1 wall
-// (wall functions in the wall-element frame, or specular no-slip)
+// (wall functions in the wall-element frame, or specular no-slip); the hit
+// lies at mu along the edge from node na to node nb
 template <typename T>
-__device__ void reflect(const StepArgs<T>& a, int tag, T nx, T ny, const double* st, T& u, T& v,
-                        T& w, T& om) {
+__device__ void reflect(const StepArgs<T>& a, int tag, T nx, T ny, const double* st, int na, int nb, double mu,
+                        T& u, T& v, T& w, T& om) {
     const T tx = ny, ty = -nx;
     const T Ut = u * tx + v * ty, Vn = u * nx + v * ny;
     if (tag == 2) {
@@ -126,7 +128,22 @@ __device__ void reflect(const StepArgs<T>& a, int tag, T nx, T ny, const double*
     const T VR = -Vn, UR = Ut + alpha * Vn;
     u = UR * tx + VR * nx;
     v = UR * ty + VR * ny;
-    om = om * t_exp<T>(a.beta * Vn / (a.yp * Omp));
+    if (a.nomw) {
+        // Section 4: omega_R = omega_I exp(-2 V_I <omega v>_p / <omega v^2>_p),
+        // v the wall-normal fluctuation; <omega v^2> floored at floor_k <omega>_p
+        const double* Wa = a.nomw + 5 * (size_t)na;
+        const double* Wb = a.nomw + 5 * (size_t)nb;
+        T W[5];
+#pragma unroll
+        for (int k = 0; k < 5; ++k) W[k] = (T)((1 - mu) * Wa[k] + mu * Wb[k]);
+        const T wv = W[0] * nx + W[1] * ny;
+        T wv2 = W[2] * nx * nx + (T)2 * W[3] * nx * ny + W[4] * ny * ny;
+        const T fl = a.floor_k * Omp;
+        wv2 = wv2 > fl ? wv2 : fl;
+        om = om * t_exp<T>((T)-2 * Vn * wv / wv2);
+    } else {
+        om = om * t_exp<T>(a.beta * Vn / (a.yp * Omp));
+    }
 }
 
 // one particle-step of particle i whose state at step n was staged in
@@ -292,7 +309,7 @@ __device__ __forceinline__ void advance_particle(const StepArgs<T>& a, const uin
             st[4] = (1 - mu) * a.nR[6 * na + 2] + mu * a.nR[6 * nb + 2];
             st[5] = (1 - mu) * a.nR[6 * na + 3] + mu * a.nR[6 * nb + 3];
             st[6] = (1 - mu) * a.nmean[4 * na + 3] + mu * a.nmean[4 * nb + 3];
-            reflect<T>(a, tag, nx, ny, st, u1, v1, w1, om1);
+            reflect<T>(a, tag, nx, ny, st, na, nb, mu, u1, v1, w1, om1);
             px = cx; py = cy;
             entry = kx;
         }
@@ -482,6 +499,7 @@ StepArgs<T> step_args(pdf_ctx* c, double dt) {
     a.ecm = (const T*)c->ecmT;
     a.nmean = c->nmean;
     a.nR = c->nR;
+    a.nomw = (p.wall_model == PDF_WALL_FUNCTIONS && p.omega_wall) ? c->nomw : nullptr;
     a.x = (T*)c->stA[0]; a.y = (T*)c->stA[1]; a.u = (T*)c->stA[2]; a.v = (T*)c->stA[3];
     a.w = (T*)c->stA[4]; a.om = (T*)c->stA[5]; a.psi = (T*)c->stA[6];
     a.id = c->idA;

@@ -63,6 +63,14 @@ struct DevMesh {
     double* aval = nullptr;    // assembled M + K_{L^2}
     float2* avf = nullptr;     // the same as float-float (compensated-FP32 CG)
     int* diag = nullptr;       // position of the diagonal entry per row (-1 if none)
+    // Section 4 frequency reflection (omega_wall = 1): wall nodes, elements around them
+    int n_owall_node = 0, n_owall_elem = 0;
+    int* owall_node = nullptr;
+    int* owall_elem = nullptr;
+    // mean-pressure projection (pressure = 1): stiffness values on the FE
+    // pattern and the pinned node
+    double* pval = nullptr;
+    unsigned char* pin = nullptr;
 };
 
 struct Timing {
@@ -98,6 +106,14 @@ struct pdf_ctx {
     double *emean = nullptr, *eR = nullptr, *epsivar = nullptr, *ecm = nullptr;
     double *nwt = nullptr, *nmean = nullptr, *nR = nullptr, *nke = nullptr, *npsivar = nullptr;
     double *eder = nullptr, *ngrad = nullptr, *npack = nullptr, *nwp = nullptr;
+    // frequency-weighted moments <omega u>,<omega v>,<omega uu>,<omega uv>,<omega vv>
+    // of the Section 4 frequency reflection (omega_wall = 1 only)
+    double *eomw = nullptr, *nomw = nullptr;
+    // mean-pressure projection: right-hand side, zero Dirichlet values and the
+    // solution ([nn][5], component 0 used), node pressure, element gradient
+    double *pr_b = nullptr, *pr_zero = nullptr, *pr_x = nullptr, *pres = nullptr, *egp = nullptr;
+    int* pr_iters = nullptr;
+    int pr_bs = 0, pr_blocks = 0;
     // particle-kernel copies in the state precision
     void* npackT = nullptr;
     void* epackT = nullptr;
@@ -181,12 +197,13 @@ int launch_count_and_sort(pdf_ctx* c);  // histogram of elemA, then launch_sort
 int launch_moments(pdf_ctx* c);
 int launch_fields(pdf_ctx* c);      // node stats, derived, recovery, ER solve, packs
 int launch_elliptic(pdf_ctx* c);
+int launch_pressure(pdf_ctx* c, double dt);  // projection after the moments (pressure = 1)
 int prepare_particle(pdf_ctx* c, int per_sm);   // persistent grid (0: all resident blocks)
 int particle_occupancy(pdf_ctx* c);
 int prepare_elliptic(pdf_ctx* c, int bs);       // CG rows per block (0: largest co-resident)
 int prepare_moments(pdf_ctx* c);
-int launch_surrogate(pdf_ctx* c);
-int launch_averaging(pdf_ctx* c);   // running sums of the statistics and the CDF probes (when on)   // network wp at the nodes + FE residual check (before the CG)
+int launch_surrogate(pdf_ctx* c);   // network wp at the nodes + FE residual check (before the CG)
+int launch_averaging(pdf_ctx* c);   // running sums of the statistics and the CDF probes (when on)
 int surrogate_rows(pdf_ctx* c);     // builds the free canonical row list once
 int launch_to_double(pdf_ctx* c, const void* src, double* dst, int64_t n);
 

@@ -7,7 +7,10 @@ same Philox streams. Bars:
     must still contain the GPU's position;
   * one-step particle state: |gpu - oracle| <= rtol (|oracle| + rms) with
     rtol = 1e-12 (FP64) and 1e-5 (FP32), rms the root mean square of that
-    component over the ensemble;
+    component over the ensemble; in FP32, particles that end within 1e-6 of
+    an element edge are left out of the state bar (a boundary crossing by
+    less than the FP32 resolution of the position can be taken or not; their
+    host element is still checked);
   * statistics from the same particles: rtol 1e-12 (FP64 reductions) or
     2e-6 (compensated FP32 reductions); bins bit-exact;
   * multi-step statistics of independent runs: within 3 Monte Carlo standard
@@ -74,10 +77,14 @@ def edge_distance(mesh, P):
     return np.minimum(np.minimum(d0, d1), d2)
 
 
-def assert_state_close(g, o, rtol):
+def assert_state_close(g, o, rtol, skip=None):
     """Relative error per particle: position and velocity against their vector
     norms (plus the ensemble rms of that norm), omega and psi against their
-    magnitude (plus the ensemble rms)."""
+    magnitude (plus the ensemble rms). Particles flagged in skip are left out."""
+    if skip is not None:
+        keep = ~skip
+        g = {k: v[keep] for k, v in g.items()}
+        o = {k: v[keep] for k, v in o.items()}
     groups = (("x", "y"), ("u", "v", "w"), ("om",), ("psi",))
     for grp in groups:
         norm = np.sqrt(sum(o[k] ** 2 for k in grp))
@@ -186,7 +193,7 @@ def test_one_step_matches_oracle(wf_mesh, er_mesh, precision, wall_model):
         Gs = {k: v[~same] for k, v in G.items()}
         assert np.all(edge_distance(mesh, Gs) > -10 * edge_tol)
     rtol = 1e-12 if precision == "fp64" else 1e-5
-    assert_state_close(G, O, rtol)
+    assert_state_close(G, O, rtol, skip=None if precision == "fp64" else near)
     assert np.array_equal(np.sort(G["elem"]), g.field("elem"))
 
 
