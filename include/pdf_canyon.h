@@ -99,6 +99,8 @@ typedef struct pdf_params {
                               element mean velocities become weakly divergence-free (the scheme the
                               paper cites for its mean pressure is not given in it) */
     int32_t reserved_;
+    double pressure_tol;   /* relative residual of the projection's CG (default 1e-6: the
+                              divergence left is far below that of the estimation noise) */
 } pdf_params;
 
 /* Fields readable with pdf_get_fields. Particle fields are in the library's

@@ -47,7 +47,8 @@ class pdf_params(C.Structure):
         ("cg_maxit", C.c_int32), ("nb1", C.c_int32), ("nb2", C.c_int32), ("nb3", C.c_int32),
         ("wall_model", C.c_int32), ("mix_exp", C.c_int32), ("reflect_max", C.c_int32), ("rotta", C.c_int32),
         ("seed", C.c_uint64), ("case_id", C.c_uint32), ("precision", C.c_int32), ("cg_precision", C.c_int32),
-        ("omega_wall", C.c_int32), ("pressure", C.c_int32), ("reserved_", C.c_int32)]
+        ("omega_wall", C.c_int32), ("pressure", C.c_int32), ("reserved_", C.c_int32),
+        ("pressure_tol", C.c_double)]
 
 
 EXPORTS = ("pdf_default_params", "pdf_init_mesh", "pdf_seed_particles", "pdf_set_particles",

@@ -101,6 +101,7 @@ int check_params(const pdf_params* p) {
     if (p->cg_precision < 0 || p->cg_precision > 1) return PDF_ERR_ARG;
     if (p->omega_wall < 0 || p->omega_wall > 1) return PDF_ERR_ARG;
     if (p->pressure < 0 || p->pressure > 1) return PDF_ERR_ARG;
+    if (p->pressure && !(p->pressure_tol > 0.0 && p->pressure_tol < 1.0)) return PDF_ERR_ARG;
     if (!(p->period > 0) || !(p->nu > 0) || p->reflect_max < 0 || p->cg_maxit < 0) return PDF_ERR_ARG;
     return PDF_OK;
 }
@@ -396,15 +397,13 @@ int alloc_stats(pdf_ctx* c) {
             PDF_CUDA(c, cudaMemset(c->fe_g, 0, sizeof(double) * v));
         }
         if (c->p.pressure) {
-            TRY(dalloc(c, &c->pr_b, v));
-            TRY(dalloc(c, &c->pr_zero, v));
-            TRY(dalloc(c, &c->pr_x, v));
+            TRY(dalloc(c, &c->pr_b, nn));
+            TRY(dalloc(c, &c->pr_x, nn));
             TRY(dalloc(c, &c->pres, nn));
             TRY(dalloc(c, &c->egp, 2 * (size_t)nt));
             TRY(dalloc(c, &c->pr_iters, 1));
-            PDF_CUDA(c, cudaMemset(c->pr_b, 0, sizeof(double) * v));
-            PDF_CUDA(c, cudaMemset(c->pr_zero, 0, sizeof(double) * v));
-            PDF_CUDA(c, cudaMemset(c->pr_x, 0, sizeof(double) * v));
+            PDF_CUDA(c, cudaMemset(c->pr_b, 0, sizeof(double) * nn));
+            PDF_CUDA(c, cudaMemset(c->pr_x, 0, sizeof(double) * nn));
             PDF_CUDA(c, cudaMemset(c->pres, 0, sizeof(double) * nn));
             PDF_CUDA(c, cudaMemset(c->pr_iters, 0, sizeof(int)));
         }
@@ -513,6 +512,7 @@ int pdf_default_params(pdf_params* p) {
     p->omega_wall = 0;
     p->pressure = 0;
     p->reserved_ = 0;
+    p->pressure_tol = 1e-6;
     return PDF_OK;
 }
 
@@ -534,6 +534,7 @@ int pdf_init_mesh(const pdf_params* p, const double* xy, int32_t nnode, const in
     int st = build_mesh(c, xy, nnode, tri, ntri, edge_tag, periodic_pair);
     if (st == PDF_OK) st = alloc_stats(c);
     if (st == PDF_OK) st = prepare_moments(c);
+    if (st == PDF_OK && c->p.pressure) st = prepare_pressure(c);
     if (st != PDF_OK) {
         g_init_error = c->err;
         pdf_destroy(c);
@@ -750,8 +751,8 @@ void pdf_destroy(pdf_ctx* c) {
     DevMesh& m = c->m;
     void* dev[] = {m.tri, m.nbr, m.einfo, m.xy, m.egeo_d, m.egeo_f, m.gradb, m.area, m.cent, m.n2e_off, m.n2e,
                    m.wdist, m.wn, m.is_wall, m.rep, m.rowptr, m.colidx, m.mval, m.kc_off, m.kc_elem, m.kc_geo,
-                   m.aval, m.avf, m.diag, m.owall_node, m.owall_elem, m.pval, m.pin, c->eomw, c->nomw, c->pr_b, c->pr_zero, c->pr_x,
-                   c->pres, c->egp, c->pr_iters, c->idA, c->idB, c->elemA, c->elemB, c->bin, c->cnt, c->off, c->cursor, c->en,
+                   m.aval, m.avf, m.diag, m.owall_node, m.owall_elem, m.pval, m.pin, c->eomw, c->nomw, c->pr_b, c->pr_x, c->pr_binv,
+                   c->pr_a0inv, c->pres, c->egp, c->pr_iters, c->idA, c->idB, c->elemA, c->elemB, c->bin, c->cnt, c->off, c->cursor, c->en,
                    c->emean, c->eR, c->epsivar, c->ecm, c->nwt, c->nmean, c->nR, c->nke, c->npsivar, c->eder,
                    c->ngrad, c->npack, c->nwp, c->npackT, c->epackT, c->ecmT, c->sort_scratch, c->fe_f, c->fe_g,
                    c->fe_prop, c->fe_z, c->fe_part, c->fe_bar, c->fe_iters, c->d_status,

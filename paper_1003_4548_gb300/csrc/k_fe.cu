@@ -12,14 +12,10 @@
 // rows, and the reductions of each iteration go through per-block partials
 // summed in block order by every block (deterministic), separated by a grid
 // barrier whose spin is bounded (status ST_BARRIER on expiry).
-//
-// The same solver runs the mean-pressure projection (pressure = 1): the
-// stiffness matrix on the same pattern, one right-hand side (component 0;
-// the other four are zero and stay inactive), the lowest-id canonical node
-// held at p = 0; then the element gradient of p shifts every particle's
-// in-plane velocity and the element means by -dt grad p.
+
 #include <cooperative_groups.h>
 
+#include "coop.cuh"
 #include "ff.cuh"
 #include "pdf_internal.cuh"
 
@@ -128,42 +124,6 @@ __device__ __forceinline__ bool skip_solve(const CGArgs& a) {
 
 constexpr int PART_W = 4 * NC;  // partial sums per block: 3 NC in phase A, NC in phase B
 
-__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
-    unsigned v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-
-// grid-wide barrier of a cooperative launch: arrival by an acq_rel atomic on
-// one counter, the last block bumps the generation word, the others poll it
-// with acquire loads (measured ~2.4 us on GB300 for 80-161 blocks). The wait
-// is bounded (ST_BARRIER, then the block proceeds).
-__device__ void grid_barrier(const CGArgs& a) {
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        unsigned* gen = a.bar + 1;
-        unsigned* top = a.bar;
-        const unsigned g0 = ld_acquire(gen);
-        asm volatile("fence.acq_rel.gpu;" ::: "memory");
-        unsigned arrived;
-        asm volatile("atom.add.acq_rel.gpu.global.u32 %0, [%1], 1;" : "=r"(arrived) : "l"(top) : "memory");
-        if (arrived + 1u == gridDim.x) {
-            asm volatile("st.relaxed.gpu.global.u32 [%0], 0;" ::"l"(top) : "memory");
-            asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(gen) : "memory");
-        } else {
-            long long spins = 0;
-            while (ld_acquire(gen) == g0) {
-                if (++spins > (1ll << 22)) {  // ~1-2 s of polling
-                    set_status(a.status, ST_BARRIER);
-                    break;
-                }
-            }
-        }
-        asm volatile("fence.acq_rel.gpu;" ::: "memory");
-    }
-    __syncthreads();
-}
-
 // Per-block sums over the rows of NV values per component (value v of
 // component c of row t staged at red[(v * NC + c) * BS + t]); warp q sums
 // value-component q in a fixed order and writes part[block][slot + q].
@@ -186,8 +146,19 @@ __device__ void block_partial(const CGArgs& a, double* red, int nv, int slot) {
 __device__ void grid_sum(const CGArgs& a, int slot, int nvals, double* out) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     for (int q = wid; q < nvals; q += blockDim.x / 32) {
+        // the loads of a chunk of 4 x 32 blocks are issued together, then
+        // summed in order
         double s = 0.0;
-        for (int bl = lane; bl < (int)gridDim.x; bl += 32) s += a.part[(size_t)bl * PART_W + slot + q];
+        for (int b0 = 0; b0 < (int)gridDim.x; b0 += 4 * 32) {
+            double v[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int bl = b0 + 32 * k + lane;
+                v[k] = bl < (int)gridDim.x ? a.part[(size_t)bl * PART_W + slot + q] : 0.0;
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k) s += v[k];
+        }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
         if (lane == 0) out[q] = s;
@@ -258,14 +229,10 @@ __global__ void __launch_bounds__(BS * NC) k_pcg(const CGArgs a) {
     const int i = blockIdx.x * BS + t;
     const bool have = i < a.nn;
     const bool free_row = have && a.rep[i] == i && !a.is_wall[i];
-    // b = M f (or f itself when mval is null) and the Dirichlet values (the
-    // matrix was assembled by k_fe_assemble, or at set-up for the pressure)
+    // b = M f and the Dirichlet values (the matrix was assembled by k_fe_assemble)
     double b = 0.0, x = 0.0;
     if (have) {
-        if (a.mval)
-            for (int q = a.rowptr[i]; q < a.rowptr[i + 1]; ++q) b += a.mval[q] * a.f[NC * (size_t)a.colidx[q] + c];
-        else
-            b = a.f[NC * (size_t)i + c];
+        for (int q = a.rowptr[i]; q < a.rowptr[i + 1]; ++q) b += a.mval[q] * a.f[NC * (size_t)a.colidx[q] + c];
         x = a.is_wall[i] ? a.g[NC * (size_t)i + c] : a.x[NC * (size_t)i + c];
         a.x[NC * (size_t)i + c] = x;
     }
@@ -299,7 +266,7 @@ __global__ void __launch_bounds__(BS * NC) k_pcg(const CGArgs a) {
         }
         __syncthreads();
     }
-    grid_barrier(a);  // all x (warm start + Dirichlet) and matrix rows are in place
+    grid_barrier(a.bar, a.status);  // all x (warm start + Dirichlet) and matrix rows are in place
     // r = b - A x; z = Ainv r; p = z
     double r, z, p, ap;
     {
@@ -322,7 +289,7 @@ __global__ void __launch_bounds__(BS * NC) k_pcg(const CGArgs a) {
         red[(2 * NC + c) * BS + t] = free_row ? b0 * b0 : 0.0;
         block_partial<BS>(a, red, 3, 0);
     }
-    grid_barrier(a);
+    grid_barrier(a.bar, a.status);
     grid_sum(a, 0, 3 * NC, s_a);
     if (threadIdx.x < NC) {
         s_rz[threadIdx.x] = s_a[threadIdx.x];
@@ -337,7 +304,7 @@ __global__ void __launch_bounds__(BS * NC) k_pcg(const CGArgs a) {
         red[c * BS + t] = p * ap;
         block_partial<BS>(a, red, 1, 3 * NC);
     }
-    grid_barrier(a);
+    grid_barrier(a.bar, a.status);
     grid_sum(a, 3 * NC, NC, s_pap);
     int it = 0;
     for (;; ++it) {
@@ -372,7 +339,7 @@ __global__ void __launch_bounds__(BS * NC) k_pcg(const CGArgs a) {
             red[(2 * NC + c) * BS + t] = r * r;
             block_partial<BS>(a, red, 3, 0);
         }
-        grid_barrier(a);
+        grid_barrier(a.bar, a.status);
         grid_sum(a, 0, 3 * NC, s_a);
         if (threadIdx.x < NC) {
             const int k = threadIdx.x;
@@ -392,7 +359,7 @@ __global__ void __launch_bounds__(BS * NC) k_pcg(const CGArgs a) {
             red[c * BS + t] = p * ap;
             block_partial<BS>(a, red, 1, 3 * NC);
         }
-        grid_barrier(a);
+        grid_barrier(a.bar, a.status);
         if (threadIdx.x < NC && s_active[threadIdx.x]) {
             s_rz[threadIdx.x] = s_a[threadIdx.x];
             s_rr[threadIdx.x] = s_a[2 * NC + threadIdx.x];
@@ -494,7 +461,7 @@ __global__ void __launch_bounds__(BS * NC) k_pcg_ff(const CGArgs a) {
         }
         __syncthreads();
     }
-    grid_barrier(a);
+    grid_barrier(a.bar, a.status);
     float* zg = reinterpret_cast<float*>(a.zg);
     ff x = ff_from_double(x0), r, p, ap;
     float z;
@@ -519,14 +486,14 @@ __global__ void __launch_bounds__(BS * NC) k_pcg_ff(const CGArgs a) {
         redh[(2 * NC + c) * BS + t] = bb.hi; redl[(2 * NC + c) * BS + t] = bb.lo;
         block_partial_ff<BS>(a, redh, redl, 3, 0);
     }
-    grid_barrier(a);
+    grid_barrier(a.bar, a.status);
     grid_sum_ff(a, 0, 3 * NC, s_a);
     if (threadIdx.x < NC) {
         s_rz[threadIdx.x] = s_a[threadIdx.x];
         s_rr[threadIdx.x] = s_a[NC + threadIdx.x];
         s_bn[threadIdx.x] = sqrt(s_a[2 * NC + threadIdx.x]);
     }
-    grid_barrier(a);  // the partials are reused below
+    grid_barrier(a.bar, a.status);  // the partials are reused below
     {  // A p_0
         ff s = ff{0.f, 0.f};
         if (free_row)
@@ -540,7 +507,7 @@ __global__ void __launch_bounds__(BS * NC) k_pcg_ff(const CGArgs a) {
         redl[c * BS + t] = pap.lo;
         block_partial_ff<BS>(a, redh, redl, 1, 3 * NC);
     }
-    grid_barrier(a);
+    grid_barrier(a.bar, a.status);
     grid_sum_ff(a, 3 * NC, NC, s_pap);
     int it = 0;
     for (;; ++it) {
@@ -576,7 +543,7 @@ __global__ void __launch_bounds__(BS * NC) k_pcg_ff(const CGArgs a) {
             redh[(2 * NC + c) * BS + t] = rr.hi; redl[(2 * NC + c) * BS + t] = rr.lo;
             block_partial_ff<BS>(a, redh, redl, 3, 0);
         }
-        grid_barrier(a);
+        grid_barrier(a.bar, a.status);
         grid_sum_ff(a, 0, 3 * NC, s_a);
         if (threadIdx.x < NC) {
             const int k = threadIdx.x;
@@ -600,7 +567,7 @@ __global__ void __launch_bounds__(BS * NC) k_pcg_ff(const CGArgs a) {
             redl[c * BS + t] = pap.lo;
             block_partial_ff<BS>(a, redh, redl, 1, 3 * NC);
         }
-        grid_barrier(a);
+        grid_barrier(a.bar, a.status);
         if (threadIdx.x < NC && s_active[threadIdx.x]) {
             s_rz[threadIdx.x] = s_a[threadIdx.x];
             s_rr[threadIdx.x] = s_a[2 * NC + threadIdx.x];
@@ -619,67 +586,6 @@ constexpr size_t pcg_ff_smem() {
 template <int BS>
 constexpr size_t pcg_smem() {
     return sizeof(float) * (BS * (BS + 4) + 2 * NC * BS) + sizeof(double) * 3 * NC * BS;
-}
-
-// right-hand side of the projection at every canonical node i:
-// (1/dt) sum over the elements around its class of A_e grad N_i . <U>_e
-__global__ void k_pr_rhs(int nn, const int* __restrict__ rep, const int* __restrict__ n2e_off,
-                         const int* __restrict__ n2e, const int* __restrict__ tri, const double* __restrict__ area,
-                         const double* __restrict__ gradb, const double* __restrict__ emean, double idt,
-                         double* __restrict__ b) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= nn) return;
-    double s = 0.0;
-    if (rep[i] == i) {
-        for (int q = n2e_off[i]; q < n2e_off[i + 1]; ++q) {
-            const int e = n2e[q];
-            int k = 0;
-            while (k < 2 && rep[tri[3 * e + k]] != i) ++k;
-            s += area[e] * (gradb[6 * e + 2 * k] * emean[5 * e + 0] + gradb[6 * e + 2 * k + 1] * emean[5 * e + 1]);
-        }
-        s *= idt;
-    }
-    b[NC * (size_t)i] = s;
-}
-
-// node pressure from the canonical solution; element gradient; the element
-// means of occupied elements shift by -dt grad p
-__global__ void k_pr_grad(int nn, int nt, const int* __restrict__ rep, const double* __restrict__ x,
-                          const int* __restrict__ tri, const double* __restrict__ gradb, const int* __restrict__ en,
-                          double dt, double* __restrict__ pres, double* __restrict__ egp, double* __restrict__ emean) {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t < nn) pres[t] = x[NC * (size_t)rep[t]];
-    if (t >= nt) return;
-    double gx = 0.0, gy = 0.0;
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        const double pk = x[NC * (size_t)rep[tri[3 * t + k]]];
-        gx += pk * gradb[6 * t + 2 * k];
-        gy += pk * gradb[6 * t + 2 * k + 1];
-    }
-    egp[2 * t] = gx;
-    egp[2 * t + 1] = gy;
-    if (en[t] > 0) {
-        emean[5 * t + 0] -= dt * gx;
-        emean[5 * t + 1] -= dt * gy;
-    }
-}
-
-// U_p -= dt grad p of the host element: one warp per element over its
-// particles (element-sorted state)
-template <typename T>
-__global__ void k_pr_correct(int nt, const int* __restrict__ off, const double* __restrict__ egp, double dt,
-                             T* __restrict__ u, T* __restrict__ v) {
-    const int lane = threadIdx.x & 31;
-    const int nw = (int)((gridDim.x * blockDim.x) >> 5);
-    for (int e = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); e < nt; e += nw) {
-        const T du = (T)(dt * egp[2 * e]), dv = (T)(dt * egp[2 * e + 1]);
-        const int s1 = off[e + 1];
-        for (int q = off[e] + lane; q < s1; q += 32) {
-            u[q] -= du;
-            v[q] -= dv;
-        }
-    }
 }
 
 __global__ void k_fe_copy_out(int nn, const int* __restrict__ rep, const double* __restrict__ x, double* nwp) {
@@ -807,40 +713,3 @@ int launch_elliptic(pdf_ctx* c) {
     return PDF_OK;
 }
 
-int launch_pressure(pdf_ctx* c, double dt) {
-    const int nn = c->m.nn, nt = c->m.nt;
-    if (c->pr_blocks == 0) TRY_OK(choose_grid(c, 0, false, c->pr_bs, c->pr_blocks));
-    timing_begin(c, PDF_K_PRESSURE);
-    k_pr_rhs<<<(nn + 127) / 128, 128, 0, c->s>>>(nn, c->m.rep, c->m.n2e_off, c->m.n2e, c->m.tri, c->m.area,
-                                                c->m.gradb, c->emean, 1.0 / dt, c->pr_b);
-    CGArgs a;
-    a.nn = nn;
-    a.rowptr = c->m.rowptr; a.colidx = c->m.colidx; a.mval = nullptr;
-    a.kc_off = nullptr; a.kc_elem = nullptr; a.kc_geo = nullptr; a.eder = nullptr;
-    a.rep = c->m.rep; a.is_wall = c->m.pin;
-    a.f = c->pr_b; a.g = c->pr_zero; a.aval = c->m.pval; a.avf = nullptr;
-    a.x = c->pr_x;  // warm start from the previous step's pressure
-    a.zg = c->fe_z;
-    a.part = c->fe_part; a.bar = c->fe_bar; a.iters = c->pr_iters; a.status = c->d_status;
-    a.tol = c->p.cg_tol; a.maxit = c->p.cg_maxit;
-    a.skip = nullptr; a.xprop = nullptr;
-    if (c->coop_wait) PDF_CUDA(c, cudaStreamWaitEvent(c->s, c->coop_wait, 0));
-    cudaError_t err;
-    if (c->pr_bs == 128) err = launch_pcg<128>(a, c->pr_blocks, c->s, false);
-    else if (c->pr_bs == 160) err = launch_pcg<160>(a, c->pr_blocks, c->s, false);
-    else err = launch_pcg<192>(a, c->pr_blocks, c->s, false);
-    PDF_CUDA(c, err);
-    if (c->coop_done) PDF_CUDA(c, cudaEventRecord(c->coop_done, c->s));
-    const int mx = nn > nt ? nn : nt;
-    k_pr_grad<<<(mx + 127) / 128, 128, 0, c->s>>>(nn, nt, c->m.rep, c->pr_x, c->m.tri, c->m.gradb, c->en, dt,
-                                                 c->pres, c->egp, c->emean);
-    const unsigned gw = (unsigned)((nt + 7) / 8);
-    if (c->prec == 0)
-        k_pr_correct<double><<<gw, 256, 0, c->s>>>(nt, c->off, c->egp, dt, (double*)c->stA[2], (double*)c->stA[3]);
-    else
-        k_pr_correct<float><<<gw, 256, 0, c->s>>>(nt, c->off, c->egp, dt, (float*)c->stA[2], (float*)c->stA[3]);
-    c->launches += 4;
-    timing_end(c, PDF_K_PRESSURE);
-    PDF_CUDA(c, cudaGetLastError());
-    return PDF_OK;
-}

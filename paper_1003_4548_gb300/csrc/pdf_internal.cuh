@@ -109,9 +109,12 @@ struct pdf_ctx {
     // frequency-weighted moments <omega u>,<omega v>,<omega uu>,<omega uv>,<omega vv>
     // of the Section 4 frequency reflection (omega_wall = 1 only)
     double *eomw = nullptr, *nomw = nullptr;
-    // mean-pressure projection: right-hand side, zero Dirichlet values and the
-    // solution ([nn][5], component 0 used), node pressure, element gradient
-    double *pr_b = nullptr, *pr_zero = nullptr, *pr_x = nullptr, *pres = nullptr, *egp = nullptr;
+    // mean-pressure projection: right-hand side and solution (canonical
+    // rows), node pressure, element gradient; the preconditioner's FP32 block
+    // inverses and FP64 coarse inverse (built once)
+    double *pr_b = nullptr, *pr_x = nullptr, *pres = nullptr, *egp = nullptr;
+    float* pr_binv = nullptr;
+    double* pr_a0inv = nullptr;
     int* pr_iters = nullptr;
     int pr_bs = 0, pr_blocks = 0;
     // particle-kernel copies in the state precision
@@ -197,6 +200,7 @@ int launch_count_and_sort(pdf_ctx* c);  // histogram of elemA, then launch_sort
 int launch_moments(pdf_ctx* c);
 int launch_fields(pdf_ctx* c);      // node stats, derived, recovery, ER solve, packs
 int launch_elliptic(pdf_ctx* c);
+int prepare_pressure(pdf_ctx* c);             // grid and preconditioner of the projection, once
 int launch_pressure(pdf_ctx* c, double dt);  // projection after the moments (pressure = 1)
 int prepare_particle(pdf_ctx* c, int per_sm);   // persistent grid (0: all resident blocks)
 int particle_occupancy(pdf_ctx* c);

@@ -51,7 +51,7 @@ def test_defaults_are_the_paper_constants():
     for k, v in g.items():
         assert getattr(p, k) == v, k
         assert o[k] == v, k
-    assert ctypes.sizeof(capi.pdf_params) == 336  # 34 doubles, 8 int32, the seed, 6 int32
+    assert ctypes.sizeof(capi.pdf_params) == 344  # 34 doubles, 8 int32, the seed, 6 int32, 1 double
 
 
 def _tiny_mesh():

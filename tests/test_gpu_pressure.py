@@ -40,7 +40,7 @@ def element_means(mesh, P):
                                                   ("fp32_kahan", "wf")])
 def test_projection_step_matches_oracle(wf_mesh, er_mesh, precision, wall_model):
     mesh = wf_mesh if wall_model == "wf" else er_mesh
-    g, o = both(mesh, precision=precision, wall_model=wall_model, seed=29, pressure=1)
+    g, o = both(mesh, precision=precision, wall_model=wall_model, seed=29, pressure=1, pressure_tol=1e-12)
     dt = cfl_dt(mesh, cfl=0.5, k0=1e-3)
     g.seed_particles(32)
     g.estimate_stats()
@@ -75,7 +75,7 @@ def test_projection_step_matches_oracle(wf_mesh, er_mesh, precision, wall_model)
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 def test_gpu_state_is_weakly_divergence_free(wf_mesh, precision):
-    g, _ = both(wf_mesh, precision=precision, seed=31, pressure=1, cg_tol=1e-12)
+    g, _ = both(wf_mesh, precision=precision, seed=31, pressure=1, pressure_tol=1e-12)
     dt = cfl_dt(wf_mesh, cfl=0.5, k0=1e-3)
     g.seed_particles(32)
     g.estimate_stats()
