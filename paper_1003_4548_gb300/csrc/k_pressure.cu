@@ -169,10 +169,13 @@ template <int BS, int NV>
 __device__ __forceinline__ void publish(const PrArgs& a, double (&v)[NV], const int (&slot)[NV], double* red) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
-    for (int k = 0; k < NV; ++k) {
+    for (int o = 16; o > 0; o >>= 1) {  // the NV trees interleaved
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
-        if (lane == 0) red[wid * NV + k] = v[k];
+        for (int k = 0; k < NV; ++k) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
+    }
+    if (lane == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) red[wid * NV + k] = v[k];
     }
     __syncthreads();
     if (threadIdx.x < NV) {
@@ -223,16 +226,28 @@ __device__ __forceinline__ double precondition(const PrArgs& a, const float* inv
     const int t = threadIdx.x, lane = t & 31;
     rv[t] = (float)r;
     if (t < 32) {
-        double s = 0.0;
-        for (int c = lane; c < a.nb; c += 32) s += a0row[c] * rc[c];
+        double s = 0.0, s1 = 0.0;  // two chains (the FP64 pipe's latency is long on GB300)
+        int c = lane;
+        for (; c + 32 < a.nb; c += 64) {
+            s = fma(a0row[c], rc[c], s);
+            s1 = fma(a0row[c + 32], rc[c + 32], s1);
+        }
+        if (c < a.nb) s = fma(a0row[c], rc[c], s);
+        s += s1;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
         if (lane == 0) *z0s = s;
     }
     __syncthreads();
-    float z = 0.f;
-#pragma unroll 8
-    for (int k = 0; k < BS; ++k) z = fmaf(inv[k * (BS + 4) + t], rv[k], z);
+    float z0 = 0.f, z1 = 0.f, z2 = 0.f, z3 = 0.f;  // four chains, summed in a fixed order
+#pragma unroll 4
+    for (int k = 0; k < BS; k += 4) {
+        z0 = fmaf(inv[k * (BS + 4) + t], rv[k], z0);
+        z1 = fmaf(inv[(k + 1) * (BS + 4) + t], rv[k + 1], z1);
+        z2 = fmaf(inv[(k + 2) * (BS + 4) + t], rv[k + 2], z2);
+        z3 = fmaf(inv[(k + 3) * (BS + 4) + t], rv[k + 3], z3);
+    }
+    const float z = (z0 + z1) + (z2 + z3);
     const double out = fr ? (double)z + *z0s : 0.0;
     __syncthreads();  // rv and z0s are rewritten by the next call
     return out;
@@ -242,9 +257,15 @@ __device__ __forceinline__ double precondition(const PrArgs& a, const float* inv
 // global memory)
 __device__ __forceinline__ double row_times(const PrArgs& a, const int* scol, const double* sval, int BSn, int t,
                                             int i, int len, const double* v) {
-    double s = 0.0;
+    double s = 0.0, s1 = 0.0;  // two chains (the FP64 pipe's latency is long on GB300)
     const int m = len < RMAX ? len : RMAX;
-    for (int k = 0; k < m; ++k) s += sval[k * BSn + t] * v[scol[k * BSn + t]];
+    int k = 0;
+    for (; k + 1 < m; k += 2) {
+        s = fma(sval[k * BSn + t], v[scol[k * BSn + t]], s);
+        s1 = fma(sval[(k + 1) * BSn + t], v[scol[(k + 1) * BSn + t]], s1);
+    }
+    if (k < m) s = fma(sval[k * BSn + t], v[scol[k * BSn + t]], s);
+    s += s1;
     if (len > RMAX) {
         const int q0 = a.rowptr[i];
         for (int k = RMAX; k < len; ++k) s += a.val[q0 + k] * v[a.colidx[q0 + k]];
@@ -377,7 +398,7 @@ int try_grid(pdf_ctx* c, int& blocks) {
         return 0;
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg_p<BS>, BS, smem) != cudaSuccess) return 0;
-    if (nb > per_sm * c->num_sms || (size_t)nb * PR_W > (size_t)15 * 4096) return 0;
+    if (nb > per_sm * c->num_sms || nb > 1024 || (size_t)nb * PR_W > (size_t)15 * 4096) return 0;
     blocks = nb;
     return BS;
 }
