@@ -45,6 +45,8 @@ def args_():
     ap.add_argument("--no-forms", action="store_true", help="skip the plain forms and the precision study")
     ap.add_argument("--save-surrogate", default=None, help="write the trained network (npz) here")
     ap.add_argument("--load-surrogate", default=None, help="use this trained network (npz) instead of training")
+    ap.add_argument("--pressure", action="store_true",
+                    help="add the mean-pressure projection to the timed form (not the published configuration)")
     ap.add_argument("--surrogate-mode", type=int, default=1, choices=[1, 3],
                     help="1: network at the nodes; 3: network at every particle inside the particle kernel")
     return ap.parse_args()
@@ -581,7 +583,10 @@ def main():
     form_name = (f"{prec} particle state, {red} statistics" +
                  (", surrogate wp with the FE solve as checked fallback" if use_sur else ", FE solve every step"))
     # each rank runs its own canyon case (independent problems, no exchange)
-    chosen = Form(cfg, mesh, stream, precision=prec, case_id=rank, cg_precision=a.cg_precision, sur=sur)
+    extra = {"pressure": 1} if a.pressure else {}
+    if a.pressure:
+        form_name += ", mean-pressure projection every step"
+    chosen = Form(cfg, mesh, stream, precision=prec, case_id=rank, cg_precision=a.cg_precision, sur=sur, **extra)
     n = chosen.g.num_particles
     r = chosen.timed(dt, a.steps, a.warmup, dist, Clocks(gpu_index(local)))
     ms = reduce_max(r["ms"], dist, "cuda")
