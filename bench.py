@@ -361,16 +361,19 @@ def prepare_surrogate(cfg, mesh, dt, seed=0, harvest_meshes=None, ratios=(0.5, 0
             m = dict(cfg["mesh"])
             m["W"], m["seed"] = W, 10 + i
             meshes.append(canyon_mesh(**m))
-    X, T, counts = surrogate.harvest(meshes, steps=100, every=5, per_element=cfg["per_element"],
+    # the harvest and the calibration span the length of a production run (the
+    # C2 recipe's 500 steps): the developed flow differs from the early
+    # transient, and a network that never saw it fails the check there
+    X, T, counts = surrogate.harvest(meshes, steps=500, every=10, per_element=cfg["per_element"],
                                      dt_of=lambda m: cfl_dt(m, cfl=cfg["cfl"], k0=cfg["k0"]), C0=cfg["C0"],
                                      seed=seed + 1000)
     t1 = time.perf_counter()
     params, norm, hist = surrogate.train(X, T, epochs=10, batch=4096, lr=2e-3, lr_final=1e-4, seed=seed)
     t2 = time.perf_counter()
-    res = surrogate.calibrate(params, norm, mesh, steps=100, every=5, per_element=cfg["per_element"], dt=dt,
+    res = surrogate.calibrate(params, norm, mesh, steps=500, every=10, per_element=cfg["per_element"], dt=dt,
                               seed=seed + 99, C0=cfg["C0"])
     tol = 1.5 * max(r[0] for r in res)
-    info = {"samples": int(X.shape[0]), "aspect_ratios": [round(float(m["W"]), 3) for m in meshes],
+    info = {"samples": int(X.shape[0]), "harvest_and_calibration_steps": 500, "aspect_ratios": [round(float(m["W"]), 3) for m in meshes],
             "harvest_triangles": [int(m["tri"].shape[0]) for m in meshes], "epochs": 10,
             "final_loss_standardised": hist[-1][1], "harvest_s": t1 - t0, "train_s": t2 - t1,
             "calibration_coarse_residual_max": max(r[0] for r in res), "residual_tol": tol,
@@ -604,7 +607,10 @@ def main():
         chosen.g.set_surrogate(sur["mode"], sur["params"], sur["norm"], sur["tol"])
 
     # end to end through the C ABI with host buffers: load the ensemble from
-    # pinned host memory, then per step advance and read the element statistics
+    # pinned host memory, then per step advance and copy that step's element
+    # statistics into its own pinned host buffer (asynchronous copies on the
+    # context stream, so the host keeps queueing steps); one sync at the end,
+    # after which the host checks every step's result
     e2e = None
     if not a.no_e2e:
         g = chosen.g
@@ -616,22 +622,23 @@ def main():
             t.numpy()[...] = v.view(np.int32) if v.dtype == np.uint32 else v
             pin[k] = t
         host = {k: (pin[k].numpy().view(np.uint32) if k == "id" else pin[k].numpy()) for k in pin}
-        out = torch.empty((g.nt, 5), dtype=torch.float64, pin_memory=True)
+        out = torch.empty((a.steps, g.nt, 5), dtype=torch.float64, pin_memory=True)
         h2d = sum(v.nbytes for v in host.values())
-        d2h = out.numel() * 8
+        d2h = g.nt * 5 * 8
         if dist:
             dist.barrier()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         g.set_particles(host, step=g.step_index)
         g.estimate_stats()
-        for _ in range(a.steps):
+        for k in range(a.steps):
             g.step(dt, 1)
-            g.field_into("elem_mean", out.data_ptr(), out.numel() * 8, device=False)
+            g.field_into("elem_mean", out[k].data_ptr(), d2h, device=False, asynchronous=True)
         g.sync(check=False)
         te = reduce_max(time.perf_counter() - t0, dist, "cuda")
+        results_finite = bool(np.isfinite(out.numpy()).all())
         e2e = {"value": whole_job_value(world, n, a.steps, te), "unit": UNIT, "h2d_bytes_per_step": h2d / a.steps,
-               "d2h_bytes_per_step": d2h}
+               "d2h_bytes_per_step": d2h, "results_finite": results_finite}
     chosen_stats = cell_stats(chosen.g, mesh) if rank == 0 else None
     chosen_step = chosen.g.step_index
     chosen.close()
@@ -656,7 +663,7 @@ def main():
                 "pressure_iterations_last": rr["pressure_iterations_last"],
                 "kernels_ms_per_step": {q: v[0] / k for q, v in rr["kt"].items()}}
             f.close()
-        stated["precision_study"] = precision_study(cfg, mesh, dt, stream, sur, steps=50)
+        stated["precision_study"] = precision_study(cfg, mesh, dt, stream, sur, steps=200)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": ms / a.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32" if prec != "fp64" else "f64",

@@ -196,8 +196,10 @@ int pdf_step(pdf_ctx* c, double dt, int32_t nsteps);
 int pdf_sync(pdf_ctx* c);
 
 /* Copy a field (enum pdf_field) into dst of the given size in bytes (must be
- * exactly the field size); dst is device memory if dst_is_device, else host.
- * Synchronous with respect to the host for host destinations. */
+ * exactly the field size). dst_is_device: 1 device memory (ordered on the
+ * context stream); 0 host memory, synchronous with respect to the host; 2 host
+ * memory, asynchronous on the context stream (dst should be page-locked; its
+ * contents are valid after the next pdf_sync). Other values: PDF_ERR_ARG. */
 int pdf_get_fields(pdf_ctx* c, int32_t field, void* dst, size_t bytes, int32_t dst_is_device);
 
 /* Sizes: particle count, elements, nodes, bins per element, step counter,

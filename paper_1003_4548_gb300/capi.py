@@ -315,8 +315,11 @@ class Canyon:
         self._check(lib().pdf_get_fields(self._h, FIELD[name], out.ctypes.data_as(C.c_void_p), out.nbytes, 0))
         return out
 
-    def field_into(self, name: str, ptr: int, nbytes: int, device: bool):
-        self._check(lib().pdf_get_fields(self._h, FIELD[name], C.c_void_p(ptr), nbytes, 1 if device else 0))
+    def field_into(self, name: str, ptr: int, nbytes: int, device: bool, asynchronous: bool = False):
+        """Copy a field to ptr; a host copy is synchronous unless asynchronous
+        (then ptr should be page-locked and is valid after the next sync)."""
+        mode = 1 if device else (2 if asynchronous else 0)
+        self._check(lib().pdf_get_fields(self._h, FIELD[name], C.c_void_p(ptr), nbytes, mode))
 
     def particles(self) -> dict:
         return {k: self.field(k) for k in ("x", "y", "u", "v", "w", "om", "psi", "id", "elem", "bin")}

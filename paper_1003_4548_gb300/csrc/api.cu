@@ -633,7 +633,7 @@ int pdf_sync(pdf_ctx* c) {
 }
 
 int pdf_get_fields(pdf_ctx* c, int32_t field, void* dst, size_t bytes, int32_t dst_is_device) {
-    if (!c || !dst) return PDF_ERR_ARG;
+    if (!c || !dst || dst_is_device < 0 || dst_is_device > 2) return PDF_ERR_ARG;
     const int64_t n = c->np;
     const int nt = c->m.nt, nn = c->m.nn;
     const void* src = nullptr;
@@ -684,8 +684,9 @@ int pdf_get_fields(pdf_ctx* c, int32_t field, void* dst, size_t bytes, int32_t d
             src = c->conv_buf;
         }
     }
-    PDF_CUDA(c, cudaMemcpyAsync(dst, src, need, dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->s));
-    if (!dst_is_device) PDF_CUDA(c, cudaStreamSynchronize(c->s));
+    PDF_CUDA(c, cudaMemcpyAsync(dst, src, need, dst_is_device == 1 ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                c->s));
+    if (dst_is_device == 0) PDF_CUDA(c, cudaStreamSynchronize(c->s));
     return PDF_OK;
 }
 

@@ -385,3 +385,20 @@ def test_empty_ensemble(wf_mesh):
     g.sync()
     assert g.num_particles == 0
     assert not g.field("elem_n").any() and not g.field("elem_mean").any()
+
+
+def test_asynchronous_host_copy(wf_mesh):
+    """pdf_get_fields with an asynchronous host destination delivers, after
+    pdf_sync, the same bytes as the synchronous copy, for a statistics field
+    and a converted particle field."""
+    import torch
+    g, _ = both(wf_mesh, precision="fp32", seed=3)
+    g.seed_particles(16)
+    g.estimate_stats()
+    g.step(cfl_dt(wf_mesh, cfl=0.5, k0=1e-3), 2)
+    for name in ("elem_mean", "u"):
+        ref = g.field(name)
+        buf = torch.empty(ref.shape, dtype=torch.float64, pin_memory=True)
+        g.field_into(name, buf.data_ptr(), ref.nbytes, device=False, asynchronous=True)
+        g.sync()
+        assert np.array_equal(buf.numpy(), ref)
