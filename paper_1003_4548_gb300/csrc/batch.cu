@@ -8,9 +8,12 @@
 // particle state between two buffers and swaps them on the host: a captured
 // pair of steps starts and ends in the same buffers. The step counter of every context lives
 // on the device (advanced by the re-sort), so replays draw new Philox streams.
-// Cooperative CG grids are chained with events (one resident at a time): two
-// partially resident cooperative grids waiting at their grid barriers could
-// otherwise starve each other.
+// Cooperative CG grids are chained with an event (one resident at a time):
+// two partially resident cooperative grids waiting at their grid barriers
+// could otherwise starve each other. The capture goes step by step over the
+// contexts (every context's first step, then every context's second), so the
+// chain runs through all first-step solves before any second-step one and a
+// context never waits for another context's later step.
 #include <algorithm>
 #include <vector>
 
@@ -76,7 +79,7 @@ int pdf_batch_create(pdf_ctx* const* ctx, const double* dt, int32_t n, void* cud
             return cuda_fail("cudaEventCreateWithFlags", err);
         }
     }
-    cudaEvent_t fork = b->ev[0];
+    cudaEvent_t fork = b->ev[0], chain = b->ev[1 + n];
     cudaError_t err = cudaStreamBeginCapture(b->s, cudaStreamCaptureModeRelaxed);
     if (err != cudaSuccess) {
         release(b);
@@ -84,24 +87,29 @@ int pdf_batch_create(pdf_ctx* const* ctx, const double* dt, int32_t n, void* cud
     }
     int st = PDF_OK;
     err = cudaEventRecord(fork, b->s);
+    for (int i = 0; i < n && err == cudaSuccess; ++i) err = cudaStreamWaitEvent(ctx[i]->s, fork, 0);
+    bool chained = false;  // a cooperative solve has been captured (the chain event holds it)
+    for (int k = 0; k < 2 && st == PDF_OK && err == cudaSuccess; ++k) {
+        for (int i = 0; i < n && st == PDF_OK && err == cudaSuccess; ++i) {
+            pdf_ctx* c = ctx[i];
+            const int timing = c->timing;
+            c->timing = 0;
+            const int64_t l0 = c->launches;
+            c->coop_wait = chained ? chain : nullptr;
+            c->coop_done = chain;
+            st = pdf_step(c, dt[i], 1);
+            if (c->launches > l0 && (c->p.wall_model == PDF_ELLIPTIC_RELAXATION || c->p.pressure)) chained = true;
+            b->launches[i] += c->launches - l0;
+            c->launches = l0;
+            c->coop_wait = c->coop_done = nullptr;
+            c->timing = timing;
+            if (st == PDF_OK) c->step -= 1;  // captured, not executed
+            else st = fail(nullptr, st, "pdf_batch_create: step of context " + std::to_string(i) + ": " + c->err);
+        }
+    }
     for (int i = 0; i < n && st == PDF_OK && err == cudaSuccess; ++i) {
-        pdf_ctx* c = ctx[i];
-        err = cudaStreamWaitEvent(c->s, fork, 0);
-        if (err != cudaSuccess) break;
-        const int timing = c->timing;
-        c->timing = 0;
-        c->coop_wait = i ? b->ev[1 + n + i - 1] : nullptr;
-        c->coop_done = b->ev[1 + n + i];
-        const int64_t l0 = c->launches;
-        st = pdf_step(c, dt[i], 2);
-        b->launches[i] = c->launches - l0;
-        c->launches = l0;
-        c->coop_wait = c->coop_done = nullptr;
-        c->timing = timing;
-        if (st == PDF_OK) c->step -= 2;  // captured, not executed
-        else st = fail(nullptr, st, "pdf_batch_create: step of context " + std::to_string(i) + ": " + c->err);
-        if (st == PDF_OK) err = cudaEventRecord(b->ev[1 + i], c->s);
-        if (st == PDF_OK && err == cudaSuccess) err = cudaStreamWaitEvent(b->s, b->ev[1 + i], 0);
+        err = cudaEventRecord(b->ev[1 + i], ctx[i]->s);
+        if (err == cudaSuccess) err = cudaStreamWaitEvent(b->s, b->ev[1 + i], 0);
     }
     const cudaError_t end = cudaStreamEndCapture(b->s, &b->graph);
     if (st != PDF_OK || err != cudaSuccess || end != cudaSuccess) {
