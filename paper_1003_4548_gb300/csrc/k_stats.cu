@@ -515,7 +515,7 @@ __global__ void __launch_bounds__(32 * WARPS_PER_BLOCK) k_moments_warp(const Mom
 // block class ranks up to 64 keys of a crowded bucket before bisecting)
 template <int NMAX>
 struct SelCfg {
-    static constexpr int NB = 256;
+    static constexpr int NB = 256;  // at most 256: a key's bucket is kept in one byte
     static constexpr int CMAX = NMAX <= 512 ? 32 : 64;
 };
 
@@ -523,9 +523,11 @@ template <int NMAX>
 struct SelSmem {
     uint32_t kv[NMAX];  // order-preserving value bits of the current level
     unsigned char grp[NMAX];
+    unsigned char bk8[NMAX];  // histogram bucket of each key at the current level (NB <= 256)
     unsigned hist[4][SelCfg<NMAX>::NB / 2];  // per-group histogram, two 16-bit counts per word
     uint32_t cv[4][SelCfg<NMAX>::CMAX], cid[4][SelCfg<NMAX>::CMAX];  // keys of each group's boundary bucket
     int nc[4], bkt[4], brank[4];
+    int cbk[4];                // boundary bucket whose keys are ranked, or -1 (crowded: bisection)
     uint32_t bv[4], bid[4];    // boundary keys of the level's groups
     int ired[8];               // team reduction scratch
     unsigned ured[2][NMAX > 512 ? 8 : 1];
@@ -699,14 +701,14 @@ __device__ __noinline__ void sel_boundaries(SelSmem<NMAX>& S, const uint32_t* __
                 S.bkt[g] = bucket;
                 S.brank[g] = Tk - below - 1;
                 S.nc[g] = 0;
+                S.cbk[g] = hcount(S, g, bucket) <= CMAX ? bucket : -1;
             }
         }
     }
     T.sync();
     for (int q = T.tid; q < n; q += NT) {  // candidates of all groups in one pass
         const int g = S.grp[q];
-        const int b = S.bkt[g];
-        if (hcount(S, g, b) <= CMAX && bk(S.kv[q]) == b) {
+        if ((int)S.bk8[q] == S.cbk[g]) {
             const int slot = atomicAdd(&S.nc[g], 1);
             S.cv[g][slot] = S.kv[q];
             S.cid[g][slot] = ids[q];
@@ -841,12 +843,28 @@ __device__ __noinline__ void kahan_moments(const MomArgs<float>& a, int e, int s
         // 16 compensated sums (12 used): 0..4 the shifted u v w psi and omega,
         // 5..10 the products uu vv ww uv uw vw, 11 psi psi
         AccK acc[16];
-        for (int q = lane; q < n; q += 32) {
-            const float du = a.u[s0 + q] - su, dv = a.v[s0 + q] - sv, dw = a.w[s0 + q] - sw;
-            const float dp = a.psi[s0 + q] - sp;
-            acc[0].add(du); acc[1].add(dv); acc[2].add(dw); acc[3].add(dp); acc[4].add(a.om[s0 + q]);
-            acc[5].add(du * du); acc[6].add(dv * dv); acc[7].add(dw * dw);
-            acc[8].add(du * dv); acc[9].add(du * dw); acc[10].add(dv * dw); acc[11].add(dp * dp);
+        // two particles per lane at a time: their ten loads are issued
+        // together, then added in particle order
+        for (int q0 = lane; q0 < n; q0 += 64) {
+            float x[2][5];
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+                const int q = q0 + 32 * r;
+                const bool in = q < n;
+                x[r][0] = in ? a.u[s0 + q] : su;
+                x[r][1] = in ? a.v[s0 + q] : sv;
+                x[r][2] = in ? a.w[s0 + q] : sw;
+                x[r][3] = in ? a.psi[s0 + q] : sp;
+                x[r][4] = in ? a.om[s0 + q] : 0.f;
+            }
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+                if (q0 + 32 * r >= n) break;
+                const float du = x[r][0] - su, dv = x[r][1] - sv, dw = x[r][2] - sw, dp = x[r][3] - sp;
+                acc[0].add(du); acc[1].add(dv); acc[2].add(dw); acc[3].add(dp); acc[4].add(x[r][4]);
+                acc[5].add(du * du); acc[6].add(dv * dv); acc[7].add(dw * dw);
+                acc[8].add(du * dv); acc[9].add(du * dw); acc[10].add(dv * dw); acc[11].add(dp * dp);
+            }
         }
         // butterfly reduce-scatter over the warp: after the xor-16, 8, 4, 2
         // exchanges (each lane merging the half it keeps with the partner's)
@@ -949,18 +967,32 @@ __device__ void sel_element(const MomArgs<float>& a, int e, int s0, int n, SelSm
         const int ngl = ng == 0 ? 1 : 2 * ng;  // groups of this level
         for (int q = T.tid; q < ngl * (SelCfg<NMAX>::NB / 2); q += NT) (&S.hist[0][0])[q] = 0u;
         T.sync();
-        for (int q = T.tid; q < n; q += NT) {
-            int g = 0;
-            if (ng) {
-                const int gp = S.grp[q];
-                const uint32_t v = S.kv[q], bv = S.bv[gp];
-                g = 2 * gp + ((v < bv || (v == bv && ids[q] <= S.bid[gp])) ? 0 : 1);
+        // four keys per thread at a time: their component loads are issued
+        // together (they come from L2), then the keys are assigned
+        for (int q0 = T.tid; q0 < n; q0 += 4 * NT) {
+            float c4[4];
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                const int q = q0 + r * NT;
+                c4[r] = q < n ? comp[s0 + q] : 0.f;
             }
-            S.grp[q] = (unsigned char)g;
-            const uint32_t k = ord32(comp[s0 + q]);
-            S.kv[q] = k;
-            const int b = bk(k);
-            atomicAdd(&S.hist[g][b >> 1], 1u << (16 * (b & 1)));
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                const int q = q0 + r * NT;
+                if (q >= n) break;
+                int g = 0;
+                if (ng) {
+                    const int gp = S.grp[q];
+                    const uint32_t v = S.kv[q], bv = S.bv[gp];
+                    g = 2 * gp + ((v < bv || (v == bv && ids[q] <= S.bid[gp])) ? 0 : 1);
+                }
+                S.grp[q] = (unsigned char)g;
+                const uint32_t k = ord32(c4[r]);
+                S.kv[q] = k;
+                const int b = bk(k);
+                S.bk8[q] = (unsigned char)b;
+                atomicAdd(&S.hist[g][b >> 1], 1u << (16 * (b & 1)));
+            }
         }
         if (ng) {  // sizes of the new groups: the lower half takes the extra key
             int ns[4] = {0, 0, 0, 0};
@@ -978,7 +1010,17 @@ __device__ void sel_element(const MomArgs<float>& a, int e, int s0, int n, SelSm
     constexpr int UNIT = NMAX <= 512 ? 54 : 51;  // psi <= 1 and n <= NMAX keep the sums below 2^63
     if (T.tid < 8) { S.binsum[T.tid] = 0ull; S.bincnt[T.tid] = 0; }
     T.sync();
-    for (int q = T.tid; q < n; q += NT) {
+    for (int q0 = T.tid; q0 < n; q0 += 4 * NT) {
+      float p4[4];  // the psi loads of four keys issued together
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const int q = q0 + r * NT;
+        p4[r] = q < n ? a.psi[s0 + q] : 0.f;
+      }
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const int q = q0 + r * NT;
+        if (q >= n) break;
         int bn = 0;
         if (ng) {
             const int gp = S.grp[q];
@@ -989,12 +1031,13 @@ __device__ void sel_element(const MomArgs<float>& a, int e, int s0, int n, SelSm
         unsigned m;
         int ex;
         bool negp;
-        f32_parts(fminf(fmaxf(a.psi[s0 + q], 0.f), 1.f), m, ex, negp);
+        f32_parts(fminf(fmaxf(p4[r], 0.f), 1.f), m, ex, negp);
         const int sh = ex - 150 + UNIT;  // m 2^(ex-150) = m 2^(ex-150+UNIT) 2^-UNIT
         const unsigned long long v = sh >= 0 ? ((unsigned long long)m << sh)
                                              : (-sh < 64 ? ((unsigned long long)m >> (-sh)) : 0ull);
         atomicAdd(&S.binsum[bn], v);
         atomicAdd(&S.bincnt[bn], 1);
+      }
     }
     T.sync();
     for (int b = T.tid; b < B; b += NT) {
