@@ -764,6 +764,9 @@ void pdf_destroy(pdf_ctx* c) {
         cudaFree(c->stB[k]);
     }
     cudaFreeHost(c->h_status);
+    if (c->side_fork) cudaEventDestroy(c->side_fork);
+    if (c->side_join) cudaEventDestroy(c->side_join);
+    if (c->s2) cudaStreamDestroy(c->s2);
     delete c;
 }
 

@@ -1068,18 +1068,23 @@ __global__ void __launch_bounds__(32 * WARPS_PER_BLOCK, KAHAN ? 8 : 4) k_moments
     const int e = blockIdx.x * WARPS_PER_BLOCK + w;
     if (e >= nt) return;
     const int s0 = a.off[e], n = a.off[e + 1] - s0;
-    if (n > 512) {  // a block kernel takes it
-        if (lane == 0) {
-            if (n <= 4096) a.listA[atomicAdd(&a.lcnt[0], 1)] = e;
-            else a.listB[atomicAdd(&a.lcnt[1], 1)] = e;
-        }
-        return;
-    }
+    if (n > 512) return;  // a block kernel takes it (listed by k_crowded)
     if (n == 0) {
         empty_element(a, e, lane, 32);
         return;
     }
     sel_element<KAHAN, 32, 512>(a, e, s0, n, sm[w]);
+}
+
+// the crowded elements from the element offsets: 512 < n <= 4096 into listA,
+// n > 4096 into listB (list order is free: every element is reduced by one
+// team in a fixed order)
+__global__ void k_crowded(const int* __restrict__ off, int nt, int* lcnt, int* listA, int* listB) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= nt) return;
+    const int n = off[e + 1] - off[e];
+    if (n > 4096) listB[atomicAdd(&lcnt[1], 1)] = e;
+    else if (n > 512) listA[atomicAdd(&lcnt[0], 1)] = e;
 }
 
 // block of 256 threads per element: 512 < n <= 4096 (crowded elements)
@@ -1121,14 +1126,27 @@ int run(pdf_ctx* c) {
         if (medians) {
             // crowded elements (particle density drifts during a run) get their
             // own size class with a larger shared-memory slice per warp
+            // the warp kernel runs on the high-priority side stream; the block
+            // kernels of the crowded elements (particle counts spread during a
+            // run) run concurrently on the context stream and fill the SMs the
+            // warp kernel's last waves leave
             a.min_n = 4096;
             a.lcnt = c->elist;
             a.listA = c->elist + 2;
             a.listB = c->elist + 2 + c->m.nt;
+            PDF_CUDA(c, cudaEventRecord(c->side_fork, c->s));
+            PDF_CUDA(c, cudaStreamWaitEvent(c->s2, c->side_fork, 0));
+            k_moments_sel<KAHAN><<<blocks, 32 * WARPS_PER_BLOCK, 0, c->s2>>>(a, c->m.nt);
+            PDF_CUDA(c, cudaEventRecord(c->side_join, c->s2));
             PDF_CUDA(c, cudaMemsetAsync(a.lcnt, 0, 2 * sizeof(int), c->s));
-            k_moments_sel<KAHAN><<<blocks, 32 * WARPS_PER_BLOCK, 0, c->s>>>(a, c->m.nt);
+            k_crowded<<<(c->m.nt + 255) / 256, 256, 0, c->s>>>(c->off, c->m.nt, a.lcnt, a.listA, a.listB);
             k_moments_sel_big<KAHAN><<<std::min(c->m.nt, 2 * c->num_sms), 256, 0, c->s>>>(a);
-            c->launches += 2;
+            const size_t smem = sizeof(SortKey) * STATS_CAP;
+            k_moments<T, KAHAN><<<(unsigned)std::min(c->m.nt, c->num_sms), STATS_THREADS, smem, c->s>>>(a);
+            PDF_CUDA(c, cudaStreamWaitEvent(c->s, c->side_join, 0));
+            c->launches += 4;
+            PDF_CUDA(c, cudaGetLastError());
+            return PDF_OK;
         } else {
             k_moments_warp<KAHAN><<<blocks, 32 * WARPS_PER_BLOCK, 0, c->s>>>(a, c->m.nt);
             ++c->launches;
@@ -1145,6 +1163,13 @@ int run(pdf_ctx* c) {
 }  // namespace
 
 int prepare_moments(pdf_ctx* c) {
+    if (!c->s2) {
+        int lo = 0, hi = 0;
+        PDF_CUDA(c, cudaDeviceGetStreamPriorityRange(&lo, &hi));
+        PDF_CUDA(c, cudaStreamCreateWithPriority(&c->s2, cudaStreamNonBlocking, hi));
+        PDF_CUDA(c, cudaEventCreateWithFlags(&c->side_fork, cudaEventDisableTiming));
+        PDF_CUDA(c, cudaEventCreateWithFlags(&c->side_join, cudaEventDisableTiming));
+    }
     const int smem = (int)(sizeof(SortKey) * STATS_CAP);
     PDF_CUDA(c, cudaFuncSetAttribute(k_moments<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     PDF_CUDA(c, cudaFuncSetAttribute(k_moments<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));

@@ -165,6 +165,10 @@ struct pdf_ctx {
     int step_sur_blocks = 0;  // persistent grid of the per-particle surrogate form
     int scatter_threads = 256;  // block size of the re-sort scatter
     cudaEvent_t coop_wait = nullptr, coop_done = nullptr;  // batch: chain of the cooperative CG launches
+    // side stream of the crowded-element moments, forked from and joined back
+    // into the context stream inside each step
+    cudaStream_t s2 = nullptr;
+    cudaEvent_t side_fork = nullptr, side_join = nullptr;
     std::string err;
     int num_sms = 0;
 };
