@@ -268,16 +268,19 @@ def roofline(kclass, kt, n, ts, workload, precision):
 
 
 def cell_stats(g, mesh, nx=12, ny=8):
-    """Particle-weighted <U>, <V>, k and <psi> over an nx x ny grid of cells
-    (element means grouped by centroid) for comparing runs."""
+    """Particle-weighted <U>, <V>, the Reynolds stresses <uu>, <vv>, <ww>,
+    <uv>, k, <psi> and the psi variance over an nx x ny grid of cells (element
+    means grouped by centroid) for comparing runs."""
     import numpy as np
     cent = mesh["xy"][mesh["tri"]].mean(1)
     cell = (np.clip((cent[:, 0] / mesh["L"] * nx).astype(int), 0, nx - 1) * ny +
             np.clip((cent[:, 1] / mesh["T"] * ny).astype(int), 0, ny - 1))
     n = g.field("elem_n").astype(float)
-    M, R = g.field("elem_mean"), g.field("elem_R")
+    M, R, pv = g.field("elem_mean"), g.field("elem_R"), g.field("elem_psivar")
     out = {}
-    for name, q in (("U", M[:, 0]), ("V", M[:, 1]), ("k", 0.5 * (R[:, 0] + R[:, 1] + R[:, 2])), ("psi", M[:, 3])):
+    for name, q in (("U", M[:, 0]), ("V", M[:, 1]), ("uu", R[:, 0]), ("vv", R[:, 1]), ("ww", R[:, 2]),
+                    ("uv", R[:, 3]), ("k", 0.5 * (R[:, 0] + R[:, 1] + R[:, 2])), ("psi", M[:, 3]),
+                    ("psi_var", pv)):
         w = np.bincount(cell, weights=n, minlength=nx * ny)
         out[name] = np.bincount(cell, weights=n * q, minlength=nx * ny) / np.maximum(w, 1.0)
     return out
@@ -639,8 +642,6 @@ def main():
         results_finite = bool(np.isfinite(out.numpy()).all())
         e2e = {"value": whole_job_value(world, n, a.steps, te), "unit": UNIT, "h2d_bytes_per_step": h2d / a.steps,
                "d2h_bytes_per_step": d2h, "results_finite": results_finite}
-    chosen_stats = cell_stats(chosen.g, mesh) if rank == 0 else None
-    chosen_step = chosen.g.step_index
     chosen.close()
 
     # the plain forms on the same workload (fewer steps), and the stated error
