@@ -42,9 +42,14 @@ def args_():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-surrogate", action="store_true", help="FE solve every step in the timed form")
+    ap.add_argument("--chosen", default="lagged", choices=["lagged", "surrogate"],
+                    help="wp of the timed form: lagged FE under the coarse residual check, or the trained network")
+    ap.add_argument("--lag-tol", type=float, default=0.05,
+                    help="coarse residual above which the lagged form solves the FE problem again")
     ap.add_argument("--no-forms", action="store_true", help="skip the plain forms and the precision study")
     ap.add_argument("--save-surrogate", default=None, help="write the trained network (npz) here")
     ap.add_argument("--load-surrogate", default=None, help="use this trained network (npz) instead of training")
+    ap.add_argument("--sur-epochs", type=int, default=10, help="training epochs of the surrogate")
     ap.add_argument("--pressure", action="store_true",
                     help="add the mean-pressure projection to the timed form (not the published configuration)")
     ap.add_argument("--surrogate-mode", type=int, default=1, choices=[1, 3],
@@ -348,7 +353,7 @@ class Form:
         self.g.close()
 
 
-def prepare_surrogate(cfg, mesh, dt, seed=0, harvest_meshes=None, ratios=(0.5, 0.75, 1.0, 1.5, 2.0)):
+def prepare_surrogate(cfg, mesh, dt, seed=0, harvest_meshes=None, ratios=(0.5, 0.75, 1.0, 1.5, 2.0), epochs=10):
     """Harvest FE runs at W/H = 0.5 .. 2 (this workload's mesh recipe, or the
     given meshes), train the network with the library's kernels, and
     calibrate the check on a held-out run of this workload: threshold = 1.5 x
@@ -371,13 +376,13 @@ def prepare_surrogate(cfg, mesh, dt, seed=0, harvest_meshes=None, ratios=(0.5, 0
                                      dt_of=lambda m: cfl_dt(m, cfl=cfg["cfl"], k0=cfg["k0"]), C0=cfg["C0"],
                                      seed=seed + 1000)
     t1 = time.perf_counter()
-    params, norm, hist = surrogate.train(X, T, epochs=10, batch=4096, lr=2e-3, lr_final=1e-4, seed=seed)
+    params, norm, hist = surrogate.train(X, T, epochs=epochs, batch=4096, lr=2e-3, lr_final=1e-4, seed=seed)
     t2 = time.perf_counter()
     res = surrogate.calibrate(params, norm, mesh, steps=500, every=10, per_element=cfg["per_element"], dt=dt,
                               seed=seed + 99, C0=cfg["C0"])
     tol = 1.5 * max(r[0] for r in res)
     info = {"samples": int(X.shape[0]), "harvest_and_calibration_steps": 500, "aspect_ratios": [round(float(m["W"]), 3) for m in meshes],
-            "harvest_triangles": [int(m["tri"].shape[0]) for m in meshes], "epochs": 10,
+            "harvest_triangles": [int(m["tri"].shape[0]) for m in meshes], "epochs": epochs,
             "final_loss_standardised": hist[-1][1], "harvest_s": t1 - t0, "train_s": t2 - t1,
             "calibration_coarse_residual_max": max(r[0] for r in res), "residual_tol": tol,
             "check": "coarse FE residual (aggregates of 128 Morton-ordered nodes) <= residual_tol"}
@@ -417,15 +422,18 @@ def run_batch(a, cfg):
     prec = a.precision or cfg["chosen_precision"]
     cases = batch_cases(cfg)
     meshes = [canyon_mesh(**c["mesh"]) for c in cases]
-    # the surrogate: trained on held-out cases of the same family (another draw
-    # of the batch recipe: W/H 0.5 .. 3, spacing 0.017 .. 0.1), calibrated on
-    # the wall-resolved W/H = 1 canyon
-    ref = dict(WORKLOADS["canyon_er_full"])
-    ref["name"] = "canyon_er_full"
-    ref_mesh = build_mesh(ref)
-    held = batch_cases(dict(cfg, seed=cfg["seed"] + 1))[:8]
-    sur, sur_info = prepare_surrogate(ref, ref_mesh, cfl_dt(ref_mesh, cfl=ref["cfl"], k0=ref["k0"]),
-                                      harvest_meshes=[canyon_mesh(**c["mesh"]) for c in held])
+    # wp: the lagged FE solve under the coarse check (the chosen form), or the
+    # network trained on held-out cases of the same family (another draw of
+    # the batch recipe: W/H 0.5 .. 3, spacing 0.017 .. 0.1), calibrated on the
+    # wall-resolved W/H = 1 canyon
+    sur, sur_info = None, {"form": "lagged FE", "residual_tol": a.lag_tol}
+    if a.chosen == "surrogate":
+        ref = dict(WORKLOADS["canyon_er_full"])
+        ref["name"] = "canyon_er_full"
+        ref_mesh = build_mesh(ref)
+        held = batch_cases(dict(cfg, seed=cfg["seed"] + 1))[:8]
+        sur, sur_info = prepare_surrogate(ref, ref_mesh, cfl_dt(ref_mesh, cfl=ref["cfl"], k0=ref["k0"]),
+                                          harvest_meshes=[canyon_mesh(**c["mesh"]) for c in held])
     # torch hands out pooled streams (32 per priority): the cases take the
     # low-priority pool, the batch stream comes from the high-priority one
     streams = [torch.cuda.Stream() for _ in cases]
@@ -440,15 +448,19 @@ def run_batch(a, cfg):
         g.seed_particles(c["per_element"])
         g.estimate_stats()
         dt = cfl_dt(m, cfl=cfg["cfl"], k0=cfg["k0"])
-        # the check's threshold per case: 1.5 x the largest coarse residual of
-        # the network's wp over this case's first steps (the warm-up)
-        g.set_surrogate(2, sur["params"], sur["norm"], 0.0)
-        res = []
-        for _ in range(3):
-            g.step(dt, 2)
-            res.append(g.surrogate_stats()[2][0])
-        tols.append(1.5 * max(res))
-        g.set_surrogate(1, sur["params"], sur["norm"], tols[-1])
+        if sur is not None:
+            # the check's threshold per case: 1.5 x the largest coarse residual
+            # of the network's wp over this case's first steps (the warm-up)
+            g.set_surrogate(2, sur["params"], sur["norm"], 0.0)
+            res = []
+            for _ in range(3):
+                g.step(dt, 2)
+                res.append(g.surrogate_stats()[2][0])
+            tols.append(1.5 * max(res))
+            g.set_surrogate(1, sur["params"], sur["norm"], tols[-1])
+        else:
+            tols.append(a.lag_tol)
+            g.set_surrogate(5, None, None, a.lag_tol)
         tunings.append(g.autotune(dt, 2))
         ctxs.append(g)
         dts.append(dt)
@@ -515,7 +527,8 @@ def run_batch(a, cfg):
                                                max(c["per_element"] for c in cases)],
                        "W_over_H_min_max": [round(min(c["mesh"]["W"] for c in cases), 3),
                                             round(max(c["mesh"]["W"] for c in cases), 3)],
-                       "precision": prec, "form": "one CUDA graph per step pair over all cases; chosen form",
+                       "precision": prec, "form": "one CUDA graph per step pair over all cases; chosen form (" +
+                       ("trained network" if sur is not None else "lagged FE") + " wp under the coarse check)",
                        "l2": "inputs larger than L2"},
             "roofline": {"bound": "hbm", "kernel": "whole step, all cases (69 B per particle-step algorithmic)",
                          "achieved": 69 * n_total * steps / (ms / 1e3) / 1e9, "peak": measured_peaks()[0],
@@ -526,10 +539,11 @@ def run_batch(a, cfg):
             "autotuned": {"step_blocks_per_sm": sorted({t["step_blocks_per_sm"] for t in tunings}),
                           "scatter_threads": sorted({t["scatter_threads"] for t in tunings}),
                           "cg_rows_per_block": sorted({t["cg_rows_per_block"] for t in tunings})},
-            "surrogate": dict(sur_info, solves=solves, fallbacks=falls,
-                              residual_tol_per_case_min_max=[min(tols), max(tols)],
-                              check_calibration="per case: 1.5 x the largest coarse residual over its first "
-                                                "6 steps (warm-up)"), "setup_s": t_setup,
+            "wp": dict(sur_info, checked_steps=solves, fe_solves=falls,
+                       residual_tol_per_case_min_max=[min(tols), max(tols)],
+                       check_calibration=("per case: 1.5 x the largest coarse residual over its first 6 steps "
+                                          "(warm-up)") if sur is not None else "the same tolerance for every case"),
+            "setup_s": t_setup,
             "e2e": None}
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -572,27 +586,37 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl")
     stream = torch.cuda.current_stream()
-    use_sur = cfg["wall_model"] == "er" and not a.no_surrogate
+    # wp of the timed form: the lagged FE solve (the previous solution kept
+    # while its coarse FE residual under the current statistics stays below
+    # --lag-tol) or the trained network under the same check. The network is
+    # trained whenever it is timed or measured beside the chosen form.
+    er = cfg["wall_model"] == "er" and not a.no_surrogate
+    use_net = er and (a.chosen == "surrogate" or not a.no_forms)
     sur, sur_info = None, None
-    if use_sur and a.load_surrogate:
+    if use_net and a.load_surrogate:
         z = np.load(a.load_surrogate)
         sur = {"params": z["params"], "norm": z["norm"], "tol": float(z["tol"])}
         sur_info = {"loaded_from": os.path.basename(a.load_surrogate), "residual_tol": sur["tol"]}
-    elif use_sur:
-        sur, sur_info = prepare_surrogate(cfg, mesh, dt)
+    elif use_net:
+        sur, sur_info = prepare_surrogate(cfg, mesh, dt, epochs=a.sur_epochs)
     if sur is not None:
         sur["mode"] = a.surrogate_mode
     if sur is not None and a.save_surrogate:
         np.savez(a.save_surrogate, params=sur["params"], norm=sur["norm"], tol=sur["tol"])
+    lagged = {"mode": 5, "params": None, "norm": None, "tol": a.lag_tol}
+    chosen_wp = (sur if a.chosen == "surrogate" else lagged) if er else None
     prec = cfg["precision"]
     red = {"fp64": "FP64", "fp32": "FP64-exact", "fp32_kahan": "compensated FP32"}[prec]
-    form_name = (f"{prec} particle state, {red} statistics" +
-                 (", surrogate wp with the FE solve as checked fallback" if use_sur else ", FE solve every step"))
+    form_name = f"{prec} particle state, {red} statistics, " + (
+        "FE solve every step" if chosen_wp is None else
+        "surrogate wp with the FE solve as checked fallback" if chosen_wp is sur else
+        f"lagged FE solve: the previous wp kept while its coarse FE residual stays below {a.lag_tol}")
     # each rank runs its own canyon case (independent problems, no exchange)
     extra = {"pressure": 1} if a.pressure else {}
     if a.pressure:
         form_name += ", mean-pressure projection every step"
-    chosen = Form(cfg, mesh, stream, precision=prec, case_id=rank, cg_precision=a.cg_precision, sur=sur, **extra)
+    chosen = Form(cfg, mesh, stream, precision=prec, case_id=rank, cg_precision=a.cg_precision, sur=chosen_wp,
+                  **extra)
     n = chosen.g.num_particles
     r = chosen.timed(dt, a.steps, a.warmup, dist, Clocks(gpu_index(local)))
     ms = reduce_max(r["ms"], dist, "cuda")
@@ -604,7 +628,10 @@ def main():
     rooflines = {k: roofline(k, kt, n, ts, a.workload, prec) for k in ("particle", "moments", "sort")}
     kernels = {k: {"ms_per_step": v[0] / a.steps, "launches": v[1]} for k, v in kt.items()}
     stated = {}
-    if use_sur:
+    if chosen_wp is not None:
+        solves, falls, _ = chosen.g.surrogate_stats()
+        stated["wp_fe_solves_in_timed_steps"] = {"steps": int(solves), "fe_solves": int(falls)}
+    if chosen_wp is not None and chosen_wp is sur:
         chosen.last_wp = chosen.g.field("node_wp")
         stated["surrogate"] = surrogate_error(chosen, mesh)
         chosen.g.set_surrogate(sur["mode"], sur["params"], sur["norm"], sur["tol"])
@@ -644,6 +671,21 @@ def main():
                "d2h_bytes_per_step": d2h, "results_finite": results_finite}
     chosen.close()
 
+    # a whole production run of the chosen form from its seeded start (the C2
+    # recipe's 500 steps): the per-element counts spread and the flow leaves
+    # the early transient, so the rate and the surrogate's fallbacks over the
+    # full run are stated beside the 100-step window above
+    sustained = None
+    if not a.no_forms and rank == 0 and chosen_wp is not None:
+        f = Form(cfg, mesh, stream, precision=prec, sur=chosen_wp, **extra)
+        s0 = f.g.surrogate_stats()
+        rr = f.timed(dt, 500, 0)
+        s1 = f.g.surrogate_stats()
+        sustained = {"steps": 500, "value": f.g.num_particles * 500 / (rr["ms"] / 1e3), "ms_per_step": rr["ms"] / 500,
+                     "checked_steps": s1[0] - s0[0], "fe_solves": s1[1] - s0[1],
+                     "kernels_ms_per_step": {q: v[0] / 500 for q, v in rr["kt"].items()}}
+        f.close()
+
     # the plain forms on the same workload (fewer steps), and the stated error
     forms = {}
     if not a.no_forms and rank == 0:
@@ -655,8 +697,19 @@ def main():
                            "steps": k, "cg_iterations_last": rr["cg_iterations_last"],
                            "kernels_ms_per_step": {q: v[0] / k for q, v in rr["kt"].items()}}
             f.close()
-        if sur is not None:  # the chosen form with the mean-pressure projection added
-            f = Form(cfg, mesh, stream, precision=prec, sur=sur, pressure=1)
+        if sur is not None and chosen_wp is not sur:  # the trained network in place of the lagged solve
+            f = Form(cfg, mesh, stream, precision=prec, sur=sur)
+            s0 = f.g.surrogate_stats()
+            rr = f.timed(dt, k, 3)
+            s1 = f.g.surrogate_stats()
+            f.last_wp = f.g.field("node_wp")
+            forms["surrogate_node_form"] = {
+                "value": f.g.num_particles * k / (rr["ms"] / 1e3), "ms_per_step": rr["ms"] / k, "steps": k,
+                "fe_fallbacks": int(s1[1] - s0[1]), "wp_error_vs_fe": surrogate_error(f, mesh),
+                "kernels_ms_per_step": {q: v[0] / k for q, v in rr["kt"].items()}}
+            f.close()
+        if chosen_wp is not None:  # the chosen form with the mean-pressure projection added
+            f = Form(cfg, mesh, stream, precision=prec, sur=chosen_wp, pressure=1)
             rr = f.timed(dt, k, 3)
             forms["chosen_with_pressure_projection"] = {
                 "value": f.g.num_particles * k / (rr["ms"] / 1e3), "ms_per_step": rr["ms"] / k, "steps": k,
@@ -664,7 +717,7 @@ def main():
                 "pressure_iterations_last": rr["pressure_iterations_last"],
                 "kernels_ms_per_step": {q: v[0] / k for q, v in rr["kt"].items()}}
             f.close()
-        stated["precision_study"] = precision_study(cfg, mesh, dt, stream, sur, steps=200)
+        stated["precision_study"] = precision_study(cfg, mesh, dt, stream, sur, steps=200, lag_tol=a.lag_tol)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": ms / a.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32" if prec != "fp64" else "f64",
@@ -672,6 +725,8 @@ def main():
             "roofline": roof, "rooflines": rooflines, "e2e": e2e, "gpu_launches": int(r["launches"]),
             "clocks": r["clocks"], "kernels": kernels, "status": capi_status(r["status"]),
             "cg_iterations_last": r["cg_iterations_last"], "surrogate": sur_info}
+    if sustained:
+        line["sustained_production_run"] = sustained
     if forms:
         line["forms"] = forms
         line["speedup_vs_plain_fp64"] = value / forms["plain_fp64_fe"]["value"]
@@ -691,27 +746,34 @@ def capi_status(st):
     return capi.ERRORS.get(st, "ok") if st else "ok"
 
 
-def precision_study(cfg, mesh, dt, stream, sur, steps):
+def precision_study(cfg, mesh, dt, stream, sur, steps, lag_tol=0.05):
     """The same seeded ensemble advanced `steps` steps in each form; statistics
     on a 12 x 8 grid of cells compared with the all-FP64 form (relative rms),
     next to the Monte Carlo scale (the FP64 form with another seed)."""
+    lag = lambda tol: {"mode": 5, "params": None, "norm": None, "tol": tol}  # noqa: E731
     variants = (("fp64_fe", "fp64", 0, None, None), ("fp64_fe_other_seed", "fp64", 0, None, 1),
                 ("fp32_fe", "fp32", 0, None, None), ("fp32_kahan_fe", "fp32_kahan", 0, None, None),
                 ("fp32_fe_ff_cg", "fp32", 1, None, None),
-                ("chosen_fp32_kahan_surrogate", "fp32_kahan", 0, sur, None))
+                ("fp32_kahan_surrogate", "fp32_kahan", 0, sur, None),
+                ("chosen_fp32_kahan_lagged_fe", "fp32_kahan", 0, lag(lag_tol), None),
+                ("fp32_kahan_frozen_wp", "fp32_kahan", 0, lag(1e30), None))
     ref, out = None, {}
     for name, prec, cgp, s, seed in variants:
-        if s is None and name == "chosen_fp32_kahan_surrogate":
+        if s is None and name == "fp32_kahan_surrogate":
             continue
         f = Form(cfg, mesh, stream, precision=prec, cg_precision=cgp, sur=s, seed=seed)
+        s0 = f.g.surrogate_stats() if s is not None else None
         rr = f.timed(dt, steps, 0)
         st = cell_stats(f.g, mesh)
         rate = f.g.num_particles * steps / (rr["ms"] / 1e3)
-        f.close()
         if ref is None:
             ref = st
         out[name] = {"particle_steps_per_s": rate,
                      "rel_rms_vs_fp64": {q: rel_rms(st[q], ref[q]) for q in st}}
+        if s is not None:
+            s1 = f.g.surrogate_stats()
+            out[name]["fe_solves"] = int(s1[1] - s0[1])
+        f.close()
     return {"steps": steps, "cells": "12 x 8 grid, particle-weighted element means", "variants": out,
             "note": "fp64_fe_other_seed is the Monte Carlo scale: differences below it are within sampling noise"}
 

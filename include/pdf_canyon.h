@@ -416,6 +416,10 @@ int pdf_surrogate_harvest(pdf_ctx* c, float* X, float* T);
  *          G_ij and C0 eps there from the particle's wp and the interpolated
  *          k, eps and stresses (FP32 state only, else PDF_ERR_ARG)
  *  mode 4  mode 3, and every particle's wp is kept (PDF_FIELD_PARTICLE_WP)
+ *  mode 5  lagged FE, no network (params and norm may be NULL): the previous
+ *          step's solution is the proposal under the same coarse check, so
+ *          the FE solve runs only when the statistics have moved its residual
+ *          above residual_tol
  * Weights are rounded to bfloat16; inference accumulates in FP32. Requires
  * an elliptic-relaxation context (else PDF_ERR_ARG). */
 int pdf_set_surrogate(pdf_ctx* c, int32_t mode, const float* params, const float* norm, double residual_tol);

@@ -335,8 +335,8 @@ class Canyon:
         self._check(lib().pdf_surrogate_harvest(self._h, _vp(X_ptr), _vp(T_ptr)))
 
     def set_surrogate(self, mode: int, params=None, norm=None, residual_tol: float = 0.0):
-        if mode == 0:
-            self._check(lib().pdf_set_surrogate(self._h, 0, None, None, 0.0))
+        if mode == 0 or mode == 5:  # mode 5 (lagged FE) has no network
+            self._check(lib().pdf_set_surrogate(self._h, mode, None, None, float(residual_tol)))
             return
         p = np.ascontiguousarray(params, np.float32)
         q = np.ascontiguousarray(norm, np.float32)

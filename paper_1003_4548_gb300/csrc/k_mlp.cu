@@ -477,6 +477,17 @@ constexpr int RES_ROWS = 128;
 // b0 (the coarse residual: one aggregate per block of RES_ROWS Morton-ordered
 // nodes, which averages out the node-to-node noise of the estimated
 // statistics), in a fixed order
+// proposal of the lagged FE mode: the previous solution at the free rows,
+// the Dirichlet values at the walls
+__global__ void k_lag_prop(int nn, const int* __restrict__ rep, const unsigned char* __restrict__ is_wall,
+                           const double* __restrict__ prev, const double* __restrict__ g, double* __restrict__ prop) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nn) return;
+    const double* src = is_wall[i] ? g : prev;
+#pragma unroll
+    for (int k = 0; k < NC; ++k) prop[NC * (size_t)i + k] = src[NC * (size_t)i + k];
+}
+
 __global__ void __launch_bounds__(RES_ROWS) k_sur_residual(ResArgs a) {
     __shared__ double red[4 * NC][RES_ROWS];
     const int t = threadIdx.x, i = blockIdx.x * RES_ROWS + t;
@@ -593,7 +604,10 @@ int surrogate_rows(pdf_ctx* c) {
 int launch_surrogate(pdf_ctx* c) {
     const int nn = c->m.nn;
     const SurArgs a = sur_args(c);
-    k_sur_nodes<<<(nn + TC_M - 1) / TC_M, TC_M, 0, c->s>>>(a, c->sur_w, c->fe_g, c->fe_prop, c->d_status);
+    if (c->sur_mode == 5)  // lagged FE: the previous solution is the proposal
+        k_lag_prop<<<(nn + 127) / 128, 128, 0, c->s>>>(nn, c->m.rep, c->m.is_wall, c->nwp, c->fe_g, c->fe_prop);
+    else
+        k_sur_nodes<<<(nn + TC_M - 1) / TC_M, TC_M, 0, c->s>>>(a, c->sur_w, c->fe_g, c->fe_prop, c->d_status);
     ResArgs r;
     r.nn = nn; r.rowptr = c->m.rowptr; r.colidx = c->m.colidx; r.mval = c->m.mval; r.aval = c->m.aval;
     r.rep = c->m.rep; r.is_wall = c->m.is_wall;
@@ -607,7 +621,7 @@ int launch_surrogate(pdf_ctx* c) {
     r.last = c->sur_part + (size_t)nb * 4 * NC;
     k_sur_residual<<<nb, RES_ROWS, 0, c->s>>>(r);
     c->launches += 2;
-    if (c->sur_mode >= 3) {
+    if (c->sur_mode == 3 || c->sur_mode == 4) {
         k_sur_featpack<<<(nn + 127) / 128, 128, 0, c->s>>>(a, c->sur_w + PDF_MLP_NPARAM, c->nsurT);
         ++c->launches;
     }
@@ -638,18 +652,19 @@ int pdf_surrogate_harvest(pdf_ctx* c, float* X, float* T) {
 
 int pdf_set_surrogate(pdf_ctx* c, int32_t mode, const float* params, const float* norm, double residual_tol) {
     if (!c) return PDF_ERR_ARG;
-    if (mode < 0 || mode > 4) return fail(c, PDF_ERR_ARG, "surrogate mode must be 0 .. 4");
-    if (mode >= 3 && c->prec == 0) return fail(c, PDF_ERR_ARG, "the per-particle surrogate needs an FP32 state");
+    if (mode < 0 || mode > 5) return fail(c, PDF_ERR_ARG, "surrogate mode must be 0 .. 5");
+    if ((mode == 3 || mode == 4) && c->prec == 0) return fail(c, PDF_ERR_ARG, "the per-particle surrogate needs an FP32 state");
     if (mode == 0) {
         c->sur_mode = 0;
         return PDF_OK;
     }
     if (c->p.wall_model != PDF_ELLIPTIC_RELAXATION) return fail(c, PDF_ERR_ARG, "surrogate needs elliptic relaxation");
-    if (!params || !norm || !(residual_tol >= 0)) return fail(c, PDF_ERR_ARG, "surrogate: NULL array or bad tolerance");
-    for (int q = 0; q < PDF_MLP_NNORM; ++q)
+    if (!(residual_tol >= 0)) return fail(c, PDF_ERR_ARG, "surrogate: bad tolerance");
+    if (mode != 5 && (!params || !norm)) return fail(c, PDF_ERR_ARG, "surrogate: NULL array");
+    for (int q = 0; q < PDF_MLP_NNORM && mode != 5; ++q)
         if (!std::isfinite(norm[q]) || (((q >= IN && q < 2 * IN) || q >= 2 * IN + OUT) && !(norm[q] > 0.f)))
             return fail(c, PDF_ERR_ARG, "surrogate: standard deviations must be positive and finite");
-    if (mode >= 3 && !c->nsurT) PDF_CUDA(c, cudaMalloc((void**)&c->nsurT, sizeof(float) * 16 * (size_t)c->m.nn));
+    if ((mode == 3 || mode == 4) && !c->nsurT) PDF_CUDA(c, cudaMalloc((void**)&c->nsurT, sizeof(float) * 16 * (size_t)c->m.nn));
     if (mode == 4 && c->pwp_n < c->np) {
         cudaFree(c->pwp);
         c->pwp = nullptr;
@@ -663,9 +678,9 @@ int pdf_set_surrogate(pdf_ctx* c, int32_t mode, const float* params, const float
         PDF_CUDA(c, cudaMalloc((void**)&c->sur_cnt, 2 * sizeof(unsigned long long)));
         PDF_CUDA(c, cudaMalloc((void**)&c->sur_part, sizeof(double) * ((size_t)sur_blocks(c) * 4 * NC + 3)));
     }
-    std::vector<float> h(PDF_MLP_NPARAM + PDF_MLP_NNORM);
-    for (int q = 0; q < PDF_MLP_NPARAM; ++q) h[q] = __bfloat162float(__float2bfloat16_rn(params[q]));
-    for (int q = 0; q < PDF_MLP_NNORM; ++q) h[PDF_MLP_NPARAM + q] = norm[q];
+    std::vector<float> h(PDF_MLP_NPARAM + PDF_MLP_NNORM, 0.f);
+    for (int q = 0; q < PDF_MLP_NPARAM && mode != 5; ++q) h[q] = __bfloat162float(__float2bfloat16_rn(params[q]));
+    for (int q = 0; q < PDF_MLP_NNORM && mode != 5; ++q) h[PDF_MLP_NPARAM + q] = norm[q];
     PDF_CUDA(c, cudaStreamSynchronize(c->s));
     PDF_CUDA(c, cudaMemcpy(c->sur_w, h.data(), sizeof(float) * h.size(), cudaMemcpyHostToDevice));
     PDF_CUDA(c, cudaMemset(c->sur_skip, 0, sizeof(int)));

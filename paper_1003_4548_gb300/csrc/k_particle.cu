@@ -648,7 +648,7 @@ int launch_particle_step(pdf_ctx* c, double dt) {
     }
     const int64_t ntiles = (c->np + TILE - 1) / TILE;
     timing_begin(c, PDF_K_PARTICLE);
-    if (c->sur_mode >= 3 && c->prec != 0) {
+    if ((c->sur_mode == 3 || c->sur_mode == 4) && c->prec != 0) {
         if (!c->step_sur_blocks) {
             int per_sm = 0;
             PDF_CUDA(c, cudaFuncSetAttribute(k_step_sur, cudaFuncAttributeMaxDynamicSharedMemorySize,

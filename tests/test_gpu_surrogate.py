@@ -284,3 +284,60 @@ def test_per_particle_form(torch, er_case):
     g.sync()
     assert g.surrogate_stats()[1] == 0
     g.close()
+
+
+def test_lagged_fe_mode(torch, er_case):
+    """Mode 5 keeps the previous FE solution while its coarse residual under
+    the current statistics stays below the tolerance: with tolerance 0 every
+    step solves and the run equals the FE-only run exactly; with an infinite
+    tolerance no step solves and wp stays the initial solution away from the
+    walls (the wall rows take the current Dirichlet values); in between, the
+    solves are counted and the wp passed on is either that held solution or
+    a fresh FE solve."""
+    mesh, make = er_case
+    tri, tag, pair = mesh["tri"], mesh["edge_tag"], mesh["periodic_pair"]
+    wall = np.zeros(len(pair), bool)
+    for k in range(3):
+        on = tag[:, k] == 1
+        wall[tri[on, (k + 1) % 3]] = wall[tri[on, (k + 2) % 3]] = True
+    wall |= np.where(pair >= 0, wall[np.maximum(pair, 0)], False)
+    inner = ~wall
+    dt = _dt(mesh)
+    a, b, c = make(), make(), make()
+    for g in (a, b, c):
+        g.seed_particles(32)
+        g.estimate_stats()
+    wp0 = c.field("node_wp")
+    b.set_surrogate(5, None, None, 0.0)
+    c.set_surrogate(5, None, None, 1e30)
+    for g in (a, b, c):
+        g.step(dt, 4)
+        g.sync()
+    assert b.surrogate_stats()[:2] == (4, 4)
+    assert np.array_equal(a.field("node_wp"), b.field("node_wp"))
+    oa, ob = np.argsort(a.field("id")), np.argsort(b.field("id"))
+    for k in ("x", "u", "om", "psi"):
+        assert np.array_equal(a.field(k)[oa], b.field(k)[ob]), k
+    assert c.surrogate_stats()[:2] == (4, 0)
+    assert c.cg_iterations == 0
+    assert np.array_equal(c.field("node_wp")[inner], wp0[inner])
+    # a moderate tolerance: the held solution until the residual crosses it
+    d = make()
+    d.seed_particles(32)
+    d.estimate_stats()
+    d.set_surrogate(5, None, None, 0.05)
+    held = d.field("node_wp")
+    solves = 0
+    for _ in range(6):
+        d.step(dt, 1)
+        d.sync()
+        n, f, res = d.surrogate_stats()
+        wp = d.field("node_wp")
+        if f > solves:  # this step solved
+            solves = f
+            assert res[0] > 0.05
+            held = wp
+        else:
+            assert res[0] <= 0.05 and np.array_equal(wp[inner], held[inner])
+    for g in (a, b, c, d):
+        g.close()
