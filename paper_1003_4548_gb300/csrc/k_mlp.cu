@@ -472,11 +472,6 @@ struct ResArgs {
 
 constexpr int RES_ROWS = 128;
 
-// r = M f - A x over the free rows (x holds the Dirichlet values at the walls),
-// b0 = M f - A_wall g; block partial sums of r^2, b0^2 (fine norm) and of r,
-// b0 (the coarse residual: one aggregate per block of RES_ROWS Morton-ordered
-// nodes, which averages out the node-to-node noise of the estimated
-// statistics), in a fixed order
 // proposal of the lagged FE mode: the previous solution at the free rows,
 // the Dirichlet values at the walls
 __global__ void k_lag_prop(int nn, const int* __restrict__ rep, const unsigned char* __restrict__ is_wall,
@@ -488,22 +483,37 @@ __global__ void k_lag_prop(int nn, const int* __restrict__ rep, const unsigned c
     for (int k = 0; k < NC; ++k) prop[NC * (size_t)i + k] = src[NC * (size_t)i + k];
 }
 
+// r = M f - A x over the free rows (x holds the Dirichlet values at the walls),
+// b0 = M f - A_wall g; block partial sums of r^2, b0^2 (fine norm) and of r,
+// b0 (the coarse residual: one aggregate per block of RES_ROWS Morton-ordered
+// nodes, which averages out the node-to-node noise of the estimated
+// statistics), in a fixed order
 __global__ void __launch_bounds__(RES_ROWS) k_sur_residual(ResArgs a) {
-    __shared__ double red[4 * NC][RES_ROWS];
+    __shared__ double red[4 * NC][RES_ROWS / 32];
     const int t = threadIdx.x, i = blockIdx.x * RES_ROWS + t;
     double r[NC] = {0, 0, 0, 0, 0}, b0[NC] = {0, 0, 0, 0, 0};
     if (i < a.nn && a.rep[i] == i && !a.is_wall[i]) {
         double b[NC] = {0, 0, 0, 0, 0}, s[NC] = {0, 0, 0, 0, 0}, sw[NC] = {0, 0, 0, 0, 0};
-        for (int q = a.rowptr[i]; q < a.rowptr[i + 1]; ++q) {
-            const int j = a.colidx[q];
-            const double A = a.aval[q], M = a.mval[q];
-            const bool wall = a.is_wall[j];
+        const int q1 = a.rowptr[i + 1];
+        for (int q0 = a.rowptr[i]; q0 < q1; q0 += 4) {
+            // four entries at a time: their column loads, then their value
+            // loads, are issued together (latency, not bandwidth, bounds this)
+            int j4[4];
 #pragma unroll
-            for (int c = 0; c < NC; ++c) {
-                b[c] += M * a.f[NC * (size_t)j + c];
-                const double ax = A * a.x[NC * (size_t)j + c];
-                s[c] += ax;
-                if (wall) sw[c] += ax;
+            for (int k = 0; k < 4; ++k) j4[k] = q0 + k < q1 ? a.colidx[q0 + k] : -1;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                if (j4[k] < 0) break;
+                const int j = j4[k];
+                const double A = a.aval[q0 + k], M = a.mval[q0 + k];
+                const bool wall = a.is_wall[j];
+#pragma unroll
+                for (int c = 0; c < NC; ++c) {
+                    b[c] += M * a.f[NC * (size_t)j + c];
+                    const double ax = A * a.x[NC * (size_t)j + c];
+                    s[c] += ax;
+                    if (wall) sw[c] += ax;
+                }
             }
         }
 #pragma unroll
@@ -512,21 +522,31 @@ __global__ void __launch_bounds__(RES_ROWS) k_sur_residual(ResArgs a) {
             b0[c] = b[c] - sw[c];
         }
     }
+    // block sums of the 20 values: warp shuffle trees (the 20 interleaved),
+    // then the RES_ROWS / 32 warps in order
+    double v20[4 * NC];
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
-        red[c][t] = r[c] * r[c];
-        red[NC + c][t] = b0[c] * b0[c];
-        red[2 * NC + c][t] = r[c];
-        red[3 * NC + c][t] = b0[c];
+        v20[c] = r[c] * r[c];
+        v20[NC + c] = b0[c] * b0[c];
+        v20[2 * NC + c] = r[c];
+        v20[3 * NC + c] = b0[c];
     }
-    __syncthreads();
-    for (int w = RES_ROWS / 2; w > 0; w >>= 1) {
-        if (t < w)
 #pragma unroll
-            for (int v = 0; v < 4 * NC; ++v) red[v][t] += red[v][t + w];
-        __syncthreads();
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int v = 0; v < 4 * NC; ++v) v20[v] += __shfl_down_sync(0xffffffffu, v20[v], o);
+    const int lane = t & 31, wid = t >> 5;
+    if (lane == 0)
+#pragma unroll
+        for (int v = 0; v < 4 * NC; ++v) red[v][wid] = v20[v];
+    __syncthreads();
+    if (t < 4 * NC) {
+        double sum = 0.0;
+#pragma unroll
+        for (int w = 0; w < RES_ROWS / 32; ++w) sum += red[t][w];
+        a.part[(size_t)blockIdx.x * 4 * NC + t] = sum;
     }
-    if (t < 4 * NC) a.part[(size_t)blockIdx.x * 4 * NC + t] = red[t][0];
     // the last block to finish reduces all partials and takes the decision
     __shared__ bool last_block;
     __threadfence();
