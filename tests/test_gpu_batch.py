@@ -36,7 +36,8 @@ def cases():
 
 def make(torch, mesh, ppe, wm, k, stream, **over):
     from paper_1003_4548_gb300 import Canyon, canyon_params
-    p = canyon_params(mesh, wall_model=wm, precision="fp64", C0=2.1, seed=100 + k, case_id=k, cg_tol=1e-10,
+    precision = over.pop("precision", "fp64")
+    p = canyon_params(mesh, wall_model=wm, precision=precision, C0=2.1, seed=100 + k, case_id=k, cg_tol=1e-10,
                       cg_maxit=20000, **over)
     g = Canyon(p, mesh, stream=stream.cuda_stream)
     g.seed_particles(ppe)
@@ -106,3 +107,41 @@ def test_autotune_changes_shapes_not_results(torch):
         assert np.array_equal(A[key], B[key]), key
     tuned.close()
     twin.close()
+
+
+def test_batch_graph_fp32_lagged_and_pressure(torch):
+    """The FP32 path in the graph: the warp-per-element moments on the side
+    stream, the lagged FE solve (mode 5) and the pressure projection's
+    cooperative solve. With exact FP32 reductions (order-independent) a
+    batched case ends exactly where the same case stepped on its own ends."""
+    from paper_1003_4548_gb300 import capi
+    specs = (("er", dict(), 5), ("er", dict(pressure=1, pressure_tol=1e-10), 5), ("wf", dict(), 0))
+    cs = cases()
+    er_mesh = cs[1][0]
+    wf_mesh = cs[0][0]
+    streams = [torch.cuda.Stream() for _ in range(2 * len(specs) + 1)]
+    batched, alone, dts = [], [], []
+    for k, (wm, over, mode) in enumerate(specs):
+        mesh = er_mesh if wm == "er" else wf_mesh
+        for lst, st in ((batched, streams[k]), (alone, streams[len(specs) + k])):
+            g = make(torch, mesh, 24, wm, k, st, **dict(over, precision="fp32"))
+            if mode:
+                g.set_surrogate(mode, None, None, 0.05)
+            lst.append(g)
+        dts.append(cfl_dt(mesh, cfl=0.5, k0=1e-3))
+    b = capi.Batch(batched, dts, streams[-1].cuda_stream)
+    for g, dt in zip(alone, dts):
+        g.step(dt, 4)
+        g.sync()
+    b.step(4)
+    b.sync()
+    for ga, gb in zip(alone, batched):
+        A, B = by_id(ga), by_id(gb)
+        for k in ("x", "y", "u", "v", "w", "om", "psi", "elem", "bin"):
+            assert np.array_equal(A[k], B[k]), k
+        assert np.array_equal(ga.field("elem_mean"), gb.field("elem_mean"))
+        assert np.array_equal(ga.field("node_pack"), gb.field("node_pack"))
+    assert np.array_equal(alone[1].field("node_p"), batched[1].field("node_p"))
+    b.close()
+    for g in batched + alone:
+        g.close()
