@@ -661,7 +661,7 @@ __device__ __forceinline__ Buckets make_buckets(double mean, double var, int nb)
 // bucket where the running count reaches Tk, then an exact rank of the keys
 // in that bucket (bisection over the value bits when it holds more than 32).
 template <int NT, int NMAX>
-__device__ __noinline__ void sel_boundaries(SelSmem<NMAX>& S, const uint32_t* __restrict__ ids, int n, int ng,
+__device__ __forceinline__ void sel_boundaries(SelSmem<NMAX>& S, const uint32_t* __restrict__ ids, int n, int ng,
                                             const int (&gsize)[4], const Buckets bk) {
     const Team<NT> T;
     constexpr int NB = SelCfg<NMAX>::NB, PL = NB / 32, CMAX = SelCfg<NMAX>::CMAX;  // PL buckets per lane
@@ -835,7 +835,7 @@ __device__ __noinline__ void exact_moments(const MomArgs<float>& a, int e, int s
 // products, then mean = s + S1/n and central moments S2/n - (S1/n)^2. With
 // NT > 32 warp 0 sums all particles.
 template <int NT, int NMAX>
-__device__ __noinline__ void kahan_moments(const MomArgs<float>& a, int e, int s0, int n, SelSmem<NMAX>& S) {
+__device__ __forceinline__ void kahan_moments(const MomArgs<float>& a, int e, int s0, int n, SelSmem<NMAX>& S) {
     const Team<NT> T;
     if (T.wid == 0) {
         const int lane = T.lane;
