@@ -144,10 +144,16 @@ KERNEL_SOURCES = {
 
 
 def kernel_source_hash(kernel: str = "k_step") -> str:
+    """Hash of the code of a kernel's sources (line comments and blank lines
+    left out, so a comment edit does not invalidate a capture)."""
+    import re
     h = hashlib.sha1()
     for f in KERNEL_SOURCES[kernel]:
-        with open(os.path.join(ROOT, "paper_1003_4548_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_1003_4548_gb300", "csrc", f), encoding="utf-8") as fh:
+            for line in fh:
+                code = re.sub(r"//.*$", "", line).strip()
+                if code:
+                    h.update(code.encode() + b"\n")
     return h.hexdigest()[:12]
 
 

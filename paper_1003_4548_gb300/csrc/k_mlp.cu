@@ -9,7 +9,9 @@
 //    pass, the backward pass of the mean-squared error, and Adam;
 //  * harvesting of (features, targets) at the free canonical nodes;
 //  * node inference with bfloat16-rounded weights and FP32 accumulation, the
-//    FE residual of its wp, and the device-side decision whether the CG runs.
+//    FE residual of its wp, and the device-side decision whether the CG runs;
+//  * the lagged FE mode: the previous solution put under the same residual
+//    check, so the FE solve runs only when the statistics have moved it.
 #include <cuda_bf16.h>
 
 #include <algorithm>

@@ -12,6 +12,15 @@
 //    the sorted segment into nb1 groups, re-sort each group by (V, id) and
 //    split into nb2, then by (W, id) into nb3; <phi|V> of a bin is its mean psi.
 // Reductions are FP64 (or compensated FP32 with PDF_FP32_KAHAN).
+//
+// FP32 particle state with median splits (2 x 2 x 2 bins), the production
+// path: one warp per element of at most 512 particles finds each split's
+// boundary key by a 256-bucket histogram and an exact rank of the keys in the
+// boundary bucket (no sort); the moments are exact fixed-point sums (FP32) or
+// compensated FP32 sums (FP32 + Kahan). Crowded elements (more than 512
+// particles, listed by k_crowded) go to 256-thread teams, and elements above
+// 4096 to the block kernel above; those run on the context stream while the
+// warp kernel runs on a high-priority side stream forked from it.
 #include <algorithm>
 
 #include "pdf_internal.cuh"
