@@ -140,6 +140,7 @@ def gpu_index(local_rank: int) -> int:
 KERNEL_SOURCES = {
     "k_step": ("k_particle.cu", "pdf_internal.cuh"),
     "k_moments_sel": ("k_stats.cu", "exact_sum.cuh", "pdf_internal.cuh"),
+    "k_scatter": ("k_sort.cu", "pdf_internal.cuh"),
 }
 
 
@@ -259,7 +260,7 @@ def algorithmic_bytes(kclass: str, ts: int):
     return None, None
 
 
-KTRAFFIC = {"particle": "k_step", "moments": "k_moments_sel"}
+KTRAFFIC = {"particle": "k_step", "moments": "k_moments_sel", "sort": "k_scatter"}
 
 
 def roofline(kclass, kt, n, ts, workload, precision):
