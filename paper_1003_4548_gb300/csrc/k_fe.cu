@@ -27,7 +27,7 @@ constexpr int FE_THREADS = 256;
 __global__ void k_fe_rhs(int nn, const double* __restrict__ nR, const double* __restrict__ ngrad,
                          const double* __restrict__ nke, const double* __restrict__ nmean,
                          const unsigned char* __restrict__ is_wall, const double* __restrict__ wn, pdf_params p,
-                         double* f, double* g) {
+                         double* f, double* g, const double* __restrict__ prev, double* __restrict__ prop) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nn) return;
     const double* R = nR + 6 * (size_t)i;
@@ -39,30 +39,43 @@ __global__ void k_fe_rhs(int nn, const double* __restrict__ nR, const double* __
     const double Rm[2][2] = {{R[0], R[3]}, {R[3], R[1]}};
     const double tr = R[0] + R[1] + R[2];
     double b[2][2] = {{0, 0}, {0, 0}};
-    if (tr > 0.0)
+    // one FP64 division per quotient at most (GB300's FP64 pipe is narrow):
+    // the anisotropy from the reciprocal of the trace, gamma5 / 3 as a product
+    if (tr > 0.0) {
+        const double itr = 1.0 / tr;
         for (int a = 0; a < 2; ++a)
-            for (int c = 0; c < 2; ++c) b[a][c] = Rm[a][c] / tr - (a == c ? 1.0 / 3.0 : 0.0);
+            for (int c = 0; c < 2; ++c) b[a][c] = Rm[a][c] * itr - (a == c ? 1.0 / 3.0 : 0.0);
+    }
     const double det = R[2] * (R[0] * R[1] - R[3] * R[3]);
     const double tk = 2.0 / 3.0 * k;
     double Av = p.Cv * det / (tk * tk * tk);
     Av = Av < 1.0 ? Av : 1.0;
     const double iso = 0.5 * (1.0 - p.C1) * k * om;
+    const double g3 = p.gamma5 * (1.0 / 3.0);
     int q = 0;
     for (int a = 0; a < 2; ++a)
         for (int c = 0; c < 2; ++c) {
-            double t = (p.C2 * Av + p.gamma5 / 3.0) * gg[a][c] - p.gamma5 / 3.0 * gg[c][a];
+            double t = (p.C2 * Av + g3) * gg[a][c] - g3 * gg[c][a];
             for (int m = 0; m < 2; ++m) t += p.gamma5 * b[a][m] * gg[m][c];
             for (int l = 0; l < 2; ++l) t -= p.gamma5 * b[a][l] * gg[c][l];
             f[NC * (size_t)i + q++] = (a == c ? iso : 0.0) + (p.rotta ? 0.0 : k * t);
         }
     f[NC * (size_t)i + 4] = iso;
-    if (is_wall[i]) {
+    const bool wall = is_wall[i];
+    if (wall) {
         const double eps = nke[2 * i + 1], nx = wn[2 * i], ny = wn[2 * i + 1];
-        g[NC * (size_t)i + 0] = -p.er_wall * eps * nx * nx;
-        g[NC * (size_t)i + 1] = -p.er_wall * eps * nx * ny;
-        g[NC * (size_t)i + 2] = -p.er_wall * eps * ny * nx;
-        g[NC * (size_t)i + 3] = -p.er_wall * eps * ny * ny;
-        g[NC * (size_t)i + 4] = 0.0;
+        const double gw[NC] = {-p.er_wall * eps * nx * nx, -p.er_wall * eps * nx * ny, -p.er_wall * eps * ny * nx,
+                               -p.er_wall * eps * ny * ny, 0.0};
+#pragma unroll
+        for (int k = 0; k < NC; ++k) {
+            g[NC * (size_t)i + k] = gw[k];
+            if (prop != nullptr) prop[NC * (size_t)i + k] = gw[k];
+        }
+    } else if (prop != nullptr) {
+        // lagged FE mode: the proposal is the previous solution at the free
+        // rows (the Dirichlet values above at the walls)
+#pragma unroll
+        for (int k = 0; k < NC; ++k) prop[NC * (size_t)i + k] = prev[NC * (size_t)i + k];
     }
 }
 
@@ -588,14 +601,6 @@ constexpr size_t pcg_smem() {
     return sizeof(float) * (BS * (BS + 4) + 2 * NC * BS) + sizeof(double) * 3 * NC * BS;
 }
 
-__global__ void k_fe_copy_out(int nn, const int* __restrict__ rep, const double* __restrict__ x, double* nwp) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= nn) return;
-    const int r = rep[i];
-#pragma unroll
-    for (int k = 0; k < NC; ++k) nwp[NC * (size_t)i + k] = x[NC * (size_t)r + k];
-}
-
 }  // namespace
 
 namespace {
@@ -670,11 +675,12 @@ int launch_elliptic(pdf_ctx* c) {
     const int nn = c->m.nn;
     timing_begin(c, PDF_K_ELLIPTIC);
     k_fe_rhs<<<(nn + 127) / 128, 128, 0, c->s>>>(nn, c->nR, c->ngrad, c->nke, c->nmean, c->m.is_wall, c->m.wn,
-                                                c->p, c->fe_f, c->fe_g);
+                                                c->p, c->fe_f, c->fe_g, c->sur_mode == 5 ? c->nwp : nullptr,
+                                                c->sur_mode == 5 ? c->fe_prop : nullptr);
     k_fe_assemble<<<(unsigned)((c->m.nnz + 255) / 256), 256, 0, c->s>>>(c->m.nnz, c->m.mval, c->m.kc_off,
                                                                        c->m.kc_elem, c->m.kc_geo, c->eder,
                                                                        c->m.aval, c->m.avf);
-    c->launches += 1;
+    c->launches += 2;
     PDF_CUDA(c, cudaGetLastError());
     if (c->sur_mode) {
         const int st = launch_surrogate(c);
@@ -706,8 +712,9 @@ int launch_elliptic(pdf_ctx* c) {
     else err = launch_pcg<192>(a, c->fe_blocks, c->s, ffv);
     PDF_CUDA(c, err);
     if (c->coop_done) PDF_CUDA(c, cudaEventRecord(c->coop_done, c->s));
-    k_fe_copy_out<<<(nn + 127) / 128, 128, 0, c->s>>>(nn, c->m.rep, c->nwp, c->nwp);
-    c->launches += 3;
+    // the periodic image rows take the canonical rows' solution in the node
+    // pack kernel that follows
+    ++c->launches;
     timing_end(c, PDF_K_ELLIPTIC);
     PDF_CUDA(c, cudaGetLastError());
     return PDF_OK;

@@ -84,17 +84,28 @@ __global__ void k_node_stats(int nn, const int* __restrict__ n2e_off, const int*
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nn) return;
     double wt = 0.0, m[4] = {0, 0, 0, 0}, R[6] = {0, 0, 0, 0, 0, 0}, pv = 0.0;
-    for (int q = n2e_off[i]; q < n2e_off[i + 1]; ++q) {
-        const int e = n2e[q];
-        const double n = (double)en[e];
-        wt += n;
-        m[0] += n * emean[5 * e + 0];
-        m[1] += n * emean[5 * e + 1];
-        m[2] += n * emean[5 * e + 3];
-        m[3] += n * emean[5 * e + 4];
+    const int q1 = n2e_off[i + 1];
+    for (int q0 = n2e_off[i]; q0 < q1; q0 += 4) {
+        // four elements at a time: their index loads, then their data loads,
+        // are issued together (latency bounds this kernel); past the node's
+        // last element the terms are zeros, so the sums equal the plain loop's
+        int e4[4];
 #pragma unroll
-        for (int k = 0; k < 6; ++k) R[k] += n * eR[6 * e + k];
-        pv += n * epsivar[e];
+        for (int k = 0; k < 4; ++k) e4[k] = q0 + k < q1 ? n2e[q0 + k] : -1;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int e = e4[k];
+            const bool in = e >= 0;
+            const double n = in ? (double)en[e] : 0.0;
+            wt += n;
+            m[0] += n * (in ? emean[5 * e + 0] : 0.0);
+            m[1] += n * (in ? emean[5 * e + 1] : 0.0);
+            m[2] += n * (in ? emean[5 * e + 3] : 0.0);
+            m[3] += n * (in ? emean[5 * e + 4] : 0.0);
+#pragma unroll
+            for (int j = 0; j < 6; ++j) R[j] += n * (in ? eR[6 * e + j] : 0.0);
+            pv += n * (in ? epsivar[e] : 0.0);
+        }
     }
     nwt[i] = wt;
     if (wt <= 0.0) return;  // keeps the previous node values
@@ -117,7 +128,7 @@ template <typename T>
 __global__ void k_elem_derived(int nt, const int* __restrict__ tri, const double* __restrict__ gradb,
                                const double* __restrict__ cent, const double* __restrict__ nmean,
                                const double* __restrict__ nR, const double* __restrict__ nke, pdf_params p,
-                               double* eder, T* epack) {
+                               int fast, double* eder, T* epack) {
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= nt) return;
     double Ux = 0, Uy = 0, Vx = 0, Vy = 0, kc = 0, ec = 0, Uc = 0, Vc = 0;
@@ -143,18 +154,37 @@ __global__ void k_elem_derived(int nt, const int* __restrict__ tri, const double
     const double P = -(Rc[0] * Ux + Rc[3] * Uy + Rc[3] * Vx + Rc[1] * Vy);
     const double iec = 1.0 / ec;
     d[6] = p.Comega2 - p.Comega1 * P * iec;
-    const double Ucn = sqrt(Uc * Uc + Vc * Vc);
     double dx = cent[2 * e] - p.x0;
     dx -= p.period * floor(dx * (1.0 / p.period) + 0.5);
-    const double dist = hypot(dx, cent[2 * e + 1] - p.y0);
-    double t1 = p.Cs * cbrt(p.r0 * p.r0 * iec);
-    t1 += (Ucn > 0.0) ? p.Ct * dist / Ucn : HUGE_VAL;
-    const double t2a = kc * iec, t2b = p.CT * sqrt(p.nu * iec);
-    const double t2 = t2a > t2b ? t2a : t2b;
-    d[7] = t1 < t2 ? t1 : t2;
+    const double dy = cent[2 * e + 1] - p.y0;
     const double Cxi = 1.0 + 1.3 * 1.0;  // C_xi = 1 + 1.3 n_i n_i with a unit normal
-    const double La = Cxi * kc * sqrt(kc) * iec, Lb = p.Ceta * sqrt(sqrt(p.nu * p.nu * p.nu * iec));
-    d[8] = p.CL * (La > Lb ? La : Lb);
+    const double t2a = kc * iec;
+    if (fast) {
+        // compensated-FP32 form: the roots of the mixing time scale and of
+        // L in FP32 (relative error below 3e-7, inside that form's
+        // statistical tolerance; GB300's FP64 pipe is narrow)
+        const float iecf = (float)iec, kcf = (float)kc;
+        const float Ucn = sqrtf((float)(Uc * Uc + Vc * Vc));
+        const float dist = hypotf((float)dx, (float)dy);
+        float t1 = (float)p.Cs * cbrtf((float)(p.r0 * p.r0 * iec));
+        t1 += (Ucn > 0.f) ? (float)p.Ct * dist / Ucn : INFINITY;
+        const float t2b = (float)p.CT * sqrtf((float)(p.nu * iec));
+        const float t2 = fmaxf((float)t2a, t2b);
+        d[7] = (double)(t1 < t2 ? t1 : t2);
+        const float La = (float)Cxi * kcf * sqrtf(kcf) * iecf;
+        const float Lb = (float)p.Ceta * sqrtf(sqrtf((float)(p.nu * p.nu * p.nu * iec)));
+        d[8] = p.CL * (double)fmaxf(La, Lb);
+    } else {
+        const double Ucn = sqrt(Uc * Uc + Vc * Vc);
+        const double dist = hypot(dx, dy);
+        double t1 = p.Cs * cbrt(p.r0 * p.r0 * iec);
+        t1 += (Ucn > 0.0) ? p.Ct * dist / Ucn : HUGE_VAL;
+        const double t2b = p.CT * sqrt(p.nu * iec);
+        const double t2 = t2a > t2b ? t2a : t2b;
+        d[7] = t1 < t2 ? t1 : t2;
+        const double La = Cxi * kc * sqrt(kc) * iec, Lb = p.Ceta * sqrt(sqrt(p.nu * p.nu * p.nu * iec));
+        d[8] = p.CL * (La > Lb ? La : Lb);
+    }
     T* ep = epack + (size_t)ELEM_PACK_W * e;
     ep[0] = (T)Ux; ep[1] = (T)Uy; ep[2] = (T)Vx; ep[3] = (T)Vy;
     ep[6] = (T)d[6]; ep[7] = (T)d[7];
@@ -165,12 +195,20 @@ __global__ void k_node_grad(int nn, const int* __restrict__ n2e_off, const int* 
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nn) return;
     double a = 0, g[4] = {0, 0, 0, 0};
-    for (int q = n2e_off[i]; q < n2e_off[i + 1]; ++q) {
-        const int e = n2e[q];
-        const double A = area[e];
-        a += A;
+    const int q1 = n2e_off[i + 1];
+    for (int q0 = n2e_off[i]; q0 < q1; q0 += 4) {  // four elements at a time, as in k_node_stats
+        int e4[4];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) g[k] += A * eder[9 * e + k];
+        for (int k = 0; k < 4; ++k) e4[k] = q0 + k < q1 ? n2e[q0 + k] : -1;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int e = e4[k];
+            const bool in = e >= 0;
+            const double A = in ? area[e] : 0.0;
+            a += A;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) g[j] += A * (in ? eder[9 * e + j] : 0.0);
+        }
     }
     const double ia = 1.0 / a;
 #pragma unroll
@@ -198,7 +236,7 @@ __global__ void k_elem_lap(int nt, const int* __restrict__ tri, const double* __
 
 template <typename T>
 __global__ void k_node_pack(int nn, const double* __restrict__ nmean, const double* __restrict__ nR,
-                            const double* __restrict__ nke, const double* __restrict__ nwp, pdf_params p,
+                            const double* __restrict__ nke, const int* __restrict__ rep, double* nwp, pdf_params p,
                             double* npack, T* npackT) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nn) return;
@@ -212,7 +250,15 @@ __global__ void k_node_pack(int nn, const double* __restrict__ nmean, const doub
         q[3] = p.C0 * eps;
         q[4] = a; q[5] = 0.0; q[6] = 0.0; q[7] = a; q[8] = a;
     } else {
-        const double* w = nwp + 5 * (size_t)i;  // Eqs. Gij and C0
+        // Eqs. Gij and C0 with the solution of the node's canonical row; a
+        // periodic image row takes that solution (canonical rows are only
+        // read here, image rows only written)
+        const int r = rep[i];
+        const double* w = nwp + 5 * (size_t)r;
+        if (r != i) {
+#pragma unroll
+            for (int k = 0; k < 5; ++k) nwp[5 * (size_t)i + k] = w[k];
+        }
         const double* R = nR + 6 * (size_t)i;
         const double ik = 1.0 / kk, h2k = 0.5 * ik;
         q[4] = (2.0 * w[0] - eps) * h2k;
@@ -239,7 +285,7 @@ int run(pdf_ctx* c) {
     k_node_stats<<<gn, tb, 0, c->s>>>(nn, c->m.n2e_off, c->m.n2e, c->en, c->emean, c->eR, c->epsivar, c->p,
                                       c->nwt, c->nmean, c->nR, c->npsivar, c->nke);
     k_elem_derived<T><<<ge, tb, 0, c->s>>>(nt, c->m.tri, c->m.gradb, c->m.cent, c->nmean, c->nR, c->nke,
-                                           c->p, c->eder, (T*)c->epackT);
+                                           c->p, c->prec == 2, c->eder, (T*)c->epackT);
     k_node_grad<<<gn, tb, 0, c->s>>>(nn, c->m.n2e_off, c->m.n2e, c->m.area, c->eder, c->ngrad);
     k_elem_lap<T><<<ge, tb, 0, c->s>>>(nt, c->m.tri, c->m.gradb, c->ngrad, c->eder, (T*)c->epackT);
     c->launches += 4;
@@ -259,7 +305,8 @@ int run(pdf_ctx* c) {
         if (st != PDF_OK) return st;
     }
     timing_begin(c, PDF_K_FIELDS);
-    k_node_pack<T><<<gn, tb, 0, c->s>>>(nn, c->nmean, c->nR, c->nke, c->nwp, c->p, c->npack, (T*)c->npackT);
+    k_node_pack<T><<<gn, tb, 0, c->s>>>(nn, c->nmean, c->nR, c->nke, c->m.rep, c->nwp, c->p, c->npack,
+                                        (T*)c->npackT);
     ++c->launches;
     timing_end(c, PDF_K_FIELDS);
     PDF_CUDA(c, cudaGetLastError());

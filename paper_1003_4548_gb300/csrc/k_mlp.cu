@@ -474,17 +474,6 @@ struct ResArgs {
 
 constexpr int RES_ROWS = 128;
 
-// proposal of the lagged FE mode: the previous solution at the free rows,
-// the Dirichlet values at the walls
-__global__ void k_lag_prop(int nn, const int* __restrict__ rep, const unsigned char* __restrict__ is_wall,
-                           const double* __restrict__ prev, const double* __restrict__ g, double* __restrict__ prop) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= nn) return;
-    const double* src = is_wall[i] ? g : prev;
-#pragma unroll
-    for (int k = 0; k < NC; ++k) prop[NC * (size_t)i + k] = src[NC * (size_t)i + k];
-}
-
 // r = M f - A x over the free rows (x holds the Dirichlet values at the walls),
 // b0 = M f - A_wall g; block partial sums of r^2, b0^2 (fine norm) and of r,
 // b0 (the coarse residual: one aggregate per block of RES_ROWS Morton-ordered
@@ -493,11 +482,16 @@ __global__ void k_lag_prop(int nn, const int* __restrict__ rep, const unsigned c
 __global__ void __launch_bounds__(RES_ROWS) k_sur_residual(ResArgs a) {
     __shared__ double red[4 * NC][RES_ROWS / 32];
     const int t = threadIdx.x, i = blockIdx.x * RES_ROWS + t;
-    double r[NC] = {0, 0, 0, 0, 0}, b0[NC] = {0, 0, 0, 0, 0};
+    // 32 slots per thread for the butterfly below: 0..4 r^2, 5..9 b0^2,
+    // 10..14 r, 15..19 b0, 20..31 zero
+    double val[32];
+#pragma unroll
+    for (int k = 0; k < 32; ++k) val[k] = 0.0;
     if (i < a.nn && a.rep[i] == i && !a.is_wall[i]) {
         double b[NC] = {0, 0, 0, 0, 0}, s[NC] = {0, 0, 0, 0, 0}, sw[NC] = {0, 0, 0, 0, 0};
-        const int q1 = a.rowptr[i + 1];
-        for (int q0 = a.rowptr[i]; q0 < q1; q0 += 4) {
+        const int qa = a.rowptr[i], q1 = a.rowptr[i + 1];
+        bool touch = false;  // a column of the row is a wall node
+        for (int q0 = qa; q0 < q1; q0 += 4) {
             // four entries at a time: their column loads, then their value
             // loads, are issued together (latency, not bandwidth, bounds this)
             int j4[4];
@@ -508,40 +502,49 @@ __global__ void __launch_bounds__(RES_ROWS) k_sur_residual(ResArgs a) {
                 if (j4[k] < 0) break;
                 const int j = j4[k];
                 const double A = a.aval[q0 + k], M = a.mval[q0 + k];
-                const bool wall = a.is_wall[j];
+                touch |= a.is_wall[j] != 0;
+                // fused multiply-adds: GB300's FP64 pipe is narrow
 #pragma unroll
                 for (int c = 0; c < NC; ++c) {
-                    b[c] += M * a.f[NC * (size_t)j + c];
-                    const double ax = A * a.x[NC * (size_t)j + c];
-                    s[c] += ax;
-                    if (wall) sw[c] += ax;
+                    b[c] = fma(M, a.f[NC * (size_t)j + c], b[c]);
+                    s[c] = fma(A, a.x[NC * (size_t)j + c], s[c]);
                 }
+            }
+        }
+        if (touch) {  // the wall-column sum, on the few rows beside a wall
+            for (int q = qa; q < q1; ++q) {
+                const int j = a.colidx[q];
+                if (!a.is_wall[j]) continue;
+                const double A = a.aval[q];
+#pragma unroll
+                for (int c = 0; c < NC; ++c) sw[c] = fma(A, a.x[NC * (size_t)j + c], sw[c]);
             }
         }
 #pragma unroll
         for (int c = 0; c < NC; ++c) {
-            r[c] = b[c] - s[c];
-            b0[c] = b[c] - sw[c];
+            const double r = b[c] - s[c], b0 = b[c] - sw[c];
+            val[c] = r * r;
+            val[NC + c] = b0 * b0;
+            val[2 * NC + c] = r;
+            val[3 * NC + c] = b0;
         }
     }
-    // block sums of the 20 values: warp shuffle trees (the 20 interleaved),
-    // then the RES_ROWS / 32 warps in order
-    double v20[4 * NC];
-#pragma unroll
-    for (int c = 0; c < NC; ++c) {
-        v20[c] = r[c] * r[c];
-        v20[NC + c] = b0[c] * b0[c];
-        v20[2 * NC + c] = r[c];
-        v20[3 * NC + c] = b0[c];
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-        for (int v = 0; v < 4 * NC; ++v) v20[v] += __shfl_down_sync(0xffffffffu, v20[v], o);
+    // warp sums of the 20 values by a butterfly reduce-scatter: at the xor-o
+    // exchange a lane keeps the half of its w slots selected by its lane bit
+    // o and adds the partner's copy of that half; lane l ends with the warp
+    // sum of value l (a fixed order of additions)
     const int lane = t & 31, wid = t >> 5;
-    if (lane == 0)
 #pragma unroll
-        for (int v = 0; v < 4 * NC; ++v) red[v][wid] = v20[v];
+    for (int w = 16, o = 16; w >= 1; w >>= 1, o >>= 1) {
+        const bool upper = (lane & o) != 0;
+#pragma unroll
+        for (int k = 0; k < w; ++k) {
+            const double send = upper ? val[k] : val[w + k];
+            const double keep = upper ? val[w + k] : val[k];
+            val[k] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+        }
+    }
+    if (lane < 4 * NC) red[lane][wid] = val[0];
     __syncthreads();
     if (t < 4 * NC) {
         double sum = 0.0;
@@ -562,35 +565,63 @@ __global__ void __launch_bounds__(RES_ROWS) k_sur_residual(ResArgs a) {
         __shared__ double acc6[6][4 * NC];
         const int grp = t / (4 * NC), v = t % (4 * NC);
         if (grp < 6) {
+            // the partials of eight blocks are loaded together, then added in
+            // block order
             double sacc = 0.0;
-            for (int b = grp; b < (int)gridDim.x; b += 6) {
-                const double q = a.part[(size_t)b * 4 * NC + v];
-                sacc += v < 2 * NC ? q : q * q;
+            const int nbk = (int)gridDim.x;
+            for (int b0 = grp; b0 < nbk; b0 += 6 * 8) {
+                double q8[8];
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    const int b = b0 + 6 * k;
+                    q8[k] = b < nbk ? a.part[(size_t)b * 4 * NC + v] : 0.0;
+                }
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    if (b0 + 6 * k >= nbk) break;
+                    sacc += v < 2 * NC ? q8[k] : q8[k] * q8[k];
+                }
             }
             acc6[grp][v] = sacc;
         }
         __syncthreads();
-        if (t == 0) {
-            double tot[4 * NC];
-            for (int k = 0; k < 4 * NC; ++k) {
-                tot[k] = 0.0;
-                for (int g2 = 0; g2 < 6; ++g2) tot[k] += acc6[g2][k];
+        __shared__ double tot[4 * NC];
+        if (t < 4 * NC) {
+            double sacc = 0.0;
+#pragma unroll
+            for (int g2 = 0; g2 < 6; ++g2) sacc += acc6[g2][t];
+            tot[t] = sacc;
+        }
+        __syncthreads();
+        if (t < 32) {
+            // lane c < NC forms the squared fine and coarse ratios of
+            // component c (every lane at once: a serial FP64 chain in one
+            // thread costs tens of microseconds on the narrow FP64 pipe); the
+            // largest ratio by shuffles, then one square root each, which
+            // equals the largest of the square roots. A NaN fails the check.
+            double xf = 0.0, xg = 0.0;
+            if (t < NC) {
+                const double rr = tot[t], bb = tot[NC + t], cr = tot[2 * NC + t], cb = tot[3 * NC + t];
+                xf = bb > 0.0 ? rr / bb : rr;
+                xg = cb > 0.0 ? cr / cb : cr;
             }
-            double fine = 0.0, coarse = 0.0;
-            for (int c = 0; c < NC; ++c) {
-                const double rr = tot[c], bb = tot[NC + c], cr = tot[2 * NC + c], cb = tot[3 * NC + c];
-                const double f = bb > 0.0 ? sqrt(rr / bb) : sqrt(rr);
-                const double g = cb > 0.0 ? sqrt(cr / cb) : sqrt(cr);
-                fine = f > fine ? f : fine;
-                coarse = g > coarse ? g : coarse;
+            const bool bad = __any_sync(0xffffffffu, !(xf == xf) || !(xg == xg));
+#pragma unroll
+            for (int o = 4; o >= 1; o >>= 1) {
+                xf = fmax(xf, __shfl_xor_sync(0xffffffffu, xf, o));
+                xg = fmax(xg, __shfl_xor_sync(0xffffffffu, xg, o));
             }
+            const double qnan = __longlong_as_double(0x7ff8000000000000ll);
+            const double fine = bad ? qnan : sqrt(xf), coarse = bad ? qnan : sqrt(xg);
             const int ok = (a.mode == 2) || (coarse <= a.tol);
-            *a.skip = ok;
-            a.last[0] = coarse;
-            a.last[1] = fine;
-            a.cnt[0] += 1ull;
-            a.cnt[1] += ok ? 0ull : 1ull;
-            *a.done = 0u;
+            if (t == 0) {
+                *a.skip = ok;
+                a.last[0] = coarse;
+                a.last[1] = fine;
+                a.cnt[0] += 1ull;
+                a.cnt[1] += ok ? 0ull : 1ull;
+                *a.done = 0u;
+            }
         }
     }
 }
@@ -626,10 +657,12 @@ int surrogate_rows(pdf_ctx* c) {
 int launch_surrogate(pdf_ctx* c) {
     const int nn = c->m.nn;
     const SurArgs a = sur_args(c);
-    if (c->sur_mode == 5)  // lagged FE: the previous solution is the proposal
-        k_lag_prop<<<(nn + 127) / 128, 128, 0, c->s>>>(nn, c->m.rep, c->m.is_wall, c->nwp, c->fe_g, c->fe_prop);
-    else
+    // lagged FE mode: the right-hand-side kernel has written the proposal
+    // (the previous solution, the Dirichlet values at the walls)
+    if (c->sur_mode != 5) {
         k_sur_nodes<<<(nn + TC_M - 1) / TC_M, TC_M, 0, c->s>>>(a, c->sur_w, c->fe_g, c->fe_prop, c->d_status);
+        ++c->launches;
+    }
     ResArgs r;
     r.nn = nn; r.rowptr = c->m.rowptr; r.colidx = c->m.colidx; r.mval = c->m.mval; r.aval = c->m.aval;
     r.rep = c->m.rep; r.is_wall = c->m.is_wall;
@@ -642,7 +675,7 @@ int launch_surrogate(pdf_ctx* c) {
     r.cnt = c->sur_cnt;
     r.last = c->sur_part + (size_t)nb * 4 * NC;
     k_sur_residual<<<nb, RES_ROWS, 0, c->s>>>(r);
-    c->launches += 2;
+    ++c->launches;
     if (c->sur_mode == 3 || c->sur_mode == 4) {
         k_sur_featpack<<<(nn + 127) / 128, 128, 0, c->s>>>(a, c->sur_w + PDF_MLP_NPARAM, c->nsurT);
         ++c->launches;

@@ -15,7 +15,9 @@ constexpr int SCAN_THREADS = 1024;
 
 // exclusive scan of the element counts by one block: warp w owns a contiguous
 // range of elements; pass 1 sums it with coalesced loads, warp 0 scans the 32
-// totals, pass 2 scans the range 32 elements at a time with a running carry
+// totals, pass 2 scans the range 32 elements at a time with a running carry.
+// Both passes load eight rows of 32 counts together, so a pass waits on
+// memory once per 256 counts instead of once per row.
 __global__ void __launch_bounds__(SCAN_THREADS) k_scan(const int* __restrict__ cnt, int nt, int* off,
                                                        int* cursor, uint32_t* bump) {
     if (bump != nullptr && threadIdx.x == 0) *bump += 1u;  // the step counter moves with the re-sort
@@ -25,8 +27,13 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan(const int* __restrict__ c
     const int per = (nt + NW - 1) / NW;
     const int b0 = min(nt, wid * per), b1 = min(nt, b0 + per);
     int s = 0;
-#pragma unroll 4
-    for (int e = b0 + lane; e < b1; e += 32) s += cnt[e];
+    for (int e0 = b0 + lane; e0 < b1; e0 += 32 * 8) {
+        int c8[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) c8[k] = e0 + 32 * k < b1 ? cnt[e0 + 32 * k] : 0;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) s += c8[k];
+    }
     s = __reduce_add_sync(0xffffffffu, s);
     if (lane == 0) warp_ex[wid] = s;
     __syncthreads();
@@ -43,20 +50,31 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan(const int* __restrict__ c
     }
     __syncthreads();
     int carry = warp_ex[wid];
-    for (int e0 = b0; e0 < b1; e0 += 32) {
-        const int e = e0 + lane;
-        const int c = e < b1 ? cnt[e] : 0;
-        int incl = c;
+    for (int e0 = b0; e0 < b1; e0 += 32 * 8) {
+        int c8[8], i8[8];
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += y;
+        for (int k = 0; k < 8; ++k) {
+            const int e = e0 + 32 * k + lane;
+            c8[k] = e < b1 ? cnt[e] : 0;
         }
-        if (e < b1) {
-            off[e] = carry + incl - c;
-            cursor[e] = carry + incl - c;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {  // eight independent row scans
+            i8[k] = c8[k];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, i8[k], o);
+                if (lane >= o) i8[k] += y;
+            }
         }
-        carry += __shfl_sync(0xffffffffu, incl, 31);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const int e = e0 + 32 * k + lane;
+            if (e < b1) {
+                off[e] = carry + i8[k] - c8[k];
+                cursor[e] = carry + i8[k] - c8[k];
+            }
+            carry += __shfl_sync(0xffffffffu, i8[k], 31);
+        }
     }
 }
 
