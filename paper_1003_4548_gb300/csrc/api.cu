@@ -353,6 +353,7 @@ int alloc_stats(pdf_ctx* c) {
     TRY(dalloc(c, &c->cnt, nt));
     TRY(dalloc(c, &c->off, nt + 1));
     TRY(dalloc(c, &c->cursor, nt));
+    TRY(dalloc(c, &c->scan_part, scan_blocks(nt) + 1));
     TRY(dalloc(c, &c->en, nt));
     TRY(dalloc(c, &c->emean, 5 * (size_t)nt));
     TRY(dalloc(c, &c->eR, 6 * (size_t)nt));
@@ -753,7 +754,7 @@ void pdf_destroy(pdf_ctx* c) {
     void* dev[] = {m.tri, m.nbr, m.einfo, m.xy, m.egeo_d, m.egeo_f, m.gradb, m.area, m.cent, m.n2e_off, m.n2e,
                    m.wdist, m.wn, m.is_wall, m.rep, m.rowptr, m.colidx, m.mval, m.kc_off, m.kc_elem, m.kc_geo,
                    m.aval, m.avf, m.diag, m.owall_node, m.owall_elem, m.pval, m.pin, c->eomw, c->nomw, c->pr_b, c->pr_x, c->pr_binv,
-                   c->pr_a0inv, c->pres, c->egp, c->pr_iters, c->idA, c->idB, c->elemA, c->elemB, c->bin, c->cnt, c->off, c->cursor, c->en,
+                   c->pr_a0inv, c->pres, c->egp, c->pr_iters, c->idA, c->idB, c->elemA, c->elemB, c->bin, c->cnt, c->off, c->cursor, c->scan_part, c->en,
                    c->emean, c->eR, c->epsivar, c->ecm, c->nwt, c->nmean, c->nR, c->nke, c->npsivar, c->eder,
                    c->ngrad, c->npack, c->nwp, c->npackT, c->epackT, c->ecmT, c->sort_scratch, c->fe_f, c->fe_g,
                    c->fe_prop, c->fe_z, c->fe_part, c->fe_bar, c->fe_iters, c->d_status,

@@ -1,7 +1,8 @@
 // k_sort.cu -- keeps the particle state sorted by host element.
 //
-// The particle kernel leaves per-element counts; one block scans them into
-// segment offsets, then every particle claims a slot in its element's
+// The particle kernel leaves per-element counts; a grid-wide scan (block
+// totals, then each block's offsets from the totals before it) turns them
+// into segment offsets, then every particle claims a slot in its element's
 // segment with a warp-aggregated atomic and moves its state there. The order
 // inside a segment is not fixed; every later reduction orders the segment by
 // (velocity, id) first, so results do not depend on it.
@@ -13,7 +14,8 @@ namespace {
 
 constexpr int SCAN_THREADS = 1024;
 
-// exclusive scan of the element counts by one block: warp w owns a contiguous
+// exclusive scan of the element counts by one block (the allocation-free
+// entry point, whose scratch holds no block totals): warp w owns a contiguous
 // range of elements; pass 1 sums it with coalesced loads, warp 0 scans the 32
 // totals, pass 2 scans the range 32 elements at a time with a running carry.
 // Both passes load eight rows of 32 counts together, so a pass waits on
@@ -76,6 +78,79 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan(const int* __restrict__ c
             carry += __shfl_sync(0xffffffffu, i8[k], 31);
         }
     }
+}
+
+// grid-wide exclusive scan of the element counts in two launches, SCAN_CHUNK
+// counts per block of 256 threads (four consecutive counts per thread), no
+// block waiting on another: k_scan_part writes each block's total,
+// k_scan_fin adds the totals of the blocks before its own and scans its chunk
+__device__ __forceinline__ void load4(const int* __restrict__ p, int e0, int n, int (&c)[4]) {
+    if (e0 + 3 < n) {
+        const int4 v = *reinterpret_cast<const int4*>(p + e0);
+        c[0] = v.x; c[1] = v.y; c[2] = v.z; c[3] = v.w;
+    } else {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) c[k] = e0 + k < n ? p[e0 + k] : 0;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_scan_part(const int* __restrict__ cnt, int nt, int* part, uint32_t* bump) {
+    __shared__ int ws[8];
+    if (bump != nullptr && blockIdx.x == 0 && threadIdx.x == 0) *bump += 1u;  // the step counter moves with the re-sort
+    const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+    int c[4];
+    load4(cnt, blockIdx.x * SCAN_CHUNK + 4 * t, nt, c);
+    int s = __reduce_add_sync(0xffffffffu, c[0] + c[1] + c[2] + c[3]);
+    if (lane == 0) ws[wid] = s;
+    __syncthreads();
+    if (t == 0) {
+        s = 0;
+#pragma unroll
+        for (int w = 0; w < 8; ++w) s += ws[w];
+        part[blockIdx.x] = s;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_scan_fin(const int* __restrict__ cnt, int nt, const int* __restrict__ part,
+                                                  int* off, int* cursor) {
+    __shared__ int ws[8];
+    __shared__ int base;
+    const int t = threadIdx.x, lane = t & 31, wid = t >> 5, b = blockIdx.x;
+    if (wid == 0) {  // counts of the blocks before this one
+        int s = 0;
+        for (int k = lane; k < b; k += 32) s += part[k];
+        s = __reduce_add_sync(0xffffffffu, s);
+        if (lane == 0) base = s;
+    }
+    const int e0 = b * SCAN_CHUNK + 4 * t;
+    int c[4];
+    load4(cnt, e0, nt, c);
+    const int loc = c[0] + c[1] + c[2] + c[3];
+    int incl = loc;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) ws[wid] = incl;
+    __syncthreads();
+    int run = base + incl - loc;
+    for (int w = 0; w < wid; ++w) run += ws[w];
+    int o4[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        o4[k] = run;
+        run += c[k];
+    }
+    if (e0 + 3 < nt) {
+        *reinterpret_cast<int4*>(off + e0) = make_int4(o4[0], o4[1], o4[2], o4[3]);
+        *reinterpret_cast<int4*>(cursor + e0) = make_int4(o4[0], o4[1], o4[2], o4[3]);
+    } else {
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            if (e0 + k < nt) off[e0 + k] = cursor[e0 + k] = o4[k];
+    }
+    if (b == (int)gridDim.x - 1 && t == 255) off[nt] = run;  // the total (counts past nt are zeros)
 }
 
 __global__ void __launch_bounds__(256) k_count(int64_t n, const int* __restrict__ elem, int nt, int* cnt,
@@ -210,8 +285,10 @@ extern "C" int pdf_sort_by_element_static(const int32_t* elem, int64_t n, int32_
 
 int launch_sort(pdf_ctx* c, bool advance_step) {
     timing_begin(c, PDF_K_SORT);
-    k_scan<<<1, SCAN_THREADS, 0, c->s>>>(c->cnt, c->m.nt, c->off, c->cursor, advance_step ? c->d_step : nullptr);
-    ++c->launches;
+    const int nb = scan_blocks(c->m.nt);
+    k_scan_part<<<nb, 256, 0, c->s>>>(c->cnt, c->m.nt, c->scan_part, advance_step ? c->d_step : nullptr);
+    k_scan_fin<<<nb, 256, 0, c->s>>>(c->cnt, c->m.nt, c->scan_part, c->off, c->cursor);
+    c->launches += 2;
     if (c->np > 0) {
         const int th = c->scatter_threads;
         const unsigned blocks = (unsigned)((c->np + th - 1) / th);

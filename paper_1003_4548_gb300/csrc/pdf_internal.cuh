@@ -101,6 +101,7 @@ struct pdf_ctx {
     int* cnt = nullptr;
     int* off = nullptr;     // nt+1
     int* cursor = nullptr;  // nt
+    int* scan_part = nullptr;  // per-block count totals of the grid-wide scan
     // statistics (FP64)
     int* en = nullptr;
     double *emean = nullptr, *eR = nullptr, *epsivar = nullptr, *ecm = nullptr;
@@ -199,6 +200,8 @@ void timing_end(pdf_ctx* c, int k);
 int launch_seed(pdf_ctx* c, int ppe);
 int launch_particle_step(pdf_ctx* c, double dt);
 int launch_sort(pdf_ctx* c, bool advance_step = false);  // scan + scatter A -> B + swap (+ d_step += 1)
+constexpr int SCAN_CHUNK = 1024;  // element counts per block of the grid-wide scan
+inline int scan_blocks(int nt) { return (nt + SCAN_CHUNK - 1) / SCAN_CHUNK; }
 int set_device_step(pdf_ctx* c);    // d_step = step
 int launch_count_and_sort(pdf_ctx* c);  // histogram of elemA, then launch_sort
 int launch_moments(pdf_ctx* c);
