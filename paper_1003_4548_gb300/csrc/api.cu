@@ -767,6 +767,7 @@ void pdf_destroy(pdf_ctx* c) {
     cudaFreeHost(c->h_status);
     if (c->side_fork) cudaEventDestroy(c->side_fork);
     if (c->side_join) cudaEventDestroy(c->side_join);
+    if (c->side_join2) cudaEventDestroy(c->side_join2);
     if (c->s2) cudaStreamDestroy(c->s2);
     delete c;
 }

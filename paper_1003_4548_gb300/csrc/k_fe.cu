@@ -671,16 +671,23 @@ int choose_grid(pdf_ctx* c, int bs, bool ffv, int& chosen_bs, int& chosen_blocks
 
 }  // namespace
 
+int launch_fe_assemble(pdf_ctx* c, cudaStream_t s) {
+    k_fe_assemble<<<(unsigned)((c->m.nnz + 255) / 256), 256, 0, s>>>(c->m.nnz, c->m.mval, c->m.kc_off, c->m.kc_elem,
+                                                                    c->m.kc_geo, c->eder, c->m.aval, c->m.avf);
+    ++c->launches;
+    PDF_CUDA(c, cudaGetLastError());
+    return PDF_OK;
+}
+
 int launch_elliptic(pdf_ctx* c) {
     const int nn = c->m.nn;
     timing_begin(c, PDF_K_ELLIPTIC);
     k_fe_rhs<<<(nn + 127) / 128, 128, 0, c->s>>>(nn, c->nR, c->ngrad, c->nke, c->nmean, c->m.is_wall, c->m.wn,
                                                 c->p, c->fe_f, c->fe_g, c->sur_mode == 5 ? c->nwp : nullptr,
                                                 c->sur_mode == 5 ? c->fe_prop : nullptr);
-    k_fe_assemble<<<(unsigned)((c->m.nnz + 255) / 256), 256, 0, c->s>>>(c->m.nnz, c->m.mval, c->m.kc_off,
-                                                                       c->m.kc_elem, c->m.kc_geo, c->eder,
-                                                                       c->m.aval, c->m.avf);
-    c->launches += 2;
+    ++c->launches;
+    // the assembly was launched on the side stream after the element fields
+    PDF_CUDA(c, cudaStreamWaitEvent(c->s, c->side_join, 0));
     PDF_CUDA(c, cudaGetLastError());
     if (c->sur_mode) {
         const int st = launch_surrogate(c);

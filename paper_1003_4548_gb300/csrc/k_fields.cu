@@ -286,8 +286,26 @@ int run(pdf_ctx* c) {
                                       c->nwt, c->nmean, c->nR, c->npsivar, c->nke);
     k_elem_derived<T><<<ge, tb, 0, c->s>>>(nt, c->m.tri, c->m.gradb, c->m.cent, c->nmean, c->nR, c->nke,
                                            c->p, c->prec == 2, c->eder, (T*)c->epackT);
+    // elliptic relaxation: the FE assembly (it needs only L, column 8 of
+    // eder) and then the element Laplacian (needed by the next particle step
+    // only) run on the side stream, beside the node gradients, the right-hand
+    // side and the residual check of the context stream; the Laplacian writes
+    // columns 4 and 5 of eder, which nothing on the context stream reads
+    // before the join at the end of this function
+    const bool er = c->p.wall_model == PDF_ELLIPTIC_RELAXATION;
+    if (er) {
+        PDF_CUDA(c, cudaEventRecord(c->side_fork, c->s));
+        PDF_CUDA(c, cudaStreamWaitEvent(c->s2, c->side_fork, 0));
+        TRY_OK(launch_fe_assemble(c, c->s2));
+        PDF_CUDA(c, cudaEventRecord(c->side_join, c->s2));
+    }
     k_node_grad<<<gn, tb, 0, c->s>>>(nn, c->m.n2e_off, c->m.n2e, c->m.area, c->eder, c->ngrad);
-    k_elem_lap<T><<<ge, tb, 0, c->s>>>(nt, c->m.tri, c->m.gradb, c->ngrad, c->eder, (T*)c->epackT);
+    if (er) {
+        PDF_CUDA(c, cudaEventRecord(c->side_fork, c->s));
+        PDF_CUDA(c, cudaStreamWaitEvent(c->s2, c->side_fork, 0));
+    }
+    k_elem_lap<T><<<ge, tb, 0, er ? c->s2 : c->s>>>(nt, c->m.tri, c->m.gradb, c->ngrad, c->eder, (T*)c->epackT);
+    if (er) PDF_CUDA(c, cudaEventRecord(c->side_join2, c->s2));
     c->launches += 4;
     if (c->m.n_owall_elem > 0) {
         const int nle = c->m.n_owall_elem, nln = c->m.n_owall_node;
@@ -308,6 +326,7 @@ int run(pdf_ctx* c) {
     k_node_pack<T><<<gn, tb, 0, c->s>>>(nn, c->nmean, c->nR, c->nke, c->m.rep, c->nwp, c->p, c->npack,
                                         (T*)c->npackT);
     ++c->launches;
+    if (er) PDF_CUDA(c, cudaStreamWaitEvent(c->s, c->side_join2, 0));  // the side stream joins back
     timing_end(c, PDF_K_FIELDS);
     PDF_CUDA(c, cudaGetLastError());
     return PDF_OK;

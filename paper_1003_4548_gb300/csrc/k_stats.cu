@@ -1178,6 +1178,7 @@ int prepare_moments(pdf_ctx* c) {
         PDF_CUDA(c, cudaStreamCreateWithPriority(&c->s2, cudaStreamNonBlocking, hi));
         PDF_CUDA(c, cudaEventCreateWithFlags(&c->side_fork, cudaEventDisableTiming));
         PDF_CUDA(c, cudaEventCreateWithFlags(&c->side_join, cudaEventDisableTiming));
+        PDF_CUDA(c, cudaEventCreateWithFlags(&c->side_join2, cudaEventDisableTiming));
     }
     const int smem = (int)(sizeof(SortKey) * STATS_CAP);
     PDF_CUDA(c, cudaFuncSetAttribute(k_moments<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));

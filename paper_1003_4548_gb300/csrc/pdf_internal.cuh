@@ -166,10 +166,12 @@ struct pdf_ctx {
     int step_sur_blocks = 0;  // persistent grid of the per-particle surrogate form
     int scatter_threads = 256;  // block size of the re-sort scatter
     cudaEvent_t coop_wait = nullptr, coop_done = nullptr;  // batch: chain of the cooperative CG launches
-    // side stream of the crowded-element moments, forked from and joined back
-    // into the context stream inside each step
+    // side stream forked from and joined back into the context stream inside
+    // each step: the warp moments kernel beside the crowded-element kernels;
+    // the FE assembly and the element Laplacian beside the node gradients,
+    // the right-hand side and the residual check (side_join2: the Laplacian)
     cudaStream_t s2 = nullptr;
-    cudaEvent_t side_fork = nullptr, side_join = nullptr;
+    cudaEvent_t side_fork = nullptr, side_join = nullptr, side_join2 = nullptr;
     std::string err;
     int num_sms = 0;
 };
@@ -206,7 +208,8 @@ int set_device_step(pdf_ctx* c);    // d_step = step
 int launch_count_and_sort(pdf_ctx* c);  // histogram of elemA, then launch_sort
 int launch_moments(pdf_ctx* c);
 int launch_fields(pdf_ctx* c);      // node stats, derived, recovery, ER solve, packs
-int launch_elliptic(pdf_ctx* c);
+int launch_elliptic(pdf_ctx* c);     // right-hand side, (wait for the assembly on side_join), check, CG
+int launch_fe_assemble(pdf_ctx* c, cudaStream_t s);  // values of M + K_{L^2} from L (column 8 of eder)
 int prepare_pressure(pdf_ctx* c);             // grid and preconditioner of the projection, once
 int launch_pressure(pdf_ctx* c, double dt);  // projection after the moments (pressure = 1)
 int prepare_particle(pdf_ctx* c, int per_sm);   // persistent grid (0: all resident blocks)
