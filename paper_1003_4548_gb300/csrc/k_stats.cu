@@ -40,12 +40,15 @@ struct AccD {
     }
 };
 
-// Neumaier-compensated FP32 sum; merges add the compensations
+// compensated FP32 sum: c accumulates the exact rounding error of every
+// addition (Knuth's TwoSum, branch-free; the same error term as Neumaier's
+// form), merges add the compensations
 struct AccK {
     float s = 0.f, c = 0.f;
     __device__ void add(float x) {
         const float t = s + x;
-        c += (fabsf(s) >= fabsf(x)) ? (s - t) + x : (x - t) + s;
+        const float bp = t - s;
+        c += (s - (t - bp)) + (x - bp);
         s = t;
     }
     __device__ void merge(const AccK& o) {
@@ -850,30 +853,42 @@ __device__ __forceinline__ void kahan_moments(const MomArgs<float>& a, int e, in
         const int lane = T.lane;
         const float su = a.u[s0], sv = a.v[s0], sw = a.w[s0], sp = a.psi[s0];
         // 16 compensated sums (12 used): 0..4 the shifted u v w psi and omega,
-        // 5..10 the products uu vv ww uv uw vw, 11 psi psi
+        // 5..10 the products uu vv ww uv uw vw, 11 psi psi. Blocked: a lane
+        // sums blocks of up to SEL_BLOCK of its particles in plain FP32 (the
+        // products fused), and only the block sums enter the compensated
+        // sums; the rounding error stays below (SEL_BLOCK + 2) u sum |x|.
         AccK acc[16];
-        // two particles per lane at a time: their ten loads are issued
-        // together, then added in particle order
-        for (int q0 = lane; q0 < n; q0 += 64) {
-            float x[2][5];
+        constexpr int SEL_BLOCK = 8;
+        for (int b0 = lane; b0 < n; b0 += 32 * SEL_BLOCK) {
+            float blk[12];
 #pragma unroll
-            for (int r = 0; r < 2; ++r) {
-                const int q = q0 + 32 * r;
-                const bool in = q < n;
-                x[r][0] = in ? a.u[s0 + q] : su;
-                x[r][1] = in ? a.v[s0 + q] : sv;
-                x[r][2] = in ? a.w[s0 + q] : sw;
-                x[r][3] = in ? a.psi[s0 + q] : sp;
-                x[r][4] = in ? a.om[s0 + q] : 0.f;
+            for (int k = 0; k < 12; ++k) blk[k] = 0.f;
+            // two particles at a time: their ten loads are issued together,
+            // then added in particle order
+#pragma unroll
+            for (int h = 0; h < SEL_BLOCK; h += 2) {
+                float x[2][5];
+#pragma unroll
+                for (int r = 0; r < 2; ++r) {
+                    const int q = b0 + 32 * (h + r);
+                    const bool in = q < n;
+                    x[r][0] = in ? a.u[s0 + q] : su;
+                    x[r][1] = in ? a.v[s0 + q] : sv;
+                    x[r][2] = in ? a.w[s0 + q] : sw;
+                    x[r][3] = in ? a.psi[s0 + q] : sp;
+                    x[r][4] = in ? a.om[s0 + q] : 0.f;
+                }
+#pragma unroll
+                for (int r = 0; r < 2; ++r) {  // a missing particle adds zeros
+                    const float du = x[r][0] - su, dv = x[r][1] - sv, dw = x[r][2] - sw, dp = x[r][3] - sp;
+                    blk[0] += du; blk[1] += dv; blk[2] += dw; blk[3] += dp; blk[4] += x[r][4];
+                    blk[5] = fmaf(du, du, blk[5]); blk[6] = fmaf(dv, dv, blk[6]); blk[7] = fmaf(dw, dw, blk[7]);
+                    blk[8] = fmaf(du, dv, blk[8]); blk[9] = fmaf(du, dw, blk[9]); blk[10] = fmaf(dv, dw, blk[10]);
+                    blk[11] = fmaf(dp, dp, blk[11]);
+                }
             }
 #pragma unroll
-            for (int r = 0; r < 2; ++r) {
-                if (q0 + 32 * r >= n) break;
-                const float du = x[r][0] - su, dv = x[r][1] - sv, dw = x[r][2] - sw, dp = x[r][3] - sp;
-                acc[0].add(du); acc[1].add(dv); acc[2].add(dw); acc[3].add(dp); acc[4].add(x[r][4]);
-                acc[5].add(du * du); acc[6].add(dv * dv); acc[7].add(dw * dw);
-                acc[8].add(du * dv); acc[9].add(du * dw); acc[10].add(dv * dw); acc[11].add(dp * dp);
-            }
+            for (int k = 0; k < 12; ++k) acc[k].add(blk[k]);
         }
         // butterfly reduce-scatter over the warp: after the xor-16, 8, 4, 2
         // exchanges (each lane merging the half it keeps with the partner's)
