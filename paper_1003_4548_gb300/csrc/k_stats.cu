@@ -544,6 +544,7 @@ struct SelSmem {
     int ired[8];               // team reduction scratch
     unsigned ured[2][NMAX > 512 ? 8 : 1];
     unsigned long long xred[NMAX > 512 ? 8 : 1][24];  // per-warp exact sums (12 x 128 bit), block teams only
+    float kred[NMAX > 512 ? 7 : 1][24];  // warps 1..7's compensated sums (s, c of 12), block teams only
     double mean[5];
     double rd[3];              // <uu>, <vv>, <ww> of the element (bucket ranges of the splits)
     unsigned long long binsum[8];  // sum of psi per bin, unit 2^-(63 - log2 NMAX) (psi in [0, 1])
@@ -677,9 +678,11 @@ __device__ __forceinline__ void sel_boundaries(SelSmem<NMAX>& S, const uint32_t*
                                             const int (&gsize)[4], const Buckets bk) {
     const Team<NT> T;
     constexpr int NB = SelCfg<NMAX>::NB, PL = NB / 32, CMAX = SelCfg<NMAX>::CMAX;  // PL buckets per lane
-    if (T.wid == 0) {  // boundary bucket of every group
+    {  // boundary bucket of every group: a warp team scans the groups in
+       // turn, a block team gives group g to its warp g
         const int lane = T.lane;
-        for (int g = 0; g < ng; ++g) {
+        const int g0 = NT == 32 ? 0 : T.wid, gstep = NT == 32 ? 1 : NT / 32;
+        for (int g = g0; g < ng; g += gstep) {
             const int Tk = (gsize[g] + 1) / 2;
             int loc[PL], tot = 0;
 #pragma unroll
@@ -845,11 +848,12 @@ __device__ __noinline__ void exact_moments(const MomArgs<float>& a, int e, int s
 // the segment's first particle (x - s, whose sums stay small when the mean is
 // large against the spread): sums of the shifted values and of their
 // products, then mean = s + S1/n and central moments S2/n - (S1/n)^2. With
-// NT > 32 warp 0 sums all particles.
+// NT > 32 every warp sums its share (particle q goes to thread q mod NT) and
+// warp 0 merges the warps' sums in warp order.
 template <int NT, int NMAX>
 __device__ __forceinline__ void kahan_moments(const MomArgs<float>& a, int e, int s0, int n, SelSmem<NMAX>& S) {
     const Team<NT> T;
-    if (T.wid == 0) {
+    {
         const int lane = T.lane;
         const float su = a.u[s0], sv = a.v[s0], sw = a.w[s0], sp = a.psi[s0];
         // 16 compensated sums (12 used): 0..4 the shifted u v w psi and omega,
@@ -859,7 +863,7 @@ __device__ __forceinline__ void kahan_moments(const MomArgs<float>& a, int e, in
         // sums; the rounding error stays below (SEL_BLOCK + 2) u sum |x|.
         AccK acc[16];
         constexpr int SEL_BLOCK = 8;
-        for (int b0 = lane; b0 < n; b0 += 32 * SEL_BLOCK) {
+        for (int b0 = T.tid; b0 < n; b0 += NT * SEL_BLOCK) {
             float blk[12];
 #pragma unroll
             for (int k = 0; k < 12; ++k) blk[k] = 0.f;
@@ -870,7 +874,7 @@ __device__ __forceinline__ void kahan_moments(const MomArgs<float>& a, int e, in
                 float x[2][5];
 #pragma unroll
                 for (int r = 0; r < 2; ++r) {
-                    const int q = b0 + 32 * (h + r);
+                    const int q = b0 + NT * (h + r);
                     const bool in = q < n;
                     x[r][0] = in ? a.u[s0 + q] : su;
                     x[r][1] = in ? a.v[s0 + q] : sv;
@@ -919,44 +923,61 @@ __device__ __forceinline__ void kahan_moments(const MomArgs<float>& a, int e, in
                 acc[0].merge(recv);
             }
         }
-        // sum v sits in lanes 2v and 2v + 1: lane q < 12 finishes moment q (FP64,
-        // all lanes at once): lanes 0..4 the means, 5..10 the central second
-        // moments uu vv ww uv uw vw, 11 the psi variance
-        int ia = 0, ib = 0, ic = 0;  // first-moment sums used by this lane; ic: its second-moment sum
-        if (lane < 5) ia = lane;
-        else if (lane < 11) {
-            const int k = lane - 5;  // uu vv ww uv uw vw
-            ia = k < 3 ? k : (k == 5 ? 1 : 0);
-            ib = k < 3 ? k : (k == 3 ? 1 : 2);
-            ic = 5 + k;
-        } else {
-            ia = ib = 3;
-            ic = 11;
-        }
-        AccK A, Bq, Cq;
-        A.s = __shfl_sync(0xffffffffu, acc[0].s, 2 * ia);
-        A.c = __shfl_sync(0xffffffffu, acc[0].c, 2 * ia);
-        Bq.s = __shfl_sync(0xffffffffu, acc[0].s, 2 * ib);
-        Bq.c = __shfl_sync(0xffffffffu, acc[0].c, 2 * ib);
-        Cq.s = __shfl_sync(0xffffffffu, acc[0].s, 2 * ic);
-        Cq.c = __shfl_sync(0xffffffffu, acc[0].c, 2 * ic);
-        if (lane < 12) {
-            const double inv_n = recip_n(n);
-            const double da = A.value() * inv_n;
-            double val;
-            if (lane < 5) {
-                const float shift = lane == 0 ? su : (lane == 1 ? sv : (lane == 2 ? sw : (lane == 3 ? sp : 0.f)));
-                val = shift + da;
-                a.emean[5 * e + lane] = val;
-                S.mean[lane] = val;
-            } else {
-                val = Cq.value() * inv_n - da * (Bq.value() * inv_n);
-                if (lane < 11) a.eR[6 * e + lane - 5] = val;
-                else a.epsivar[e] = val;
-                if (lane < 8) S.rd[lane - 5] = val;
+        if constexpr (NT > 32) {  // warp 0 merges the other warps' sums, in warp order
+            if (lane < 24 && T.wid > 0) {
+                S.kred[T.wid - 1][lane] = (lane & 1) ? acc[0].c : acc[0].s;
+            }
+            __syncthreads();
+            if (T.wid == 0 && lane < 24) {
+#pragma unroll 1
+                for (int w = 0; w < NT / 32 - 1; ++w) {
+                    AccK o;
+                    o.s = S.kred[w][lane & ~1];
+                    o.c = S.kred[w][lane | 1];
+                    acc[0].merge(o);
+                }
             }
         }
-        if (lane == 0) a.en[e] = n;
+        if (T.wid == 0) {  // finalisation
+            // sum v sits in lanes 2v and 2v + 1: lane q < 12 finishes moment q (FP64,
+            // all lanes at once): lanes 0..4 the means, 5..10 the central second
+            // moments uu vv ww uv uw vw, 11 the psi variance
+            int ia = 0, ib = 0, ic = 0;  // first-moment sums used by this lane; ic: its second-moment sum
+            if (lane < 5) ia = lane;
+            else if (lane < 11) {
+                const int k = lane - 5;  // uu vv ww uv uw vw
+                ia = k < 3 ? k : (k == 5 ? 1 : 0);
+                ib = k < 3 ? k : (k == 3 ? 1 : 2);
+                ic = 5 + k;
+            } else {
+                ia = ib = 3;
+                ic = 11;
+            }
+            AccK A, Bq, Cq;
+            A.s = __shfl_sync(0xffffffffu, acc[0].s, 2 * ia);
+            A.c = __shfl_sync(0xffffffffu, acc[0].c, 2 * ia);
+            Bq.s = __shfl_sync(0xffffffffu, acc[0].s, 2 * ib);
+            Bq.c = __shfl_sync(0xffffffffu, acc[0].c, 2 * ib);
+            Cq.s = __shfl_sync(0xffffffffu, acc[0].s, 2 * ic);
+            Cq.c = __shfl_sync(0xffffffffu, acc[0].c, 2 * ic);
+            if (lane < 12) {
+                const double inv_n = recip_n(n);
+                const double da = A.value() * inv_n;
+                double val;
+                if (lane < 5) {
+                    const float shift = lane == 0 ? su : (lane == 1 ? sv : (lane == 2 ? sw : (lane == 3 ? sp : 0.f)));
+                    val = shift + da;
+                    a.emean[5 * e + lane] = val;
+                    S.mean[lane] = val;
+                } else {
+                    val = Cq.value() * inv_n - da * (Bq.value() * inv_n);
+                    if (lane < 11) a.eR[6 * e + lane - 5] = val;
+                    else a.epsivar[e] = val;
+                    if (lane < 8) S.rd[lane - 5] = val;
+                }
+            }
+            if (lane == 0) a.en[e] = n;
+        }
     }
     T.sync();
 }
