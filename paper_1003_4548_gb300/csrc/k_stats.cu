@@ -135,8 +135,9 @@ struct MomArgs {
     int64_t scratch_n;
     int* status;
     int min_n;  // the block kernel only takes elements with more particles than this
-    // FP32 median path: elements too crowded for a warp, appended by the warp
-    // kernel (lcnt[0]: 512 < n <= 4096 in listA, lcnt[1]: n > 4096 in listB)
+    // FP32 median path: elements too crowded for a warp, listed by k_crowded
+    // (lcnt[0]: 512 < n <= 4096 in listA, lcnt[1]: n > 4096 in listB; lcnt[2]:
+    // the next listA entry a block of k_moments_sel_big takes)
     int* lcnt;
     int* listA;
     int* listB;
@@ -1132,16 +1133,23 @@ __global__ void k_crowded(const int* __restrict__ off, int nt, int* lcnt, int* l
     else if (n > 512) listA[atomicAdd(&lcnt[0], 1)] = e;
 }
 
-// block of 256 threads per element: 512 < n <= 4096 (crowded elements)
+// block of 256 threads per element: 512 < n <= 4096 (crowded elements). The
+// blocks take the listed elements from a shared counter (lcnt[2]), so a block
+// that drew large elements does not hold up the others.
 template <bool KAHAN>
 __global__ void __launch_bounds__(256) k_moments_sel_big(const MomArgs<float> a) {
     __shared__ SelSmem<4096> sm;
+    __shared__ int jnext;
     const int cnt = a.lcnt[0];
-    for (int j = blockIdx.x; j < cnt; j += gridDim.x) {
+    for (;;) {
+        if (threadIdx.x == 0) jnext = atomicAdd(&a.lcnt[2], 1);
+        __syncthreads();
+        const int j = jnext;
+        if (j >= cnt) break;
         const int e = a.listA[j];
         const int s0 = a.off[e], n = a.off[e + 1] - s0;
         sel_element<KAHAN, 256, 4096>(a, e, s0, n, sm);
-        __syncthreads();
+        __syncthreads();  // the element's shared memory and jnext are free again
     }
 }
 
@@ -1176,16 +1184,16 @@ int run(pdf_ctx* c) {
             // run) run concurrently on the context stream and fill the SMs the
             // warp kernel's last waves leave
             a.min_n = 4096;
-            a.lcnt = c->elist;
-            a.listA = c->elist + 2;
-            a.listB = c->elist + 2 + c->m.nt;
+            a.lcnt = c->elist;  // [0], [1]: list lengths; [2]: next element of listA to take
+            a.listA = c->elist + 4;
+            a.listB = c->elist + 4 + c->m.nt;
             PDF_CUDA(c, cudaEventRecord(c->side_fork, c->s));
             PDF_CUDA(c, cudaStreamWaitEvent(c->s2, c->side_fork, 0));
             k_moments_sel<KAHAN><<<blocks, 32 * WARPS_PER_BLOCK, 0, c->s2>>>(a, c->m.nt);
             PDF_CUDA(c, cudaEventRecord(c->side_join, c->s2));
-            PDF_CUDA(c, cudaMemsetAsync(a.lcnt, 0, 2 * sizeof(int), c->s));
+            PDF_CUDA(c, cudaMemsetAsync(a.lcnt, 0, 3 * sizeof(int), c->s));
             k_crowded<<<(c->m.nt + 255) / 256, 256, 0, c->s>>>(c->off, c->m.nt, a.lcnt, a.listA, a.listB);
-            k_moments_sel_big<KAHAN><<<std::min(c->m.nt, 2 * c->num_sms), 256, 0, c->s>>>(a);
+            k_moments_sel_big<KAHAN><<<std::min(c->m.nt, 3 * c->num_sms), 256, 0, c->s>>>(a);
             const size_t smem = sizeof(SortKey) * STATS_CAP;
             k_moments<T, KAHAN><<<(unsigned)std::min(c->m.nt, c->num_sms), STATS_THREADS, smem, c->s>>>(a);
             PDF_CUDA(c, cudaStreamWaitEvent(c->s, c->side_join, 0));
