@@ -338,12 +338,16 @@ __device__ __forceinline__ void advance_particle(const StepArgs<T>& a, const uin
 
 // ---------------------------------------------------------------------------
 // The step kernel: a persistent grid over tiles of TILE consecutive particles.
-// Thread 0 of a block stages the next tile's state (seven state arrays, id,
-// element, bin) into shared memory with bulk asynchronous copies that complete
-// on an mbarrier, while the block advances the current tile, so the load
-// latency of the HBM-streamed state overlaps the arithmetic. The arrays are
-// allocated in whole tiles, so every copy starts 16-byte aligned and its size
-// is rounded up to 16 bytes inside the allocation.
+// Thread 0 of a block stages the tile NSTAGE - 1 ahead (seven state arrays,
+// id, element, bin) into shared memory with bulk asynchronous copies that
+// complete on the stage's "full" mbarrier, while the block advances the
+// current tile, so the load latency of the HBM-streamed state overlaps the
+// arithmetic. A warp that has finished a tile arrives on the stage's "empty"
+// mbarrier; only thread 0 waits for those arrivals, before it refills the
+// stage, so the other warps never wait for the block's slowest particle (a
+// wall reflection, a walk over several elements) at a block barrier. The
+// arrays are allocated in whole tiles, so every copy starts 16-byte aligned
+// and its size is rounded up to 16 bytes inside the allocation.
 // ---------------------------------------------------------------------------
 constexpr int TILE = 256;
 
@@ -359,6 +363,10 @@ __device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)
 
 __device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
 }
 
 __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
@@ -407,29 +415,47 @@ __device__ __forceinline__ void stage_tile(const StepArgs<T>& a, Stage<T>& st, u
     bulk_to_smem(st.bin, a.bin + base, b1, bar);
 }
 
+// stages of the particle kernel: three for FP32 state (28 KB of static
+// shared memory), two for FP64 (33 KB; three would pass the 48 KB static limit)
+template <typename T> constexpr int NSTAGE = sizeof(T) == 4 ? 3 : 2;
+
 template <typename T>
 __global__ void __launch_bounds__(TILE) k_step(const StepArgs<T> a) {
-    __shared__ __align__(128) Stage<T> st[2];
-    __shared__ __align__(8) uint64_t bar[2];
+    constexpr int NS = NSTAGE<T>, PD = NS - 1, NW = TILE / 32;  // PD: tiles staged ahead
+    __shared__ __align__(128) Stage<T> st[NS];
+    __shared__ __align__(8) uint64_t full[NS], empty[NS];
     const int64_t ntiles = (a.n + TILE - 1) / TILE;
     if (threadIdx.x == 0) {
-        mbar_init(&bar[0], 1);
-        mbar_init(&bar[1], 1);
+#pragma unroll
+        for (int q = 0; q < NS; ++q) {
+            mbar_init(&full[q], 1);
+            mbar_init(&empty[q], NW);
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
     const uint32_t step = *a.stepp;
-    int64_t t = blockIdx.x;
-    if (threadIdx.x == 0 && t < ntiles) stage_tile(a, st[0], &bar[0], t * TILE, (int)min((int64_t)TILE, a.n - t * TILE));
-    for (int k = 0; t < ntiles; t += gridDim.x, ++k) {
-        const int s = k & 1;
-        const int64_t tn = t + gridDim.x;
-        if (threadIdx.x == 0 && tn < ntiles) {
-            // the other stage was released by every thread at the end of the last tile
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            stage_tile(a, st[s ^ 1], &bar[s ^ 1], tn * TILE, (int)min((int64_t)TILE, a.n - tn * TILE));
+    const int64_t t0 = blockIdx.x, tstep = gridDim.x;
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int q = 0; q < PD; ++q) {
+            const int64_t tq = t0 + q * tstep;
+            if (tq < ntiles) stage_tile(a, st[q], &full[q], tq * TILE, (int)min((int64_t)TILE, a.n - tq * TILE));
         }
-        mbar_wait(&bar[s], (unsigned)((k >> 1) & 1), a.status);
+    }
+    int k = 0;
+    for (int64_t t = t0; t < ntiles; t += tstep, ++k) {
+        const int s = k % NS;
+        const int64_t tn = t + PD * tstep;
+        if (threadIdx.x == 0 && tn < ntiles) {
+            // stage (k + PD) mod NS = (k - 1) mod NS: every warp has released
+            // tile k - 1 from it (use (k - 1) / NS of that stage)
+            const int sp = (k + PD) % NS;
+            if (k >= 1) mbar_wait(&empty[sp], (unsigned)(((k - 1) / NS) & 1), a.status);
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            stage_tile(a, st[sp], &full[sp], tn * TILE, (int)min((int64_t)TILE, a.n - tn * TILE));
+        }
+        mbar_wait(&full[s], (unsigned)((k / NS) & 1), a.status);
         const int64_t i = t * TILE + threadIdx.x;
         if (i < a.n) {
             const Stage<T>& q = st[s];
@@ -437,7 +463,8 @@ __global__ void __launch_bounds__(TILE) k_step(const StepArgs<T> a) {
             advance_particle(a, step, (int)i, q.s[0][j], q.s[1][j], q.s[2][j], q.s[3][j], q.s[4][j], q.s[5][j], q.s[6][j],
                              q.id[j], q.elem[j], (int)q.bin[j]);
         }
-        __syncthreads();
+        __syncwarp();
+        if ((threadIdx.x & 31) == 0) mbar_arrive(&empty[s]);  // this warp is done with stage s
     }
 }
 
