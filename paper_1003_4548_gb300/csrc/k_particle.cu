@@ -415,9 +415,10 @@ __device__ __forceinline__ void stage_tile(const StepArgs<T>& a, Stage<T>& st, u
     bulk_to_smem(st.bin, a.bin + base, b1, bar);
 }
 
-// stages of the particle kernel: three for FP32 state (28 KB of static
-// shared memory), two for FP64 (33 KB; three would pass the 48 KB static limit)
-template <typename T> constexpr int NSTAGE = sizeof(T) == 4 ? 3 : 2;
+// stages of the particle kernel (FP32 state: 19 KB of static shared memory
+// per block; a third or fourth stage measured no faster, or slower, as the
+// staging takes L1 from the node and element gathers)
+template <typename T> constexpr int NSTAGE = 2;
 
 template <typename T>
 __global__ void __launch_bounds__(TILE) k_step(const StepArgs<T> a) {
