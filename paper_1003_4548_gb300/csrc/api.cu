@@ -377,6 +377,7 @@ int alloc_stats(pdf_ctx* c) {
     }
     PDF_CUDA(c, cudaMalloc(&c->npackT, ts * NODE_PACK_W * nn));
     PDF_CUDA(c, cudaMalloc(&c->epackT, ts * ELEM_PACK_W * nt));
+    PDF_CUDA(c, cudaMalloc(&c->eaffT, ts * ELEM_AFF_W * nt));
     PDF_CUDA(c, cudaMalloc(&c->ecmT, ts * (size_t)B * nt));
     // node statistics start at zero (a node without particles keeps its old value)
     PDF_CUDA(c, cudaMemset(c->nmean, 0, sizeof(double) * 4 * nn));
@@ -756,7 +757,7 @@ void pdf_destroy(pdf_ctx* c) {
                    m.aval, m.avf, m.diag, m.owall_node, m.owall_elem, m.pval, m.pin, c->eomw, c->nomw, c->pr_b, c->pr_x, c->pr_binv,
                    c->pr_a0inv, c->pres, c->egp, c->pr_iters, c->idA, c->idB, c->elemA, c->elemB, c->bin, c->cnt, c->off, c->cursor, c->scan_part, c->en,
                    c->emean, c->eR, c->epsivar, c->ecm, c->nwt, c->nmean, c->nR, c->nke, c->npsivar, c->eder,
-                   c->ngrad, c->npack, c->nwp, c->npackT, c->epackT, c->ecmT, c->sort_scratch, c->fe_f, c->fe_g,
+                   c->ngrad, c->npack, c->nwp, c->npackT, c->epackT, c->eaffT, c->ecmT, c->sort_scratch, c->fe_f, c->fe_g,
                    c->fe_prop, c->fe_z, c->fe_part, c->fe_bar, c->fe_iters, c->d_status,
                    c->conv_buf, c->elist, c->d_step, c->nsurT, c->pwp, c->avg_sum, c->avg_count, c->cdf_elem, c->cdf_hist, c->sur_w, c->sur_rows, c->sur_skip, c->sur_cnt, c->sur_part};
     for (void* p : dev) cudaFree(p);

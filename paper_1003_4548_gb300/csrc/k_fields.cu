@@ -277,6 +277,76 @@ __global__ void k_node_pack(int nn, const double* __restrict__ nmean, const doub
     for (int k = 0; k < NODE_PACK_W; ++k) npackT[(size_t)NODE_PACK_W * i + k] = (T)q[k];
 }
 
+// the node pack written as an affine function on each element: with the
+// barycentric coordinates l_k = a_k dx + b_k dy + c_k (dx, dy from the
+// element's reference point), sum_k l_k F_k = dx sum_k a_k F_k +
+// dy sum_k b_k F_k + sum_k c_k F_k, so a particle evaluates F0 + Fx dx + Fy dy
+// from one record of its element instead of three node records
+constexpr int AFF_THREADS = 128;  // elements per block of k_elem_affine
+
+template <typename T>
+__device__ __forceinline__ void load_row12(const T* __restrict__ p, T (&o)[12]) {
+    if constexpr (sizeof(T) == 4) {
+        const float4* q = reinterpret_cast<const float4*>(p);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const float4 v = __ldg(q + k);
+            o[4 * k] = v.x; o[4 * k + 1] = v.y; o[4 * k + 2] = v.z; o[4 * k + 3] = v.w;
+        }
+    } else {
+        const double2* q = reinterpret_cast<const double2*>(p);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            const double2 v = __ldg(q + k);
+            o[2 * k] = v.x; o[2 * k + 1] = v.y;
+        }
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(AFF_THREADS) k_elem_affine(int nt, const int* __restrict__ tri,
+                                                            const T* __restrict__ egeo,
+                                                            const T* __restrict__ npackT, T* eaff) {
+    // the block's records are assembled in shared memory, then written as one
+    // contiguous run with 16-byte stores
+    __shared__ __align__(16) T rec[AFF_THREADS * ELEM_AFF_W];
+    const int e0 = blockIdx.x * AFF_THREADS, e = e0 + threadIdx.x;
+    const int ne = min(AFF_THREADS, nt - e0);
+    if (e < nt) {
+        T g[12];
+        load_row12(egeo + (size_t)EGEO_W * e, g);
+        T F0[NODE_PACK_W], Fx[NODE_PACK_W], Fy[NODE_PACK_W];
+#pragma unroll
+        for (int q = 0; q < NODE_PACK_W; ++q) F0[q] = Fx[q] = Fy[q] = (T)0;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            T P[12];
+            load_row12(npackT + (size_t)NODE_PACK_W * tri[3 * e + k], P);
+            const T ak = g[2 + 3 * k], bk = g[3 + 3 * k], ck = g[4 + 3 * k];
+#pragma unroll
+            for (int q = 0; q < NODE_PACK_W; ++q) {
+                Fx[q] += ak * P[q];
+                Fy[q] += bk * P[q];
+                F0[q] += ck * P[q];
+            }
+        }
+        T* o = rec + ELEM_AFF_W * threadIdx.x;
+#pragma unroll
+        for (int q = 0; q < NODE_PACK_W; ++q) {
+            o[q] = F0[q];
+            o[NODE_PACK_W + q] = Fx[q];
+            o[2 * NODE_PACK_W + q] = Fy[q];
+        }
+    }
+    __syncthreads();
+    // ne records of ELEM_AFF_W values: 16-byte words (ELEM_AFF_W * sizeof(T) is a multiple of 16)
+    constexpr int VW = 16 / sizeof(T);
+    const int nwords = ne * ELEM_AFF_W / VW;
+    const float4* src = reinterpret_cast<const float4*>(rec);
+    float4* dst = reinterpret_cast<float4*>(eaff + (size_t)ELEM_AFF_W * e0);
+    for (int w = threadIdx.x; w < nwords; w += AFF_THREADS) dst[w] = src[w];
+}
+
 template <typename T>
 int run(pdf_ctx* c) {
     const int nn = c->m.nn, nt = c->m.nt, tb = 128;
@@ -325,7 +395,10 @@ int run(pdf_ctx* c) {
     timing_begin(c, PDF_K_FIELDS);
     k_node_pack<T><<<gn, tb, 0, c->s>>>(nn, c->nmean, c->nR, c->nke, c->m.rep, c->nwp, c->p, c->npack,
                                         (T*)c->npackT);
-    ++c->launches;
+    k_elem_affine<T><<<(nt + AFF_THREADS - 1) / AFF_THREADS, AFF_THREADS, 0, c->s>>>(
+        nt, c->m.tri, (const T*)(sizeof(T) == 8 ? (const void*)c->m.egeo_d : (const void*)c->m.egeo_f),
+        (const T*)c->npackT, (T*)c->eaffT);
+    c->launches += 2;
     if (er) PDF_CUDA(c, cudaStreamWaitEvent(c->s, c->side_join2, 0));  // the side stream joins back
     timing_end(c, PDF_K_FIELDS);
     PDF_CUDA(c, cudaGetLastError());

@@ -72,6 +72,7 @@ struct StepArgs {
     const T* __restrict__ egeo;
     const T* __restrict__ npack;
     const T* __restrict__ epack;
+    const T* __restrict__ eaff;  // node pack fields as F0 + Fx dx + Fy dy on each element
     const T* __restrict__ ecm;
     const double* __restrict__ nmean;
     const double* __restrict__ nR;
@@ -153,22 +154,27 @@ __device__ __forceinline__ void advance_particle(const StepArgs<T>& a, const uin
                                                  const T y, T u, T v, T w, T om, T psi, const uint32_t pid,
                                                  const int e0, const int b, const float* ysur = nullptr) {
 
-    // barycentric coordinates in the host element
+    // P1 interpolation of the node pack at the particle: the element's affine
+    // record, F = F0 + Fx dx + Fy dy with (dx, dy) from the element's
+    // reference point (the barycentric sum regrouped per element)
     T g[EGEO_W];
     load_pack<EGEO_W>(a.egeo + EGEO_W * e0, g);
     const T dx = x - g[0], dy = y - g[1];
-    const T l0 = g[2] * dx + g[3] * dy + g[4];
-    const T l1 = g[5] * dx + g[6] * dy + g[7];
-    const T l2 = g[8] * dx + g[9] * dy + g[10];
-    const int n0 = a.tri[3 * e0], n1 = a.tri[3 * e0 + 1], n2 = a.tri[3 * e0 + 2];
+    T lw[3] = {(T)0, (T)0, (T)0};  // barycentric coordinates, for the per-particle network's features
+    if constexpr (SUR) {
+        lw[0] = g[2] * dx + g[3] * dy + g[4];
+        lw[1] = g[5] * dx + g[6] * dy + g[7];
+        lw[2] = g[8] * dx + g[9] * dy + g[10];
+    }
     T F[NODE_PACK_W];
     {
-        T A[NODE_PACK_W], Bv[NODE_PACK_W], Cv[NODE_PACK_W];
-        load_pack<NODE_PACK_W>(a.npack + NODE_PACK_W * n0, A);
-        load_pack<NODE_PACK_W>(a.npack + NODE_PACK_W * n1, Bv);
-        load_pack<NODE_PACK_W>(a.npack + NODE_PACK_W * n2, Cv);
+        T F0[NODE_PACK_W], Fx[NODE_PACK_W], Fy[NODE_PACK_W];
+        const T* r = a.eaff + (size_t)ELEM_AFF_W * e0;
+        load_pack<NODE_PACK_W>(r, F0);
+        load_pack<NODE_PACK_W>(r + NODE_PACK_W, Fx);
+        load_pack<NODE_PACK_W>(r + 2 * NODE_PACK_W, Fy);
 #pragma unroll
-        for (int q = 0; q < 11; ++q) F[q] = l0 * A[q] + l1 * Bv[q] + l2 * Cv[q];
+        for (int q = 0; q < 11; ++q) F[q] = F0[q] + Fx[q] * dx + Fy[q] * dy;
     }
     if constexpr (SUR) {
         if (ysur != nullptr) {
@@ -176,8 +182,7 @@ __device__ __forceinline__ void advance_particle(const StepArgs<T>& a, const uin
             // then G_ij and C0 eps from it as Eqs. Gij and C0 do at the nodes,
             // with k, eps and the stresses interpolated to the particle
             float kk = 0.f, ee = 0.f, R[4] = {0.f, 0.f, 0.f, 0.f};
-            const int nd[3] = {n0, n1, n2};
-            const T lw[3] = {l0, l1, l2};
+            const int nd[3] = {a.tri[3 * e0], a.tri[3 * e0 + 1], a.tri[3 * e0 + 2]};
 #pragma unroll
             for (int m = 0; m < 3; ++m) {
                 const float4 ke = __ldg(reinterpret_cast<const float4*>(a.nsur + 16 * (size_t)nd[m]) + 2);
@@ -524,6 +529,7 @@ StepArgs<T> step_args(pdf_ctx* c, double dt) {
     a.egeo = (const T*)(sizeof(T) == 8 ? (const void*)c->m.egeo_d : (const void*)c->m.egeo_f);
     a.npack = (const T*)c->npackT;
     a.epack = (const T*)c->epackT;
+    a.eaff = (const T*)c->eaffT;
     a.ecm = (const T*)c->ecmT;
     a.nmean = c->nmean;
     a.nR = c->nR;

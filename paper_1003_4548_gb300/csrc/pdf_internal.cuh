@@ -27,6 +27,7 @@ constexpr int STATS_CAP = 2048;     // particles per element held in shared memo
 constexpr int NODE_PACK_W = 12;     // <U>,<V>,<omega>,C0eps,G11,G12,G21,G22,G33,Fx,Fy,0
 constexpr int ELEM_PACK_W = 8;      // Ux,Uy,Vx,Vy,lapU,lapV,S_omega,t_m
 constexpr int EGEO_W = 12;          // xref,yref,(ax,ay,c) x 3, area
+constexpr int ELEM_AFF_W = 36;      // the node pack as an affine function on the element: F0, dF/dx, dF/dy
 
 // element -> sort key of the velocity-bin construction (16 bytes)
 struct SortKey {
@@ -121,6 +122,7 @@ struct pdf_ctx {
     // particle-kernel copies in the state precision
     void* npackT = nullptr;
     void* epackT = nullptr;
+    void* eaffT = nullptr;  // ELEM_AFF_W*nt in the state type: node pack fields affine on each element
     void* ecmT = nullptr;
     // crowded-element lists of the FP32 moments path: 2 counters, then 2 x nt ids
     int* elist = nullptr;
