@@ -3,8 +3,9 @@
 //
 // Per step: the right-hand side f_ij = 1/2 (1 - C1) k <omega> delta_ij +
 // k H_ijkl d<U_k>/dx_l at the nodes (statistically two-dimensional field:
-// in-plane wp_11, wp_12, wp_21, wp_22 and wp_33), the wall values
-// wp_ij = -er_wall eps n_i n_j, and the Galerkin system (M + K_{L^2}) wp = M f
+// in-plane wp_11, wp_12, wp_21, wp_22 and wp_33) and the wall values
+// wp_ij = -er_wall eps n_i n_j (both formed in the node gradient kernel of
+// k_fields.cu, from the node's own gradient), and the Galerkin system (M + K_{L^2}) wp = M f
 // over the periodic-merged nodes, solved for the five components at once by
 // Jacobi-preconditioned CG in FP64 (warm start from the previous step).
 //
@@ -22,62 +23,6 @@
 namespace {
 
 constexpr int NC = 5;
-constexpr int FE_THREADS = 256;
-
-__global__ void k_fe_rhs(int nn, const double* __restrict__ nR, const double* __restrict__ ngrad,
-                         const double* __restrict__ nke, const double* __restrict__ nmean,
-                         const unsigned char* __restrict__ is_wall, const double* __restrict__ wn, pdf_params p,
-                         double* f, double* g, const double* __restrict__ prev, double* __restrict__ prop) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= nn) return;
-    const double* R = nR + 6 * (size_t)i;
-    const double* gr = ngrad + 4 * (size_t)i;
-    const double k = nke[2 * i];
-    double om = nmean[4 * i + 3];
-    om = om > p.floor_omega ? om : p.floor_omega;
-    const double gg[2][2] = {{gr[0], gr[1]}, {gr[2], gr[3]}};
-    const double Rm[2][2] = {{R[0], R[3]}, {R[3], R[1]}};
-    const double tr = R[0] + R[1] + R[2];
-    double b[2][2] = {{0, 0}, {0, 0}};
-    // one FP64 division per quotient at most (GB300's FP64 pipe is narrow):
-    // the anisotropy from the reciprocal of the trace, gamma5 / 3 as a product
-    if (tr > 0.0) {
-        const double itr = 1.0 / tr;
-        for (int a = 0; a < 2; ++a)
-            for (int c = 0; c < 2; ++c) b[a][c] = Rm[a][c] * itr - (a == c ? 1.0 / 3.0 : 0.0);
-    }
-    const double det = R[2] * (R[0] * R[1] - R[3] * R[3]);
-    const double tk = 2.0 / 3.0 * k;
-    double Av = p.Cv * det / (tk * tk * tk);
-    Av = Av < 1.0 ? Av : 1.0;
-    const double iso = 0.5 * (1.0 - p.C1) * k * om;
-    const double g3 = p.gamma5 * (1.0 / 3.0);
-    int q = 0;
-    for (int a = 0; a < 2; ++a)
-        for (int c = 0; c < 2; ++c) {
-            double t = (p.C2 * Av + g3) * gg[a][c] - g3 * gg[c][a];
-            for (int m = 0; m < 2; ++m) t += p.gamma5 * b[a][m] * gg[m][c];
-            for (int l = 0; l < 2; ++l) t -= p.gamma5 * b[a][l] * gg[c][l];
-            f[NC * (size_t)i + q++] = (a == c ? iso : 0.0) + (p.rotta ? 0.0 : k * t);
-        }
-    f[NC * (size_t)i + 4] = iso;
-    const bool wall = is_wall[i];
-    if (wall) {
-        const double eps = nke[2 * i + 1], nx = wn[2 * i], ny = wn[2 * i + 1];
-        const double gw[NC] = {-p.er_wall * eps * nx * nx, -p.er_wall * eps * nx * ny, -p.er_wall * eps * ny * nx,
-                               -p.er_wall * eps * ny * ny, 0.0};
-#pragma unroll
-        for (int k = 0; k < NC; ++k) {
-            g[NC * (size_t)i + k] = gw[k];
-            if (prop != nullptr) prop[NC * (size_t)i + k] = gw[k];
-        }
-    } else if (prop != nullptr) {
-        // lagged FE mode: the proposal is the previous solution at the free
-        // rows (the Dirichlet values above at the walls)
-#pragma unroll
-        for (int k = 0; k < NC; ++k) prop[NC * (size_t)i + k] = prev[NC * (size_t)i + k];
-    }
-}
 
 // values of M + K_{L^2} (Eq. elliptic-relaxation in Galerkin form): each
 // nonzero is its mass entry plus the L^2-weighted stiffness contributions of
@@ -682,11 +627,9 @@ int launch_fe_assemble(pdf_ctx* c, cudaStream_t s) {
 int launch_elliptic(pdf_ctx* c) {
     const int nn = c->m.nn;
     timing_begin(c, PDF_K_ELLIPTIC);
-    k_fe_rhs<<<(nn + 127) / 128, 128, 0, c->s>>>(nn, c->nR, c->ngrad, c->nke, c->nmean, c->m.is_wall, c->m.wn,
-                                                c->p, c->fe_f, c->fe_g, c->sur_mode == 5 ? c->nwp : nullptr,
-                                                c->sur_mode == 5 ? c->fe_prop : nullptr);
-    ++c->launches;
-    // the assembly was launched on the side stream after the element fields
+    // the right-hand side (and the lagged proposal) was written by the node
+    // gradient kernel; the assembly was launched on the side stream after the
+    // element fields
     PDF_CUDA(c, cudaStreamWaitEvent(c->s, c->side_join, 0));
     PDF_CUDA(c, cudaGetLastError());
     if (c->sur_mode) {

@@ -190,8 +190,78 @@ __global__ void k_elem_derived(int nt, const int* __restrict__ tri, const double
     ep[6] = (T)d[6]; ep[7] = (T)d[7];
 }
 
+// right-hand side of Eq. elliptic-relaxation at node i (the source f of the
+// five components wp11, wp12, wp21, wp22, wp33 with Eq. H: the isotropic part
+// and, unless the Rotta variant of Section 4 drops it, the H_ijkl term from
+// the node's gradient gr), the Dirichlet value wp_ij = -er_wall eps n_i n_j at
+// a wall node (the resolved-wall reading), and in the lagged FE mode the
+// proposal (the previous solution at the free rows, the Dirichlet values at
+// the walls)
+struct RhsArgs {
+    const double* __restrict__ nR;
+    const double* __restrict__ nke;
+    const double* __restrict__ nmean;
+    const unsigned char* __restrict__ is_wall;
+    const double* __restrict__ wn;
+    double* f;     // NULL: no elliptic relaxation
+    double* g;
+    const double* __restrict__ prev;
+    double* __restrict__ prop;  // NULL unless the lagged FE mode
+};
+
+__device__ __forceinline__ void fe_rhs_node(int i, const double (&gr)[4], const RhsArgs& r, const pdf_params& p) {
+    constexpr int NC = 5;
+    const double* R = r.nR + 6 * (size_t)i;
+    const double k = r.nke[2 * i];
+    double om = r.nmean[4 * i + 3];
+    om = om > p.floor_omega ? om : p.floor_omega;
+    const double gg[2][2] = {{gr[0], gr[1]}, {gr[2], gr[3]}};
+    const double Rm[2][2] = {{R[0], R[3]}, {R[3], R[1]}};
+    const double tr = R[0] + R[1] + R[2];
+    double b[2][2] = {{0, 0}, {0, 0}};
+    // one FP64 division per quotient at most (GB300's FP64 pipe is narrow):
+    // the anisotropy from the reciprocal of the trace, gamma5 / 3 as a product
+    if (tr > 0.0) {
+        const double itr = 1.0 / tr;
+        for (int a = 0; a < 2; ++a)
+            for (int c = 0; c < 2; ++c) b[a][c] = Rm[a][c] * itr - (a == c ? 1.0 / 3.0 : 0.0);
+    }
+    const double det = R[2] * (R[0] * R[1] - R[3] * R[3]);
+    const double tk = 2.0 / 3.0 * k;
+    double Av = p.Cv * det / (tk * tk * tk);
+    Av = Av < 1.0 ? Av : 1.0;
+    const double iso = 0.5 * (1.0 - p.C1) * k * om;
+    const double g3 = p.gamma5 * (1.0 / 3.0);
+    int q = 0;
+    for (int a = 0; a < 2; ++a)
+        for (int c = 0; c < 2; ++c) {
+            double t = (p.C2 * Av + g3) * gg[a][c] - g3 * gg[c][a];
+            for (int m = 0; m < 2; ++m) t += p.gamma5 * b[a][m] * gg[m][c];
+            for (int l = 0; l < 2; ++l) t -= p.gamma5 * b[a][l] * gg[c][l];
+            r.f[NC * (size_t)i + q++] = (a == c ? iso : 0.0) + (p.rotta ? 0.0 : k * t);
+        }
+    r.f[NC * (size_t)i + 4] = iso;
+    if (r.is_wall[i]) {
+        const double eps = r.nke[2 * i + 1], nx = r.wn[2 * i], ny = r.wn[2 * i + 1];
+        const double gw[NC] = {-p.er_wall * eps * nx * nx, -p.er_wall * eps * nx * ny, -p.er_wall * eps * ny * nx,
+                               -p.er_wall * eps * ny * ny, 0.0};
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            r.g[NC * (size_t)i + c] = gw[c];
+            if (r.prop != nullptr) r.prop[NC * (size_t)i + c] = gw[c];
+        }
+    } else if (r.prop != nullptr) {
+#pragma unroll
+        for (int c = 0; c < NC; ++c) r.prop[NC * (size_t)i + c] = r.prev[NC * (size_t)i + c];
+    }
+}
+
+// node gradients of the mean velocity (area-weighted element gradients), and
+// with elliptic relaxation the node's FE right-hand side from them, which
+// needs nothing of other nodes
 __global__ void k_node_grad(int nn, const int* __restrict__ n2e_off, const int* __restrict__ n2e,
-                            const double* __restrict__ area, const double* __restrict__ eder, double* ngrad) {
+                            const double* __restrict__ area, const double* __restrict__ eder, double* ngrad,
+                            const RhsArgs rhs, const pdf_params p) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nn) return;
     double a = 0, g[4] = {0, 0, 0, 0};
@@ -211,8 +281,13 @@ __global__ void k_node_grad(int nn, const int* __restrict__ n2e_off, const int* 
         }
     }
     const double ia = 1.0 / a;
+    double gr[4];
 #pragma unroll
-    for (int k = 0; k < 4; ++k) ngrad[4 * i + k] = g[k] * ia;
+    for (int k = 0; k < 4; ++k) {
+        gr[k] = g[k] * ia;
+        ngrad[4 * i + k] = gr[k];
+    }
+    if (rhs.f != nullptr) fe_rhs_node(i, gr, rhs, p);
 }
 
 template <typename T>
@@ -369,7 +444,13 @@ int run(pdf_ctx* c) {
         TRY_OK(launch_fe_assemble(c, c->s2));
         PDF_CUDA(c, cudaEventRecord(c->side_join, c->s2));
     }
-    k_node_grad<<<gn, tb, 0, c->s>>>(nn, c->m.n2e_off, c->m.n2e, c->m.area, c->eder, c->ngrad);
+    RhsArgs rhs;
+    rhs.nR = c->nR; rhs.nke = c->nke; rhs.nmean = c->nmean; rhs.is_wall = c->m.is_wall; rhs.wn = c->m.wn;
+    rhs.f = er ? c->fe_f : nullptr;
+    rhs.g = c->fe_g;
+    rhs.prev = c->nwp;
+    rhs.prop = er && c->sur_mode == 5 ? c->fe_prop : nullptr;
+    k_node_grad<<<gn, tb, 0, c->s>>>(nn, c->m.n2e_off, c->m.n2e, c->m.area, c->eder, c->ngrad, rhs, c->p);
     if (er) {
         PDF_CUDA(c, cudaEventRecord(c->side_fork, c->s));
         PDF_CUDA(c, cudaStreamWaitEvent(c->s2, c->side_fork, 0));
