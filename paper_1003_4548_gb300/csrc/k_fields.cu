@@ -424,7 +424,10 @@ __global__ void __launch_bounds__(AFF_THREADS) k_elem_affine(int nt, const int* 
 
 template <typename T>
 int run(pdf_ctx* c) {
-    const int nn = c->m.nn, nt = c->m.nt, tb = 128;
+    // one warp per block: these kernels are bound by GB300's FP64 pipe, and
+    // with 20.5k nodes (40k elements) larger blocks leave some SMs with twice
+    // the work of others
+    const int nn = c->m.nn, nt = c->m.nt, tb = 32;
     const unsigned gn = (nn + tb - 1) / tb, ge = (nt + tb - 1) / tb;
     timing_begin(c, PDF_K_FIELDS);
     k_node_stats<<<gn, tb, 0, c->s>>>(nn, c->m.n2e_off, c->m.n2e, c->en, c->emean, c->eR, c->epsivar, c->p,
