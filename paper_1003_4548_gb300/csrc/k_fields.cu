@@ -1,16 +1,19 @@
 // k_fields.cu -- node averages, derived element fields and the particle packs.
 //
-// FP64 throughout (a few doubles per node and element):
+// FP64 (a few doubles per node and element; in the compensated-FP32 form the
+// roots of t_m and L are taken in FP32):
 //  * node statistics: particle-count weighted means over the incident
 //    elements (periodic partners merged), k = <u_i u_i>/2 and
 //    Eq. dissipation-from-frequency eps = <omega>(k + nu C_T^2 <omega>);
 //  * element: P1 gradient of <U>, production P = -<u_i u_j> d<U_i>/dx_j,
 //    Eq. frequency_source S_omega, Eq. micromixing-timescale t_m and the
 //    length scale of Eq. L at the centroid;
-//  * node gradient recovery (area-weighted) and the element Laplacian;
+//  * node gradient recovery (area-weighted), with elliptic relaxation the
+//    node's FE right-hand side from it, and the element Laplacian;
 //  * node pack for the particle kernel: <U>, <V>, <omega>, C0 eps and G_ij
 //    (Eq. wall-GandC, or Eqs. Gij and C0 from the elliptic relaxation), and
-//    the imposed mean driving force;
+//    the imposed mean driving force; then the same pack as an affine function
+//    on each element (the record the particle kernel interpolates from);
 //  * with the Section 4 frequency reflection: <omega u_i> and <omega u_i u_j>
 //    (in-plane, fluctuations about the element mean) in the elements around
 //    the wall nodes, then their count-weighted means at the wall nodes.

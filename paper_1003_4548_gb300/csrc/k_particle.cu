@@ -6,7 +6,8 @@
 // the statistics S^n (forward Euler-Maruyama, end of Section 2.2):
 //   Eq. IECM           psi <- psi - r (psi - <phi|V>_bin),  r = dt/t_m
 //   Eq. frequency-model, Eq. frequency_source
-//   Eq. Lagrangian-velocity (G_ij and C0 eps interpolated from the nodes)
+//   Eq. Lagrangian-velocity (G_ij and C0 eps interpolated from the nodes,
+//   through the element's affine record of the node pack)
 //   Eq. Lagrangian-position with the velocity at step n
 //   boundaries: periodic seams, symmetry top, wall reflections
 //   (Eqs. wall-normal-velocity .. wall-omega, or specular no-slip), the
