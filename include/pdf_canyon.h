@@ -281,10 +281,26 @@ typedef struct pdf_batch pdf_batch;
  * estimated statistics and created with its own non-NULL stream, distinct
  * from the others and from cuda_stream (PDF_ERR_ARG otherwise). Nothing is
  * executed by this call; per-context launch set-up (grids, attributes) is
- * done first. The contexts must not be stepped or destroyed by other calls
- * while the batch exists. Returns PDF_ERR_CUDA if the capture or the
+ * done first. The contexts must not be stepped, given new particles
+ * (pdf_seed_particles and pdf_set_particles re-sort the ensemble, which moves
+ * it between the context's two state buffers, while the graph keeps the
+ * buffers it was captured with) or destroyed by other calls while the batch
+ * exists; create the batch after loading the particles. Returns PDF_ERR_CUDA if the capture or the
  * instantiation fails (message in pdf_last_error(NULL)). */
 int pdf_batch_create(pdf_ctx* const* ctx, const double* dt, int32_t n, void* cuda_stream, pdf_batch** out);
+
+/* pdf_batch_create with per-step results: after each of the two captured
+ * steps of context i, the graph copies field `field` (any PDF_FIELD_* id that
+ * pdf_get_fields accepts for that context) into the caller's device buffer
+ * out_dev[2 i + k] (k = 0 after the first step of the pair, k = 1 after the
+ * second), field_bytes[i] bytes (the field's size in context i, as
+ * pdf_get_fields requires; PDF_ERR_ARG otherwise). The buffers stay the
+ * caller's and must outlive the batch; every graph launch overwrites them,
+ * so read them on cuda_stream (e.g. an asynchronous copy to pinned host
+ * memory) before the next pdf_batch_step. Other arguments and errors as
+ * pdf_batch_create. */
+int pdf_batch_create_out(pdf_ctx* const* ctx, const double* dt, int32_t n, void* cuda_stream, int32_t field,
+                         void* const* out_dev, const size_t* field_bytes, pdf_batch** out);
 
 /* Advance every context by nsteps (even; PDF_ERR_ARG otherwise): nsteps/2
  * launches of the graph on the batch stream (asynchronous). */

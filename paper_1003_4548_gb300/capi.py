@@ -59,7 +59,7 @@ EXPORTS = ("pdf_default_params", "pdf_init_mesh", "pdf_seed_particles", "pdf_set
            "pdf_destroy", "pdf_sort_by_element_static", "pdf_mlp_work_floats", "pdf_mlp_forward",
            "pdf_mlp_loss_grad", "pdf_mlp_adam", "pdf_mlp_column_stats", "pdf_mlp_gather_rows",
            "pdf_mlp_standardize", "pdf_surrogate_rows", "pdf_surrogate_harvest", "pdf_set_surrogate",
-           "pdf_surrogate_stats", "pdf_batch_create", "pdf_batch_step", "pdf_batch_sync", "pdf_batch_destroy",
+           "pdf_surrogate_stats", "pdf_batch_create", "pdf_batch_create_out", "pdf_batch_step", "pdf_batch_sync", "pdf_batch_destroy",
            "pdf_autotune", "pdf_set_averaging", "pdf_averaging_count", "pdf_get_averages", "pdf_probe",
            "pdf_set_cdf_probes", "pdf_get_cdf")
 
@@ -126,6 +126,7 @@ def lib(allow_build: bool = True):
         L.pdf_set_surrogate.argtypes = [vp, C.c_int32, P(C.c_float), P(C.c_float), C.c_double]
         L.pdf_surrogate_stats.argtypes = [vp, P(C.c_int64), P(C.c_int64), d]
         L.pdf_batch_create.argtypes = [P(vp), d, C.c_int32, vp, P(vp)]
+        L.pdf_batch_create_out.argtypes = [P(vp), d, C.c_int32, vp, C.c_int32, P(vp), P(C.c_size_t), P(vp)]
         L.pdf_batch_step.argtypes = [vp, C.c_int32]
         L.pdf_batch_sync.argtypes = [vp, i32]
         L.pdf_batch_destroy.argtypes = [vp]
@@ -410,13 +411,25 @@ class Canyon:
 class Batch:
     """One CUDA graph holding a time step of several contexts (pdf_batch_*)."""
 
-    def __init__(self, canyons, dts, stream: int):
+    def __init__(self, canyons, dts, stream: int, outputs=None):
+        """outputs: None, or (field name, 2n device pointers, n byte counts) for
+        pdf_batch_create_out (the field after each of the two captured steps
+        of every context)."""
         L = lib()
         self.canyons = list(canyons)
-        hs = (C.c_void_p * len(self.canyons))(*[c.handle.value for c in self.canyons])
-        dt = (C.c_double * len(self.canyons))(*[float(x) for x in dts])
+        n = len(self.canyons)
+        hs = (C.c_void_p * n)(*[c.handle.value for c in self.canyons])
+        dt = (C.c_double * n)(*[float(x) for x in dts])
         h = C.c_void_p()
-        st = L.pdf_batch_create(hs, dt, len(self.canyons), C.c_void_p(stream), C.byref(h))
+        if outputs is None:
+            st = L.pdf_batch_create(hs, dt, n, C.c_void_p(stream), C.byref(h))
+        else:
+            name, ptrs, nbytes = outputs
+            if len(ptrs) != 2 * n or len(nbytes) != n:
+                raise ValueError("outputs: 2 device pointers and one byte count per context")
+            pv = (C.c_void_p * (2 * n))(*[int(q) for q in ptrs])
+            bv = (C.c_size_t * n)(*[int(q) for q in nbytes])
+            st = L.pdf_batch_create_out(hs, dt, n, C.c_void_p(stream), FIELD[name], pv, bv, C.byref(h))
         if st != PDF_OK:
             raise PdfError(st, L.pdf_last_error(None).decode())
         self._h = h

@@ -634,8 +634,11 @@ int pdf_sync(pdf_ctx* c) {
     return PDF_OK;
 }
 
-int pdf_get_fields(pdf_ctx* c, int32_t field, void* dst, size_t bytes, int32_t dst_is_device) {
-    if (!c || !dst || dst_is_device < 0 || dst_is_device > 2) return PDF_ERR_ARG;
+}  // extern "C"
+
+// device source, size in bytes and FP64 conversion of a field (the mapping
+// behind pdf_get_fields; also used to check a batch's output sizes)
+int field_source(pdf_ctx* c, int32_t field, const void** src_out, size_t* need_out, bool* convert_out) {
     const int64_t n = c->np;
     const int nt = c->m.nt, nn = c->m.nn;
     const void* src = nullptr;
@@ -676,6 +679,21 @@ int pdf_get_fields(pdf_ctx* c, int32_t field, void* dst, size_t bytes, int32_t d
         src = c->pwp; need = 4 * 5 * (size_t)n; break;
     default: return fail(c, PDF_ERR_ARG, "unknown field id");
     }
+    *src_out = src;
+    *need_out = need;
+    *convert_out = convert;
+    return PDF_OK;
+}
+
+extern "C" {
+
+int pdf_get_fields(pdf_ctx* c, int32_t field, void* dst, size_t bytes, int32_t dst_is_device) {
+    if (!c || !dst || dst_is_device < 0 || dst_is_device > 2) return PDF_ERR_ARG;
+    const int64_t n = c->np;
+    const void* src = nullptr;
+    size_t need = 0;
+    bool convert = false;
+    TRY(field_source(c, field, &src, &need, &convert));
     if (bytes != need) return fail(c, PDF_ERR_ARG, "field size mismatch: expected " + std::to_string(need));
     if (need == 0) return PDF_OK;
     if (convert) {

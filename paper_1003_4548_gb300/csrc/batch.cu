@@ -44,12 +44,19 @@ int cuda_fail(const char* what, cudaError_t e) {
 
 }  // namespace
 
+// the field mapping of pdf_get_fields (api.cu)
+int field_source(pdf_ctx* c, int32_t field, const void** src, size_t* need, bool* convert);
+
 extern "C" {
 
-int pdf_batch_create(pdf_ctx* const* ctx, const double* dt, int32_t n, void* cuda_stream, pdf_batch** out) {
+int pdf_batch_create_out(pdf_ctx* const* ctx, const double* dt, int32_t n, void* cuda_stream, int32_t field,
+                         void* const* fout, const size_t* fbytes, pdf_batch** out) {
     if (!out) return fail(nullptr, PDF_ERR_ARG, "pdf_batch_create: out is NULL");
     *out = nullptr;
     if (!ctx || !dt || n < 1 || !cuda_stream) return fail(nullptr, PDF_ERR_ARG, "pdf_batch_create: bad arguments");
+    if (fout && !fbytes) return fail(nullptr, PDF_ERR_ARG, "pdf_batch_create_out: bytes is NULL");
+    for (int i = 0; fout && i < 2 * n; ++i)
+        if (!fout[i]) return fail(nullptr, PDF_ERR_ARG, "pdf_batch_create_out: NULL output buffer");
     for (int i = 0; i < n; ++i) {
         pdf_ctx* c = ctx[i];
         if (!c || !c->s || c->s == (cudaStream_t)cuda_stream || !(dt[i] > 0) || !c->stats_valid)
@@ -58,6 +65,18 @@ int pdf_batch_create(pdf_ctx* const* ctx, const double* dt, int32_t n, void* cud
         for (int j = 0; j < i; ++j)
             if (ctx[j] == c || ctx[j]->s == c->s)
                 return fail(nullptr, PDF_ERR_ARG, "pdf_batch_create: contexts and streams must be distinct");
+    }
+    // output sizes checked before the capture (a failure inside it would leave
+    // a context with a step captured and its state buffers swapped)
+    for (int i = 0; fout && i < n; ++i) {
+        const void* src = nullptr;
+        size_t need = 0;
+        bool convert = false;
+        const int st = field_source(ctx[i], field, &src, &need, &convert);
+        if (st != PDF_OK) return fail(nullptr, st, "pdf_batch_create_out: context " + std::to_string(i) + ": " + ctx[i]->err);
+        if (fbytes[i] != need)
+            return fail(nullptr, PDF_ERR_ARG, "pdf_batch_create_out: context " + std::to_string(i) +
+                                                  ": field size mismatch, expected " + std::to_string(need));
     }
     // launch set-up outside the capture
     for (int i = 0; i < n; ++i) {
@@ -99,6 +118,9 @@ int pdf_batch_create(pdf_ctx* const* ctx, const double* dt, int32_t n, void* cud
             c->coop_done = chain;
             st = pdf_step(c, dt[i], 1);
             if (c->launches > l0 && (c->p.wall_model == PDF_ELLIPTIC_RELAXATION || c->p.pressure)) chained = true;
+            // the requested field after this step: an asynchronous device copy on
+            // the context stream, captured as a node of the graph
+            if (st == PDF_OK && fout) st = pdf_get_fields(c, field, fout[2 * i + k], fbytes[i], 1);
             b->launches[i] += c->launches - l0;
             c->launches = l0;
             c->coop_wait = c->coop_done = nullptr;
@@ -153,6 +175,10 @@ int pdf_batch_sync(pdf_batch* b, int32_t* failed) {
         }
     }
     return PDF_OK;
+}
+
+int pdf_batch_create(pdf_ctx* const* ctx, const double* dt, int32_t n, void* cuda_stream, pdf_batch** out) {
+    return pdf_batch_create_out(ctx, dt, n, cuda_stream, 0, nullptr, nullptr, out);
 }
 
 void pdf_batch_destroy(pdf_batch* b) {

@@ -145,3 +145,43 @@ def test_batch_graph_fp32_lagged_and_pressure(torch):
     b.close()
     for g in batched + alone:
         g.close()
+
+
+def test_batch_outputs_per_step(torch):
+    """pdf_batch_create_out: the graph copies the element means after each of
+    its two steps into the caller's device buffers, overwritten by every
+    replay. They equal the means of the same cases stepped one step at a time
+    (FP64 reductions, deterministic)."""
+    from paper_1003_4548_gb300 import capi
+    cs = cases()[:2]
+    streams = [torch.cuda.Stream() for _ in range(2 * len(cs) + 1)]
+    batched = [make(torch, m, ppe, wm, k, streams[k]) for m, ppe, wm, k in cs]
+    alone = [make(torch, m, ppe, wm, k, streams[len(cs) + k]) for m, ppe, wm, k in cs]
+    dts = [cfl_dt(m, cfl=0.5, k0=1e-3) for m, _, _, _ in cs]
+    bufs = [torch.zeros((g.nt, 5), dtype=torch.float64, device="cuda") for g in batched for _ in range(2)]
+    nbytes = [g.nt * 5 * 8 for g in batched]
+    with pytest.raises(capi.PdfError):  # a byte count that is not the field's size
+        capi.Batch(batched, dts, streams[-1].cuda_stream,
+                   outputs=("elem_mean", [t.data_ptr() for t in bufs], [b + 8 for b in nbytes]))
+    b = capi.Batch(batched, dts, streams[-1].cuda_stream,
+                   outputs=("elem_mean", [t.data_ptr() for t in bufs], nbytes))
+    expect = []
+    for g, dt in zip(alone, dts):
+        per = []
+        for _ in range(4):
+            g.step(dt, 1)
+            g.sync()
+            per.append(g.field("elem_mean"))
+        expect.append(per)
+    for pair in range(2):
+        b.step(2)
+        b.sync()
+        for j in range(len(batched)):
+            for k in range(2):
+                got = bufs[2 * j + k].cpu().numpy()
+                assert np.array_equal(got, expect[j][2 * pair + k]), (j, pair, k)
+    for g in batched:
+        assert g.step_index == 4
+    b.close()
+    for g in batched + alone:
+        g.close()
