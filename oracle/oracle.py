@@ -50,48 +50,61 @@ def build(force: bool = False) -> str:
     os.makedirs(BUILD_DIR, exist_ok=True)
     if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < max(
             os.path.getmtime(SRC), os.path.getmtime(os.path.join(HERE, "pdf_oracle.h"))):
-        tmp = LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared",
-                               "-o", tmp, SRC, "-lm"])
-        os.replace(tmp, LIB)
+        compile_source(SRC, LIB)
     return LIB
+
+
+def compile_source(src: str, out: str) -> str:
+    """Compile one copy of the oracle's C source into a shared library (the
+    mutation pins build altered copies with the same flags)."""
+    tmp = out + f".tmp{os.getpid()}"
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared",
+                           "-I", HERE, "-o", tmp, src, "-lm"])
+    os.replace(tmp, out)
+    return out
+
+
+def load(path: str):
+    """Open an oracle library and declare its entry points."""
+    L = C.CDLL(path)
+    P = C.POINTER
+    d, i32, u8, u32 = P(C.c_double), P(C.c_int32), P(C.c_uint8), P(C.c_uint32)
+    L.orc_create.restype = C.c_void_p
+    L.orc_create.argtypes = [P(orc_params), C.c_int32, d, C.c_int32, i32, i32, i32, i32]
+    L.orc_destroy.argtypes = [C.c_void_p]
+    L.orc_num_particles.argtypes = [C.c_void_p]
+    L.orc_step_index.argtypes = [C.c_void_p]
+    L.orc_cg_iterations.argtypes = [C.c_void_p]
+    L.orc_seed.argtypes = [C.c_void_p, C.c_int32]
+    L.orc_set_particles.argtypes = [C.c_void_p, C.c_int32] + [d] * 7 + [u32, i32, C.c_int32]
+    L.orc_get_particles.argtypes = [C.c_void_p] + [d] * 7 + [u32, i32, u8]
+    L.orc_estimate_stats.argtypes = [C.c_void_p]
+    L.orc_advance.argtypes = [C.c_void_p, C.c_double]
+    L.orc_project.argtypes = [C.c_void_p, C.c_double]
+    L.orc_step.argtypes = [C.c_void_p, C.c_double, C.c_int32]
+    L.orc_advance_subset.argtypes = [C.c_void_p, C.c_double, i32, C.c_int32]
+    L.orc_get_field.argtypes = [C.c_void_p, C.c_int32, d]
+    L.orc_philox4x32_10.argtypes = [u32, u32, u32]
+    L.orc_philox4x32_10.restype = None
+    L.orc_gauss8.argtypes = [C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint32, d]
+    L.orc_gauss8.restype = None
+    L.orc_locate.argtypes = [C.c_void_p, C.c_double, C.c_double]
+    L.orc_reflect.argtypes = [C.c_void_p, C.c_int32, d, d, d, d, d, d]
+    L.orc_sde.argtypes = [P(orc_params), C.c_int32, C.c_double, d, d, d, d, d, d, d]
+    L.orc_sde.restype = None
+    L.orc_fe_solve.argtypes = [C.c_void_p, d, d, d, u8, d, C.c_int32]
+    L.orc_bins.argtypes = [P(orc_params), C.c_int32, d, d, d, u32, i32]
+    L.orc_set_node_fields.argtypes = [C.c_void_p, d, d, d]
+    L.orc_set_node_wp.argtypes = [C.c_void_p, d]
+    L.orc_h_contract.argtypes = [P(orc_params), d, d, C.c_double, C.c_double, d]
+    return L
 
 
 def lib():
     global _lib
     with _lock:
         if _lib is None:
-            L = C.CDLL(build())
-            P = C.POINTER
-            d, i32, u8, u32 = P(C.c_double), P(C.c_int32), P(C.c_uint8), P(C.c_uint32)
-            L.orc_create.restype = C.c_void_p
-            L.orc_create.argtypes = [P(orc_params), C.c_int32, d, C.c_int32, i32, i32, i32, i32]
-            L.orc_destroy.argtypes = [C.c_void_p]
-            L.orc_num_particles.argtypes = [C.c_void_p]
-            L.orc_step_index.argtypes = [C.c_void_p]
-            L.orc_cg_iterations.argtypes = [C.c_void_p]
-            L.orc_seed.argtypes = [C.c_void_p, C.c_int32]
-            L.orc_set_particles.argtypes = [C.c_void_p, C.c_int32] + [d] * 7 + [u32, i32, C.c_int32]
-            L.orc_get_particles.argtypes = [C.c_void_p] + [d] * 7 + [u32, i32, u8]
-            L.orc_estimate_stats.argtypes = [C.c_void_p]
-            L.orc_advance.argtypes = [C.c_void_p, C.c_double]
-            L.orc_project.argtypes = [C.c_void_p, C.c_double]
-            L.orc_step.argtypes = [C.c_void_p, C.c_double, C.c_int32]
-            L.orc_advance_subset.argtypes = [C.c_void_p, C.c_double, i32, C.c_int32]
-            L.orc_get_field.argtypes = [C.c_void_p, C.c_int32, d]
-            L.orc_philox4x32_10.argtypes = [u32, u32, u32]
-            L.orc_philox4x32_10.restype = None
-            L.orc_gauss8.argtypes = [C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint32, d]
-            L.orc_gauss8.restype = None
-            L.orc_locate.argtypes = [C.c_void_p, C.c_double, C.c_double]
-            L.orc_reflect.argtypes = [C.c_void_p, C.c_int32, d, d, d, d, d, d]
-            L.orc_sde.argtypes = [P(orc_params), C.c_int32, C.c_double, d, d, d, d, d, d, d]
-            L.orc_sde.restype = None
-            L.orc_fe_solve.argtypes = [C.c_void_p, d, d, d, u8, d, C.c_int32]
-            L.orc_bins.argtypes = [P(orc_params), C.c_int32, d, d, d, u32, i32]
-            L.orc_set_node_fields.argtypes = [C.c_void_p, d, d, d]
-            L.orc_h_contract.argtypes = [P(orc_params), d, d, C.c_double, C.c_double, d]
-            _lib = L
+            _lib = load(build())
     return _lib
 
 
@@ -128,8 +141,8 @@ FIELDS = dict(elem_n=(0, 1), elem_mean=(1, 5), elem_R=(2, 6), elem_psivar=(3, 1)
 class Oracle:
     """One oracle context over one mesh."""
 
-    def __init__(self, params: dict, mesh: dict):
-        L = lib()
+    def __init__(self, params: dict, mesh: dict, library=None):
+        L = self._L = library if library is not None else lib()
         self.params = dict(params)
         self._p = make_params(self.params)
         self.nnode = int(mesh["xy"].shape[0])
@@ -149,28 +162,28 @@ class Oracle:
     def __del__(self):
         c = getattr(self, "_c", None)
         if c:
-            lib().orc_destroy(c)
+            self._L.orc_destroy(c)
             self._c = None
 
     def seed(self, per_element: int):
-        self._check(lib().orc_seed(self._c, per_element))
+        self._check(self._L.orc_seed(self._c, per_element))
 
     def set_particles(self, st: dict, step: int = 0):
         n = int(st["x"].shape[0])
         arr = {k: np.ascontiguousarray(st[k], dtype=np.float64) for k in ("x", "y", "u", "v", "w", "om", "psi")}
         ids = np.ascontiguousarray(st["id"], dtype=np.uint32)
         el = np.ascontiguousarray(st["elem"], dtype=np.int32)
-        self._check(lib().orc_set_particles(self._c, n, *[_p(arr[k], C.c_double) for k in
+        self._check(self._L.orc_set_particles(self._c, n, *[_p(arr[k], C.c_double) for k in
                                                           ("x", "y", "u", "v", "w", "om", "psi")],
                                             _p(ids, C.c_uint32), _p(el, C.c_int32), step))
 
     def particles(self) -> dict:
-        n = lib().orc_num_particles(self._c)
+        n = self._L.orc_num_particles(self._c)
         out = {k: np.empty(n, np.float64) for k in ("x", "y", "u", "v", "w", "om", "psi")}
         out["id"] = np.empty(n, np.uint32)
         out["elem"] = np.empty(n, np.int32)
         out["bin"] = np.empty(n, np.uint8)
-        self._check(lib().orc_get_particles(self._c, *[_p(out[k], C.c_double) for k in
+        self._check(self._L.orc_get_particles(self._c, *[_p(out[k], C.c_double) for k in
                                                        ("x", "y", "u", "v", "w", "om", "psi")],
                                             _p(out["id"], C.c_uint32), _p(out["elem"], C.c_int32),
                                             _p(out["bin"], C.c_uint8)))
@@ -178,39 +191,39 @@ class Oracle:
 
     @property
     def step_index(self) -> int:
-        return lib().orc_step_index(self._c)
+        return self._L.orc_step_index(self._c)
 
     @property
     def cg_iterations(self) -> int:
-        return lib().orc_cg_iterations(self._c)
+        return self._L.orc_cg_iterations(self._c)
 
     def estimate_stats(self, check: bool = True) -> int:
-        st = lib().orc_estimate_stats(self._c)
+        st = self._L.orc_estimate_stats(self._c)
         if check:
             self._check(st)
         return st
 
     def advance(self, dt: float, check: bool = True) -> int:
-        st = lib().orc_advance(self._c, dt)
+        st = self._L.orc_advance(self._c, dt)
         if check:
             self._check(st)
         return st
 
     def project(self, dt: float, check: bool = True) -> int:
-        st = lib().orc_project(self._c, dt)
+        st = self._L.orc_project(self._c, dt)
         if check:
             self._check(st)
         return st
 
     def advance_subset(self, dt: float, idx, check: bool = True) -> int:
         idx = np.ascontiguousarray(idx, np.int32)
-        st = lib().orc_advance_subset(self._c, dt, _p(idx, C.c_int32), idx.size)
+        st = self._L.orc_advance_subset(self._c, dt, _p(idx, C.c_int32), idx.size)
         if check:
             self._check(st)
         return st
 
     def step(self, dt: float, nsteps: int = 1, check: bool = True) -> int:
-        st = lib().orc_step(self._c, dt, nsteps)
+        st = self._L.orc_step(self._c, dt, nsteps)
         if check:
             self._check(st)
         return st
@@ -221,21 +234,25 @@ class Oracle:
             width = self.nbins
         rows = self.ntri if name.startswith("elem") else self.nnode
         out = np.empty(rows * width, np.float64)
-        self._check(lib().orc_get_field(self._c, fid, _p(out, C.c_double)))
+        self._check(self._L.orc_get_field(self._c, fid, _p(out, C.c_double)))
         return out.reshape(rows, width) if width > 1 else out
 
     def set_node_fields(self, nmean, nR, nke):
         a = [np.ascontiguousarray(v, np.float64) for v in (nmean, nR, nke)]
-        self._check(lib().orc_set_node_fields(self._c, *[_p(v, C.c_double) for v in a]))
+        self._check(self._L.orc_set_node_fields(self._c, *[_p(v, C.c_double) for v in a]))
+
+    def set_node_wp(self, wp):
+        wp = np.ascontiguousarray(wp, np.float64)
+        self._check(self._L.orc_set_node_wp(self._c, _p(wp, C.c_double)))
 
     def locate(self, x: float, y: float) -> int:
-        return lib().orc_locate(self._c, x, y)
+        return self._L.orc_locate(self._c, x, y)
 
     def reflect(self, tag: int, n, stat, u, v, w, om):
         n = np.ascontiguousarray(n, np.float64)
         stat = np.pad(np.asarray(stat, np.float64), (0, 12 - len(stat)))
         vals = [C.c_double(u), C.c_double(v), C.c_double(w), C.c_double(om)]
-        self._check(lib().orc_reflect(self._c, tag, _p(n, C.c_double), _p(stat, C.c_double),
+        self._check(self._L.orc_reflect(self._c, tag, _p(n, C.c_double), _p(stat, C.c_double),
                                       *[C.byref(x) for x in vals]))
         return tuple(x.value for x in vals)
 
@@ -246,7 +263,7 @@ class Oracle:
         g_node = np.ascontiguousarray(g_node, np.float64)
         is_dir = np.ascontiguousarray(is_dir, np.uint8)
         x = np.zeros_like(f_node) if x0 is None else np.ascontiguousarray(x0, np.float64).copy()
-        st = lib().orc_fe_solve(self._c, _p(L_elem, C.c_double), _p(f_node, C.c_double),
+        st = self._L.orc_fe_solve(self._c, _p(L_elem, C.c_double), _p(f_node, C.c_double),
                                 _p(g_node, C.c_double), _p(is_dir, C.c_uint8), _p(x, C.c_double), ncomp)
         self._check(st)
         return x

@@ -1260,6 +1260,14 @@ int orc_set_node_fields(orc_ctx* c, const double* nmean, const double* nR, const
     return st;
 }
 
+/* Test hook: replace the node wp (nnode x 5) and rebuild the node pack from
+ * it with the node statistics as they stand (Eqs. Gij and C0). */
+int orc_set_node_wp(orc_ctx* c, const double* wp) {
+    memcpy(c->nwp, wp, sizeof(double) * 5 * (size_t)c->nn);
+    node_pack(c);
+    return ORC_OK;
+}
+
 int orc_get_field(const orc_ctx* c, int32_t f, double* out) {
     const int nt = c->nt, nn = c->nn;
     switch (f) {

@@ -113,6 +113,7 @@ int orc_fe_solve(orc_ctx* c, const double* L_elem, const double* f_node, const d
 int orc_bins(const orc_params* p, int32_t n, const double* u, const double* v, const double* w,
              const uint32_t* id, int32_t* bin);
 int orc_set_node_fields(orc_ctx* c, const double* nmean, const double* nR, const double* nke);
+int orc_set_node_wp(orc_ctx* c, const double* wp);
 int orc_h_contract(const orc_params* p, const double R[6], const double g[4], double k,
                    double om, double f[5]);
 
