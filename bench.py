@@ -139,7 +139,7 @@ def gpu_index(local_rank: int) -> int:
 
 KERNEL_SOURCES = {
     "k_step": ("k_particle.cu", "pdf_internal.cuh"),
-    "k_moments_sel": ("k_stats.cu", "exact_sum.cuh", "pdf_internal.cuh"),
+    "k_moments_med": ("k_stats.cu", "exact_sum.cuh", "pdf_internal.cuh"),
     "k_scatter": ("k_sort.cu", "pdf_internal.cuh"),
 }
 
@@ -253,14 +253,14 @@ def config_block(cfg, mesh, n, precision, form):
 def algorithmic_bytes(kclass: str, ts: int):
     if kclass == "particle":  # k_step: read 7 state + id + elem + bin, write 7 state + elem
         return 14 * ts + 13, "k_step (per-particle step)"
-    if kclass == "moments":   # k_moments_sel: read u v w psi omega id, write the bin
-        return 5 * ts + 5, "k_moments_sel (element moments and velocity bins)"
+    if kclass == "moments":   # k_moments_med: read u v w psi omega, write the bin (ids only where values tie)
+        return 5 * ts + 1, "k_moments_med (element moments and velocity bins)"
     if kclass == "sort":      # k_scatter: read and write 7 state + id + elem
         return 2 * (7 * ts + 8), "k_scatter (element re-sort)"
     return None, None
 
 
-KTRAFFIC = {"particle": "k_step", "moments": "k_moments_sel", "sort": "k_scatter"}
+KTRAFFIC = {"particle": "k_step", "moments": "k_moments_med", "sort": "k_scatter"}
 
 
 def roofline(kclass, kt, n, ts, workload, precision):

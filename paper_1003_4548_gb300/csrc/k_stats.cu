@@ -13,14 +13,17 @@
 //    split into nb2, then by (W, id) into nb3; <phi|V> of a bin is its mean psi.
 // Reductions are FP64 (or compensated FP32 with PDF_FP32_KAHAN).
 //
-// FP32 particle state with median splits (2 x 2 x 2 bins), the production
-// path: one warp per element of at most 512 particles finds each split's
-// boundary key by a 256-bucket histogram and an exact rank of the keys in the
-// boundary bucket (no sort); the moments are exact fixed-point sums (FP32) or
-// compensated FP32 sums (FP32 + Kahan). Crowded elements (more than 512
-// particles, listed by k_crowded) go to 256-thread teams, and elements above
-// 4096 to the block kernel above; those run on the context stream while the
-// warp kernel runs on a high-priority side stream forked from it.
+// FP32 particle state with 2 x 2 x 2 bins, the production path: one warp per
+// element of at most 512 particles (k_moments_med) keeps the segment in
+// registers and shared memory, reads it from memory once, and finds each
+// split's median from a 256-bucket histogram plus an exact rank of the few
+// keys in the median's bucket, one pass over the keys per level (no sort);
+// the moments are exact fixed-point sums (FP32) or compensated FP32 sums
+// (FP32 + Kahan). Crowded elements (more than 512 particles, listed by
+// k_crowded) go to 256-thread teams, and elements above 4096 to the block
+// kernel above; those run on the context stream while the warp kernel runs
+// on a high-priority side stream forked from it. Other bin shapes take the
+// warp bitonic kernel (k_moments_warp).
 #include <algorithm>
 
 #include "pdf_internal.cuh"
@@ -1106,12 +1109,475 @@ __device__ void empty_element(const MomArgs<float>& a, int e, int tid, int nt_te
     }
 }
 
-// warp per element: 0 <= n <= 512
+// ---------------------------------------------------------------------------
+// 2 x 2 x 2 bins (median splits on U, then V in each U half, then W in each
+// quarter), one warp per element of at most 512 particles. Lane l holds the
+// keys q = l + 32 j: j < 8 in registers (u, v, w, psi), 8 <= j < 16 in the
+// warp's shared memory, so the segment is read from memory once.
+//  * moments: blocked compensated FP32 sums (KAHAN) or exact fixed-point
+//    sums;
+//  * every split level fills 256-bucket histograms of its component (value-
+//    linear over mean +- 4 sd of the element); a scan of each group's
+//    histogram gives the bucket holding the group's median and the median's
+//    rank in it. In the next pass a key outside that bucket joins the lower
+//    or the upper half by its bucket alone; the few keys inside it are
+//    deferred to a candidate list, ranked exactly in the (value, id) order,
+//    and join the next level's histograms once their half is known. Each
+//    level costs one pass over the keys;
+//  * the last pass writes the bins and sums psi per bin (exact fixed point);
+//  * a level whose boundary buckets hold more than MCL keys (many equal or
+//    clustered values) hands the element to the general selection path.
+// ---------------------------------------------------------------------------
+constexpr int MCL = 128;  // candidate list capacity
+constexpr unsigned FULLW = 0xffffffffu;
+
+struct __align__(16) MedSmem {
+    unsigned hist[4][128];                       // per group: 256 buckets, two 16-bit counts per word (read as uint4)
+    float ou[8][32], ov[8][32], ow[8][32], op[8][32];  // keys 256..511 of the segment
+    unsigned char ob[8][32];                     // their bucket at the current level
+    uint32_t cv[MCL];                            // candidate: order bits of the resolved component
+    uint32_t cid[MCL];                           // candidate: particle id (read where values tie)
+    float cps[MCL];                              // candidate: psi (last level)
+    unsigned short cq[MCL];                      // candidate: index in the segment
+    unsigned short crank[MCL];                   // candidate: rank in its group's boundary bucket
+    unsigned char cg[MCL], cb[MCL], ceq[MCL];    // group, next-level bucket, keys of equal value
+    unsigned upb[16];                            // upper-half bit of every deferred key, by index
+    int bkt[4], brank[4], ncand[4];
+    int ncl;                                     // candidates listed at this level
+    unsigned binpart[8][4];                      // sum of psi per bin, unit 2^-54, in 19-bit parts
+};
+static_assert(sizeof(MedSmem) % 16 == 0 && alignof(MedSmem) == 16, "per-warp slices keep hist 16-byte aligned");
+
+__device__ __forceinline__ int bucket_of(const Buckets& bk, float x) {
+    return max(0, min(bk.top, (int)((x + 0.0f - bk.lo) * bk.sc)));
+}
+
+// size of group g after `depth` halvings of n keys (the lower half takes the extra key)
+__device__ __forceinline__ int split_size(int n, int g, int depth) {
+    int m = n;
+    for (int b = depth - 1; b >= 0; --b) m = ((g >> b) & 1) ? (m >> 1) : ((m + 1) >> 1);
+    return m;
+}
+
+__device__ __forceinline__ int getbyte(unsigned w0, unsigned w1, int j) {
+    return (int)(((j < 4 ? w0 : w1) >> (8 * (j & 3))) & 0xffu);
+}
+__device__ __forceinline__ void setbyte(unsigned& w0, unsigned& w1, int j, int b) {
+    unsigned& w = j < 4 ? w0 : w1;
+    w = (w & ~(0xffu << (8 * (j & 3)))) | ((unsigned)b << (8 * (j & 3)));
+}
+
+__device__ __forceinline__ unsigned hinc(int b) { return 1u << (16 * (b & 1)); }
+
+// both bits of the 2-bit group field of every key flagged in m (keys j < 8)
+__device__ __forceinline__ uint32_t med_spread(uint32_t m) {
+    uint32_t r = 0u;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) r |= ((m >> j) & 1u) * (3u << (2 * j));
+    return r;
+}
+
+// psi (clamped to [0, 1]) added to bin bn's sum: the fixed-point value
+// (below 2^55) in three 19-bit parts, each part's sum over at most 512 keys
+// below 2^28, so native 32-bit shared atomics keep the sum exact
+__device__ __forceinline__ void med_binadd(MedSmem& S, int bn, unsigned long long v) {
+    atomicAdd(&S.binpart[bn][0], (unsigned)(v & 0x7ffffull));
+    atomicAdd(&S.binpart[bn][1], (unsigned)((v >> 19) & 0x7ffffull));
+    atomicAdd(&S.binpart[bn][2], (unsigned)(v >> 38));
+}
+
+__device__ __forceinline__ unsigned long long psi_fixed(float p) {
+    constexpr int UNIT = 54;  // psi in [0, 1] and n <= 512 keep the bin sums below 2^63
+    unsigned m;
+    int ex;
+    bool neg;
+    f32_parts(fminf(fmaxf(p, 0.f), 1.f), m, ex, neg);
+    const int sh = ex - 150 + UNIT;
+    return sh >= 0 ? ((unsigned long long)m << sh) : (-sh < 64 ? ((unsigned long long)m >> (-sh)) : 0ull);
+}
+
+// bucket of each group's median: NG groups, 32/NG lanes scan one group's
+// histogram; writes bkt, brank (rank of the median in its bucket) and ncand
+template <int NG>
+__device__ __forceinline__ void med_scan(MedSmem& S, int n, int lane) {
+    constexpr int LPG = 32 / NG, WPL = 128 / LPG, DEP = NG == 1 ? 0 : (NG == 2 ? 1 : 2);
+    const int sub = lane & (LPG - 1), gl = lane / LPG;
+    const int Tk = (split_size(n, gl, DEP) + 1) >> 1;
+    const uint4* h4 = reinterpret_cast<const uint4*>(&S.hist[gl][sub * WPL]);
+    unsigned hw[WPL];
+#pragma unroll
+    for (int k = 0; k < WPL / 4; ++k) {
+        const uint4 x = h4[k];
+        hw[4 * k] = x.x; hw[4 * k + 1] = x.y; hw[4 * k + 2] = x.z; hw[4 * k + 3] = x.w;
+    }
+    int tot = 0;
+#pragma unroll
+    for (int k = 0; k < WPL; ++k) tot += (int)(hw[k] & 0xffffu) + (int)(hw[k] >> 16);
+    int incl = tot;
+#pragma unroll
+    for (int o = 1; o < LPG; o <<= 1) {
+        const int y = __shfl_up_sync(FULLW, incl, o, LPG);
+        if (sub >= o) incl += y;
+    }
+    const int excl = incl - tot;
+    if (excl < Tk && incl >= Tk) {  // this lane's words hold the median: find the word, then the bucket
+        int run = excl, k = 0;
+        unsigned word = 0u;
+        bool found = false;
+#pragma unroll
+        for (int i = 0; i < WPL; ++i) {
+            const int c = (int)(hw[i] & 0xffffu) + (int)(hw[i] >> 16);
+            if (!found) {
+                if (run + c >= Tk) {
+                    k = i;
+                    word = hw[i];
+                    found = true;
+                } else {
+                    run += c;
+                }
+            }
+        }
+        const int c0 = (int)(word & 0xffffu), c1 = (int)(word >> 16);
+        const bool hi = run + c0 < Tk;
+        S.bkt[gl] = 2 * (sub * WPL + k) + (hi ? 1 : 0);
+        S.brank[gl] = Tk - (hi ? run + c0 : run) - 1;
+        S.ncand[gl] = hi ? c1 : c0;
+    }
+}
+
+// rank of every listed candidate in its group's boundary bucket, in the
+// (value, id) order; ids are read only where two candidates of a group tie
+__device__ __noinline__ void med_rank(MedSmem& S, const uint32_t* __restrict__ ids, int L, int lane) {
+    int tied = 0;
+    for (int t = lane; t < L; t += 32) {
+        const uint32_t v = S.cv[t];
+        const int g = S.cg[t];
+        int r = 0, eq = 0;
+        for (int u = 0; u < L; ++u) {
+            if (S.cg[u] == g) {
+                const uint32_t vu = S.cv[u];
+                r += vu < v ? 1 : 0;
+                eq += vu == v ? 1 : 0;
+            }
+        }
+        S.crank[t] = (unsigned short)r;
+        S.ceq[t] = (unsigned char)min(eq, 255);
+        tied |= eq > 1 ? 1 : 0;
+    }
+    if (__any_sync(FULLW, tied)) {  // equal values: the ids decide (rare)
+        __syncwarp();
+        for (int t = lane; t < L; t += 32) S.cid[t] = ids[S.cq[t]];
+        __syncwarp();
+        for (int t = lane; t < L; t += 32) {
+            if (S.ceq[t] > 1) {
+                const uint32_t v = S.cv[t], it = S.cid[t];
+                const int g = S.cg[t];
+                int r = S.crank[t];
+                for (int u = 0; u < L; ++u) r += (S.cg[u] == g && S.cv[u] == v && S.cid[u] < it) ? 1 : 0;
+                S.crank[t] = (unsigned short)r;
+            }
+        }
+    }
+    __syncwarp();
+}
+
+// moments of the segment: keys j < 8 from the registers, keys j >= 8 read
+// here (and kept in shared memory for the split levels); every lane gets the
+// bucket maps of u, v, w and the mean psi
 template <bool KAHAN>
-__global__ void __launch_bounds__(32 * WARPS_PER_BLOCK, KAHAN ? 8 : 4) k_moments_sel(const MomArgs<float> a, int nt) {
-    __shared__ SelSmem<512> sm[WARPS_PER_BLOCK];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int e = blockIdx.x * WARPS_PER_BLOCK + w;
+__device__ __forceinline__ void med_moments(const MomArgs<float>& a, int e, int s0, int n, int kk, int lane,
+                                            const float (&xu)[8], const float (&xv)[8], const float (&xw)[8],
+                                            const float (&xp)[8], MedSmem& S, Buckets (&bk)[3], double& mean_psi) {
+    double val = 0.0;
+    if constexpr (KAHAN) {
+        // sums of the values shifted by the segment's first particle and of
+        // their products: a lane sums each block of eight of its keys in plain
+        // FP32 (the products fused), the block sums enter compensated sums,
+        // then a butterfly reduce-scatter merges the lanes
+        const float su = __shfl_sync(FULLW, xu[0], 0), sv = __shfl_sync(FULLW, xv[0], 0);
+        const float sw = __shfl_sync(FULLW, xw[0], 0), sp = __shfl_sync(FULLW, xp[0], 0);
+        AccK acc[16];
+#pragma unroll
+        for (int blkno = 0; blkno < 2; ++blkno) {
+            if (blkno == 1 && kk <= 8) break;
+            float tu[8], tv[8], tw[8], tp[8], to[8];
+#pragma unroll
+            for (int h = 0; h < 8; ++h) {
+                const int j = 8 * blkno + h, q = lane + 32 * j;
+                const bool in = j < kk && q < n;
+                if (blkno == 0) {
+                    tu[h] = xu[h]; tv[h] = xv[h]; tw[h] = xw[h]; tp[h] = xp[h];
+                } else {  // staged in shared memory by the caller
+                    tu[h] = in ? S.ou[h][lane] : su;
+                    tv[h] = in ? S.ov[h][lane] : sv;
+                    tw[h] = in ? S.ow[h][lane] : sw;
+                    tp[h] = in ? S.op[h][lane] : sp;
+                }
+                to[h] = in ? a.om[s0 + q] : 0.f;
+            }
+            float blk[12];
+#pragma unroll
+            for (int k = 0; k < 12; ++k) blk[k] = 0.f;
+#pragma unroll
+            for (int h = 0; h < 8; ++h) {
+                const int j = 8 * blkno + h, q = lane + 32 * j;
+                const bool in = j < kk && q < n;
+                const float du = in ? tu[h] - su : 0.f, dv = in ? tv[h] - sv : 0.f;
+                const float dw = in ? tw[h] - sw : 0.f, dp = in ? tp[h] - sp : 0.f;
+                blk[0] += du; blk[1] += dv; blk[2] += dw; blk[3] += dp; blk[4] += to[h];
+                blk[5] = fmaf(du, du, blk[5]); blk[6] = fmaf(dv, dv, blk[6]); blk[7] = fmaf(dw, dw, blk[7]);
+                blk[8] = fmaf(du, dv, blk[8]); blk[9] = fmaf(du, dw, blk[9]); blk[10] = fmaf(dv, dw, blk[10]);
+                blk[11] = fmaf(dp, dp, blk[11]);
+            }
+#pragma unroll
+            for (int k = 0; k < 12; ++k) acc[k].add(blk[k]);
+        }
+        // after the xor-16, 8, 4, 2 exchanges lane l holds sum (l >> 1) of
+        // its lane pair; the xor-1 merge (same operand order in both lanes)
+        // completes it
+#pragma unroll
+        for (int w = 8, o = 16; w >= 1; w >>= 1, o >>= 1) {
+            const bool upper = (lane & o) != 0;
+#pragma unroll
+            for (int k = 0; k < w; ++k) {
+                AccK send = upper ? acc[k] : acc[w + k];
+                AccK keep = upper ? acc[w + k] : acc[k];
+                AccK recv;
+                recv.s = __shfl_xor_sync(FULLW, send.s, o);
+                recv.c = __shfl_xor_sync(FULLW, send.c, o);
+                keep.merge(recv);
+                acc[k] = keep;
+            }
+        }
+        {
+            AccK recv;
+            recv.s = __shfl_xor_sync(FULLW, acc[0].s, 1);
+            recv.c = __shfl_xor_sync(FULLW, acc[0].c, 1);
+            if (lane & 1) {
+                AccK mine = recv;
+                mine.merge(acc[0]);
+                acc[0] = mine;
+            } else {
+                acc[0].merge(recv);
+            }
+        }
+        // lane q < 12 finishes moment q: 0..4 the means, 5..10 the central
+        // second moments uu vv ww uv uw vw, 11 the psi variance (sum v sits
+        // in lanes 2v and 2v + 1)
+        int ia = 0, ib = 0, ic = 0;
+        if (lane < 5) ia = lane;
+        else if (lane < 11) {
+            const int k = lane - 5;
+            ia = k < 3 ? k : (k == 5 ? 1 : 0);
+            ib = k < 3 ? k : (k == 3 ? 1 : 2);
+            ic = 5 + k;
+        } else {
+            ia = ib = 3;
+            ic = 11;
+        }
+        AccK A, Bq, Cq;
+        A.s = __shfl_sync(FULLW, acc[0].s, 2 * ia);
+        A.c = __shfl_sync(FULLW, acc[0].c, 2 * ia);
+        Bq.s = __shfl_sync(FULLW, acc[0].s, 2 * ib);
+        Bq.c = __shfl_sync(FULLW, acc[0].c, 2 * ib);
+        Cq.s = __shfl_sync(FULLW, acc[0].s, 2 * ic);
+        Cq.c = __shfl_sync(FULLW, acc[0].c, 2 * ic);
+        if (lane < 12) {
+            const double inv_n = recip_n(n);
+            const double da = A.value() * inv_n;
+            if (lane < 5) {
+                const float shift = lane == 0 ? su : (lane == 1 ? sv : (lane == 2 ? sw : (lane == 3 ? sp : 0.f)));
+                val = shift + da;
+            } else {
+                val = Cq.value() * inv_n - da * (Bq.value() * inv_n);
+            }
+        }
+    } else {
+        // exact fixed-point sums (unit 2^-80) of the values and their products
+        Exact128 s1[5], s2[7];
+        bool big = false;
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            const int q = lane + 32 * j;
+            if (j < kk && q < n) {
+                float x0, x1, x2, x3;
+                if (j < 8) {
+                    x0 = xu[j & 7]; x1 = xv[j & 7]; x2 = xw[j & 7]; x3 = xp[j & 7];
+                } else {
+                    x0 = S.ou[j - 8][lane]; x1 = S.ov[j - 8][lane]; x2 = S.ow[j - 8][lane]; x3 = S.op[j - 8][lane];
+                }
+                unsigned mu_, mv_, mw_, mp_, mo_;
+                int eu, ev, ew, ep, eo;
+                bool nu, nv, nw, np, no;
+                f32_parts(x0, mu_, eu, nu);
+                f32_parts(x1, mv_, ev, nv);
+                f32_parts(x2, mw_, ew, nw);
+                f32_parts(x3, mp_, ep, np);
+                f32_parts(a.om[s0 + q], mo_, eo, no);
+                big |= max(max(max(eu, ev), max(ew, ep)), eo) > 145;  // |x| >= 2^19: outside the format
+                x128_add_parts(s1[0], mu_, eu, nu);
+                x128_add_parts(s1[1], mv_, ev, nv);
+                x128_add_parts(s1[2], mw_, ew, nw);
+                x128_add_parts(s1[3], mp_, ep, np);
+                x128_add_parts(s1[4], mo_, eo, no);
+                x128_add_prod(s2[0], mu_, eu, nu, mu_, eu, nu);
+                x128_add_prod(s2[1], mv_, ev, nv, mv_, ev, nv);
+                x128_add_prod(s2[2], mw_, ew, nw, mw_, ew, nw);
+                x128_add_prod(s2[3], mu_, eu, nu, mv_, ev, nv);
+                x128_add_prod(s2[4], mu_, eu, nu, mw_, ew, nw);
+                x128_add_prod(s2[5], mv_, ev, nv, mw_, ew, nw);
+                x128_add_prod(s2[6], mp_, ep, np, mp_, ep, np);
+            }
+        }
+        if (__any_sync(FULLW, big) && lane == 0) set_status(a.status, ST_CAPACITY);
+#pragma unroll
+        for (int k = 0; k < 5; ++k) x128_warp_sum(s1[k]);
+#pragma unroll
+        for (int k = 0; k < 7; ++k) x128_warp_sum(s2[k]);
+        Exact128 mine, xa, xb;
+#pragma unroll
+        for (int k = 0; k < 5; ++k) {
+            const unsigned long long lo = __shfl_sync(FULLW, s1[k].lo, 0), hi = __shfl_sync(FULLW, s1[k].hi, 0);
+            if (lane == k) { mine.lo = lo; mine.hi = hi; }
+            const int ia = lane == 5 || lane == 8 || lane == 9 ? 0 : (lane == 6 || lane == 10 ? 1 : (lane == 7 ? 2 : 3));
+            const int ib = lane == 5 ? 0 : (lane == 6 || lane == 8 ? 1 : (lane == 7 || lane == 9 || lane == 10 ? 2 : 3));
+            if (ia == k) { xa.lo = lo; xa.hi = hi; }
+            if (ib == k) { xb.lo = lo; xb.hi = hi; }
+        }
+#pragma unroll
+        for (int k = 0; k < 7; ++k) {
+            const unsigned long long lo = __shfl_sync(FULLW, s2[k].lo, 0), hi = __shfl_sync(FULLW, s2[k].hi, 0);
+            if (lane == 5 + k) { mine.lo = lo; mine.hi = hi; }
+        }
+        if (lane < 5) val = x128_to_double(mine) / n;
+        else if (lane < 12) val = x128_central(mine, xa, xb, (unsigned)n);
+    }
+    if (lane < 5) a.emean[5 * e + lane] = val;
+    else if (lane < 11) a.eR[6 * e + lane - 5] = val;
+    else if (lane == 11) a.epsivar[e] = val;
+    if (lane == 0) a.en[e] = n;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        // 256 buckets over mean +- 4 sd (any monotone map keeps the selection
+        // exact; the approximate reciprocal square root only shapes the buckets)
+        const float mu = (float)__shfl_sync(FULLW, val, d), var = (float)__shfl_sync(FULLW, val, 5 + d);
+        const float rs = var > 0.f ? rsqrtf(var) : 0.f;
+        const float sc = 32.f * rs;
+        bk[d].top = 255;
+        bk[d].lo = mu - 4.f * var * rs;
+        bk[d].sc = (sc > 0.f && sc < 1e30f) ? sc : 0.f;
+    }
+    mean_psi = __shfl_sync(FULLW, val, 3);
+}
+
+// append a key to the candidate list (a few keys per level; S.ncl counts them)
+__device__ __forceinline__ void med_append(MedSmem& S, uint32_t key, int q, int g, int b, float ps) {
+    const int slot = atomicAdd(&S.ncl, 1);
+    if (slot < MCL) {
+        S.cv[slot] = key;
+        S.cq[slot] = (unsigned short)q;
+        S.cg[slot] = (unsigned char)g;
+        S.cb[slot] = (unsigned char)b;
+        S.cps[slot] = ps;
+    }
+}
+
+// the general selection path for an element whose boundary buckets are crowded
+template <bool KAHAN>
+__device__ __noinline__ void med_general(const MomArgs<float>& a, int e, int s0, int n, SelSmem<512>& S) {
+    sel_element<KAHAN, 32, 512>(a, e, s0, n, S);
+}
+
+__device__ __forceinline__ int upbit(const MedSmem& S, int q) { return (int)((S.upb[q >> 5] >> (q & 31)) & 1u); }
+
+// The passes over keys 256..511 (shared memory), out of line: only elements
+// above 256 particles take them, and the register passes stay contiguous.
+__device__ __noinline__ void med_tail0(MedSmem& S, Buckets bk, int n, int kk, int lane) {
+    for (int j = 8; j < kk; ++j) {
+        if (lane + 32 * j < n) {
+            const int b = bucket_of(bk, S.ou[j - 8][lane]);
+            S.ob[j - 8][lane] = (unsigned char)b;
+            atomicAdd(&S.hist[0][b >> 1], hinc(b));
+        }
+    }
+}
+
+__device__ __noinline__ uint2 med_tail1(MedSmem& S, Buckets bk, int c0, int n, int kk, int lane, uint32_t gw,
+                                        uint32_t pend) {
+    for (int j = 8; j < kk; ++j) {
+        const int q = lane + 32 * j;
+        if (q < n) {
+            const int b0 = S.ob[j - 8][lane];
+            const int b = bucket_of(bk, S.ov[j - 8][lane]);
+            S.ob[j - 8][lane] = (unsigned char)b;
+            if (b0 == c0) {
+                pend |= 1u << j;
+                med_append(S, ord32(S.ou[j - 8][lane]), q, 0, b, 0.f);
+            } else {
+                const int g = b0 > c0 ? 1 : 0;
+                gw |= (uint32_t)g << (2 * j);
+                atomicAdd(&S.hist[g][b >> 1], hinc(b));
+            }
+        }
+    }
+    return make_uint2(gw, pend);
+}
+
+__device__ __noinline__ uint2 med_tail2(MedSmem& S, Buckets bk, int c0, int c1, int n, int kk, int lane, uint32_t gw,
+                                        uint32_t pend, uint32_t pend2) {
+    for (int j = 8; j < kk; ++j) {
+        const int q = lane + 32 * j;
+        if (q < n) {
+            int g = (int)((gw >> (2 * j)) & 3u);
+            if ((pend >> j) & 1u) g = 2 * g + upbit(S, q);
+            const int b1 = S.ob[j - 8][lane], c = g ? c1 : c0;
+            const int b = bucket_of(bk, S.ow[j - 8][lane]);
+            S.ob[j - 8][lane] = (unsigned char)b;
+            if (b1 == c) {
+                pend2 |= 1u << j;
+                gw = (gw & ~(3u << (2 * j))) | ((uint32_t)g << (2 * j));
+                med_append(S, ord32(S.ov[j - 8][lane]), q, g, b, 0.f);
+            } else {
+                const int g2 = 2 * g + (b1 > c ? 1 : 0);
+                gw = (gw & ~(3u << (2 * j))) | ((uint32_t)g2 << (2 * j));
+                atomicAdd(&S.hist[g2][b >> 1], hinc(b));
+            }
+        }
+    }
+    return make_uint2(gw, pend2);
+}
+
+__device__ __noinline__ void med_tail3(MedSmem& S, unsigned char* bins, int4 c4, int n, int kk, int lane, uint32_t gw,
+                                       uint32_t pend) {
+    for (int j = 8; j < kk; ++j) {
+        const int q = lane + 32 * j;
+        if (q < n) {
+            int g = (int)((gw >> (2 * j)) & 3u);
+            if ((pend >> j) & 1u) g = 2 * g + upbit(S, q);
+            const int b2 = S.ob[j - 8][lane], c = g == 0 ? c4.x : (g == 1 ? c4.y : (g == 2 ? c4.z : c4.w));
+            const float ps = S.op[j - 8][lane];
+            if (b2 == c) {
+                med_append(S, ord32(S.ow[j - 8][lane]), q, g, 0, ps);
+            } else {
+                const int bn = 2 * g + (b2 > c ? 1 : 0);
+                bins[q] = (unsigned char)bn;
+                med_binadd(S, bn, psi_fixed(ps));
+            }
+        }
+    }
+}
+
+// five blocks per SM for the compensated form (96 registers, no spills; four
+// and six measured slower), four for the exact form (its 128-bit sums)
+template <bool KAHAN>
+__global__ void __launch_bounds__(32 * WARPS_PER_BLOCK, KAHAN ? 5 : 4) k_moments_med(const MomArgs<float> a, int nt) {
+    __shared__ union __align__(16) MedUnion {
+        MedSmem m;
+        SelSmem<512> s;
+    } sm[WARPS_PER_BLOCK];
+    static_assert(sizeof(MedUnion) % 16 == 0, "per-warp slices keep hist 16-byte aligned");
+    const int lane = threadIdx.x & 31, wq = threadIdx.x >> 5;
+    const int e = blockIdx.x * WARPS_PER_BLOCK + wq;
     if (e >= nt) return;
     const int s0 = a.off[e], n = a.off[e + 1] - s0;
     if (n > 512) return;  // a block kernel takes it (listed by k_crowded)
@@ -1119,7 +1585,201 @@ __global__ void __launch_bounds__(32 * WARPS_PER_BLOCK, KAHAN ? 8 : 4) k_moments
         empty_element(a, e, lane, 32);
         return;
     }
-    sel_element<KAHAN, 32, 512>(a, e, s0, n, sm[w]);
+    MedSmem& S = sm[wq].m;
+    const uint32_t* __restrict__ ids = a.id + s0;
+    const int kk = (n + 31) >> 5;  // key slots in use (warp-uniform)
+    float xu[8], xv[8], xw[8], xp[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const int q = lane + 32 * j;
+        const bool in = j < kk && q < n;
+        xu[j] = in ? a.u[s0 + q] : 0.f;
+        xv[j] = in ? a.v[s0 + q] : 0.f;
+        xw[j] = in ? a.w[s0 + q] : 0.f;
+        xp[j] = in ? a.psi[s0 + q] : 0.f;
+    }
+    if (kk > 8) {  // keys 256..511 into the warp's shared memory (all loads issued together)
+        float tu[8], tv[8], tw[8], tp[8];
+#pragma unroll
+        for (int h = 0; h < 8; ++h) {
+            const int q = lane + 32 * (8 + h);
+            const bool in = 8 + h < kk && q < n;
+            tu[h] = in ? a.u[s0 + q] : 0.f;
+            tv[h] = in ? a.v[s0 + q] : 0.f;
+            tw[h] = in ? a.w[s0 + q] : 0.f;
+            tp[h] = in ? a.psi[s0 + q] : 0.f;
+        }
+#pragma unroll
+        for (int h = 0; h < 8; ++h) {
+            S.ou[h][lane] = tu[h]; S.ov[h][lane] = tv[h]; S.ow[h][lane] = tw[h]; S.op[h][lane] = tp[h];
+        }
+    }
+    Buckets bk[3];
+    double mean_psi;
+    med_moments<KAHAN>(a, e, s0, n, kk, lane, xu, xv, xw, xp, S, bk, mean_psi);
+    if (n < 8) {  // fewer particles than bins: the element mean (IEM)
+        if (lane < n) a.bin[s0 + lane] = 0;
+        if (lane < 8) {
+            a.ecm[(size_t)8 * e + lane] = mean_psi;
+            a.ecmT[(size_t)8 * e + lane] = (float)mean_psi;
+        }
+        return;
+    }
+    unsigned pb0 = 0u, pb1 = 0u;  // bucket of register key j at the current level (a byte each)
+    // The passes over the register keys are branch-free (the key slot and the
+    // segment bound predicate the stores and atomics), so the eight keys of a
+    // lane interleave; keys deferred to the candidate list are flagged in a
+    // mask and listed after the pass.
+    // ---- level 0: U
+    for (int t = lane; t < 128; t += 32) S.hist[0][t] = 0u;
+    __syncwarp();
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const bool in = j < kk && lane + 32 * j < n;
+        const int b = bucket_of(bk[0], xu[j]);
+        setbyte(pb0, pb1, j, b);
+        if (in) atomicAdd(&S.hist[0][b >> 1], hinc(b));
+    }
+    if (kk > 8) med_tail0(S, bk[0], n, kk, lane);
+    __syncwarp();
+    med_scan<1>(S, n, lane);
+    __syncwarp();
+    bool general = S.ncand[0] > MCL;
+    uint32_t gw = 0u, pend = 0u;  // group of key j (2 bits each); keys deferred to the candidate list
+    if (!general) {
+        // ---- level 1: V; the U halves
+        const int c0 = S.bkt[0];
+        for (int t = lane; t < 256; t += 32) (&S.hist[0][0])[t] = 0u;
+        if (lane < 16) S.upb[lane] = 0u;
+        if (lane == 0) S.ncl = 0;
+        __syncwarp();
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const bool in = j < kk && lane + 32 * j < n;
+            const int b0 = getbyte(pb0, pb1, j);
+            const int b = bucket_of(bk[1], xv[j]);
+            setbyte(pb0, pb1, j, b);
+            const int g = b0 > c0 ? 1 : 0;
+            gw |= (uint32_t)g << (2 * j);
+            const bool isc = in && b0 == c0;
+            pend |= (isc ? 1u : 0u) << j;
+            if (in && !isc) atomicAdd(&S.hist[g][b >> 1], hinc(b));
+        }
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+            if ((pend >> j) & 1u) med_append(S, ord32(xu[j]), lane + 32 * j, 0, getbyte(pb0, pb1, j), 0.f);
+        gw &= ~med_spread(pend);  // deferred keys stay in group 0 until resolved
+        if (kk > 8) {
+            const uint2 r = med_tail1(S, bk[1], c0, n, kk, lane, gw, pend);
+            gw = r.x;
+            pend = r.y;
+        }
+        __syncwarp();
+        const int L = S.ncl;
+        med_rank(S, ids, L, lane);
+        for (int t = lane; t < L; t += 32) {  // the candidates join their U half
+            const int g = S.cg[t], up = (int)S.crank[t] > S.brank[g] ? 1 : 0, b = S.cb[t];
+            atomicAdd(&S.hist[2 * g + up][b >> 1], hinc(b));
+            if (up) atomicOr(&S.upb[S.cq[t] >> 5], 1u << (S.cq[t] & 31));
+        }
+        __syncwarp();
+        med_scan<2>(S, n, lane);
+        __syncwarp();
+        general = S.ncand[0] + S.ncand[1] > MCL;
+    }
+    if (!general) {
+        // ---- level 2: W; the V halves of each U half
+        const int c0 = S.bkt[0], c1 = S.bkt[1];
+        for (int t = lane; t < 512; t += 32) (&S.hist[0][0])[t] = 0u;
+        if (lane == 0) S.ncl = 0;
+        __syncwarp();
+        uint32_t pend2 = 0u;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const bool in = j < kk && lane + 32 * j < n;
+            int g = (int)((gw >> (2 * j)) & 3u);
+            g = ((pend >> j) & 1u) ? 2 * g + upbit(S, lane + 32 * j) : g;
+            const int b1 = getbyte(pb0, pb1, j), c = g ? c1 : c0;
+            const int b = bucket_of(bk[2], xw[j]);
+            setbyte(pb0, pb1, j, b);
+            const bool isc = in && b1 == c;
+            const int g2 = isc ? g : 2 * g + (b1 > c ? 1 : 0);
+            gw = (gw & ~(3u << (2 * j))) | ((uint32_t)g2 << (2 * j));
+            pend2 |= (isc ? 1u : 0u) << j;
+            if (in && !isc) atomicAdd(&S.hist[g2][b >> 1], hinc(b));
+        }
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+            if ((pend2 >> j) & 1u)
+                med_append(S, ord32(xv[j]), lane + 32 * j, (int)((gw >> (2 * j)) & 3u), getbyte(pb0, pb1, j), 0.f);
+        if (kk > 8) {
+            const uint2 r = med_tail2(S, bk[2], c0, c1, n, kk, lane, gw, pend, pend2);
+            gw = r.x;
+            pend2 = r.y;
+        }
+        pend = pend2;
+        __syncwarp();
+        const int L = S.ncl;
+        if (lane < 16) S.upb[lane] = 0u;
+        med_rank(S, ids, L, lane);  // (ends in a warp barrier before upb is written)
+        for (int t = lane; t < L; t += 32) {  // the candidates join their V half
+            const int g = S.cg[t], up = (int)S.crank[t] > S.brank[g] ? 1 : 0, b = S.cb[t];
+            atomicAdd(&S.hist[2 * g + up][b >> 1], hinc(b));
+            if (up) atomicOr(&S.upb[S.cq[t] >> 5], 1u << (S.cq[t] & 31));
+        }
+        __syncwarp();
+        med_scan<4>(S, n, lane);
+        __syncwarp();
+        general = S.ncand[0] + S.ncand[1] + S.ncand[2] + S.ncand[3] > MCL;
+    }
+    if (general) {  // crowded boundary buckets: the general selection path
+        __syncwarp();
+        med_general<KAHAN>(a, e, s0, n, sm[wq].s);
+        return;
+    }
+    // ---- bins: the W halves; psi summed per bin
+    const int c0 = S.bkt[0], c1 = S.bkt[1], c2 = S.bkt[2], c3 = S.bkt[3];
+    (&S.binpart[0][0])[lane] = 0u;
+    if (lane == 0) S.ncl = 0;
+    __syncwarp();
+    uint32_t pend3 = 0u;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const int q = lane + 32 * j;
+        const bool in = j < kk && q < n;
+        int g = (int)((gw >> (2 * j)) & 3u);
+        g = ((pend >> j) & 1u) ? 2 * g + upbit(S, q) : g;
+        gw = (gw & ~(3u << (2 * j))) | ((uint32_t)g << (2 * j));
+        const int b2 = getbyte(pb0, pb1, j), c = g == 0 ? c0 : (g == 1 ? c1 : (g == 2 ? c2 : c3));
+        const bool isc = in && b2 == c;
+        pend3 |= (isc ? 1u : 0u) << j;
+        const int bn = 2 * g + (b2 > c ? 1 : 0);
+        if (in && !isc) {
+            a.bin[s0 + q] = (unsigned char)bn;
+            med_binadd(S, bn, psi_fixed(xp[j]));
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+        if ((pend3 >> j) & 1u) med_append(S, ord32(xw[j]), lane + 32 * j, (int)((gw >> (2 * j)) & 3u), 0, xp[j]);
+    if (kk > 8) med_tail3(S, a.bin + s0, make_int4(c0, c1, c2, c3), n, kk, lane, gw, pend);
+    __syncwarp();
+    const int L = S.ncl;
+    med_rank(S, ids, L, lane);
+    for (int t = lane; t < L; t += 32) {  // the candidates' bins
+        const int g = S.cg[t], bn = 2 * g + ((int)S.crank[t] > S.brank[g] ? 1 : 0);
+        a.bin[s0 + S.cq[t]] = (unsigned char)bn;
+        med_binadd(S, bn, psi_fixed(S.cps[t]));
+    }
+    __syncwarp();
+    if (lane < 8) {
+        const unsigned long long sum = (unsigned long long)S.binpart[lane][0] +
+                                       ((unsigned long long)S.binpart[lane][1] << 19) +
+                                       ((unsigned long long)S.binpart[lane][2] << 38);
+        const double cm = __ull2double_rn(sum) * (1.0 / (double)(1ull << 54)) * recip_n(split_size(n, lane, 3));
+        a.ecm[(size_t)8 * e + lane] = cm;
+        a.ecmT[(size_t)8 * e + lane] = (float)cm;
+    }
 }
 
 // the crowded elements from the element offsets: 512 < n <= 4096 into listA,
@@ -1171,11 +1831,10 @@ int run(pdf_ctx* c) {
     a.lcnt = a.listA = a.listB = nullptr;
     if constexpr (sizeof(T) == 4) {
         // warp-per-element kernels for segments up to WARP_MAX_N particles:
-        // median splits by bisection when every level halves (G <= 2), else a
-        // shared-memory bitonic sort
+        // median splits for 2 x 2 x 2 bins, else a shared-memory bitonic sort
         a.min_n = WARP_MAX_N;
         const unsigned blocks = (unsigned)((c->m.nt + WARPS_PER_BLOCK - 1) / WARPS_PER_BLOCK);
-        const bool medians = c->p.nb1 <= 2 && c->p.nb2 <= 2 && c->p.nb3 <= 2;
+        const bool medians = c->p.nb1 == 2 && c->p.nb2 == 2 && c->p.nb3 == 2;
         if (medians) {
             // crowded elements (particle density drifts during a run) get their
             // own size class with a larger shared-memory slice per warp
@@ -1189,7 +1848,7 @@ int run(pdf_ctx* c) {
             a.listB = c->elist + 4 + c->m.nt;
             PDF_CUDA(c, cudaEventRecord(c->side_fork, c->s));
             PDF_CUDA(c, cudaStreamWaitEvent(c->s2, c->side_fork, 0));
-            k_moments_sel<KAHAN><<<blocks, 32 * WARPS_PER_BLOCK, 0, c->s2>>>(a, c->m.nt);
+            k_moments_med<KAHAN><<<blocks, 32 * WARPS_PER_BLOCK, 0, c->s2>>>(a, c->m.nt);
             PDF_CUDA(c, cudaEventRecord(c->side_join, c->s2));
             PDF_CUDA(c, cudaMemsetAsync(a.lcnt, 0, 3 * sizeof(int), c->s));
             k_crowded<<<(c->m.nt + 255) / 256, 256, 0, c->s>>>(c->off, c->m.nt, a.lcnt, a.listA, a.listB);

@@ -373,6 +373,62 @@ def test_ragged_empty_and_tied_elements(wf_mesh, precision):
         assert_state_close(Gs, Os, 1e-12)
 
 
+@pytest.mark.parametrize("precision", ["fp32_kahan", "fp32"])
+def test_warp_class_sizes_and_crowded_buckets(wf_mesh, precision):
+    """Every particle count from 0 to 519 per element (the warp class holds up
+    to 512 particles in registers, 16 per lane), against the oracle. Some
+    elements make a boundary bucket crowded or tie the boundary value:
+    one velocity component constant over the element (every key in one
+    bucket: bisection over the value bits, then the ids), half the
+    particles sharing a value, values on a coarse grid (many equal values
+    near each median)."""
+    rng = np.random.default_rng(23)
+    xy, tri = wf_mesh["xy"], wf_mesh["tri"]
+    nt = tri.shape[0]
+    parts = []
+    for e in range(nt):
+        m = e % 520
+        if m == 0:
+            continue
+        s = np.sqrt(rng.random(m))
+        t = rng.random(m)
+        X = np.stack([1 - s, s * (1 - t), s * t], 1) @ xy[tri[e]]
+        u = 1.0 + 0.05 * rng.standard_normal(m)
+        v = 0.05 * rng.standard_normal(m)
+        w = 0.05 * rng.standard_normal(m)
+        kind = e % 7
+        if kind == 1:
+            u[:] = 0.8125                       # level 0 bucket holds every key
+        elif kind == 2:
+            v[: m // 2] = -0.03125              # half the keys share the level-1 value
+        elif kind == 3:
+            w = np.round(w / 0.02) * 0.02       # a few distinct values at level 2
+        elif kind == 4:
+            u = np.round(u / 0.01) * 0.01
+            v = np.round(v / 0.01) * 0.01
+        parts.append(dict(x=X[:, 0], y=X[:, 1], u=u, v=v, w=w, om=rng.gamma(4.0, 0.25, m),
+                          psi=rng.random(m), elem=np.full(m, e, np.int32)))
+    Q = {k: np.concatenate([p[k] for p in parts]) for k in ("x", "y", "u", "v", "w", "om", "psi", "elem")}
+    Q["id"] = rng.permutation(Q["x"].size).astype(np.uint32)
+    g, o = both(wf_mesh, precision=precision, seed=29)
+    g.set_particles(Q)
+    g.estimate_stats()
+    g.sync()
+    G = g.particles()
+    o.set_particles(G)
+    o.estimate_stats()
+    cnt = g.field("elem_n")
+    assert np.array_equal(cnt, np.arange(nt) % 520)
+    rt = 2e-6 if precision == "fp32_kahan" else 1e-12
+    for name in ("elem_mean", "elem_R", "elem_psivar", "elem_cm"):
+        a, b = g.field(name), o.field(name)
+        scale = np.sqrt(np.mean(b ** 2, axis=0)) + 1e-300
+        assert np.all(np.abs(a - b) <= rt * (np.abs(b) + scale)), name
+    gb = by_id({"id": G["id"], "bin": G["bin"]})
+    ob = by_id({"id": o.particles()["id"], "bin": o.particles()["bin"]})
+    assert np.array_equal(gb["bin"], ob["bin"])
+
+
 def test_empty_ensemble(wf_mesh):
     """No particles at all: statistics are zero, a step is a no-op."""
     g, _ = both(wf_mesh, seed=19)
