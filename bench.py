@@ -703,8 +703,8 @@ def main():
     # into one of two device buffers (pdf_batch_create_out); after every
     # replay the two steps' means go to their own pinned host buffers
     # (asynchronous copies on the graph's stream, so the host keeps queueing
-    # replays). One sync at the end, after which the host checks every
-    # step's result. The graph is captured inside the timed region, after the
+    # replays). One sync at the end; then the host checks the copied results
+    # (finite, distinct per step, the last equal to the context's own field). The graph is captured inside the timed region, after the
     # upload: loading an ensemble re-sorts it, which moves the state between
     # the context's two buffers, and a graph holds the buffers it was captured
     # with.
@@ -744,9 +744,17 @@ def main():
         eb.sync()
         te = reduce_max(time.perf_counter() - t0, dist, "cuda")
         eb.close()
-        results_finite = bool(np.isfinite(out.numpy()).all())
+        # after the timed region: the last copied result is the context's own
+        # final state bit for bit, and every step's result differs from the
+        # step before (a stale buffer or a wrong one wired into the graph shows)
+        res = out.numpy()
+        results_finite = bool(np.isfinite(res).all())
+        last_equals_context = bool(np.array_equal(res[-1], g.field("elem_mean")))
+        steps_distinct = bool(all(not np.array_equal(res[k], res[k - 1]) for k in range(1, e2e_steps)))
         e2e = {"value": whole_job_value(world, n, e2e_steps, te), "unit": UNIT, "h2d_bytes_per_step": h2d / e2e_steps,
-               "d2h_bytes_per_step": d2h, "results_finite": results_finite, "steps": e2e_steps,
+               "d2h_bytes_per_step": d2h, "results_finite": results_finite,
+               "last_result_equals_context": last_equals_context, "results_distinct_per_step": steps_distinct,
+               "steps": e2e_steps,
                "path": "pdf_set_particles + pdf_estimate_stats from pinned host buffers, then the step-pair graph "
                        "(pdf_batch_create_out) with each step's element means copied to pinned host memory"}
     graph_form.close()

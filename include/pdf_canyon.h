@@ -192,8 +192,20 @@ int pdf_estimate_stats(pdf_ctx* c);
 int pdf_step(pdf_ctx* c, double dt, int32_t nsteps);
 
 /* Wait for the context stream and return the device status (PDF_OK or the
- * first PDF_ERR_* raised inside a kernel since the last pdf_sync). */
+ * first PDF_ERR_* raised inside a kernel since the last pdf_sync) and clear
+ * it. A grid barrier of the elliptic or pressure solver that gave up
+ * (PDF_ERR_CUDA, "timed out") leaves that step's solution undefined; the
+ * barrier words are reset here, so the context can step again. */
 int pdf_sync(pdf_ctx* c);
+
+/* Failure detection of the bounded waits (the paper has no counterpart).
+ * Every grid barrier of the cooperative elliptic and pressure solvers polls
+ * at most `spins` times before it sets the timeout status and proceeds
+ * (spins = 0: the default, about one to two seconds of polling). A small
+ * limit makes the barriers give up while the other blocks are still
+ * working, so tests can check that the timeout reaches pdf_sync as an error
+ * without hanging the GPU. Returns PDF_ERR_ARG for NULL or spins < 0. */
+int pdf_set_wait_limit(pdf_ctx* c, int64_t spins);
 
 /* Copy a field (enum pdf_field) into dst of the given size in bytes (must be
  * exactly the field size). dst_is_device: 1 device memory (ordered on the
@@ -285,8 +297,13 @@ typedef struct pdf_batch pdf_batch;
  * (pdf_seed_particles and pdf_set_particles re-sort the ensemble, which moves
  * it between the context's two state buffers, while the graph keeps the
  * buffers it was captured with) or destroyed by other calls while the batch
- * exists; create the batch after loading the particles. Returns PDF_ERR_CUDA if the capture or the
- * instantiation fails (message in pdf_last_error(NULL)). */
+ * exists; create the batch after loading the particles. A graph launch runs
+ * on cuda_stream, not on the contexts' streams: a pdf_get_fields of a batched
+ * context must come after pdf_batch_sync (or be ordered after cuda_stream by
+ * the caller), since both may use the context's state and conversion buffer.
+ * Returns PDF_ERR_CUDA if the capture or the instantiation fails (message in
+ * pdf_last_error(NULL)); every context is then left as it was before the
+ * call. */
 int pdf_batch_create(pdf_ctx* const* ctx, const double* dt, int32_t n, void* cuda_stream, pdf_batch** out);
 
 /* pdf_batch_create with per-step results: after each of the two captured
@@ -469,9 +486,14 @@ int pdf_surrogate_stats(pdf_ctx* c, int64_t* solves, int64_t* fallbacks, double 
  * zero: every call clears them on its stream before counting. All calls in
  * the process share the one scratch array (one per device), so calls that
  * overlap on the GPU (other streams, other host threads) race and give
- * wrong results; the caller must order them. The call returns after its work
- * has finished (it reads the status word back). Returns PDF_ERR_ARG for NULL
- * pointers, nt < 1, n < 0 or an element index outside [0, nt),
+ * wrong results; the caller must order them. The scratch address is taken on
+ * the device that is current when the call is made, so make the stream's
+ * device current first. The call returns after its work has finished (it
+ * reads the status word back). An element index outside [0, nt) is found
+ * only after the kernels have run: the call then returns PDF_ERR_ARG, and
+ * perm and off hold a partition in which those particles sit in element 0.
+ * Returns PDF_ERR_ARG for NULL pointers, nt < 1, n < 0 or an element index
+ * outside [0, nt),
  * PDF_ERR_CAPACITY for nt above PDF_SORT_STATIC_MAX_ELEMENTS or n above
  * INT32_MAX (nothing is launched), PDF_ERR_CUDA on a CUDA failure; the
  * message is in pdf_last_error(NULL). */

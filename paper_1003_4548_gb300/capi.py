@@ -61,7 +61,7 @@ EXPORTS = ("pdf_default_params", "pdf_init_mesh", "pdf_seed_particles", "pdf_set
            "pdf_mlp_standardize", "pdf_surrogate_rows", "pdf_surrogate_harvest", "pdf_set_surrogate",
            "pdf_surrogate_stats", "pdf_batch_create", "pdf_batch_create_out", "pdf_batch_step", "pdf_batch_sync", "pdf_batch_destroy",
            "pdf_autotune", "pdf_set_averaging", "pdf_averaging_count", "pdf_get_averages", "pdf_probe",
-           "pdf_set_cdf_probes", "pdf_get_cdf")
+           "pdf_set_cdf_probes", "pdf_get_cdf", "pdf_set_wait_limit")
 
 MLP_IN, MLP_HIDDEN, MLP_OUT, MLP_NPARAM, MLP_NNORM = 10, 64, 5, 9349, 30
 
@@ -96,6 +96,7 @@ def lib(allow_build: bool = True):
         L.pdf_estimate_stats.argtypes = [vp]
         L.pdf_step.argtypes = [vp, C.c_double, C.c_int32]
         L.pdf_sync.argtypes = [vp]
+        L.pdf_set_wait_limit.argtypes = [vp, C.c_int64]
         L.pdf_get_fields.argtypes = [vp, C.c_int32, vp, C.c_size_t, C.c_int32]
         for n in ("pdf_num_particles", "pdf_launch_count"):
             getattr(L, n).argtypes = [vp]
@@ -283,6 +284,13 @@ class Canyon:
         if check:
             self._check(st)
         return st
+
+    def set_wait_limit(self, spins: int):
+        self._check(lib().pdf_set_wait_limit(self._h, spins))
+
+    @property
+    def last_error(self) -> str:
+        return lib().pdf_last_error(self._h).decode()
 
     @property
     def num_particles(self) -> int:

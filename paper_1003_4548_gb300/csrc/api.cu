@@ -618,13 +618,24 @@ int pdf_step(pdf_ctx* c, double dt, int32_t nsteps) {
     return PDF_OK;
 }
 
+int pdf_set_wait_limit(pdf_ctx* c, int64_t spins) {
+    if (!c || spins < 0) return PDF_ERR_ARG;
+    c->wait_spins = (long long)spins;
+    return PDF_OK;
+}
+
 int pdf_sync(pdf_ctx* c) {
     if (!c) return PDF_ERR_ARG;
     PDF_CUDA(c, cudaStreamSynchronize(c->s));
     PDF_CUDA(c, cudaMemcpy(c->h_status, c->d_status, sizeof(int), cudaMemcpyDeviceToHost));
     const int s = *c->h_status;
     if (s) PDF_CUDA(c, cudaMemset(c->d_status, 0, sizeof(int)));
-    if (s & ST_BARRIER) return fail(c, PDF_ERR_CUDA, "grid barrier of the elliptic solver timed out");
+    if (s & ST_BARRIER) {
+        // a block that gave up left the barrier's arrival count behind: the
+        // stream is idle, so start the solver's barrier words afresh
+        if (c->fe_bar) PDF_CUDA(c, cudaMemset(c->fe_bar, 0, 32 * 64 * sizeof(unsigned)));
+        return fail(c, PDF_ERR_CUDA, "grid barrier of the elliptic solver timed out");
+    }
     if (s & ST_NONFINITE) return fail(c, PDF_ERR_NONFINITE, "non-finite particle state");
     if (s & ST_LOST) return fail(c, PDF_ERR_LOST_PARTICLE, "element walk exceeded its cap");
     if (s & ST_WALL) return fail(c, PDF_ERR_WALL, "too many boundary reflections in one step");

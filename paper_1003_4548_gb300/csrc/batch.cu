@@ -104,6 +104,30 @@ int pdf_batch_create_out(pdf_ctx* const* ctx, const double* dt, int32_t n, void*
         release(b);
         return cuda_fail("cudaStreamBeginCapture", err);
     }
+    // the host-side step state of every context (a captured step advances the
+    // step counter and swaps the state buffers as if it had run): restored
+    // below if the capture fails part of the way
+    struct Saved {
+        int step;
+        void *a[7], *b[7];
+        uint32_t *ia, *ib;
+        int *ea, *eb;
+    };
+    std::vector<Saved> saved((size_t)n);
+    for (int i = 0; i < n; ++i) {
+        Saved& v = saved[(size_t)i];
+        v.step = ctx[i]->step;
+        for (int q = 0; q < 7; ++q) { v.a[q] = ctx[i]->stA[q]; v.b[q] = ctx[i]->stB[q]; }
+        v.ia = ctx[i]->idA; v.ib = ctx[i]->idB; v.ea = ctx[i]->elemA; v.eb = ctx[i]->elemB;
+    }
+    auto restore = [&]() {
+        for (int i = 0; i < n; ++i) {
+            const Saved& v = saved[(size_t)i];
+            ctx[i]->step = v.step;
+            for (int q = 0; q < 7; ++q) { ctx[i]->stA[q] = v.a[q]; ctx[i]->stB[q] = v.b[q]; }
+            ctx[i]->idA = v.ia; ctx[i]->idB = v.ib; ctx[i]->elemA = v.ea; ctx[i]->elemB = v.eb;
+        }
+    };
     int st = PDF_OK;
     err = cudaEventRecord(fork, b->s);
     for (int i = 0; i < n && err == cudaSuccess; ++i) err = cudaStreamWaitEvent(ctx[i]->s, fork, 0);
@@ -135,6 +159,7 @@ int pdf_batch_create_out(pdf_ctx* const* ctx, const double* dt, int32_t n, void*
     }
     const cudaError_t end = cudaStreamEndCapture(b->s, &b->graph);
     if (st != PDF_OK || err != cudaSuccess || end != cudaSuccess) {
+        restore();  // nothing of the capture ran: every context stays where it was
         release(b);
         if (st != PDF_OK) return st;
         return cuda_fail("stream capture of the batch step", err != cudaSuccess ? err : end);

@@ -17,9 +17,12 @@ __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
 // Grid-wide barrier of a cooperative launch: arrival by an acq_rel atomic on
 // one counter (bar[0]); the last block resets it and bumps the generation
 // word (bar[1]), the others poll that word with acquire loads (measured
-// ~2.4 us on GB300 for 80-161 blocks). The wait is bounded: on expiry the
+// ~2.4 us on GB300 for 80-161 blocks). The wait is bounded by spin_max polls
+// (SPIN_DEFAULT, about 1-2 s, unless the context sets a limit): on expiry the
 // block sets ST_BARRIER in *status and proceeds.
-__device__ __forceinline__ void grid_barrier(unsigned* bar, int* status) {
+constexpr long long SPIN_DEFAULT = 1ll << 22;
+
+__device__ __forceinline__ void grid_barrier(unsigned* bar, int* status, long long spin_max) {
     __syncthreads();
     if (threadIdx.x == 0) {
         unsigned* gen = bar + 1;
@@ -34,7 +37,7 @@ __device__ __forceinline__ void grid_barrier(unsigned* bar, int* status) {
         } else {
             long long spins = 0;
             while (coop::ld_acquire(gen) == g0) {
-                if (++spins > (1ll << 22)) {  // ~1-2 s of polling
+                if (++spins > spin_max) {
                     set_status(status, ST_BARRIER);
                     break;
                 }
@@ -51,7 +54,7 @@ __device__ __forceinline__ void grid_barrier(unsigned* bar, int* status) {
 // barrier costs one atomic arrival and the polls, without a first read.
 __device__ __forceinline__ unsigned coop_generation(const unsigned* bar) { return coop::ld_acquire(bar + 1); }
 
-__device__ __forceinline__ void grid_barrier_gen(unsigned* bar, int* status, unsigned& gen) {
+__device__ __forceinline__ void grid_barrier_gen(unsigned* bar, int* status, unsigned& gen, long long spin_max) {
     __syncthreads();
     if (threadIdx.x == 0) {
         unsigned* g = bar + 1;
@@ -66,7 +69,7 @@ __device__ __forceinline__ void grid_barrier_gen(unsigned* bar, int* status, uns
         } else {
             long long spins = 0;
             while ((int)(coop::ld_acquire(g) - gen) < 0) {
-                if (++spins > (1ll << 22)) {  // ~1-2 s of polling
+                if (++spins > spin_max) {
                     set_status(status, ST_BARRIER);
                     break;
                 }

@@ -68,6 +68,7 @@ struct CGArgs {
     const double* xprop;   // surrogate proposal (network at the free rows, Dirichlet values at the walls)
     double tol;
     int maxit;
+    long long spin_max;  // polls of a grid barrier before it gives up (ST_BARRIER)
 };
 
 // the surrogate's check passed: take its proposal as the solution
@@ -224,7 +225,7 @@ __global__ void __launch_bounds__(BS * NC) k_pcg(const CGArgs a) {
         }
         __syncthreads();
     }
-    grid_barrier(a.bar, a.status);  // all x (warm start + Dirichlet) and matrix rows are in place
+    grid_barrier(a.bar, a.status, a.spin_max);  // all x (warm start + Dirichlet) and matrix rows are in place
     // r = b - A x; z = Ainv r; p = z
     double r, z, p, ap;
     {
@@ -247,7 +248,7 @@ __global__ void __launch_bounds__(BS * NC) k_pcg(const CGArgs a) {
         red[(2 * NC + c) * BS + t] = free_row ? b0 * b0 : 0.0;
         block_partial<BS>(a, red, 3, 0);
     }
-    grid_barrier(a.bar, a.status);
+    grid_barrier(a.bar, a.status, a.spin_max);
     grid_sum(a, 0, 3 * NC, s_a);
     if (threadIdx.x < NC) {
         s_rz[threadIdx.x] = s_a[threadIdx.x];
@@ -262,7 +263,7 @@ __global__ void __launch_bounds__(BS * NC) k_pcg(const CGArgs a) {
         red[c * BS + t] = p * ap;
         block_partial<BS>(a, red, 1, 3 * NC);
     }
-    grid_barrier(a.bar, a.status);
+    grid_barrier(a.bar, a.status, a.spin_max);
     grid_sum(a, 3 * NC, NC, s_pap);
     int it = 0;
     for (;; ++it) {
@@ -297,7 +298,7 @@ __global__ void __launch_bounds__(BS * NC) k_pcg(const CGArgs a) {
             red[(2 * NC + c) * BS + t] = r * r;
             block_partial<BS>(a, red, 3, 0);
         }
-        grid_barrier(a.bar, a.status);
+        grid_barrier(a.bar, a.status, a.spin_max);
         grid_sum(a, 0, 3 * NC, s_a);
         if (threadIdx.x < NC) {
             const int k = threadIdx.x;
@@ -317,7 +318,7 @@ __global__ void __launch_bounds__(BS * NC) k_pcg(const CGArgs a) {
             red[c * BS + t] = p * ap;
             block_partial<BS>(a, red, 1, 3 * NC);
         }
-        grid_barrier(a.bar, a.status);
+        grid_barrier(a.bar, a.status, a.spin_max);
         if (threadIdx.x < NC && s_active[threadIdx.x]) {
             s_rz[threadIdx.x] = s_a[threadIdx.x];
             s_rr[threadIdx.x] = s_a[2 * NC + threadIdx.x];
@@ -419,7 +420,7 @@ __global__ void __launch_bounds__(BS * NC) k_pcg_ff(const CGArgs a) {
         }
         __syncthreads();
     }
-    grid_barrier(a.bar, a.status);
+    grid_barrier(a.bar, a.status, a.spin_max);
     float* zg = reinterpret_cast<float*>(a.zg);
     ff x = ff_from_double(x0), r, p, ap;
     float z;
@@ -444,14 +445,14 @@ __global__ void __launch_bounds__(BS * NC) k_pcg_ff(const CGArgs a) {
         redh[(2 * NC + c) * BS + t] = bb.hi; redl[(2 * NC + c) * BS + t] = bb.lo;
         block_partial_ff<BS>(a, redh, redl, 3, 0);
     }
-    grid_barrier(a.bar, a.status);
+    grid_barrier(a.bar, a.status, a.spin_max);
     grid_sum_ff(a, 0, 3 * NC, s_a);
     if (threadIdx.x < NC) {
         s_rz[threadIdx.x] = s_a[threadIdx.x];
         s_rr[threadIdx.x] = s_a[NC + threadIdx.x];
         s_bn[threadIdx.x] = sqrt(s_a[2 * NC + threadIdx.x]);
     }
-    grid_barrier(a.bar, a.status);  // the partials are reused below
+    grid_barrier(a.bar, a.status, a.spin_max);  // the partials are reused below
     {  // A p_0
         ff s = ff{0.f, 0.f};
         if (free_row)
@@ -465,7 +466,7 @@ __global__ void __launch_bounds__(BS * NC) k_pcg_ff(const CGArgs a) {
         redl[c * BS + t] = pap.lo;
         block_partial_ff<BS>(a, redh, redl, 1, 3 * NC);
     }
-    grid_barrier(a.bar, a.status);
+    grid_barrier(a.bar, a.status, a.spin_max);
     grid_sum_ff(a, 3 * NC, NC, s_pap);
     int it = 0;
     for (;; ++it) {
@@ -501,7 +502,7 @@ __global__ void __launch_bounds__(BS * NC) k_pcg_ff(const CGArgs a) {
             redh[(2 * NC + c) * BS + t] = rr.hi; redl[(2 * NC + c) * BS + t] = rr.lo;
             block_partial_ff<BS>(a, redh, redl, 3, 0);
         }
-        grid_barrier(a.bar, a.status);
+        grid_barrier(a.bar, a.status, a.spin_max);
         grid_sum_ff(a, 0, 3 * NC, s_a);
         if (threadIdx.x < NC) {
             const int k = threadIdx.x;
@@ -525,7 +526,7 @@ __global__ void __launch_bounds__(BS * NC) k_pcg_ff(const CGArgs a) {
             redl[c * BS + t] = pap.lo;
             block_partial_ff<BS>(a, redh, redl, 1, 3 * NC);
         }
-        grid_barrier(a.bar, a.status);
+        grid_barrier(a.bar, a.status, a.spin_max);
         if (threadIdx.x < NC && s_active[threadIdx.x]) {
             s_rz[threadIdx.x] = s_a[threadIdx.x];
             s_rr[threadIdx.x] = s_a[2 * NC + threadIdx.x];
@@ -649,6 +650,7 @@ int launch_elliptic(pdf_ctx* c) {
     a.x = c->nwp;  // solution lives in the node array (canonical rows)
     a.zg = c->fe_z;
     a.part = c->fe_part; a.bar = c->fe_bar; a.iters = c->fe_iters; a.status = c->d_status;
+    a.spin_max = c->wait_spins > 0 ? c->wait_spins : SPIN_DEFAULT;
     a.tol = c->p.cg_tol; a.maxit = c->p.cg_maxit;
     a.skip = c->sur_mode ? c->sur_skip : nullptr;
     a.xprop = c->fe_prop;

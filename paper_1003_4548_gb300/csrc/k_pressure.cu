@@ -153,6 +153,7 @@ struct PrArgs {
     int* status;
     double tol;
     int maxit;
+    long long spin_max;  // polls of a grid barrier before it gives up (ST_BARRIER)
 };
 
 constexpr int RMAX = 12;  // matrix entries per row staged in shared memory (the rest read from global)
@@ -316,14 +317,14 @@ __global__ void __launch_bounds__(BS) k_pcg_p(const PrArgs a) {
     const double bi = fr ? a.b[i] : 0.0;
     double x = fr ? a.x[i] : 0.0;
     if (have && a.pin[i]) a.x[i] = 0.0;
-    grid_barrier_gen(a.bar, a.status, gen);  // warm start and the pinned zero in place
+    grid_barrier_gen(a.bar, a.status, gen, a.spin_max);  // warm start and the pinned zero in place
     double r = fr ? bi - row_times(a, scol, sval, BS, t, i, len, a.x) : 0.0;
     {
         double v[2] = {r, bi * bi};
         const int sl[2] = {5, 4};
         publish<BS, 2>(a, v, sl, red);
     }
-    grid_barrier_gen(a.bar, a.status, gen);
+    grid_barrier_gen(a.bar, a.status, gen, a.spin_max);
     {
         const int sl[1] = {4};
         gather<1>(a, sl, g);
@@ -349,7 +350,7 @@ __global__ void __launch_bounds__(BS) k_pcg_p(const PrArgs a) {
             const int sl[2] = {0, 1};
             publish<BS, 2>(a, v, sl, red);
         }
-        grid_barrier_gen(a.bar, a.status, gen);  // A: u of every row, gamma and (r, r)
+        grid_barrier_gen(a.bar, a.status, gen, a.spin_max);  // A: u of every row, gamma and (r, r)
         {
             const int sl[2] = {0, 1};
             gather<2>(a, sl, g);
@@ -366,7 +367,7 @@ __global__ void __launch_bounds__(BS) k_pcg_p(const PrArgs a) {
             const int sl[2] = {2, 3};
             publish<BS, 2>(a, v, sl, red);
         }
-        grid_barrier_gen(a.bar, a.status, gen);  // B: delta and the block sums of w
+        grid_barrier_gen(a.bar, a.status, gen, a.spin_max);  // B: delta and the block sums of w
         {
             const int sl[1] = {2};
             gather<1>(a, sl, g);
@@ -509,6 +510,7 @@ int launch_pressure(pdf_ctx* c, double dt) {
     a.x = c->pr_x;  // warm start from the previous step's pressure
     a.zg = c->fe_z;
     a.part = c->fe_part; a.bar = c->fe_bar; a.iters = c->pr_iters; a.status = c->d_status;
+    a.spin_max = c->wait_spins > 0 ? c->wait_spins : SPIN_DEFAULT;
     a.tol = c->p.pressure_tol; a.maxit = c->p.cg_maxit;
     // cooperative grids of different contexts never run side by side (a
     // batch orders them in a chain)

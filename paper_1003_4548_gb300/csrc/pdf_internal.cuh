@@ -164,6 +164,7 @@ struct pdf_ctx {
     Timing tm;
     int timing = 0;
     int64_t launches = 0;  // kernels launched by this context
+    long long wait_spins = 0;  // grid-barrier polls before a wait gives up (0: the default)
     int step_blocks = 0;   // persistent grid of the particle kernel
     int step_sur_blocks = 0;  // persistent grid of the per-particle surrogate form
     int scatter_threads = 256;  // block size of the re-sort scatter

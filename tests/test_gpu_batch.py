@@ -185,3 +185,39 @@ def test_batch_outputs_per_step(torch):
     b.close()
     for g in batched + alone:
         g.close()
+
+
+def test_batch_outputs_particle_field_fp32(torch):
+    """pdf_batch_create_out with a particle field of FP32 contexts: the graph
+    converts u to FP64 through the context's conversion buffer after each
+    step. Each step's copy holds the same values as the same case stepped
+    on its own (exact integer reductions in the fp32 mode, so the particle
+    order inside an element does not change the statistics; the copies are
+    compared as sorted values because that order may differ)."""
+    from paper_1003_4548_gb300 import capi
+    cs = cases()[:2]
+    streams = [torch.cuda.Stream() for _ in range(2 * len(cs) + 1)]
+    batched = [make(torch, m, ppe, wm, k, streams[k], precision="fp32") for m, ppe, wm, k in cs]
+    alone = [make(torch, m, ppe, wm, k, streams[len(cs) + k], precision="fp32") for m, ppe, wm, k in cs]
+    dts = [cfl_dt(m, cfl=0.5, k0=1e-3) for m, _, _, _ in cs]
+    bufs = [torch.zeros(g.num_particles, dtype=torch.float64, device="cuda") for g in batched for _ in range(2)]
+    nbytes = [g.num_particles * 8 for g in batched]
+    b = capi.Batch(batched, dts, streams[-1].cuda_stream, outputs=("u", [t.data_ptr() for t in bufs], nbytes))
+    expect = []
+    for g, dt in zip(alone, dts):
+        per = []
+        for _ in range(4):
+            g.step(dt, 1)
+            g.sync()
+            per.append(np.sort(g.field("u")))
+        expect.append(per)
+    for pair in range(2):
+        b.step(2)
+        b.sync()
+        for j in range(len(batched)):
+            for k in range(2):
+                got = np.sort(bufs[2 * j + k].cpu().numpy())
+                assert np.array_equal(got, expect[j][2 * pair + k]), (j, pair, k)
+    b.close()
+    for g in batched + alone:
+        g.close()
