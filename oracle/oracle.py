@@ -97,6 +97,12 @@ def load(path: str):
     L.orc_set_node_fields.argtypes = [C.c_void_p, d, d, d]
     L.orc_set_node_wp.argtypes = [C.c_void_p, d]
     L.orc_h_contract.argtypes = [P(orc_params), d, d, C.c_double, C.c_double, d]
+    L.orc_set_averaging.argtypes = [C.c_void_p, C.c_int32, C.c_int32]
+    L.orc_averaging_count.argtypes = [C.c_void_p]
+    L.orc_get_averages.argtypes = [C.c_void_p, C.c_int32, d]
+    L.orc_probe.argtypes = [C.c_void_p, C.c_int32, C.c_int32, d, d, C.c_int32, d, i32]
+    L.orc_set_cdf_probes.argtypes = [C.c_void_p, d, d, C.c_int32, C.c_int32]
+    L.orc_get_cdf.argtypes = [C.c_void_p, d, i32]
     return L
 
 
@@ -244,6 +250,46 @@ class Oracle:
     def set_node_wp(self, wp):
         wp = np.ascontiguousarray(wp, np.float64)
         self._check(self._L.orc_set_node_wp(self._c, _p(wp, C.c_double)))
+
+    # time averages, probes, scalar CDFs (Section 3, Table 1, Fig. 7)
+    AVERAGES = dict(elem_mean=(0, 5), elem_R=(1, 6), elem_psivar=(2, 1), node_mean=(3, 4))
+    PROBES = dict(node_mean=0, elem_mean=1, elem_R=2, avg_node_mean=3, avg_elem_mean=4, avg_elem_R=5)
+
+    def set_averaging(self, on: bool, reset: bool = False):
+        self._check(self._L.orc_set_averaging(self._c, int(on), int(reset)))
+
+    @property
+    def averaging_count(self) -> int:
+        return self._L.orc_averaging_count(self._c)
+
+    def averages(self, name: str) -> np.ndarray:
+        which, width = self.AVERAGES[name]
+        rows = self.nnode if name == "node_mean" else self.ntri
+        out = np.empty(rows * width, np.float64)
+        self._check(self._L.orc_get_averages(self._c, which, _p(out, C.c_double)))
+        return out.reshape(rows, width) if width > 1 else out
+
+    def probe(self, name: str, comp: int, x, y):
+        x = np.ascontiguousarray(x, np.float64)
+        y = np.ascontiguousarray(y, np.float64)
+        out = np.empty(x.size, np.float64)
+        el = np.empty(x.size, np.int32)
+        self._check(self._L.orc_probe(self._c, self.PROBES[name], comp, _p(x, C.c_double), _p(y, C.c_double),
+                                      x.size, _p(out, C.c_double), _p(el, C.c_int32)))
+        return out, el
+
+    def set_cdf_probes(self, x, y, nbins: int):
+        x = np.ascontiguousarray(x, np.float64)
+        y = np.ascontiguousarray(y, np.float64)
+        self._cdf_shape = (x.size, nbins)
+        self._check(self._L.orc_set_cdf_probes(self._c, _p(x, C.c_double), _p(y, C.c_double), x.size, nbins))
+
+    def cdf(self):
+        n, nb = self._cdf_shape
+        out = np.empty(n * nb, np.float64)
+        el = np.empty(n, np.int32)
+        self._check(self._L.orc_get_cdf(self._c, _p(out, C.c_double), _p(el, C.c_int32)))
+        return out.reshape(n, nb), el
 
     def locate(self, x: float, y: float) -> int:
         return self._L.orc_locate(self._c, x, y)

@@ -97,6 +97,12 @@ struct orc_ctx {
     /* FE matrix (CSR over canonical nodes) */
     int *rowptr, *colidx;
     double* aval;
+    /* time averaging (Section 3): sums over the averaged steps */
+    int avg_on, avg_n;
+    double *avg_e, *avg_nd;     /* ntri x 12 (means 5, second moments 6, psi variance), nnode x 4 */
+    int cdf_n, cdf_bins;
+    int* cdf_elem;              /* element of each CDF point */
+    double* cdf_hist;           /* cdf_n x cdf_bins counts of particle psi */
 };
 
 /* ------------------------------------------------------------------------- */
@@ -205,7 +211,7 @@ void orc_destroy(orc_ctx* c) {
                     c->wnx, c->wny, c->wdist, c->is_wall, c->gb_off, c->gb, c->x, c->y, c->u, c->v,
                     c->w, c->om, c->psi, c->id, c->elem, c->bin, c->en, c->emean, c->eR, c->epsivar,
                     c->ecm, c->eomw, c->nomw, c->npres, c->nwt, c->nmean, c->nR, c->nke, c->npsivar, c->eder, c->ngrad, c->npack,
-                    c->nwp, c->rowptr, c->colidx, c->aval};
+                    c->nwp, c->rowptr, c->colidx, c->aval, c->avg_e, c->avg_nd, c->cdf_elem, c->cdf_hist};
     for (size_t i = 0; i < sizeof(ptrs) / sizeof(ptrs[0]); ++i) free(ptrs[i]);
     free(c);
 }
@@ -1234,6 +1240,157 @@ int orc_project(orc_ctx* c, double dt) {
     return orc_estimate_stats(c);
 }
 
+/* ------------------------------------------------------------------------- */
+/* time averages, probes and scalar CDFs (Section 3: once the flow is          */
+/* statistically stationary the statistics are averaged in time; the scalar  */
+/* is sampled at the wall points of Table 1; Fig. 7 shows cumulative           */
+/* distributions of the scalar at points of the canyon)                        */
+/* ------------------------------------------------------------------------- */
+
+/* the element of a point: the largest smallest barycentric coordinate over
+ * all elements (the containing element, or the nearest one for a point
+ * outside the fluid domain), lowest id on ties; x taken modulo the period;
+ * lam gets the point's barycentric coordinates in that element */
+static int probe_element(const orc_ctx* c, double x, double y, double lam[3]) {
+    x -= c->p.period * floor(x / c->p.period);
+    int best = 0;
+    double bm = -HUGE_VAL;
+    for (int e = 0; e < c->nt; ++e) {
+        double l[3];
+        for (int k = 0; k < 3; ++k) {
+            const int a = c->tri[3 * e + (k + 1) % 3], b = c->tri[3 * e + (k + 2) % 3];
+            l[k] = orient(c->xy[2 * a], c->xy[2 * a + 1], c->xy[2 * b], c->xy[2 * b + 1], x, y) / c->area2[e];
+        }
+        const double m = mind(l[0], mind(l[1], l[2]));
+        if (m > bm) {
+            bm = m;
+            best = e;
+            lam[0] = l[0]; lam[1] = l[1]; lam[2] = l[2];
+        }
+    }
+    return best;
+}
+
+int orc_set_averaging(orc_ctx* c, int32_t on, int32_t reset) {
+    if (!c->avg_e) {
+        c->avg_e = (double*)xcalloc((size_t)12 * c->nt, sizeof(double));
+        c->avg_nd = (double*)xcalloc((size_t)4 * c->nn, sizeof(double));
+        reset = 1;
+    }
+    if (reset) {
+        memset(c->avg_e, 0, sizeof(double) * 12 * (size_t)c->nt);
+        memset(c->avg_nd, 0, sizeof(double) * 4 * (size_t)c->nn);
+        c->avg_n = 0;
+        if (c->cdf_hist) memset(c->cdf_hist, 0, sizeof(double) * (size_t)c->cdf_n * c->cdf_bins);
+    }
+    c->avg_on = on ? 1 : 0;
+    return ORC_OK;
+}
+
+int32_t orc_averaging_count(const orc_ctx* c) { return c->avg_n; }
+
+/* one averaged step: the current element and node statistics join the sums,
+ * and the psi of every particle in a CDF point's element its histogram */
+static void accumulate_averages(orc_ctx* c) {
+    if (!c->avg_on) return;
+    for (int e = 0; e < c->nt; ++e) {
+        double* s = &c->avg_e[12 * e];
+        for (int q = 0; q < 5; ++q) s[q] += c->emean[5 * e + q];
+        for (int q = 0; q < 6; ++q) s[5 + q] += c->eR[6 * e + q];
+        s[11] += c->epsivar[e];
+    }
+    for (int i = 0; i < c->nn; ++i)
+        for (int q = 0; q < 4; ++q) c->avg_nd[4 * i + q] += c->nmean[4 * i + q];
+    c->avg_n++;
+    for (int k = 0; k < c->cdf_n; ++k)
+        for (int i = 0; i < c->np; ++i) {
+            if (c->elem[i] != c->cdf_elem[k]) continue;
+            int b = (int)(c->psi[i] * c->cdf_bins);
+            if (b < 0) b = 0;
+            if (b >= c->cdf_bins) b = c->cdf_bins - 1;
+            c->cdf_hist[(size_t)k * c->cdf_bins + b] += 1.0;
+        }
+}
+
+/* which: 0 element means [ntri][5], 1 second moments [ntri][6], 2 psi
+ * variance [ntri], 3 node means [nnode][4]; the sums over the averaged
+ * steps divided by their number */
+int orc_get_averages(const orc_ctx* c, int32_t which, double* out) {
+    if (which < 0 || which > 3) return ORC_ERR_ARG;
+    if (c->avg_n == 0) return ORC_ERR_STATE;
+    if (which == 3) {
+        for (int i = 0; i < 4 * c->nn; ++i) out[i] = c->avg_nd[i] / c->avg_n;
+        return ORC_OK;
+    }
+    const int w = which == 0 ? 5 : (which == 1 ? 6 : 1), f = which == 0 ? 0 : (which == 1 ? 5 : 11);
+    for (int e = 0; e < c->nt; ++e)
+        for (int q = 0; q < w; ++q) out[w * e + q] = c->avg_e[12 * e + f + q] / c->avg_n;
+    return ORC_OK;
+}
+
+/* which: 0 node means (linear in the element), 1 element means, 2 element
+ * second moments, 3 .. 5 the same time-averaged; component comp */
+int orc_probe(const orc_ctx* c, int32_t which, int32_t comp, const double* x, const double* y, int32_t n,
+              double* out, int32_t* elem_out) {
+    const int width[6] = {4, 5, 6, 4, 5, 6};
+    if (which < 0 || which > 5 || comp < 0 || comp >= width[which]) return ORC_ERR_ARG;
+    if (which >= 3 && c->avg_n == 0) return ORC_ERR_STATE;
+    for (int k = 0; k < n; ++k) {
+        double lam[3];
+        const int e = probe_element(c, x[k], y[k], lam);
+        if (elem_out) elem_out[k] = e;
+        if (which == 0 || which == 3) {
+            double v = 0.0;
+            for (int m = 0; m < 3; ++m) {
+                const int a = c->tri[3 * e + m];
+                v += lam[m] * (which == 0 ? c->nmean[4 * a + comp] : c->avg_nd[4 * a + comp] / c->avg_n);
+            }
+            out[k] = v;
+        } else if (which == 1) {
+            out[k] = c->emean[5 * e + comp];
+        } else if (which == 2) {
+            out[k] = c->eR[6 * e + comp];
+        } else {
+            out[k] = c->avg_e[12 * e + (which == 4 ? 0 : 5) + comp] / c->avg_n;
+        }
+    }
+    return ORC_OK;
+}
+
+int orc_set_cdf_probes(orc_ctx* c, const double* x, const double* y, int32_t n, int32_t nbins) {
+    if (n < 0 || nbins < 1) return ORC_ERR_ARG;
+    free(c->cdf_elem);
+    free(c->cdf_hist);
+    c->cdf_elem = NULL;
+    c->cdf_hist = NULL;
+    c->cdf_n = 0;
+    if (n == 0) return ORC_OK;
+    c->cdf_elem = (int*)xcalloc(n, sizeof(int));
+    c->cdf_hist = (double*)xcalloc((size_t)n * nbins, sizeof(double));
+    for (int k = 0; k < n; ++k) {
+        double lam[3];
+        c->cdf_elem[k] = probe_element(c, x[k], y[k], lam);
+    }
+    c->cdf_n = n;
+    c->cdf_bins = nbins;
+    return ORC_OK;
+}
+
+/* F at the bin edges 1/nbins .. 1 of every CDF point: out[n][nbins] */
+int orc_get_cdf(const orc_ctx* c, double* out, int32_t* elem_out) {
+    if (c->cdf_n == 0) return ORC_ERR_STATE;
+    for (int k = 0; k < c->cdf_n; ++k) {
+        double tot = 0.0, run = 0.0;
+        for (int b = 0; b < c->cdf_bins; ++b) tot += c->cdf_hist[(size_t)k * c->cdf_bins + b];
+        for (int b = 0; b < c->cdf_bins; ++b) {
+            run += c->cdf_hist[(size_t)k * c->cdf_bins + b];
+            out[(size_t)k * c->cdf_bins + b] = tot > 0.0 ? run / tot : 0.0;
+        }
+        if (elem_out) elem_out[k] = c->cdf_elem[k];
+    }
+    return ORC_OK;
+}
+
 int orc_step(orc_ctx* c, double dt, int32_t nsteps) {
     for (int s = 0; s < nsteps; ++s) {
         int st = orc_advance(c, dt);
@@ -1244,6 +1401,7 @@ int orc_step(orc_ctx* c, double dt, int32_t nsteps) {
             st = orc_project(c, dt);
             if (st != ORC_OK) return st;
         }
+        accumulate_averages(c);
     }
     return ORC_OK;
 }

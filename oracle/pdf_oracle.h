@@ -95,6 +95,18 @@ int orc_advance_subset(orc_ctx* c, double dt, const int32_t* idx, int32_t n);
 int orc_get_field(const orc_ctx* c, int32_t field, double* out);
 int32_t orc_cg_iterations(const orc_ctx* c);
 
+/* Time averages, probes and scalar CDFs (Section 3, Table 1, Fig. 7): while
+ * averaging is on, every orc_step adds its element and node statistics to
+ * running sums and the psi of the particles in each CDF point's element to
+ * that point's histogram (nbins equal bins on [0, 1]). */
+int orc_set_averaging(orc_ctx* c, int32_t on, int32_t reset);
+int32_t orc_averaging_count(const orc_ctx* c);
+int orc_get_averages(const orc_ctx* c, int32_t which, double* out);
+int orc_probe(const orc_ctx* c, int32_t which, int32_t comp, const double* x, const double* y, int32_t n,
+              double* out, int32_t* elem_out);
+int orc_set_cdf_probes(orc_ctx* c, const double* x, const double* y, int32_t n, int32_t nbins);
+int orc_get_cdf(const orc_ctx* c, double* out, int32_t* elem_out);
+
 /* test hooks (pins) */
 void orc_philox4x32_10(const uint32_t key[2], const uint32_t ctr[4], uint32_t out[4]);
 void orc_gauss8(uint64_t seed, uint32_t case_id, uint32_t id, uint32_t step, double z[8]);
