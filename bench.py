@@ -52,6 +52,8 @@ def args_():
     ap.add_argument("--sur-epochs", type=int, default=10, help="training epochs of the surrogate")
     ap.add_argument("--pressure", action="store_true",
                     help="add the mean-pressure projection to the timed form (not the published configuration)")
+    ap.add_argument("--se-seeds", type=int, default=8,
+                    help="independent seeds per form in the standard-error study of the stated error")
     ap.add_argument("--surrogate-mode", type=int, default=1, choices=[1, 3],
                     help="1: network at the nodes; 3: network at every particle inside the particle kernel")
     return ap.parse_args()
@@ -807,6 +809,8 @@ def main():
                 "kernels_ms_per_step": {q: v[0] / k for q, v in rr["kt"].items()}}
             f.close()
         stated["precision_study"] = precision_study(cfg, mesh, dt, stream, sur, steps=200, lag_tol=a.lag_tol)
+        stated["standard_errors"] = standard_error_study(cfg, mesh, dt, stream, sur, lag_tol=a.lag_tol,
+                                                         seeds=a.se_seeds)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps_timed,
             "warmup": a.warmup, "ms_per_step": ms / steps_timed, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32" if prec != "fp64" else "f64",
@@ -870,6 +874,69 @@ def precision_study(cfg, mesh, dt, stream, sur, steps, lag_tol=0.05):
         f.close()
     return {"steps": steps, "cells": "12 x 8 grid, particle-weighted element means", "variants": out,
             "note": "fp64_fe_other_seed is the Monte Carlo scale: differences below it are within sampling noise"}
+
+
+def z_cells(A, B):
+    """Per cell and statistic, the difference of two seed ensembles' means in
+    standard errors, (mean_A - mean_B) / sqrt(s_A^2 / M_A + s_B^2 / M_B)
+    (a statistic identical in every run, e.g. psi = 0 far from the source,
+    gives 0); then the largest |z| and the fraction of |z| above 3."""
+    import numpy as np
+    out, flat, allz = {}, [], []
+    for q in A[0]:
+        a, b = np.array([x[q] for x in A]), np.array([x[q] for x in B])
+        d = a.mean(0) - b.mean(0)
+        se = np.sqrt(a.var(0, ddof=1) / len(A) + b.var(0, ddof=1) / len(B))
+        ok = se > 0
+        z = np.where(ok, d / np.where(ok, se, 1.0), 0.0)
+        # cells with no spread in either ensemble (every run of both sets
+        # gives the same value, e.g. psi = 0 where the scalar has not
+        # arrived): listed with their values, not turned into a z
+        for c in np.flatnonzero(~ok & (d != 0))[:4]:
+            flat.append({"stat": q, "cell": int(c), "value": float(a[0, c]), "reference": float(b[0, c])})
+        out[q] = float(np.abs(z).max())
+        allz.append(np.abs(z[ok]))
+    allz = np.concatenate(allz)
+    return {"max_abs_z": float(allz.max()), "frac_above_3": float(np.mean(allz > 3)), "tests": int(allz.size),
+            "max_abs_z_per_stat": out, "cells_without_spread_differing": flat}
+
+
+def standard_error_study(cfg, mesh, dt, stream, sur, lag_tol=0.05, seeds=8, checkpoints=(200, 500)):
+    """The stated error of each form in Monte Carlo standard errors: `seeds`
+    runs of the plain FP64 form (FE solve every step) and `seeds` runs of
+    each other form, with disjoint seeds, from their seeded starts; at each
+    checkpoint step the 12 x 8 cell statistics (<U>, <V>, <uu>, <vv>, <ww>,
+    <uv>, k, <psi>, psi variance) of the two ensembles are compared cell by
+    cell in standard errors of the difference of their means. Without a bias
+    |z| follows Student's t with 2 seeds - 2 degrees of freedom (about 1 % of
+    the tests above 3 for 8 seeds)."""
+    lag = {"mode": 5, "params": None, "norm": None, "tol": lag_tol}
+    forms = [("fp64_fe", "fp64", None, 1000), ("chosen_fp32_kahan_lagged_fe", "fp32_kahan", lag, 2000),
+             ("fp32_kahan_fe", "fp32_kahan", None, 3000)]
+    if sur is not None:
+        forms.append(("fp32_kahan_surrogate_node_form", "fp32_kahan", sur, 4000))
+    t0 = time.perf_counter()
+    cells = {}
+    for name, prec, s, base in forms:
+        runs = {c: [] for c in checkpoints}
+        for i in range(seeds):
+            f = Form(cfg, mesh, stream, precision=prec, sur=s, seed=base + i)
+            done = 0
+            for c in checkpoints:
+                f.g.step(dt, c - done)
+                done = c
+                f.g.sync()
+                runs[c].append(cell_stats(f.g, mesh))
+            f.close()
+        cells[name] = runs
+    out = {"seeds_per_form": seeds, "checkpoints": list(checkpoints), "reference": "fp64_fe",
+           "cells": "12 x 8 grid, particle-weighted element statistics", "wall_s": None}
+    for name in cells:
+        if name == "fp64_fe":
+            continue
+        out[name] = {str(c): z_cells(cells[name][c], cells["fp64_fe"][c]) for c in checkpoints}
+    out["wall_s"] = round(time.perf_counter() - t0, 1)
+    return out
 
 
 if __name__ == "__main__":

@@ -19,7 +19,9 @@ canyon centre) and the workload sizes of this project:
                     step, 256 particles per element (~10.3M), FP32 particle state
                     with FP64 statistics and CG, 500 steps. The chosen form
                     keeps the FP32 state, reduces in compensated FP32 and
-                    takes wp from the surrogate (FE solve as checked fallback).
+                    keeps the previous step's wp while its coarse FE residual
+                    under the current statistics stays below a tolerance
+                    (the FE solve runs when it does not).
 
 The time step follows a CFL rule that depends on the mesh and the initial
 condition only: dt = CFL * min_e(2 r_e) / U_ref, with r_e the inradius and

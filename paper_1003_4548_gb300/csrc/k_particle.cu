@@ -48,14 +48,45 @@ __device__ __forceinline__ void load_pack(const T* __restrict__ p, T (&o)[W]) {
 __device__ __forceinline__ void gauss_pair(double ua, double ub, double& za, double& zb) {
     box_muller(ua, ub, za, zb);
 }
+__device__ __forceinline__ float lg2_approx(float x) {
+    float y;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float rsqrt_approx(float x) {
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float sin_approx(float x) {
+    float y;
+    asm("sin.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float cos_approx(float x) {
+    float y;
+    asm("cos.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+// the radius sqrt(-2 ln ua) of the FP32 pair: ua in [2^-32, 1] is normal, so
+// the flush-to-zero hardware forms need no denormal handling; -2 ln ua =
+// -2 ln(2) log2(ua)
+__device__ __forceinline__ float bm_radius(float ua) {
+    const float m2l = -1.3862943611198906f * lg2_approx(ua);
+    return m2l > 0.f ? m2l * rsqrt_approx(m2l) : 0.f;
+}
 __device__ __forceinline__ void gauss_pair(float ua, float ub, float& za, float& zb) {
-    const float m2l = -2.0f * __logf(ua);  // absolute error < 4e-7 on (0, 1]: within the FP32 step tolerance
-    const float r = m2l > 0.f ? m2l * rsqrtf(m2l) : 0.f;
+    const float r = bm_radius(ua);
     const float th = 3.14159265358979f * fmaf(2.0f, ub, -1.0f);
-    float sn, cs;
-    __sincosf(th, &sn, &cs);
-    za = -r * cs;
-    zb = -r * sn;
+    za = -r * cos_approx(th);
+    zb = -r * sin_approx(th);
+}
+// one member of a pair (the step uses six of its eight Gaussians)
+__device__ __forceinline__ float gauss_cos(float ua, float ub) {
+    return -bm_radius(ua) * cos_approx(3.14159265358979f * fmaf(2.0f, ub, -1.0f));
+}
+__device__ __forceinline__ float gauss_sin(float ua, float ub) {
+    return -bm_radius(ua) * sin_approx(3.14159265358979f * fmaf(2.0f, ub, -1.0f));
 }
 
 template <typename T> __device__ __forceinline__ T t_div(T a, T b) { return a / b; }
@@ -67,6 +98,7 @@ struct StepArgs {
     T dt, sdt, s2nu, nu;
     const uint32_t* stepp;  // step counter on the device (advanced by the sort after each step)
     uint2 key;
+    PhiloxKeys rk;          // the key's ten round keys
     const int* __restrict__ tri;
     const int* __restrict__ nbr;
     const int* __restrict__ einfo;
@@ -85,7 +117,7 @@ struct StepArgs {
     int* cnt;
     int* status;
     int B, wall_model, mix_exp, reflect_max;
-    T C3, C4, C0, Cmu_half, kappa, E, yp, beta, fx, fy, x0, y0, r0, period, floor_k, floor_om;
+    T C3, C4, C0, Cmu_half, kappa, E, yp, beta, fx, fy, x0, y0, r0, period, inv_period, floor_k, floor_om;
     // per-particle surrogate (FP32 state only)
     const float* __restrict__ nsur;   // node pack: 10 standardised features, k, eps, uu, vv, ww, uv
     const float* __restrict__ surw;   // bf16-rounded parameters, then the standardisation
@@ -148,12 +180,23 @@ __device__ void reflect(const StepArgs<T>& a, int tag, T nx, T ny, const double*
     }
 }
 
-// one particle-step of particle i whose state at step n was staged in
-// shared memory; writes the state at step n+1 in place
+// a particle between its SDEs and its boundaries: position at step n (P),
+// the new position (Q), the new velocity, frequency and scalar (before the
+// source), its element at step n
+template <typename T>
+struct Mid {
+    int i, e0;
+    T x, y, qx, qy, u, v, w, om, psi;
+};
+
+// first half of the particle-step of particle i whose state at step n was
+// staged in shared memory: the mixing, frequency, velocity and position
+// updates; `stays` reports whether Q lies in the particle's element (then
+// the second half has no element walk to do)
 template <typename T, bool SUR = false>
-__device__ __forceinline__ void advance_particle(const StepArgs<T>& a, const uint32_t step, const int i, const T x,
-                                                 const T y, T u, T v, T w, T om, T psi, const uint32_t pid,
-                                                 const int e0, const int b, const float* ysur = nullptr) {
+__device__ __forceinline__ Mid<T> step_sde(const StepArgs<T>& a, const uint32_t step, const int i, const T x,
+                                           const T y, T u, T v, T w, T om, T psi, const uint32_t pid, const int e0,
+                                           const int b, bool& stays, const float* ysur = nullptr) {
 
     // P1 interpolation of the node pack at the particle: the element's affine
     // record, F = F0 + Fx dx + Fy dy with (dx, dy) from the element's
@@ -218,13 +261,26 @@ __device__ __forceinline__ void advance_particle(const StepArgs<T>& a, const uin
     const T Som = ep[6], tm = ep[7];
     const T cm = a.ecm[a.B * e0 + b];
 
-    // eight Gaussians: counter (id, step, call, 0)
+    // eight Gaussians: counter (id, step, call, 0); the step uses z[0], z[1]
+    // (dW_1,2), z[3..5] (dW'), z[6] (dW for omega): z[2] (dW_3, paired with
+    // the zero spanwise gradient) and z[7] are left out in FP32
     T z[8];
-#pragma unroll
-    for (uint32_t call = 0; call < 2; ++call) {
-        const uint4 r = philox4x32_10(a.key, make_uint4(pid, step, call, 0u));
-        gauss_pair(unif<T>(r.x), unif<T>(r.y), z[4 * call + 0], z[4 * call + 1]);
-        gauss_pair(unif<T>(r.z), unif<T>(r.w), z[4 * call + 2], z[4 * call + 3]);
+    {
+        const uint4 r0 = philox4x32_10_rk(a.rk, make_uint4(pid, step, 0u, 0u));
+        const uint4 r1 = philox4x32_10_rk(a.rk, make_uint4(pid, step, 1u, 0u));
+        if constexpr (sizeof(T) == 4) {
+            gauss_pair(unif<T>(r0.x), unif<T>(r0.y), z[0], z[1]);
+            z[2] = (T)0;
+            z[3] = gauss_sin(unif<T>(r0.z), unif<T>(r0.w));
+            gauss_pair(unif<T>(r1.x), unif<T>(r1.y), z[4], z[5]);
+            z[6] = gauss_cos(unif<T>(r1.z), unif<T>(r1.w));
+            z[7] = (T)0;
+        } else {
+            gauss_pair(unif<T>(r0.x), unif<T>(r0.y), z[0], z[1]);
+            gauss_pair(unif<T>(r0.z), unif<T>(r0.w), z[2], z[3]);
+            gauss_pair(unif<T>(r1.x), unif<T>(r1.y), z[4], z[5]);
+            gauss_pair(unif<T>(r1.z), unif<T>(r1.w), z[6], z[7]);
+        }
     }
     const T dt = a.dt, sdt = a.sdt;
 
@@ -249,10 +305,35 @@ __device__ __forceinline__ void advance_particle(const StepArgs<T>& a, const uin
     T qx = x + u * dt + a.s2nu * z[0] * sdt;
     T qy = y + v * dt + a.s2nu * z[1] * sdt;
 
-    // boundaries and the element walk along the straight path P -> Q
+    // Most particles end the step in their own element: the walk's first
+    // test (Q inside e0, the same arithmetic) decides that without the walk.
+    {
+        T ge[EGEO_W];
+        load_pack<EGEO_W>(a.egeo + EGEO_W * e0, ge);
+        const T qdx = qx - ge[0], qdy = qy - ge[1];
+        const T lq0 = ge[2] * qdx + ge[3] * qdy + ge[4];
+        const T lq1 = ge[5] * qdx + ge[6] * qdy + ge[7];
+        const T lq2 = ge[8] * qdx + ge[9] * qdy + ge[10];
+        stays = lq0 >= (T)0 && lq1 >= (T)0 && lq2 >= (T)0;
+    }
+    Mid<T> m;
+    m.i = i; m.e0 = e0; m.x = x; m.y = y; m.qx = qx; m.qy = qy;
+    m.u = u1; m.v = v1; m.w = w1; m.om = om1; m.psi = psi1;
+    return m;
+}
+
+// second half: boundaries and the element walk along the straight path
+// P -> Q (skipped when Q stays in e0), the source, the checks, the stores and
+// the element histogram of the sort
+template <typename T>
+__device__ __forceinline__ void finish_particle(const StepArgs<T>& a, const Mid<T>& m, const bool stays) {
+    const int i = m.i, e0 = m.e0;
+    const T x = m.x, y = m.y;
+    T qx = m.qx, qy = m.qy, u1 = m.u, v1 = m.v, w1 = m.w, om1 = m.om;
+    const T psi1 = m.psi;
     T px = x, py = y;
     int e = e0, entry = -1, nref = 0, it = 0;
-    for (; it < WALK_MAX; ++it) {
+    for (; !stays && it < WALK_MAX; ++it) {
         T ge[EGEO_W];
         load_pack<EGEO_W>(a.egeo + EGEO_W * e, ge);
         const T qdx = qx - ge[0], qdy = qy - ge[1];
@@ -300,22 +381,35 @@ __device__ __forceinline__ void advance_particle(const StepArgs<T>& a, const uin
             const T sd = lqk * inv;  // signed distance of Q from the edge line (< 0)
             qx -= (T)2 * sd * nx;
             qy -= (T)2 * sd * ny;
-            // wall statistics at the hit point, linear along the edge
-            const int ka = (kx + 1) % 3, kb = (kx + 2) % 3;
-            const T cdx = cx - ge[0], cdy = cy - ge[1];
-            const T la = ge[2 + 3 * ka] * cdx + ge[3 + 3 * ka] * cdy + ge[4 + 3 * ka];
-            const T lb = ge[2 + 3 * kb] * cdx + ge[3 + 3 * kb] * cdy + ge[4 + 3 * kb];
-            const double mu = (double)(lb / (la + lb));
-            const int na = a.tri[3 * e + ka], nb = a.tri[3 * e + kb];
-            double st[7];
-            st[0] = (1 - mu) * a.nmean[4 * na + 0] + mu * a.nmean[4 * nb + 0];
-            st[1] = (1 - mu) * a.nmean[4 * na + 1] + mu * a.nmean[4 * nb + 1];
-            st[2] = (1 - mu) * a.nR[6 * na + 0] + mu * a.nR[6 * nb + 0];
-            st[3] = (1 - mu) * a.nR[6 * na + 1] + mu * a.nR[6 * nb + 1];
-            st[4] = (1 - mu) * a.nR[6 * na + 2] + mu * a.nR[6 * nb + 2];
-            st[5] = (1 - mu) * a.nR[6 * na + 3] + mu * a.nR[6 * nb + 3];
-            st[6] = (1 - mu) * a.nmean[4 * na + 3] + mu * a.nmean[4 * nb + 3];
-            reflect<T>(a, tag, nx, ny, st, na, nb, mu, u1, v1, w1, om1);
+            if (tag == 2 || a.wall_model == PDF_ELLIPTIC_RELAXATION) {
+                // symmetry top, or the no-slip wall of the resolved case: no
+                // wall statistics needed
+                if (tag == 2) {  // the normal component reversed, as reflect<T> does
+                    const T tx = ny, ty = -nx;
+                    const T Ut = u1 * tx + v1 * ty, Vn = u1 * nx + v1 * ny;
+                    u1 = Ut * tx - Vn * nx;
+                    v1 = Ut * ty - Vn * ny;
+                } else {
+                    u1 = -u1; v1 = -v1; w1 = -w1;
+                }
+            } else {
+                // wall functions: the statistics at the hit point, linear along the edge
+                const int ka = (kx + 1) % 3, kb = (kx + 2) % 3;
+                const T cdx = cx - ge[0], cdy = cy - ge[1];
+                const T la = ge[2 + 3 * ka] * cdx + ge[3 + 3 * ka] * cdy + ge[4 + 3 * ka];
+                const T lb = ge[2 + 3 * kb] * cdx + ge[3 + 3 * kb] * cdy + ge[4 + 3 * kb];
+                const double mu = (double)(lb / (la + lb));
+                const int na = a.tri[3 * e + ka], nb = a.tri[3 * e + kb];
+                double st[7];
+                st[0] = (1 - mu) * a.nmean[4 * na + 0] + mu * a.nmean[4 * nb + 0];
+                st[1] = (1 - mu) * a.nmean[4 * na + 1] + mu * a.nmean[4 * nb + 1];
+                st[2] = (1 - mu) * a.nR[6 * na + 0] + mu * a.nR[6 * nb + 0];
+                st[3] = (1 - mu) * a.nR[6 * na + 1] + mu * a.nR[6 * nb + 1];
+                st[4] = (1 - mu) * a.nR[6 * na + 2] + mu * a.nR[6 * nb + 2];
+                st[5] = (1 - mu) * a.nR[6 * na + 3] + mu * a.nR[6 * nb + 3];
+                st[6] = (1 - mu) * a.nmean[4 * na + 3] + mu * a.nmean[4 * nb + 3];
+                reflect<T>(a, tag, nx, ny, st, na, nb, mu, u1, v1, w1, om1);
+            }
             px = cx; py = cy;
             entry = kx;
         }
@@ -324,11 +418,13 @@ __device__ __forceinline__ void advance_particle(const StepArgs<T>& a, const uin
         set_status(a.status, ST_LOST);
         e = e0; qx = x; qy = y;
     }
-    // continuous source (minimum-image distance in x)
+    // continuous source (minimum-image distance in x; the image choice can
+    // differ from an exact division only half a period from the source,
+    // far outside the disc)
     T psi2 = psi1;
     {
         T ddx = qx - a.x0;
-        ddx -= a.period * t_floor<T>(ddx / a.period + (T)0.5);
+        ddx -= a.period * t_floor<T>(ddx * a.inv_period + (T)0.5);
         const T ddy = qy - a.y0;
         if (ddx * ddx + ddy * ddy < a.r0 * a.r0) psi2 = (T)1;
     }
@@ -340,6 +436,16 @@ __device__ __forceinline__ void advance_particle(const StepArgs<T>& a, const uin
     // element histogram for the sort (warp-aggregated)
     const unsigned mask = __match_any_sync(__activemask(), e);
     if ((threadIdx.x & 31) == __ffs(mask) - 1) atomicAdd(&a.cnt[e], __popc(mask));
+}
+
+// both halves of a particle-step
+template <typename T, bool SUR = false>
+__device__ __forceinline__ void advance_particle(const StepArgs<T>& a, const uint32_t step, const int i, const T x,
+                                                 const T y, T u, T v, T w, T om, T psi, const uint32_t pid,
+                                                 const int e0, const int b, const float* ysur = nullptr) {
+    bool stays;
+    const Mid<T> m = step_sde<T, SUR>(a, step, i, x, y, u, v, w, om, psi, pid, e0, b, stays, ysur);
+    finish_particle(a, m, stays);
 }
 
 // ---------------------------------------------------------------------------
@@ -426,11 +532,23 @@ __device__ __forceinline__ void stage_tile(const StepArgs<T>& a, Stage<T>& st, u
 // staging takes L1 from the node and element gathers)
 template <typename T> constexpr int NSTAGE = 2;
 
+// Movers (particles whose new position leaves their element, a few per
+// cent) would make a whole warp walk with them: in the FP32 kernel each warp
+// queues its movers in shared memory and walks them 32 at a time, so the
+// walk's cost follows the number of movers, not of warps holding one.
+constexpr int QCAP = 64;  // queue entries per warp (fewer than 32 left plus at most 32 new)
+
 template <typename T>
 __global__ void __launch_bounds__(TILE) k_step(const StepArgs<T> a) {
     constexpr int NS = NSTAGE<T>, PD = NS - 1, NW = TILE / 32;  // PD: tiles staged ahead
+    constexpr bool DEFER = sizeof(T) == 4;
     __shared__ __align__(128) Stage<T> st[NS];
     __shared__ __align__(8) uint64_t full[NS], empty[NS];
+    __shared__ Mid<T> mq[DEFER ? NW : 1][DEFER ? QCAP : 1];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const unsigned ltmask = (1u << lane) - 1u;
+    int qhead = 0, qn = 0;  // the warp's queue (warp-uniform)
+    (void)wid; (void)ltmask; (void)qhead; (void)qn;
     const int64_t ntiles = (a.n + TILE - 1) / TILE;
     if (threadIdx.x == 0) {
 #pragma unroll
@@ -464,14 +582,44 @@ __global__ void __launch_bounds__(TILE) k_step(const StepArgs<T> a) {
         }
         mbar_wait(&full[s], (unsigned)((k / NS) & 1), a.status);
         const int64_t i = t * TILE + threadIdx.x;
-        if (i < a.n) {
-            const Stage<T>& q = st[s];
-            const int j = threadIdx.x;
-            advance_particle(a, step, (int)i, q.s[0][j], q.s[1][j], q.s[2][j], q.s[3][j], q.s[4][j], q.s[5][j], q.s[6][j],
-                             q.id[j], q.elem[j], (int)q.bin[j]);
+        if constexpr (DEFER) {
+            bool mover = false;
+            Mid<T> m;
+            if (i < a.n) {
+                const Stage<T>& q = st[s];
+                const int j = threadIdx.x;
+                bool stays;
+                m = step_sde<T>(a, step, (int)i, q.s[0][j], q.s[1][j], q.s[2][j], q.s[3][j], q.s[4][j], q.s[5][j],
+                                q.s[6][j], q.id[j], q.elem[j], (int)q.bin[j], stays);
+                if (stays) finish_particle(a, m, true);
+                else mover = true;
+            }
+            // the warp's movers join its queue; the stage is free again
+            const unsigned mv = __ballot_sync(0xffffffffu, mover);
+            if (mover) mq[wid][(qhead + qn + __popc(mv & ltmask)) & (QCAP - 1)] = m;
+            qn += __popc(mv);
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty[s]);
+            if (qn >= 32) {  // a full warp of movers: their walks side by side
+                const Mid<T> w = mq[wid][(qhead + lane) & (QCAP - 1)];
+                __syncwarp();
+                finish_particle(a, w, false);
+                qhead = (qhead + 32) & (QCAP - 1);
+                qn -= 32;
+            }
+        } else {
+            if (i < a.n) {
+                const Stage<T>& q = st[s];
+                const int j = threadIdx.x;
+                advance_particle(a, step, (int)i, q.s[0][j], q.s[1][j], q.s[2][j], q.s[3][j], q.s[4][j], q.s[5][j],
+                                 q.s[6][j], q.id[j], q.elem[j], (int)q.bin[j]);
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty[s]);  // this warp is done with stage s
         }
-        __syncwarp();
-        if ((threadIdx.x & 31) == 0) mbar_arrive(&empty[s]);  // this warp is done with stage s
+    }
+    if constexpr (DEFER) {
+        if (lane < qn) finish_particle(a, mq[wid][(qhead + lane) & (QCAP - 1)], false);  // the last movers
     }
 }
 
@@ -524,6 +672,7 @@ StepArgs<T> step_args(pdf_ctx* c, double dt) {
     a.nu = (T)p.nu;
     a.stepp = c->d_step;
     a.key = philox_key(p.seed, p.case_id);
+    a.rk = philox_round_keys(a.key);
     a.tri = c->m.tri;
     a.nbr = c->m.nbr;
     a.einfo = c->m.einfo;
@@ -551,7 +700,7 @@ StepArgs<T> step_args(pdf_ctx* c, double dt) {
     a.kappa = (T)p.kappa; a.E = (T)p.E; a.yp = (T)p.yp;
     a.beta = (T)(-2.0 / (0.5 + 0.75 * p.C0 + p.C3 + p.Comega2 - p.Comega1));
     a.fx = (T)p.fx; a.fy = (T)p.fy;
-    a.x0 = (T)p.x0; a.y0 = (T)p.y0; a.r0 = (T)p.r0; a.period = (T)p.period;
+    a.x0 = (T)p.x0; a.y0 = (T)p.y0; a.r0 = (T)p.r0; a.period = (T)p.period; a.inv_period = (T)(1.0 / p.period);
     a.floor_k = (T)p.floor_k; a.floor_om = (T)p.floor_omega;
     a.nsur = nullptr; a.surw = nullptr; a.sur_ok = nullptr; a.pwp = nullptr;
     return a;

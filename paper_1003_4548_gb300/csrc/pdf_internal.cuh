@@ -247,13 +247,45 @@ __host__ __device__ inline uint2 philox_key(uint64_t seed, uint32_t case_id) {
     return make_uint2((uint32_t)seed, (uint32_t)(seed >> 32) ^ case_id);
 }
 
+// The ten round keys of Philox4x32-10 for one key (the Weyl schedule), made
+// once on the host: the key is the same for every particle of a step, so a
+// kernel that takes them as a parameter reads them from the constant bank
+// instead of advancing the schedule per call.
+struct PhiloxKeys {
+    uint32_t k[20];  // round r: k[2 r], k[2 r + 1]
+};
+
+inline PhiloxKeys philox_round_keys(uint2 key) {
+    PhiloxKeys rk;
+    for (int r = 0; r < 10; ++r) {
+        rk.k[2 * r] = key.x;
+        rk.k[2 * r + 1] = key.y;
+        key.x += 0x9E3779B9u;
+        key.y += 0xBB67AE85u;
+    }
+    return rk;
+}
+
+// Philox4x32-10 from precomputed round keys; each round's two 32 x 32-bit
+// products as 64-bit wide multiplies. Bit for bit philox4x32_10.
+__device__ __forceinline__ uint4 philox4x32_10_rk(const PhiloxKeys& rk, uint4 c) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint64_t p0 = (uint64_t)0xD2511F53u * c.x;
+        const uint64_t p1 = (uint64_t)0xCD9E8D57u * c.z;
+        c = make_uint4((uint32_t)(p1 >> 32) ^ c.y ^ rk.k[2 * r], (uint32_t)p1,
+                       (uint32_t)(p0 >> 32) ^ c.w ^ rk.k[2 * r + 1], (uint32_t)p0);
+    }
+    return c;
+}
+
 // uniform in (0, 1]: (w + 1) 2^-32, exact in double, rounded in float
 template <typename T> __device__ __forceinline__ T unif(uint32_t w);
 template <> __device__ __forceinline__ double unif<double>(uint32_t w) {
     return ((double)w + 1.0) * 2.3283064365386963e-10;
 }
 template <> __device__ __forceinline__ float unif<float>(uint32_t w) {
-    return ((float)w + 1.0f) * 2.3283064365386963e-10f;
+    return fmaf((float)w, 2.3283064365386963e-10f, 2.3283064365386963e-10f);
 }
 
 // Box & Muller (1958)
