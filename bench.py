@@ -142,7 +142,8 @@ def gpu_index(local_rank: int) -> int:
 
 KERNEL_SOURCES = {
     "k_step": ("k_particle.cu", "pdf_internal.cuh"),
-    "k_moments_med": ("k_stats.cu", "exact_sum.cuh", "pdf_internal.cuh"),
+    "k_moments_w": ("k_stats.cu", "exact_sum.cuh", "pdf_internal.cuh"),
+    "k_bins_med": ("k_stats.cu", "exact_sum.cuh", "pdf_internal.cuh"),
     "k_scatter": ("k_sort.cu", "pdf_internal.cuh"),
 }
 
@@ -256,14 +257,16 @@ def config_block(cfg, mesh, n, precision, form):
 def algorithmic_bytes(kclass: str, ts: int):
     if kclass == "particle":  # k_step: read 7 state + id + elem + bin, write 7 state + elem
         return 14 * ts + 13, "k_step (per-particle step)"
-    if kclass == "moments":   # k_moments_med: read u v w psi omega, write the bin (ids only where values tie)
-        return 5 * ts + 1, "k_moments_med (element moments and velocity bins)"
+    if kclass == "moments":   # k_moments_w: read u v w psi omega (12 values per element written)
+        return 5 * ts, "k_moments_w (element moments)"
+    if kclass == "bins":      # k_bins_med: read u v w psi, write the bin (ids only where values tie)
+        return 4 * ts + 1, "k_bins_med (velocity bins and <phi|V>, beside the field chain)"
     if kclass == "sort":      # k_scatter: read and write 7 state + id + elem
         return 2 * (7 * ts + 8), "k_scatter (element re-sort)"
     return None, None
 
 
-KTRAFFIC = {"particle": "k_step", "moments": "k_moments_med", "sort": "k_scatter"}
+KTRAFFIC = {"particle": "k_step", "moments": "k_moments_w", "bins": "k_bins_med", "sort": "k_scatter"}
 
 
 def roofline(kclass, kt, n, ts, workload, precision):
@@ -593,7 +596,8 @@ def run_batch(a, cfg, emit=True):
             "streams_without_graph": {"value": no_graph, "steps": k},
             "autotuned": {"step_blocks_per_sm": sorted({t["step_blocks_per_sm"] for t in tunings}),
                           "scatter_threads": sorted({t["scatter_threads"] for t in tunings}),
-                          "cg_rows_per_block": sorted({t["cg_rows_per_block"] for t in tunings})},
+                          "cg_rows_per_block": sorted({t["cg_rows_per_block"] for t in tunings}),
+                          "bins_blocks_per_sm": sorted({t["bins_blocks_per_sm"] for t in tunings})},
             "wp": dict(sur_info, checked_steps=solves, fe_solves=falls,
                        residual_tol_per_case_min_max=[min(tols), max(tols)],
                        check_calibration=("per case: 1.5 x the largest coarse residual over its first 6 steps "
@@ -731,7 +735,8 @@ def main():
     ts = 8 if prec == "fp64" else 4
     dominant = max((k for k in kt if kt[k][1]), key=lambda k: kt[k][0])
     roof = roofline(dominant, kt, n, ts, a.workload, prec)
-    rooflines = {k: roofline(k, kt, n, ts, a.workload, prec) for k in ("particle", "moments", "sort")}
+    rooflines = {k: roofline(k, kt, n, ts, a.workload, prec) for k in ("particle", "moments", "bins", "sort")
+                 if k in kt and kt[k][1]}
     kernels = {k: {"ms_per_step": v[0] / a.steps, "launches": v[1]} for k, v in kt.items()}
     stated = {}
     if chosen_wp is not None:

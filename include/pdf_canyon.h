@@ -136,15 +136,19 @@ enum pdf_field {
     PDF_FIELD_NODE_P = 27     /* double[nnode] projection pressure p of the last step (pressure = 1) */
 };
 
-/* Kernel classes timed by pdf_kernel_time (CUDA events on the context stream). */
+/* Kernel classes timed by pdf_kernel_time (CUDA events on the context stream;
+ * PDF_K_BINS on the bins stream, where it overlaps PDF_K_FIELDS and
+ * PDF_K_ELLIPTIC, so the classes' times may add up to more than a step). */
 enum pdf_kernel {
     PDF_K_PARTICLE = 0,  /* per-particle step: Eqs. IECM, frequency-model, velocity, position, walls, walk */
     PDF_K_SORT = 1,      /* element histogram scan + scatter of the particle state */
-    PDF_K_MOMENTS = 2,   /* element moments and <phi|V> bins */
+    PDF_K_MOMENTS = 2,   /* element moments (and the <phi|V> bins where no bins stream runs) */
     PDF_K_FIELDS = 3,    /* node averages, gradients, t_m, S_omega, G_ij packs */
     PDF_K_ELLIPTIC = 4,  /* FE assembly + Jacobi-PCG of Eq. elliptic-relaxation */
     PDF_K_PRESSURE = 5,  /* mean-pressure projection: right-hand side, PCG, velocity correction */
-    PDF_K_COUNT = 6
+    PDF_K_BINS = 6,      /* FP32 state, 2x2x2 bins: velocity bins and <phi|V> of the elements of at
+                            most 512 particles, on a third stream beside the field chain */
+    PDF_K_COUNT = 7
 };
 
 /* Defaults: Table 2, C0 = 3.5 and C_mu, kappa, E of Section 2.2, nu = 1/12000,
@@ -183,7 +187,11 @@ int pdf_set_particles(pdf_ctx* c, int32_t n, const double* x, const double* y, c
 
 /* Estimate S^n from the particles: element moments and <phi|V> bins, node
  * averages, gradients, t_m, S_omega, and G_ij (Eq. wall-GandC, or Eqs. Gij/C0
- * from the finite-element solve of Eq. elliptic-relaxation). */
+ * from the finite-element solve of Eq. elliptic-relaxation). With FP32 state
+ * and 2x2x2 bins the bins run on a stream of the context, forked from the
+ * context stream after the moments and joined back into it before the call
+ * returns (pdf_step likewise per step), so all work stays ordered on the
+ * context stream. */
 int pdf_estimate_stats(pdf_ctx* c);
 
 /* Advance nsteps forward Euler-Maruyama steps of size dt: per step the
@@ -334,14 +342,19 @@ typedef struct pdf_tuning {
     int32_t step_blocks_per_sm;  /* persistent grid of the particle kernel */
     int32_t scatter_threads;     /* block size of the re-sort scatter */
     int32_t cg_rows_per_block;   /* elliptic CG block (block-Jacobi) size, 0 without elliptic relaxation */
+    int32_t bins_blocks_per_sm;  /* grid of the bins kernel beside the field chain (FP32 state, 2x2x2 bins;
+                                    0: one block per four elements); -1 where it does not run */
     double ms_particle, ms_sort, ms_elliptic;  /* best per-step times (CUDA events) */
+    double ms_step_bins[5];      /* step time with 3, 4, 5, 6 bins blocks per SM and with one block per
+                                    four elements (0 where not timed) */
 } pdf_tuning;
 
 /* Autotuner: times the candidate launch shapes of the particle kernel
- * (1 .. resident blocks per SM), of the scatter (128, 256, 512 threads) and
- * of the CG block (128, 160, 192 rows, those whose grid is co-resident) by
- * running steps_per_trial steps of dt for each candidate, one parameter at a
- * time, and keeps the fastest. The context advances by every step it times
+ * (1 .. resident blocks per SM), of the scatter (128, 256, 512 threads), of
+ * the CG block (128, 160, 192 rows, those whose grid is co-resident) and of
+ * the bins kernel (by the whole step's time, since it overlaps the field
+ * chain) by running steps_per_trial steps of dt for each candidate, one
+ * parameter at a time, and keeps the fastest. The context advances by every step it times
  * (use it as warm-up). Results of a step do not depend on the particle-kernel
  * grid or on the scatter block size for the FP64 and exact-FP32 reductions
  * (the compensated-FP32 sums depend on the order of the particles inside an

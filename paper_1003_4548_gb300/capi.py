@@ -35,7 +35,7 @@ FIELD = dict(x=0, y=1, u=2, v=3, w=4, om=5, psi=6, id=7, elem=8, bin=9, elem_n=1
              elem_psivar=13, elem_cm=14, node_mean=15, node_R=16, node_ke=17, elem_der=18, node_pack=19,
              node_wp=20, node_wdist=21, node_grad=22, node_psivar=23, particle_wp=24,
              elem_omw=25, node_omw=26, node_p=27)
-KERNEL = dict(particle=0, sort=1, moments=2, fields=3, elliptic=4, pressure=5)
+KERNEL = dict(particle=0, sort=1, moments=2, fields=3, elliptic=4, pressure=5, bins=6)
 
 _DOUBLES = ("C1", "C2", "C3", "C4", "CT", "CL", "Ceta", "Cv", "gamma5", "Comega1", "Comega2", "Cs", "Ct",
             "C0", "Cmu", "kappa", "E", "nu", "fx", "fy", "yp", "wall_offset", "x0", "y0", "r0", "period",
@@ -70,7 +70,8 @@ SORT_STATIC_MAX_ELEMENTS = 131072  # PDF_SORT_STATIC_MAX_ELEMENTS
 
 class pdf_tuning(C.Structure):
     _fields_ = [("step_blocks_per_sm", C.c_int32), ("scatter_threads", C.c_int32), ("cg_rows_per_block", C.c_int32),
-                ("ms_particle", C.c_double), ("ms_sort", C.c_double), ("ms_elliptic", C.c_double)]
+                ("bins_blocks_per_sm", C.c_int32), ("ms_particle", C.c_double), ("ms_sort", C.c_double),
+                ("ms_elliptic", C.c_double), ("ms_step_bins", C.c_double * 5)]
 
 
 def library_path() -> str:
@@ -362,7 +363,9 @@ class Canyon:
     def autotune(self, dt: float, steps_per_trial: int = 3) -> dict:
         t = pdf_tuning()
         self._check(lib().pdf_autotune(self._h, dt, steps_per_trial, C.byref(t)))
-        return {n: getattr(t, n) for n, _ in pdf_tuning._fields_}
+        out = {n: getattr(t, n) for n, _ in pdf_tuning._fields_}
+        out["ms_step_bins"] = list(out["ms_step_bins"])
+        return out
 
     # -- time averaging, probes, scalar CDFs --------------------------------
     def set_averaging(self, on: bool, reset: bool = False):

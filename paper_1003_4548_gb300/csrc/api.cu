@@ -20,7 +20,7 @@ int fail(pdf_ctx* c, int code, const std::string& msg) {
     return code;
 }
 
-void timing_begin(pdf_ctx* c, int k) {
+void timing_begin(pdf_ctx* c, int k, cudaStream_t st) {
     if (!c->timing) return;
     std::pair<cudaEvent_t, cudaEvent_t> ev;
     if (!c->tm.pool.empty()) {
@@ -30,13 +30,13 @@ void timing_begin(pdf_ctx* c, int k) {
         cudaEventCreate(&ev.first);
         cudaEventCreate(&ev.second);
     }
-    cudaEventRecord(ev.first, c->s);
+    cudaEventRecord(ev.first, st ? st : c->s);
     c->tm.ev[k].push_back(ev);
 }
 
-void timing_end(pdf_ctx* c, int k) {
+void timing_end(pdf_ctx* c, int k, cudaStream_t st) {
     if (!c->timing || c->tm.ev[k].empty()) return;
-    cudaEventRecord(c->tm.ev[k].back().second, c->s);
+    cudaEventRecord(c->tm.ev[k].back().second, st ? st : c->s);
 }
 
 static void timing_collect(pdf_ctx* c) {
@@ -598,6 +598,7 @@ int pdf_estimate_stats(pdf_ctx* c) {
     if (!c->seeded) return fail(c, PDF_ERR_STATE, "no particles");
     TRY(launch_moments(c));
     TRY(launch_fields(c));
+    TRY(join_bins(c));
     c->stats_valid = true;
     return PDF_OK;
 }
@@ -611,8 +612,12 @@ int pdf_step(pdf_ctx* c, double dt, int32_t nsteps) {
         TRY(launch_sort(c, true));
         c->step++;
         TRY(launch_moments(c));
-        if (c->p.pressure) TRY(launch_pressure(c, dt));
+        if (c->p.pressure) {  // the projection moves the velocities the bins read
+            TRY(join_bins(c));
+            TRY(launch_pressure(c, dt));
+        }
         TRY(launch_fields(c));
+        TRY(join_bins(c));
         TRY(launch_averaging(c));
     }
     return PDF_OK;
@@ -626,6 +631,7 @@ int pdf_set_wait_limit(pdf_ctx* c, int64_t spins) {
 
 int pdf_sync(pdf_ctx* c) {
     if (!c) return PDF_ERR_ARG;
+    TRY(join_bins(c));  // (left pending only by a launch that failed)
     PDF_CUDA(c, cudaStreamSynchronize(c->s));
     PDF_CUDA(c, cudaMemcpy(c->h_status, c->d_status, sizeof(int), cudaMemcpyDeviceToHost));
     const int s = *c->h_status;
@@ -799,6 +805,9 @@ void pdf_destroy(pdf_ctx* c) {
     if (c->side_join) cudaEventDestroy(c->side_join);
     if (c->side_join2) cudaEventDestroy(c->side_join2);
     if (c->s2) cudaStreamDestroy(c->s2);
+    if (c->bins_join) cudaEventDestroy(c->bins_join);
+    if (c->s3) cudaStreamDestroy(c->s3);
+    if (c->s_cond) cudaStreamDestroy(c->s_cond);
     delete c;
 }
 

@@ -274,6 +274,36 @@ int pdf_autotune(pdf_ctx* c, double dt, int32_t steps_per_trial, pdf_tuning* out
         t.cg_rows_per_block = c->fe_bs;
         t.ms_elliptic = best_ms;
     }
+    // bins grid (FP32 state, 2x2x2 bins): it runs beside the field chain, so
+    // the whole step's time decides
+    t.bins_blocks_per_sm = -1;
+    if (st == PDF_OK && c->prec != 0 && c->p.nb1 == 2 && c->p.nb2 == 2 && c->p.nb3 == 2) {
+        const int cand[5] = {3, 4, 5, 6, 0};
+        int best = c->bins_bps;
+        double best_ms = 1e300;
+        cudaEvent_t ev[2] = {nullptr, nullptr};
+        cudaError_t ce = cudaEventCreate(&ev[0]);
+        if (ce == cudaSuccess) ce = cudaEventCreate(&ev[1]);
+        if (ce != cudaSuccess) st = fail(c, PDF_ERR_CUDA, std::string("cudaEventCreate: ") + cudaGetErrorString(ce));
+        for (int k = 0; k < 5 && st == PDF_OK; ++k) {
+            c->bins_bps = cand[k];
+            st = pdf_step(c, dt, 1);  // warm-up with the new grid
+            if (st == PDF_OK) st = cudaEventRecord(ev[0], c->s) == cudaSuccess ? PDF_OK : PDF_ERR_CUDA;
+            if (st == PDF_OK) st = pdf_step(c, dt, steps_per_trial);
+            if (st == PDF_OK) st = cudaEventRecord(ev[1], c->s) == cudaSuccess ? PDF_OK : PDF_ERR_CUDA;
+            if (st == PDF_OK) st = pdf_sync(c);
+            float ms = 0.f;
+            if (st == PDF_OK && cudaEventElapsedTime(&ms, ev[0], ev[1]) != cudaSuccess) st = PDF_ERR_CUDA;
+            if (st == PDF_OK) {
+                t.ms_step_bins[k] = ms / steps_per_trial;
+                if (t.ms_step_bins[k] < best_ms) { best_ms = t.ms_step_bins[k]; best = cand[k]; }
+            }
+        }
+        c->bins_bps = best;
+        t.bins_blocks_per_sm = best;
+        for (cudaEvent_t e : ev)
+            if (e) cudaEventDestroy(e);
+    }
     c->timing = timing;
     if (st == PDF_OK && out) *out = t;
     return st;

@@ -576,6 +576,26 @@ cudaError_t launch_pcg(const CGArgs& a, int blocks, cudaStream_t s, bool ffv) {
 
 }  // namespace
 
+// Lagged or surrogate wp inside a captured graph: the residual check decides
+// on the device whether the FE solve runs. This gate takes the proposal as
+// the solution where the check passed and sets the graph condition of the
+// node that holds the cooperative CG, so a step that keeps its wp launches no
+// cooperative grid (whose launch waits until the whole grid fits beside the
+// kernels already running, e.g. the bins kernel beside the field chain).
+__global__ void k_cg_gate(cudaGraphConditionalHandle h, const int* skip, const double* xprop, const int* rep,
+                          double* x, int* iters, int nn) {
+    const bool keep = *(volatile const int*)skip != 0;
+    const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (keep && t < (size_t)nn * NC) {
+        const int i = (int)(t / NC);
+        if (rep[i] == i) x[t] = xprop[t];
+    }
+    if (t == 0) {
+        if (keep) *iters = 0;
+        cudaGraphSetConditional(h, keep ? 0u : 1u);
+    }
+}
+
 // grid of the cooperative CG for rows-per-block bs (0: the largest size whose
 // grid is co-resident: fewer blocks and partial sums, a stronger block-Jacobi
 // preconditioner)
@@ -659,9 +679,46 @@ int launch_elliptic(pdf_ctx* c) {
     // cooperative grids of different contexts never run side by side (a
     // batch orders them in a chain)
     if (c->coop_wait) PDF_CUDA(c, cudaStreamWaitEvent(c->s, c->coop_wait, 0));
-    if (c->fe_bs == 128) err = launch_pcg<128>(a, c->fe_blocks, c->s, ffv);
-    else if (c->fe_bs == 160) err = launch_pcg<160>(a, c->fe_blocks, c->s, ffv);
-    else err = launch_pcg<192>(a, c->fe_blocks, c->s, ffv);
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaGraph_t graph = nullptr;
+    if (c->sur_mode) PDF_CUDA(c, cudaStreamGetCaptureInfo(c->s, &cs, nullptr, &graph, nullptr, nullptr, nullptr));
+    cudaStream_t cg_stream = c->s;
+    if (c->sur_mode && cs == cudaStreamCaptureStatusActive) {
+        // captured: the CG goes into the body of a conditional node that the
+        // gate kernel opens only when the check rejected the proposal (the
+        // condition defaults to 1: without the gate the CG runs and makes
+        // the same decision itself)
+        cudaGraphConditionalHandle h;
+        PDF_CUDA(c, cudaGraphConditionalHandleCreate(&h, graph, 1, cudaGraphCondAssignDefault));
+        const size_t tot = (size_t)nn * NC;
+        k_cg_gate<<<(unsigned)((tot + 255) / 256), 256, 0, c->s>>>(h, c->sur_skip, c->fe_prop, c->m.rep, c->nwp,
+                                                                    c->fe_iters, nn);
+        ++c->launches;
+        PDF_CUDA(c, cudaGetLastError());
+        const cudaGraphNode_t* deps = nullptr;
+        size_t nd = 0;
+        PDF_CUDA(c, cudaStreamGetCaptureInfo(c->s, &cs, nullptr, &graph, &deps, nullptr, &nd));
+        cudaGraphNodeParams np = {};
+        np.type = cudaGraphNodeTypeConditional;
+        np.conditional.handle = h;
+        np.conditional.type = cudaGraphCondTypeIf;
+        np.conditional.size = 1;
+        cudaGraphNode_t node;
+        PDF_CUDA(c, cudaGraphAddNode(&node, graph, deps, nullptr, nd, &np));
+        PDF_CUDA(c, cudaStreamUpdateCaptureDependencies(c->s, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+        PDF_CUDA(c, cudaStreamBeginCaptureToGraph(c->s_cond, np.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                                  cudaStreamCaptureModeRelaxed));
+        cg_stream = c->s_cond;
+    }
+    if (c->fe_bs == 128) err = launch_pcg<128>(a, c->fe_blocks, cg_stream, ffv);
+    else if (c->fe_bs == 160) err = launch_pcg<160>(a, c->fe_blocks, cg_stream, ffv);
+    else err = launch_pcg<192>(a, c->fe_blocks, cg_stream, ffv);
+    if (cg_stream != c->s) {
+        cudaGraph_t body = nullptr;
+        const cudaError_t end = cudaStreamEndCapture(cg_stream, &body);
+        PDF_CUDA(c, err);
+        PDF_CUDA(c, end);
+    }
     PDF_CUDA(c, err);
     if (c->coop_done) PDF_CUDA(c, cudaEventRecord(c->coop_done, c->s));
     // the periodic image rows take the canonical rows' solution in the node

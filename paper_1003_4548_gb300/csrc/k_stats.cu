@@ -13,17 +13,19 @@
 //    split into nb2, then by (W, id) into nb3; <phi|V> of a bin is its mean psi.
 // Reductions are FP64 (or compensated FP32 with PDF_FP32_KAHAN).
 //
-// FP32 particle state with 2 x 2 x 2 bins, the production path: one warp per
-// element of at most 512 particles (k_moments_med) keeps the segment in
-// registers and shared memory, reads it from memory once, and finds each
-// split's median from a 256-bucket histogram plus an exact rank of the few
-// keys in the median's bucket, one pass over the keys per level (no sort);
-// the moments are exact fixed-point sums (FP32) or compensated FP32 sums
-// (FP32 + Kahan). Crowded elements (more than 512 particles, listed by
-// k_crowded) go to 256-thread teams, and elements above 4096 to the block
-// kernel above; those run on the context stream while the warp kernel runs
-// on a high-priority side stream forked from it. Other bin shapes take the
-// warp bitonic kernel (k_moments_warp).
+// FP32 particle state with 2 x 2 x 2 bins, the production path, for elements
+// of at most 512 particles: one warp per element computes the moments
+// (k_moments_w: exact fixed-point sums for FP32, compensated FP32 sums for
+// FP32 + Kahan) on a high-priority side stream; then, on a third stream, one
+// warp per element (k_bins_med) keeps the segment in registers and shared
+// memory and finds each split's median from a 256-bucket histogram plus an
+// exact rank of the few keys in the median's bucket, one pass over the keys
+// per level (no sort). Only the next particle step reads the bins, so they
+// run beside the field chain, which needs the moments alone. Crowded
+// elements (more than 512 particles, listed by k_crowded) go to 256-thread
+// teams, and elements above 4096 to the block kernel above, moments and bins
+// together on the context stream. Other bin shapes take the warp bitonic
+// kernel (k_moments_warp).
 #include <algorithm>
 
 #include "pdf_internal.cuh"
@@ -991,13 +993,24 @@ __device__ __forceinline__ void kahan_moments(const MomArgs<float>& a, int e, in
 // applies the previous level's boundaries, loads the level's component and
 // fills its histogram, and one candidate pass; a last pass applies the last
 // level and sums psi per bin.
-template <bool KAHAN, int NT, int NMAX>
+// PART selects the work: SEL_MOMENTS, SEL_BINS or both. The bins alone take
+// the element means and variances (bucket ranges, the mean psi of an element
+// with fewer particles than bins) from a moments launch that ran before.
+constexpr int SEL_MOMENTS = 1, SEL_BINS = 2, SEL_ALL = 3;
+template <bool KAHAN, int NT, int NMAX, int PART = SEL_ALL>
 __device__ void sel_element(const MomArgs<float>& a, int e, int s0, int n, SelSmem<NMAX>& S) {
     const Team<NT> T;
     const int B = a.B;
     const uint32_t* __restrict__ ids = a.id + s0;
-    if (KAHAN) kahan_moments<NT>(a, e, s0, n, S);
-    else exact_moments<NT>(a, e, s0, n, S);
+    if constexpr ((PART & SEL_MOMENTS) != 0) {
+        if constexpr (KAHAN) kahan_moments<NT>(a, e, s0, n, S);
+        else exact_moments<NT>(a, e, s0, n, S);
+    } else {
+        if (T.tid < 5) S.mean[T.tid] = a.emean[5 * e + T.tid];
+        else if (T.tid < 8) S.rd[T.tid - 5] = a.eR[6 * e + T.tid - 5];
+        T.sync();
+    }
+    if constexpr ((PART & SEL_BINS) == 0) return;
     if (n < B) {
         for (int q = T.tid; q < n; q += NT) a.bin[s0 + q] = 0;
         for (int b = T.tid; b < B; b += NT) {
@@ -1096,13 +1109,17 @@ __device__ void sel_element(const MomArgs<float>& a, int e, int s0, int n, SelSm
     }
 }
 
-__device__ void empty_element(const MomArgs<float>& a, int e, int tid, int nt_team) {
+__device__ void empty_moments(const MomArgs<float>& a, int e, int tid) {
     if (tid == 0) {
         a.en[e] = 0;
         for (int q = 0; q < 5; ++q) a.emean[5 * e + q] = 0.0;
         for (int q = 0; q < 6; ++q) a.eR[6 * e + q] = 0.0;
         a.epsivar[e] = 0.0;
     }
+}
+
+__device__ void empty_element(const MomArgs<float>& a, int e, int tid, int nt_team) {
+    empty_moments(a, e, tid);
     for (int b = tid; b < a.B; b += nt_team) {
         a.ecm[(size_t)a.B * e + b] = 0.0;
         a.ecmT[(size_t)a.B * e + b] = 0.f;
@@ -1281,21 +1298,19 @@ __device__ __noinline__ void med_rank(MedSmem& S, const uint32_t* __restrict__ i
     __syncwarp();
 }
 
-// moments of the segment: keys j < 8 from the registers, keys j >= 8 read
-// here (and kept in shared memory for the split levels); every lane gets the
-// bucket maps of u, v, w and the mean psi
+// moments of the segment of at most 512 particles, read from memory in
+// blocks of eight keys per lane (key q = lane + 32 j); lanes 0..11 write the
+// means, the central second moments and the psi variance, lane 0 the count
 template <bool KAHAN>
-__device__ __forceinline__ void med_moments(const MomArgs<float>& a, int e, int s0, int n, int kk, int lane,
-                                            const float (&xu)[8], const float (&xv)[8], const float (&xw)[8],
-                                            const float (&xp)[8], MedSmem& S, Buckets (&bk)[3], double& mean_psi) {
+__device__ __forceinline__ void warp_moments(const MomArgs<float>& a, int e, int s0, int n, int lane) {
+    const int kk = (n + 31) >> 5;
     double val = 0.0;
     if constexpr (KAHAN) {
         // sums of the values shifted by the segment's first particle and of
         // their products: a lane sums each block of eight of its keys in plain
         // FP32 (the products fused), the block sums enter compensated sums,
         // then a butterfly reduce-scatter merges the lanes
-        const float su = __shfl_sync(FULLW, xu[0], 0), sv = __shfl_sync(FULLW, xv[0], 0);
-        const float sw = __shfl_sync(FULLW, xw[0], 0), sp = __shfl_sync(FULLW, xp[0], 0);
+        const float su = a.u[s0], sv = a.v[s0], sw = a.w[s0], sp = a.psi[s0];
         AccK acc[16];
 #pragma unroll
         for (int blkno = 0; blkno < 2; ++blkno) {
@@ -1305,14 +1320,10 @@ __device__ __forceinline__ void med_moments(const MomArgs<float>& a, int e, int 
             for (int h = 0; h < 8; ++h) {
                 const int j = 8 * blkno + h, q = lane + 32 * j;
                 const bool in = j < kk && q < n;
-                if (blkno == 0) {
-                    tu[h] = xu[h]; tv[h] = xv[h]; tw[h] = xw[h]; tp[h] = xp[h];
-                } else {  // staged in shared memory by the caller
-                    tu[h] = in ? S.ou[h][lane] : su;
-                    tv[h] = in ? S.ov[h][lane] : sv;
-                    tw[h] = in ? S.ow[h][lane] : sw;
-                    tp[h] = in ? S.op[h][lane] : sp;
-                }
+                tu[h] = in ? a.u[s0 + q] : su;
+                tv[h] = in ? a.v[s0 + q] : sv;
+                tw[h] = in ? a.w[s0 + q] : sw;
+                tp[h] = in ? a.psi[s0 + q] : sp;
                 to[h] = in ? a.om[s0 + q] : 0.f;
             }
             float blk[12];
@@ -1400,12 +1411,7 @@ __device__ __forceinline__ void med_moments(const MomArgs<float>& a, int e, int 
         for (int j = 0; j < 16; ++j) {
             const int q = lane + 32 * j;
             if (j < kk && q < n) {
-                float x0, x1, x2, x3;
-                if (j < 8) {
-                    x0 = xu[j & 7]; x1 = xv[j & 7]; x2 = xw[j & 7]; x3 = xp[j & 7];
-                } else {
-                    x0 = S.ou[j - 8][lane]; x1 = S.ov[j - 8][lane]; x2 = S.ow[j - 8][lane]; x3 = S.op[j - 8][lane];
-                }
+                const float x0 = a.u[s0 + q], x1 = a.v[s0 + q], x2 = a.w[s0 + q], x3 = a.psi[s0 + q];
                 unsigned mu_, mv_, mw_, mp_, mo_;
                 int eu, ev, ew, ep, eo;
                 bool nu, nv, nw, np, no;
@@ -1456,18 +1462,22 @@ __device__ __forceinline__ void med_moments(const MomArgs<float>& a, int e, int 
     else if (lane < 11) a.eR[6 * e + lane - 5] = val;
     else if (lane == 11) a.epsivar[e] = val;
     if (lane == 0) a.en[e] = n;
+}
+
+// the bucket maps of the three split levels: 256 buckets over mean +- 4 sd of
+// the element's u, v, w, from the moments in memory (any monotone map keeps
+// the selection exact; the approximate reciprocal square root only shapes
+// the buckets)
+__device__ __forceinline__ void med_buckets(const MomArgs<float>& a, int e, Buckets (&bk)[3]) {
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
-        // 256 buckets over mean +- 4 sd (any monotone map keeps the selection
-        // exact; the approximate reciprocal square root only shapes the buckets)
-        const float mu = (float)__shfl_sync(FULLW, val, d), var = (float)__shfl_sync(FULLW, val, 5 + d);
+        const float mu = (float)a.emean[5 * e + d], var = (float)a.eR[6 * e + d];
         const float rs = var > 0.f ? rsqrtf(var) : 0.f;
         const float sc = 32.f * rs;
         bk[d].top = 255;
         bk[d].lo = mu - 4.f * var * rs;
         bk[d].sc = (sc > 0.f && sc < 1e30f) ? sc : 0.f;
     }
-    mean_psi = __shfl_sync(FULLW, val, 3);
 }
 
 // append a key to the candidate list (a few keys per level; S.ncl counts them)
@@ -1482,10 +1492,10 @@ __device__ __forceinline__ void med_append(MedSmem& S, uint32_t key, int q, int 
     }
 }
 
-// the general selection path for an element whose boundary buckets are crowded
-template <bool KAHAN>
+// the general selection path for an element whose boundary buckets are
+// crowded (bins only: the moments are in memory)
 __device__ __noinline__ void med_general(const MomArgs<float>& a, int e, int s0, int n, SelSmem<512>& S) {
-    sel_element<KAHAN, 32, 512>(a, e, s0, n, S);
+    sel_element<true, 32, 512, SEL_BINS>(a, e, s0, n, S);
 }
 
 __device__ __forceinline__ int upbit(const MedSmem& S, int q) { return (int)((S.upb[q >> 5] >> (q & 31)) & 1u); }
@@ -1567,25 +1577,42 @@ __device__ __noinline__ void med_tail3(MedSmem& S, unsigned char* bins, int4 c4,
     }
 }
 
-// five blocks per SM for the compensated form (96 registers, no spills; four
-// and six measured slower), four for the exact form (its 128-bit sums)
+// moments of the elements of at most 512 particles, one warp per element
 template <bool KAHAN>
-__global__ void __launch_bounds__(32 * WARPS_PER_BLOCK, KAHAN ? 5 : 4) k_moments_med(const MomArgs<float> a, int nt) {
-    __shared__ union __align__(16) MedUnion {
-        MedSmem m;
-        SelSmem<512> s;
-    } sm[WARPS_PER_BLOCK];
-    static_assert(sizeof(MedUnion) % 16 == 0, "per-warp slices keep hist 16-byte aligned");
-    const int lane = threadIdx.x & 31, wq = threadIdx.x >> 5;
-    const int e = blockIdx.x * WARPS_PER_BLOCK + wq;
+__global__ void __launch_bounds__(32 * WARPS_PER_BLOCK) k_moments_w(const MomArgs<float> a, int nt) {
+    const int lane = threadIdx.x & 31;
+    const int e = blockIdx.x * WARPS_PER_BLOCK + (threadIdx.x >> 5);
     if (e >= nt) return;
     const int s0 = a.off[e], n = a.off[e + 1] - s0;
     if (n > 512) return;  // a block kernel takes it (listed by k_crowded)
     if (n == 0) {
-        empty_element(a, e, lane, 32);
+        empty_moments(a, e, lane);
         return;
     }
-    MedSmem& S = sm[wq].m;
+    warp_moments<KAHAN>(a, e, s0, n, lane);
+}
+
+// the bins of element e (at most 512 particles: larger ones are left to the
+// crowded-element kernels) by the warp
+union __align__(16) MedUnion {
+    MedSmem m;
+    SelSmem<512> s;
+};
+static_assert(sizeof(MedUnion) % 16 == 0, "per-warp slices keep hist 16-byte aligned");
+
+__device__ __forceinline__ void med_bins_element(const MomArgs<float>& a, int e, int lane, MedUnion& U) {
+    const int s0 = a.off[e], n = a.off[e + 1] - s0;
+    if (n > 512) return;  // a block kernel takes it (listed by k_crowded)
+    if (n < 8) {  // no particles: <phi|V> = 0; fewer particles than bins: the element mean (IEM)
+        const double mean_psi = n == 0 ? 0.0 : a.emean[5 * e + 3];
+        if (lane < n) a.bin[s0 + lane] = 0;
+        if (lane < 8) {
+            a.ecm[(size_t)8 * e + lane] = mean_psi;
+            a.ecmT[(size_t)8 * e + lane] = (float)mean_psi;
+        }
+        return;
+    }
+    MedSmem& S = U.m;
     const uint32_t* __restrict__ ids = a.id + s0;
     const int kk = (n + 31) >> 5;  // key slots in use (warp-uniform)
     float xu[8], xv[8], xw[8], xp[8];
@@ -1615,16 +1642,7 @@ __global__ void __launch_bounds__(32 * WARPS_PER_BLOCK, KAHAN ? 5 : 4) k_moments
         }
     }
     Buckets bk[3];
-    double mean_psi;
-    med_moments<KAHAN>(a, e, s0, n, kk, lane, xu, xv, xw, xp, S, bk, mean_psi);
-    if (n < 8) {  // fewer particles than bins: the element mean (IEM)
-        if (lane < n) a.bin[s0 + lane] = 0;
-        if (lane < 8) {
-            a.ecm[(size_t)8 * e + lane] = mean_psi;
-            a.ecmT[(size_t)8 * e + lane] = (float)mean_psi;
-        }
-        return;
-    }
+    med_buckets(a, e, bk);
     unsigned pb0 = 0u, pb1 = 0u;  // bucket of register key j at the current level (a byte each)
     // The passes over the register keys are branch-free (the key slot and the
     // segment bound predicate the stores and atomics), so the eight keys of a
@@ -1734,7 +1752,7 @@ __global__ void __launch_bounds__(32 * WARPS_PER_BLOCK, KAHAN ? 5 : 4) k_moments
     }
     if (general) {  // crowded boundary buckets: the general selection path
         __syncwarp();
-        med_general<KAHAN>(a, e, s0, n, sm[wq].s);
+        med_general(a, e, s0, n, U.s);
         return;
     }
     // ---- bins: the W halves; psi summed per bin
@@ -1779,6 +1797,21 @@ __global__ void __launch_bounds__(32 * WARPS_PER_BLOCK, KAHAN ? 5 : 4) k_moments
         const double cm = __ull2double_rn(sum) * (1.0 / (double)(1ull << 54)) * recip_n(split_size(n, lane, 3));
         a.ecm[(size_t)8 * e + lane] = cm;
         a.ecmT[(size_t)8 * e + lane] = (float)cm;
+    }
+}
+
+// 2 x 2 x 2 bins and <phi|V> of the elements of at most 512 particles, one
+// warp per element, after their moments (bucket ranges and the element mean
+// psi come from memory). Six blocks per SM at most: 80 registers and 36 KB of
+// shared memory per 4-warp block. The grid may hold fewer blocks than
+// element groups (the warps then stride over them), leaving SM room for the
+// field chain that runs beside it.
+__global__ void __launch_bounds__(32 * WARPS_PER_BLOCK, 6) k_bins_med(const MomArgs<float> a, int nt) {
+    __shared__ MedUnion sm[WARPS_PER_BLOCK];
+    const int lane = threadIdx.x & 31, wq = threadIdx.x >> 5;
+    for (int e = blockIdx.x * WARPS_PER_BLOCK + wq; e < nt; e += gridDim.x * WARPS_PER_BLOCK) {
+        med_bins_element(a, e, lane, sm[wq]);
+        __syncwarp();  // the warp's shared memory is free for its next element
     }
 }
 
@@ -1846,9 +1879,17 @@ int run(pdf_ctx* c) {
             a.lcnt = c->elist;  // [0], [1]: list lengths; [2]: next element of listA to take
             a.listA = c->elist + 4;
             a.listB = c->elist + 4 + c->m.nt;
+            // side stream: the moments of the elements of at most 512
+            // particles; the context stream: the crowded elements, moments and
+            // bins together. Then the bins of the warp elements, which only
+            // the next particle step reads, go to a third stream beside the
+            // field chain of the context stream (pdf_step and
+            // pdf_estimate_stats join it back). The bins start after every
+            // moment kernel: started earlier, their blocks fill the SMs and the
+            // crowded-element blocks (larger shared memory) wait for them all.
             PDF_CUDA(c, cudaEventRecord(c->side_fork, c->s));
             PDF_CUDA(c, cudaStreamWaitEvent(c->s2, c->side_fork, 0));
-            k_moments_med<KAHAN><<<blocks, 32 * WARPS_PER_BLOCK, 0, c->s2>>>(a, c->m.nt);
+            k_moments_w<KAHAN><<<blocks, 32 * WARPS_PER_BLOCK, 0, c->s2>>>(a, c->m.nt);
             PDF_CUDA(c, cudaEventRecord(c->side_join, c->s2));
             PDF_CUDA(c, cudaMemsetAsync(a.lcnt, 0, 3 * sizeof(int), c->s));
             k_crowded<<<(c->m.nt + 255) / 256, 256, 0, c->s>>>(c->off, c->m.nt, a.lcnt, a.listA, a.listB);
@@ -1856,7 +1897,15 @@ int run(pdf_ctx* c) {
             const size_t smem = sizeof(SortKey) * STATS_CAP;
             k_moments<T, KAHAN><<<(unsigned)std::min(c->m.nt, c->num_sms), STATS_THREADS, smem, c->s>>>(a);
             PDF_CUDA(c, cudaStreamWaitEvent(c->s, c->side_join, 0));
-            c->launches += 4;
+            PDF_CUDA(c, cudaEventRecord(c->side_fork, c->s));
+            PDF_CUDA(c, cudaStreamWaitEvent(c->s3, c->side_fork, 0));
+            timing_begin(c, PDF_K_BINS, c->s3);
+            const unsigned bgrid = c->bins_bps > 0 ? std::min(blocks, (unsigned)(c->bins_bps * c->num_sms)) : blocks;
+            k_bins_med<<<bgrid, 32 * WARPS_PER_BLOCK, 0, c->s3>>>(a, c->m.nt);
+            timing_end(c, PDF_K_BINS, c->s3);
+            PDF_CUDA(c, cudaEventRecord(c->bins_join, c->s3));
+            c->bins_pending = true;
+            c->launches += 5;
             PDF_CUDA(c, cudaGetLastError());
             return PDF_OK;
         } else {
@@ -1882,11 +1931,23 @@ int prepare_moments(pdf_ctx* c) {
         PDF_CUDA(c, cudaEventCreateWithFlags(&c->side_fork, cudaEventDisableTiming));
         PDF_CUDA(c, cudaEventCreateWithFlags(&c->side_join, cudaEventDisableTiming));
         PDF_CUDA(c, cudaEventCreateWithFlags(&c->side_join2, cudaEventDisableTiming));
+        // the bins stream at the lowest priority: blocks of the field chain
+        // take the SM slots the bins kernel frees first
+        PDF_CUDA(c, cudaStreamCreateWithPriority(&c->s3, cudaStreamNonBlocking, lo));
+        PDF_CUDA(c, cudaEventCreateWithFlags(&c->bins_join, cudaEventDisableTiming));
+        PDF_CUDA(c, cudaStreamCreateWithFlags(&c->s_cond, cudaStreamNonBlocking));
     }
     const int smem = (int)(sizeof(SortKey) * STATS_CAP);
     PDF_CUDA(c, cudaFuncSetAttribute(k_moments<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     PDF_CUDA(c, cudaFuncSetAttribute(k_moments<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     PDF_CUDA(c, cudaFuncSetAttribute(k_moments<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    return PDF_OK;
+}
+
+int join_bins(pdf_ctx* c) {
+    if (!c->bins_pending) return PDF_OK;
+    c->bins_pending = false;
+    PDF_CUDA(c, cudaStreamWaitEvent(c->s, c->bins_join, 0));
     return PDF_OK;
 }
 

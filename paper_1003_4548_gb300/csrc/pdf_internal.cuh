@@ -175,6 +175,16 @@ struct pdf_ctx {
     // the right-hand side and the residual check (side_join2: the Laplacian)
     cudaStream_t s2 = nullptr;
     cudaEvent_t side_fork = nullptr, side_join = nullptr, side_join2 = nullptr;
+    // bins stream: the velocity bins and <phi|V> of a step, forked after the
+    // warp moments, joined back into the context stream before the step ends
+    cudaStream_t s3 = nullptr;
+    cudaEvent_t bins_join = nullptr;
+    bool bins_pending = false;
+    int bins_bps = 5;  // blocks per SM of the bins kernel (0: one block per four elements)
+    // stream that captures the body of the conditional node around the
+    // elliptic CG (lagged or surrogate wp in a captured graph); used for
+    // nothing else
+    cudaStream_t s_cond = nullptr;
     std::string err;
     int num_sms = 0;
 };
@@ -196,8 +206,8 @@ int fail(pdf_ctx* c, int code, const std::string& msg);
     } while (0)
 
 // kernel-class timing brackets (no-ops unless timing is on)
-void timing_begin(pdf_ctx* c, int k);
-void timing_end(pdf_ctx* c, int k);
+void timing_begin(pdf_ctx* c, int k, cudaStream_t st = nullptr);  // st: the context stream if null
+void timing_end(pdf_ctx* c, int k, cudaStream_t st = nullptr);
 
 // ---------------------------------------------------------------------------
 // launchers (one translation unit each)
@@ -210,6 +220,7 @@ inline int scan_blocks(int nt) { return (nt + SCAN_CHUNK - 1) / SCAN_CHUNK; }
 int set_device_step(pdf_ctx* c);    // d_step = step
 int launch_count_and_sort(pdf_ctx* c);  // histogram of elemA, then launch_sort
 int launch_moments(pdf_ctx* c);
+int join_bins(pdf_ctx* c);          // the context stream waits for the bins stream (no-op if nothing is pending)
 int launch_fields(pdf_ctx* c);      // node stats, derived, recovery, ER solve, packs
 int launch_elliptic(pdf_ctx* c);     // right-hand side, (wait for the assembly on side_join), check, CG
 int launch_fe_assemble(pdf_ctx* c, cudaStream_t s);  // values of M + K_{L^2} from L (column 8 of eder)

@@ -112,22 +112,26 @@ def test_autotune_changes_shapes_not_results(torch):
 
 def test_batch_graph_fp32_lagged_and_pressure(torch):
     """The FP32 path in the graph: the warp-per-element moments on the side
-    stream, the lagged FE solve (mode 5) and the pressure projection's
-    cooperative solve. With exact FP32 reductions (order-independent) a
-    batched case ends exactly where the same case stepped on its own ends."""
+    stream and the bins on the third, the lagged FE solve (mode 5; in the
+    graph the CG sits in a conditional node opened by the residual check:
+    tolerance 0 solves every step, 1e30 never, 0.05 as the check decides)
+    and the pressure projection's cooperative solve. With exact FP32
+    reductions (order-independent) a batched case ends exactly where the
+    same case stepped on its own ends, with the same solve count."""
     from paper_1003_4548_gb300 import capi
-    specs = (("er", dict(), 5), ("er", dict(pressure=1, pressure_tol=1e-10), 5), ("wf", dict(), 0))
+    specs = (("er", dict(), 5, 0.05), ("er", dict(pressure=1, pressure_tol=1e-10), 5, 0.05), ("wf", dict(), 0, 0),
+             ("er", dict(), 5, 0.0), ("er", dict(), 5, 1e30))
     cs = cases()
     er_mesh = cs[1][0]
     wf_mesh = cs[0][0]
     streams = [torch.cuda.Stream() for _ in range(2 * len(specs) + 1)]
     batched, alone, dts = [], [], []
-    for k, (wm, over, mode) in enumerate(specs):
+    for k, (wm, over, mode, tol) in enumerate(specs):
         mesh = er_mesh if wm == "er" else wf_mesh
         for lst, st in ((batched, streams[k]), (alone, streams[len(specs) + k])):
             g = make(torch, mesh, 24, wm, k, st, **dict(over, precision="fp32"))
             if mode:
-                g.set_surrogate(mode, None, None, 0.05)
+                g.set_surrogate(mode, None, None, tol)
             lst.append(g)
         dts.append(cfl_dt(mesh, cfl=0.5, k0=1e-3))
     b = capi.Batch(batched, dts, streams[-1].cuda_stream)
@@ -143,6 +147,14 @@ def test_batch_graph_fp32_lagged_and_pressure(torch):
         assert np.array_equal(ga.field("elem_mean"), gb.field("elem_mean"))
         assert np.array_equal(ga.field("node_pack"), gb.field("node_pack"))
     assert np.array_equal(alone[1].field("node_p"), batched[1].field("node_p"))
+    for k, (wm, _, mode, tol) in enumerate(specs):
+        if mode:
+            (sa, fa, _), (sb, fb, _) = alone[k].surrogate_stats(), batched[k].surrogate_stats()
+            assert (sa, fa) == (sb, fb), k
+            if tol == 0.0:
+                assert fa == sa == 4  # every check rejects: the CG runs in every step
+            if tol == 1e30:
+                assert fa == 0 and sa == 4
     b.close()
     for g in batched + alone:
         g.close()
