@@ -411,6 +411,19 @@ int pdf_mlp_forward(const float* params, const float* X, int32_t n, float* Y, fl
 int pdf_mlp_loss_grad(const float* params, const float* X, const float* T, int32_t n, float* work, float* grad,
                       float* loss, void* cuda_stream);
 
+/* The same loss and gradient on the tensor cores (tcgen05, bfloat16 operands,
+ * FP32 accumulation; the parameters stay FP32): one 128-sample tile per CTA,
+ * forward and backward chained in tensor memory, the tiles' partial
+ * gradients summed in tile order (deterministic, no atomics). Every operand
+ * of a product is rounded to bfloat16 where it enters it: the weights, the
+ * inputs, the hidden activations, dY and each layer's dZ; a bias gradient is
+ * the sum of the rounded dZ. Same arguments and work size as
+ * pdf_mlp_loss_grad (work holds ceil(n/128) * (PDF_MLP_NPARAM + 1) + 1
+ * floats of it). If a tensor-core completion wait runs out, grad and loss are
+ * set to NaN. Enqueued on cuda_stream. */
+int pdf_mlp_loss_grad_bf16(const float* params, const float* X, const float* T, int32_t n, float* work,
+                           float* grad, float* loss, void* cuda_stream);
+
 /* One Adam step (Kingma & Ba 2015) on device params/m/v with gradient grad:
  *   m = b1 m + (1 - b1) g;  v = b2 v + (1 - b2) g^2;
  *   params -= lr (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps)

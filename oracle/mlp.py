@@ -74,28 +74,37 @@ def forward(p, X, bf16: bool = False, bf16_act: bool = False):
     return a3 @ w["W4"].T + w["b4"]
 
 
-def loss_grad(p, X, T):
-    """L = sum((Y - T)^2) / (5 n) and dL/dp (chain rule, layer by layer)."""
+def loss_grad(p, X, T, bf16: bool = False):
+    """L = sum((Y - T)^2) / (5 n) and dL/dp (chain rule, layer by layer).
+
+    bf16=True: the mixed precision of a bfloat16 tensor-core product chain.
+    Every operand of a matrix product is rounded to bfloat16 where it enters
+    the product (FP32 value first, then bfloat16): the weights, the inputs,
+    the hidden activations, dY and each layer's dZ. Bias adds, SiLU and its
+    derivative, the loss and every sum stay exact. A bias gradient is the sum
+    of the rounded dZ, as the weight-gradient product gives it."""
     w = unpack(p)
-    X = np.asarray(X, np.float64)
+    r = (lambda a: bf16_round(np.asarray(a, np.float32)).astype(np.float64)) if bf16 else (lambda a: a)
+    W = {k: r(w[k]) for k in ("W1", "W2", "W3", "W4")}
+    X = r(np.asarray(X, np.float64))
     T = np.asarray(T, np.float64)
     n = X.shape[0]
-    z1 = X @ w["W1"].T + w["b1"]
-    a1 = silu(z1)
-    z2 = a1 @ w["W2"].T + w["b2"]
-    a2 = silu(z2)
-    z3 = a2 @ w["W3"].T + w["b3"]
-    a3 = silu(z3)
-    Y = a3 @ w["W4"].T + w["b4"]
+    z1 = X @ W["W1"].T + w["b1"]
+    a1 = r(silu(z1))
+    z2 = a1 @ W["W2"].T + w["b2"]
+    a2 = r(silu(z2))
+    z3 = a2 @ W["W3"].T + w["b3"]
+    a3 = r(silu(z3))
+    Y = a3 @ W["W4"].T + w["b4"]
     E = Y - T
     L = float(np.sum(E * E) / (OUT * n))
-    dY = 2.0 * E / (OUT * n)
+    dY = r(2.0 * E / (OUT * n))
     g = {"W4": dY.T @ a3, "b4": dY.sum(0)}
-    dz3 = (dY @ w["W4"]) * silu_grad(z3)
+    dz3 = r((dY @ W["W4"]) * silu_grad(z3))
     g["W3"], g["b3"] = dz3.T @ a2, dz3.sum(0)
-    dz2 = (dz3 @ w["W3"]) * silu_grad(z2)
+    dz2 = r((dz3 @ W["W3"]) * silu_grad(z2))
     g["W2"], g["b2"] = dz2.T @ a1, dz2.sum(0)
-    dz1 = (dz2 @ w["W2"]) * silu_grad(z1)
+    dz1 = r((dz2 @ W["W2"]) * silu_grad(z1))
     g["W1"], g["b1"] = dz1.T @ X, dz1.sum(0)
     return L, pack(g)
 

@@ -57,7 +57,7 @@ EXPORTS = ("pdf_default_params", "pdf_init_mesh", "pdf_seed_particles", "pdf_set
            "pdf_pressure_iterations",
            "pdf_set_timing", "pdf_kernel_time", "pdf_reset_timing", "pdf_launch_count", "pdf_last_error",
            "pdf_destroy", "pdf_sort_by_element_static", "pdf_mlp_work_floats", "pdf_mlp_forward",
-           "pdf_mlp_loss_grad", "pdf_mlp_adam", "pdf_mlp_column_stats", "pdf_mlp_gather_rows",
+           "pdf_mlp_loss_grad", "pdf_mlp_loss_grad_bf16", "pdf_mlp_adam", "pdf_mlp_column_stats", "pdf_mlp_gather_rows",
            "pdf_mlp_standardize", "pdf_surrogate_rows", "pdf_surrogate_harvest", "pdf_set_surrogate",
            "pdf_surrogate_stats", "pdf_batch_create", "pdf_batch_create_out", "pdf_batch_step", "pdf_batch_sync", "pdf_batch_destroy",
            "pdf_autotune", "pdf_set_averaging", "pdf_averaging_count", "pdf_get_averages", "pdf_probe",
@@ -118,6 +118,7 @@ def lib(allow_build: bool = True):
         L.pdf_mlp_work_floats.restype = C.c_int64
         L.pdf_mlp_forward.argtypes = [vp, vp, C.c_int32, vp, vp, C.c_int32, vp]
         L.pdf_mlp_loss_grad.argtypes = [vp, vp, vp, C.c_int32, vp, vp, vp, vp]
+        L.pdf_mlp_loss_grad_bf16.argtypes = [vp, vp, vp, C.c_int32, vp, vp, vp, vp]
         L.pdf_mlp_adam.argtypes = [vp, vp, vp, vp, C.c_int32, C.c_float, C.c_float, C.c_float, C.c_float, vp]
         L.pdf_mlp_column_stats.argtypes = [vp, C.c_int64, C.c_int32, vp, vp, vp]
         L.pdf_mlp_gather_rows.argtypes = [vp, vp, C.c_int32, C.c_int32, vp, vp]
@@ -197,6 +198,11 @@ def mlp_forward(params, X, n, Y, work, bf16_weights=False, stream=0):
 def mlp_loss_grad(params, X, T, n, work, grad, loss, stream=0):
     _chk(lib().pdf_mlp_loss_grad(_vp(params), _vp(X), _vp(T), n, _vp(work), _vp(grad), _vp(loss), _vp(stream)),
          "pdf_mlp_loss_grad")
+
+
+def mlp_loss_grad_bf16(params, X, T, n, work, grad, loss, stream=0):
+    _chk(lib().pdf_mlp_loss_grad_bf16(_vp(params), _vp(X), _vp(T), n, _vp(work), _vp(grad), _vp(loss),
+                                      _vp(stream)), "pdf_mlp_loss_grad_bf16")
 
 
 def mlp_adam(params, grad, m, v, t, lr, beta1=0.9, beta2=0.999, eps=1e-8, stream=0):

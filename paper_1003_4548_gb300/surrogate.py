@@ -6,7 +6,8 @@ features and the FE solution wp_ij / eps (pdf_surrogate_harvest).
 
 Train: the C-ABI kernels standardise the columns and draw mini-batches. Adam
 steps the FP32 parameters, with the network's own forward and backward
-kernels (pdf_mlp_loss_grad). The host only orders the calls and holds the
+kernels on the tensor cores (pdf_mlp_loss_grad_bf16; the FP32 kernels of
+pdf_mlp_loss_grad on request). The host only orders the calls and holds the
 seeded batch permutation.
 
 PyTorch supplies the device buffers and the stream; no step of the network
@@ -70,10 +71,13 @@ def harvest(meshes, *, steps: int, every: int, per_element: int, dt_of, C0: floa
 
 
 def train(X, T, *, epochs: int = 10, batch: int = 4096, lr: float = 2e-3, lr_final: float = 1e-4, seed: int = 0,
-          params=None, torch=None, log=None):
-    """Standardise, then Adam over seeded mini-batches. Returns (params,
-    norm, history) with params/norm as float32 numpy arrays in the C-ABI
-    layout and history a list of (epoch, mean batch loss)."""
+          params=None, torch=None, log=None, tensor_cores: bool = True):
+    """Standardise, then Adam over seeded mini-batches. The loss gradient of a
+    batch comes from the tensor-core kernels (bfloat16 operands, FP32
+    accumulation and FP32 parameters; pdf_mlp_loss_grad_bf16), or with
+    tensor_cores=False from the FP32 kernels (pdf_mlp_loss_grad). Returns
+    (params, norm, history) with params/norm as float32 numpy arrays in the
+    C-ABI layout and history a list of (epoch, mean batch loss)."""
     import torch as _torch
     torch = torch or _torch
     s = torch.cuda.current_stream().cuda_stream
@@ -93,6 +97,7 @@ def train(X, T, *, epochs: int = 10, batch: int = 4096, lr: float = 2e-3, lr_fin
     xb = torch.empty((b, IN), dtype=torch.float32, device="cuda")
     tb = torch.empty((b, OUT), dtype=torch.float32, device="cuda")
     loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+    grad_fn = capi.mlp_loss_grad_bf16 if tensor_cores else capi.mlp_loss_grad
     rng = np.random.default_rng(seed)
     nb = max(1, n // b)
     total = epochs * nb
@@ -105,8 +110,7 @@ def train(X, T, *, epochs: int = 10, batch: int = 4096, lr: float = 2e-3, lr_fin
             idx = perm[k * b:(k + 1) * b]
             capi.mlp_gather_rows(Xs.data_ptr(), idx.data_ptr(), b, IN, xb.data_ptr(), s)
             capi.mlp_gather_rows(Ts.data_ptr(), idx.data_ptr(), b, OUT, tb.data_ptr(), s)
-            capi.mlp_loss_grad(P.data_ptr(), xb.data_ptr(), tb.data_ptr(), b, work.data_ptr(), G.data_ptr(),
-                               loss.data_ptr(), s)
+            grad_fn(P.data_ptr(), xb.data_ptr(), tb.data_ptr(), b, work.data_ptr(), G.data_ptr(), loss.data_ptr(), s)
             t += 1
             rate = lr * (lr_final / lr) ** (t / max(1, total))  # geometric decay
             capi.mlp_adam(P.data_ptr(), G.data_ptr(), M.data_ptr(), V.data_ptr(), t, rate, stream=s)

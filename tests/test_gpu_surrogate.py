@@ -2,7 +2,8 @@
 and the surrogate inside an elliptic-relaxation context.
 
 Bars: the FP32 loss gradient within 1e-4 of the oracle (relative to the
-gradient's magnitude plus its rms); FP32 forward within 1e-5 and the bf16
+gradient's magnitude plus its rms), the tensor-core gradient within 1e-3 of
+the oracle's gradient with the same bfloat16 rounding points; FP32 forward within 1e-5 and the bf16
 forward within 1e-4 of the oracle with the same bf16-rounded weights (FP32
 accumulation is the only difference); Adam, column statistics,
 standardisation and gathers to FP32 rounding; harvested features within 1e-6
@@ -56,6 +57,41 @@ def test_loss_gradient_matches_oracle(torch):
     # a second call on the same buffers gives the same numbers (no accumulation)
     G2 = G.clone()
     capi.mlp_loss_grad(P.data_ptr(), Xd.data_ptr(), Td.data_ptr(), n, work.data_ptr(), G.data_ptr(), L.data_ptr(), s)
+    torch.cuda.synchronize()
+    assert torch.equal(G, G2)
+
+
+def test_tensor_core_gradient_matches_oracle(torch):
+    """pdf_mlp_loss_grad_bf16 against the oracle's mixed-precision gradient
+    (the same bfloat16 rounding points; FP32 accumulation and the hardware
+    exponential are the only differences): within 1e-3 of it, and at least
+    four times closer to it than to the exact FP64 gradient, so the rounding
+    points are the oracle's. Three tiles, the last ragged; deterministic."""
+    from paper_1003_4548_gb300 import capi
+    rng = np.random.default_rng(7)
+    n = 333
+    p = (rng.normal(0, 0.3, mlp.NPARAM)).astype(np.float32)
+    X = rng.normal(size=(n, mlp.IN)).astype(np.float32)
+    T = rng.normal(size=(n, mlp.OUT)).astype(np.float32)
+    P, Xd, Td = dev(torch, p), dev(torch, X), dev(torch, T)
+    G = torch.zeros(mlp.NPARAM, dtype=torch.float32, device="cuda")
+    L = torch.zeros(1, dtype=torch.float32, device="cuda")
+    work = torch.empty(capi.mlp_work_floats(n), dtype=torch.float32, device="cuda")
+    s = torch.cuda.current_stream().cuda_stream
+    capi.mlp_loss_grad_bf16(P.data_ptr(), Xd.data_ptr(), Td.data_ptr(), n, work.data_ptr(), G.data_ptr(),
+                            L.data_ptr(), s)
+    torch.cuda.synchronize()
+    Lb, gb = mlp.loss_grad(p.astype(np.float64), X, T, bf16=True)
+    _, ge = mlp.loss_grad(p.astype(np.float64), X, T)
+    g = G.cpu().numpy()
+    assert float(L.item()) == pytest.approx(Lb, rel=1e-5)
+    ok, err = close(g, gb, 1e-3)
+    assert ok, err
+    _, err_exact = close(g, ge, 1.0)
+    assert err < err_exact / 4, (err, err_exact)
+    G2 = G.clone()
+    capi.mlp_loss_grad_bf16(P.data_ptr(), Xd.data_ptr(), Td.data_ptr(), n, work.data_ptr(), G.data_ptr(),
+                            L.data_ptr(), s)
     torch.cuda.synchronize()
     assert torch.equal(G, G2)
 

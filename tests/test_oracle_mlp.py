@@ -104,3 +104,49 @@ def test_bf16_activation_mode_closed_form():
     # and it differs from the FP32-activation network by about a bf16 ulp
     Yf = mlp.forward(p, X, bf16=True)
     assert 0 < np.max(np.abs(Y - Yf)) < 0.05 * np.max(np.abs(Yf))
+
+
+def test_bf16_gradient_closed_form_with_zero_hidden_weights():
+    """With W1 = W2 = W3 = 0 every hidden activation is a constant row:
+    a_l = bf16(SiLU(b_l)). The mixed-precision gradients of the top two
+    layers then have closed forms in the rounded quantities: with
+    dY = bf16(2 (Y - T) / 5n), gW4 = (sum_r dY_r) a3^T, gb4 = sum_r dY_r,
+    dz3 = bf16((dY bf16(W4)) * SiLU'(b3)), gW3 = (sum_r dz3_r) a2^T,
+    gb3 = sum_r dz3_r."""
+    rng = np.random.default_rng(9)
+    w = mlp.unpack(random_params(rng))
+    w["W1"][:] = 0.0
+    w["W2"][:] = 0.0
+    w["W3"][:] = 0.0
+    p = mlp.pack(w).astype(np.float32).astype(np.float64)
+    n = 6
+    X = rng.normal(size=(n, mlp.IN))
+    T = rng.normal(size=(n, mlp.OUT))
+    L, g = mlp.loss_grad(p, X, T, bf16=True)
+    q = mlp.unpack(p)
+    rb = lambda a: mlp.bf16_round(np.asarray(a, np.float32)).astype(np.float64)
+    a2, a3 = rb(mlp.silu(q["b2"])), rb(mlp.silu(q["b3"]))
+    W4 = rb(q["W4"])
+    Y = np.tile(W4 @ a3 + q["b4"], (n, 1))
+    dY = rb(2.0 * (Y - T) / (5 * n))
+    dz3 = rb((dY @ W4) * mlp.silu_grad(q["b3"])[None, :])
+    G = mlp.unpack(g)
+    assert L == pytest.approx(np.sum((Y - T) ** 2) / (5 * n), rel=1e-14)
+    assert np.allclose(G["W4"], np.outer(dY.sum(0), a3), rtol=1e-14, atol=1e-300)
+    assert np.allclose(G["b4"], dY.sum(0), rtol=1e-14, atol=1e-300)
+    assert np.allclose(G["W3"], np.outer(dz3.sum(0), a2), rtol=1e-14, atol=1e-300)
+    assert np.allclose(G["b3"], dz3.sum(0), rtol=1e-14, atol=1e-300)
+
+
+def test_bf16_gradient_is_the_exact_one_within_bf16_rounding():
+    """The mixed-precision gradient differs from the exact one, by a few
+    bfloat16 ulps of the gradient's scale at most."""
+    rng = np.random.default_rng(10)
+    p = random_params(rng).astype(np.float32).astype(np.float64)
+    X = rng.normal(size=(40, mlp.IN))
+    T = rng.normal(size=(40, mlp.OUT))
+    L0, g0 = mlp.loss_grad(p, X, T)
+    L1, g1 = mlp.loss_grad(p, X, T, bf16=True)
+    d = np.max(np.abs(g1 - g0)) / np.max(np.abs(g0))
+    assert 0 < d < 8 * 2.0 ** -8
+    assert L1 == pytest.approx(L0, rel=0.05)
