@@ -362,6 +362,15 @@ typedef struct pdf_tuning {
  * within the CG tolerance. out may be NULL. */
 int pdf_autotune(pdf_ctx* c, double dt, int32_t steps_per_trial, pdf_tuning* out);
 
+/* Apply launch shapes (from pdf_autotune of this or a like context) without
+ * timing anything: step_blocks_per_sm (> 0), scatter_threads (128, 256 or
+ * 512), cg_rows_per_block (128, 160 or 192; elliptic relaxation only; 0
+ * keeps the current grid) and bins_blocks_per_sm (>= 0; -1 keeps it).
+ * PDF_ERR_ARG for a value outside these sets,
+ * PDF_ERR_CAPACITY for a CG block whose grid would not be co-resident.
+ * The ms_* fields are ignored. */
+int pdf_apply_tuning(pdf_ctx* c, const pdf_tuning* t);
+
 /* ---------------------------------------------------------------------------
  * Learned surrogate of the elliptic-relaxation solve (Eqs. elliptic-relaxation,
  * Gij, C0). The paper solves Eq. elliptic-relaxation by finite elements every

@@ -60,7 +60,7 @@ EXPORTS = ("pdf_default_params", "pdf_init_mesh", "pdf_seed_particles", "pdf_set
            "pdf_mlp_loss_grad", "pdf_mlp_loss_grad_bf16", "pdf_mlp_adam", "pdf_mlp_column_stats", "pdf_mlp_gather_rows",
            "pdf_mlp_standardize", "pdf_surrogate_rows", "pdf_surrogate_harvest", "pdf_set_surrogate",
            "pdf_surrogate_stats", "pdf_batch_create", "pdf_batch_create_out", "pdf_batch_step", "pdf_batch_sync", "pdf_batch_destroy",
-           "pdf_autotune", "pdf_set_averaging", "pdf_averaging_count", "pdf_get_averages", "pdf_probe",
+           "pdf_autotune", "pdf_apply_tuning", "pdf_set_averaging", "pdf_averaging_count", "pdf_get_averages", "pdf_probe",
            "pdf_set_cdf_probes", "pdf_get_cdf", "pdf_set_wait_limit")
 
 MLP_IN, MLP_HIDDEN, MLP_OUT, MLP_NPARAM, MLP_NNORM = 10, 64, 5, 9349, 30
@@ -135,6 +135,7 @@ def lib(allow_build: bool = True):
         L.pdf_batch_destroy.argtypes = [vp]
         L.pdf_batch_destroy.restype = None
         L.pdf_autotune.argtypes = [vp, C.c_double, C.c_int32, P(pdf_tuning)]
+        L.pdf_apply_tuning.argtypes = [vp, P(pdf_tuning)]
         L.pdf_set_averaging.argtypes = [vp, C.c_int32, C.c_int32]
         L.pdf_averaging_count.argtypes = [vp]
         L.pdf_averaging_count.restype = C.c_int64
@@ -372,6 +373,16 @@ class Canyon:
         out = {n: getattr(t, n) for n, _ in pdf_tuning._fields_}
         out["ms_step_bins"] = list(out["ms_step_bins"])
         return out
+
+    def apply_tuning(self, tuning: dict):
+        """Set launch shapes (a dict as autotune returns it; missing keys keep
+        the defaults of pdf_tuning's fields as autotune would report them)."""
+        t = pdf_tuning()
+        t.step_blocks_per_sm = int(tuning.get("step_blocks_per_sm", 4))
+        t.scatter_threads = int(tuning.get("scatter_threads", 256))
+        t.cg_rows_per_block = int(tuning.get("cg_rows_per_block", 0))
+        t.bins_blocks_per_sm = int(tuning.get("bins_blocks_per_sm", -1))
+        self._check(lib().pdf_apply_tuning(self._h, C.byref(t)))
 
     # -- time averaging, probes, scalar CDFs --------------------------------
     def set_averaging(self, on: bool, reset: bool = False):

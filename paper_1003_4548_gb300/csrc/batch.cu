@@ -309,4 +309,22 @@ int pdf_autotune(pdf_ctx* c, double dt, int32_t steps_per_trial, pdf_tuning* out
     return st;
 }
 
+int pdf_apply_tuning(pdf_ctx* c, const pdf_tuning* t) {
+    if (!c || !t) return PDF_ERR_ARG;
+    const int sc = t->scatter_threads;
+    if (t->step_blocks_per_sm < 1 || (sc != 128 && sc != 256 && sc != 512) || t->bins_blocks_per_sm < -1 ||
+        (t->cg_rows_per_block != 0 && t->cg_rows_per_block != 128 && t->cg_rows_per_block != 160 &&
+         t->cg_rows_per_block != 192))
+        return fail(c, PDF_ERR_ARG, "pdf_apply_tuning: launch shape outside the tuned sets");
+    int st = prepare_particle(c, t->step_blocks_per_sm);
+    if (st != PDF_OK) return st;
+    c->scatter_threads = sc;
+    if (t->cg_rows_per_block && c->p.wall_model == PDF_ELLIPTIC_RELAXATION) {
+        st = prepare_elliptic(c, t->cg_rows_per_block);
+        if (st != PDF_OK) return st;
+    }
+    if (t->bins_blocks_per_sm >= 0) c->bins_bps = t->bins_blocks_per_sm;
+    return PDF_OK;
+}
+
 }  // extern "C"

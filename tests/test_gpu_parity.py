@@ -34,12 +34,16 @@ def gpu_params(mesh, **kw):
     return canyon_params(mesh, **kw)
 
 
-def both(mesh, *, precision="fp64", wall_model="wf", C0=2.1, seed=0, cg_tol=1e-12, cg_precision=0, **over):
+def both(mesh, *, precision="fp64", wall_model="wf", C0=2.1, seed=0, cg_tol=1e-14, cg_precision=0, **over):
+    """A GPU context and an oracle on the same mesh and parameters. Both FE
+    solves of the elliptic relaxation converge to a relative residual of
+    1e-14 by default, so the drift tensor they give agrees far below the
+    1e-12 bar of the one-step state."""
     from paper_1003_4548_gb300 import Canyon
     gp = gpu_params(mesh, wall_model=wall_model, precision=precision, C0=C0, seed=seed, cg_tol=cg_tol,
                     cg_maxit=20000, cg_precision=cg_precision, **over)
     op = oracle_params_for(mesh, wall_model=0 if wall_model == "wf" else 1, C0=C0, seed=seed,
-                           cg_tol=1e-13, **over)
+                           cg_tol=min(cg_tol, 1e-14), **over)
     return Canyon(gp, mesh), Oracle(op, mesh)
 
 
@@ -77,28 +81,32 @@ def edge_distance(mesh, P):
     return np.minimum(np.minimum(d0, d1), d2)
 
 
-def assert_state_close(g, o, rtol, skip=None):
-    """Relative error per particle: position and velocity against their vector
-    norms (plus the ensemble rms of that norm), omega and psi against their
-    magnitude (plus the ensemble rms). Particles flagged in skip are left out."""
+def assert_state_close(g, o, rtol, skip=None, velocity="component"):
+    """Relative error per particle and component: each of x, y, u, v, w,
+    omega, psi against its own magnitude plus the ensemble rms of that
+    component (a small v beside a large u is judged against the spread of v,
+    not against |U|). velocity="vector" judges u, v, w against the velocity
+    vector's magnitude plus its ensemble rms instead: for the mean-pressure
+    projection, whose correction -dt grad p is a vector from an iterative
+    solve, its error is of the size of |grad p| in every component.
+    Particles flagged in skip are left out."""
     if skip is not None:
         keep = ~skip
         g = {k: v[keep] for k, v in g.items()}
         o = {k: v[keep] for k, v in o.items()}
-    groups = (("x", "y"), ("u", "v", "w"), ("om",), ("psi",))
-    for grp in groups:
-        norm = np.sqrt(sum(o[k] ** 2 for k in grp))
-        scale = norm + np.sqrt(np.mean(norm ** 2)) + 1e-300
-        for k in grp:
-            d = np.abs(g[k] - o[k])
-            lim = rtol * scale
-            bad = d > lim
-            if bad.any():
-                w = np.argsort(-(d / lim))[:5]
-                detail = [{q: float(o[q][i]) for q in STATE} | {"gpu": float(g[k][i]), "elem": int(o["elem"][i])}
-                          for i in w]
-                raise AssertionError(f"{k}: {int(bad.sum())} of {d.size} beyond rtol {rtol}; worst ratio "
-                                     f"{float(np.max(d / lim)):.2f}; worst: {detail}")
+    speed = np.sqrt(o["u"] ** 2 + o["v"] ** 2 + o["w"] ** 2)
+    for k in ("x", "y", "u", "v", "w", "om", "psi"):
+        ref = speed if (velocity == "vector" and k in ("u", "v", "w")) else np.abs(o[k])
+        scale = ref + np.sqrt(np.mean(ref ** 2)) + 1e-300
+        d = np.abs(g[k] - o[k])
+        lim = rtol * scale
+        bad = d > lim
+        if bad.any():
+            w = np.argsort(-(d / lim))[:5]
+            detail = [{q: float(o[q][i]) for q in STATE} | {"gpu": float(g[k][i]), "elem": int(o["elem"][i])}
+                      for i in w]
+            raise AssertionError(f"{k}: {int(bad.sum())} of {d.size} beyond rtol {rtol}; worst ratio "
+                                 f"{float(np.max(d / lim)):.2f}; worst: {detail}")
 
 
 def small_mesh():
