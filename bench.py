@@ -285,6 +285,31 @@ def roofline(kclass, kt, n, ts, workload, precision):
             if peak_kind == "measured" else "fallback 6.8 TB/s"}
 
 
+def fp64_roofline(kt, n, workload):
+    """The FP64 form's particle kernel against the GPU's measured FP64 FMA
+    rate: FP64 FLOPs per particle (2 per DFMA, 1 per DADD and DMUL, counted
+    by ncu on the current source of k_step<double>) times the particles,
+    over the kernel's CUDA-event time per launch."""
+    from paper_1003_4548_gb300 import capi
+    peak = capi.measure_fp64_fma_rate()
+    ms, launches = kt["particle"]
+    fpp = None
+    try:
+        with open(os.path.join(ROOT, "profiles", "kernel_traffic.json")) as fh:
+            e = json.load(fh)[f"k_step:{workload}:fp64"]
+        if e.get("source_hash") == kernel_source_hash("k_step"):
+            fpp = float(e["fp64_flops_per_particle"])
+    except Exception:
+        fpp = None
+    out = {"bound": "alu", "kernel": "k_step<double> (per-particle step, FP64 state)", "peak": peak,
+           "unit": "TFLOP/s", "peak_source": "measured FP64 FMA rate (pdf_measure_fp64_fma_rate)",
+           "ms_per_launch": ms / max(launches, 1), "fp64_flops_per_particle": fpp, "achieved": None, "frac": None}
+    if fpp and launches:
+        out["achieved"] = fpp * n / (ms / launches / 1e3) / 1e12
+        out["frac"] = out["achieved"] / peak
+    return out
+
+
 def cell_stats(g, mesh, nx=12, ny=8):
     """Particle-weighted <U>, <V>, the Reynolds stresses <uu>, <vv>, <ww>,
     <uv>, k, <psi> and the psi variance over an nx x ny grid of cells (element
@@ -835,6 +860,8 @@ def main():
             forms[name] = {"value": f.g.num_particles * k / (rr["ms"] / 1e3), "ms_per_step": rr["ms"] / k,
                            "steps": k, "cg_iterations_last": rr["cg_iterations_last"],
                            "kernels_ms_per_step": {q: v[0] / k for q, v in rr["kt"].items()}}
+            if fp == "fp64":
+                forms[name]["roofline_fp64"] = fp64_roofline(rr["kt"], f.g.num_particles, a.workload)
             f.close()
         if sur is not None and chosen_wp is not sur:  # the trained network in place of the lagged solve
             f = Form(cfg, mesh, stream, precision=prec, sur=sur)

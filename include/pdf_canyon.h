@@ -362,6 +362,14 @@ typedef struct pdf_tuning {
  * within the CG tolerance. out may be NULL. */
 int pdf_autotune(pdf_ctx* c, double dt, int32_t steps_per_trial, pdf_tuning* out);
 
+/* Measured FP64 fused multiply-add rate of the current device, in TFLOP/s
+ * (two FLOPs per FMA): eight independent FMA chains per thread, eight
+ * 256-thread blocks per SM, timed with CUDA events on cuda_stream after a
+ * warm-up launch. The peak against which the FP64 forms' arithmetic-bound
+ * kernels are reported. Synchronises the stream; allocates 8 bytes of device
+ * memory for the duration of the call. */
+int pdf_measure_fp64_fma_rate(void* cuda_stream, double* tflops);
+
 /* Apply launch shapes (from pdf_autotune of this or a like context) without
  * timing anything: step_blocks_per_sm (> 0), scatter_threads (128, 256 or
  * 512), cg_rows_per_block (128, 160 or 192; elliptic relaxation only; 0

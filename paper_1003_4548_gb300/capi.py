@@ -60,7 +60,7 @@ EXPORTS = ("pdf_default_params", "pdf_init_mesh", "pdf_seed_particles", "pdf_set
            "pdf_mlp_loss_grad", "pdf_mlp_loss_grad_bf16", "pdf_mlp_adam", "pdf_mlp_column_stats", "pdf_mlp_gather_rows",
            "pdf_mlp_standardize", "pdf_surrogate_rows", "pdf_surrogate_harvest", "pdf_set_surrogate",
            "pdf_surrogate_stats", "pdf_batch_create", "pdf_batch_create_out", "pdf_batch_step", "pdf_batch_sync", "pdf_batch_destroy",
-           "pdf_autotune", "pdf_apply_tuning", "pdf_set_averaging", "pdf_averaging_count", "pdf_get_averages", "pdf_probe",
+           "pdf_autotune", "pdf_apply_tuning", "pdf_measure_fp64_fma_rate", "pdf_set_averaging", "pdf_averaging_count", "pdf_get_averages", "pdf_probe",
            "pdf_set_cdf_probes", "pdf_get_cdf", "pdf_set_wait_limit")
 
 MLP_IN, MLP_HIDDEN, MLP_OUT, MLP_NPARAM, MLP_NNORM = 10, 64, 5, 9349, 30
@@ -136,6 +136,7 @@ def lib(allow_build: bool = True):
         L.pdf_batch_destroy.restype = None
         L.pdf_autotune.argtypes = [vp, C.c_double, C.c_int32, P(pdf_tuning)]
         L.pdf_apply_tuning.argtypes = [vp, P(pdf_tuning)]
+        L.pdf_measure_fp64_fma_rate.argtypes = [vp, d]
         L.pdf_set_averaging.argtypes = [vp, C.c_int32, C.c_int32]
         L.pdf_averaging_count.argtypes = [vp]
         L.pdf_averaging_count.restype = C.c_int64
@@ -199,6 +200,13 @@ def mlp_forward(params, X, n, Y, work, bf16_weights=False, stream=0):
 def mlp_loss_grad(params, X, T, n, work, grad, loss, stream=0):
     _chk(lib().pdf_mlp_loss_grad(_vp(params), _vp(X), _vp(T), n, _vp(work), _vp(grad), _vp(loss), _vp(stream)),
          "pdf_mlp_loss_grad")
+
+
+def measure_fp64_fma_rate(stream=0) -> float:
+    """Measured FP64 FMA rate of the current device in TFLOP/s."""
+    r = C.c_double()
+    _chk(lib().pdf_measure_fp64_fma_rate(_vp(stream), C.byref(r)), "pdf_measure_fp64_fma_rate")
+    return r.value
 
 
 def mlp_loss_grad_bf16(params, X, T, n, work, grad, loss, stream=0):
