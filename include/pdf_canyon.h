@@ -473,7 +473,7 @@ int32_t pdf_surrogate_rows(const pdf_ctx* c);
  * context stream. */
 int pdf_surrogate_harvest(pdf_ctx* c, float* X, float* T);
 
-/* Install (mode 1, 2) or remove (mode 0) the surrogate. Host arrays are copied.
+/* Install (modes 1 to 6) or remove (mode 0) the surrogate. Host arrays are copied.
  *  mode 0  FE solve every step (the paper's method)
  *  mode 1  the network at the nodes proposes wp; its FE residual
  *          r = M f - (M + K_{L^2}) wp is checked on the device in a coarse
@@ -496,6 +496,14 @@ int pdf_surrogate_harvest(pdf_ctx* c, float* X, float* T);
  *          step's solution is the proposal under the same coarse check, so
  *          the FE solve runs only when the statistics have moved its residual
  *          above residual_tol
+ *  mode 6  lagged FE with the network's correction: the proposal is the
+ *          last FE solution plus the change of the network's wp since that
+ *          solve, wp_s + eps y(x) - eps_s y(x_s) (y the network, x the node
+ *          features), under the same coarse check; a failed check runs the
+ *          FE solve, whose solution and network values become the new
+ *          reference. The network's bias, which local features cannot
+ *          remove, cancels in the difference. Needs estimated statistics:
+ *          the current wp and network values are the first reference.
  * Weights are rounded to bfloat16; inference accumulates in FP32. Requires
  * an elliptic-relaxation context (else PDF_ERR_ARG). */
 int pdf_set_surrogate(pdf_ctx* c, int32_t mode, const float* params, const float* norm, double residual_tol);

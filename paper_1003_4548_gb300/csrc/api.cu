@@ -794,7 +794,7 @@ void pdf_destroy(pdf_ctx* c) {
                    c->emean, c->eR, c->epsivar, c->ecm, c->nwt, c->nmean, c->nR, c->nke, c->npsivar, c->eder,
                    c->ngrad, c->npack, c->nwp, c->npackT, c->epackT, c->eaffT, c->ecmT, c->sort_scratch, c->fe_f, c->fe_g,
                    c->fe_prop, c->fe_z, c->fe_part, c->fe_bar, c->fe_iters, c->d_status,
-                   c->conv_buf, c->elist, c->d_step, c->nsurT, c->pwp, c->avg_sum, c->avg_count, c->cdf_elem, c->cdf_hist, c->sur_w, c->sur_rows, c->sur_skip, c->sur_cnt, c->sur_part};
+                   c->conv_buf, c->elist, c->d_step, c->nsurT, c->pwp, c->avg_sum, c->avg_count, c->cdf_elem, c->cdf_hist, c->sur_w, c->sur_rows, c->sur_skip, c->sur_cnt, c->sur_part, c->sur_base, c->sur_snap, c->sur_y};
     for (void* p : dev) cudaFree(p);
     for (int k = 0; k < 7; ++k) {
         cudaFree(c->stA[k]);

@@ -721,6 +721,7 @@ int launch_elliptic(pdf_ctx* c) {
     }
     PDF_CUDA(c, err);
     if (c->coop_done) PDF_CUDA(c, cudaEventRecord(c->coop_done, c->s));
+    TRY_OK(launch_surrogate_rebase(c));
     // the periodic image rows take the canonical rows' solution in the node
     // pack kernel that follows
     ++c->launches;

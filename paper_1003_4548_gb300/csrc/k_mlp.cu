@@ -409,8 +409,14 @@ struct TcSmem {
     uint32_t tmem;
 };
 
+// x = eps y(x) at the free canonical nodes (the Dirichlet values g at the
+// walls); with base and snap (mode 6), x = base + eps y - snap, and eps y is
+// also written to yout
 __global__ void __launch_bounds__(TC_M) k_sur_nodes(SurArgs a, const float* __restrict__ wq,
-                                                    const double* __restrict__ g, double* x, int* status) {
+                                                    const double* __restrict__ g, double* x, int* status,
+                                                    const double* __restrict__ base = nullptr,
+                                                    const double* __restrict__ snap = nullptr,
+                                                    double* yout = nullptr) {
     __shared__ TcSmem S;
     const int t = threadIdx.x, warp = t >> 5;
     mlptc::load(S.W, wq, t, TC_M);
@@ -437,7 +443,13 @@ __global__ void __launch_bounds__(TC_M) k_sur_nodes(SurArgs a, const float* __re
 #pragma unroll
         for (int o = 0; o < OUT; ++o) {
             const double yo = (double)y[o] * S.W.nm[2 * IN + OUT + o] + S.W.nm[2 * IN + o];
-            x[NC * (size_t)i + o] = eps * yo;
+            const size_t q = NC * (size_t)i + o;
+            if (base) {
+                yout[q] = eps * yo;
+                x[q] = base[q] + (eps * yo - snap[q]);
+            } else {
+                x[q] = eps * yo;
+            }
         }
     }
     if (!ok && t == 0) set_status(status, ST_BARRIER);
@@ -659,7 +671,11 @@ int launch_surrogate(pdf_ctx* c) {
     const SurArgs a = sur_args(c);
     // lagged FE mode: the right-hand-side kernel has written the proposal
     // (the previous solution, the Dirichlet values at the walls)
-    if (c->sur_mode != 5) {
+    if (c->sur_mode == 6) {
+        k_sur_nodes<<<(nn + TC_M - 1) / TC_M, TC_M, 0, c->s>>>(a, c->sur_w, c->fe_g, c->fe_prop, c->d_status,
+                                                               c->sur_base, c->sur_snap, c->sur_y);
+        ++c->launches;
+    } else if (c->sur_mode != 5) {
         k_sur_nodes<<<(nn + TC_M - 1) / TC_M, TC_M, 0, c->s>>>(a, c->sur_w, c->fe_g, c->fe_prop, c->d_status);
         ++c->launches;
     }
@@ -680,6 +696,26 @@ int launch_surrogate(pdf_ctx* c) {
         k_sur_featpack<<<(nn + 127) / 128, 128, 0, c->s>>>(a, c->sur_w + PDF_MLP_NPARAM, c->nsurT);
         ++c->launches;
     }
+    PDF_CUDA(c, cudaGetLastError());
+    return PDF_OK;
+}
+
+// mode 6, after the CG: where the check rejected the proposal (the FE solve
+// ran), that solution and this step's network values become the reference
+__global__ void k_sur_rebase(const int* __restrict__ skip, const double* __restrict__ wp, const double* __restrict__ y,
+                             double* base, double* snap, int64_t n) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n || *(volatile const int*)skip != 0) return;
+    base[t] = wp[t];
+    snap[t] = y[t];
+}
+
+int launch_surrogate_rebase(pdf_ctx* c) {
+    if (c->sur_mode != 6) return PDF_OK;
+    const int64_t n = (int64_t)NC * c->m.nn;
+    k_sur_rebase<<<(unsigned)((n + 255) / 256), 256, 0, c->s>>>(c->sur_skip, c->nwp, c->sur_y, c->sur_base,
+                                                                 c->sur_snap, n);
+    ++c->launches;
     PDF_CUDA(c, cudaGetLastError());
     return PDF_OK;
 }
@@ -707,7 +743,8 @@ int pdf_surrogate_harvest(pdf_ctx* c, float* X, float* T) {
 
 int pdf_set_surrogate(pdf_ctx* c, int32_t mode, const float* params, const float* norm, double residual_tol) {
     if (!c) return PDF_ERR_ARG;
-    if (mode < 0 || mode > 5) return fail(c, PDF_ERR_ARG, "surrogate mode must be 0 .. 5");
+    if (mode < 0 || mode > 6) return fail(c, PDF_ERR_ARG, "surrogate mode must be 0 .. 6");
+    if (mode == 6 && !c->stats_valid) return fail(c, PDF_ERR_STATE, "surrogate mode 6: statistics not estimated");
     if ((mode == 3 || mode == 4) && c->prec == 0) return fail(c, PDF_ERR_ARG, "the per-particle surrogate needs an FP32 state");
     if (mode == 0) {
         c->sur_mode = 0;
@@ -741,6 +778,24 @@ int pdf_set_surrogate(pdf_ctx* c, int32_t mode, const float* params, const float
     PDF_CUDA(c, cudaMemset(c->sur_skip, 0, sizeof(int)));
     PDF_CUDA(c, cudaMemset(c->sur_cnt, 0, 2 * sizeof(unsigned long long)));
     PDF_CUDA(c, cudaMemset(c->sur_part, 0, sizeof(double) * ((size_t)sur_blocks(c) * 4 * NC + 3)));
+    if (mode == 6) {
+        // the first reference: the current wp and the network at the current statistics
+        const size_t nb = sizeof(double) * NC * (size_t)c->m.nn;
+        if (!c->sur_base) {
+            PDF_CUDA(c, cudaMalloc((void**)&c->sur_base, nb));
+            PDF_CUDA(c, cudaMalloc((void**)&c->sur_snap, nb));
+            PDF_CUDA(c, cudaMalloc((void**)&c->sur_y, nb));
+        }
+        PDF_CUDA(c, cudaMemcpyAsync(c->sur_base, c->nwp, nb, cudaMemcpyDeviceToDevice, c->s));
+        PDF_CUDA(c, cudaMemsetAsync(c->sur_snap, 0, nb, c->s));
+        PDF_CUDA(c, cudaMemsetAsync(c->sur_y, 0, nb, c->s));
+        const int nn = c->m.nn;
+        k_sur_nodes<<<(nn + TC_M - 1) / TC_M, TC_M, 0, c->s>>>(sur_args(c), c->sur_w, c->fe_g, c->sur_snap,
+                                                               c->d_status);
+        ++c->launches;
+        PDF_CUDA(c, cudaGetLastError());
+        PDF_CUDA(c, cudaStreamSynchronize(c->s));
+    }
     c->sur_mode = mode;
     c->sur_tol = residual_tol;
     return PDF_OK;

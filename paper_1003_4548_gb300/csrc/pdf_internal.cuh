@@ -148,6 +148,9 @@ struct pdf_ctx {
     float* nsurT = nullptr;               // per-particle form: node pack [nn][16] (10 standardised
                                           // features, k, eps, uu, vv, ww, uv)
     float* pwp = nullptr;                 // per-particle form, mode 4: wp of every particle [n][5]
+    double* sur_base = nullptr;           // mode 6: wp of the last FE solve [nn][5] (canonical rows)
+    double* sur_snap = nullptr;           // mode 6: eps y(x) at the last FE solve [nn][5]
+    double* sur_y = nullptr;              // mode 6: eps y(x) of this step [nn][5]
     int64_t pwp_n = 0;
     // time averaging and probes
     int avg_on = 0;
@@ -231,6 +234,7 @@ int particle_occupancy(pdf_ctx* c);
 int prepare_elliptic(pdf_ctx* c, int bs);       // CG rows per block (0: largest co-resident)
 int prepare_moments(pdf_ctx* c);
 int launch_surrogate(pdf_ctx* c);   // network wp at the nodes + FE residual check (before the CG)
+int launch_surrogate_rebase(pdf_ctx* c);  // mode 6: after the CG, a solve's wp and network values become the reference
 int launch_averaging(pdf_ctx* c);   // running sums of the statistics and the CDF probes (when on)
 int surrogate_rows(pdf_ctx* c);     // builds the free canonical row list once
 int launch_to_double(pdf_ctx* c, const void* src, double* dst, int64_t n);

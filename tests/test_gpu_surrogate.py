@@ -377,3 +377,64 @@ def test_lagged_fe_mode(torch, er_case):
             assert res[0] <= 0.05 and np.array_equal(wp[inner], held[inner])
     for g in (a, b, c, d):
         g.close()
+
+
+def test_lagged_fe_with_network_correction(torch, er_case):
+    """Mode 6 proposes the last FE solution plus the network's change since
+    that solve. With tolerance 0 every step solves and the run equals the
+    FE-only run exactly; with an infinite tolerance no step solves, and at
+    every free node wp / eps = (wp_0 - eps_0 y_0) / eps + y (y the bf16
+    network of the oracle on the harvested features, index 0 the reference
+    taken when the mode is set), within the tensor-core inference bar."""
+    from paper_1003_4548_gb300 import capi, surrogate
+    mesh, make = er_case
+    dt = _dt(mesh)
+    g0 = make()
+    g0.seed_particles(32)
+    g0.estimate_stats()
+    rows = g0.surrogate_rows()
+    Xh = torch.empty((rows, 10), dtype=torch.float32, device="cuda")
+    Th = torch.empty((rows, 5), dtype=torch.float32, device="cuda")
+    g0.surrogate_harvest(Xh.data_ptr(), Th.data_ptr())
+    torch.cuda.synchronize()
+    x0, t0 = Xh.cpu().numpy().astype(np.float64), Th.cpu().numpy().astype(np.float64)
+    norm = np.concatenate([x0.mean(0), x0.std(0) + 1e-3, t0.mean(0), t0.std(0) + 1e-6]).astype(np.float32)
+    params = surrogate.init_params(5)
+    g0.close()
+
+    def net(X):  # wp / eps of the network (bf16 operands, as the node inference)
+        Z = (X - norm[:10]) / norm[10:20]
+        return mlp.forward(params, Z, bf16=True, bf16_act=True) * norm[25:30] + norm[20:25]
+
+    a, b, c = make(), make(), make()
+    for g in (a, b, c):
+        g.seed_particles(32)
+        g.estimate_stats()
+    b.set_surrogate(6, params, norm, 0.0)
+    c.set_surrogate(6, params, norm, 1e30)
+    X0 = torch.empty_like(Xh)
+    T0 = torch.empty_like(Th)
+    c.surrogate_harvest(X0.data_ptr(), T0.data_ptr())
+    torch.cuda.synchronize()
+    X0, T0 = X0.cpu().numpy().astype(np.float64), T0.cpu().numpy().astype(np.float64)
+    for g in (a, b, c):
+        g.step(dt, 4)
+        g.sync()
+    assert b.surrogate_stats()[:2] == (4, 4)
+    assert np.array_equal(a.field("node_wp"), b.field("node_wp"))
+    oa, ob = np.argsort(a.field("id")), np.argsort(b.field("id"))
+    for k in ("x", "u", "om", "psi"):
+        assert np.array_equal(a.field(k)[oa], b.field(k)[ob]), k
+    assert c.surrogate_stats()[:2] == (4, 0) and c.cg_iterations == 0
+    Xn = torch.empty_like(Xh)
+    Tn = torch.empty_like(Th)
+    c.surrogate_harvest(Xn.data_ptr(), Tn.data_ptr())
+    torch.cuda.synchronize()
+    Xn, Tn = Xn.cpu().numpy().astype(np.float64), Tn.cpu().numpy().astype(np.float64)
+    e0, en = np.exp(X0[:, 2])[:, None], np.exp(Xn[:, 2])[:, None]  # feature 2 is log eps
+    expect = (T0 - net(X0)) * e0 / en + net(Xn)
+    rel = np.abs(Tn - expect) / (np.abs(expect) + np.sqrt(np.mean(expect * expect, axis=0)))
+    assert np.quantile(rel, 0.99) < 3e-3 and rel.max() < 5e-2, (np.quantile(rel, 0.99), rel.max())
+    assert np.max(np.abs(Tn - T0)) > 0  # the correction moved wp
+    for g in (a, b, c):
+        g.close()
