@@ -43,8 +43,9 @@ def args_():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-surrogate", action="store_true", help="FE solve every step in the timed form")
-    ap.add_argument("--chosen", default="lagged", choices=["lagged", "surrogate"],
-                    help="wp of the timed form: lagged FE under the coarse residual check, or the trained network")
+    ap.add_argument("--chosen", default="lagged", choices=["lagged", "corrected", "surrogate"],
+                    help="wp of the timed form: lagged FE under the coarse residual check, the lagged FE plus the "
+                         "trained network's change since the last solve, or the trained network alone")
     ap.add_argument("--lag-tol", type=float, default=0.05,
                     help="coarse residual above which the lagged form solves the FE problem again")
     ap.add_argument("--no-forms", action="store_true", help="skip the plain forms and the precision study")
@@ -717,7 +718,7 @@ def main():
     # --lag-tol) or the trained network under the same check. The network is
     # trained whenever it is timed or measured beside the chosen form.
     er = cfg["wall_model"] == "er" and not a.no_surrogate
-    use_net = er and (a.chosen == "surrogate" or not a.no_forms)
+    use_net = er and (a.chosen in ("surrogate", "corrected") or not a.no_forms)
     sur, sur_info = None, None
     if use_net and a.load_surrogate:
         z = np.load(a.load_surrogate)
@@ -730,12 +731,15 @@ def main():
     if sur is not None and a.save_surrogate:
         np.savez(a.save_surrogate, params=sur["params"], norm=sur["norm"], tol=sur["tol"])
     lagged = {"mode": 5, "params": None, "norm": None, "tol": a.lag_tol}
-    chosen_wp = (sur if a.chosen == "surrogate" else lagged) if er else None
+    corrected = dict(sur, mode=6, tol=a.lag_tol) if sur is not None else None
+    chosen_wp = ({"surrogate": sur, "corrected": corrected}.get(a.chosen, lagged)) if er else None
     prec = cfg["precision"]
     red = {"fp64": "FP64", "fp32": "FP64-exact", "fp32_kahan": "compensated FP32"}[prec]
     form_name = f"{prec} particle state, {red} statistics, " + (
         "FE solve every step" if chosen_wp is None else
         "surrogate wp with the FE solve as checked fallback" if chosen_wp is sur else
+        (f"lagged FE solve plus the trained network's change since the last solve, kept while its coarse FE "
+         f"residual stays below {a.lag_tol}") if chosen_wp is corrected else
         f"lagged FE solve: the previous wp kept while its coarse FE residual stays below {a.lag_tol}")
     # each rank runs its own canyon case (independent problems, no exchange)
     extra = {"pressure": 1} if a.pressure else {}
@@ -839,16 +843,25 @@ def main():
     # recipe's 500 steps): the per-element counts spread and the flow leaves
     # the early transient, so the rate and the surrogate's fallbacks over the
     # full run are stated beside the 100-step window above
-    sustained = None
-    if not a.no_forms and rank == 0 and chosen_wp is not None:
-        f = Form(cfg, mesh, stream, precision=prec, sur=chosen_wp, **extra)
+    def sustained_run(wp):
+        f = Form(cfg, mesh, stream, precision=prec, sur=wp, **extra)
         s0 = f.g.surrogate_stats()
         rr = f.timed(dt, 500, 0)
         s1 = f.g.surrogate_stats()
-        sustained = {"steps": 500, "value": f.g.num_particles * 500 / (rr["ms"] / 1e3), "ms_per_step": rr["ms"] / 500,
-                     "checked_steps": s1[0] - s0[0], "fe_solves": s1[1] - s0[1],
-                     "kernels_ms_per_step": {q: v[0] / 500 for q, v in rr["kt"].items()}}
+        out = {"steps": 500, "value": f.g.num_particles * 500 / (rr["ms"] / 1e3), "ms_per_step": rr["ms"] / 500,
+               "checked_steps": s1[0] - s0[0], "fe_solves": s1[1] - s0[1],
+               "kernels_ms_per_step": {q: v[0] / 500 for q, v in rr["kt"].items()}}
         f.close()
+        return out
+
+    sustained = None
+    sustained_other = {}
+    if not a.no_forms and rank == 0 and chosen_wp is not None:
+        sustained = sustained_run(chosen_wp)
+        # the other checked forms over the same 500 steps: FE solves and rate
+        for nm, wp in (("lagged_fe", lagged), ("lagged_fe_with_network_correction", corrected)):
+            if wp is not None and wp is not chosen_wp:
+                sustained_other[nm] = sustained_run(wp)
 
     # the plain forms on the same workload (fewer steps), and the stated error
     forms = {}
@@ -906,6 +919,8 @@ def main():
             "cg_iterations_last": r["cg_iterations_last"], "surrogate": sur_info}
     if sustained:
         line["sustained_production_run"] = sustained
+        if sustained_other:
+            line["sustained_other_forms"] = sustained_other
     if workloads:
         line["workloads"] = workloads
     if forms:
@@ -1006,6 +1021,8 @@ def standard_error_study(cfg, mesh, dt, stream, sur, lag_tol=0.05, seeds=8, chec
              ("fp32_kahan_fe", "fp32_kahan", None, 3000)]
     if sur is not None:
         forms.append(("fp32_kahan_surrogate_node_form", "fp32_kahan", sur, 4000))
+        forms.append(("fp32_kahan_lagged_fe_with_network_correction", "fp32_kahan",
+                      dict(sur, mode=6, tol=lag_tol), 5000))
     t0 = time.perf_counter()
     cells = {}
     for name, prec, s, base in forms:

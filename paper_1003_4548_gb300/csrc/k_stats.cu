@@ -1806,10 +1806,17 @@ __device__ __forceinline__ void med_bins_element(const MomArgs<float>& a, int e,
 // shared memory per 4-warp block. The grid may hold fewer blocks than
 // element groups (the warps then stride over them), leaving SM room for the
 // field chain that runs beside it.
-__global__ void __launch_bounds__(32 * WARPS_PER_BLOCK, 6) k_bins_med(const MomArgs<float> a, int nt) {
+__global__ void __launch_bounds__(32 * WARPS_PER_BLOCK, 6) k_bins_med(const MomArgs<float> a, int nt,
+                                                                       int* next) {
     __shared__ MedUnion sm[WARPS_PER_BLOCK];
     const int lane = threadIdx.x & 31, wq = threadIdx.x >> 5;
-    for (int e = blockIdx.x * WARPS_PER_BLOCK + wq; e < nt; e += gridDim.x * WARPS_PER_BLOCK) {
+    // each warp takes the next element from a counter (zeroed before the
+    // launch), so warps that drew large elements do not set the kernel's end
+    for (;;) {
+        int e = 0;
+        if (lane == 0) e = atomicAdd(next, 1);
+        e = __shfl_sync(FULLW, e, 0);
+        if (e >= nt) break;
         med_bins_element(a, e, lane, sm[wq]);
         __syncwarp();  // the warp's shared memory is free for its next element
     }
@@ -1876,7 +1883,7 @@ int run(pdf_ctx* c) {
             // run) run concurrently on the context stream and fill the SMs the
             // warp kernel's last waves leave
             a.min_n = 4096;
-            a.lcnt = c->elist;  // [0], [1]: list lengths; [2]: next element of listA to take
+            a.lcnt = c->elist;  // [0], [1]: list lengths; [2]: next element of listA to take; [3]: of the bins
             a.listA = c->elist + 4;
             a.listB = c->elist + 4 + c->m.nt;
             // side stream: the moments of the elements of at most 512
@@ -1901,7 +1908,8 @@ int run(pdf_ctx* c) {
             PDF_CUDA(c, cudaStreamWaitEvent(c->s3, c->side_fork, 0));
             timing_begin(c, PDF_K_BINS, c->s3);
             const unsigned bgrid = c->bins_bps > 0 ? std::min(blocks, (unsigned)(c->bins_bps * c->num_sms)) : blocks;
-            k_bins_med<<<bgrid, 32 * WARPS_PER_BLOCK, 0, c->s3>>>(a, c->m.nt);
+            PDF_CUDA(c, cudaMemsetAsync(a.lcnt + 3, 0, sizeof(int), c->s3));
+            k_bins_med<<<bgrid, 32 * WARPS_PER_BLOCK, 0, c->s3>>>(a, c->m.nt, a.lcnt + 3);
             timing_end(c, PDF_K_BINS, c->s3);
             PDF_CUDA(c, cudaEventRecord(c->bins_join, c->s3));
             c->bins_pending = true;
