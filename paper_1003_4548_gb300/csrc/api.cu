@@ -359,7 +359,7 @@ int alloc_stats(pdf_ctx* c) {
     TRY(dalloc(c, &c->eR, 6 * (size_t)nt));
     TRY(dalloc(c, &c->epsivar, nt));
     TRY(dalloc(c, &c->ecm, (size_t)B * nt));
-    TRY(dalloc(c, &c->elist, 4 + 2 * (size_t)nt));  // 4 counters, then the two lists
+    TRY(dalloc(c, &c->elist, 8 + 2 * (size_t)nt));  // 8 counters, then the two lists
     TRY(dalloc(c, &c->nwt, nn));
     TRY(dalloc(c, &c->nmean, 4 * (size_t)nn));
     TRY(dalloc(c, &c->nR, 6 * (size_t)nn));

@@ -141,8 +141,9 @@ struct MomArgs {
     int* status;
     int min_n;  // the block kernel only takes elements with more particles than this
     // FP32 median path: elements too crowded for a warp, listed by k_crowded
-    // (lcnt[0]: 512 < n <= 4096 in listA, lcnt[1]: n > 4096 in listB; lcnt[2]:
-    // the next listA entry a block of k_moments_sel_big takes)
+    // (lcnt[0]: 512 < n <= 4096 in listA, lcnt[1]: n > 4096 in listB; lcnt[2],
+    // lcnt[4]: the next listA entry a block of k_moments_sel_big takes for its
+    // moments, for its bins; lcnt[3]: the next element of the warp bins kernel)
     int* lcnt;
     int* listA;
     int* listB;
@@ -1836,19 +1837,20 @@ __global__ void k_crowded(const int* __restrict__ off, int nt, int* lcnt, int* l
 // block of 256 threads per element: 512 < n <= 4096 (crowded elements). The
 // blocks take the listed elements from a shared counter (lcnt[2]), so a block
 // that drew large elements does not hold up the others.
-template <bool KAHAN>
+template <bool KAHAN, int PART>
 __global__ void __launch_bounds__(256) k_moments_sel_big(const MomArgs<float> a) {
     __shared__ SelSmem<4096> sm;
     __shared__ int jnext;
     const int cnt = a.lcnt[0];
+    int* next = PART == SEL_BINS ? &a.lcnt[4] : &a.lcnt[2];
     for (;;) {
-        if (threadIdx.x == 0) jnext = atomicAdd(&a.lcnt[2], 1);
+        if (threadIdx.x == 0) jnext = atomicAdd(next, 1);
         __syncthreads();
         const int j = jnext;
         if (j >= cnt) break;
         const int e = a.listA[j];
         const int s0 = a.off[e], n = a.off[e + 1] - s0;
-        sel_element<KAHAN, 256, 4096>(a, e, s0, n, sm);
+        sel_element<KAHAN, 256, 4096, PART>(a, e, s0, n, sm);
         __syncthreads();  // the element's shared memory and jnext are free again
     }
 }
@@ -1883,24 +1885,29 @@ int run(pdf_ctx* c) {
             // run) run concurrently on the context stream and fill the SMs the
             // warp kernel's last waves leave
             a.min_n = 4096;
-            a.lcnt = c->elist;  // [0], [1]: list lengths; [2]: next element of listA to take; [3]: of the bins
-            a.listA = c->elist + 4;
-            a.listB = c->elist + 4 + c->m.nt;
+            // [0], [1]: list lengths; [2]: next element of listA for its moments,
+            // [4] for its bins; [3]: next element of the warp bins kernel
+            a.lcnt = c->elist;
+            a.listA = c->elist + 8;
+            a.listB = c->elist + 8 + c->m.nt;
             // side stream: the moments of the elements of at most 512
-            // particles; the context stream: the crowded elements, moments and
-            // bins together. Then the bins of the warp elements, which only
-            // the next particle step reads, go to a third stream beside the
-            // field chain of the context stream (pdf_step and
-            // pdf_estimate_stats join it back). The bins start after every
-            // moment kernel: started earlier, their blocks fill the SMs and the
-            // crowded-element blocks (larger shared memory) wait for them all.
+            // particles; the context stream: the moments of the crowded
+            // elements (the block kernel above 4096 particles takes moments
+            // and bins together). Then the bins, which only the next particle
+            // step reads, go to a third stream beside the field chain of the
+            // context stream (pdf_step and pdf_estimate_stats join it back):
+            // the warp elements', then the crowded elements'. The bins start
+            // after every moment kernel: started earlier, their blocks fill
+            // the SMs and the crowded-element blocks (larger shared memory)
+            // wait for them all.
             PDF_CUDA(c, cudaEventRecord(c->side_fork, c->s));
             PDF_CUDA(c, cudaStreamWaitEvent(c->s2, c->side_fork, 0));
             k_moments_w<KAHAN><<<blocks, 32 * WARPS_PER_BLOCK, 0, c->s2>>>(a, c->m.nt);
             PDF_CUDA(c, cudaEventRecord(c->side_join, c->s2));
-            PDF_CUDA(c, cudaMemsetAsync(a.lcnt, 0, 3 * sizeof(int), c->s));
+            PDF_CUDA(c, cudaMemsetAsync(a.lcnt, 0, 8 * sizeof(int), c->s));
             k_crowded<<<(c->m.nt + 255) / 256, 256, 0, c->s>>>(c->off, c->m.nt, a.lcnt, a.listA, a.listB);
-            k_moments_sel_big<KAHAN><<<std::min(c->m.nt, 3 * c->num_sms), 256, 0, c->s>>>(a);
+            const int big = std::min(c->m.nt, 3 * c->num_sms);
+            k_moments_sel_big<KAHAN, SEL_MOMENTS><<<big, 256, 0, c->s>>>(a);
             const size_t smem = sizeof(SortKey) * STATS_CAP;
             k_moments<T, KAHAN><<<(unsigned)std::min(c->m.nt, c->num_sms), STATS_THREADS, smem, c->s>>>(a);
             PDF_CUDA(c, cudaStreamWaitEvent(c->s, c->side_join, 0));
@@ -1908,12 +1915,12 @@ int run(pdf_ctx* c) {
             PDF_CUDA(c, cudaStreamWaitEvent(c->s3, c->side_fork, 0));
             timing_begin(c, PDF_K_BINS, c->s3);
             const unsigned bgrid = c->bins_bps > 0 ? std::min(blocks, (unsigned)(c->bins_bps * c->num_sms)) : blocks;
-            PDF_CUDA(c, cudaMemsetAsync(a.lcnt + 3, 0, sizeof(int), c->s3));
             k_bins_med<<<bgrid, 32 * WARPS_PER_BLOCK, 0, c->s3>>>(a, c->m.nt, a.lcnt + 3);
+            k_moments_sel_big<KAHAN, SEL_BINS><<<big, 256, 0, c->s3>>>(a);
             timing_end(c, PDF_K_BINS, c->s3);
             PDF_CUDA(c, cudaEventRecord(c->bins_join, c->s3));
             c->bins_pending = true;
-            c->launches += 5;
+            c->launches += 6;
             PDF_CUDA(c, cudaGetLastError());
             return PDF_OK;
         } else {
