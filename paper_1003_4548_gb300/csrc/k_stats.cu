@@ -1204,14 +1204,12 @@ __device__ __forceinline__ void med_binadd(MedSmem& S, int bn, unsigned long lon
     atomicAdd(&S.binpart[bn][2], (unsigned)(v >> 38));
 }
 
+// psi (clamped to [0, 1]) in fixed point, unit 2^-54, truncated: the scaling
+// by 2^54 is exact in FP32 (no overflow; subnormal inputs become normal) and
+// the conversion truncates toward zero, as a right shift of the mantissa would
 __device__ __forceinline__ unsigned long long psi_fixed(float p) {
-    constexpr int UNIT = 54;  // psi in [0, 1] and n <= 512 keep the bin sums below 2^63
-    unsigned m;
-    int ex;
-    bool neg;
-    f32_parts(fminf(fmaxf(p, 0.f), 1.f), m, ex, neg);
-    const int sh = ex - 150 + UNIT;
-    return sh >= 0 ? ((unsigned long long)m << sh) : (-sh < 64 ? ((unsigned long long)m >> (-sh)) : 0ull);
+    constexpr float SCALE = 18014398509481984.0f;  // 2^54: psi in [0, 1] and n <= 512 keep the bin sums below 2^63
+    return __float2ull_rz(fminf(fmaxf(p, 0.f), 1.f) * SCALE);
 }
 
 // bucket of each group's median: NG groups, 32/NG lanes scan one group's
