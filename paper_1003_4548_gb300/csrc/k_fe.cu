@@ -676,9 +676,6 @@ int launch_elliptic(pdf_ctx* c) {
     a.xprop = c->fe_prop;
     cudaError_t err;
     const bool ffv = c->p.cg_precision == 1;
-    // cooperative grids of different contexts never run side by side (a
-    // batch orders them in a chain)
-    if (c->coop_wait) PDF_CUDA(c, cudaStreamWaitEvent(c->s, c->coop_wait, 0));
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     cudaGraph_t graph = nullptr;
     if (c->sur_mode) PDF_CUDA(c, cudaStreamGetCaptureInfo(c->s, &cs, nullptr, &graph, nullptr, nullptr, nullptr));
@@ -695,6 +692,10 @@ int launch_elliptic(pdf_ctx* c) {
                                                                     c->fe_iters, nn);
         ++c->launches;
         PDF_CUDA(c, cudaGetLastError());
+        // cooperative grids of different contexts never run side by side (a
+        // batch orders them in a chain): the chain joins the conditional node
+        // only, so the gate and what precedes it do not wait for it
+        if (c->coop_wait) PDF_CUDA(c, cudaStreamWaitEvent(c->s, c->coop_wait, 0));
         const cudaGraphNode_t* deps = nullptr;
         size_t nd = 0;
         PDF_CUDA(c, cudaStreamGetCaptureInfo(c->s, &cs, nullptr, &graph, &deps, nullptr, &nd));
@@ -709,6 +710,10 @@ int launch_elliptic(pdf_ctx* c) {
         PDF_CUDA(c, cudaStreamBeginCaptureToGraph(c->s_cond, np.conditional.phGraph_out[0], nullptr, nullptr, 0,
                                                   cudaStreamCaptureModeRelaxed));
         cg_stream = c->s_cond;
+    } else if (c->coop_wait) {
+        // cooperative grids of different contexts never run side by side (a
+        // batch orders them in a chain)
+        PDF_CUDA(c, cudaStreamWaitEvent(c->s, c->coop_wait, 0));
     }
     if (c->fe_bs == 128) err = launch_pcg<128>(a, c->fe_blocks, cg_stream, ffv);
     else if (c->fe_bs == 160) err = launch_pcg<160>(a, c->fe_blocks, cg_stream, ffv);
