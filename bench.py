@@ -163,6 +163,36 @@ def kernel_source_hash(kernel: str = "k_step") -> str:
     return h.hexdigest()[:12]
 
 
+def profiled_instructions(kernel: str, workload: str, precision: str):
+    """Warp instructions of one launch of a kernel (smsp__inst_executed.sum
+    from the committed ncu summary), if taken on the current source."""
+    path = os.path.join(ROOT, "profiles", "kernel_traffic.json")
+    try:
+        with open(path) as f:
+            e = json.load(f)[f"{kernel}:{workload}:{precision}"]
+        if e.get("source_hash") != kernel_source_hash(kernel):
+            return None
+        return float(e["warp_instructions_per_launch"])
+    except Exception:
+        return None
+
+
+def issue_roofline(kernel, ms_per_launch, workload, precision, sm_mhz):
+    """A kernel bound by instruction issue rather than by HBM: its warp
+    instructions per launch over its event time, against the issue rate of
+    one warp instruction per cycle per SM sub-partition (4 per SM) at the SM
+    clock seen in the timed region."""
+    w = profiled_instructions(kernel, workload, precision)
+    if not w or not sm_mhz or not ms_per_launch:
+        return None
+    import torch
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    peak = sms * 4 * sm_mhz * 1e6
+    got = w / (ms_per_launch / 1e3)
+    return {"bound": "issue", "warp_instructions_per_launch": w, "achieved_per_s": got, "peak_per_s": peak,
+            "frac": got / peak, "peak_source": f"{sms} SMs x 4 schedulers x {sm_mhz:.0f} MHz"}
+
+
 def profiled_traffic(kernel: str, workload: str, precision: str):
     """DRAM bytes per particle of a kernel from the committed ncu summary, if
     it was taken on the current source of that kernel."""
@@ -905,6 +935,18 @@ def main():
     if not a.no_forms and rank == 0 and world == 1:
         workloads["canyon_wf_small"] = small_case_summary(stream)
         workloads["canyon_batch32"] = batch_summary(a)
+    # the instruction-issue roofline of the kernels that issue rather than
+    # stream bound (their HBM fraction alone reads low)
+    sm_mhz = (rg["clocks"] or {}).get("sm_mhz")
+    for k, r in rooflines.items():
+        if k in KTRAFFIC and r.get("ms_per_launch"):
+            iss = issue_roofline(KTRAFFIC[k], r["ms_per_launch"], a.workload, prec, sm_mhz)
+            if iss:
+                r["issue"] = iss
+    if roof.get("ms_per_launch") and dominant in KTRAFFIC:
+        iss = issue_roofline(KTRAFFIC[dominant], roof["ms_per_launch"], a.workload, prec, sm_mhz)
+        if iss:
+            roof["issue"] = iss
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps_timed,
             "warmup": a.warmup, "ms_per_step": ms / steps_timed, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32" if prec != "fp64" else "f64",
