@@ -806,6 +806,7 @@ void pdf_destroy(pdf_ctx* c) {
     if (c->side_join2) cudaEventDestroy(c->side_join2);
     if (c->s2) cudaStreamDestroy(c->s2);
     if (c->bins_join) cudaEventDestroy(c->bins_join);
+    if (c->crowd_done) cudaEventDestroy(c->crowd_done);
     if (c->s3) cudaStreamDestroy(c->s3);
     if (c->s_cond) cudaStreamDestroy(c->s_cond);
     delete c;

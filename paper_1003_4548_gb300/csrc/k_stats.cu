@@ -16,12 +16,13 @@
 // FP32 particle state with 2 x 2 x 2 bins, the production path, for elements
 // of at most 512 particles: one warp per element computes the moments
 // (k_moments_w: exact fixed-point sums for FP32, compensated FP32 sums for
-// FP32 + Kahan) on a high-priority side stream; then, on a third stream, one
-// warp per element (k_bins_med) keeps the segment in registers and shared
-// memory and finds each split's median from a 256-bucket histogram plus an
-// exact rank of the few keys in the median's bucket, one pass over the keys
-// per level (no sort). Only the next particle step reads the bins, so they
-// run beside the field chain, which needs the moments alone. Crowded
+// FP32 + Kahan) on a high-priority side stream; beside it, on a third
+// stream, one warp per element (k_bins_med) keeps the segment in registers
+// and shared memory and finds each split's median from a 256-bucket
+// histogram (over the element's own value range) plus an exact rank of the
+// few keys in the median's bucket, one pass over the keys per level (no
+// sort). Only the next particle step reads the bins, so they run beside the
+// moments and the field chain, which needs the moments alone. Crowded
 // elements (more than 512 particles, listed by k_crowded) go to 256-thread
 // teams, and elements above 4096 to the block kernel above, moments and bins
 // together on the context stream. Other bin shapes take the warp bitonic
@@ -998,6 +999,7 @@ __device__ __forceinline__ void kahan_moments(const MomArgs<float>& a, int e, in
 // the element means and variances (bucket ranges, the mean psi of an element
 // with fewer particles than bins) from a moments launch that ran before.
 constexpr int SEL_MOMENTS = 1, SEL_BINS = 2, SEL_ALL = 3;
+constexpr int SEL_RANGES_GIVEN = 4;  // with SEL_BINS: S.mean[0..2], S.rd[0..2] already hold the bucket ranges
 template <bool KAHAN, int NT, int NMAX, int PART = SEL_ALL>
 __device__ void sel_element(const MomArgs<float>& a, int e, int s0, int n, SelSmem<NMAX>& S) {
     const Team<NT> T;
@@ -1006,7 +1008,7 @@ __device__ void sel_element(const MomArgs<float>& a, int e, int s0, int n, SelSm
     if constexpr ((PART & SEL_MOMENTS) != 0) {
         if constexpr (KAHAN) kahan_moments<NT>(a, e, s0, n, S);
         else exact_moments<NT>(a, e, s0, n, S);
-    } else {
+    } else if constexpr ((PART & SEL_RANGES_GIVEN) == 0) {
         if (T.tid < 5) S.mean[T.tid] = a.emean[5 * e + T.tid];
         else if (T.tid < 8) S.rd[T.tid - 5] = a.eR[6 * e + T.tid - 5];
         T.sync();
@@ -1479,6 +1481,29 @@ __device__ __forceinline__ void med_buckets(const MomArgs<float>& a, int e, Buck
     }
 }
 
+// the bucket map of one split level from the element's value range
+// [lo, hi] (256 equal buckets; any monotone map keeps the selection exact)
+__device__ __forceinline__ Buckets range_buckets(float lo, float hi) {
+    Buckets b;
+    b.top = 255;
+    b.lo = lo;
+    const float w = hi - lo;
+    const float sc = w > 0.f ? 256.f / w : 0.f;
+    b.sc = (sc > 0.f && sc < 1e30f) ? sc : 0.f;
+    return b;
+}
+
+__device__ __forceinline__ float warp_min(float x) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x = fminf(x, __shfl_xor_sync(0xffffffffu, x, o));
+    return x;
+}
+__device__ __forceinline__ float warp_max(float x) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x = fmaxf(x, __shfl_xor_sync(0xffffffffu, x, o));
+    return x;
+}
+
 // append a key to the candidate list (a few keys per level; S.ncl counts them)
 __device__ __forceinline__ void med_append(MedSmem& S, uint32_t key, int q, int g, int b, float ps) {
     const int slot = atomicAdd(&S.ncl, 1);
@@ -1493,8 +1518,19 @@ __device__ __forceinline__ void med_append(MedSmem& S, uint32_t key, int q, int 
 
 // the general selection path for an element whose boundary buckets are
 // crowded (bins only: the moments are in memory)
-__device__ __noinline__ void med_general(const MomArgs<float>& a, int e, int s0, int n, SelSmem<512>& S) {
-    sel_element<true, 32, 512, SEL_BINS>(a, e, s0, n, S);
+__device__ __noinline__ void med_general(const MomArgs<float>& a, int e, int s0, int n, SelSmem<512>& S,
+                                         float lo0, float hi0, float lo1, float hi1, float lo2, float hi2) {
+    // bucket ranges [lo, hi] written as mean +- 4 sd, the form sel_element reads
+    if (threadIdx.x % 32 == 0) {
+        const float lo[3] = {lo0, lo1, lo2}, hi[3] = {hi0, hi1, hi2};
+        for (int d = 0; d < 3; ++d) {
+            const double sd = ((double)hi[d] - (double)lo[d]) * 0.125;
+            S.mean[d] = 0.5 * ((double)hi[d] + (double)lo[d]);
+            S.rd[d] = sd * sd;
+        }
+    }
+    __syncwarp();
+    sel_element<true, 32, 512, SEL_BINS | SEL_RANGES_GIVEN>(a, e, s0, n, S);
 }
 
 __device__ __forceinline__ int upbit(const MedSmem& S, int q) { return (int)((S.upb[q >> 5] >> (q & 31)) & 1u); }
@@ -1602,8 +1638,11 @@ static_assert(sizeof(MedUnion) % 16 == 0, "per-warp slices keep hist 16-byte ali
 __device__ __forceinline__ void med_bins_element(const MomArgs<float>& a, int e, int lane, MedUnion& U) {
     const int s0 = a.off[e], n = a.off[e + 1] - s0;
     if (n > 512) return;  // a block kernel takes it (listed by k_crowded)
-    if (n < 8) {  // no particles: <phi|V> = 0; fewer particles than bins: the element mean (IEM)
-        const double mean_psi = n == 0 ? 0.0 : a.emean[5 * e + 3];
+    if (n < 8) {  // no particles: <phi|V> = 0; fewer particles than bins: the element mean psi (IEM)
+        double p = lane < n ? (double)a.psi[s0 + lane] : 0.0;
+#pragma unroll
+        for (int o = 4; o > 0; o >>= 1) p += __shfl_xor_sync(FULLW, p, o);  // lanes 0..7, a fixed order
+        const double mean_psi = n == 0 ? 0.0 : p / n;
         if (lane < n) a.bin[s0 + lane] = 0;
         if (lane < 8) {
             a.ecm[(size_t)8 * e + lane] = mean_psi;
@@ -1640,8 +1679,33 @@ __device__ __forceinline__ void med_bins_element(const MomArgs<float>& a, int e,
             S.ou[h][lane] = tu[h]; S.ov[h][lane] = tv[h]; S.ow[h][lane] = tw[h]; S.op[h][lane] = tp[h];
         }
     }
+    // the bucket ranges: the element's own minimum and maximum of u, v, w (the
+    // bins need no moments, so they run beside the moments kernel)
+    float rl[3] = {3.4e38f, 3.4e38f, 3.4e38f}, rh[3] = {-3.4e38f, -3.4e38f, -3.4e38f};
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        if (j < kk && lane + 32 * j < n) {
+            rl[0] = fminf(rl[0], xu[j]); rh[0] = fmaxf(rh[0], xu[j]);
+            rl[1] = fminf(rl[1], xv[j]); rh[1] = fmaxf(rh[1], xv[j]);
+            rl[2] = fminf(rl[2], xw[j]); rh[2] = fmaxf(rh[2], xw[j]);
+        }
+    }
+    if (kk > 8) {
+        for (int h = 0; h < 8; ++h) {
+            if (8 + h < kk && lane + 32 * (8 + h) < n) {
+                rl[0] = fminf(rl[0], S.ou[h][lane]); rh[0] = fmaxf(rh[0], S.ou[h][lane]);
+                rl[1] = fminf(rl[1], S.ov[h][lane]); rh[1] = fmaxf(rh[1], S.ov[h][lane]);
+                rl[2] = fminf(rl[2], S.ow[h][lane]); rh[2] = fmaxf(rh[2], S.ow[h][lane]);
+            }
+        }
+    }
     Buckets bk[3];
-    med_buckets(a, e, bk);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        rl[d] = warp_min(rl[d]);
+        rh[d] = warp_max(rh[d]);
+        bk[d] = range_buckets(rl[d], rh[d]);
+    }
     unsigned pb0 = 0u, pb1 = 0u;  // bucket of register key j at the current level (a byte each)
     // The passes over the register keys are branch-free (the key slot and the
     // segment bound predicate the stores and atomics), so the eight keys of a
@@ -1751,7 +1815,7 @@ __device__ __forceinline__ void med_bins_element(const MomArgs<float>& a, int e,
     }
     if (general) {  // crowded boundary buckets: the general selection path
         __syncwarp();
-        med_general(a, e, s0, n, U.s);
+        med_general(a, e, s0, n, U.s, rl[0], rh[0], rl[1], rh[1], rl[2], rh[2]);
         return;
     }
     // ---- bins: the W halves; psi summed per bin
@@ -1800,11 +1864,14 @@ __device__ __forceinline__ void med_bins_element(const MomArgs<float>& a, int e,
 }
 
 // 2 x 2 x 2 bins and <phi|V> of the elements of at most 512 particles, one
-// warp per element, after their moments (bucket ranges and the element mean
-// psi come from memory). Six blocks per SM at most: 80 registers and 36 KB of
-// shared memory per 4-warp block. The grid may hold fewer blocks than
-// element groups (the warps then stride over them), leaving SM room for the
-// field chain that runs beside it.
+// warp per element, independent of the moments (bucket ranges from the
+// element's own value range, the mean psi of an element with fewer
+// particles than bins from its particles). Six blocks per SM at most: 80
+// registers (a few spilled: at 96, without spills, the kernel took more of
+// the SM from the moments beside it and the step was no faster) and 36 KB of
+// shared memory per 4-warp block. The grid may hold
+// fewer blocks than element groups (the warps then take elements from the
+// counter), leaving SM room for the kernels that run beside it.
 __global__ void __launch_bounds__(32 * WARPS_PER_BLOCK, 6) k_bins_med(const MomArgs<float> a, int nt,
                                                                        int* next) {
     __shared__ MedUnion sm[WARPS_PER_BLOCK];
@@ -1888,36 +1955,38 @@ int run(pdf_ctx* c) {
             a.lcnt = c->elist;
             a.listA = c->elist + 8;
             a.listB = c->elist + 8 + c->m.nt;
-            // side stream: the moments of the elements of at most 512
-            // particles; the context stream: the moments of the crowded
-            // elements (the block kernel above 4096 particles takes moments
-            // and bins together). Then the bins, which only the next particle
-            // step reads, go to a third stream beside the field chain of the
-            // context stream (pdf_step and pdf_estimate_stats join it back):
-            // the warp elements', then the crowded elements'. The bins start
-            // after every moment kernel: started earlier, their blocks fill
-            // the SMs and the crowded-element blocks (larger shared memory)
-            // wait for them all.
+            // Three streams from the sorted state on: the side stream takes the
+            // moments of the elements of at most 512 particles, the bins
+            // stream their bins (which need no moments: the bucket ranges are
+            // each element's own value range, and only the next particle step
+            // reads the bins), the context stream the crowded elements'
+            // moments (the block kernel above 4096 particles takes moments and
+            // bins together) and then the field chain, which waits for the
+            // moments only. The crowded elements' bins follow the warp bins
+            // on the bins stream, after the crowded moments (their bucket
+            // ranges). pdf_step and pdf_estimate_stats join the bins stream
+            // back before the step ends.
+            PDF_CUDA(c, cudaMemsetAsync(a.lcnt, 0, 8 * sizeof(int), c->s));
             PDF_CUDA(c, cudaEventRecord(c->side_fork, c->s));
             PDF_CUDA(c, cudaStreamWaitEvent(c->s2, c->side_fork, 0));
+            PDF_CUDA(c, cudaStreamWaitEvent(c->s3, c->side_fork, 0));
             k_moments_w<KAHAN><<<blocks, 32 * WARPS_PER_BLOCK, 0, c->s2>>>(a, c->m.nt);
             PDF_CUDA(c, cudaEventRecord(c->side_join, c->s2));
-            PDF_CUDA(c, cudaMemsetAsync(a.lcnt, 0, 8 * sizeof(int), c->s));
+            timing_begin(c, PDF_K_BINS, c->s3);
+            const unsigned bgrid = c->bins_bps > 0 ? std::min(blocks, (unsigned)(c->bins_bps * c->num_sms)) : blocks;
+            k_bins_med<<<bgrid, 32 * WARPS_PER_BLOCK, 0, c->s3>>>(a, c->m.nt, a.lcnt + 3);
             k_crowded<<<(c->m.nt + 255) / 256, 256, 0, c->s>>>(c->off, c->m.nt, a.lcnt, a.listA, a.listB);
             const int big = std::min(c->m.nt, 3 * c->num_sms);
             k_moments_sel_big<KAHAN, SEL_MOMENTS><<<big, 256, 0, c->s>>>(a);
             const size_t smem = sizeof(SortKey) * STATS_CAP;
             k_moments<T, KAHAN><<<(unsigned)std::min(c->m.nt, c->num_sms), STATS_THREADS, smem, c->s>>>(a);
-            PDF_CUDA(c, cudaStreamWaitEvent(c->s, c->side_join, 0));
-            PDF_CUDA(c, cudaEventRecord(c->side_fork, c->s));
-            PDF_CUDA(c, cudaStreamWaitEvent(c->s3, c->side_fork, 0));
-            timing_begin(c, PDF_K_BINS, c->s3);
-            const unsigned bgrid = c->bins_bps > 0 ? std::min(blocks, (unsigned)(c->bins_bps * c->num_sms)) : blocks;
-            k_bins_med<<<bgrid, 32 * WARPS_PER_BLOCK, 0, c->s3>>>(a, c->m.nt, a.lcnt + 3);
+            PDF_CUDA(c, cudaEventRecord(c->crowd_done, c->s));
+            PDF_CUDA(c, cudaStreamWaitEvent(c->s3, c->crowd_done, 0));
             k_moments_sel_big<KAHAN, SEL_BINS><<<big, 256, 0, c->s3>>>(a);
             timing_end(c, PDF_K_BINS, c->s3);
             PDF_CUDA(c, cudaEventRecord(c->bins_join, c->s3));
             c->bins_pending = true;
+            PDF_CUDA(c, cudaStreamWaitEvent(c->s, c->side_join, 0));
             c->launches += 6;
             PDF_CUDA(c, cudaGetLastError());
             return PDF_OK;
@@ -1948,6 +2017,7 @@ int prepare_moments(pdf_ctx* c) {
         // take the SM slots the bins kernel frees first
         PDF_CUDA(c, cudaStreamCreateWithPriority(&c->s3, cudaStreamNonBlocking, lo));
         PDF_CUDA(c, cudaEventCreateWithFlags(&c->bins_join, cudaEventDisableTiming));
+        PDF_CUDA(c, cudaEventCreateWithFlags(&c->crowd_done, cudaEventDisableTiming));
         PDF_CUDA(c, cudaStreamCreateWithFlags(&c->s_cond, cudaStreamNonBlocking));
     }
     const int smem = (int)(sizeof(SortKey) * STATS_CAP);

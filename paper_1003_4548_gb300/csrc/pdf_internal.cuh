@@ -179,9 +179,11 @@ struct pdf_ctx {
     cudaStream_t s2 = nullptr;
     cudaEvent_t side_fork = nullptr, side_join = nullptr, side_join2 = nullptr;
     // bins stream: the velocity bins and <phi|V> of a step, forked after the
-    // warp moments, joined back into the context stream before the step ends
+    // re-sort beside the moments, joined back into the context stream before
+    // the step ends
     cudaStream_t s3 = nullptr;
     cudaEvent_t bins_join = nullptr;
+    cudaEvent_t crowd_done = nullptr;  // the crowded elements' moments (bucket ranges of their bins)
     bool bins_pending = false;
     int bins_bps = 5;  // blocks per SM of the bins kernel (0: one block per four elements)
     // stream that captures the body of the conditional node around the
