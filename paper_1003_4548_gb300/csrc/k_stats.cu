@@ -1121,14 +1121,6 @@ __device__ void empty_moments(const MomArgs<float>& a, int e, int tid) {
     }
 }
 
-__device__ void empty_element(const MomArgs<float>& a, int e, int tid, int nt_team) {
-    empty_moments(a, e, tid);
-    for (int b = tid; b < a.B; b += nt_team) {
-        a.ecm[(size_t)a.B * e + b] = 0.0;
-        a.ecmT[(size_t)a.B * e + b] = 0.f;
-    }
-}
-
 // ---------------------------------------------------------------------------
 // 2 x 2 x 2 bins (median splits on U, then V in each U half, then W in each
 // quarter), one warp per element of at most 512 particles. Lane l holds the
@@ -1463,22 +1455,6 @@ __device__ __forceinline__ void warp_moments(const MomArgs<float>& a, int e, int
     else if (lane < 11) a.eR[6 * e + lane - 5] = val;
     else if (lane == 11) a.epsivar[e] = val;
     if (lane == 0) a.en[e] = n;
-}
-
-// the bucket maps of the three split levels: 256 buckets over mean +- 4 sd of
-// the element's u, v, w, from the moments in memory (any monotone map keeps
-// the selection exact; the approximate reciprocal square root only shapes
-// the buckets)
-__device__ __forceinline__ void med_buckets(const MomArgs<float>& a, int e, Buckets (&bk)[3]) {
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-        const float mu = (float)a.emean[5 * e + d], var = (float)a.eR[6 * e + d];
-        const float rs = var > 0.f ? rsqrtf(var) : 0.f;
-        const float sc = 32.f * rs;
-        bk[d].top = 255;
-        bk[d].lo = mu - 4.f * var * rs;
-        bk[d].sc = (sc > 0.f && sc < 1e30f) ? sc : 0.f;
-    }
 }
 
 // the bucket map of one split level from the element's value range
