@@ -938,11 +938,11 @@ def main():
     # the instruction-issue roofline of the kernels that issue rather than
     # stream bound (their HBM fraction alone reads low)
     sm_mhz = (rg["clocks"] or {}).get("sm_mhz")
-    for k, r in rooflines.items():
-        if k in KTRAFFIC and r.get("ms_per_launch"):
-            iss = issue_roofline(KTRAFFIC[k], r["ms_per_launch"], a.workload, prec, sm_mhz)
+    for k, rl_k in rooflines.items():
+        if k in KTRAFFIC and rl_k.get("ms_per_launch"):
+            iss = issue_roofline(KTRAFFIC[k], rl_k["ms_per_launch"], a.workload, prec, sm_mhz)
             if iss:
-                r["issue"] = iss
+                rl_k["issue"] = iss
     if roof.get("ms_per_launch") and dominant in KTRAFFIC:
         iss = issue_roofline(KTRAFFIC[dominant], roof["ms_per_launch"], a.workload, prec, sm_mhz)
         if iss:
