@@ -1124,8 +1124,9 @@ __device__ void empty_moments(const MomArgs<float>& a, int e, int tid) {
 // ---------------------------------------------------------------------------
 // 2 x 2 x 2 bins (median splits on U, then V in each U half, then W in each
 // quarter), one warp per element of at most 512 particles. Lane l holds the
-// keys q = l + 32 j: j < 8 in registers (u, v, w, psi), 8 <= j < 16 in the
-// warp's shared memory, so the segment is read from memory once.
+// keys q = l + 32 j: j < MRK in registers (u, v, w, psi, each loaded one level
+// ahead of its use, so that at most two are live), MRK <= j < 16 in the warp's
+// shared memory; the segment is read from memory once.
 //  * moments: blocked compensated FP32 sums (KAHAN) or exact fixed-point
 //    sums;
 //  * every split level fills 256-bucket histograms of its component (value-
@@ -1141,12 +1142,13 @@ __device__ void empty_moments(const MomArgs<float>& a, int e, int tid) {
 //    clustered values) hands the element to the general selection path.
 // ---------------------------------------------------------------------------
 constexpr int MCL = 128;  // candidate list capacity
+constexpr int MRK = 9;    // register key slots per lane: elements of up to 288 particles stay in registers
 constexpr unsigned FULLW = 0xffffffffu;
 
 struct __align__(16) MedSmem {
     unsigned hist[4][128];                       // per group: 256 buckets, two 16-bit counts per word (read as uint4)
-    float ou[8][32], ov[8][32], ow[8][32], op[8][32];  // keys 256..511 of the segment
-    unsigned char ob[8][32];                     // their bucket at the current level
+    float ou[16 - MRK][32], ov[16 - MRK][32], ow[16 - MRK][32], op[16 - MRK][32];  // keys j >= MRK, slot j - MRK
+    unsigned char ob[16 - MRK][32];              // their bucket at the current level
     uint32_t cv[MCL];                            // candidate: order bits of the resolved component
     uint32_t cid[MCL];                           // candidate: particle id (read where values tie)
     float cps[MCL];                              // candidate: psi (last level)
@@ -1171,21 +1173,22 @@ __device__ __forceinline__ int split_size(int n, int g, int depth) {
     return m;
 }
 
-__device__ __forceinline__ int getbyte(unsigned w0, unsigned w1, int j) {
-    return (int)(((j < 4 ? w0 : w1) >> (8 * (j & 3))) & 0xffu);
+// byte j of the register keys' packed buckets (j a compile-time index after unrolling)
+__device__ __forceinline__ int getbyte(const unsigned (&pb)[(MRK + 3) / 4], int j) {
+    return (int)((pb[j >> 2] >> (8 * (j & 3))) & 0xffu);
 }
-__device__ __forceinline__ void setbyte(unsigned& w0, unsigned& w1, int j, int b) {
-    unsigned& w = j < 4 ? w0 : w1;
+__device__ __forceinline__ void setbyte(unsigned (&pb)[(MRK + 3) / 4], int j, int b) {
+    unsigned& w = pb[j >> 2];
     w = (w & ~(0xffu << (8 * (j & 3)))) | ((unsigned)b << (8 * (j & 3)));
 }
 
 __device__ __forceinline__ unsigned hinc(int b) { return 1u << (16 * (b & 1)); }
 
-// both bits of the 2-bit group field of every key flagged in m (keys j < 8)
+// both bits of the 2-bit group field of every key flagged in m (register keys j < MRK)
 __device__ __forceinline__ uint32_t med_spread(uint32_t m) {
     uint32_t r = 0u;
 #pragma unroll
-    for (int j = 0; j < 8; ++j) r |= ((m >> j) & 1u) * (3u << (2 * j));
+    for (int j = 0; j < MRK; ++j) r |= ((m >> j) & 1u) * (3u << (2 * j));
     return r;
 }
 
@@ -1494,14 +1497,23 @@ __device__ __forceinline__ void med_append(MedSmem& S, uint32_t key, int q, int 
 
 // the general selection path for an element whose boundary buckets are
 // crowded (bins only: the moments are in memory)
-__device__ __noinline__ void med_general(const MomArgs<float>& a, int e, int s0, int n, SelSmem<512>& S,
-                                         float lo0, float hi0, float lo1, float hi1, float lo2, float hi2) {
-    // bucket ranges [lo, hi] written as mean +- 4 sd, the form sel_element reads
-    if (threadIdx.x % 32 == 0) {
-        const float lo[3] = {lo0, lo1, lo2}, hi[3] = {hi0, hi1, hi2};
-        for (int d = 0; d < 3; ++d) {
-            const double sd = ((double)hi[d] - (double)lo[d]) * 0.125;
-            S.mean[d] = 0.5 * ((double)hi[d] + (double)lo[d]);
+__device__ __noinline__ void med_general(const MomArgs<float>& a, int e, int s0, int n, SelSmem<512>& S) {
+    // the element's value ranges [lo, hi] (read again: the register passes
+    // may not have reached every component), written as mean +- 4 sd, the
+    // form sel_element reads
+    const int lane = threadIdx.x % 32;
+    const float* __restrict__ x[3] = {a.u + s0, a.v + s0, a.w + s0};
+    for (int d = 0; d < 3; ++d) {
+        float lo = 3.4e38f, hi = -3.4e38f;
+        for (int q = lane; q < n; q += 32) {
+            lo = fminf(lo, x[d][q]);
+            hi = fmaxf(hi, x[d][q]);
+        }
+        lo = warp_min(lo);
+        hi = warp_max(hi);
+        if (lane == 0) {
+            const double sd = ((double)hi - (double)lo) * 0.125;
+            S.mean[d] = 0.5 * ((double)hi + (double)lo);
             S.rd[d] = sd * sd;
         }
     }
@@ -1509,15 +1521,38 @@ __device__ __noinline__ void med_general(const MomArgs<float>& a, int e, int s0,
     sel_element<true, 32, 512, SEL_BINS | SEL_RANGES_GIVEN>(a, e, s0, n, S);
 }
 
+// buckets over the element's value range of one component: register keys
+// x[j < MRK] (slots 8.. only when rx) and the shared-memory keys xs[j - MRK]
+__device__ __forceinline__ Buckets med_range(const float (&x)[MRK], const float (*xs)[32], bool rx, int kk, int n,
+                                             int lane) {
+    float lo = 3.4e38f, hi = -3.4e38f;
+#pragma unroll
+    for (int j = 0; j < MRK; ++j) {
+        if (j >= 8 && !rx) break;
+        if (j < kk && lane + 32 * j < n) {
+            lo = fminf(lo, x[j]);
+            hi = fmaxf(hi, x[j]);
+        }
+    }
+    for (int j = MRK; j < kk; ++j) {
+        if (lane + 32 * j < n) {
+            lo = fminf(lo, xs[j - MRK][lane]);
+            hi = fmaxf(hi, xs[j - MRK][lane]);
+        }
+    }
+    return range_buckets(warp_min(lo), warp_max(hi));
+}
+
 __device__ __forceinline__ int upbit(const MedSmem& S, int q) { return (int)((S.upb[q >> 5] >> (q & 31)) & 1u); }
 
-// The passes over keys 256..511 (shared memory), out of line: only elements
-// above 256 particles take them, and the register passes stay contiguous.
+// The passes over the keys j >= MRK (shared memory, slot j - MRK), out of line:
+// only elements above 32 MRK particles take them, and the register passes stay
+// contiguous.
 __device__ __noinline__ void med_tail0(MedSmem& S, Buckets bk, int n, int kk, int lane) {
-    for (int j = 8; j < kk; ++j) {
+    for (int j = MRK; j < kk; ++j) {
         if (lane + 32 * j < n) {
-            const int b = bucket_of(bk, S.ou[j - 8][lane]);
-            S.ob[j - 8][lane] = (unsigned char)b;
+            const int b = bucket_of(bk, S.ou[j - MRK][lane]);
+            S.ob[j - MRK][lane] = (unsigned char)b;
             atomicAdd(&S.hist[0][b >> 1], hinc(b));
         }
     }
@@ -1525,15 +1560,15 @@ __device__ __noinline__ void med_tail0(MedSmem& S, Buckets bk, int n, int kk, in
 
 __device__ __noinline__ uint2 med_tail1(MedSmem& S, Buckets bk, int c0, int n, int kk, int lane, uint32_t gw,
                                         uint32_t pend) {
-    for (int j = 8; j < kk; ++j) {
+    for (int j = MRK; j < kk; ++j) {
         const int q = lane + 32 * j;
         if (q < n) {
-            const int b0 = S.ob[j - 8][lane];
-            const int b = bucket_of(bk, S.ov[j - 8][lane]);
-            S.ob[j - 8][lane] = (unsigned char)b;
+            const int b0 = S.ob[j - MRK][lane];
+            const int b = bucket_of(bk, S.ov[j - MRK][lane]);
+            S.ob[j - MRK][lane] = (unsigned char)b;
             if (b0 == c0) {
                 pend |= 1u << j;
-                med_append(S, ord32(S.ou[j - 8][lane]), q, 0, b, 0.f);
+                med_append(S, ord32(S.ou[j - MRK][lane]), q, 0, b, 0.f);
             } else {
                 const int g = b0 > c0 ? 1 : 0;
                 gw |= (uint32_t)g << (2 * j);
@@ -1546,18 +1581,18 @@ __device__ __noinline__ uint2 med_tail1(MedSmem& S, Buckets bk, int c0, int n, i
 
 __device__ __noinline__ uint2 med_tail2(MedSmem& S, Buckets bk, int c0, int c1, int n, int kk, int lane, uint32_t gw,
                                         uint32_t pend, uint32_t pend2) {
-    for (int j = 8; j < kk; ++j) {
+    for (int j = MRK; j < kk; ++j) {
         const int q = lane + 32 * j;
         if (q < n) {
             int g = (int)((gw >> (2 * j)) & 3u);
             if ((pend >> j) & 1u) g = 2 * g + upbit(S, q);
-            const int b1 = S.ob[j - 8][lane], c = g ? c1 : c0;
-            const int b = bucket_of(bk, S.ow[j - 8][lane]);
-            S.ob[j - 8][lane] = (unsigned char)b;
+            const int b1 = S.ob[j - MRK][lane], c = g ? c1 : c0;
+            const int b = bucket_of(bk, S.ow[j - MRK][lane]);
+            S.ob[j - MRK][lane] = (unsigned char)b;
             if (b1 == c) {
                 pend2 |= 1u << j;
                 gw = (gw & ~(3u << (2 * j))) | ((uint32_t)g << (2 * j));
-                med_append(S, ord32(S.ov[j - 8][lane]), q, g, b, 0.f);
+                med_append(S, ord32(S.ov[j - MRK][lane]), q, g, b, 0.f);
             } else {
                 const int g2 = 2 * g + (b1 > c ? 1 : 0);
                 gw = (gw & ~(3u << (2 * j))) | ((uint32_t)g2 << (2 * j));
@@ -1570,15 +1605,15 @@ __device__ __noinline__ uint2 med_tail2(MedSmem& S, Buckets bk, int c0, int c1, 
 
 __device__ __noinline__ void med_tail3(MedSmem& S, unsigned char* bins, int4 c4, int n, int kk, int lane, uint32_t gw,
                                        uint32_t pend) {
-    for (int j = 8; j < kk; ++j) {
+    for (int j = MRK; j < kk; ++j) {
         const int q = lane + 32 * j;
         if (q < n) {
             int g = (int)((gw >> (2 * j)) & 3u);
             if ((pend >> j) & 1u) g = 2 * g + upbit(S, q);
-            const int b2 = S.ob[j - 8][lane], c = g == 0 ? c4.x : (g == 1 ? c4.y : (g == 2 ? c4.z : c4.w));
-            const float ps = S.op[j - 8][lane];
+            const int b2 = S.ob[j - MRK][lane], c = g == 0 ? c4.x : (g == 1 ? c4.y : (g == 2 ? c4.z : c4.w));
+            const float ps = S.op[j - MRK][lane];
             if (b2 == c) {
-                med_append(S, ord32(S.ow[j - 8][lane]), q, g, 0, ps);
+                med_append(S, ord32(S.ow[j - MRK][lane]), q, g, 0, ps);
             } else {
                 const int bn = 2 * g + (b2 > c ? 1 : 0);
                 bins[q] = (unsigned char)bn;
@@ -1629,75 +1664,60 @@ __device__ __forceinline__ void med_bins_element(const MomArgs<float>& a, int e,
     MedSmem& S = U.m;
     const uint32_t* __restrict__ ids = a.id + s0;
     const int kk = (n + 31) >> 5;  // key slots in use (warp-uniform)
-    float xu[8], xv[8], xw[8], xp[8];
+    float xu[MRK] = {}, xv[MRK] = {}, xw[MRK] = {}, xp[MRK] = {};
+    const bool rx = kk > 8;  // the register slots 8.. are in use (warp-uniform: smaller elements skip them)
+    // the register keys' components are loaded one level ahead of their use
+    // (v during the first scan, w once u is spent, psi once v is spent), so
+    // at most two of them are live at a time
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
+    for (int j = 0; j < MRK; ++j) {
+        if (j >= 8 && !rx) break;
         const int q = lane + 32 * j;
-        const bool in = j < kk && q < n;
-        xu[j] = in ? a.u[s0 + q] : 0.f;
-        xv[j] = in ? a.v[s0 + q] : 0.f;
-        xw[j] = in ? a.w[s0 + q] : 0.f;
-        xp[j] = in ? a.psi[s0 + q] : 0.f;
+        xu[j] = j < kk && q < n ? a.u[s0 + q] : 0.f;
     }
-    if (kk > 8) {  // keys 256..511 into the warp's shared memory (all loads issued together)
-        float tu[8], tv[8], tw[8], tp[8];
+    if (kk > MRK) {  // keys 32 MRK..511 into the warp's shared memory (all loads issued together)
+        float tu[16 - MRK], tv[16 - MRK], tw[16 - MRK], tp[16 - MRK];
 #pragma unroll
-        for (int h = 0; h < 8; ++h) {
-            const int q = lane + 32 * (8 + h);
-            const bool in = 8 + h < kk && q < n;
+        for (int h = 0; h < 16 - MRK; ++h) {
+            const int q = lane + 32 * (MRK + h);
+            const bool in = MRK + h < kk && q < n;
             tu[h] = in ? a.u[s0 + q] : 0.f;
             tv[h] = in ? a.v[s0 + q] : 0.f;
             tw[h] = in ? a.w[s0 + q] : 0.f;
             tp[h] = in ? a.psi[s0 + q] : 0.f;
         }
 #pragma unroll
-        for (int h = 0; h < 8; ++h) {
+        for (int h = 0; h < 16 - MRK; ++h) {
             S.ou[h][lane] = tu[h]; S.ov[h][lane] = tv[h]; S.ow[h][lane] = tw[h]; S.op[h][lane] = tp[h];
         }
     }
-    // the bucket ranges: the element's own minimum and maximum of u, v, w (the
-    // bins need no moments, so they run beside the moments kernel)
-    float rl[3] = {3.4e38f, 3.4e38f, 3.4e38f}, rh[3] = {-3.4e38f, -3.4e38f, -3.4e38f};
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-        if (j < kk && lane + 32 * j < n) {
-            rl[0] = fminf(rl[0], xu[j]); rh[0] = fmaxf(rh[0], xu[j]);
-            rl[1] = fminf(rl[1], xv[j]); rh[1] = fmaxf(rh[1], xv[j]);
-            rl[2] = fminf(rl[2], xw[j]); rh[2] = fmaxf(rh[2], xw[j]);
-        }
-    }
-    if (kk > 8) {
-        for (int h = 0; h < 8; ++h) {
-            if (8 + h < kk && lane + 32 * (8 + h) < n) {
-                rl[0] = fminf(rl[0], S.ou[h][lane]); rh[0] = fmaxf(rh[0], S.ou[h][lane]);
-                rl[1] = fminf(rl[1], S.ov[h][lane]); rh[1] = fmaxf(rh[1], S.ov[h][lane]);
-                rl[2] = fminf(rl[2], S.ow[h][lane]); rh[2] = fmaxf(rh[2], S.ow[h][lane]);
-            }
-        }
-    }
-    Buckets bk[3];
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-        rl[d] = warp_min(rl[d]);
-        rh[d] = warp_max(rh[d]);
-        bk[d] = range_buckets(rl[d], rh[d]);
-    }
-    unsigned pb0 = 0u, pb1 = 0u;  // bucket of register key j at the current level (a byte each)
+    // the bucket ranges: the element's own minimum and maximum of each
+    // component (the bins need no moments, so they run beside the moments
+    // kernel), taken when the component's level starts
+    Buckets bk = med_range(xu, S.ou, rx, kk, n, lane);
+    unsigned pb[(MRK + 3) / 4] = {};  // bucket of register key j at the current level (a byte each)
     // The passes over the register keys are branch-free (the key slot and the
-    // segment bound predicate the stores and atomics), so the eight keys of a
-    // lane interleave; keys deferred to the candidate list are flagged in a
-    // mask and listed after the pass.
+    // segment bound predicate the stores and atomics), so the keys of a lane
+    // interleave; keys deferred to the candidate list are flagged in a mask
+    // and listed after the pass.
     // ---- level 0: U
     for (int t = lane; t < 128; t += 32) S.hist[0][t] = 0u;
     __syncwarp();
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
+    for (int j = 0; j < MRK; ++j) {
+        if (j >= 8 && !rx) break;
         const bool in = j < kk && lane + 32 * j < n;
-        const int b = bucket_of(bk[0], xu[j]);
-        setbyte(pb0, pb1, j, b);
+        const int b = bucket_of(bk, xu[j]);
+        setbyte(pb, j, b);
         if (in) atomicAdd(&S.hist[0][b >> 1], hinc(b));
     }
-    if (kk > 8) med_tail0(S, bk[0], n, kk, lane);
+    if (kk > MRK) med_tail0(S, bk, n, kk, lane);
+#pragma unroll
+    for (int j = 0; j < MRK; ++j) {  // v of the register keys, in flight during the scan
+        if (j >= 8 && !rx) break;
+        const int q = lane + 32 * j;
+        xv[j] = j < kk && q < n ? a.v[s0 + q] : 0.f;
+    }
     __syncwarp();
     med_scan<1>(S, n, lane);
     __syncwarp();
@@ -1709,13 +1729,15 @@ __device__ __forceinline__ void med_bins_element(const MomArgs<float>& a, int e,
         for (int t = lane; t < 256; t += 32) (&S.hist[0][0])[t] = 0u;
         if (lane < 16) S.upb[lane] = 0u;
         if (lane == 0) S.ncl = 0;
+        bk = med_range(xv, S.ov, rx, kk, n, lane);
         __syncwarp();
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
+        for (int j = 0; j < MRK; ++j) {
+            if (j >= 8 && !rx) break;
             const bool in = j < kk && lane + 32 * j < n;
-            const int b0 = getbyte(pb0, pb1, j);
-            const int b = bucket_of(bk[1], xv[j]);
-            setbyte(pb0, pb1, j, b);
+            const int b0 = getbyte(pb, j);
+            const int b = bucket_of(bk, xv[j]);
+            setbyte(pb, j, b);
             const int g = b0 > c0 ? 1 : 0;
             gw |= (uint32_t)g << (2 * j);
             const bool isc = in && b0 == c0;
@@ -1723,11 +1745,17 @@ __device__ __forceinline__ void med_bins_element(const MomArgs<float>& a, int e,
             if (in && !isc) atomicAdd(&S.hist[g][b >> 1], hinc(b));
         }
 #pragma unroll
-        for (int j = 0; j < 8; ++j)
-            if ((pend >> j) & 1u) med_append(S, ord32(xu[j]), lane + 32 * j, 0, getbyte(pb0, pb1, j), 0.f);
+        for (int j = 0; j < MRK; ++j)
+            if ((pend >> j) & 1u) med_append(S, ord32(xu[j]), lane + 32 * j, 0, getbyte(pb, j), 0.f);
+#pragma unroll
+        for (int j = 0; j < MRK; ++j) {  // u is spent: w of the register keys
+            if (j >= 8 && !rx) break;
+            const int q = lane + 32 * j;
+            xw[j] = j < kk && q < n ? a.w[s0 + q] : 0.f;
+        }
         gw &= ~med_spread(pend);  // deferred keys stay in group 0 until resolved
-        if (kk > 8) {
-            const uint2 r = med_tail1(S, bk[1], c0, n, kk, lane, gw, pend);
+        if (kk > MRK) {
+            const uint2 r = med_tail1(S, bk, c0, n, kk, lane, gw, pend);
             gw = r.x;
             pend = r.y;
         }
@@ -1749,16 +1777,18 @@ __device__ __forceinline__ void med_bins_element(const MomArgs<float>& a, int e,
         const int c0 = S.bkt[0], c1 = S.bkt[1];
         for (int t = lane; t < 512; t += 32) (&S.hist[0][0])[t] = 0u;
         if (lane == 0) S.ncl = 0;
+        bk = med_range(xw, S.ow, rx, kk, n, lane);
         __syncwarp();
         uint32_t pend2 = 0u;
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
+        for (int j = 0; j < MRK; ++j) {
+            if (j >= 8 && !rx) break;
             const bool in = j < kk && lane + 32 * j < n;
             int g = (int)((gw >> (2 * j)) & 3u);
             g = ((pend >> j) & 1u) ? 2 * g + upbit(S, lane + 32 * j) : g;
-            const int b1 = getbyte(pb0, pb1, j), c = g ? c1 : c0;
-            const int b = bucket_of(bk[2], xw[j]);
-            setbyte(pb0, pb1, j, b);
+            const int b1 = getbyte(pb, j), c = g ? c1 : c0;
+            const int b = bucket_of(bk, xw[j]);
+            setbyte(pb, j, b);
             const bool isc = in && b1 == c;
             const int g2 = isc ? g : 2 * g + (b1 > c ? 1 : 0);
             gw = (gw & ~(3u << (2 * j))) | ((uint32_t)g2 << (2 * j));
@@ -1766,11 +1796,17 @@ __device__ __forceinline__ void med_bins_element(const MomArgs<float>& a, int e,
             if (in && !isc) atomicAdd(&S.hist[g2][b >> 1], hinc(b));
         }
 #pragma unroll
-        for (int j = 0; j < 8; ++j)
+        for (int j = 0; j < MRK; ++j)
             if ((pend2 >> j) & 1u)
-                med_append(S, ord32(xv[j]), lane + 32 * j, (int)((gw >> (2 * j)) & 3u), getbyte(pb0, pb1, j), 0.f);
-        if (kk > 8) {
-            const uint2 r = med_tail2(S, bk[2], c0, c1, n, kk, lane, gw, pend, pend2);
+                med_append(S, ord32(xv[j]), lane + 32 * j, (int)((gw >> (2 * j)) & 3u), getbyte(pb, j), 0.f);
+#pragma unroll
+        for (int j = 0; j < MRK; ++j) {  // v is spent: psi of the register keys (for the last pass)
+            if (j >= 8 && !rx) break;
+            const int q = lane + 32 * j;
+            xp[j] = j < kk && q < n ? a.psi[s0 + q] : 0.f;
+        }
+        if (kk > MRK) {
+            const uint2 r = med_tail2(S, bk, c0, c1, n, kk, lane, gw, pend, pend2);
             gw = r.x;
             pend2 = r.y;
         }
@@ -1791,7 +1827,7 @@ __device__ __forceinline__ void med_bins_element(const MomArgs<float>& a, int e,
     }
     if (general) {  // crowded boundary buckets: the general selection path
         __syncwarp();
-        med_general(a, e, s0, n, U.s, rl[0], rh[0], rl[1], rh[1], rl[2], rh[2]);
+        med_general(a, e, s0, n, U.s);
         return;
     }
     // ---- bins: the W halves; psi summed per bin
@@ -1801,13 +1837,14 @@ __device__ __forceinline__ void med_bins_element(const MomArgs<float>& a, int e,
     __syncwarp();
     uint32_t pend3 = 0u;
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
+    for (int j = 0; j < MRK; ++j) {
+        if (j >= 8 && !rx) break;
         const int q = lane + 32 * j;
         const bool in = j < kk && q < n;
         int g = (int)((gw >> (2 * j)) & 3u);
         g = ((pend >> j) & 1u) ? 2 * g + upbit(S, q) : g;
         gw = (gw & ~(3u << (2 * j))) | ((uint32_t)g << (2 * j));
-        const int b2 = getbyte(pb0, pb1, j), c = g == 0 ? c0 : (g == 1 ? c1 : (g == 2 ? c2 : c3));
+        const int b2 = getbyte(pb, j), c = g == 0 ? c0 : (g == 1 ? c1 : (g == 2 ? c2 : c3));
         const bool isc = in && b2 == c;
         pend3 |= (isc ? 1u : 0u) << j;
         const int bn = 2 * g + (b2 > c ? 1 : 0);
@@ -1817,9 +1854,9 @@ __device__ __forceinline__ void med_bins_element(const MomArgs<float>& a, int e,
         }
     }
 #pragma unroll
-    for (int j = 0; j < 8; ++j)
+    for (int j = 0; j < MRK; ++j)
         if ((pend3 >> j) & 1u) med_append(S, ord32(xw[j]), lane + 32 * j, (int)((gw >> (2 * j)) & 3u), 0, xp[j]);
-    if (kk > 8) med_tail3(S, a.bin + s0, make_int4(c0, c1, c2, c3), n, kk, lane, gw, pend);
+    if (kk > MRK) med_tail3(S, a.bin + s0, make_int4(c0, c1, c2, c3), n, kk, lane, gw, pend);
     __syncwarp();
     const int L = S.ncl;
     med_rank(S, ids, L, lane);
