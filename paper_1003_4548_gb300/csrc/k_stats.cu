@@ -1182,6 +1182,20 @@ __device__ __forceinline__ void setbyte(unsigned (&pb)[(MRK + 3) / 4], int j, in
     w = (w & ~(0xffu << (8 * (j & 3)))) | ((unsigned)b << (8 * (j & 3)));
 }
 
+// register key j of x for a run-time j (a select chain: the array stays in registers)
+__device__ __forceinline__ float pick(const float (&x)[MRK], int j) {
+    float r = x[0];
+#pragma unroll
+    for (int k = 1; k < MRK; ++k) r = j == k ? x[k] : r;
+    return r;
+}
+__device__ __forceinline__ int getbyte_rt(const unsigned (&pb)[(MRK + 3) / 4], int j) {
+    unsigned w = pb[0];
+#pragma unroll
+    for (int k = 1; k < (MRK + 3) / 4; ++k) w = (j >> 2) == k ? pb[k] : w;
+    return (int)((w >> (8 * (j & 3))) & 0xffu);
+}
+
 __device__ __forceinline__ unsigned hinc(int b) { return 1u << (16 * (b & 1)); }
 
 // both bits of the 2-bit group field of every key flagged in m (register keys j < MRK)
@@ -1744,9 +1758,11 @@ __device__ __forceinline__ void med_bins_element(const MomArgs<float>& a, int e,
             pend |= (isc ? 1u : 0u) << j;
             if (in && !isc) atomicAdd(&S.hist[g][b >> 1], hinc(b));
         }
-#pragma unroll
-        for (int j = 0; j < MRK; ++j)
-            if ((pend >> j) & 1u) med_append(S, ord32(xu[j]), lane + 32 * j, 0, getbyte(pb, j), 0.f);
+        // the deferred register keys, lane by lane (a few per warp)
+        for (uint32_t p = pend; p; p &= p - 1u) {
+            const int j = __ffs(p) - 1;
+            med_append(S, ord32(pick(xu, j)), lane + 32 * j, 0, getbyte_rt(pb, j), 0.f);
+        }
 #pragma unroll
         for (int j = 0; j < MRK; ++j) {  // u is spent: w of the register keys
             if (j >= 8 && !rx) break;
@@ -1795,10 +1811,10 @@ __device__ __forceinline__ void med_bins_element(const MomArgs<float>& a, int e,
             pend2 |= (isc ? 1u : 0u) << j;
             if (in && !isc) atomicAdd(&S.hist[g2][b >> 1], hinc(b));
         }
-#pragma unroll
-        for (int j = 0; j < MRK; ++j)
-            if ((pend2 >> j) & 1u)
-                med_append(S, ord32(xv[j]), lane + 32 * j, (int)((gw >> (2 * j)) & 3u), getbyte(pb, j), 0.f);
+        for (uint32_t p = pend2; p; p &= p - 1u) {
+            const int j = __ffs(p) - 1;
+            med_append(S, ord32(pick(xv, j)), lane + 32 * j, (int)((gw >> (2 * j)) & 3u), getbyte_rt(pb, j), 0.f);
+        }
 #pragma unroll
         for (int j = 0; j < MRK; ++j) {  // v is spent: psi of the register keys (for the last pass)
             if (j >= 8 && !rx) break;
@@ -1853,9 +1869,10 @@ __device__ __forceinline__ void med_bins_element(const MomArgs<float>& a, int e,
             med_binadd(S, bn, psi_fixed(xp[j]));
         }
     }
-#pragma unroll
-    for (int j = 0; j < MRK; ++j)
-        if ((pend3 >> j) & 1u) med_append(S, ord32(xw[j]), lane + 32 * j, (int)((gw >> (2 * j)) & 3u), 0, xp[j]);
+    for (uint32_t p = pend3; p; p &= p - 1u) {
+        const int j = __ffs(p) - 1;
+        med_append(S, ord32(pick(xw, j)), lane + 32 * j, (int)((gw >> (2 * j)) & 3u), 0, pick(xp, j));
+    }
     if (kk > MRK) med_tail3(S, a.bin + s0, make_int4(c0, c1, c2, c3), n, kk, lane, gw, pend);
     __syncwarp();
     const int L = S.ncl;
