@@ -46,8 +46,11 @@ def args_():
     ap.add_argument("--chosen", default="lagged", choices=["lagged", "corrected", "surrogate"],
                     help="wp of the timed form: lagged FE under the coarse residual check, the lagged FE plus the "
                          "trained network's change since the last solve, or the trained network alone")
-    ap.add_argument("--lag-tol", type=float, default=0.05,
-                    help="coarse residual above which the lagged form solves the FE problem again")
+    ap.add_argument("--lag-tol", type=float, default=None,
+                    help="coarse residual above which the lagged form solves the FE problem again (default: the "
+                         "workload's lag_tol)")
+    ap.add_argument("--lag-cg-tol", type=float, default=None,
+                    help="relative residual of the lagged form's FE solves (default: the workload's lag_cg_tol)")
     ap.add_argument("--no-forms", action="store_true", help="skip the plain forms and the precision study")
     ap.add_argument("--save-surrogate", default=None, help="write the trained network (npz) here")
     ap.add_argument("--load-surrogate", default=None, help="use this trained network (npz) instead of training")
@@ -371,6 +374,8 @@ class Form:
 
     def __init__(self, cfg, mesh, stream, *, precision, case_id=0, seed=None, cg_precision=0, sur=None, **extra):
         from paper_1003_4548_gb300 import Canyon, canyon_params
+        if sur is not None and sur.get("cg_tol") is not None and "cg_tol" not in extra:
+            extra["cg_tol"] = sur["cg_tol"]  # the lagged forms' FE solve tolerance
         p = canyon_params(mesh, wall_model=cfg["wall_model"], precision=precision, C0=cfg["C0"],
                           bins=cfg["bins"], seed=cfg["seed"] if seed is None else seed, k0=cfg["k0"],
                           case_id=case_id, cg_precision=cg_precision, **extra)
@@ -540,7 +545,7 @@ def run_batch(a, cfg, emit=True):
     # network trained on held-out cases of the same family (another draw of
     # the batch recipe: W/H 0.5 .. 3, spacing 0.017 .. 0.1), calibrated on the
     # wall-resolved W/H = 1 canyon
-    sur, sur_info = None, {"form": "lagged FE", "residual_tol": a.lag_tol}
+    sur, sur_info = None, {"form": "lagged FE", "residual_tol": a.lag_tol, "cg_tol": a.lag_cg_tol}
     if a.chosen == "surrogate":
         ref = dict(WORKLOADS["canyon_er_full"])
         ref["name"] = "canyon_er_full"
@@ -557,7 +562,7 @@ def run_batch(a, cfg, emit=True):
     t0 = time.perf_counter()
     for c, m, st in zip(cases, meshes, streams):
         p = canyon_params(m, wall_model="er", precision=prec, C0=cfg["C0"], bins=cfg["bins"], seed=c["seed"],
-                          k0=cfg["k0"], case_id=rank)
+                          k0=cfg["k0"], case_id=rank, **({"cg_tol": a.lag_cg_tol} if sur is None else {}))
         g = Canyon(p, m, stream=st.cuda_stream)
         g.seed_particles(c["per_element"])
         g.estimate_stats()
@@ -716,6 +721,11 @@ def main():
     from canyon_inputs.configs import WORKLOADS, build_mesh, cfl_dt
     cfg = dict(WORKLOADS[a.workload])
     cfg["name"] = a.workload
+    # the lagged FE form's schedule: the workload's check and solve tolerances
+    if a.lag_tol is None:
+        a.lag_tol = cfg.get("lag_tol", 0.03)
+    if a.lag_cg_tol is None:
+        a.lag_cg_tol = cfg.get("lag_cg_tol")
     if cfg.get("kind") == "batch":
         if a.impl == "reference":
             print(json.dumps({"impl": "reference", "unavailable": "the batch workload has no oracle arm"}))
@@ -760,8 +770,8 @@ def main():
         sur["mode"] = a.surrogate_mode
     if sur is not None and a.save_surrogate:
         np.savez(a.save_surrogate, params=sur["params"], norm=sur["norm"], tol=sur["tol"])
-    lagged = {"mode": 5, "params": None, "norm": None, "tol": a.lag_tol}
-    corrected = dict(sur, mode=6, tol=a.lag_tol) if sur is not None else None
+    lagged = {"mode": 5, "params": None, "norm": None, "tol": a.lag_tol, "cg_tol": a.lag_cg_tol}
+    corrected = dict(sur, mode=6, tol=a.lag_tol, cg_tol=a.lag_cg_tol) if sur is not None else None
     chosen_wp = ({"surrogate": sur, "corrected": corrected}.get(a.chosen, lagged)) if er else None
     prec = cfg["precision"]
     red = {"fp64": "FP64", "fp32": "FP64-exact", "fp32_kahan": "compensated FP32"}[prec]
@@ -926,8 +936,10 @@ def main():
                 "pressure_iterations_last": rr["pressure_iterations_last"],
                 "kernels_ms_per_step": {q: v[0] / k for q, v in rr["kt"].items()}}
             f.close()
-        stated["precision_study"] = precision_study(cfg, mesh, dt, stream, sur, steps=200, lag_tol=a.lag_tol)
+        stated["precision_study"] = precision_study(cfg, mesh, dt, stream, sur, steps=200, lag_tol=a.lag_tol,
+                                                    lag_cg_tol=a.lag_cg_tol)
         stated["standard_errors"] = standard_error_study(cfg, mesh, dt, stream, sur, lag_tol=a.lag_tol,
+                                                         lag_cg_tol=a.lag_cg_tol,
                                                          seeds=a.se_seeds)
     # the other workloads of the recipe, measured in the same run: the small
     # wall-function canyon and the 32-case batch
@@ -984,11 +996,11 @@ def capi_status(st):
     return capi.ERRORS.get(st, "ok") if st else "ok"
 
 
-def precision_study(cfg, mesh, dt, stream, sur, steps, lag_tol=0.05):
+def precision_study(cfg, mesh, dt, stream, sur, steps, lag_tol=0.03, lag_cg_tol=None):
     """The same seeded ensemble advanced `steps` steps in each form; statistics
     on a 12 x 8 grid of cells compared with the all-FP64 form (relative rms),
     next to the Monte Carlo scale (the FP64 form with another seed)."""
-    lag = lambda tol: {"mode": 5, "params": None, "norm": None, "tol": tol}  # noqa: E731
+    lag = lambda tol: {"mode": 5, "params": None, "norm": None, "tol": tol, "cg_tol": lag_cg_tol}  # noqa: E731
     variants = (("fp64_fe", "fp64", 0, None, None), ("fp64_fe_other_seed", "fp64", 0, None, 1),
                 ("fp32_fe", "fp32", 0, None, None), ("fp32_kahan_fe", "fp32_kahan", 0, None, None),
                 ("fp32_fe_ff_cg", "fp32", 1, None, None),
@@ -1049,7 +1061,8 @@ def z_cells(A, B):
             "cells_with_values_below_fp32_normal_range": tiny}
 
 
-def standard_error_study(cfg, mesh, dt, stream, sur, lag_tol=0.05, seeds=8, checkpoints=(200, 500)):
+def standard_error_study(cfg, mesh, dt, stream, sur, lag_tol=0.03, lag_cg_tol=None, seeds=8,
+                         checkpoints=(200, 500)):
     """The stated error of each form in Monte Carlo standard errors: `seeds`
     runs of the plain FP64 form (FE solve every step) and `seeds` runs of
     each other form, with disjoint seeds, from their seeded starts; at each
@@ -1058,13 +1071,13 @@ def standard_error_study(cfg, mesh, dt, stream, sur, lag_tol=0.05, seeds=8, chec
     cell in standard errors of the difference of their means. Without a bias
     |z| follows Student's t with 2 x seeds - 2 degrees of freedom (about 1 % of
     the tests above 3 for 8 seeds)."""
-    lag = {"mode": 5, "params": None, "norm": None, "tol": lag_tol}
+    lag = {"mode": 5, "params": None, "norm": None, "tol": lag_tol, "cg_tol": lag_cg_tol}
     forms = [("fp64_fe", "fp64", None, 1000), ("chosen_fp32_kahan_lagged_fe", "fp32_kahan", lag, 2000),
              ("fp32_kahan_fe", "fp32_kahan", None, 3000)]
     if sur is not None:
         forms.append(("fp32_kahan_surrogate_node_form", "fp32_kahan", sur, 4000))
         forms.append(("fp32_kahan_lagged_fe_with_network_correction", "fp32_kahan",
-                      dict(sur, mode=6, tol=lag_tol), 5000))
+                      dict(sur, mode=6, tol=lag_tol, cg_tol=lag_cg_tol), 5000))
     t0 = time.perf_counter()
     cells = {}
     for name, prec, s, base in forms:
@@ -1079,14 +1092,57 @@ def standard_error_study(cfg, mesh, dt, stream, sur, lag_tol=0.05, seeds=8, chec
                 runs[c].append(cell_stats(f.g, mesh))
             f.close()
         cells[name] = runs
+    # the chosen form again on the FP64 runs' own seeds: paired differences,
+    # in which the Monte Carlo noise common to a pair cancels
+    paired = {c: [] for c in checkpoints}
+    for i in range(seeds):
+        f = Form(cfg, mesh, stream, precision="fp32_kahan", sur=lag, seed=1000 + i)
+        done = 0
+        for c in checkpoints:
+            f.g.step(dt, c - done)
+            done = c
+            f.g.sync()
+            paired[c].append(cell_stats(f.g, mesh))
+        f.close()
     out = {"seeds_per_form": seeds, "checkpoints": list(checkpoints), "reference": "fp64_fe",
            "cells": "12 x 8 grid, particle-weighted element statistics", "wall_s": None}
     for name in cells:
         if name == "fp64_fe":
             continue
         out[name] = {str(c): z_cells(cells[name][c], cells["fp64_fe"][c]) for c in checkpoints}
+    out["chosen_paired_with_fp64_seeds"] = {str(c): paired_bias(paired[c], cells["fp64_fe"][c]) for c in checkpoints}
     out["wall_s"] = round(time.perf_counter() - t0, 1)
     return out
+
+
+def paired_bias(A, B):
+    """Runs A[i] and B[i] share a seed: per cell and statistic the mean of
+    the paired differences d = A - B, in units of the Monte Carlo standard
+    error of B's ensemble mean (s_B / sqrt(M)), and the paired t = mean(d) /
+    (s_d / sqrt(M)) (Student's t with M - 1 degrees of freedom without a
+    bias: about 2 % of the tests above 3 for 8 pairs)."""
+    import numpy as np
+    bias, tmax, allt, flat = {}, {}, [], []
+    for q in A[0]:
+        a, b = np.array([x[q] for x in A]), np.array([x[q] for x in B])
+        a, b = np.where(np.abs(a) < FLT_MIN, 0.0, a), np.where(np.abs(b) < FLT_MIN, 0.0, b)
+        d = a - b
+        m = len(A)
+        se_b = b.std(0, ddof=1) / np.sqrt(m)
+        sd_d = d.std(0, ddof=1) / np.sqrt(m)
+        ok = se_b > 0
+        r = np.where(ok, np.abs(d.mean(0)) / np.where(ok, se_b, 1.0), 0.0)
+        okd = sd_d > 0
+        t = np.where(okd, d.mean(0) / np.where(okd, sd_d, 1.0), 0.0)
+        bias[q] = float(r.max())
+        tmax[q] = float(np.abs(t).max())
+        allt.append(np.abs(t[okd]))
+        flat.append(r[ok])
+    allt, flat = np.concatenate(allt), np.concatenate(flat)
+    return {"max_bias_in_se": float(flat.max()), "median_bias_in_se": float(np.median(flat)),
+            "max_bias_in_se_per_stat": bias, "max_abs_paired_t": float(allt.max()),
+            "frac_paired_t_above_3": float(np.mean(allt > 3)), "tests": int(allt.size),
+            "max_abs_paired_t_per_stat": tmax}
 
 
 if __name__ == "__main__":

@@ -20,8 +20,9 @@ canyon centre) and the workload sizes of this project:
                     with FP64 statistics and CG, 500 steps. The chosen form
                     keeps the FP32 state, reduces in compensated FP32 and
                     keeps the previous step's wp while its coarse FE residual
-                    under the current statistics stays below a tolerance
-                    (the FE solve runs when it does not).
+                    under the current statistics stays below lag_tol = 0.03
+                    (the FE solve, to a relative residual of lag_cg_tol =
+                    1e-6, runs when it does not).
 
 The time step follows a CFL rule that depends on the mesh and the initial
 condition only: dt = CFL * min_e(2 r_e) / U_ref, with r_e the inradius and
@@ -54,13 +55,14 @@ WORKLOADS = {
         mesh=dict(H=1.0, W=1.0, B=2.0, T=2.0, offset=0.0, h=0.017, y1=NU / USTAR,
                   growth=1.2, seed=0),
         wall_model="er", per_element=256, bins=(2, 2, 2), C0=2.1, steps=500, cfl=0.5,
-        precision="fp32", chosen_precision="fp32_kahan", seed=0, k0=1e-3),
+        precision="fp32", chosen_precision="fp32_kahan", seed=0, k0=1e-3, lag_tol=0.03, lag_cg_tol=1e-6),
 }
 
 
 WORKLOADS["canyon_batch32"] = dict(kind="batch", cases=32, seed=0, wall_model="er", bins=(2, 2, 2), C0=2.1,
                                    cfl=0.5, k0=1e-3, precision="fp32", chosen_precision="fp32_kahan",
-                                   mesh=WORKLOADS["canyon_er_full"]["mesh"], per_element=256)
+                                   mesh=WORKLOADS["canyon_er_full"]["mesh"], per_element=256, lag_tol=0.03,
+                                   lag_cg_tol=1e-6)
 
 
 def batch_cases(cfg: dict) -> list[dict]:

@@ -24,7 +24,7 @@ def main(argv=None):
     ap.add_argument("--workload", default="canyon_er_full")
     ap.add_argument("--steps", type=int, default=4)
     ap.add_argument("--precision", default=None, help="state/reduction precision (default: the chosen form's)")
-    ap.add_argument("--lag-tol", type=float, default=0.05)
+    ap.add_argument("--lag-tol", type=float, default=None, help="default: the workload's lag_tol")
     a = ap.parse_args(argv)
 
     import torch
@@ -37,13 +37,15 @@ def main(argv=None):
     mesh = build_mesh(cfg)
     dt = cfl_dt(mesh, cfl=cfg["cfl"], k0=cfg["k0"])
     torch.cuda.set_device(0)
+    lagged = cfg["wall_model"] == "er"
+    extra = {"cg_tol": cfg["lag_cg_tol"]} if lagged and cfg.get("lag_cg_tol") else {}
     p = canyon_params(mesh, wall_model=cfg["wall_model"], precision=prec, C0=cfg["C0"], bins=cfg["bins"],
-                      seed=cfg["seed"], k0=cfg["k0"])
+                      seed=cfg["seed"], k0=cfg["k0"], **extra)
     g = Canyon(p, mesh, stream=torch.cuda.current_stream().cuda_stream)
     g.seed_particles(cfg["per_element"])
     g.estimate_stats()
-    if cfg["wall_model"] == "er":
-        g.set_surrogate(5, None, None, a.lag_tol)
+    if lagged:
+        g.set_surrogate(5, None, None, a.lag_tol if a.lag_tol is not None else cfg.get("lag_tol", 0.03))
     g.step(dt, a.steps)
     g.sync()
     print(f"{a.workload}: {g.num_particles} particles, {a.steps} steps, {prec}")

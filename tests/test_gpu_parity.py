@@ -249,7 +249,8 @@ def test_multistep_cells_within_standard_errors_of_oracle(case):
     element; the frequency reflection of Section 4) and a wall-resolved one with the elliptic relaxation solved
     every step (3,928 triangles, 32 per element). "er-chosen" runs the
     chosen form on the GPU instead (FP32 state, compensated FP32 statistics,
-    the lagged FE solve under the coarse check at 0.05) against the same
+    the lagged FE solve under the coarse check at the wall-resolved
+    workload's lag_tol, solved to its lag_cg_tol) against the same
     FP64 oracle with the FE solve every step. Per cell of a 6 x 4 grid
     and per statistic (<U>, <V>, <uu>, <vv>, <ww>, <uv>, k, <psi>, psi
     variance) z is the difference of the two ensemble means in standard
@@ -281,12 +282,14 @@ def test_multistep_cells_within_standard_errors_of_oracle(case):
         from paper_1003_4548_gb300 import Canyon
         gpu = []
         for i in range(M):
+            er_full = WORKLOADS["canyon_er_full"]
             g = Canyon(gpu_params(mesh, wall_model=wm, precision="fp32_kahan" if chosen else "fp64", C0=2.1,
-                                  seed=100 + i, cg_tol=1e-10, cg_maxit=20000, omega_wall=ow), mesh)
+                                  seed=100 + i, cg_tol=er_full["lag_cg_tol"] if chosen else 1e-10, cg_maxit=20000,
+                                  omega_wall=ow), mesh)
             g.seed_particles(ppe)
             g.estimate_stats()
             if chosen:
-                g.set_surrogate(5, None, None, 0.05)
+                g.set_surrogate(5, None, None, er_full["lag_tol"])
             g.step(dt, steps)
             g.sync()
             gpu.append(multiseed.cell_stats(g.field, mesh, nx, ny))
