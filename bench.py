@@ -1056,7 +1056,8 @@ def z_cells(A, B):
         out[q] = float(np.abs(z).max())
         allz.append(np.abs(z[ok]))
     allz = np.concatenate(allz)
-    return {"max_abs_z": float(allz.max()), "frac_above_3": float(np.mean(allz > 3)), "tests": int(allz.size),
+    return {"max_abs_z": float(allz.max()) if allz.size else 0.0,
+            "frac_above_3": float(np.mean(allz > 3)) if allz.size else 0.0, "tests": int(allz.size),
             "max_abs_z_per_stat": out, "cells_without_spread_differing": flat,
             "cells_with_values_below_fp32_normal_range": tiny}
 
@@ -1139,9 +1140,11 @@ def paired_bias(A, B):
         allt.append(np.abs(t[okd]))
         flat.append(r[ok])
     allt, flat = np.concatenate(allt), np.concatenate(flat)
-    return {"max_bias_in_se": float(flat.max()), "median_bias_in_se": float(np.median(flat)),
-            "max_bias_in_se_per_stat": bias, "max_abs_paired_t": float(allt.max()),
-            "frac_paired_t_above_3": float(np.mean(allt > 3)), "tests": int(allt.size),
+    # (pairs that agree exactly leave no paired t: their bias is 0)
+    return {"max_bias_in_se": float(flat.max()) if flat.size else 0.0,
+            "median_bias_in_se": float(np.median(flat)) if flat.size else 0.0,
+            "max_bias_in_se_per_stat": bias, "max_abs_paired_t": float(allt.max()) if allt.size else 0.0,
+            "frac_paired_t_above_3": float(np.mean(allt > 3)) if allt.size else 0.0, "tests": int(allt.size),
             "max_abs_paired_t_per_stat": tmax}
 
 
