@@ -420,8 +420,10 @@ def test_ragged_empty_and_tied_elements(wf_mesh, precision):
 
 @pytest.mark.parametrize("precision", ["fp32_kahan", "fp32"])
 def test_warp_class_sizes_and_crowded_buckets(wf_mesh, precision):
-    """Every particle count from 0 to 519 per element (the warp class holds up
-    to 512 particles in registers, 16 per lane), against the oracle. Some
+    """Every particle count from 0 to 519 per element (the warp kernels take
+    up to 512 particles: the bins kernel nine keys per lane in registers and
+    the rest in shared memory, the moments kernel blocks of eight keys per
+    lane; larger elements go to the block kernels), against the oracle. Some
     elements make a boundary bucket crowded or tie the boundary value:
     one velocity component constant over the element (every key in one
     bucket: bisection over the value bits, then the ids), half the
