@@ -1071,7 +1071,9 @@ def standard_error_study(cfg, mesh, dt, stream, sur, lag_tol=0.03, lag_cg_tol=No
     <uv>, k, <psi>, psi variance) of the two ensembles are compared cell by
     cell in standard errors of the difference of their means. Without a bias
     |z| follows Student's t with 2 x seeds - 2 degrees of freedom (about 1 % of
-    the tests above 3 for 8 seeds)."""
+    the tests above 3 for 8 seeds). The chosen form also runs on the FP64
+    runs' own seeds: the paired differences state its bias per cell in
+    standard errors of the FP64 ensemble's mean (paired_bias)."""
     lag = {"mode": 5, "params": None, "norm": None, "tol": lag_tol, "cg_tol": lag_cg_tol}
     forms = [("fp64_fe", "fp64", None, 1000), ("chosen_fp32_kahan_lagged_fe", "fp32_kahan", lag, 2000),
              ("fp32_kahan_fe", "fp32_kahan", None, 3000)]
